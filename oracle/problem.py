@@ -1,0 +1,116 @@
+"""Discrete impedance Helmholtz problem (oracle side; test infrastructure only).
+
+Continuous problem: -Delta u - k^2 u = f with d_n u - i k u = g on the boundary
+(Eq. (1) in 1D, Sec. 3.1 in 2D).  The paper discretises with Q1 finite elements;
+this build uses second-order finite differences on nodes x_i = i h, i = 0..S-1,
+h = 1/(n+1), S = n+2, with the impedance condition imposed through a ghost node
+eliminated by the centred difference of d_n u, and every row scaled by h^2 times
+the nodal weights w_i w_j (w = 1/2 on boundary nodes, 1 inside).  The scaling keeps
+the matrix complex symmetric (A = A^T), which the adjoint solves rely on.
+
+Row (i, j) (i along x, j along y):
+
+    (A u)_ij = w_j X_i(u_.j) + w_i Y_j(u_i.) - (kh)^2 w_i w_j u_ij
+               - i kh (w_j bx_i + w_i by_j) u_ij
+    b_ij     = h^2 w_i w_j f_ij + h (w_j gx_ij + w_i gy_ij)
+
+X is the second difference along x (2u_i - u_{i-1} - u_{i+1} inside, u_0 - u_1 and
+u_{S-1} - u_{S-2} at the ends), bx_i flags the two x-boundary nodes, and gx is the
+impedance datum of the x-side the node lies on; Y, by, gy likewise along y.  A 1D
+problem is the same formula with the x-direction absent (X = 0, w_x = 1, bx = 0).
+
+A subdomain operator A~_i (Eq. (2)) is the same formula on a band of rows
+[ra, rb): its first and last rows take the boundary treatment with zero impedance
+data, i.e. -(u' + iku) = 0 and (u' - iku) = 0 on the artificial boundary (Sec. 1).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def direction(n: int, present: bool = True):
+    """Line operator pieces for one direction of ``n`` nodes: (X, w, boundary flags).
+
+    X is the (halved-at-the-ends) second difference, w the nodal weights and the
+    flags mark the two end nodes.  An absent direction (1D problems) contributes
+    X = 0, w = 1 and no boundary term.
+    """
+    if not present:
+        return sp.csr_matrix((1, 1), dtype=np.float64), np.ones(1), np.zeros(1)
+    if n < 2:
+        raise ValueError("a present direction needs at least two nodes")
+    main = np.full(n, 2.0)
+    main[0] = main[-1] = 1.0
+    off = -np.ones(n - 1)
+    X = sp.diags([off, main, off], [-1, 0, 1], format="csr")
+    w = np.ones(n)
+    w[0] = w[-1] = 0.5
+    bnd = np.zeros(n)
+    bnd[0] = bnd[-1] = 1.0
+    return X, w, bnd
+
+
+def operator(kh: float, xdir, ydir) -> sp.csr_matrix:
+    """Assemble the weighted 5-point operator for a rectangle of nodes.
+
+    Unknowns are ordered row-major, index = j * Sx + i (x fastest), so Kronecker
+    products read kron(y-part, x-part).
+    """
+    Xx, wx, bx = xdir
+    Yy, wy, by = ydir
+    Wx, Wy = sp.diags(wx), sp.diags(wy)
+    A = (sp.kron(Wy, Xx) + sp.kron(Yy, Wx)
+         - (kh * kh) * sp.kron(Wy, Wx)
+         - 1j * kh * (sp.kron(Wy, sp.diags(bx)) + sp.kron(sp.diags(by), Wx)))
+    return sp.csr_matrix(A, dtype=np.complex128)
+
+
+class Problem:
+    """Grid and discrete operators for one impedance Helmholtz problem.
+
+    dim: 1 or 2.  n: interior nodes per side.  k: wavenumber.
+    Vectors are flattened row-major [S_y][S_x]; S_x = 1 in 1D.
+    """
+
+    def __init__(self, dim: int, n: int, k: float):
+        if dim not in (1, 2):
+            raise ValueError("dim must be 1 or 2")
+        self.dim, self.n, self.k = dim, n, float(k)
+        self.S = n + 2
+        self.h = 1.0 / (n + 1)
+        self.kh = self.k * self.h
+        self.Sy = self.S
+        self.Sx = self.S if dim == 2 else 1
+        self._xdir = direction(self.Sx, present=(dim == 2))
+
+    @property
+    def N(self) -> int:
+        return self.Sx * self.Sy
+
+    def band_operator(self, ra: int, rb: int) -> sp.csr_matrix:
+        """A~ on rows [ra, rb): impedance (Robin, zero data) rows at both band ends."""
+        return operator(self.kh, self._xdir, direction(rb - ra))
+
+    def A(self) -> sp.csr_matrix:
+        """The global operator A (the band covering every row)."""
+        return self.band_operator(0, self.Sy)
+
+    def rhs(self, f: np.ndarray, g: np.ndarray) -> np.ndarray:
+        """b = h^2 w_i w_j f + h (w_j gx + w_i gy), flattened row-major."""
+        h = self.h
+        _, wx, _ = self._xdir
+        _, wy, _ = direction(self.Sy)
+        f = np.asarray(f, dtype=np.complex128).reshape(self.Sy, self.Sx)
+        b = (h * h) * wy[:, None] * wx[None, :] * f
+        g = np.asarray(g, dtype=np.complex128)
+        if self.dim == 1:
+            b[0, 0] += h * g[0]
+            b[-1, 0] += h * g[1]
+        else:
+            g = g.reshape(4, self.S)
+            b[:, 0] += h * wy * g[0]        # side x = 0, indexed along y
+            b[:, -1] += h * wy * g[1]       # side x = 1
+            b[0, :] += h * wx * g[2]        # side y = 0, indexed along x
+            b[-1, :] += h * wx * g[3]       # side y = 1
+        return b.reshape(-1)

@@ -1,0 +1,164 @@
+"""Pins of the oracle's O-method (CPU only).
+
+Each test checks a fact the paper or the mathematics fixes, not the oracle's own
+formulas:
+
+* T1 (Sec. 1): with the full a-harmonic interface space the coarse-corrected ORAS
+  step from zero is exact -- in 1D with two vectors, in 2D with r = interface
+  dimension, and in the hierarchy when sub-solves are exact.
+* T2 (Sec. 3.1, Table 2 discussion): without coarse correction and with one
+  sub-level iteration, one hierarchical DD iteration equals one flat DD iteration.
+* T3/T9: manufactured solutions are recovered; the iteration's fixed point is A^{-1}b.
+* T6 (Sec. 2): with enough samples the randomised SVD reproduces the dense SVD of
+  the interface map formed column by column.
+* T7 (Sec. 2): <T x, y> = <x, T^* y> for the Euclidean inner product.
+* T8 (Sec. 1): Galerkin orthogonality C^H (f - A u) = 0 after the coarse step.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import direct
+from oracle.hierarchy import build_tree, interface_row, owned_in_parent
+from oracle.method import OMethod
+from oracle.problem import Problem
+from workloads import WORKLOADS, problem_inputs, random_complex
+
+
+def test_T1_1d_two_subdomains_one_step_exact():
+    w = WORKLOADS["helm1d_n1000_k20pi"]
+    P = Problem(1, w.n, w.k)
+    f, g = problem_inputs(w)
+    M = OMethod(P, w.levels, w.overlap, w.rank, w.oversample, seed=3)
+    assert M.tree[1].ra == 0 and M.tree[1].rb == 503
+    assert M.tree[2].ra == 499 and M.tree[2].rb == 1002
+    u1 = M.precondition(P.rhs(f, g))
+    assert direct.rel_err(u1, direct.solve(P, f, g)) < 1e-11
+    # without the coarse correction the one-step iterate is far from exact
+    M0 = OMethod(P, w.levels, w.overlap, 0, 0, seed=3)
+    assert direct.rel_err(M0.precondition(P.rhs(f, g)), direct.solve(P, f, g)) > 1e-3
+
+
+@pytest.mark.parametrize("levels,exact", [(1, False), (2, True), (3, True)])
+def test_T1_2d_full_interface_space_one_step_exact(levels, exact):
+    n = 26 if levels < 3 else 46
+    P = Problem(2, n, 11.0)
+    f = random_complex((P.S, P.S), 5)
+    g = random_complex((4, P.S), 6)
+    M = OMethod(P, levels, 2, P.S, 0, seed=9, exact_subsolves=exact)
+    u1 = M.precondition(P.rhs(f, g))
+    assert direct.rel_err(u1, direct.solve(P, f, g)) < 1e-10
+
+
+def _flat_oras_step(P, tree, r):
+    """Flat ORAS (no coarse space) over the leaves, by brute force per strip."""
+    u = np.zeros_like(r).reshape(P.Sy, P.Sx)
+    R = r.reshape(P.Sy, P.Sx)
+    for nd in tree:
+        if not nd.is_leaf:
+            continue
+        x = spla.spsolve(P.band_operator(nd.ra, nd.rb).tocsc(), R[nd.ra:nd.rb].reshape(-1))
+        x = x.reshape(nd.b, P.Sx)
+        u[nd.oa:nd.ob] = x[nd.oa - nd.ra:nd.ob - nd.ra]     # flat restricted prolongation
+    return u.reshape(-1)
+
+
+@pytest.mark.parametrize("dim,n,levels,overlap", [(2, 40, 2, 2), (2, 60, 3, 4), (1, 300, 3, 4)])
+def test_T2_hierarchical_equals_flat_without_coarse(dim, n, levels, overlap):
+    P = Problem(dim, n, 13.0)
+    r = random_complex((P.N,), 21)
+    M = OMethod(P, levels, overlap, 0, 0, n_inner=1)
+    z = M.precondition(r)
+    zf = _flat_oras_step(P, M.tree, r)
+    assert np.max(np.abs(z - zf)) <= 1e-12 * np.max(np.abs(zf))
+
+
+def test_T3_manufactured_solution_recovered():
+    P = Problem(2, 62, 14.0)
+    u_true = random_complex((P.N,), 33)
+    b = P.A() @ u_true
+    M = OMethod(P, 2, 2, 8, 6, seed=4)
+    u, it, hist = M.solve(b, tol=1e-12, maxit=200)
+    assert hist[-1] < 1e-12
+    assert direct.rel_err(u, u_true) < 1e-9
+    assert all(np.isfinite(hist))
+
+
+def test_T9_fixed_point_residual_decays_to_floor():
+    w = WORKLOADS["helm2d_n255_k40_L2"]
+    P = Problem(2, 63, 10.0)                       # same kh as the 255 / k = 40 case
+    f, _ = problem_inputs(w)
+    f = f[::4, ::4][:P.S, :P.S]
+    g = np.zeros((4, P.S), dtype=complex)
+    M = OMethod(P, 2, 2, 16, 10, seed=1)
+    u, it, hist = M.solve(P.rhs(f, g), tol=1e-13, maxit=300)
+    assert hist[-1] < 1e-13
+    assert direct.rel_err(u, direct.solve(P, f, g)) < 1e-10
+
+
+def _explicit_T(M, c):
+    I = np.eye(M.Sx, dtype=complex)
+    return M.T(c, I)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_T6_rsvd_equals_dense_svd_when_samples_cover(dim):
+    P = Problem(dim, 22 if dim == 2 else 80, 9.0)
+    Sx = P.Sx
+    M = OMethod(P, 1, 2, Sx, 0, seed=12)
+    for c in (1, 2):
+        T = _explicit_T(M, c)
+        s_dense = np.linalg.svd(T, compute_uv=False)
+        np.testing.assert_allclose(M.sigma[c], s_dense, rtol=1e-11, atol=1e-13 * s_dense[0])
+    # fewer modes: the leading subspace matches the dense one (clear spectral gap
+    # is not guaranteed, so compare the leading vector's span and the values)
+    M2 = OMethod(P, 1, 2, 3, Sx, seed=12)
+    T = _explicit_T(M2, 1)
+    _, s, Vh = np.linalg.svd(T)
+    np.testing.assert_allclose(M2.sigma[1][:3], s[:3], rtol=1e-10)
+    v = Vh.conj().T[:, :1]
+    proj = M2.V[1] @ (M2.V[1].conj().T @ v)
+    assert np.linalg.norm(proj - v) < 1e-8
+
+
+def test_T7_adjoint_identity_and_explicit_adjoint():
+    P = Problem(2, 24, 8.0)
+    M = OMethod(P, 2, 2, 4, 3, seed=2)
+    for c in (3, 4, 5, 6):                         # leaves: exact solves
+        x = random_complex((P.Sx, 2), 40 + c)
+        y = random_complex((P.Sx, 2), 50 + c)
+        lhs = np.vdot(y, M.T(c, x))
+        rhs = np.vdot(M.T_adjoint(c, y), x)
+        assert abs(lhs - rhs) <= 1e-13 * abs(lhs) + 1e-15
+        T = _explicit_T(M, c)
+        np.testing.assert_allclose(M.T_adjoint(c, y), T.conj().T @ y, rtol=1e-12, atol=1e-14)
+
+
+def test_T8_galerkin_orthogonality_and_symmetric_forms():
+    P = Problem(2, 30, 12.0)
+    M = OMethod(P, 1, 2, 6, 4, seed=8)
+    C = M.C[0].reshape(P.N, -1)
+    A = P.A()
+    np.testing.assert_allclose(M.Ac[0], (A.getH() @ C).conj().T @ C, rtol=1e-12, atol=1e-14)
+    r = random_complex((P.N,), 77)
+    z = M.coarse(0, r.reshape(P.Sy, P.Sx, 1)).reshape(-1)
+    resid = r - A @ z
+    assert np.linalg.norm(C.conj().T @ resid) < 1e-11 * np.linalg.norm(C.conj().T @ r)
+    # each child's block is supported on the rows it owns inside the parent
+    for j, c in enumerate(M.tree[0].children):
+        a, b = owned_in_parent(M.tree, M.tree[c])
+        Cc = M.C[0][:, :, j * M.r:(j + 1) * M.r]
+        assert np.all(Cc[:a] == 0) and np.all(Cc[b:] == 0)
+
+
+def test_hierarchy_layout():
+    tree = build_tree(257, 2, 2)
+    got = [(nd.id, nd.oa, nd.ob, nd.ra, nd.rb) for nd in tree]
+    assert got == [(0, 0, 257, 0, 257), (1, 0, 128, 0, 129), (2, 128, 257, 127, 257),
+                   (3, 0, 64, 0, 65), (4, 64, 128, 63, 129), (5, 128, 192, 127, 193),
+                   (6, 192, 257, 191, 257)]
+    assert [interface_row(tree, tree[c]) for c in (1, 2, 3, 4)] == [128, 127, 64, 63]
+    with pytest.raises(ValueError):
+        build_tree(20, 3, 4)
+    with pytest.raises(ValueError):
+        build_tree(100, 1, 3)

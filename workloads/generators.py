@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs for the impedance Helmholtz problem.
+
+The paper's experiments use synthetic data only: a random discrete solution with
+f = A u and zero initial guess (Sec. 3.1).  The workloads below follow the same
+idea; none needs a dataset.  Every array is complex128 and seeded; the layouts are
+the ones the library's C-ABI documents:
+
+* ``f``: ``[S_y][S_x]`` row-major (x fastest); 1D problems use ``[S]``.
+* ``g``: ``[4][S]`` impedance data per side, order x=0, x=1, y=0, y=1, each indexed
+  along its side; 1D problems use ``[2] = (g0, g1)``.
+
+Grid convention: ``n`` interior nodes per side plus the two impedance boundary
+nodes, so ``S = n + 2`` unknowns per side and ``h = 1 / (n + 1)``.
+
+This module contains no part of the solver: only random numbers and the
+closed-form inputs (Gaussian sources, plane waves) the tests feed to both sides.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BASE_SEED = 2512_12538
+
+
+def random_complex(shape, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Complex array with independent N(0, scale^2) real and imaginary parts."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    re = rng.standard_normal(shape)
+    im = rng.standard_normal(shape)
+    return (scale * (re + 1j * im)).astype(np.complex128)
+
+
+def point_source_rhs(n: int, seed: int, n_src: int = 8, width_h: float = 2.0) -> np.ndarray:
+    """Sum of ``n_src`` Gaussian point sources on the unit square, sampled on the grid.
+
+    f(x) = sum_s a_s exp(-|x - x_s|^2 / (2 sigma^2)) with sigma = width_h * h,
+    complex amplitudes a_s with N(0,1) real and imaginary parts and centres x_s
+    uniform in (0,1)^2.  Returns ``[S][S]`` complex128 (rows = y).
+    """
+    S = n + 2
+    h = 1.0 / (n + 1)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amp = rng.standard_normal(n_src) + 1j * rng.standard_normal(n_src)
+    ctr = rng.uniform(0.0, 1.0, size=(n_src, 2))
+    sigma = width_h * h
+    x = np.arange(S) * h
+    f = np.zeros((S, S), dtype=np.complex128)
+    for s in range(n_src):
+        gx = np.exp(-((x - ctr[s, 0]) ** 2) / (2 * sigma * sigma))
+        gy = np.exp(-((x - ctr[s, 1]) ** 2) / (2 * sigma * sigma))
+        f += amp[s] * np.outer(gy, gx)
+    return f
+
+
+def plane_wave_2d(n: int, k: float, theta: float):
+    """Continuous plane wave u = exp(i k (cos t x + sin t y)) with matching data.
+
+    Returns (u_exact [S][S], f = 0, g [4][S]) where g = d_n u - i k u on each side
+    (outward normals -x, +x, -y, +y).  The discrete solution converges to u at
+    second order, which pins the discretisation independently of its derivation.
+    """
+    S = n + 2
+    h = 1.0 / (n + 1)
+    x = np.arange(S) * h
+    kx, ky = k * math.cos(theta), k * math.sin(theta)
+    U = np.exp(1j * (kx * x[None, :] + ky * x[:, None]))
+    g = np.zeros((4, S), dtype=np.complex128)
+    # side x=0: points (0, y_j); d_n u = -u_x
+    g[0] = (-1j * kx - 1j * k) * np.exp(1j * ky * x)
+    # side x=1: points (1, y_j); d_n u = +u_x
+    g[1] = (1j * kx - 1j * k) * np.exp(1j * (kx + ky * x))
+    # side y=0: points (x_i, 0); d_n u = -u_y
+    g[2] = (-1j * ky - 1j * k) * np.exp(1j * kx * x)
+    # side y=1: points (x_i, 1); d_n u = +u_y
+    g[3] = (1j * ky - 1j * k) * np.exp(1j * (kx * x + ky))
+    return U, np.zeros((S, S), dtype=np.complex128), g
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One named synthetic workload: problem, method parameters and RHS recipe."""
+
+    name: str
+    dim: int
+    n: int
+    k: float
+    levels: int
+    overlap: int
+    rank: int
+    oversample: int
+    n_inner: int = 1
+    rhs: str = "point_sources"      # "point_sources" | "random"
+
+    @property
+    def S(self) -> int:
+        return self.n + 2
+
+    @property
+    def h(self) -> float:
+        return 1.0 / (self.n + 1)
+
+
+WORKLOADS = {
+    # 1D, n = 1000 interior points, k = 20 pi, two overlapping subdomains with
+    # 4 shared points, a-harmonic coarse space (one vector per subdomain).
+    "helm1d_n1000_k20pi": Workload("helm1d_n1000_k20pi", 1, 1000, 20 * math.pi, 1, 4, 1, 0,
+                                   rhs="random"),
+    # 2D 255x255 interior grid, k = 40, 2-level binary strip hierarchy
+    # (4 leaf strips), overlap 2 rows, sketch rank 16 with oversampling 10.
+    "helm2d_n255_k40_L2": Workload("helm2d_n255_k40_L2", 2, 255, 40.0, 2, 2, 16, 10),
+    # 2D 1023x1023, k = 100, 3-level hierarchy (8 leaf strips), overlap 4 rows,
+    # rank 32, oversampling 10.
+    "helm2d_n1023_k100_L3": Workload("helm2d_n1023_k100_L3", 2, 1023, 100.0, 3, 4, 32, 10),
+}
+
+
+def problem_inputs(w: Workload, index: int = 0):
+    """Seeded (f, g) for workload ``w``; ``index`` selects an independent draw."""
+    seed = BASE_SEED + 1000 * index + w.n
+    if w.dim == 1:
+        f = random_complex((w.S,), seed)
+        g = random_complex((2,), seed + 1)
+        return f, g
+    if w.rhs == "random":
+        f = random_complex((w.S, w.S), seed)
+    else:
+        f = point_source_rhs(w.n, seed)
+    g = np.zeros((4, w.S), dtype=np.complex128)
+    return f, g
