@@ -1,0 +1,175 @@
+/*
+ * hh.h -- C-ABI of the GB300 hierarchical ORAS Helmholtz library (libhh.so).
+ *
+ * Problem (Gander, Jiang & Zhang, "Hierarchical Coarse Basis by Randomised SVD: the
+ * Helmholtz Problem", Eq. (1) in 1D and Sec. 3.1 in 2D):
+ *
+ *     -Delta u - k^2 u = f  in (0,1)^d,     d_n u - i k u = g  on the boundary,
+ *
+ * discretised by second-order finite differences on S = n + 2 nodes per side
+ * (n interior nodes plus the two impedance boundary nodes, h = 1/(n+1)), rows scaled
+ * by h^2 and the nodal weights (1/2 on boundary nodes) so that A is complex symmetric.
+ * The solver is the hierarchical optimised restricted additive Schwarz iteration of
+ * Eqs. (2)-(3) over a binary hierarchy of row bands (Sec. 1), with coarse spaces built
+ * per level from a randomised SVD of the interface maps (Sec. 2).
+ *
+ * Conventions for every entry point below
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im) pairs of double ("complex128").
+ * - Grid vectors (f, u, b, residuals) are row-major [S_y][S_x], x fastest; a 1D
+ *   problem has S_x = 1 and S_y = S.  Multi-column node vectors are
+ *   [rows][S_x][ncols] with the column index fastest.
+ * - g (impedance data): 2D [4][S], sides x=0, x=1, y=0, y=1, each indexed along the
+ *   side; 1D [2] = (g0, g1) with -(u'+iku)(0) = g0 and (u'-iku)(1) = g1 (Eq. (1)).
+ * - Pointers named d_* are DEVICE pointers on the current CUDA device; pointers named
+ *   h_* are HOST pointers.  The caller owns every pointer it passes; the library never
+ *   frees them and keeps no reference after the call returns.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue their
+ *   work on it and return; calls that return host scalars or hh_stats synchronise it.
+ * - The library owns its factors, bases and work buffers.  It obtains them in one
+ *   block per handle from the allocator set by hh_set_allocator (default:
+ *   cudaMallocAsync/cudaFreeAsync on the handle's stream) and returns it in hh_destroy.
+ * - Errors are returned as hh_status; no call exits, traps or prints.  A handle is not
+ *   thread-safe: use one host thread and one stream per handle.
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HH_OK = 0,
+    HH_EINVAL = -1,       /* invalid parameter, pointer, node index or size            */
+    HH_ENOMEM = -2,       /* the allocator returned NULL                              */
+    HH_ENOCONV = -3,      /* max_iter reached or the residual stopped being finite;   */
+                          /* u holds the last iterate, stats the achieved residual    */
+    HH_EBREAKDOWN = -4,   /* zero pivot in a subdomain or coarse factorisation        */
+    HH_ETIMEOUT = -5,     /* a bounded device-side wait gave up                       */
+    HH_ECUDA = -6,        /* a CUDA runtime call failed                               */
+    HH_ENOTIMPL = -7
+} hh_status;
+
+typedef enum {
+    HH_PREC_FP64 = 0,     /* complex128 everywhere, FP64 CUDA-core arithmetic          */
+    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches and bases;  */
+                          /* FP64 residual, Galerkin matrices, their inverse and the   */
+                          /* sketch SVD; the outer iteration refines in FP64           */
+} hh_precision;
+
+typedef struct {
+    int dim;              /* 1 or 2                                                      */
+    int n;                /* interior nodes per side; S = n + 2, h = 1/(n+1); n >= 4     */
+    double k;             /* wavenumber k > 0 (Eq. (1))                                  */
+    int levels;           /* hierarchy depth L >= 1: 2^L leaf bands (Sec. 1)             */
+    int overlap;          /* rows shared by two siblings; even, >= 2; e = overlap/2 rows */
+                          /* added on each side of a non-overlapping split (Sec. 3)      */
+    int rank;             /* r: coarse vectors per child (n_c of Sec. 3), >= 1           */
+    int oversample;       /* p: extra random samples (Sec. 3 uses n_c + 5 samples)       */
+    int n_inner;          /* n_i: sub-level iterations (Sec. 3), >= 1                    */
+    double tol;           /* stop when ||b - A u||_2 < tol ||b||_2 (FP64)                */
+    int max_iter;         /* outer iterations, >= 1                                      */
+    int precision;        /* hh_precision                                                */
+    unsigned long long seed;  /* sketch generator seed                                  */
+} hh_params;
+
+typedef struct {
+    int iters;            /* outer iterations taken                                      */
+    double rel_res;       /* final ||b - A u|| / ||b|| (FP64)                            */
+    double t_setup_ms;    /* device time of hh_setup (CUDA events)                       */
+    double t_solve_ms;    /* device time of the last hh_solve                            */
+    size_t footprint_bytes;
+} hh_stats;
+
+typedef struct hh_handle hh_handle;
+
+/* Device allocator hook.  alloc(bytes, stream, ctx) returns device memory usable on
+ * `stream` or NULL; free_(ptr, bytes, stream, ctx) returns it.  Passing alloc = NULL
+ * restores the default.  Affects handles created afterwards. */
+hh_status hh_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
+                           void (*free_)(void* ptr, size_t bytes, void* stream, void* ctx),
+                           void* ctx);
+
+/* Host-only: device bytes hh_setup will allocate for these parameters (admission). */
+hh_status hh_footprint(const hh_params* params, size_t* bytes);
+
+/* Set-up (Sec. 1-2): build the hierarchy, factor every leaf band (block-tridiagonal
+ * Schur recursion S_j = D_j - L_j S_{j-1}^{-1} U_j over grid columns), sketch every
+ * interface map T_c by the randomised SVD, extend the leading right singular vectors
+ * into the coarse bases C_c = P_c A~_c^{-1} B_c^T V_c, and form and invert the Galerkin
+ * matrices A_c = C^H A~ C, children before parents.  Synchronises `stream`.
+ * Errors: HH_EINVAL (parameters; e.g. odd overlap, a band owning fewer than overlap+2
+ * rows, levels < 1), HH_ENOMEM, HH_EBREAKDOWN, HH_ECUDA. */
+hh_status hh_setup(const hh_params* params, void* stream, hh_handle** out,
+                   size_t* footprint_out);
+
+/* Solve A u = b(f, g) by the coarse-corrected ORAS iteration of Eqs. (2)-(3) from
+ * u = 0 until the FP64 relative residual is below params.tol.  d_f [S_y][S_x],
+ * d_g [4][S] (or [2]), d_u [S_y][S_x] complex128 device arrays.  Synchronises.
+ * Returns HH_ENOCONV (u = last iterate) if max_iter is reached. */
+hh_status hh_solve(hh_handle* h, const void* d_f, const void* d_g, void* d_u,
+                   void* stream, hh_stats* stats);
+
+/* Same as hh_solve with HOST arrays (pinned or pageable): copies f and g in, solves,
+ * copies u out, all on `stream`.  Synchronises. */
+hh_status hh_solve_host(hh_handle* h, const void* h_f, const void* h_g, void* h_u,
+                        void* stream, hh_stats* stats);
+
+/* ||b(f,g) - A u||_2 / ||b||_2 in FP64 (the stopping test of hh_solve).  Synchronises. */
+hh_status hh_residual(hh_handle* h, const void* d_f, const void* d_g, const void* d_u,
+                      void* stream, double* rel_res);
+
+void hh_destroy(hh_handle* h);
+const char* hh_status_string(hh_status s);
+
+/* --------------------------------------------------------------------------------
+ * Step-level entry points.  Each runs one step of the path on device arrays so that it
+ * can be checked on its own.  Nodes are numbered as in Sec. 1: root 0, children of i
+ * are 2i+1 and 2i+2.  Node vectors are complex128 [b_node][S_x][ncols] over the node's
+ * band of rows (hh_node_info).  Asynchronous on `stream` unless stated.
+ * -------------------------------------------------------------------------------- */
+
+/* info[0..9] = owned rows [oa, ob), region rows [ra, rb), level, parent, child0,
+ * child1, S_x, interface row (global row of the band's artificial boundary facing its
+ * sibling, -1 for the root).  Host-only. */
+hh_status hh_node_info(const hh_handle* h, int node, int info[10]);
+
+/* d_y = A~_node d_x for ncols columns (A for the root), the weighted 5-point operator
+ * with impedance rows on the band's artificial boundaries (Sec. 1, Sec. 2). */
+hh_status hh_apply_operator(hh_handle* h, int node, const void* d_x, void* d_y, int ncols,
+                            void* stream);
+
+/* d_x = A~_leaf^{-1} d_v by the leaf's block forward and backward substitution
+ * (the subdomain solves of Eq. (2)).  ncols >= 1 columns. */
+hh_status hh_leaf_solve(hh_handle* h, int leaf, const void* d_v, void* d_x, int ncols,
+                        void* stream);
+
+/* Interface map of child c (Sec. 2): adjoint = 0: d_out = T_c d_in; adjoint = 1:
+ * d_out = T_c^* d_in.  T_c = B_s A~_s R_s R_c^T M_c B_c^T with s the sibling and M_c the
+ * leaf solve (leaves) or n_i sub-level iterations (internal children); the adjoint of
+ * M_c is taken as conj o M_c o conj.  d_in, d_out: [S_x][ncols] complex128. */
+hh_status hh_interface_map(hh_handle* h, int child, int adjoint, const void* d_in,
+                           void* d_out, int ncols, void* stream);
+
+/* Copies child c's coarse modes V_c ([S_x][r] complex128) and the singular values of
+ * its sketch (r + p doubles, descending) to HOST arrays.  Synchronises. */
+hh_status hh_get_basis(hh_handle* h, int child, void* h_V, double* h_sigma);
+
+/* d_z = C_p A_c^{-1} C_p^H d_r on node p's band (Eq. (3)), one column. */
+hh_status hh_coarse_apply(hh_handle* h, int node, const void* d_r, void* d_z, void* stream);
+
+/* d_z = one coarse-corrected ORAS step from zero applied to the global residual d_r
+ * (Eqs. (2)-(3) with u^(n-1) = 0): the preconditioner of the outer iteration. */
+hh_status hh_precondition(hh_handle* h, const void* d_r, void* d_z, void* stream);
+
+/* Writes the counter-based complex Gaussian sketch of child c ([S_x][r+p]) used by
+ * the randomised SVD (SplitMix64 + Box-Muller, re/im ~ N(0, 1/2)). */
+hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HH_H */

@@ -1,0 +1,222 @@
+"""ctypes binding of libhh.so (the C-ABI declared in include/hh.h).
+
+Argument marshalling only: every function forwards to the C entry point of the same
+name.  Device arrays are passed as torch tensors (complex128, on the current CUDA
+device) or as raw integer pointers; streams default to torch's current stream.  There
+is no fallback: if the shared library is missing or cannot be loaded, import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhh.so")
+
+HH_OK, HH_EINVAL, HH_ENOMEM, HH_ENOCONV, HH_EBREAKDOWN, HH_ETIMEOUT, HH_ECUDA, HH_ENOTIMPL = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+HH_PREC_FP64, HH_PREC_MIXED = 0, 1
+
+
+class hh_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_double),
+                ("levels", ctypes.c_int), ("overlap", ctypes.c_int), ("rank", ctypes.c_int),
+                ("oversample", ctypes.c_int), ("n_inner", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong)]
+
+
+class hh_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class HHError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2512_12538_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "hh_set_allocator": (i, [vp, vp, vp]),
+        "hh_footprint": (i, [P(hh_params), P(sz)]),
+        "hh_setup": (i, [P(hh_params), vp, P(vp), P(sz)]),
+        "hh_solve": (i, [vp, vp, vp, vp, vp, P(hh_stats)]),
+        "hh_solve_host": (i, [vp, vp, vp, vp, vp, P(hh_stats)]),
+        "hh_residual": (i, [vp, vp, vp, vp, vp, P(d)]),
+        "hh_destroy": (None, [vp]),
+        "hh_status_string": (ctypes.c_char_p, [i]),
+        "hh_node_info": (i, [vp, i, P(i)]),
+        "hh_apply_operator": (i, [vp, i, vp, vp, i, vp]),
+        "hh_leaf_solve": (i, [vp, i, vp, vp, i, vp]),
+        "hh_interface_map": (i, [vp, i, i, vp, vp, i, vp]),
+        "hh_get_basis": (i, [vp, i, vp, P(d)]),
+        "hh_coarse_apply": (i, [vp, i, vp, vp, vp]),
+        "hh_precondition": (i, [vp, vp, vp, vp]),
+        "hh_sketch_samples": (i, [vp, i, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def status_string(s: int) -> str:
+    return LIB.hh_status_string(int(s)).decode()
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(st: int, where: str, ok=(HH_OK,)):
+    if st not in ok:
+        raise HHError(st, where)
+    return st
+
+
+def make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, n_inner=1,
+                tol=1e-10, max_iter=200, precision=HH_PREC_FP64, seed=0) -> hh_params:
+    if isinstance(precision, str):
+        precision = {"fp64": HH_PREC_FP64, "mixed": HH_PREC_MIXED}[precision]
+    return hh_params(dim, n, float(k), levels, overlap, rank, oversample, n_inner, float(tol), max_iter,
+                     precision, seed)
+
+
+# ------------------------------------------------------------------ allocator hook
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_keep = []
+
+
+def use_torch_allocator() -> None:
+    """Route the library's device allocations through torch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_T(_alloc), _FREE_T(_free)
+    _keep[:] = [a, f]
+    _check(LIB.hh_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None),
+           "hh_set_allocator")
+
+
+def hh_set_allocator(alloc=None, free=None, ctx=None) -> int:
+    return _check(LIB.hh_set_allocator(alloc, free, ctx), "hh_set_allocator")
+
+
+# ------------------------------------------------------------------- entry points
+def hh_footprint(params: hh_params) -> int:
+    b = ctypes.c_size_t()
+    _check(LIB.hh_footprint(ctypes.byref(params), ctypes.byref(b)), "hh_footprint")
+    return b.value
+
+
+def hh_setup(params: hh_params, stream=None):
+    """Returns (handle, footprint_bytes).  Raises HHError on failure."""
+    h = ctypes.c_void_p()
+    fp = ctypes.c_size_t()
+    _check(LIB.hh_setup(ctypes.byref(params), _stream(stream), ctypes.byref(h), ctypes.byref(fp)), "hh_setup")
+    return h, fp.value
+
+
+def hh_solve(h, f, g, u, stream=None, allow_noconv=False) -> hh_stats:
+    st = hh_stats()
+    ok = (HH_OK, HH_ENOCONV) if allow_noconv else (HH_OK,)
+    _check(LIB.hh_solve(h, _ptr(f), _ptr(g), _ptr(u), _stream(stream), ctypes.byref(st)), "hh_solve", ok)
+    return st
+
+
+def hh_solve_host(h, f_host, g_host, u_host, stream=None, allow_noconv=False) -> hh_stats:
+    """Host arrays: numpy complex128 (C-contiguous) or CPU torch tensors."""
+    def hp(a):
+        if hasattr(a, "ctypes"):
+            return a.ctypes.data
+        return a.data_ptr()
+    st = hh_stats()
+    ok = (HH_OK, HH_ENOCONV) if allow_noconv else (HH_OK,)
+    _check(LIB.hh_solve_host(h, hp(f_host), hp(g_host), hp(u_host), _stream(stream), ctypes.byref(st)),
+           "hh_solve_host", ok)
+    return st
+
+
+def hh_residual(h, f, g, u, stream=None) -> float:
+    r = ctypes.c_double()
+    _check(LIB.hh_residual(h, _ptr(f), _ptr(g), _ptr(u), _stream(stream), ctypes.byref(r)), "hh_residual")
+    return r.value
+
+
+def hh_destroy(h) -> None:
+    LIB.hh_destroy(h)
+
+
+def hh_node_info(h, node: int) -> dict:
+    a = (ctypes.c_int * 10)()
+    _check(LIB.hh_node_info(h, node, a), "hh_node_info")
+    keys = ["oa", "ob", "ra", "rb", "level", "parent", "child0", "child1", "Sx", "ifrow"]
+    return dict(zip(keys, list(a)))
+
+
+def hh_apply_operator(h, node, x, y, ncols, stream=None) -> None:
+    _check(LIB.hh_apply_operator(h, node, _ptr(x), _ptr(y), ncols, _stream(stream)), "hh_apply_operator")
+
+
+def hh_leaf_solve(h, leaf, v, x, ncols, stream=None) -> None:
+    _check(LIB.hh_leaf_solve(h, leaf, _ptr(v), _ptr(x), ncols, _stream(stream)), "hh_leaf_solve")
+
+
+def hh_interface_map(h, child, adjoint, x, y, ncols, stream=None) -> None:
+    _check(LIB.hh_interface_map(h, child, int(adjoint), _ptr(x), _ptr(y), ncols, _stream(stream)),
+           "hh_interface_map")
+
+
+def hh_get_basis(h, child, V_host=None, sigma_host=None) -> None:
+    vp = V_host.ctypes.data if V_host is not None else None
+    sp = sigma_host.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if sigma_host is not None else None
+    _check(LIB.hh_get_basis(h, child, vp, sp), "hh_get_basis")
+
+
+def hh_coarse_apply(h, node, r, z, stream=None) -> None:
+    _check(LIB.hh_coarse_apply(h, node, _ptr(r), _ptr(z), _stream(stream)), "hh_coarse_apply")
+
+
+def hh_precondition(h, r, z, stream=None) -> None:
+    _check(LIB.hh_precondition(h, _ptr(r), _ptr(z), _stream(stream)), "hh_precondition")
+
+
+def hh_sketch_samples(h, child, out, stream=None) -> None:
+    _check(LIB.hh_sketch_samples(h, child, _ptr(out), _stream(stream)), "hh_sketch_samples")

@@ -1,0 +1,136 @@
+// hh_core.cuh -- shared device/host helpers of the CUDA path: complex arithmetic,
+// the discrete operator's row coefficients, error flags, bounded mbarrier waits and
+// 1D bulk (TMA) copies.  Included by every translation unit of libhh.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HH_HD __host__ __device__ __forceinline__
+
+// ------------------------------------------------------------------ complex numbers
+template <typename T>
+struct alignas(2 * sizeof(T)) cplx {
+    T re, im;
+};
+using c64 = cplx<float>;
+using c128 = cplx<double>;
+
+template <typename T> HH_HD cplx<T> mk(T r, T i) { return cplx<T>{r, i}; }
+template <typename T> HH_HD cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> HH_HD cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> HH_HD cplx<T> operator-(cplx<T> a) { return {-a.re, -a.im}; }
+template <typename T> HH_HD cplx<T> operator*(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> HH_HD cplx<T> operator*(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> HH_HD cplx<T> conj(cplx<T> a) { return {a.re, -a.im}; }
+template <typename T> HH_HD T abs2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
+// acc += a * b
+template <typename T> HH_HD void cfma(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+    acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+    acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+// acc += conj(a) * b
+template <typename T> HH_HD void cfma_cj(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+    acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+    acc.im = fma(a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+template <typename T> HH_HD cplx<T> cinv(cplx<T> a) {
+    T d = a.re * a.re + a.im * a.im;
+    return {a.re / d, -a.im / d};
+}
+template <typename D, typename S> HH_HD cplx<D> cvt(cplx<S> a) { return {(D)a.re, (D)a.im}; }
+
+// ------------------------------------------------------------- discrete operator
+// Weighted 5-point operator on a band of `b` rows and Sx columns (Sx == 1: 1D):
+//   (A u)_ij = w_j X_i(u_.j) + w_i Y_j(u_i.) - (kh)^2 w_i w_j u_ij
+//              - i kh (w_j bx_i + w_i by_j) u_ij,
+// with w = 1/2 on the band's first/last row and on x = 0, Sx-1 (1 elsewhere), X and Y
+// the second differences halved at the ends, bx/by the boundary flags.  A 1D band has
+// no x-direction: X = 0, w_i = 1, bx = 0.  Every band edge carries the impedance row
+// (zero data on artificial boundaries).
+struct OpGeom {
+    int b;        // rows in the band
+    int Sx;       // columns
+    double kh;    // k * h
+};
+
+HH_HD double wrow(int j, int b) { return (j == 0 || j == b - 1) ? 0.5 : 1.0; }
+HH_HD double wcol(int i, int Sx) { return Sx == 1 ? 1.0 : ((i == 0 || i == Sx - 1) ? 0.5 : 1.0); }
+
+// Diagonal coefficient of row (j, i) and the off-diagonal weights.
+HH_HD c128 op_diag(int j, int i, const OpGeom& g) {
+    const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+    const bool by = (j == 0 || j == g.b - 1);
+    const double cy = by ? 1.0 : 2.0;
+    double cx = 0.0, bx = 0.0;
+    if (g.Sx > 1) {
+        const bool xb = (i == 0 || i == g.Sx - 1);
+        cx = xb ? 1.0 : 2.0;
+        bx = xb ? 1.0 : 0.0;
+    }
+    const double re = wj * cx + wi * cy - g.kh * g.kh * wi * wj;
+    const double im = -g.kh * (wj * bx + wi * (by ? 1.0 : 0.0));
+    return {re, im};
+}
+
+// ------------------------------------------------------------------ error reporting
+// Device-side status word (per process): kernels record the first failure here and
+// the host reads it after synchronising.  Codes mirror hh_status.
+enum DevErr : int { DEV_OK = 0, DEV_BREAKDOWN = 1, DEV_TIMEOUT = 2, DEV_BADARG = 3 };
+
+// ----------------------------------------------------------- mbarrier + bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: returns false if the phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+// 1D bulk copy global -> shared (TMA engine), completion signalled on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// --------------------------------------------------------------------- reductions
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T> __device__ __forceinline__ cplx<T> warp_sum(cplx<T> v) {
+    v.re = warp_sum(v.re);
+    v.im = warp_sum(v.im);
+    return v;
+}
+
+HH_HD size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -1,0 +1,799 @@
+// hh_solver.cu -- host driver and C-ABI of libhh.
+//
+// Method (Gander, Jiang & Zhang): hierarchical ORAS with randomised-SVD coarse spaces.
+//  * Hierarchy (Sec. 1): binary bands of grid rows, node i has children 2i+1, 2i+2;
+//    a node owning rows [oa, ob) splits at mid = oa + (ob-oa)/2, every non-root region
+//    is its owned rows extended by e = overlap/2 rows each side (Sec. 3), clipped; the
+//    first child owns [parent.ra, mid) inside its parent, the second [mid, parent.rb).
+//  * Sub-level solve M_p (Sec. 1, Sec. 3 "n_i"): n_i iterations from zero of
+//        w~ = w + sum_c P_c M_c R_c (v - A~_p w)          (Eq. (2))
+//        w  = w~ + C_p A_c^{-1} C_p^H (v - A~_p w~)         (Eq. (3))
+//    with exact leaf solves.  The outer iteration is the same step at the root in FP64:
+//        u <- u + M_root(b - A u) until ||b - A u|| < tol ||b||.
+//  * Coarse space of p (Sec. 2): for each child c, randomised SVD of the interface map
+//    T_c = B_s A~_s R_s R_c^T M_c B_c^T (s = sibling), V_c = leading right singular
+//    vectors, C_c = P_c M_c B_c^T V_c, A_c = C_p^H A~_p C_p, children before parents.
+//
+// Every level is processed in batch: all nodes of a level run each step together.
+// Storage: node vectors [rows][Sx][ncols] (column index fastest); a child's input is a
+// contiguous row window of its parent's residual buffer.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "../../include/hh.h"
+#include "kernels.h"
+
+namespace hh {
+
+// ----------------------------------------------------------------- allocator hook
+struct AllocHook {
+    void* (*alloc)(size_t, void*, void*) = nullptr;
+    void (*free_)(void*, size_t, void*, void*) = nullptr;
+    void* ctx = nullptr;
+};
+static AllocHook g_alloc;
+
+static void* dev_alloc(size_t bytes, cudaStream_t s, const AllocHook& a) {
+    if (a.alloc) return a.alloc(bytes, (void*)s, a.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+    return p;
+}
+static void dev_free(void* p, size_t bytes, cudaStream_t s, const AllocHook& a) {
+    if (!p) return;
+    if (a.alloc) {
+        if (a.free_) a.free_(p, bytes, (void*)s, a.ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------------- hierarchy
+struct Node {
+    int id = 0, level = 0, oa = 0, ob = 0, ra = 0, rb = 0, parent = -1;
+    int child[2] = {-1, -1};
+    int own_a = 0, own_b = 0;   // rows owned inside the parent's region (global)
+    int ifrow = -1;             // artificial boundary row facing the sibling (global)
+    int inward = -1;            // the row next to ifrow, inside the band
+    int sib = -1;
+    int b() const { return rb - ra; }
+    bool leaf() const { return child[0] < 0; }
+};
+
+static hh_status build_tree(int S, int L, int e, std::vector<Node>& nodes) {
+    nodes.assign((size_t)(1 << (L + 1)) - 1, Node());
+    nodes[0].ob = S;
+    nodes[0].rb = S;
+    for (int id = 0; id < (1 << L) - 1; ++id) {
+        Node& p = nodes[id];
+        const int mid = p.oa + (p.ob - p.oa) / 2;
+        for (int k = 0; k < 2; ++k) {
+            const int cid = 2 * id + 1 + k;
+            Node& c = nodes[cid];
+            c.id = cid;
+            c.level = p.level + 1;
+            c.parent = id;
+            c.oa = k ? mid : p.oa;
+            c.ob = k ? p.ob : mid;
+            if (c.ob - c.oa < 2 * e + 2) return HH_EINVAL;
+            c.ra = std::max(0, c.oa - e);
+            c.rb = std::min(S, c.ob + e);
+            c.own_a = k ? mid : p.ra;
+            c.own_b = k ? p.rb : mid;
+            c.ifrow = k ? c.ra : c.rb - 1;
+            c.inward = k ? c.ra + 1 : c.rb - 2;
+            c.sib = 2 * id + 2 - k;
+            p.child[k] = cid;
+        }
+    }
+    return HH_OK;
+}
+
+static hh_status validate(const hh_params* P) {
+    if (!P) return HH_EINVAL;
+    if (P->dim != 1 && P->dim != 2) return HH_EINVAL;
+    if (P->n < 4 || P->n > 1 << 20) return HH_EINVAL;
+    if (!(P->k > 0.0) || !std::isfinite(P->k)) return HH_EINVAL;
+    if (P->levels < 1 || P->levels > 10) return HH_EINVAL;
+    if (P->overlap < 2 || (P->overlap & 1)) return HH_EINVAL;
+    if (P->rank < 1 || P->oversample < 0 || P->n_inner < 1) return HH_EINVAL;
+    if (!(P->tol > 0.0) || P->max_iter < 1) return HH_EINVAL;
+    if (P->precision != HH_PREC_FP64 && P->precision != HH_PREC_MIXED) return HH_EINVAL;
+    const int Sx = P->dim == 2 ? P->n + 2 : 1;
+    const int m = std::min(P->rank + P->oversample, Sx);
+    if (2 * std::min(P->rank, m) > 64 || m > 64) return HH_EINVAL;   // dense coarse kernels
+    std::vector<Node> nodes;
+    return build_tree(P->n + 2, P->levels, P->overlap / 2, nodes);
+}
+
+// ----------------------------------------------------------------- arena planning
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class X> X* take(size_t count) {
+        off = align_up(off, 256);
+        X* p = base ? (X*)(base + off) : nullptr;
+        off += sizeof(X) * std::max<size_t>(count, 1);
+        return p;
+    }
+};
+
+static inline cudaError_t ck(cudaError_t e, cudaError_t& first) {
+    if (e != cudaSuccess && first == cudaSuccess) first = e;
+    return e;
+}
+
+static const int MAX_PART_BLOCKS = 304;   // 2 x 152 SMs
+
+struct SolverBase {
+    hh_params P{};
+    AllocHook hook;
+    void* block = nullptr;
+    size_t footprint = 0;
+    cudaStream_t stream = nullptr;
+    double t_setup_ms = 0.0, t_solve_ms = 0.0;
+    virtual ~SolverBase() {}
+    virtual size_t plan(char* base) = 0;
+    virtual hh_status setup() = 0;
+    virtual hh_status solve(const c128* f, const c128* g, c128* u, hh_stats* st) = 0;
+    virtual hh_status residual(const c128* f, const c128* g, const c128* u, double* rel) = 0;
+    virtual hh_status node_info(int node, int info[10]) const = 0;
+    virtual hh_status apply_operator(int node, const c128* x, c128* y, int nc) = 0;
+    virtual hh_status leaf_solve(int leaf, const c128* v, c128* x, int nc) = 0;
+    virtual hh_status interface_map(int child, int adj, const c128* in, c128* out, int nc) = 0;
+    virtual hh_status get_basis(int child, void* hV, double* hsig) = 0;
+    virtual hh_status coarse_apply(int node, const c128* r, c128* z) = 0;
+    virtual hh_status precondition(const c128* r, c128* z) = 0;
+    virtual hh_status sketch_samples(int child, c128* out) = 0;
+    virtual c128* staging_f() = 0;
+    virtual c128* staging_g() = 0;
+    virtual c128* iterate() = 0;
+    virtual int npoints() const = 0;
+};
+
+template <typename T>
+struct Solver final : SolverBase {
+    using CT = cplx<T>;
+    int S = 0, Sx = 0, Sy = 0, L = 0, e = 0, m = 0, r = 0, nmax = 0, nn = 0;
+    double h = 0, kh = 0;
+    std::vector<Node> nodes;
+    std::vector<std::vector<int>> lev;
+    // device buffers
+    std::vector<CT*> W, R, Vs, C, X, Om, Z, Vc;
+    std::vector<c128*> Ainv, ycoef, Gm, U;
+    std::vector<double*> lam;
+    std::vector<int> ldx;
+    c128 *u = nullptr, *ut = nullptr, *bvec = nullptr, *res = nullptr, *gbuf = nullptr;
+    CT* RT = nullptr;
+    c128* partial = nullptr;
+    double *npart = nullptr, *dnorm = nullptr;
+    int* derr = nullptr;
+    LeafTask *d_tasks_view = nullptr, *d_tasks_own = nullptr, *d_task_one = nullptr;
+    void** d_ptrs = nullptr;
+    double* h_norm = nullptr;   // pinned host
+    int b_max = 0;
+    cudaError_t cerr = cudaSuccess;
+
+    ~Solver() override {
+        if (h_norm) cudaFreeHost(h_norm);
+        if (block) dev_free(block, footprint, stream, hook);
+        if (stream) cudaStreamSynchronize(stream);
+    }
+
+    OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh}; }
+    size_t pts(int id) const { return (size_t)nodes[id].b() * Sx; }
+    size_t row_off(int id, int grow, int nc) const { return (size_t)(grow - nodes[id].ra) * Sx * nc; }
+
+    void init_geometry() {
+        S = P.n + 2;
+        Sy = S;
+        Sx = P.dim == 2 ? S : 1;
+        h = 1.0 / (P.n + 1);
+        kh = P.k * h;
+        L = P.levels;
+        e = P.overlap / 2;
+        m = std::min(P.rank + P.oversample, Sx);
+        r = std::min(P.rank, m);
+        nmax = std::max(m, 1);
+        build_tree(S, L, e, nodes);
+        nn = (int)nodes.size();
+        lev.assign(L + 1, {});
+        for (auto& nd : nodes) lev[nd.level].push_back(nd.id);
+        b_max = 0;
+        for (auto& nd : nodes)
+            if (nd.leaf()) b_max = std::max(b_max, nd.b());
+    }
+
+    size_t plan(char* base) override {
+        Arena a;
+        a.base = base;
+        W.assign(nn, nullptr); R.assign(nn, nullptr); Vs.assign(nn, nullptr); C.assign(nn, nullptr);
+        X.assign(nn, nullptr); Om.assign(nn, nullptr); Z.assign(nn, nullptr); Vc.assign(nn, nullptr);
+        Ainv.assign(nn, nullptr); ycoef.assign(nn, nullptr); Gm.assign(nn, nullptr); U.assign(nn, nullptr);
+        lam.assign(nn, nullptr); ldx.assign(nn, 0);
+        const size_t N = (size_t)Sy * Sx;
+        u = a.take<c128>(N); ut = a.take<c128>(N); bvec = a.take<c128>(N); res = a.take<c128>(N);
+        gbuf = a.take<c128>(4 * (size_t)S);
+        RT = a.take<CT>(N * nmax);
+        for (auto& nd : nodes) {
+            const int id = nd.id;
+            const size_t np = pts(id);
+            if (id != 0) {
+                W[id] = a.take<CT>(np * nmax);
+                Vs[id] = a.take<CT>(np * nmax);
+                Om[id] = a.take<CT>((size_t)Sx * nmax);
+                Z[id] = a.take<CT>((size_t)Sx * nmax);
+                Vc[id] = a.take<CT>((size_t)Sx * std::max(r, 1));
+                Gm[id] = a.take<c128>((size_t)m * m);
+                U[id] = a.take<c128>((size_t)m * m);
+                lam[id] = a.take<double>(m);
+            }
+            if (!nd.leaf()) {
+                if (id != 0) R[id] = a.take<CT>(np * nmax);
+                C[id] = a.take<CT>(np * 2 * r);
+                Ainv[id] = a.take<c128>((size_t)4 * r * r);
+                ycoef[id] = a.take<c128>((size_t)2 * r * nmax);
+            } else {
+                ldx[id] = leaf_ldx(nd.b(), (int)sizeof(CT));
+                X[id] = a.take<CT>(Sx == 1 ? (size_t)nd.b() : (size_t)Sx * nd.b() * ldx[id]);
+            }
+        }
+        R[0] = RT;
+        partial = a.take<c128>((size_t)MAX_PART_BLOCKS * 64 * 64);
+        npart = a.take<double>(2048);
+        dnorm = a.take<double>(4);
+        derr = a.take<int>(4);
+        const int nleaf = 1 << L;
+        d_tasks_view = a.take<LeafTask>(nleaf);
+        d_tasks_own = a.take<LeafTask>(nleaf);
+        d_task_one = a.take<LeafTask>(1);
+        d_ptrs = a.take<void*>(3 * 64);
+        return align_up(a.off, 256);
+    }
+
+    // ------------------------------------------------------------- small helpers
+    bool sync_check(hh_status& st) {
+        ck(cudaGetLastError(), cerr);
+        ck(cudaStreamSynchronize(stream), cerr);
+        if (cerr != cudaSuccess) { st = HH_ECUDA; return false; }
+        int e2 = 0;
+        ck(cudaMemcpy(&e2, derr, sizeof(int), cudaMemcpyDeviceToHost), cerr);
+        if (e2 == DEV_BREAKDOWN) { st = HH_EBREAKDOWN; return false; }
+        if (e2 == DEV_TIMEOUT) { st = HH_ETIMEOUT; return false; }
+        if (e2 == DEV_BADARG) { st = HH_EINVAL; return false; }
+        st = HH_OK;
+        return true;
+    }
+    void zero(void* p, size_t bytes) { ck(cudaMemsetAsync(p, 0, bytes, stream), cerr); }
+    void d2d(void* dst, const void* src, size_t bytes) {
+        ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream), cerr);
+    }
+
+    std::vector<LeafTask> leaf_tasks(bool own) const {
+        std::vector<LeafTask> t;
+        for (int id : lev[L]) {
+            const Node& nd = nodes[id];
+            LeafTask k;
+            k.X = X[id];
+            k.W = W[id];
+            k.b = nd.b();
+            k.ldx = ldx[id];
+            if (own) k.F = Vs[id];
+            else k.F = R[nd.parent] + (size_t)(nd.ra - nodes[nd.parent].ra) * Sx * 0;  // fixed per call
+            t.push_back(k);
+        }
+        return t;
+    }
+    // The view tasks depend on the column count (row stride = Sx * nc).
+    void upload_view_tasks(int nc) {
+        std::vector<LeafTask> t;
+        for (int id : lev[L]) {
+            const Node& nd = nodes[id];
+            LeafTask k;
+            k.X = X[id];
+            k.W = W[id];
+            k.b = nd.b();
+            k.ldx = ldx[id];
+            k.F = R[nd.parent] + row_off(nd.parent, nd.ra, nc);
+            t.push_back(k);
+        }
+        ck(cudaMemcpyAsync(d_tasks_view, t.data(), sizeof(LeafTask) * t.size(), cudaMemcpyHostToDevice, stream),
+           cerr);
+    }
+    int view_nc = -1;
+
+    // Input of node id at the top level of an apply: its own buffer or a view into
+    // the parent's residual.
+    const CT* input(int id, int nc, bool own) const {
+        if (own) return Vs[id];
+        const int p = nodes[id].parent;
+        return R[p] + row_off(p, nodes[id].ra, nc);
+    }
+
+    // ------------------------------------------------- sub-level solve M at level l
+    void apply_M(int l, int nc, bool own) {
+        if (l == L) {
+            if (own) {
+                launch_sweep<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, nc, derr, stream);
+            } else {
+                if (view_nc != nc) { upload_view_tasks(nc); view_nc = nc; }
+                launch_sweep<T>(d_tasks_view, (int)lev[L].size(), b_max, Sx, nc, derr, stream);
+            }
+            return;
+        }
+        for (int it = 0; it < P.n_inner; ++it) {
+            for (int p : lev[l]) {
+                const CT* vin = input(p, nc, own);
+                if (it == 0) d2d(R[p], vin, sizeof(CT) * pts(p) * nc);
+                else launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
+            }
+            apply_M(l + 1, nc, false);
+            for (int p : lev[l]) {
+                for (int c : nodes[p].child) {
+                    const Node& cn = nodes[c];
+                    const size_t n = (size_t)(cn.own_b - cn.own_a) * Sx * nc;
+                    launch_copy<T, T>(W[c] + row_off(c, cn.own_a, nc), W[p] + row_off(p, cn.own_a, nc), n, it > 0,
+                                      false, stream);
+                }
+                coarse_correct(p, input(p, nc, own), nc);
+            }
+        }
+    }
+
+    // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
+    void coarse_correct(int p, const CT* vin, int nc) {
+        launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
+        const int nb = launch_ip_partial<T, T>(C[p], 2 * r, R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
+                                               stream);
+        launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
+        launch_coarse_update<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
+    }
+
+    // ------------------------------------------------------------------ set-up
+    void sketch_level(int l) {   // children at level l of the nodes at level l-1
+        const std::vector<int>& cs = lev[l];
+        // Y = T_c Omega
+        for (int c : cs) {
+            const Node& cn = nodes[c];
+            launch_sketch<T>(Om[c], Sx, m, c, P.seed, stream);
+            zero(Vs[c], sizeof(CT) * pts(c) * m);
+            d2d(Vs[c] + row_off(c, cn.ifrow, m), Om[c], sizeof(CT) * Sx * m);
+        }
+        apply_M(l, m, true);
+        for (int c : cs) {
+            const Node& cn = nodes[c];
+            const Node& sn = nodes[cn.sib];
+            launch_robin_trace<T>(W[c] + row_off(c, sn.ifrow, m), W[c] + row_off(c, sn.inward, m), Om[c], sn.b(), Sx,
+                                  m, kh, stream);
+        }
+        // Q = orth(Y)
+        std::vector<CT*> ys;
+        for (int c : cs) ys.push_back(Om[c]);
+        launch_qr<T>(ys.data(), (int)ys.size(), Sx, m, (CT**)d_ptrs, stream);
+        // Z = T_c^* Q = B_c conj(M_c conj(A~_s B_s^T ... )) ; here as conj(M_c(A~_s B_s^T conj Q))
+        for (int c : cs) {
+            const Node& cn = nodes[c];
+            const Node& sn = nodes[cn.sib];
+            zero(Vs[c], sizeof(CT) * pts(c) * m);
+            launch_adjoint_place<T>(Om[c], Vs[c] + row_off(c, sn.ifrow, m), Vs[c] + row_off(c, sn.inward, m), sn.b(),
+                                    Sx, m, kh, stream);
+        }
+        apply_M(l, m, true);
+        for (int c : cs)
+            launch_copy<T, T>(W[c] + row_off(c, nodes[c].ifrow, m), Z[c], (size_t)Sx * m, false, true, stream);
+        // SVD of Z^H = Q^H T: Gram Z^H Z (FP64), Hermitian Jacobi, V = Z U Sigma^{-1}
+        for (int c : cs) {
+            const int nb = launch_ip_partial<T, T>(Z[c], m, Z[c], m, Sx, m, m, partial, MAX_PART_BLOCKS, stream);
+            launch_ip_reduce(partial, nb, m, m, Gm[c], nullptr, nullptr, stream);
+        }
+        std::vector<c128*> gs, us;
+        std::vector<double*> ls;
+        for (int c : cs) { gs.push_back(Gm[c]); us.push_back(U[c]); ls.push_back(lam[c]); }
+        launch_jacobi(gs.data(), us.data(), ls.data(), (int)cs.size(), m, d_ptrs, stream);
+        for (int c : cs) launch_form_v<T>(Z[c], U[c], lam[c], Vc[c], Sx, m, r, stream);
+        // C_c = P_c M_c B_c^T V_c
+        for (int c : cs) {
+            zero(Vs[c], sizeof(CT) * pts(c) * r);
+            d2d(Vs[c] + row_off(c, nodes[c].ifrow, r), Vc[c], sizeof(CT) * Sx * r);
+        }
+        apply_M(l, r, true);
+        for (int p : lev[l - 1]) {
+            zero(C[p], sizeof(CT) * pts(p) * 2 * r);
+            for (int k = 0; k < 2; ++k) {
+                const int c = nodes[p].child[k];
+                const Node& cn = nodes[c];
+                ck(cudaMemcpy2DAsync(C[p] + row_off(p, cn.own_a, 2 * r) + k * r, sizeof(CT) * 2 * r,
+                                     W[c] + row_off(c, cn.own_a, r), sizeof(CT) * r, sizeof(CT) * r,
+                                     (size_t)(cn.own_b - cn.own_a) * Sx, cudaMemcpyDeviceToDevice, stream),
+                   cerr);
+            }
+            // A_c = C_p^H A~_p C_p, then its inverse
+            const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, partial, MAX_PART_BLOCKS, stream);
+            launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
+            launch_gj_inverse(Ainv[p], 2 * r, derr, stream);
+        }
+    }
+
+    hh_status setup() override {
+        zero(derr, sizeof(int) * 4);
+        for (int id = 1; id < nn; ++id) zero(Vs[id], sizeof(CT) * pts(id) * nmax);
+        std::vector<LeafTask> own = leaf_tasks(true);
+        ck(cudaMemcpyAsync(d_tasks_own, own.data(), sizeof(LeafTask) * own.size(), cudaMemcpyHostToDevice, stream),
+           cerr);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, stream);
+        launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
+        for (int l = L; l >= 1; --l) sketch_level(l);
+        cudaEventRecord(e1, stream);
+        hh_status st;
+        const bool ok = sync_check(st);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t_setup_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (!ok) return st;
+        ck(cudaMallocHost(&h_norm, 4 * sizeof(double)), cerr);
+        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+    }
+
+    // --------------------------------------------------------- the outer iteration
+    // One coarse-corrected ORAS step from the FP64 residual `rr` (kept in res):
+    // ut = base + sum_c P_c M_c R_c rr ; res <- b - A ut (or rr - A(ut - base));
+    // out = ut + C A_c^{-1} C^H res.
+    void oras_step(const c128* base, const c128* rhs, c128* out) {
+        const size_t N = (size_t)Sy * Sx;
+        launch_copy<double, T>(res, RT, N, false, false, stream);
+        apply_M(1, 1, false);
+        if (base) d2d(ut, base, sizeof(c128) * N);
+        else zero(ut, sizeof(c128) * N);
+        for (int c : lev[1]) {
+            const Node& cn = nodes[c];
+            launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), ut + row_off(0, cn.own_a, 1),
+                                   (size_t)(cn.own_b - cn.own_a) * Sx, true, false, stream);
+        }
+        launch_apply<double, double, double>(ut, rhs, res, geom(0), 1, 1.0, nullptr, nullptr, stream);
+        const int nb = launch_ip_partial<T, double>(C[0], 2 * r, res, 1, N, 2 * r, 1, partial, MAX_PART_BLOCKS,
+                                                    stream);
+        launch_ip_reduce(partial, nb, 2 * r, 1, nullptr, Ainv[0], ycoef[0], stream);
+        if (out != ut) d2d(out, ut, sizeof(c128) * N);
+        launch_coarse_update<T, double>(C[0], ycoef[0], out, N, 2 * r, 1, stream);
+    }
+
+    hh_status norm_sq(const c128* x, double* dst) {
+        const size_t N = (size_t)Sy * Sx;
+        const int nb = launch_ip_partial<double, double>(x, 1, x, 1, N, 1, 1, partial, MAX_PART_BLOCKS, stream);
+        launch_ip_reduce(partial, nb, 1, 1, (c128*)dst, nullptr, nullptr, stream);
+        return HH_OK;
+    }
+
+    hh_status solve(const c128* f, const c128* g, c128* uo, hh_stats* stt) override {
+        const size_t N = (size_t)Sy * Sx;
+        zero(derr, sizeof(int) * 4);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, stream);
+        launch_rhs(f, g, bvec, P.dim, S, h, stream);
+        norm_sq(bvec, dnorm + 2);   // dnorm[2..3] = ||b||^2 as a complex
+        zero(u, sizeof(c128) * N);
+        int it = 0;
+        double rel = 0.0;
+        hh_status st = HH_OK;
+        for (;;) {
+            int nb = 0;
+            launch_apply<double, double, double>(u, bvec, res, geom(0), 1, 1.0, npart, &nb, stream);
+            launch_sum(npart, nb, dnorm, stream);
+            ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+            if (!sync_check(st)) break;
+            rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
+            if (!std::isfinite(rel)) { st = HH_ENOCONV; break; }
+            if (rel < P.tol) break;
+            if (it >= P.max_iter) { st = HH_ENOCONV; break; }
+            oras_step(u, bvec, u);
+            ++it;
+        }
+        d2d(uo, u, sizeof(c128) * N);
+        cudaEventRecord(e1, stream);
+        hh_status st2;
+        sync_check(st2);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t_solve_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (stt) {
+            stt->iters = it;
+            stt->rel_res = rel;
+            stt->t_setup_ms = t_setup_ms;
+            stt->t_solve_ms = t_solve_ms;
+            stt->footprint_bytes = footprint;
+        }
+        if (st != HH_OK) return st;
+        return st2;
+    }
+
+    hh_status residual(const c128* f, const c128* g, const c128* uu, double* rel) override {
+        launch_rhs(f, g, bvec, P.dim, S, h, stream);
+        norm_sq(bvec, dnorm + 2);
+        int nb = 0;
+        launch_apply<double, double, double>(uu, bvec, res, geom(0), 1, 1.0, npart, &nb, stream);
+        launch_sum(npart, nb, dnorm, stream);
+        ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        hh_status st;
+        if (!sync_check(st)) return st;
+        *rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
+        return HH_OK;
+    }
+
+    // --------------------------------------------------------- step-level access
+    bool valid_node(int id) const { return id >= 0 && id < nn; }
+
+    hh_status node_info(int id, int info[10]) const override {
+        if (!valid_node(id) || !info) return HH_EINVAL;
+        const Node& nd = nodes[id];
+        const int v[10] = {nd.oa, nd.ob, nd.ra, nd.rb, nd.level, nd.parent, nd.child[0], nd.child[1], Sx,
+                           nd.ifrow};
+        std::memcpy(info, v, sizeof(v));
+        return HH_OK;
+    }
+
+    hh_status apply_operator(int id, const c128* x, c128* y, int nc) override {
+        if (!valid_node(id) || nc < 1 || !x || !y) return HH_EINVAL;
+        launch_apply<double, double, double>(x, nullptr, y, geom(id), nc, -1.0, nullptr, nullptr, stream);
+        ck(cudaGetLastError(), cerr);
+        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+    }
+
+    hh_status leaf_solve(int id, const c128* v, c128* x, int nc) override {
+        if (!valid_node(id) || !nodes[id].leaf() || nc < 1 || nc > nmax || !v || !x) return HH_EINVAL;
+        const size_t n = pts(id) * nc;
+        launch_copy<double, T>(v, Vs[id], n, false, false, stream);
+        LeafTask k;
+        k.X = X[id];
+        k.F = Vs[id];
+        k.W = W[id];
+        k.b = nodes[id].b();
+        k.ldx = ldx[id];
+        ck(cudaMemcpyAsync(d_task_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
+        launch_sweep<T>(d_task_one, 1, nodes[id].b(), Sx, nc, derr, stream);
+        launch_copy<T, double>(W[id], x, n, false, false, stream);
+        hh_status st;
+        sync_check(st);
+        return st;
+    }
+
+    hh_status interface_map(int c, int adj, const c128* in, c128* out, int nc) override {
+        if (!valid_node(c) || c == 0 || nc < 1 || nc > m || !in || !out) return HH_EINVAL;
+        const Node& cn = nodes[c];
+        const Node& sn = nodes[cn.sib];
+        const int l = cn.level;
+        for (int o : lev[l]) zero(Vs[o], sizeof(CT) * pts(o) * nc);
+        if (!adj) {
+            launch_copy<double, T>(in, Vs[c] + row_off(c, cn.ifrow, nc), (size_t)Sx * nc, false, false, stream);
+            apply_M(l, nc, true);
+            launch_robin_trace<T>(W[c] + row_off(c, sn.ifrow, nc), W[c] + row_off(c, sn.inward, nc), Om[c], sn.b(), Sx,
+                                  nc, kh, stream);
+            launch_copy<T, double>(Om[c], out, (size_t)Sx * nc, false, false, stream);
+        } else {
+            launch_copy<double, T>(in, Om[c], (size_t)Sx * nc, false, false, stream);
+            launch_adjoint_place<T>(Om[c], Vs[c] + row_off(c, sn.ifrow, nc), Vs[c] + row_off(c, sn.inward, nc), sn.b(),
+                                    Sx, nc, kh, stream);
+            apply_M(l, nc, true);
+            launch_copy<T, double>(W[c] + row_off(c, cn.ifrow, nc), out, (size_t)Sx * nc, false, true, stream);
+        }
+        hh_status st;
+        sync_check(st);
+        return st;
+    }
+
+    hh_status get_basis(int c, void* hV, double* hsig) override {
+        if (!valid_node(c) || c == 0) return HH_EINVAL;
+        hh_status st;
+        if (hV) {
+            launch_copy<T, double>(Vc[c], res, (size_t)Sx * r, false, false, stream);
+            if (!sync_check(st)) return st;
+            ck(cudaMemcpy(hV, res, sizeof(c128) * Sx * r, cudaMemcpyDeviceToHost), cerr);
+        }
+        if (hsig) {
+            if (!sync_check(st)) return st;
+            ck(cudaMemcpy(hsig, lam[c], sizeof(double) * m, cudaMemcpyDeviceToHost), cerr);
+            for (int j = 0; j < m; ++j) hsig[j] = std::sqrt(std::max(0.0, hsig[j]));
+        }
+        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+    }
+
+    hh_status coarse_apply(int p, const c128* rr, c128* z) override {
+        if (!valid_node(p) || nodes[p].leaf() || !rr || !z) return HH_EINVAL;
+        const int nb = launch_ip_partial<T, double>(C[p], 2 * r, rr, 1, pts(p), 2 * r, 1, partial, MAX_PART_BLOCKS,
+                                                    stream);
+        launch_ip_reduce(partial, nb, 2 * r, 1, nullptr, Ainv[p], ycoef[p], stream);
+        zero(z, sizeof(c128) * pts(p));
+        launch_coarse_update<T, double>(C[p], ycoef[p], z, pts(p), 2 * r, 1, stream);
+        hh_status st;
+        sync_check(st);
+        return st;
+    }
+
+    hh_status precondition(const c128* rr, c128* z) override {
+        if (!rr || !z) return HH_EINVAL;
+        d2d(res, rr, sizeof(c128) * (size_t)Sy * Sx);
+        d2d(bvec, rr, sizeof(c128) * (size_t)Sy * Sx);   // residual of the second half: rr - A ut
+        oras_step(nullptr, bvec, z);
+        hh_status st;
+        sync_check(st);
+        return st;
+    }
+
+    hh_status sketch_samples(int c, c128* out) override {
+        if (!valid_node(c) || c == 0 || !out) return HH_EINVAL;
+        launch_sketch<double>(out, Sx, m, c, P.seed, stream);
+        hh_status st;
+        sync_check(st);
+        return st;
+    }
+
+    c128* staging_f() override { return res; }
+    c128* staging_g() override { return gbuf; }
+    c128* iterate() override { return u; }
+    int npoints() const override { return Sy * Sx; }
+};
+
+static SolverBase* make_solver(const hh_params* P) {
+    SolverBase* s = nullptr;
+    if (P->precision == HH_PREC_MIXED) {
+        auto* x = new Solver<float>();
+        x->P = *P;
+        x->init_geometry();
+        s = x;
+    } else {
+        auto* x = new Solver<double>();
+        x->P = *P;
+        x->init_geometry();
+        s = x;
+    }
+    return s;
+}
+
+}  // namespace hh
+
+// ============================================================================= C-ABI
+struct hh_handle {
+    hh::SolverBase* s;
+};
+
+extern "C" {
+
+hh_status hh_set_allocator(void* (*alloc)(size_t, void*, void*), void (*free_)(void*, size_t, void*, void*),
+                           void* ctx) {
+    if (alloc && !free_) return HH_EINVAL;
+    hh::g_alloc.alloc = alloc;
+    hh::g_alloc.free_ = alloc ? free_ : nullptr;
+    hh::g_alloc.ctx = alloc ? ctx : nullptr;
+    return HH_OK;
+}
+
+hh_status hh_footprint(const hh_params* params, size_t* bytes) {
+    if (!bytes) return HH_EINVAL;
+    const hh_status v = hh::validate(params);
+    if (v != HH_OK) return v;
+    std::unique_ptr<hh::SolverBase> s(hh::make_solver(params));
+    *bytes = s->plan(nullptr);
+    return HH_OK;
+}
+
+hh_status hh_setup(const hh_params* params, void* stream, hh_handle** out, size_t* footprint_out) {
+    if (!out) return HH_EINVAL;
+    *out = nullptr;
+    const hh_status v = hh::validate(params);
+    if (v != HH_OK) return v;
+    std::unique_ptr<hh::SolverBase> s(hh::make_solver(params));
+    s->stream = (cudaStream_t)stream;
+    s->hook = hh::g_alloc;
+    s->footprint = s->plan(nullptr);
+    s->block = hh::dev_alloc(s->footprint, s->stream, s->hook);
+    if (!s->block) return HH_ENOMEM;
+    s->plan((char*)s->block);
+    const hh_status st = s->setup();
+    if (footprint_out) *footprint_out = s->footprint;
+    if (st != HH_OK) return st;
+    *out = new hh_handle{s.release()};
+    return HH_OK;
+}
+
+hh_status hh_solve(hh_handle* h, const void* d_f, const void* d_g, void* d_u, void* stream, hh_stats* stats) {
+    if (!h || !d_f || !d_g || !d_u) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->solve((const c128*)d_f, (const c128*)d_g, (c128*)d_u, stats);
+}
+
+hh_status hh_solve_host(hh_handle* h, const void* h_f, const void* h_g, void* h_u, void* stream,
+                        hh_stats* stats) {
+    if (!h || !h_f || !h_g || !h_u) return HH_EINVAL;
+    hh::SolverBase* s = h->s;
+    s->stream = (cudaStream_t)stream;
+    const size_t N = (size_t)s->npoints();
+    const size_t ng = s->P.dim == 2 ? 4 * (size_t)(s->P.n + 2) : 2;
+    if (cudaMemcpyAsync(s->staging_f(), h_f, sizeof(c128) * N, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->staging_g(), h_g, sizeof(c128) * ng, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return HH_ECUDA;
+    const hh_status st = s->solve(s->staging_f(), s->staging_g(), s->iterate(), stats);
+    if (cudaMemcpyAsync(h_u, s->iterate(), sizeof(c128) * N, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return HH_ECUDA;
+    return st;
+}
+
+hh_status hh_residual(hh_handle* h, const void* d_f, const void* d_g, const void* d_u, void* stream,
+                      double* rel_res) {
+    if (!h || !d_f || !d_g || !d_u || !rel_res) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->residual((const c128*)d_f, (const c128*)d_g, (const c128*)d_u, rel_res);
+}
+
+void hh_destroy(hh_handle* h) {
+    if (!h) return;
+    delete h->s;
+    delete h;
+}
+
+const char* hh_status_string(hh_status s) {
+    switch (s) {
+        case HH_OK: return "ok";
+        case HH_EINVAL: return "invalid argument";
+        case HH_ENOMEM: return "out of device memory";
+        case HH_ENOCONV: return "iteration did not converge";
+        case HH_EBREAKDOWN: return "zero pivot in a factorisation";
+        case HH_ETIMEOUT: return "bounded device wait gave up";
+        case HH_ECUDA: return "CUDA runtime error";
+        case HH_ENOTIMPL: return "not implemented";
+    }
+    return "unknown status";
+}
+
+hh_status hh_node_info(const hh_handle* h, int node, int info[10]) {
+    if (!h) return HH_EINVAL;
+    return h->s->node_info(node, info);
+}
+hh_status hh_apply_operator(hh_handle* h, int node, const void* d_x, void* d_y, int ncols, void* stream) {
+    if (!h) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->apply_operator(node, (const c128*)d_x, (c128*)d_y, ncols);
+}
+hh_status hh_leaf_solve(hh_handle* h, int leaf, const void* d_v, void* d_x, int ncols, void* stream) {
+    if (!h) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->leaf_solve(leaf, (const c128*)d_v, (c128*)d_x, ncols);
+}
+hh_status hh_interface_map(hh_handle* h, int child, int adjoint, const void* d_in, void* d_out, int ncols,
+                           void* stream) {
+    if (!h) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->interface_map(child, adjoint, (const c128*)d_in, (c128*)d_out, ncols);
+}
+hh_status hh_get_basis(hh_handle* h, int child, void* h_V, double* h_sigma) {
+    if (!h) return HH_EINVAL;
+    return h->s->get_basis(child, h_V, h_sigma);
+}
+hh_status hh_coarse_apply(hh_handle* h, int node, const void* d_r, void* d_z, void* stream) {
+    if (!h) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->coarse_apply(node, (const c128*)d_r, (c128*)d_z);
+}
+hh_status hh_precondition(hh_handle* h, const void* d_r, void* d_z, void* stream) {
+    if (!h) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->precondition((const c128*)d_r, (c128*)d_z);
+}
+hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream) {
+    if (!h) return HH_EINVAL;
+    h->s->stream = (cudaStream_t)stream;
+    return h->s->sketch_samples(child, (c128*)d_out);
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+// k_field.cu -- grid-field kernels: the weighted 5-point operator and residuals
+// (Eqs. (2)-(3) need f - A u at every level), right-hand-side assembly (Eq. (1),
+// Sec. 3.1), precision casts and restricted prolongation (Sec. 1), the interface
+// traces B_s A~_s (Sec. 2), the counter-based sketch and the coarse update C y.
+#include "kernels.h"
+
+namespace hh {
+
+static int grid_for(size_t n, int threads, int cap = 152 * 16) {
+    size_t g = (n + threads - 1) / threads;
+    if (g > (size_t)cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ------------------------------------------------------------------ operator apply
+// One thread per (point, column); grid-stride.  Compute type = TY.
+template <typename TX, typename TV, typename TY>
+__global__ void k_apply(const cplx<TX>* __restrict__ x, const cplx<TV>* __restrict__ v,
+                        cplx<TY>* __restrict__ y, OpGeom g, int nc, TY sgn, double* part) {
+    const size_t total = (size_t)g.b * g.Sx * nc;
+    const size_t ldr = (size_t)g.Sx * nc;
+    double acc2 = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % nc);
+        const size_t pt = t / nc;
+        const int i = (int)(pt % g.Sx);
+        const int j = (int)(pt / g.Sx);
+        const c128 d = op_diag(j, i, g);
+        const cplx<TY> dg = {(TY)d.re, (TY)d.im};
+        cplx<TY> ax = dg * cvt<TY>(x[t]);
+        const TY wj = (TY)wrow(j, g.b), wi = (TY)wcol(i, g.Sx);
+        // x-neighbours: coefficient -w_j
+        if (g.Sx > 1) {
+            if (i > 0) ax = ax - wj * cvt<TY>(x[t - nc]);
+            if (i < g.Sx - 1) ax = ax - wj * cvt<TY>(x[t + nc]);
+        }
+        // y-neighbours: coefficient -w_i
+        if (j > 0) ax = ax - wi * cvt<TY>(x[t - ldr]);
+        if (j < g.b - 1) ax = ax - wi * cvt<TY>(x[t + ldr]);
+        cplx<TY> out = (-sgn) * ax;
+        if (v) out = cvt<TY>(v[t]) + out;
+        y[t] = out;
+        if (part) acc2 += (double)abs2(out);
+    }
+    if (part) {
+        __shared__ double red[32];
+        acc2 = warp_sum(acc2);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+            s2 = warp_sum(s2);
+            if (threadIdx.x == 0) part[blockIdx.x] = s2;
+        }
+    }
+}
+
+template <typename TX, typename TV, typename TY>
+void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, int nc, double sgn,
+                  double* part, int* nblk_out, cudaStream_t s) {
+    const size_t total = (size_t)g.b * g.Sx * nc;
+    const int th = 256;
+    const int grid = grid_for(total, th, 152 * 8);
+    k_apply<TX, TV, TY><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    if (nblk_out) *nblk_out = grid;
+}
+
+__global__ void k_sum(const double* part, int n, double* out) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+    __shared__ double red[32];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s2 = warp_sum(s2);
+        if (threadIdx.x == 0) *out = s2;
+    }
+}
+void launch_sum(const double* part, int n, double* out, cudaStream_t s) {
+    k_sum<<<1, 256, 0, s>>>(part, n, out);
+}
+
+// --------------------------------------------------------------------------- rhs
+__global__ void k_rhs(const c128* __restrict__ f, const c128* __restrict__ g, c128* __restrict__ b,
+                      int dim, int S, double h) {
+    const int Sx = dim == 2 ? S : 1;
+    const size_t total = (size_t)S * Sx;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % Sx), j = (int)(t / Sx);
+        const double wj = wrow(j, S), wi = wcol(i, Sx);
+        c128 v = (h * h * wi * wj) * f[t];
+        if (dim == 1) {
+            if (j == 0) v = v + h * g[0];
+            if (j == S - 1) v = v + h * g[1];
+        } else {
+            if (i == 0) v = v + (h * wj) * g[0 * S + j];
+            if (i == Sx - 1) v = v + (h * wj) * g[1 * S + j];
+            if (j == 0) v = v + (h * wi) * g[2 * S + i];
+            if (j == S - 1) v = v + (h * wi) * g[3 * S + i];
+        }
+        b[t] = v;
+    }
+}
+void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s) {
+    const size_t total = (size_t)S * (dim == 2 ? S : 1);
+    k_rhs<<<grid_for(total, 256), 256, 0, s>>>(f, g, b, dim, S, h);
+}
+
+// -------------------------------------------------------------------------- copy
+template <typename TS, typename TD>
+__global__ void k_copy(const cplx<TS>* __restrict__ src, cplx<TD>* __restrict__ dst, size_t n, bool acc,
+                       bool cj) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        cplx<TD> v = cvt<TD>(src[t]);
+        if (cj) v = conj(v);
+        dst[t] = acc ? dst[t] + v : v;
+    }
+}
+template <typename TS, typename TD>
+void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, bool conjugate,
+                 cudaStream_t s) {
+    if (n == 0) return;
+    k_copy<TS, TD><<<grid_for(n, 256), 256, 0, s>>>(src, dst, n, accumulate, conjugate);
+}
+
+// ------------------------------------------------------------- interface traces
+// Boundary row (local row 0 of a band of b_s rows; by symmetry the same for the last
+// row) of A~_s: coefficient op_diag on the row itself, -1/2 to the x-neighbours on the
+// row (X halved by w_j = 1/2), -w_i to the inward row.
+template <typename T>
+__global__ void k_robin_trace(const cplx<T>* __restrict__ uif, const cplx<T>* __restrict__ uin,
+                              cplx<T>* __restrict__ Y, int b_s, int Sx, int nc, double kh) {
+    const OpGeom g{b_s, Sx, kh};
+    const size_t total = (size_t)Sx * nc;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / nc);
+        const c128 d = op_diag(0, i, g);
+        c128 y = d * cvt<double>(uif[t]);
+        if (Sx > 1) {
+            if (i > 0) y = y - 0.5 * cvt<double>(uif[t - nc]);
+            if (i < Sx - 1) y = y - 0.5 * cvt<double>(uif[t + nc]);
+        }
+        y = y - wcol(i, Sx) * cvt<double>(uin[t]);
+        Y[t] = cvt<T>(y);
+    }
+}
+template <typename T>
+void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, int b_s, int Sx, int nc,
+                        double kh, cudaStream_t s) {
+    const size_t total = (size_t)Sx * nc;
+    k_robin_trace<T><<<grid_for(total, 256), 256, 0, s>>>(u_if, u_in, Y, b_s, Sx, nc, kh);
+}
+
+template <typename T>
+__global__ void k_adjoint_place(const cplx<T>* __restrict__ Q, cplx<T>* __restrict__ vif,
+                                cplx<T>* __restrict__ vin, int b_s, int Sx, int nc, double kh) {
+    const OpGeom g{b_s, Sx, kh};
+    const size_t total = (size_t)Sx * nc;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / nc);
+        const c128 d = op_diag(0, i, g);
+        const c128 q = conj(cvt<double>(Q[t]));
+        c128 y = d * q;
+        if (Sx > 1) {
+            if (i > 0) y = y - 0.5 * conj(cvt<double>(Q[t - nc]));
+            if (i < Sx - 1) y = y - 0.5 * conj(cvt<double>(Q[t + nc]));
+        }
+        vif[t] = cvt<T>(y);
+        vin[t] = cvt<T>((-wcol(i, Sx)) * q);
+    }
+}
+template <typename T>
+void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_s, int Sx, int nc,
+                          double kh, cudaStream_t s) {
+    const size_t total = (size_t)Sx * nc;
+    k_adjoint_place<T><<<grid_for(total, 256), 256, 0, s>>>(Q, v_if, v_in, b_s, Sx, nc, kh);
+}
+
+// ------------------------------------------------------------------ sketch (RNG)
+// SplitMix64 (Steele, Lea & Flood 2014): n-th output = mix(seed + (n+1) * gamma).
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                            unsigned long long n) {
+    unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+template <typename T>
+__global__ void k_sketch(cplx<T>* Om, int Sx, int m, int node, unsigned long long seed) {
+    const size_t total = (size_t)Sx * m;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long j = t % m, x = t / m;
+        const unsigned long long idx = ((unsigned long long)node * 4096ull + j) * (1ull << 20) + x;
+        const unsigned long long z1 = splitmix64_at(seed, 2ull * idx);
+        const unsigned long long z2 = splitmix64_at(seed, 2ull * idx + 1ull);
+        const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;
+        const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+        const double rho = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        Om[t] = cplx<T>{(T)(rho * cs), (T)(rho * sn)};
+    }
+}
+template <typename T>
+void launch_sketch(cplx<T>* Om, int Sx, int m, int node, unsigned long long seed, cudaStream_t s) {
+    k_sketch<T><<<grid_for((size_t)Sx * m, 256), 256, 0, s>>>(Om, Sx, m, node, seed);
+}
+
+// ---------------------------------------------------------------- coarse update
+template <typename TC, typename TW>
+__global__ void k_coarse_update(const cplx<TC>* __restrict__ C, const c128* __restrict__ y,
+                                cplx<TW>* __restrict__ W, size_t npts, int p, int nc) {
+    extern __shared__ c128 ys[];
+    for (int t = threadIdx.x; t < p * nc; t += blockDim.x) ys[t] = y[t];
+    __syncthreads();
+    const size_t total = npts * nc;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % nc);
+        const size_t pt = t / nc;
+        const cplx<TC>* cr = C + pt * p;
+        c128 acc = {0.0, 0.0};
+        for (int j = 0; j < p; ++j) cfma(acc, cvt<double>(cr[j]), ys[j * nc + c]);
+        W[t] = cvt<TW>(cvt<double>(W[t]) + acc);
+    }
+}
+template <typename TC, typename TW>
+void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t npts, int p, int nc,
+                          cudaStream_t s) {
+    const size_t total = npts * nc;
+    k_coarse_update<TC, TW><<<grid_for(total, 256), 256, sizeof(c128) * p * nc, s>>>(C, y, W, npts, p, nc);
+}
+
+// ------------------------------------------------------------ instantiations
+#define HH_APPLY(TX, TV, TY)                                                                           \
+    template void launch_apply<TX, TV, TY>(const cplx<TX>*, const cplx<TV>*, cplx<TY>*, OpGeom, int, \
+                                           double, double*, int*, cudaStream_t);
+HH_APPLY(double, double, double)
+HH_APPLY(float, float, float)
+HH_APPLY(float, double, double)
+HH_APPLY(double, float, float)
+
+#define HH_COPY(TS, TD) \
+    template void launch_copy<TS, TD>(const cplx<TS>*, cplx<TD>*, size_t, bool, bool, cudaStream_t);
+HH_COPY(double, double)
+HH_COPY(float, float)
+HH_COPY(double, float)
+HH_COPY(float, double)
+
+#define HH_PREC(T)                                                                                    \
+    template void launch_robin_trace<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, int, int, int, double, \
+                                        cudaStream_t);                                                \
+    template void launch_adjoint_place<T>(const cplx<T>*, cplx<T>*, cplx<T>*, int, int, int, double,   \
+                                          cudaStream_t);                                              \
+    template void launch_sketch<T>(cplx<T>*, int, int, int, unsigned long long, cudaStream_t);
+
+HH_PREC(float)
+HH_PREC(double)
+template void launch_coarse_update<float, float>(const c64*, const c128*, c64*, size_t, int, int, cudaStream_t);
+template void launch_coarse_update<float, double>(const c64*, const c128*, c128*, size_t, int, int, cudaStream_t);
+template void launch_coarse_update<double, double>(const c128*, const c128*, c128*, size_t, int, int,
+                                                   cudaStream_t);
+
+}  // namespace hh

@@ -1,0 +1,90 @@
+// kernels.h -- host-side launchers of the libhh CUDA kernels (internal header).
+#pragma once
+#include <cuda_runtime.h>
+#include "hh_core.cuh"
+
+namespace hh {
+
+// ---- field kernels (k_field.cu) ----------------------------------------------------
+// y = (v ? v : 0) - sgn * A~ x  on a band (b rows, Sx cols, nc columns per point).
+// With `v` null and sgn = -1 this is y = A~ x.  If `part` is non-null each block writes
+// its partial sum of |y|^2 to part[blockIdx.x] (nblk_out receives the block count).
+template <typename TX, typename TV, typename TY>
+void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, int nc, double sgn,
+                  double* part, int* nblk_out, cudaStream_t s);
+
+// out = sum of n doubles (deterministic single-block reduction)
+void launch_sum(const double* part, int n, double* out, cudaStream_t s);
+
+// b = h^2 w_i w_j f + h (w_j gx + w_i gy) for the global problem.
+void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s);
+
+// dst[i] (+)= (TD) src[i], i < n
+template <typename TS, typename TD>
+void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, bool conjugate,
+                 cudaStream_t s);
+
+// Y[x][c] = boundary row of A~_s applied to u: u_if = row on the sibling's artificial
+// boundary, u_in = the next row inward (both rows of the child's solution).
+template <typename T>
+void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, int b_s, int Sx, int nc,
+                        double kh, cudaStream_t s);
+
+// v_if/v_in = rows of A~_s B_s^T conj(Q) (the adjoint trace, conjugated for the
+// conj o solve o conj adjoint); other rows untouched.
+template <typename T>
+void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_s, int Sx, int nc,
+                          double kh, cudaStream_t s);
+
+// Omega[x][j] (Sx x m) for child `node`: SplitMix64 + Box-Muller, re/im ~ N(0,1/2).
+template <typename T>
+void launch_sketch(cplx<T>* Om, int Sx, int m, int node, unsigned long long seed, cudaStream_t s);
+
+// W[n][c] += sum_j C[n][j] y[j][c]   (n < npts, j < p, c < nc), y FP64 [p][nc]
+template <typename TC, typename TW>
+void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t npts, int p, int nc,
+                          cudaStream_t s);
+
+// ---- dense kernels (k_dense.cu) ----------------------------------------------------
+// partial[blk][i][j] = sum_{n in blk} conj(A[n*lda+i]) * B[n*ldb+j]; returns nblk.
+template <typename TA, typename TB>
+int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, size_t N, int p, int q,
+                      c128* partial, int max_blocks, cudaStream_t s);
+// out[i][j] = sum_blk partial; if Minv != null, out2 = Minv (p x p) * out  (p x q).
+void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, const c128* Minv,
+                      c128* out2, cudaStream_t s);
+// Galerkin partials: partial[blk][a][l] = sum_pts conj(C[pt][a]) (A~ C)[pt][l]  (p = 2r)
+template <typename T>
+int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, c128* partial, int max_blocks,
+                            cudaStream_t s);
+// In-place QR (classical Gram-Schmidt, two passes) of nq independent Sx x m blocks.
+template <typename T>
+void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s);
+// Hermitian Jacobi eigensolver on nq m x m FP64 matrices: eigenvalues descending in
+// lam, eigenvectors (columns) in U.  G is overwritten.
+void launch_jacobi(c128* const* G, c128* const* U, double* const* lam, int nq, int m,
+                   void** dev_ptr_scratch, cudaStream_t s);
+// V[x][j] = sum_k Z[x][k] U[k][j] / sqrt(lam_j)  for j < r
+template <typename T>
+void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* V, int Sx, int m, int r,
+                   cudaStream_t s);
+// In-place Gauss-Jordan inverse with partial pivoting of an n x n FP64 matrix.
+void launch_gj_inverse(c128* A, int n, int* err, cudaStream_t s);
+
+// ---- leaf kernels (k_leaf.cu) ------------------------------------------------------
+struct LeafTask {
+    void* X;          // factor store: Sx steps of b x ldx blocks (2D) or b diagonal inverses (1D)
+    const void* F;    // right-hand sides [b][Sx][nrhs]
+    void* W;          // solutions [b][Sx][nrhs]
+    int b;
+    int ldx;
+};
+template <typename T>
+void launch_factor(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,
+                   cudaStream_t s);
+template <typename T>
+void launch_sweep(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, int* err,
+                  cudaStream_t s);
+int leaf_ldx(int b, int elem_bytes);
+
+}  // namespace hh

@@ -1,0 +1,297 @@
+"""GPU parity: every step of the CUDA path against the FP64 CPU oracle, through the C-ABI.
+
+Tolerances (relative, 2-norm over the compared array):
+* FP64 form, single steps (operator, leaf solve, interface map, one ORAS step): the
+  two sides evaluate the same definitions in different orders; errors are rounding
+  amplified by the subdomain condition numbers -> 1e-11 (operator 1e-14).
+* FP64 form, full solves against the direct solution u* = A^{-1} b: 1e-10.
+* Mixed form (complex64 subdomain work, FP64 refinement): full solves 1e-8; single
+  complex64 leaf solves 1e-4 (FP32 rounding times the subdomain condition number).
+* Randomised bases: compared as subspaces (projector distance) and singular values,
+  since singular vectors are unique only up to phases.
+"""
+import numpy as np
+import pytest
+
+from oracle import direct
+from oracle.method import OMethod
+from oracle.problem import Problem
+from oracle.sketch import gaussian_sketch
+from workloads import WORKLOADS, point_source_rhs, problem_inputs, random_complex
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hh():
+    from paper_2512_12538_gb300 import build
+    build.build()
+    import paper_2512_12538_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def host(x):
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+# small 2D case with ragged bands: S = 47, 4 leaves of 12..14 rows, e = 1
+SMALL = dict(dim=2, n=45, k=12.0, levels=2, overlap=2, rank=6, oversample=4, seed=11)
+
+
+def make_pair(hh, precision="fp64", **kw):
+    cfg = dict(SMALL)
+    cfg.update(kw)
+    P = Problem(cfg["dim"], cfg["n"], cfg["k"])
+    O = OMethod(P, cfg["levels"], cfg["overlap"], cfg["rank"], cfg["oversample"], seed=cfg["seed"])
+    params = hh.make_params(cfg["dim"], cfg["n"], cfg["k"], cfg["levels"], cfg["overlap"], cfg["rank"],
+                            cfg["oversample"], 1, 1e-13, 400, precision, cfg["seed"])
+    h, _ = hh.hh_setup(params)
+    return P, O, h
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_operator_every_node(hh, dim):
+    P, O, h = make_pair(hh, dim=dim, n=45 if dim == 2 else 200, rank=min(6, 1 if dim == 1 else 6))
+    try:
+        for nid in range(len(O.tree)):
+            info = hh.hh_node_info(h, nid)
+            nd = O.tree[nid]
+            assert (info["ra"], info["rb"], info["oa"], info["ob"]) == (nd.ra, nd.rb, nd.oa, nd.ob)
+            x = random_complex((nd.b, P.Sx, 3), 100 + nid)
+            y = torch.empty_like(dev(x))
+            hh.hh_apply_operator(h, nid, dev(x), y, 3)
+            assert rel(host(y), O.apply(nid, x)) < 1e-14
+    finally:
+        hh.hh_destroy(h)
+
+
+def test_sketch_samples_match_generator(hh):
+    P, O, h = make_pair(hh)
+    try:
+        for c in (1, 4, 6):
+            out = torch.empty((P.Sx, O.m), dtype=torch.complex128, device="cuda")
+            hh.hh_sketch_samples(h, c, out)
+            assert rel(host(out), gaussian_sketch(SMALL["seed"], c, P.Sx, O.m)) < 1e-14
+    finally:
+        hh.hh_destroy(h)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+@pytest.mark.parametrize("ncols", [1, 3, 10])
+def test_leaf_solve(hh, precision, tol, ncols):
+    P, O, h = make_pair(hh, precision)
+    try:
+        for leaf in (3, 4, 5, 6):
+            nd = O.tree[leaf]
+            v = random_complex((nd.b, P.Sx, ncols), 7 * leaf + ncols)
+            x = torch.empty_like(dev(v))
+            hh.hh_leaf_solve(h, leaf, dev(v), x, ncols)
+            assert rel(host(x), O.leaf_solve(leaf, v)) < tol, (leaf, ncols)
+    finally:
+        hh.hh_destroy(h)
+
+
+def test_leaf_solve_1d(hh):
+    P, O, h = make_pair(hh, dim=1, n=300, levels=2, overlap=4, rank=1, oversample=0)
+    try:
+        for leaf in (3, 4, 5, 6):
+            nd = O.tree[leaf]
+            v = random_complex((nd.b, 1, 2), leaf)
+            x = torch.empty_like(dev(v))
+            hh.hh_leaf_solve(h, leaf, dev(v), x, 2)
+            assert rel(host(x), O.leaf_solve(leaf, v)) < 1e-12
+    finally:
+        hh.hh_destroy(h)
+
+
+@pytest.mark.parametrize("child", [1, 2, 3, 6])
+def test_interface_map_and_adjoint(hh, child):
+    P, O, h = make_pair(hh)
+    try:
+        X = random_complex((P.Sx, 4), 31 + child)
+        Y = torch.empty_like(dev(X))
+        hh.hh_interface_map(h, child, 0, dev(X), Y, 4)
+        assert rel(host(Y), O.T(child, X)) < 1e-10
+        hh.hh_interface_map(h, child, 1, dev(X), Y, 4)
+        assert rel(host(Y), O.T_adjoint(child, X)) < 1e-10
+    finally:
+        hh.hh_destroy(h)
+
+
+def _proj_dist(V1, V2):
+    P1 = V1 @ np.linalg.pinv(V1)
+    P2 = V2 @ np.linalg.pinv(V2)
+    return np.linalg.norm(P1 - P2, 2)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-7), ("mixed", 1e-3)])
+def test_sketch_basis_subspace_and_singular_values(hh, precision, tol):
+    P, O, h = make_pair(hh, precision)
+    try:
+        for c in range(1, 7):
+            V = np.zeros((P.Sx, O.r), dtype=np.complex128)
+            sig = np.zeros(O.m)
+            hh.hh_get_basis(h, c, V, sig)
+            assert np.allclose(V.conj().T @ V, np.eye(O.r), atol=10 * tol)
+            np.testing.assert_allclose(sig, O.sigma[c][:O.m], rtol=tol, atol=tol * O.sigma[c][0])
+            gap = O.sigma[c][O.r - 1] / max(O.sigma[c][O.r], 1e-300)
+            if gap > 1.05:   # subspace well defined only across a spectral gap
+                assert _proj_dist(V, O.V[c]) < 50 * tol / (gap - 1.0), (c, gap)
+    finally:
+        hh.hh_destroy(h)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-3)])
+def test_coarse_correction_operator(hh, precision, tol):
+    P, O, h = make_pair(hh, precision)
+    try:
+        for p in (0, 1, 2):
+            nd = O.tree[p]
+            rr = random_complex((nd.b, P.Sx, 1), 55 + p)
+            z = torch.empty_like(dev(rr))
+            hh.hh_coarse_apply(h, p, dev(rr), z)
+            assert rel(host(z), O.coarse(p, rr)) < tol, p
+    finally:
+        hh.hh_destroy(h)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-3)])
+def test_one_oras_step(hh, precision, tol):
+    P, O, h = make_pair(hh, precision)
+    try:
+        rr = random_complex((P.N,), 77)
+        z = torch.empty_like(dev(rr))
+        hh.hh_precondition(h, dev(rr), z)
+        assert rel(host(z), O.precondition(rr)) < tol
+    finally:
+        hh.hh_destroy(h)
+
+
+def test_residual(hh):
+    P, O, h = make_pair(hh)
+    try:
+        f = random_complex((P.S, P.S), 3)
+        g = random_complex((4, P.S), 4)
+        u = random_complex((P.S, P.S), 5)
+        b = P.rhs(f, g)
+        want = np.linalg.norm(b - P.A() @ u.reshape(-1)) / np.linalg.norm(b)
+        got = hh.hh_residual(h, dev(f), dev(g), dev(u))
+        assert abs(got - want) <= 1e-12 * want
+        us = direct.solve(P, f, g).reshape(P.S, P.S)
+        assert hh.hh_residual(h, dev(f), dev(g), dev(us)) < 1e-13
+    finally:
+        hh.hh_destroy(h)
+
+
+def test_1d_two_subdomains_converges_in_one_step(hh):
+    w = WORKLOADS["helm1d_n1000_k20pi"]
+    P = Problem(1, w.n, w.k)
+    f, g = problem_inputs(w)
+    us = direct.solve(P, f, g)
+    s = hh.Solver(1, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, tol=1e-12, max_iter=5)
+    u, st = s.solve(dev(f.reshape(-1, 1)), dev(g))
+    s.close()
+    assert st["iters"] <= 2
+    assert rel(host(u), us) < 1e-10
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+@pytest.mark.parametrize("case", ["small", "ragged3", "deep1d"])
+def test_solve_against_direct(hh, precision, tol, case):
+    if case == "small":
+        dim, n, k, L, ov, r, p = 2, 45, 12.0, 2, 2, 6, 4
+    elif case == "ragged3":
+        dim, n, k, L, ov, r, p = 2, 77, 20.0, 3, 4, 8, 5
+    else:
+        dim, n, k, L, ov, r, p = 1, 411, 30.0, 3, 4, 1, 0
+    P = Problem(dim, n, k)
+    if dim == 2:
+        f = point_source_rhs(n, 9)
+        g = random_complex((4, P.S), 10)
+    else:
+        f = random_complex((P.S, 1), 9)
+        g = random_complex((2,), 10)
+    us = direct.solve(P, f, g)
+    s = hh.Solver(dim, n, k, L, ov, r, p, tol=1e-13, max_iter=500, precision=precision, seed=3)
+    u, st = s.solve(dev(f), dev(g))
+    s.close()
+    assert rel(host(u), us) < tol, st
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_solve_255_k40_two_levels(hh, precision, tol):
+    """The 255 x 255 interior grid, k = 40, 4 leaf bands, r = 16, p = 10 workload."""
+    w = WORKLOADS["helm2d_n255_k40_L2"]
+    P = Problem(2, w.n, w.k)
+    f, g = problem_inputs(w)
+    us = direct.solve(P, f, g)
+    s = hh.Solver(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, tol=1e-12, max_iter=300,
+                  precision=precision, seed=1)
+    u, st = s.solve(dev(f), dev(g))
+    s.close()
+    err = rel(host(u), us)
+    assert err < tol, (err, st)
+
+
+def test_solve_host_entry_point(hh):
+    P = Problem(2, 45, 12.0)
+    f = point_source_rhs(45, 2)
+    g = np.zeros((4, P.S), dtype=np.complex128)
+    us = direct.solve(P, f, g)
+    params = hh.make_params(2, 45, 12.0, 2, 2, 6, 4, 1, 1e-13, 300, "mixed", 0)
+    h, _ = hh.hh_setup(params)
+    try:
+        u = np.zeros((P.S, P.S), dtype=np.complex128)
+        st = hh.hh_solve_host(h, f, g, u)
+        assert rel(u, us) < 1e-8
+        assert st.iters > 0 and st.rel_res < 1e-13
+    finally:
+        hh.hh_destroy(h)
+
+
+def test_invalid_calls_rejected(hh):
+    P, O, h = make_pair(hh)
+    try:
+        x = torch.zeros((P.S, P.S), dtype=torch.complex128, device="cuda")
+        with pytest.raises(hh.HHError):
+            hh.hh_leaf_solve(h, 1, x, x, 1)          # not a leaf
+        with pytest.raises(hh.HHError):
+            hh.hh_leaf_solve(h, 3, x, x, 1000)       # too many columns
+        with pytest.raises(hh.HHError):
+            hh.hh_interface_map(h, 0, 0, x, x, 1)    # the root has no interface map
+        with pytest.raises(hh.HHError):
+            hh.hh_apply_operator(h, 99, x, x, 1)
+    finally:
+        hh.hh_destroy(h)
+    with pytest.raises(hh.HHError):
+        hh.hh_setup(hh.make_params(2, 45, 12.0, 2, 3, 6, 4))     # odd overlap
+
+
+def test_noconvergence_reports_last_iterate(hh):
+    P = Problem(2, 45, 12.0)
+    f = point_source_rhs(45, 2)
+    g = np.zeros((4, P.S), dtype=np.complex128)
+    params = hh.make_params(2, 45, 12.0, 2, 2, 6, 4, 1, 1e-15, 2, "fp64", 0)
+    h, _ = hh.hh_setup(params)
+    try:
+        u = torch.zeros((P.S, P.S), dtype=torch.complex128, device="cuda")
+        with pytest.raises(hh.HHError) as ei:
+            hh.hh_solve(h, dev(f), dev(g), u)
+        assert ei.value.status == hh.HH_ENOCONV
+        st = hh.hh_solve(h, dev(f), dev(g), u, allow_noconv=True)
+        assert st.iters == 2 and 0 < st.rel_res < 1
+        assert np.isfinite(host(u)).all()
+    finally:
+        hh.hh_destroy(h)

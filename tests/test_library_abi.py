@@ -1,0 +1,59 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, and exports every entry point
+declared in include/hh.h; host-only calls validate parameters (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "hh.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hh_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def hh():
+    from paper_2512_12538_gb300 import build
+    build.build()
+    import paper_2512_12538_gb300 as m
+    return m
+
+
+def test_every_declared_symbol_exported(hh):
+    names = _declared()
+    assert "hh_setup" in names and "hh_solve" in names
+    lib = ctypes.CDLL(hh.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(hh):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert hh.status_string(s) and hh.status_string(s) != "unknown status"
+
+
+def test_footprint_host_only_and_validation(hh):
+    p = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
+    fp = hh.hh_footprint(p)
+    # at least the FP64 leaf factors: 4 leaves x 257 columns x 66^2 x 16 bytes
+    assert fp > 4 * 257 * 65 * 65 * 16
+    pm = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, precision="mixed")
+    assert hh.hh_footprint(pm) < fp
+    bad = [dict(overlap=3), dict(overlap=0), dict(levels=0), dict(n=2), dict(rank=0), dict(k=-1.0),
+           dict(n=20, levels=4), dict(rank=40, oversample=0), dict(dim=3), dict(n_inner=0), dict(tol=0.0)]
+    for kw in bad:
+        args = dict(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
+        args.update(kw)
+        with pytest.raises(hh.HHError) as ei:
+            hh.hh_footprint(hh.make_params(**args))
+        assert ei.value.status == hh.HH_EINVAL, kw
+
+
+def test_footprint_1d(hh):
+    p = hh.make_params(dim=1, n=1000, k=62.83, levels=1, overlap=4, rank=1, oversample=0)
+    assert 0 < hh.hh_footprint(p) < 64 << 20
