@@ -1,0 +1,392 @@
+"""Benchmark: one-shot Helmholtz solves per second at relative error 1e-8.
+
+A step is one pass of the whole path for one problem: set-up (hierarchy, leaf
+factorisation, interface sketches, coarse bases, Galerkin matrices and their inverses)
+followed by the outer iteration to the calibrated FP64 residual tolerance, then the
+handle is released.  Default workload: 255 x 255 interior grid (257^2 unknowns), k = 40,
+2-level binary band hierarchy (4 leaves), overlap 2 rows, r = 16, p = 10, seeded
+Gaussian point sources.  The headline runs the mixed form (complex64 subdomain work,
+FP64 residual / Galerkin / coarse inverse / sketch SVD); the FP64 GPU form runs the
+same workload for comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this project) on the
+same workload.  Under torchrun (N > 1) every rank solves its own independent problems
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Helmholtz solves/sec at rel err 1e-8 (mixed vs FP64 GPU); p50/p99 latency"
+UNIT = "solves/s"
+WORKLOAD = "helm2d_n255_k40_L2"
+# FP64 relative-residual stopping tolerance giving relative error <= 1e-8 against the
+# direct solution on this workload (checked by tests/test_gpu_bench_calibration.py).
+TOL = 1e-11
+MAX_ITER = 400
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT, FP32_LANES = 152, 128
+
+
+# ------------------------------------------------------------------------ helpers
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [t.strip() for t in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_inputs():
+    from workloads import WORKLOADS, problem_inputs
+    w = WORKLOADS[WORKLOAD]
+    f, g = problem_inputs(w)
+    return w, f, g
+
+
+def leaf_bands(w):
+    """Rows of every leaf band (the same split rule as the library)."""
+    e = w.overlap // 2
+    S = w.S
+    nodes = [(0, S)]
+    for _ in range(w.levels):
+        nxt = []
+        for oa, ob in nodes:
+            mid = oa + (ob - oa) // 2
+            nxt += [(oa, mid), (mid, ob)]
+        nodes = nxt
+    return [min(S, ob + e) - max(0, oa - e) for oa, ob in nodes]
+
+
+def sweep_bytes(w, ncols, esz):
+    """Algorithmic HBM bytes of one leaf-sweep launch (all leaves): every stored
+    inverse X_i read twice (forward and backward; ldx-padded rows), right-hand sides
+    read once, solutions written twice and read once."""
+    per16 = 16 // esz
+    tot = 0
+    for b in leaf_bands(w):
+        ldx = (b + per16 - 1) // per16 * per16
+        tot += (2 * w.S - 1) * b * ldx * esz
+        tot += 4 * b * w.S * ncols * esz
+    return tot
+
+
+def factor_flops(w):
+    """Algorithmic flops of one factorisation launch: per leaf and column i, the Schur
+    update b^2 complex multiply-adds and the Gauss-Jordan inverse b^3."""
+    return sum(w.S * 8.0 * (b ** 3 + b ** 2) for b in leaf_bands(w))
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_12538_gb300 as hh
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    hh.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    w, f, g = workload_inputs()
+    fd = torch.from_numpy(f).cuda()
+    gd = torch.from_numpy(g).cuda()
+    u = torch.empty_like(fd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def params(prec):
+        return hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, w.n_inner, TOL, MAX_ITER,
+                              prec, 1 + rank)
+
+    def one(prec, profile=False):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h, _ = hh.hh_setup(params(prec), stream)
+        st = hh.hh_solve(h, fd, gd, u, stream)
+        e1.record(stream)
+        prof = hh.hh_profile_read(h) if profile else None
+        hh.hh_destroy(h)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st, prof
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        one("mixed")
+    one("fp64")
+
+    # timed: mixed form, headline.  The library's event profiler is on for these handles:
+    # it records CUDA events on `stream` around its kernels, which gives the dominant
+    # kernel's average launch duration over the timed region.
+    barrier()
+    launches0 = hh.hh_launch_count()
+    step_ms, iters, prof_total = [], [], {}
+    hh.hh_profile_enable(None, True)
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ms, st, prof = one("mixed", profile=True)
+            step_ms.append(ms)
+            iters.append(st.iters)
+            for k, (pms, cnt) in prof.items():
+                a, b = prof_total.get(k, (0.0, 0))
+                prof_total[k] = (a + pms, b + cnt)
+        barrier()
+        wall = time.perf_counter() - t0
+    hh.hh_profile_enable(None, False)
+    launches = hh.hh_launch_count() - launches0
+    prof_iters = iters
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # FP64 GPU form of the same method on the same workload
+    fp64_ms = []
+    fp64_iters = []
+    for _ in range(max(1, args.steps // 2)):
+        ms, st, _ = one("fp64")
+        fp64_ms.append(ms)
+        fp64_iters.append(st.iters)
+
+    # end to end through the C-ABI with host buffers (pinned): H2D f, g and D2H u inside
+    fh = torch.from_numpy(f).pin_memory()
+    gh = torch.from_numpy(g).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h, _ = hh.hh_setup(params("mixed"), stream)
+        hh.hh_solve_host(h, fh, gh, uh, stream)
+        hh.hh_destroy(h)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    N = w.S * w.S
+    e2e = {"value": world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": 16 * (N + 4 * w.S), "d2h_bytes_per_step": 16 * N}
+
+    pk, pk_kind = peaks()
+    roof = roofline(w, prof_total, prof_iters, pk, pk_kind)
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": f"{w.S}x{w.S} nodes ({w.n}^2 interior)", "k": w.k,
+                   "levels": w.levels, "leaves": 2 ** w.levels, "overlap": w.overlap, "rank": w.rank,
+                   "oversample": w.oversample, "n_inner": w.n_inner, "tol_rel_residual": TOL,
+                   "precision": "mixed", "step": "setup+solve+release of one problem per rank",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
+        "iterations": {"mixed": statistics.median(iters), "fp64": statistics.median(fp64_iters)},
+        "fp64_form": {"value": world * len(fp64_ms) / (sum(fp64_ms) / 1e3), "unit": UNIT,
+                      "ms_per_step": statistics.mean(fp64_ms)},
+        "mixed_over_fp64": (value / world) / (len(fp64_ms) / (sum(fp64_ms) / 1e3)),
+        "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(w, f, g)
+    return out
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q / 100.0
+    lo, hi = int(k), min(int(k) + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def roofline(w, prof, iters, pk, pk_kind):
+    """Dominant kernel of the mixed form with its algorithmic rate against its peak."""
+    if not prof:
+        return None
+    name = max(prof, key=lambda k: prof[k][0])
+    ms, launches = prof[name]
+    n_runs = len(iters)
+    esz = 8
+    if name == "sweep":
+        m = min(w.rank + w.oversample, w.S)
+        r = min(w.rank, m)
+        per_run_cols = [m, m, r] * w.levels
+        byts = n_runs * sum(sweep_bytes(w, c, esz) for c in per_run_cols)
+        byts += sum(iters) * sweep_bytes(w, 1, esz)
+        achieved = byts / (ms / 1e3) / 1e9
+        peak = pk["hbm_gbs"]
+        return {"kernel": "k_sweep2d (leaf forward/backward block substitution)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "launches": launches, "avg_launch_ms": ms / max(launches, 1),
+                "peak_kind": f"{pk_kind} hbm_gbs", "share_of_profiled_ms": ms / sum(v[0] for v in prof.values())}
+    if name == "factor":
+        fl = n_runs * factor_flops(w)
+        achieved = fl / (ms / 1e3) / 1e12
+        peak = SM_COUNT * FP32_LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"kernel": "k_factor2d (Schur recursion, Gauss-Jordan inverses)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "launches": launches, "avg_launch_ms": ms / max(launches, 1),
+                "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock",
+                "share_of_profiled_ms": ms / sum(v[0] for v in prof.values())}
+    return {"kernel": name, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
+            "share_of_profiled_ms": ms / sum(v[0] for v in prof.values())}
+
+
+# ------------------------------------------------------------------ CPU baseline
+def cpu_baseline(w, f, g, n_solves=1):
+    """The FP64 oracle, as it stands, on the same workload: n one-shot solves."""
+    from oracle.method import OMethod
+    from oracle.problem import Problem
+    P = Problem(2, w.n, w.k)
+    t0 = time.perf_counter()
+    for _ in range(n_solves):
+        M = OMethod(P, w.levels, w.overlap, w.rank, w.oversample, n_inner=w.n_inner, seed=1)
+        M.solve(P.rhs(f, g), tol=TOL, maxit=MAX_ITER)
+    dt = time.perf_counter() - t0
+    return {"value": n_solves / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_solves} one-shot solve(s) (set-up + iteration to tol {TOL}) of {WORKLOAD}; "
+                      "numpy/scipy, BLAS threads up to the core count"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w, f, g = workload_inputs()
+    from oracle.method import OMethod
+    from oracle.problem import Problem
+    P = Problem(2, w.n, w.k)
+    b = P.rhs(f, g)
+
+    def step():
+        M = OMethod(P, w.levels, w.overlap, w.rank, w.oversample, n_inner=w.n_inner, seed=1)
+        M.solve(b, tol=TOL, maxit=MAX_ITER)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "tol_rel_residual": TOL, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} one-shot solves of {WORKLOAD}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

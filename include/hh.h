@@ -169,6 +169,20 @@ hh_status hh_precondition(hh_handle* h, const void* d_r, void* d_z, void* stream
  * the randomised SVD (SplitMix64 + Box-Muller, re/im ~ N(0, 1/2)). */
 hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
 
+/* --------------------------------------------------------------------------------
+ * Tracing.  With profiling enabled a handle records CUDA events on its stream around
+ * the kernels of each category below (events cost a few microseconds of stream time
+ * each); totals accumulate over hh_setup/hh_solve calls until the next enable.
+ * Categories: 0 leaf factorisation, 1 leaf sweeps, 2 FP64 global residual, 3 coarse
+ * projection C^H r, 4 Galerkin product, 5 sketch orthonormalisation, 6 sketch SVD.
+ * -------------------------------------------------------------------------------- */
+/* h != NULL: (re)start profiling of that handle, clearing its totals; h == NULL: set
+ * whether handles created afterwards profile from their first set-up kernel. */
+hh_status hh_profile_enable(hh_handle* h, int enable);
+hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches);
+/* Number of CUDA kernels this library has launched in the calling process. */
+unsigned long long hh_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

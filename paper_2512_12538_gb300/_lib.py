@@ -64,6 +64,9 @@ def _load():
         "hh_coarse_apply": (i, [vp, i, vp, vp, vp]),
         "hh_precondition": (i, [vp, vp, vp, vp]),
         "hh_sketch_samples": (i, [vp, i, vp, vp]),
+        "hh_profile_enable": (i, [vp, i]),
+        "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong)]),
+        "hh_launch_count": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,3 +223,25 @@ def hh_precondition(h, r, z, stream=None) -> None:
 
 def hh_sketch_samples(h, child, out, stream=None) -> None:
     _check(LIB.hh_sketch_samples(h, child, _ptr(out), _stream(stream)), "hh_sketch_samples")
+
+
+PROFILE_CATEGORIES = ["factor", "sweep", "residual", "coarse_project", "galerkin", "qr", "svd"]
+
+
+def hh_profile_enable(h, enable=True) -> None:
+    _check(LIB.hh_profile_enable(h, int(bool(enable))), "hh_profile_enable")
+
+
+def hh_profile_read(h) -> dict:
+    """{category: (total_ms, launches)} for every profiler category."""
+    out = {}
+    for i, name in enumerate(PROFILE_CATEGORIES):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(LIB.hh_profile_read(h, i, ctypes.byref(ms), ctypes.byref(n)), "hh_profile_read")
+        out[name] = (ms.value, n.value)
+    return out
+
+
+def hh_launch_count() -> int:
+    return int(LIB.hh_launch_count())

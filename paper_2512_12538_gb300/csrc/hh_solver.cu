@@ -18,6 +18,7 @@
 // Storage: node vectors [rows][Sx][ncols] (column index fastest); a child's input is a
 // contiguous row window of its parent's residual buffer.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -27,6 +28,14 @@
 #include "kernels.h"
 
 namespace hh {
+
+// ------------------------------------------------------------------ launch counter
+static std::atomic<unsigned long long> g_launches{0};
+static bool g_prof_default = false;   // profiling state of newly created handles
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Kernel categories timed by the optional event profiler (hh_profile_*).
+enum ProfCat { PC_FACTOR = 0, PC_SWEEP, PC_SPMV, PC_COARSE, PC_GALERKIN, PC_QR, PC_JACOBI, PC_NCAT };
 
 // ----------------------------------------------------------------- allocator hook
 struct AllocHook {
@@ -135,7 +144,50 @@ struct SolverBase {
     size_t footprint = 0;
     cudaStream_t stream = nullptr;
     double t_setup_ms = 0.0, t_solve_ms = 0.0;
-    virtual ~SolverBase() {}
+    // event profiler: pairs recorded around the kernels of one category
+    struct EvPair { cudaEvent_t a, b; int cat; };
+    bool prof_on = false;
+    std::vector<EvPair> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[PC_NCAT] = {0};
+    long long prof_n[PC_NCAT] = {0};
+    cudaEvent_t prof_ev() {
+        if (!prof_pool.empty()) { cudaEvent_t e = prof_pool.back(); prof_pool.pop_back(); return e; }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void pbeg(int cat) {
+        if (!prof_on) return;
+        EvPair p{prof_ev(), nullptr, cat};
+        cudaEventRecord(p.a, stream);
+        prof_pending.push_back(p);
+    }
+    void pend() {
+        if (!prof_on || prof_pending.empty() || prof_pending.back().b) return;
+        prof_pending.back().b = prof_ev();
+        cudaEventRecord(prof_pending.back().b, stream);
+    }
+    void prof_collect() {   // call after synchronising the stream
+        for (auto& p : prof_pending) {
+            float ms = 0.f;
+            if (p.b && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                prof_ms[p.cat] += ms;
+                prof_n[p.cat] += 1;
+            }
+            prof_pool.push_back(p.a);
+            if (p.b) prof_pool.push_back(p.b);
+        }
+        prof_pending.clear();
+    }
+    void prof_reset(bool on) {
+        prof_on = on;
+        for (int i = 0; i < PC_NCAT; ++i) { prof_ms[i] = 0; prof_n[i] = 0; }
+    }
+    virtual ~SolverBase() {
+        for (auto& p : prof_pending) { prof_pool.push_back(p.a); if (p.b) prof_pool.push_back(p.b); }
+        for (auto e : prof_pool) cudaEventDestroy(e);
+    }
     virtual size_t plan(char* base) = 0;
     virtual hh_status setup() = 0;
     virtual hh_status solve(const c128* f, const c128* g, c128* u, hh_stats* st) = 0;
@@ -197,7 +249,7 @@ struct Solver final : SolverBase {
         e = P.overlap / 2;
         m = std::min(P.rank + P.oversample, Sx);
         r = std::min(P.rank, m);
-        nmax = std::max(m, 1);
+        nmax = std::max(m, 4);   // columns of every node buffer (>= r + p)
         build_tree(S, L, e, nodes);
         nn = (int)nodes.size();
         lev.assign(L + 1, {});
@@ -317,10 +369,14 @@ struct Solver final : SolverBase {
     void apply_M(int l, int nc, bool own) {
         if (l == L) {
             if (own) {
+                pbeg(PC_SWEEP);
                 launch_sweep<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, nc, derr, stream);
+                pend();
             } else {
                 if (view_nc != nc) { upload_view_tasks(nc); view_nc = nc; }
+                pbeg(PC_SWEEP);
                 launch_sweep<T>(d_tasks_view, (int)lev[L].size(), b_max, Sx, nc, derr, stream);
+                pend();
             }
             return;
         }
@@ -346,8 +402,10 @@ struct Solver final : SolverBase {
     // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
     void coarse_correct(int p, const CT* vin, int nc) {
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
+        pbeg(PC_COARSE);
         const int nb = launch_ip_partial<T, T>(C[p], 2 * r, R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
                                                stream);
+        pend();
         launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
         launch_coarse_update<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
     }
@@ -372,7 +430,9 @@ struct Solver final : SolverBase {
         // Q = orth(Y)
         std::vector<CT*> ys;
         for (int c : cs) ys.push_back(Om[c]);
+        pbeg(PC_QR);
         launch_qr<T>(ys.data(), (int)ys.size(), Sx, m, (CT**)d_ptrs, stream);
+        pend();
         // Z = T_c^* Q = B_c conj(M_c conj(A~_s B_s^T ... )) ; here as conj(M_c(A~_s B_s^T conj Q))
         for (int c : cs) {
             const Node& cn = nodes[c];
@@ -392,7 +452,9 @@ struct Solver final : SolverBase {
         std::vector<c128*> gs, us;
         std::vector<double*> ls;
         for (int c : cs) { gs.push_back(Gm[c]); us.push_back(U[c]); ls.push_back(lam[c]); }
+        pbeg(PC_JACOBI);
         launch_jacobi(gs.data(), us.data(), ls.data(), (int)cs.size(), m, d_ptrs, stream);
+        pend();
         for (int c : cs) launch_form_v<T>(Z[c], U[c], lam[c], Vc[c], Sx, m, r, stream);
         // C_c = P_c M_c B_c^T V_c
         for (int c : cs) {
@@ -411,7 +473,9 @@ struct Solver final : SolverBase {
                    cerr);
             }
             // A_c = C_p^H A~_p C_p, then its inverse
+            pbeg(PC_GALERKIN);
             const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, partial, MAX_PART_BLOCKS, stream);
+            pend();
             launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
             launch_gj_inverse(Ainv[p], 2 * r, derr, stream);
         }
@@ -427,11 +491,14 @@ struct Solver final : SolverBase {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, stream);
+        pbeg(PC_FACTOR);
         launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
+        pend();
         for (int l = L; l >= 1; --l) sketch_level(l);
         cudaEventRecord(e1, stream);
         hh_status st;
         const bool ok = sync_check(st);
+        prof_collect();
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         t_setup_ms = ms;
@@ -487,7 +554,9 @@ struct Solver final : SolverBase {
         hh_status st = HH_OK;
         for (;;) {
             int nb = 0;
+            pbeg(PC_SPMV);
             launch_apply<double, double, double>(u, bvec, res, geom(0), 1, 1.0, npart, &nb, stream);
+            pend();
             launch_sum(npart, nb, dnorm, stream);
             ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
             if (!sync_check(st)) break;
@@ -502,6 +571,7 @@ struct Solver final : SolverBase {
         cudaEventRecord(e1, stream);
         hh_status st2;
         sync_check(st2);
+        prof_collect();
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         t_solve_ms = ms;
@@ -699,6 +769,7 @@ hh_status hh_setup(const hh_params* params, void* stream, hh_handle** out, size_
     s->block = hh::dev_alloc(s->footprint, s->stream, s->hook);
     if (!s->block) return HH_ENOMEM;
     s->plan((char*)s->block);
+    s->prof_reset(hh::g_prof_default);
     const hh_status st = s->setup();
     if (footprint_out) *footprint_out = s->footprint;
     if (st != HH_OK) return st;
@@ -790,6 +861,22 @@ hh_status hh_precondition(hh_handle* h, const void* d_r, void* d_z, void* stream
     h->s->stream = (cudaStream_t)stream;
     return h->s->precondition((const c128*)d_r, (c128*)d_z);
 }
+hh_status hh_profile_enable(hh_handle* h, int enable) {
+    if (!h) {
+        hh::g_prof_default = enable != 0;
+        return HH_OK;
+    }
+    h->s->prof_reset(enable != 0);
+    return HH_OK;
+}
+hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches) {
+    if (!h || category < 0 || category >= hh::PC_NCAT) return HH_EINVAL;
+    if (total_ms) *total_ms = h->s->prof_ms[category];
+    if (launches) *launches = h->s->prof_n[category];
+    return HH_OK;
+}
+unsigned long long hh_launch_count(void) { return hh::g_launches.load(); }
+
 hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream) {
     if (!h) return HH_EINVAL;
     h->s->stream = (cudaStream_t)stream;

@@ -99,6 +99,7 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
         attr_set = true;
     }
     k_ip_partial<TA, TB><<<grid, IP_THREADS, sm, s>>>(A, lda, B, ldb, N, p, q, partial);
+    note_launch();
     return grid;
 }
 
@@ -130,6 +131,7 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
         attr = true;
     }
     k_ip_reduce<<<1, 256, sizeof(c128) * p * q, s>>>(partial, nblk, p, q, out, Minv, out2);
+    note_launch();
 }
 
 // ------------------------------------------------------------------- Galerkin
@@ -188,6 +190,7 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, c128* partial, in
         attr_set = true;
     }
     k_galerkin_partial<T><<<grid, IP_THREADS, sm, s>>>(C, g, p, partial);
+    note_launch();
     return grid;
 }
 
@@ -238,6 +241,7 @@ template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s) {
     cudaMemcpyAsync(dev_ptr_scratch, Y, sizeof(cplx<T>*) * nq, cudaMemcpyHostToDevice, s);
     k_qr<T><<<nq, 512, 0, s>>>(dev_ptr_scratch, Sx, m);
+    note_launch();
 }
 
 // -------------------------------------------------------------- Jacobi (FP64)
@@ -366,6 +370,7 @@ void launch_jacobi(c128* const* G, c128* const* U, double* const* lam, int nq, i
     }
     k_jacobi<<<nq, 256, sm, s>>>((c128* const*)scratch, (c128* const*)(scratch + nq),
                                  (double* const*)(scratch + 2 * nq), m);
+    note_launch();
 }
 
 // V[x][j] = sum_k Z[x][k] U[k][j] / sqrt(lam_j)
@@ -389,6 +394,7 @@ void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* 
     const size_t total = (size_t)Sx * r;
     int grid = (int)((total + 255) / 256);
     k_form_v<T><<<grid, 256, 0, s>>>(Z, U, lam, V, Sx, m, r);
+    note_launch();
 }
 
 // ------------------------------------------------------- Gauss-Jordan (FP64)
@@ -472,6 +478,7 @@ void launch_gj_inverse(c128* A, int n, int* err, cudaStream_t s) {
         attr = true;
     }
     k_gj_inverse<<<1, 256, sm, s>>>(A, n, err);
+    note_launch();
 }
 
 // ------------------------------------------------------------ instantiations

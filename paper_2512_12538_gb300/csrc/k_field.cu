@@ -64,6 +64,7 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
     const int th = 256;
     const int grid = grid_for(total, th, 152 * 8);
     k_apply<TX, TV, TY><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    note_launch();
     if (nblk_out) *nblk_out = grid;
 }
 
@@ -82,6 +83,7 @@ __global__ void k_sum(const double* part, int n, double* out) {
 }
 void launch_sum(const double* part, int n, double* out, cudaStream_t s) {
     k_sum<<<1, 256, 0, s>>>(part, n, out);
+    note_launch();
 }
 
 // --------------------------------------------------------------------------- rhs
@@ -109,6 +111,7 @@ __global__ void k_rhs(const c128* __restrict__ f, const c128* __restrict__ g, c1
 void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s) {
     const size_t total = (size_t)S * (dim == 2 ? S : 1);
     k_rhs<<<grid_for(total, 256), 256, 0, s>>>(f, g, b, dim, S, h);
+    note_launch();
 }
 
 // -------------------------------------------------------------------------- copy
@@ -126,6 +129,7 @@ void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, 
                  cudaStream_t s) {
     if (n == 0) return;
     k_copy<TS, TD><<<grid_for(n, 256), 256, 0, s>>>(src, dst, n, accumulate, conjugate);
+    note_launch();
 }
 
 // ------------------------------------------------------------- interface traces
@@ -155,6 +159,7 @@ void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, in
                         double kh, cudaStream_t s) {
     const size_t total = (size_t)Sx * nc;
     k_robin_trace<T><<<grid_for(total, 256), 256, 0, s>>>(u_if, u_in, Y, b_s, Sx, nc, kh);
+    note_launch();
 }
 
 template <typename T>
@@ -181,6 +186,7 @@ void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_
                           double kh, cudaStream_t s) {
     const size_t total = (size_t)Sx * nc;
     k_adjoint_place<T><<<grid_for(total, 256), 256, 0, s>>>(Q, v_if, v_in, b_s, Sx, nc, kh);
+    note_launch();
 }
 
 // ------------------------------------------------------------------ sketch (RNG)
@@ -212,6 +218,7 @@ __global__ void k_sketch(cplx<T>* Om, int Sx, int m, int node, unsigned long lon
 template <typename T>
 void launch_sketch(cplx<T>* Om, int Sx, int m, int node, unsigned long long seed, cudaStream_t s) {
     k_sketch<T><<<grid_for((size_t)Sx * m, 256), 256, 0, s>>>(Om, Sx, m, node, seed);
+    note_launch();
 }
 
 // ---------------------------------------------------------------- coarse update
@@ -237,6 +244,7 @@ void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t 
                           cudaStream_t s) {
     const size_t total = npts * nc;
     k_coarse_update<TC, TW><<<grid_for(total, 256), 256, sizeof(c128) * p * nc, s>>>(C, y, W, npts, p, nc);
+    note_launch();
 }
 
 // ------------------------------------------------------------ instantiations

@@ -150,11 +150,13 @@ template <typename T>
 void launch_factor(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err, cudaStream_t s) {
     if (Sx == 1) {
         k_factor1d<T><<<(ntasks + 31) / 32, 32, 0, s>>>(d_tasks, ntasks, kh, err);
+        note_launch();
         return;
     }
     const size_t sm = sizeof(cplx<T>) * ((size_t)b_max * b_max + 2 * b_max) + sizeof(int) * b_max;
     cudaFuncSetAttribute(k_factor2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_factor2d<T><<<ntasks, 256, sm, s>>>(d_tasks, Sx, kh, err);
+    note_launch();
 }
 
 // ------------------------------------------------------------------ sweep (2D)
@@ -330,6 +332,7 @@ static void sweep_cfg(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, in
     cudaFuncSetAttribute(k_sweep2d<T, NC, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((nrhs + NC - 1) / NC, ntasks);
     k_sweep2d<T, NC, G><<<grid, threads, sm, s>>>(d_tasks, Sx, nrhs, nslot, prow, slot_bytes / esz, err);
+    note_launch();
 }
 
 template <typename T>
@@ -337,6 +340,7 @@ void launch_sweep(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, int nr
     if (Sx == 1) {
         dim3 grid((nrhs + 63) / 64, ntasks);
         k_sweep1d<T><<<grid, 64, 0, s>>>(d_tasks, nrhs);
+        note_launch();
         return;
     }
     // prow * G threads must fit in one CTA; rows beyond are handled as further pieces

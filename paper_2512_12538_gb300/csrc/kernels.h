@@ -5,6 +5,9 @@
 
 namespace hh {
 
+// Counts kernel launches made by this library (process-wide); see hh_launch_count().
+void note_launch();
+
 // ---- field kernels (k_field.cu) ----------------------------------------------------
 // y = (v ? v : 0) - sgn * A~ x  on a band (b rows, Sx cols, nc columns per point).
 // With `v` null and sgn = -1 this is y = A~ x.  If `part` is non-null each block writes
