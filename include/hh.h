@@ -74,7 +74,22 @@ typedef struct {
     int max_iter;         /* outer iterations, >= 1                                      */
     int precision;        /* hh_precision                                                */
     unsigned long long seed;  /* sketch generator seed                                  */
+    int leaf_solver;      /* hh_leaf_solver                                              */
+    int outer;            /* hh_outer                                                    */
+    int restart;          /* Krylov vectors per GMRES cycle (outer = HH_OUTER_GMRES), 1..64 */
 } hh_params;
+
+typedef enum {
+    HH_LEAF_EIGEN = 0,    /* 2D leaves: the block Schur recursion evaluated in the eigenbasis */
+                          /* of the column pencil (scalar recursions + two b x b transforms)  */
+    HH_LEAF_BLOCK = 1     /* 2D leaves: the block Schur recursion with explicit b x b inverses */
+                          /* S_j^{-1} (Gauss-Jordan, partial pivoting) and block substitution  */
+} hh_leaf_solver;         /* 1D leaves always use the scalar recursion along the line         */
+
+typedef enum {
+    HH_OUTER_ORAS = 0,    /* stationary iteration u <- u + M (b - A u) (Eqs. (2)-(3))          */
+    HH_OUTER_GMRES = 1    /* flexible GMRES right-preconditioned by M (Sec. 3), FP64 Arnoldi   */
+} hh_outer;
 
 typedef struct {
     int iters;            /* outer iterations taken                                      */

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "libhh.so")
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ENOCONV, HH_EBREAKDOWN, HH_ETIMEOUT, HH_ECUDA, HH_ENOTIMPL = (
     0, -1, -2, -3, -4, -5, -6, -7)
 HH_PREC_FP64, HH_PREC_MIXED = 0, 1
+HH_LEAF_EIGEN, HH_LEAF_BLOCK = 0, 1
+HH_OUTER_ORAS, HH_OUTER_GMRES = 0, 1
 
 
 class hh_params(ctypes.Structure):
@@ -23,7 +25,8 @@ class hh_params(ctypes.Structure):
                 ("levels", ctypes.c_int), ("overlap", ctypes.c_int), ("rank", ctypes.c_int),
                 ("oversample", ctypes.c_int), ("n_inner", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong), ("leaf_solver", ctypes.c_int), ("outer", ctypes.c_int),
+                ("restart", ctypes.c_int)]
 
 
 class hh_stats(ctypes.Structure):
@@ -106,11 +109,16 @@ def _check(st: int, where: str, ok=(HH_OK,)):
 
 
 def make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, n_inner=1,
-                tol=1e-10, max_iter=200, precision=HH_PREC_FP64, seed=0) -> hh_params:
+                tol=1e-10, max_iter=200, precision=HH_PREC_FP64, seed=0, leaf_solver=HH_LEAF_EIGEN,
+                outer=HH_OUTER_ORAS, restart=40) -> hh_params:
     if isinstance(precision, str):
         precision = {"fp64": HH_PREC_FP64, "mixed": HH_PREC_MIXED}[precision]
+    if isinstance(leaf_solver, str):
+        leaf_solver = {"eigen": HH_LEAF_EIGEN, "block": HH_LEAF_BLOCK}[leaf_solver]
+    if isinstance(outer, str):
+        outer = {"oras": HH_OUTER_ORAS, "gmres": HH_OUTER_GMRES}[outer]
     return hh_params(dim, n, float(k), levels, overlap, rank, oversample, n_inner, float(tol), max_iter,
-                     precision, seed)
+                     precision, seed, leaf_solver, outer, restart)
 
 
 # ------------------------------------------------------------------ allocator hook

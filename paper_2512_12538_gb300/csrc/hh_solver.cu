@@ -111,11 +111,20 @@ static hh_status validate(const hh_params* P) {
     if (P->rank < 1 || P->oversample < 0 || P->n_inner < 1) return HH_EINVAL;
     if (!(P->tol > 0.0) || P->max_iter < 1) return HH_EINVAL;
     if (P->precision != HH_PREC_FP64 && P->precision != HH_PREC_MIXED) return HH_EINVAL;
+    if (P->leaf_solver != HH_LEAF_EIGEN && P->leaf_solver != HH_LEAF_BLOCK) return HH_EINVAL;
+    if (P->outer != HH_OUTER_ORAS && P->outer != HH_OUTER_GMRES) return HH_EINVAL;
+    if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
+    if (P->levels > 6) return HH_EINVAL;
     const int Sx = P->dim == 2 ? P->n + 2 : 1;
     const int m = std::min(P->rank + P->oversample, Sx);
     if (2 * std::min(P->rank, m) > 64 || m > 64) return HH_EINVAL;   // dense coarse kernels
     std::vector<Node> nodes;
-    return build_tree(P->n + 2, P->levels, P->overlap / 2, nodes);
+    const hh_status st = build_tree(P->n + 2, P->levels, P->overlap / 2, nodes);
+    if (st != HH_OK) return st;
+    if (P->dim == 2 && P->leaf_solver == HH_LEAF_EIGEN)
+        for (auto& nd : nodes)
+            if (nd.leaf() && nd.b() > eig_bmax()) return HH_EINVAL;   // band too tall for this path
+    return HH_OK;
 }
 
 // ----------------------------------------------------------------- arena planning
@@ -224,6 +233,16 @@ struct Solver final : SolverBase {
     double *npart = nullptr, *dnorm = nullptr;
     int* derr = nullptr;
     LeafTask *d_tasks_view = nullptr, *d_tasks_own = nullptr, *d_task_one = nullptr;
+    // eigenbasis leaf path
+    bool eig = false;
+    std::vector<CT*> EV, EXI, EFh;
+    std::vector<c128*> ELAM, EWK;
+    EigTask *d_etasks_view = nullptr, *d_etasks_own = nullptr, *d_etask_one = nullptr;
+    // flexible GMRES
+    int mk = 0;                                   // restart length
+    c128 *Vb = nullptr, *Zb = nullptr, *gw = nullptr, *gv = nullptr, *gz = nullptr, *gdots = nullptr,
+         *gy = nullptr;
+    c128* h_dots = nullptr;                       // pinned host copy of the dot products
     void** d_ptrs = nullptr;
     double* h_norm = nullptr;   // pinned host
     int b_max = 0;
@@ -231,6 +250,7 @@ struct Solver final : SolverBase {
 
     ~Solver() override {
         if (h_norm) cudaFreeHost(h_norm);
+        if (h_dots) cudaFreeHost(h_dots);
         if (block) dev_free(block, footprint, stream, hook);
         if (stream) cudaStreamSynchronize(stream);
     }
@@ -257,6 +277,8 @@ struct Solver final : SolverBase {
         b_max = 0;
         for (auto& nd : nodes)
             if (nd.leaf()) b_max = std::max(b_max, nd.b());
+        eig = (Sx > 1 && P.leaf_solver == HH_LEAF_EIGEN);
+        mk = P.outer == HH_OUTER_GMRES ? P.restart : 0;
     }
 
     size_t plan(char* base) override {
@@ -266,6 +288,8 @@ struct Solver final : SolverBase {
         X.assign(nn, nullptr); Om.assign(nn, nullptr); Z.assign(nn, nullptr); Vc.assign(nn, nullptr);
         Ainv.assign(nn, nullptr); ycoef.assign(nn, nullptr); Gm.assign(nn, nullptr); U.assign(nn, nullptr);
         lam.assign(nn, nullptr); ldx.assign(nn, 0);
+        EV.assign(nn, nullptr); EXI.assign(nn, nullptr); EFh.assign(nn, nullptr);
+        ELAM.assign(nn, nullptr); EWK.assign(nn, nullptr);
         const size_t N = (size_t)Sy * Sx;
         u = a.take<c128>(N); ut = a.take<c128>(N); bvec = a.take<c128>(N); res = a.take<c128>(N);
         gbuf = a.take<c128>(4 * (size_t)S);
@@ -288,6 +312,13 @@ struct Solver final : SolverBase {
                 C[id] = a.take<CT>(np * 2 * r);
                 Ainv[id] = a.take<c128>((size_t)4 * r * r);
                 ycoef[id] = a.take<c128>((size_t)2 * r * nmax);
+            } else if (eig) {
+                const int b = nd.b();
+                EV[id] = a.take<CT>((size_t)b * b);
+                EXI[id] = a.take<CT>((size_t)Sx * b);
+                ELAM[id] = a.take<c128>(b);
+                EFh[id] = a.take<CT>(np * nmax);
+                EWK[id] = a.take<c128>(eig_work_elems(b));
             } else {
                 ldx[id] = leaf_ldx(nd.b(), (int)sizeof(CT));
                 X[id] = a.take<CT>(Sx == 1 ? (size_t)nd.b() : (size_t)Sx * nd.b() * ldx[id]);
@@ -302,6 +333,18 @@ struct Solver final : SolverBase {
         d_tasks_view = a.take<LeafTask>(nleaf);
         d_tasks_own = a.take<LeafTask>(nleaf);
         d_task_one = a.take<LeafTask>(1);
+        d_etasks_view = a.take<EigTask>(nleaf);
+        d_etasks_own = a.take<EigTask>(nleaf);
+        d_etask_one = a.take<EigTask>(1);
+        if (mk > 0) {
+            Vb = a.take<c128>(N * (mk + 1));
+            Zb = a.take<c128>(N * mk);
+            gw = a.take<c128>(N);
+            gv = a.take<c128>(N);
+            gz = a.take<c128>(N);
+            gdots = a.take<c128>(4 * 80);
+            gy = a.take<c128>(80);
+        }
         d_ptrs = a.take<void*>(3 * 64);
         return align_up(a.off, 256);
     }
@@ -357,6 +400,43 @@ struct Solver final : SolverBase {
     }
     int view_nc = -1;
 
+    EigTask eig_task(int id, const void* F, void* Wout) const {
+        EigTask k;
+        k.V = EV[id];
+        k.xi = EXI[id];
+        k.lam = ELAM[id];
+        k.F = F;
+        k.Fh = EFh[id];
+        k.W = Wout;
+        k.work = EWK[id];
+        k.b = nodes[id].b();
+        return k;
+    }
+    void upload_eig_view_tasks(int nc) {
+        std::vector<EigTask> t;
+        for (int id : lev[L]) {
+            const Node& nd = nodes[id];
+            t.push_back(eig_task(id, R[nd.parent] + row_off(nd.parent, nd.ra, nc), W[id]));
+        }
+        ck(cudaMemcpyAsync(d_etasks_view, t.data(), sizeof(EigTask) * t.size(), cudaMemcpyHostToDevice, stream),
+           cerr);
+    }
+    // all leaves: W[leaf] = A~_leaf^{-1} F (F = own buffers or views into the parents)
+    void leaf_sweep_all(int nc, bool own) {
+        const int nl = (int)lev[L].size();
+        if (eig) {
+            if (!own && view_nc != nc) { upload_eig_view_tasks(nc); view_nc = nc; }
+            pbeg(PC_SWEEP);
+            launch_eig_sweep<T>(own ? d_etasks_own : d_etasks_view, nl, b_max, Sx, nc, stream);
+            pend();
+            return;
+        }
+        if (!own && view_nc != nc) { upload_view_tasks(nc); view_nc = nc; }
+        pbeg(PC_SWEEP);
+        launch_sweep<T>(own ? d_tasks_own : d_tasks_view, nl, b_max, Sx, nc, derr, stream);
+        pend();
+    }
+
     // Input of node id at the top level of an apply: its own buffer or a view into
     // the parent's residual.
     const CT* input(int id, int nc, bool own) const {
@@ -368,16 +448,7 @@ struct Solver final : SolverBase {
     // ------------------------------------------------- sub-level solve M at level l
     void apply_M(int l, int nc, bool own) {
         if (l == L) {
-            if (own) {
-                pbeg(PC_SWEEP);
-                launch_sweep<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, nc, derr, stream);
-                pend();
-            } else {
-                if (view_nc != nc) { upload_view_tasks(nc); view_nc = nc; }
-                pbeg(PC_SWEEP);
-                launch_sweep<T>(d_tasks_view, (int)lev[L].size(), b_max, Sx, nc, derr, stream);
-                pend();
-            }
+            leaf_sweep_all(nc, own);
             return;
         }
         for (int it = 0; it < P.n_inner; ++it) {
@@ -484,15 +555,25 @@ struct Solver final : SolverBase {
     hh_status setup() override {
         zero(derr, sizeof(int) * 4);
         for (int id = 1; id < nn; ++id) zero(Vs[id], sizeof(CT) * pts(id) * nmax);
-        std::vector<LeafTask> own = leaf_tasks(true);
-        ck(cudaMemcpyAsync(d_tasks_own, own.data(), sizeof(LeafTask) * own.size(), cudaMemcpyHostToDevice, stream),
-           cerr);
+        if (eig) {
+            std::vector<EigTask> own;
+            for (int id : lev[L]) own.push_back(eig_task(id, Vs[id], W[id]));
+            ck(cudaMemcpyAsync(d_etasks_own, own.data(), sizeof(EigTask) * own.size(), cudaMemcpyHostToDevice,
+                               stream),
+               cerr);
+        } else {
+            std::vector<LeafTask> own = leaf_tasks(true);
+            ck(cudaMemcpyAsync(d_tasks_own, own.data(), sizeof(LeafTask) * own.size(), cudaMemcpyHostToDevice,
+                               stream),
+               cerr);
+        }
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, stream);
         pbeg(PC_FACTOR);
-        launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
+        if (eig) launch_eig_factor<T>(d_etasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
+        else launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
         pend();
         for (int l = L; l >= 1; --l) sketch_level(l);
         cudaEventRecord(e1, stream);
@@ -506,6 +587,7 @@ struct Solver final : SolverBase {
         cudaEventDestroy(e1);
         if (!ok) return st;
         ck(cudaMallocHost(&h_norm, 4 * sizeof(double)), cerr);
+        if (mk > 0) ck(cudaMallocHost(&h_dots, 4 * 80 * sizeof(c128)), cerr);
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
 
@@ -539,6 +621,118 @@ struct Solver final : SolverBase {
         return HH_OK;
     }
 
+    // z = M v: one coarse-corrected ORAS step from zero (v, z distinct from res and ut)
+    void precond(const c128* v, c128* z) {
+        d2d(res, v, sizeof(c128) * (size_t)Sy * Sx);
+        oras_step(nullptr, v, z);
+    }
+
+    // ||b - A u||^2 into h_norm[0] (synchronises); ||b||^2 must be in dnorm[2].
+    bool true_residual(c128* dst, hh_status& st) {
+        int nb = 0;
+        pbeg(PC_SPMV);
+        launch_apply<double, double, double>(u, bvec, dst, geom(0), 1, 1.0, npart, &nb, stream);
+        pend();
+        launch_sum(npart, nb, dnorm, stream);
+        ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        return sync_check(st);
+    }
+
+    // Stationary iteration u <- u + M (b - A u)  (Eqs. (2)-(3)).
+    hh_status loop_oras(int& it, double& rel) {
+        hh_status st = HH_OK;
+        for (;;) {
+            if (!true_residual(res, st)) return st;
+            rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
+            if (!std::isfinite(rel)) return HH_ENOCONV;
+            if (rel < P.tol) return HH_OK;
+            if (it >= P.max_iter) return HH_ENOCONV;
+            oras_step(u, bvec, u);
+            ++it;
+        }
+    }
+
+    // Flexible GMRES(mk) right-preconditioned by M (Sec. 3 solves the preconditioned
+    // system by GMRES).  Arnoldi in FP64 with classical Gram-Schmidt applied twice; the
+    // preconditioned directions z_j = M v_j are kept, so M may vary between steps (the
+    // complex64 form).  Convergence is tested on the recurrence residual and confirmed
+    // on the true residual at every restart.
+    hh_status loop_gmres(int& it, double& rel) {
+        const size_t N = (size_t)Sy * Sx;
+        const int ld = mk + 1;
+        hh_status st = HH_OK;
+        const c128 one = {1.0, 0.0};
+        c128* gone = gdots + 3 * 80;
+        ck(cudaMemcpyAsync(gone, &one, sizeof(c128), cudaMemcpyHostToDevice, stream), cerr);
+        std::vector<c128> H((size_t)(mk + 1) * mk), sn(mk), gq(mk + 1), y(mk);
+        std::vector<double> cs(mk);
+        const double nbv = std::sqrt(std::max(h_norm[2], 0.0));
+        for (;;) {
+            if (!true_residual(gw, st)) return st;
+            const double beta = std::sqrt(std::max(h_norm[0], 0.0));
+            rel = nbv > 0 ? beta / nbv : 0.0;
+            if (!std::isfinite(rel)) return HH_ENOCONV;
+            if (rel < P.tol) return HH_OK;
+            if (it >= P.max_iter) return HH_ENOCONV;
+            launch_col_store_normalised(Vb, ld, 0, gw, (const c128*)dnorm, N, stream);
+            std::fill(gq.begin(), gq.end(), c128{0.0, 0.0});
+            gq[0] = {beta, 0.0};
+            int j = 0;
+            while (j < mk && it < P.max_iter) {
+                launch_col_load(Vb, ld, j, gv, N, stream);
+                precond(gv, gz);
+                launch_col_store_normalised(Zb, mk, j, gz, gone, N, stream);
+                launch_apply<double, double, double>(gz, nullptr, gw, geom(0), 1, -1.0, nullptr, nullptr, stream);
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int nbk = launch_ip_partial<double, double>(gw, 1, Vb, ld, N, 1, j + 1, partial,
+                                                                      MAX_PART_BLOCKS, stream);
+                    launch_ip_reduce(partial, nbk, 1, j + 1, gdots + pass * 80, nullptr, nullptr, stream);
+                    launch_basis_combine(Vb, ld, j + 1, gdots + pass * 80, true, -1.0, gw, N, stream);
+                }
+                const int nbn = launch_ip_partial<double, double>(gw, 1, gw, 1, N, 1, 1, partial, MAX_PART_BLOCKS,
+                                                                  stream);
+                launch_ip_reduce(partial, nbn, 1, 1, gdots + 160, nullptr, nullptr, stream);
+                launch_col_store_normalised(Vb, ld, j + 1, gw, gdots + 160, N, stream);
+                ck(cudaMemcpyAsync(h_dots, gdots, sizeof(c128) * 3 * 80, cudaMemcpyDeviceToHost, stream), cerr);
+                if (!sync_check(st)) return st;
+                // column j of the Hessenberg matrix: h_ij = conj(sum conj(w) v_i) over both passes
+                for (int i = 0; i <= j; ++i) H[(size_t)i * mk + j] = conj(h_dots[i]) + conj(h_dots[80 + i]);
+                const double hn = std::sqrt(std::max(h_dots[160].re, 0.0));
+                for (int i = 0; i < j; ++i) {
+                    const c128 a0 = H[(size_t)i * mk + j], a1 = H[(size_t)(i + 1) * mk + j];
+                    H[(size_t)i * mk + j] = cs[i] * a0 + sn[i] * a1;
+                    H[(size_t)(i + 1) * mk + j] = cs[i] * a1 - conj(sn[i]) * a0;
+                }
+                const c128 a = H[(size_t)j * mk + j];
+                const double aa = std::sqrt(abs2(a)), t = std::sqrt(abs2(a) + hn * hn);
+                if (t == 0.0) { cs[j] = 1.0; sn[j] = {0.0, 0.0}; }
+                else if (aa == 0.0) { cs[j] = 0.0; sn[j] = {1.0, 0.0}; H[(size_t)j * mk + j] = {hn, 0.0}; }
+                else {
+                    const c128 ph = (1.0 / aa) * a;
+                    cs[j] = aa / t;
+                    sn[j] = (hn / t) * ph;
+                    H[(size_t)j * mk + j] = t * ph;
+                }
+                gq[j + 1] = -(conj(sn[j]) * gq[j]);
+                gq[j] = cs[j] * gq[j];
+                ++j;
+                ++it;
+                const double est = nbv > 0 ? std::sqrt(abs2(gq[j])) / nbv : 0.0;
+                if (!std::isfinite(est)) return HH_ENOCONV;
+                if (est < 0.5 * P.tol || hn == 0.0) break;
+            }
+            // y = R^{-1} g  (j x j upper triangular), u += Z y
+            for (int i = j - 1; i >= 0; --i) {
+                c128 acc = gq[i];
+                for (int k = i + 1; k < j; ++k) acc = acc - H[(size_t)i * mk + k] * y[k];
+                const c128 d = H[(size_t)i * mk + i];
+                y[i] = abs2(d) > 0 ? acc * cinv(d) : c128{0.0, 0.0};
+            }
+            ck(cudaMemcpyAsync(gy, y.data(), sizeof(c128) * j, cudaMemcpyHostToDevice, stream), cerr);
+            launch_basis_combine(Zb, mk, j, gy, false, 1.0, u, N, stream);
+        }
+    }
+
     hh_status solve(const c128* f, const c128* g, c128* uo, hh_stats* stt) override {
         const size_t N = (size_t)Sy * Sx;
         zero(derr, sizeof(int) * 4);
@@ -548,25 +742,12 @@ struct Solver final : SolverBase {
         cudaEventRecord(e0, stream);
         launch_rhs(f, g, bvec, P.dim, S, h, stream);
         norm_sq(bvec, dnorm + 2);   // dnorm[2..3] = ||b||^2 as a complex
+        ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
         zero(u, sizeof(c128) * N);
         int it = 0;
         double rel = 0.0;
         hh_status st = HH_OK;
-        for (;;) {
-            int nb = 0;
-            pbeg(PC_SPMV);
-            launch_apply<double, double, double>(u, bvec, res, geom(0), 1, 1.0, npart, &nb, stream);
-            pend();
-            launch_sum(npart, nb, dnorm, stream);
-            ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
-            if (!sync_check(st)) break;
-            rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
-            if (!std::isfinite(rel)) { st = HH_ENOCONV; break; }
-            if (rel < P.tol) break;
-            if (it >= P.max_iter) { st = HH_ENOCONV; break; }
-            oras_step(u, bvec, u);
-            ++it;
-        }
+        if (sync_check(st)) st = mk > 0 ? loop_gmres(it, rel) : loop_oras(it, rel);
         d2d(uo, u, sizeof(c128) * N);
         cudaEventRecord(e1, stream);
         hh_status st2;
@@ -624,14 +805,20 @@ struct Solver final : SolverBase {
         if (!valid_node(id) || !nodes[id].leaf() || nc < 1 || nc > nmax || !v || !x) return HH_EINVAL;
         const size_t n = pts(id) * nc;
         launch_copy<double, T>(v, Vs[id], n, false, false, stream);
-        LeafTask k;
-        k.X = X[id];
-        k.F = Vs[id];
-        k.W = W[id];
-        k.b = nodes[id].b();
-        k.ldx = ldx[id];
-        ck(cudaMemcpyAsync(d_task_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
-        launch_sweep<T>(d_task_one, 1, nodes[id].b(), Sx, nc, derr, stream);
+        if (eig) {
+            EigTask k = eig_task(id, Vs[id], W[id]);
+            ck(cudaMemcpyAsync(d_etask_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
+            launch_eig_sweep<T>(d_etask_one, 1, nodes[id].b(), Sx, nc, stream);
+        } else {
+            LeafTask k;
+            k.X = X[id];
+            k.F = Vs[id];
+            k.W = W[id];
+            k.b = nodes[id].b();
+            k.ldx = ldx[id];
+            ck(cudaMemcpyAsync(d_task_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
+            launch_sweep<T>(d_task_one, 1, nodes[id].b(), Sx, nc, derr, stream);
+        }
         launch_copy<T, double>(W[id], x, n, false, false, stream);
         hh_status st;
         sync_check(st);

@@ -247,6 +247,51 @@ void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t 
     note_launch();
 }
 
+// --------------------------------------------------------- Krylov basis helpers
+// Basis matrices are stored point-major: B[n * ld + j] is entry n of basis vector j.
+__global__ void k_col_load(const c128* __restrict__ B, int ld, int col, c128* __restrict__ dst, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        dst[t] = B[t * ld + col];
+}
+void launch_col_load(const c128* B, int ld, int col, c128* dst, size_t n, cudaStream_t s) {
+    k_col_load<<<grid_for(n, 256), 256, 0, s>>>(B, ld, col, dst, n);
+    note_launch();
+}
+// B[n][col] = src[n] / sqrt(*nrm2)   (nrm2 read on the device; zero if nrm2 == 0)
+__global__ void k_col_store_normalised(c128* __restrict__ B, int ld, int col, const c128* __restrict__ src,
+                                       const c128* __restrict__ nrm2, size_t n) {
+    const double v = nrm2->re;
+    const double sc = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        B[t * ld + col] = sc * src[t];
+}
+void launch_col_store_normalised(c128* B, int ld, int col, const c128* src, const c128* nrm2, size_t n,
+                                 cudaStream_t s) {
+    k_col_store_normalised<<<grid_for(n, 256), 256, 0, s>>>(B, ld, col, src, nrm2, n);
+    note_launch();
+}
+// w[n] += sgn * sum_{i<j} B[n][i] * c_i, with c_i = conj(coef[i]) if cj else coef[i]
+__global__ void k_basis_combine(const c128* __restrict__ B, int ld, int j, const c128* __restrict__ coef, bool cj,
+                                double sgn, c128* __restrict__ w, size_t n) {
+    __shared__ c128 cs[128];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        const c128 c = cj ? conj(coef[i]) : coef[i];
+        cs[i] = sgn * c;
+    }
+    __syncthreads();
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        c128 a = w[t];
+        const c128* br = B + t * ld;
+        for (int i = 0; i < j; ++i) cfma(a, br[i], cs[i]);
+        w[t] = a;
+    }
+}
+void launch_basis_combine(const c128* B, int ld, int j, const c128* coef, bool cj, double sgn, c128* w, size_t n,
+                          cudaStream_t s) {
+    k_basis_combine<<<grid_for(n, 256), 256, 0, s>>>(B, ld, j, coef, cj, sgn, w, n);
+    note_launch();
+}
+
 // ------------------------------------------------------------ instantiations
 #define HH_APPLY(TX, TV, TY)                                                                           \
     template void launch_apply<TX, TV, TY>(const cplx<TX>*, const cplx<TV>*, cplx<TY>*, OpGeom, int, \

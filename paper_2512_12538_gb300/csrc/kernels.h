@@ -48,6 +48,14 @@ template <typename TC, typename TW>
 void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t npts, int p, int nc,
                           cudaStream_t s);
 
+// Krylov bases, point-major B[n * ld + j]:
+void launch_col_load(const c128* B, int ld, int col, c128* dst, size_t n, cudaStream_t s);
+void launch_col_store_normalised(c128* B, int ld, int col, const c128* src, const c128* nrm2, size_t n,
+                                 cudaStream_t s);
+// w += sgn * B[:, :j] c   (c = conj(coef) if cj), coef on the device, j <= 128
+void launch_basis_combine(const c128* B, int ld, int j, const c128* coef, bool cj, double sgn, c128* w, size_t n,
+                          cudaStream_t s);
+
 // ---- dense kernels (k_dense.cu) ----------------------------------------------------
 // partial[blk][i][j] = sum_{n in blk} conj(A[n*lda+i]) * B[n*ldb+j]; returns nblk.
 template <typename TA, typename TB>
@@ -89,5 +97,24 @@ template <typename T>
 void launch_sweep(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, int* err,
                   cudaStream_t s);
 int leaf_ldx(int b, int elem_bytes);
+
+// ---- eigenbasis leaf path (k_eig.cu) -------------------------------------------------
+struct EigTask {
+    void* V;          // [b][b] generalised eigenvectors of the column pencil (V^T W V = I)
+    void* xi;         // [Sx][b] scalar Schur recursion coefficients
+    void* lam;        // [b] eigenvalues (complex128)
+    const void* F;    // right-hand sides [b][Sx][nrhs]
+    void* Fh;         // transformed right-hand sides / solutions [b][Sx][nrhs]
+    void* W;          // solutions [b][Sx][nrhs]
+    void* work;       // set-up workspace, eig_work_elems(b) complex128
+    int b;
+};
+template <typename T>
+void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,
+                       cudaStream_t s);
+template <typename T>
+void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s);
+int eig_bmax();
+size_t eig_work_elems(int b);
 
 }  // namespace hh

@@ -11,9 +11,10 @@ class Solver:
     """
 
     def __init__(self, dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, n_inner=1,
-                 tol=1e-10, max_iter=200, precision="fp64", seed=0, stream=None):
+                 tol=1e-10, max_iter=200, precision="fp64", seed=0, stream=None, leaf_solver="eigen",
+                 outer="oras", restart=40):
         self.params = _lib.make_params(dim, n, k, levels, overlap, rank, oversample, n_inner, tol, max_iter,
-                                       precision, seed)
+                                       precision, seed, leaf_solver, outer, restart)
         self.S = n + 2
         self.Sx = self.S if dim == 2 else 1
         self.dim = dim

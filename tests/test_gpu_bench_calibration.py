@@ -32,7 +32,7 @@ def case():
 def test_bench_tolerance_gives_rel_err_1e8(hh, case, precision):
     bench, w, f, g, us = case
     p = hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, w.n_inner, bench.TOL,
-                       bench.MAX_ITER, precision, 1)
+                       bench.MAX_ITER, precision, 1, outer=bench.OUTER, restart=bench.RESTART)
     h, _ = hh.hh_setup(p)
     try:
         u = torch.empty((w.S, w.S), dtype=torch.complex128, device="cuda")

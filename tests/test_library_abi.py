@@ -38,20 +38,31 @@ def test_status_strings(hh):
 
 
 def test_footprint_host_only_and_validation(hh):
-    p = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
+    p = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, leaf_solver="block")
     fp = hh.hh_footprint(p)
-    # at least the FP64 leaf factors: 4 leaves x 257 columns x 66^2 x 16 bytes
+    # at least the FP64 explicit leaf inverses: 4 leaves x 257 columns x 65^2 x 16 bytes
     assert fp > 4 * 257 * 65 * 65 * 16
-    pm = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, precision="mixed")
+    pm = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, precision="mixed",
+                        leaf_solver="block")
     assert hh.hh_footprint(pm) < fp
+    pe = hh.make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
+    assert hh.hh_footprint(pe) < fp          # the eigenbasis path stores b^2 + Sx b per leaf
     bad = [dict(overlap=3), dict(overlap=0), dict(levels=0), dict(n=2), dict(rank=0), dict(k=-1.0),
-           dict(n=20, levels=4), dict(rank=40, oversample=0), dict(dim=3), dict(n_inner=0), dict(tol=0.0)]
+           dict(n=20, levels=4), dict(rank=40, oversample=0), dict(dim=3), dict(n_inner=0), dict(tol=0.0),
+           dict(leaf_solver=7), dict(outer=3), dict(outer=1, restart=0), dict(outer=1, restart=65),
+           dict(n=1023, levels=2), dict(levels=7, n=4000)]
     for kw in bad:
         args = dict(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
         args.update(kw)
         with pytest.raises(hh.HHError) as ei:
             hh.hh_footprint(hh.make_params(**args))
         assert ei.value.status == hh.HH_EINVAL, kw
+
+
+def test_block_leaf_path_accepts_tall_bands(hh):
+    # the explicit-inverse leaf path has no eigenbasis band limit
+    p = hh.make_params(dim=2, n=1023, k=100.0, levels=2, overlap=4, rank=16, oversample=8, leaf_solver="block")
+    assert hh.hh_footprint(p) > 0
 
 
 def test_footprint_1d(hh):
