@@ -166,16 +166,34 @@ struct SolverBase {
         cudaEventCreate(&e);
         return e;
     }
+    // While the stream is being captured into a graph, the records become external
+    // event-record nodes, so replays of the graph stamp the same events again.
+    void ev_record(cudaEvent_t e) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(stream, &cs);
+        if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
+        else cudaEventRecord(e, stream);
+    }
     void pbeg(int cat) {
         if (!prof_on) return;
         EvPair p{prof_ev(), nullptr, cat};
-        cudaEventRecord(p.a, stream);
+        ev_record(p.a);
         prof_pending.push_back(p);
     }
     void pend() {
         if (!prof_on || prof_pending.empty() || prof_pending.back().b) return;
         prof_pending.back().b = prof_ev();
-        cudaEventRecord(prof_pending.back().b, stream);
+        ev_record(prof_pending.back().b);
+    }
+    // event pairs owned by captured graphs: read after every synchronised replay
+    void prof_read_pairs(const std::vector<EvPair>& v) {
+        for (auto& p : v) {
+            float ms = 0.f;
+            if (p.b && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                prof_ms[p.cat] += ms;
+                prof_n[p.cat] += 1;
+            }
+        }
     }
     void prof_collect() {   // call after synchronising the stream
         for (auto& p : prof_pending) {
@@ -243,12 +261,25 @@ struct Solver final : SolverBase {
     c128 *Vb = nullptr, *Zb = nullptr, *gw = nullptr, *gv = nullptr, *gz = nullptr, *gdots = nullptr,
          *gy = nullptr;
     c128* h_dots = nullptr;                       // pinned host copy of the dot products
+    // captured graphs of the preconditioner step (slot 0: gv -> gz for GMRES, slot 1:
+    // the stationary update of u)
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        bool failed = false;
+        bool replayed = false;
+        std::vector<EvPair> prof;
+    };
+    Graph graphs[2];
     void** d_ptrs = nullptr;
     double* h_norm = nullptr;   // pinned host
     int b_max = 0;
     cudaError_t cerr = cudaSuccess;
 
     ~Solver() override {
+        for (auto& g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            for (auto& p : g.prof) { prof_pool.push_back(p.a); if (p.b) prof_pool.push_back(p.b); }
+        }
         if (h_norm) cudaFreeHost(h_norm);
         if (h_dots) cudaFreeHost(h_dots);
         if (block) dev_free(block, footprint, stream, hook);
@@ -474,8 +505,8 @@ struct Solver final : SolverBase {
     void coarse_correct(int p, const CT* vin, int nc) {
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
         pbeg(PC_COARSE);
-        const int nb = launch_ip_partial<T, T>(C[p], 2 * r, R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
-                                               stream);
+        const int nb = launch_ip_partial<T, T, T>(C[p], 2 * r, R[p], nc, pts(p), 2 * r, nc, partial,
+                                                  MAX_PART_BLOCKS, stream);
         pend();
         launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
         launch_coarse_update<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
@@ -545,7 +576,8 @@ struct Solver final : SolverBase {
             }
             // A_c = C_p^H A~_p C_p, then its inverse
             pbeg(PC_GALERKIN);
-            const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, partial, MAX_PART_BLOCKS, stream);
+            const int split = nodes[nodes[p].child[1]].own_a - nodes[p].ra;
+            const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS, stream);
             pend();
             launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
             launch_gj_inverse(Ainv[p], 2 * r, derr, stream);
@@ -607,8 +639,8 @@ struct Solver final : SolverBase {
                                    (size_t)(cn.own_b - cn.own_a) * Sx, true, false, stream);
         }
         launch_apply<double, double, double>(ut, rhs, res, geom(0), 1, 1.0, nullptr, nullptr, stream);
-        const int nb = launch_ip_partial<T, double>(C[0], 2 * r, res, 1, N, 2 * r, 1, partial, MAX_PART_BLOCKS,
-                                                    stream);
+        const int nb = launch_ip_partial<T, double, T>(C[0], 2 * r, res, 1, N, 2 * r, 1, partial, MAX_PART_BLOCKS,
+                                                       stream);
         launch_ip_reduce(partial, nb, 2 * r, 1, nullptr, Ainv[0], ycoef[0], stream);
         if (out != ut) d2d(out, ut, sizeof(c128) * N);
         launch_coarse_update<T, double>(C[0], ycoef[0], out, N, 2 * r, 1, stream);
@@ -627,6 +659,45 @@ struct Solver final : SolverBase {
         oras_step(nullptr, v, z);
     }
 
+    // Runs `body` through a CUDA graph: the first call runs it directly (which also
+    // performs any one-time uploads and attribute settings) and then captures it; later
+    // calls replay the graph.  Buffers used by `body` must not change between calls.
+    template <class F> void via_graph(int slot, F body) {
+        Graph& g = graphs[slot];
+        if (g.exec) {
+            cudaGraphLaunch(g.exec, stream);
+            g.replayed = true;
+            return;
+        }
+        body();
+        if (g.failed) return;
+        cudaGraph_t graph = nullptr;
+        const size_t npend = prof_pending.size();
+        if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            g.failed = true;
+            return;
+        }
+        body();
+        const cudaError_t e1 = cudaStreamEndCapture(stream, &graph);
+        if (e1 != cudaSuccess || !graph || cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            g.failed = true;
+            g.exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        // the pairs recorded during capture belong to the graph
+        g.prof.assign(prof_pending.begin() + npend, prof_pending.end());
+        prof_pending.resize(npend);
+    }
+    // after a synchronisation: account the graphs' profiler events of the last replay
+    void graphs_collect() {
+        for (auto& g : graphs) {
+            if (g.replayed && prof_on) prof_read_pairs(g.prof);
+            g.replayed = false;
+        }
+    }
+
     // ||b - A u||^2 into h_norm[0] (synchronises); ||b||^2 must be in dnorm[2].
     bool true_residual(c128* dst, hh_status& st) {
         int nb = 0;
@@ -635,7 +706,9 @@ struct Solver final : SolverBase {
         pend();
         launch_sum(npart, nb, dnorm, stream);
         ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
-        return sync_check(st);
+        const bool ok = sync_check(st);
+        graphs_collect();
+        return ok;
     }
 
     // Stationary iteration u <- u + M (b - A u)  (Eqs. (2)-(3)).
@@ -647,7 +720,7 @@ struct Solver final : SolverBase {
             if (!std::isfinite(rel)) return HH_ENOCONV;
             if (rel < P.tol) return HH_OK;
             if (it >= P.max_iter) return HH_ENOCONV;
-            oras_step(u, bvec, u);
+            via_graph(1, [&] { oras_step(u, bvec, u); });
             ++it;
         }
     }
@@ -680,7 +753,7 @@ struct Solver final : SolverBase {
             int j = 0;
             while (j < mk && it < P.max_iter) {
                 launch_col_load(Vb, ld, j, gv, N, stream);
-                precond(gv, gz);
+                via_graph(0, [&] { precond(gv, gz); });
                 launch_col_store_normalised(Zb, mk, j, gz, gone, N, stream);
                 launch_apply<double, double, double>(gz, nullptr, gw, geom(0), 1, -1.0, nullptr, nullptr, stream);
                 for (int pass = 0; pass < 2; ++pass) {
@@ -695,6 +768,7 @@ struct Solver final : SolverBase {
                 launch_col_store_normalised(Vb, ld, j + 1, gw, gdots + 160, N, stream);
                 ck(cudaMemcpyAsync(h_dots, gdots, sizeof(c128) * 3 * 80, cudaMemcpyDeviceToHost, stream), cerr);
                 if (!sync_check(st)) return st;
+                graphs_collect();
                 // column j of the Hessenberg matrix: h_ij = conj(sum conj(w) v_i) over both passes
                 for (int i = 0; i <= j; ++i) H[(size_t)i * mk + j] = conj(h_dots[i]) + conj(h_dots[80 + i]);
                 const double hn = std::sqrt(std::max(h_dots[160].re, 0.0));

@@ -14,14 +14,17 @@ static constexpr int IP_THREADS = 256;
 static constexpr int IP_MAXOUT = 16;   // outputs per thread when p*q >= IP_THREADS
 
 // Accumulate conj(As[n][i]) * Bs[n][j] over a tile of `rows` rows held in shared memory.
-__device__ __forceinline__ void ip_tile_accumulate(const c128* As, const c128* Bs, int rows, int p, int q,
-                                                   int split, c128* acc) {
+// Rows i outside [ilo, ihi) contribute nothing for this tile (ihi = 0: no restriction).
+template <typename ACC>
+__device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cplx<ACC>* Bs, int rows, int p, int q,
+                                                   int split, cplx<ACC>* acc, int ilo, int ihi) {
     const int nout = p * q;
     if (split == 1) {
         int k = 0;
         for (int o = threadIdx.x; o < nout; o += IP_THREADS, ++k) {
             const int i = o / q, j = o % q;
-            c128 a = acc[k];
+            if (ihi > 0 && (i < ilo || i >= ihi)) continue;
+            cplx<ACC> a = acc[k];
             for (int n = 0; n < rows; ++n) cfma_cj(a, As[n * p + i], Bs[n * q + j]);
             acc[k] = a;
         }
@@ -29,90 +32,101 @@ __device__ __forceinline__ void ip_tile_accumulate(const c128* As, const c128* B
         const int s = threadIdx.x / nout, o = threadIdx.x % nout;
         if (s < split) {
             const int i = o / q, j = o % q;
-            c128 a = acc[0];
+            if (ihi > 0 && (i < ilo || i >= ihi)) return;
+            cplx<ACC> a = acc[0];
             for (int n = s; n < rows; n += split) cfma_cj(a, As[n * p + i], Bs[n * q + j]);
             acc[0] = a;
         }
     }
 }
 
-__device__ __forceinline__ void ip_store_partial(c128* acc, int p, int q, int split, c128* red, c128* out) {
+template <typename ACC>
+__device__ __forceinline__ void ip_store_partial(cplx<ACC>* acc, int p, int q, int split, cplx<ACC>* red,
+                                                 c128* out) {
     const int nout = p * q;
     if (split == 1) {
         int k = 0;
-        for (int o = threadIdx.x; o < nout; o += IP_THREADS, ++k) out[o] = acc[k];
+        for (int o = threadIdx.x; o < nout; o += IP_THREADS, ++k) out[o] = cvt<double>(acc[k]);
     } else {
         const int s = threadIdx.x / nout, o = threadIdx.x % nout;
         if (s < split) red[s * nout + o] = acc[0];
         __syncthreads();
         for (int o2 = threadIdx.x; o2 < nout; o2 += IP_THREADS) {
             c128 t = {0.0, 0.0};
-            for (int s2 = 0; s2 < split; ++s2) t = t + red[s2 * nout + o2];
+            for (int s2 = 0; s2 < split; ++s2) t = t + cvt<double>(red[s2 * nout + o2]);
             out[o2] = t;
         }
     }
 }
 
-template <typename TA, typename TB>
+template <typename TA, typename TB, typename ACC>
 __global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __restrict__ A, int lda,
                                                            const cplx<TB>* __restrict__ B, int ldb,
                                                            size_t N, int p, int q, c128* partial) {
-    extern __shared__ c128 sm[];
-    c128* As = sm;
-    c128* Bs = As + IP_TILE * p;
-    c128* red = Bs + IP_TILE * q;
+    extern __shared__ __align__(16) unsigned char ipsm[];
+    using CA = cplx<ACC>;
+    CA* As = (CA*)ipsm;
+    CA* Bs = As + IP_TILE * p;
+    CA* red = Bs + IP_TILE * q;
     const int nout = p * q;
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
-    c128 acc[IP_MAXOUT];
-    for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = {0.0, 0.0};
+    CA acc[IP_MAXOUT];
+    for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = {0, 0};
     const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
     const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
         const int rows = (int)min((size_t)IP_TILE, n1 - t0);
         for (int e = threadIdx.x; e < rows * p; e += IP_THREADS)
-            As[e] = cvt<double>(A[(t0 + e / p) * lda + e % p]);
+            As[e] = cvt<ACC>(A[(t0 + e / p) * lda + e % p]);
         for (int e = threadIdx.x; e < rows * q; e += IP_THREADS)
-            Bs[e] = cvt<double>(B[(t0 + e / q) * ldb + e % q]);
+            Bs[e] = cvt<ACC>(B[(t0 + e / q) * ldb + e % q]);
         __syncthreads();
-        ip_tile_accumulate(As, Bs, rows, p, q, split, acc);
+        ip_tile_accumulate<ACC>(As, Bs, rows, p, q, split, acc, 0, 0);
         __syncthreads();
     }
-    ip_store_partial(acc, p, q, split, red, partial + (size_t)blockIdx.x * nout);
+    ip_store_partial<ACC>(acc, p, q, split, red, partial + (size_t)blockIdx.x * nout);
 }
 
-static size_t ip_smem(int p, int q) {
+static size_t ip_smem(int p, int q, size_t esz = sizeof(c128)) {
     const int nout = p * q;
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
-    return sizeof(c128) * ((size_t)IP_TILE * (p + q) + (split > 1 ? (size_t)split * nout : 0));
+    return esz * ((size_t)IP_TILE * (p + q) + (split > 1 ? (size_t)split * nout : 0));
 }
 
-template <typename TA, typename TB>
+template <typename TA, typename TB, typename ACC>
 int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, size_t N, int p, int q,
                       c128* partial, int max_blocks, cudaStream_t s) {
-    int grid = (int)((N + 255) / 256);
+    // rows per block: enough work per block to amortise the reduction over blocks
+    const size_t per = (size_t)p * q >= 256 ? 256 : 1024;
+    int grid = (int)((N + per - 1) / per);
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
-    const size_t sm = ip_smem(p, q);
+    const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(k_ip_partial<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_ip_partial<TA, TB, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    k_ip_partial<TA, TB><<<grid, IP_THREADS, sm, s>>>(A, lda, B, ldb, N, p, q, partial);
+    k_ip_partial<TA, TB, ACC><<<grid, IP_THREADS, sm, s>>>(A, lda, B, ldb, N, p, q, partial);
     note_launch();
     return grid;
 }
 
-// out = sum over blocks; optional out2 = Minv * out.
-__global__ void k_ip_reduce(const c128* __restrict__ partial, int nblk, int p, int q, c128* out,
-                            const c128* __restrict__ Minv, c128* out2) {
+// out = sum over blocks (one warp per output, lanes across blocks: fixed order, so
+// deterministic); optional out2 = Minv * out computed by the same (single) block.
+__global__ void __launch_bounds__(1024) k_ip_reduce(const c128* __restrict__ partial, int nblk, int p, int q,
+                                                    c128* out, const c128* __restrict__ Minv, c128* out2) {
     extern __shared__ c128 s_out[];
     const int nout = p * q;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o = blockIdx.x * nw + (threadIdx.x >> 5); o < nout; o += gridDim.x * nw) {
         c128 t = {0.0, 0.0};
-        for (int b = 0; b < nblk; ++b) t = t + partial[(size_t)b * nout + o];
-        s_out[o] = t;
-        if (out) out[o] = t;
+        for (int b = lane; b < nblk; b += 32) t = t + partial[(size_t)b * nout + o];
+        t = warp_sum(t);
+        if (lane == 0) {
+            if (Minv) s_out[o] = t;
+            if (out) out[o] = t;
+        }
     }
     if (!Minv) return;
     __syncthreads();
@@ -130,7 +144,14 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
         cudaFuncSetAttribute(k_ip_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_ip_reduce<<<1, 256, sizeof(c128) * p * q, s>>>(partial, nblk, p, q, out, Minv, out2);
+    const int nout = p * q;
+    if (Minv) {
+        k_ip_reduce<<<1, 1024, sizeof(c128) * nout, s>>>(partial, nblk, p, q, out, Minv, out2);
+    } else {
+        int grid = (nout + 7) / 8;
+        if (grid > 304) grid = 304;
+        k_ip_reduce<<<grid, 256, 0, s>>>(partial, nblk, p, q, out, nullptr, nullptr);
+    }
     note_launch();
 }
 
@@ -138,7 +159,7 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 // partial[blk][a][l] = sum over the block's points of conj(C[pt][a]) * (A~ C)[pt][l].
 template <typename T>
 __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* __restrict__ C, OpGeom g, int p,
-                                                                 c128* partial) {
+                                                                 int split_row, c128* partial) {
     extern __shared__ c128 sm[];
     c128* As = sm;
     c128* Bs = As + IP_TILE * p;
@@ -171,14 +192,23 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
             Bs[e] = ax;
         }
         __syncthreads();
-        ip_tile_accumulate(As, Bs, rows, p, p, split, acc);
+        // C's columns [0, p/2) live on rows < split_row, [p/2, p) on the others; a tile
+        // inside one row touches one block of conj(C)
+        int ilo = 0, ihi = 0;
+        if (split_row >= 0) {
+            const int j0 = (int)(t0 / g.Sx), j1 = (int)((t0 + rows - 1) / g.Sx);
+            if (j1 < split_row) { ilo = 0; ihi = p / 2; }
+            else if (j0 >= split_row) { ilo = p / 2; ihi = p; }
+        }
+        ip_tile_accumulate<double>(As, Bs, rows, p, p, split, acc, ilo, ihi);
         __syncthreads();
     }
-    ip_store_partial(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
+    ip_store_partial<double>(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
 }
 
 template <typename T>
-int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, c128* partial, int max_blocks, cudaStream_t s) {
+int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
+                            cudaStream_t s) {
     const size_t N = (size_t)g.b * g.Sx;
     int grid = (int)((N + 127) / 128);
     if (grid > max_blocks) grid = max_blocks;
@@ -189,7 +219,7 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, c128* partial, in
         cudaFuncSetAttribute(k_galerkin_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    k_galerkin_partial<T><<<grid, IP_THREADS, sm, s>>>(C, g, p, partial);
+    k_galerkin_partial<T><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
     note_launch();
     return grid;
 }
@@ -278,7 +308,7 @@ __global__ void __launch_bounds__(256) k_jacobi(c128* const* Gp, c128* const* Up
         dg = warp_sum(dg);
         if ((threadIdx.x & 31) == 0) { atomicAdd(&off_s, off); atomicAdd(&diag_s, dg); }
         __syncthreads();
-        if (off_s <= 1e-30 * diag_s || off_s == 0.0) break;
+        if (off_s <= 1e-24 * diag_s || off_s == 0.0) break;   // off-diagonal <= 1e-12 relative
         __syncthreads();
         for (int round = 0; round < n - 1; ++round) {
             if (threadIdx.x < npair) {
@@ -482,14 +512,18 @@ void launch_gj_inverse(c128* A, int n, int* err, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ instantiations
-template int launch_ip_partial<float, float>(const c64*, int, const c64*, int, size_t, int, int, c128*, int,
-                                             cudaStream_t);
-template int launch_ip_partial<double, double>(const c128*, int, const c128*, int, size_t, int, int, c128*, int,
-                                               cudaStream_t);
-template int launch_ip_partial<float, double>(const c64*, int, const c128*, int, size_t, int, int, c128*, int,
-                                              cudaStream_t);
-template int launch_galerkin_partial<float>(const c64*, OpGeom, int, c128*, int, cudaStream_t);
-template int launch_galerkin_partial<double>(const c128*, OpGeom, int, c128*, int, cudaStream_t);
+template int launch_ip_partial<float, float, float>(const c64*, int, const c64*, int, size_t, int, int, c128*, int,
+                                                    cudaStream_t);
+template int launch_ip_partial<float, float, double>(const c64*, int, const c64*, int, size_t, int, int, c128*,
+                                                     int, cudaStream_t);
+template int launch_ip_partial<double, double, double>(const c128*, int, const c128*, int, size_t, int, int, c128*,
+                                                       int, cudaStream_t);
+template int launch_ip_partial<float, double, float>(const c64*, int, const c128*, int, size_t, int, int, c128*,
+                                                     int, cudaStream_t);
+template int launch_ip_partial<float, double, double>(const c64*, int, const c128*, int, size_t, int, int, c128*,
+                                                      int, cudaStream_t);
+template int launch_galerkin_partial<float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
+template int launch_galerkin_partial<double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t);
 template void launch_qr<float>(c64* const*, int, int, int, c64**, cudaStream_t);
 template void launch_qr<double>(c128* const*, int, int, int, c128**, cudaStream_t);
 template void launch_form_v<float>(const c64*, const c128*, const double*, c64*, int, int, int, cudaStream_t);

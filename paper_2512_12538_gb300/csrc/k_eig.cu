@@ -18,125 +18,108 @@
 // and x = V x^ (a second contraction).
 //
 // Eigenpairs: V = W^{-1/2} Q with Q the eigenvectors of the complex symmetric
-// tridiagonal W^{-1/2} K W^{-1/2}; eigenvalues by the implicit QL algorithm with
-// complex orthogonal plane rotations (the symmetric tridiagonal QL method carried over
-// to complex symmetric matrices), eigenvectors by inverse iteration with a pivoted
-// tridiagonal LU, normalised q^T q = 1 (no conjugation).
+// tridiagonal W^{-1/2} K W^{-1/2}; eigenvalues by the Aberth-Ehrlich simultaneous
+// iteration on its characteristic polynomial, eigenvectors by inverse iteration with a
+// pivoted tridiagonal LU, normalised q^T q = 1 (no conjugation).
 #include "kernels.h"
 
 namespace hh {
 
 static constexpr int EIG_BMAX = 136;     // rows of a leaf band supported by the eigenbasis path
 
-// ------------------------------------------------------------ complex helpers (FP64)
-__device__ __forceinline__ double cabs_(c128 z) { return hypot(z.re, z.im); }
-__device__ __forceinline__ c128 cdiv_(c128 a, c128 b) {
+// ------------------------------------------------------------ complex helpers
+template <typename R> __device__ __forceinline__ R cabs_(cplx<R> z) { return hypot(z.re, z.im); }
+template <typename R> __device__ __forceinline__ cplx<R> cdiv_(cplx<R> a, cplx<R> b) {
     // Smith's algorithm for a / b
     if (fabs(b.re) >= fabs(b.im)) {
-        const double r = b.im / b.re, den = b.re + b.im * r;
+        const R r = b.im / b.re, den = b.re + b.im * r;
         return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
     }
-    const double r = b.re / b.im, den = b.re * r + b.im;
+    const R r = b.re / b.im, den = b.re * r + b.im;
     return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
 }
 // principal square root from |z|: re = sqrt((|z| + x)/2), im = y / (2 re), with the
 // cancellation-free branch for x < 0.
-__device__ __forceinline__ c128 csqrt_(c128 z) {
-    const double r = cabs_(z);
-    if (r == 0.0) return {0.0, 0.0};
-    const double t = sqrt(0.5 * (r + fabs(z.re)));
-    if (z.re >= 0.0) return {t, z.im / (2.0 * t)};
-    return {fabs(z.im) / (2.0 * t), copysign(t, z.im)};
+template <typename R> __device__ __forceinline__ cplx<R> csqrt_(cplx<R> z) {
+    const R r = cabs_(z);
+    if (r == (R)0) return {0, 0};
+    const R t = sqrt((R)0.5 * (r + fabs(z.re)));
+    if (z.re >= (R)0) return {t, z.im / ((R)2 * t)};
+    return {fabs(z.im) / ((R)2 * t), copysign(t, z.im)};
 }
+template <typename R> struct Eps;
+template <> struct Eps<float> { static constexpr float v = 1.1920929e-07f; static constexpr float tiny = 1e-5f; };
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; static constexpr double tiny = 1e-12; };
 
-// Complex symmetric tridiagonal line operator of a band (b rows), scaled W^{-1/2} K W^{-1/2}.
-__device__ __forceinline__ void band_tridiag(int b, double kh, int a, c128& d, c128& e) {
+// Complex symmetric tridiagonal line operator of a band (b rows), scaled
+// W^{-1/2} K W^{-1/2}: diagonal d_a and coupling e_a between rows a and a+1.
+template <typename R>
+__device__ __forceinline__ void band_tridiag(int b, double kh, int a, cplx<R>& d, cplx<R>& e) {
     const double wa = wrow(a, b);
     const bool edge = (a == 0 || a == b - 1);
     const double cy = edge ? 1.0 : 2.0;
-    d = {(cy - kh * kh * wa) / wa, -(edge ? kh : 0.0) / wa};
-    e = {a < b - 1 ? -1.0 / sqrt(wa * wrow(a + 1, b)) : 0.0, 0.0};
+    d = {(R)((cy - kh * kh * wa) / wa), (R)(-(edge ? kh : 0.0) / wa)};
+    e = {(R)(a < b - 1 ? -1.0 / sqrt(wa * wrow(a + 1, b)) : 0.0), (R)0};
 }
 
-// Implicit QL for a complex symmetric tridiagonal matrix (d diagonal, e[i] couples i
-// and i+1, e[n-1] = 0).  Eigenvalues overwrite d.  Returns false if an eigenvalue
-// needs more than 60 iterations or a rotation degenerates.
-__device__ bool ql_complex_symmetric(c128* d, c128* e, int n) {
-    const double eps = 2.220446049250313e-16;
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        for (;;) {
-            int m = l;
-            for (; m < n - 1; ++m) {
-                const double dd = cabs_(d[m]) + cabs_(d[m + 1]);
-                if (cabs_(e[m]) <= eps * dd) break;
-            }
-            if (m == l) break;
-            if (++iter > 60) return false;
-            c128 g = cdiv_(d[l + 1] - d[l], 2.0 * e[l]);
-            c128 r = csqrt_(g * g + c128{1.0, 0.0});
-            const c128 gp = g + r, gm = g - r;
-            g = d[m] - d[l] + cdiv_(e[l], cabs_(gp) >= cabs_(gm) ? gp : gm);
-            c128 s = {1.0, 0.0}, c = {1.0, 0.0}, p = {0.0, 0.0};
-            bool early = false;
-            for (int i = m - 1; i >= l; --i) {
-                const c128 f = s * e[i], bb = c * e[i];
-                r = csqrt_(f * f + g * g);
-                e[i + 1] = r;
-                if (cabs_(r) == 0.0) {
-                    d[i + 1] = d[i + 1] - p;
-                    e[m] = {0.0, 0.0};
-                    early = true;
-                    break;
-                }
-                s = cdiv_(f, r);
-                c = cdiv_(g, r);
-                g = d[i + 1] - p;
-                r = (d[i] - g) * s + 2.0 * (c * bb);
-                p = s * r;
-                d[i + 1] = g + p;
-                g = c * r - bb;
-            }
-            if (early) continue;
-            d[l] = d[l] - p;
-            e[l] = g;
-            e[m] = {0.0, 0.0};
-        }
+// Newton correction p(z) / p'(z) of the characteristic polynomial p of the tridiagonal
+// matrix, from the ratios r_j = p_j / p_{j-1} of its leading principal minors:
+//   r_0 = d_0 - z,  r_j = d_j - z - e_{j-1}^2 / r_{j-1},
+//   r'_j = -1 + e_{j-1}^2 r'_{j-1} / r_{j-1}^2,   p'/p = sum_j r'_j / r_j.
+// A ratio that vanishes is replaced by a tiny value (the usual Sturm-sequence guard).
+template <typename R>
+__device__ cplx<R> newton_step(const cplx<R>* d, const cplx<R>* e2, int b, cplx<R> z) {
+    const R tiny = Eps<R>::tiny;
+    cplx<R> r = d[0] - z;
+    if (cabs_(r) < tiny) r = {tiny, 0};
+    cplx<R> rp = {(R)-1, 0};
+    cplx<R> ir = cdiv_(cplx<R>{1, 0}, r);
+    cplx<R> s = rp * ir;
+    for (int j = 1; j < b; ++j) {
+        const cplx<R> q = e2[j - 1] * ir;          // e^2 / r
+        cplx<R> rn = d[j] - z - q;
+        if (cabs_(rn) < tiny) rn = {tiny, 0};
+        rp = cplx<R>{(R)-1, 0} + q * (rp * ir);
+        r = rn;
+        ir = cdiv_(cplx<R>{1, 0}, r);
+        s = s + rp * ir;
     }
-    return true;
+    return cdiv_(cplx<R>{1, 0}, s);
 }
 
 // Inverse iteration for the eigenvector of eigenvalue mu: (T - mu) x = x_prev with a
-// pivoted tridiagonal LU (row interchanges between neighbours), three iterations.
-__device__ void inverse_iteration(int b, double kh, c128 mu, c128* x, c128* ws) {
-    // ws: 5 b complex doubles of per-thread workspace (global memory)
-    c128* dg = ws;
-    c128* up = ws + b;
-    c128* up2 = ws + 2 * b;
-    c128* lo = ws + 3 * b;
-    double* sw = (double*)(ws + 4 * b);   // interchange flags
+// pivoted tridiagonal LU (row interchanges between neighbours), three iterations,
+// normalised q^T q = 1 (complex symmetric, no conjugation).
+template <typename R>
+__device__ void inverse_iteration(int b, double kh, cplx<R> mu, cplx<R>* x, cplx<R>* ws) {
+    using C = cplx<R>;
+    C* dg = ws;
+    C* up = ws + b;
+    C* up2 = ws + 2 * b;
+    C* lo = ws + 3 * b;
+    R* sw = (R*)(ws + 4 * b);   // interchange flags
     for (int a = 0; a < b; ++a) {
-        c128 d, e;
-        band_tridiag(b, kh, a, d, e);
+        C d, e;
+        band_tridiag<R>(b, kh, a, d, e);
         dg[a] = d - mu;
         up[a] = e;
-        up2[a] = {0.0, 0.0};
-        x[a] = {1.0 + 1e-3 * a, 1e-3 * (a % 7)};
+        up2[a] = {0, 0};
+        x[a] = {(R)(1.0 + 1e-3 * a), (R)(1e-3 * (a % 7))};
     }
     for (int j = 0; j < b - 1; ++j) {
-        c128 dsub, esub;
-        band_tridiag(b, kh, j, dsub, esub);   // esub = sub-diagonal entry (j+1, j)
+        C dsub, esub;
+        band_tridiag<R>(b, kh, j, dsub, esub);   // esub = sub-diagonal entry (j+1, j)
         if (cabs_(dg[j]) >= cabs_(esub)) {
-            sw[j] = 0.0;
-            const c128 fact = cabs_(dg[j]) > 0.0 ? cdiv_(esub, dg[j]) : c128{0.0, 0.0};
+            sw[j] = 0;
+            const C fact = cabs_(dg[j]) > (R)0 ? cdiv_(esub, dg[j]) : C{0, 0};
             lo[j] = fact;
             dg[j + 1] = dg[j + 1] - fact * up[j];
         } else {
-            sw[j] = 1.0;
-            const c128 fact = cdiv_(dg[j], esub);
+            sw[j] = 1;
+            const C fact = cdiv_(dg[j], esub);
             dg[j] = esub;
             lo[j] = fact;
-            const c128 temp = up[j];
+            const C temp = up[j];
             up[j] = dg[j + 1];
             dg[j + 1] = temp - fact * dg[j + 1];
             if (j < b - 2) {
@@ -145,15 +128,14 @@ __device__ void inverse_iteration(int b, double kh, c128 mu, c128* x, c128* ws) 
             }
         }
     }
-    const double tiny = 1e-300;
     for (int a = 0; a < b; ++a)
-        if (cabs_(dg[a]) < tiny) dg[a] = {1e-30, 0.0};
+        if (cabs_(dg[a]) < Eps<R>::tiny * Eps<R>::v) dg[a] = {Eps<R>::tiny * Eps<R>::v, 0};
     for (int it = 0; it < 3; ++it) {
         for (int j = 0; j < b - 1; ++j) {
-            if (sw[j] == 0.0) {
+            if (sw[j] == (R)0) {
                 x[j + 1] = x[j + 1] - lo[j] * x[j];
             } else {
-                const c128 t = x[j];
+                const C t = x[j];
                 x[j] = x[j + 1];
                 x[j + 1] = t - lo[j] * x[j];
             }
@@ -161,52 +143,80 @@ __device__ void inverse_iteration(int b, double kh, c128 mu, c128* x, c128* ws) 
         x[b - 1] = cdiv_(x[b - 1], dg[b - 1]);
         if (b > 1) x[b - 2] = cdiv_(x[b - 2] - up[b - 2] * x[b - 1], dg[b - 2]);
         for (int j = b - 3; j >= 0; --j) x[j] = cdiv_(x[j] - up[j] * x[j + 1] - up2[j] * x[j + 2], dg[j]);
-        double mx = 0.0;
+        R mx = 0;
         for (int a = 0; a < b; ++a) mx = fmax(mx, cabs_(x[a]));
-        const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+        const R inv = mx > (R)0 ? (R)1 / mx : (R)1;
         for (int a = 0; a < b; ++a) x[a] = inv * x[a];
     }
-    // complex symmetric normalisation q^T q = 1
-    c128 qq = {0.0, 0.0};
+    C qq = {0, 0};
     for (int a = 0; a < b; ++a) qq = qq + x[a] * x[a];
-    const c128 nr = csqrt_(qq);
+    const C nr = csqrt_(qq);
     for (int a = 0; a < b; ++a) x[a] = cdiv_(x[a], nr);
 }
 
+// Set-up of one leaf per CTA, in the precision of the leaf path (FP32 for the mixed
+// form, FP64 for the FP64 form).
+// Eigenvalues: Aberth-Ehrlich simultaneous iteration, one thread per eigenvalue,
+//   z_j <- z_j - w_j / (1 - w_j sum_{k != j} 1/(z_j - z_k)),  w_j = p(z_j)/p'(z_j),
+// started from the closed-form spectrum of the real part, 2 - 2cos(j pi/(b-1)) - (kh)^2
+// (the halved-end second difference has the cosine eigenvectors), shifted by the
+// first-order effect of the two impedance corners.
 template <typename T>
 __global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ tasks, int Sx, double kh,
                                                     int* err) {
+    using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.x];
     const int b = tk.b;
-    __shared__ c128 d[EIG_BMAX], e[EIG_BMAX];
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        for (int a = 0; a < b; ++a) band_tridiag(b, kh, a, d[a], e[a]);
-        ok = ql_complex_symmetric(d, e, b) ? 1 : 0;
-        if (!ok) atomicExch(err, DEV_BREAKDOWN);
+    __shared__ C d[EIG_BMAX], e2[EIG_BMAX], z[EIG_BMAX];
+    for (int a = threadIdx.x; a < b; a += blockDim.x) {
+        C dd, ee;
+        band_tridiag<T>(b, kh, a, dd, ee);
+        d[a] = dd;
+        e2[a] = ee * ee;
+        const double mu = 2.0 - 2.0 * cos(M_PI * a / (b - 1)) - kh * kh;
+        z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 4.0) / (b - 1))};
     }
     __syncthreads();
+    for (int it = 0; it < 48; ++it) {
+        C zn = {0, 0};
+        bool small = true;
+        if (threadIdx.x < b) {
+            const int j = threadIdx.x;
+            const C zj = z[j];
+            const C w = newton_step<T>(d, e2, b, zj);
+            C s = {0, 0};
+            for (int k = 0; k < b; ++k)
+                if (k != j) s = s + cdiv_(C{1, 0}, zj - z[k]);
+            const C dz = cdiv_(w, C{1, 0} - w * s);
+            zn = zj - dz;
+            small = cabs_(dz) <= (T)64 * Eps<T>::v * fmax(cabs_(zj), (T)1);
+        }
+        __syncthreads();
+        if (threadIdx.x < b) z[threadIdx.x] = zn;
+        if (__syncthreads_and(small) && it >= 3) break;
+    }
     c128* lam = (c128*)tk.lam;
-    cplx<T>* V = (cplx<T>*)tk.V;
-    cplx<T>* xi = (cplx<T>*)tk.xi;
+    C* V = (C*)tk.V;
+    C* xi = (C*)tk.xi;
     for (int m = threadIdx.x; m < b; m += blockDim.x) {
-        const c128 lm = d[m];
-        lam[m] = lm;
-        c128* ws = (c128*)tk.work + (size_t)m * 6 * b;
-        c128* q = ws + 5 * b;
-        const c128 mu = lm + c128{1e-13 * fmax(1.0, cabs_(lm)), 0.0};
-        inverse_iteration(b, kh, mu, q, ws);
-        for (int a = 0; a < b; ++a) V[a * b + m] = cvt<T>((1.0 / sqrt(wrow(a, b))) * q[a]);
+        const C lm = z[m];
+        if (!(isfinite(lm.re) && isfinite(lm.im))) atomicExch(err, DEV_BREAKDOWN);
+        lam[m] = cvt<double>(lm);
+        C* ws = (C*)tk.work + (size_t)m * 6 * b;
+        C* q = ws + 5 * b;
+        const C mu = lm + C{(T)(8 * Eps<T>::v) * fmax(cabs_(lm), (T)1), (T)0};
+        inverse_iteration<T>(b, kh, mu, q, ws);
+        for (int a = 0; a < b; ++a) V[a * b + m] = ((T)(1.0 / sqrt(wrow(a, b)))) * q[a];
         // scalar Schur recursions along the columns
-        c128 prev = {0.0, 0.0};
+        C prev = {0, 0};
         for (int i = 0; i < Sx; ++i) {
-            const double wi = wcol(i, Sx);
+            const T wi = (T)wcol(i, Sx);
             const bool xb = (i == 0 || i == Sx - 1);
-            const c128 delta = c128{xb ? 1.0 : 2.0, xb ? -kh : 0.0} + wi * lm;
-            const c128 s = delta - prev;
-            if (!(abs2(s) > 0.0)) atomicExch(err, DEV_BREAKDOWN);
-            prev = cdiv_(c128{1.0, 0.0}, s);
-            xi[(size_t)i * b + m] = cvt<T>(prev);
+            const C delta = C{(T)(xb ? 1.0 : 2.0), (T)(xb ? -kh : 0.0)} + wi * lm;
+            const C sdel = delta - prev;
+            if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
+            prev = cdiv_(C{1, 0}, sdel);
+            xi[(size_t)i * b + m] = prev;
         }
     }
 }
@@ -313,7 +323,7 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
         cudaMemcpyAsync(err, &one, sizeof(int), cudaMemcpyHostToDevice, s);
         return;
     }
-    k_eig_factor<T><<<ntasks, 128, 0, s>>>(d_tasks, Sx, kh, err);
+    k_eig_factor<T><<<ntasks, 160, 0, s>>>(d_tasks, Sx, kh, err);
     note_launch();
 }
 

@@ -233,10 +233,11 @@ __global__ void k_coarse_update(const cplx<TC>* __restrict__ C, const c128* __re
          t += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(t % nc);
         const size_t pt = t / nc;
+        // the correction is accumulated in the precision of the basis C
         const cplx<TC>* cr = C + pt * p;
-        c128 acc = {0.0, 0.0};
-        for (int j = 0; j < p; ++j) cfma(acc, cvt<double>(cr[j]), ys[j * nc + c]);
-        W[t] = cvt<TW>(cvt<double>(W[t]) + acc);
+        cplx<TC> acc = {0, 0};
+        for (int j = 0; j < p; ++j) cfma(acc, cr[j], cvt<TC>(ys[j * nc + c]));
+        W[t] = W[t] + cvt<TW>(acc);
     }
 }
 template <typename TC, typename TW>

@@ -58,15 +58,17 @@ void launch_basis_combine(const c128* B, int ld, int j, const c128* coef, bool c
 
 // ---- dense kernels (k_dense.cu) ----------------------------------------------------
 // partial[blk][i][j] = sum_{n in blk} conj(A[n*lda+i]) * B[n*ldb+j]; returns nblk.
-template <typename TA, typename TB>
+// ACC is the accumulation precision (double, or float for complex64 working data).
+template <typename TA, typename TB, typename ACC = double>
 int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, size_t N, int p, int q,
                       c128* partial, int max_blocks, cudaStream_t s);
 // out[i][j] = sum_blk partial; if Minv != null, out2 = Minv (p x p) * out  (p x q).
 void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, const c128* Minv,
                       c128* out2, cudaStream_t s);
-// Galerkin partials: partial[blk][a][l] = sum_pts conj(C[pt][a]) (A~ C)[pt][l]  (p = 2r)
+// Galerkin partials: partial[blk][a][l] = sum_pts conj(C[pt][a]) (A~ C)[pt][l]  (p = 2r).
+// split_row >= 0: columns [0, p/2) of C vanish on rows >= split_row and [p/2, p) below it.
 template <typename T>
-int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, c128* partial, int max_blocks,
+int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
                             cudaStream_t s);
 // In-place QR (classical Gram-Schmidt, two passes) of nq independent Sx x m blocks.
 template <typename T>
@@ -106,7 +108,7 @@ struct EigTask {
     const void* F;    // right-hand sides [b][Sx][nrhs]
     void* Fh;         // transformed right-hand sides / solutions [b][Sx][nrhs]
     void* W;          // solutions [b][Sx][nrhs]
-    void* work;       // set-up workspace, eig_work_elems(b) complex128
+    void* work;       // set-up workspace, eig_work_elems(b) complex128 (used as complex<T>)
     int b;
 };
 template <typename T>
