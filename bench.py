@@ -37,7 +37,7 @@ WORKLOAD = "helm2d_n255_k40_L2"
 # direct solution on this workload (checked by tests/test_gpu_bench_calibration.py).
 TOL = 1e-10
 MAX_ITER = 400
-OUTER = "gmres"                     # flexible GMRES preconditioned by the hierarchical ORAS step
+OUTER = "oras"                      # stationary ORAS iteration (GMRES: outer="gmres")
 RESTART = 40
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -132,23 +132,34 @@ def leaf_bands(w):
     return [min(S, ob + e) - max(0, oa - e) for oa, ob in nodes]
 
 
-def sweep_bytes(w, ncols, esz):
-    """Algorithmic HBM bytes of one leaf-sweep launch (all leaves): every stored
-    inverse X_i read twice (forward and backward; ldx-padded rows), right-hand sides
-    read once, solutions written twice and read once."""
-    per16 = 16 // esz
-    tot = 0
-    for b in leaf_bands(w):
-        ldx = (b + per16 - 1) // per16 * per16
-        tot += (2 * w.S - 1) * b * ldx * esz
-        tot += 4 * b * w.S * ncols * esz
-    return tot
+def sweep_columns(w, n_solves, iters_total):
+    """Right-hand-side counts of every leaf-sweep launch: per solve 3 sketch passes per
+    level (r + p, r + p and r columns), then one column per outer iteration."""
+    m = min(w.rank + w.oversample, w.S)
+    r = min(w.rank, m)
+    return [m, m, r] * w.levels * n_solves + [1] * iters_total
 
 
-def factor_flops(w):
-    """Algorithmic flops of one factorisation launch: per leaf and column i, the Schur
-    update b^2 complex multiply-adds and the Gauss-Jordan inverse b^3."""
-    return sum(w.S * 8.0 * (b ** 3 + b ** 2) for b in leaf_bands(w))
+def kernel_work(w, cat, n_solves, iters_total, esz=8):
+    """Algorithmic work of all launches of one profiler category over the timed solves:
+    (amount, unit, bound, kernel name).  Per launch and leaf of b rows, Sx = S columns,
+    nc right-hand sides:
+      transforms f^ = V^T f, x = V x^: 8 b^2 Sx nc flops (complex multiply-add = 8 flops);
+      recursions: read xi (Sx b), read and write f^ (2 b Sx nc) elements;
+      FP64 residual: 48 bytes per node (read u, read b, write r)."""
+    bands = leaf_bands(w)
+    S = w.S
+    cols = sweep_columns(w, n_solves, iters_total)
+    if cat in ("sweep_in", "sweep_out"):
+        fl = sum(8.0 * b * b * S * nc for nc in cols for b in bands)
+        name = "k_eig_gemm<float," + ("1> (f^ = V^T f)" if cat == "sweep_in" else "0> (x = V x^)")
+        return fl, "flop", "alu", name
+    if cat == "sweep_recur":
+        by = sum(esz * S * b * (1.0 + 2.0 * nc) for nc in cols for b in bands)
+        return by, "byte", "hbm", "k_eig_recur<float> (scalar Schur recursions along the line)"
+    if cat == "residual":
+        return 48.0 * S * S * (iters_total + n_solves), "byte", "hbm", "k_apply<double> (FP64 residual b - A u)"
+    return None, None, "latency", cat
 
 
 # --------------------------------------------------------------------- our arm
@@ -269,6 +280,7 @@ def run_ours(args, rank, world):
                       "ms_per_step": statistics.mean(fp64_ms)},
         "mixed_over_fp64": (value / world) / (len(fp64_ms) / (sum(fp64_ms) / 1e3)),
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+        "kernel_ms": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof_total.items()},
         "wall_s_timed": wall,
     }
     if rank == 0:
@@ -286,37 +298,30 @@ def pct(xs, q):
 
 
 def roofline(w, prof, iters, pk, pk_kind):
-    """Dominant kernel of the mixed form with its algorithmic rate against its peak."""
+    """Dominant kernel (largest total device time in the timed solves, measured with CUDA
+    events on the launching stream) with its algorithmic rate against its peak."""
     if not prof:
         return None
+    tot_ms = sum(v[0] for v in prof.values())
     name = max(prof, key=lambda k: prof[k][0])
     ms, launches = prof[name]
-    n_runs = len(iters)
-    esz = 8
-    if name == "sweep":
-        m = min(w.rank + w.oversample, w.S)
-        r = min(w.rank, m)
-        per_run_cols = [m, m, r] * w.levels
-        byts = n_runs * sum(sweep_bytes(w, c, esz) for c in per_run_cols)
-        byts += sum(iters) * sweep_bytes(w, 1, esz)
-        achieved = byts / (ms / 1e3) / 1e9
+    amount, unit, bound, kname = kernel_work(w, name, len(iters), sum(iters))
+    out = {"kernel": kname, "category": name, "bound": bound, "launches": launches,
+           "avg_launch_ms": ms / max(launches, 1), "share_of_profiled_ms": ms / tot_ms, "traffic": None}
+    if amount is None:
+        out.update({"achieved": None, "peak": None, "unit": None, "frac": None})
+        return out
+    if unit == "byte":
+        achieved = amount / (ms / 1e3) / 1e9
         peak = pk["hbm_gbs"]
-        return {"kernel": "k_sweep2d (leaf forward/backward block substitution)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "launches": launches, "avg_launch_ms": ms / max(launches, 1),
-                "peak_kind": f"{pk_kind} hbm_gbs", "share_of_profiled_ms": ms / sum(v[0] for v in prof.values())}
-    if name == "factor":
-        fl = n_runs * factor_flops(w)
-        achieved = fl / (ms / 1e3) / 1e12
+        out.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_kind": f"{pk_kind} hbm_gbs"})
+    else:
+        achieved = amount / (ms / 1e3) / 1e12
         peak = SM_COUNT * FP32_LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        return {"kernel": "k_factor2d (Schur recursion, Gauss-Jordan inverses)", "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "launches": launches, "avg_launch_ms": ms / max(launches, 1),
-                "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock",
-                "share_of_profiled_ms": ms / sum(v[0] for v in prof.values())}
-    return {"kernel": name, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
-            "share_of_profiled_ms": ms / sum(v[0] for v in prof.values())}
+        out.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock (derived)"})
+    return out
 
 
 # ------------------------------------------------------------------ CPU baseline

@@ -188,8 +188,11 @@ hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
  * Tracing.  With profiling enabled a handle records CUDA events on its stream around
  * the kernels of each category below (events cost a few microseconds of stream time
  * each); totals accumulate over hh_setup/hh_solve calls until the next enable.
- * Categories: 0 leaf factorisation, 1 leaf sweeps, 2 FP64 global residual, 3 coarse
- * projection C^H r, 4 Galerkin product, 5 sketch orthonormalisation, 6 sketch SVD.
+ * Categories: 0 leaf factorisation, 1 leaf sweep transform into the column eigenbasis,
+ * 2 leaf sweep recursions along the line (scalar recursions, or the block substitution
+ * of the explicit-inverse path), 3 leaf sweep transform back, 4 FP64 global residual,
+ * 5 coarse projection C^H r, 6 Galerkin product, 7 sketch orthonormalisation, 8 sketch
+ * SVD.
  * -------------------------------------------------------------------------------- */
 /* h != NULL: (re)start profiling of that handle, clearing its totals; h == NULL: set
  * whether handles created afterwards profile from their first set-up kernel. */

@@ -233,7 +233,8 @@ def hh_sketch_samples(h, child, out, stream=None) -> None:
     _check(LIB.hh_sketch_samples(h, child, _ptr(out), _stream(stream)), "hh_sketch_samples")
 
 
-PROFILE_CATEGORIES = ["factor", "sweep", "residual", "coarse_project", "galerkin", "qr", "svd"]
+PROFILE_CATEGORIES = ["factor", "sweep_in", "sweep_recur", "sweep_out", "residual", "coarse_project",
+                      "galerkin", "qr", "svd"]
 
 
 def hh_profile_enable(h, enable=True) -> None:

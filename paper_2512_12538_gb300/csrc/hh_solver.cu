@@ -35,7 +35,18 @@ static bool g_prof_default = false;   // profiling state of newly created handle
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Kernel categories timed by the optional event profiler (hh_profile_*).
-enum ProfCat { PC_FACTOR = 0, PC_SWEEP, PC_SPMV, PC_COARSE, PC_GALERKIN, PC_QR, PC_JACOBI, PC_NCAT };
+enum ProfCat {
+    PC_FACTOR = 0,   // leaf factorisation (eigen set-up or explicit block inverses)
+    PC_TIN,          // leaf sweep: transform into the eigenbasis
+    PC_RECUR,        // leaf sweep: recursions along the line (scalar, or the block substitution)
+    PC_TOUT,         // leaf sweep: transform back
+    PC_SPMV,         // FP64 global residual
+    PC_COARSE,       // coarse projection C^H r
+    PC_GALERKIN,     // Galerkin product
+    PC_QR,           // sketch orthonormalisation
+    PC_JACOBI,       // sketch SVD
+    PC_NCAT
+};
 
 // ----------------------------------------------------------------- allocator hook
 struct AllocHook {
@@ -457,13 +468,15 @@ struct Solver final : SolverBase {
         const int nl = (int)lev[L].size();
         if (eig) {
             if (!own && view_nc != nc) { upload_eig_view_tasks(nc); view_nc = nc; }
-            pbeg(PC_SWEEP);
-            launch_eig_sweep<T>(own ? d_etasks_own : d_etasks_view, nl, b_max, Sx, nc, stream);
-            pend();
+            for (int stg = 0; stg < 3; ++stg) {
+                pbeg(PC_TIN + stg);
+                launch_eig_sweep_stage<T>(stg, own ? d_etasks_own : d_etasks_view, nl, b_max, Sx, nc, stream);
+                pend();
+            }
             return;
         }
         if (!own && view_nc != nc) { upload_view_tasks(nc); view_nc = nc; }
-        pbeg(PC_SWEEP);
+        pbeg(PC_RECUR);
         launch_sweep<T>(own ? d_tasks_own : d_tasks_view, nl, b_max, Sx, nc, derr, stream);
         pend();
     }
@@ -546,7 +559,7 @@ struct Solver final : SolverBase {
         apply_M(l, m, true);
         for (int c : cs)
             launch_copy<T, T>(W[c] + row_off(c, nodes[c].ifrow, m), Z[c], (size_t)Sx * m, false, true, stream);
-        // SVD of Z^H = Q^H T: Gram Z^H Z (FP64), Hermitian Jacobi, V = Z U Sigma^{-1}
+        // SVD of Z^H = Q^H T: Gram Z^H Z (FP64), its Hermitian eigenproblem, V = Z U Sigma^{-1}
         for (int c : cs) {
             const int nb = launch_ip_partial<T, T>(Z[c], m, Z[c], m, Sx, m, m, partial, MAX_PART_BLOCKS, stream);
             launch_ip_reduce(partial, nb, m, m, Gm[c], nullptr, nullptr, stream);
@@ -555,7 +568,7 @@ struct Solver final : SolverBase {
         std::vector<double*> ls;
         for (int c : cs) { gs.push_back(Gm[c]); us.push_back(U[c]); ls.push_back(lam[c]); }
         pbeg(PC_JACOBI);
-        launch_jacobi(gs.data(), us.data(), ls.data(), (int)cs.size(), m, d_ptrs, stream);
+        launch_heig(gs.data(), us.data(), ls.data(), (int)cs.size(), m, r, d_ptrs, stream);
         pend();
         for (int c : cs) launch_form_v<T>(Z[c], U[c], lam[c], Vc[c], Sx, m, r, stream);
         // C_c = P_c M_c B_c^T V_c

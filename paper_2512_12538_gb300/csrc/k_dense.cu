@@ -3,7 +3,8 @@
 //    Gram matrix of the sketch);
 //  * the Galerkin product A_c = C^H A~ C (Sec. 1) fused with the 5-point operator;
 //  * orthonormalisation of the sketch Y = T Omega (Sec. 2, randomised SVD);
-//  * the small SVD: Hermitian Jacobi on Z^H Z in FP64 and V = Z U Sigma^{-1};
+//  * the small SVD: Hermitian eigenproblem of Z^H Z in FP64 (tridiagonal reduction,
+//    bisection, inverse iteration) and V = Z U Sigma^{-1};
 //  * Gauss-Jordan inversion with partial pivoting of A_c (FP64).
 #include "kernels.h"
 
@@ -87,6 +88,52 @@ __global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __res
     ip_store_partial<ACC>(acc, p, q, split, red, partial + (size_t)blockIdx.x * nout);
 }
 
+// Skinny products (p * q <= 64): each lane owns at most two outputs; warps stride over
+// rows with several rows in flight; the block's warps are combined in shared memory.
+template <typename TA, typename TB, typename ACC>
+__global__ void __launch_bounds__(256) k_ip_skinny(const cplx<TA>* __restrict__ A, int lda,
+                                                   const cplx<TB>* __restrict__ B, int ldb, size_t N, int p,
+                                                   int q, c128* partial) {
+    using CA = cplx<ACC>;
+    __shared__ CA red[8][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nout = p * q;
+    const int o0 = lane, o1 = lane + 32;
+    const int i0 = o0 / q, j0 = o0 - (o0 / q) * q;
+    const int i1 = o1 / q, j1 = o1 - (o1 / q) * q;
+    const bool h0 = o0 < nout, h1 = o1 < nout;
+    CA a0 = {0, 0}, a1 = {0, 0};
+    const size_t gw = (size_t)gridDim.x * 8;
+    size_t n = (size_t)blockIdx.x * 8 + warp;
+    constexpr int U = 4;
+    for (; n + (U - 1) * gw < N; n += U * gw) {
+        CA x0[U], y0[U], x1[U], y1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t r = n + u * gw;
+            if (h0) { x0[u] = cvt<ACC>(A[r * lda + i0]); y0[u] = cvt<ACC>(B[r * ldb + j0]); }
+            if (h1) { x1[u] = cvt<ACC>(A[r * lda + i1]); y1[u] = cvt<ACC>(B[r * ldb + j1]); }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (h0) cfma_cj(a0, x0[u], y0[u]);
+            if (h1) cfma_cj(a1, x1[u], y1[u]);
+        }
+    }
+    for (; n < N; n += gw) {
+        if (h0) cfma_cj(a0, cvt<ACC>(A[n * lda + i0]), cvt<ACC>(B[n * ldb + j0]));
+        if (h1) cfma_cj(a1, cvt<ACC>(A[n * lda + i1]), cvt<ACC>(B[n * ldb + j1]));
+    }
+    red[warp][o0] = a0;
+    red[warp][o1] = a1;
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        c128 t = {0.0, 0.0};
+        for (int w = 0; w < 8; ++w) t = t + cvt<double>(red[w][o]);
+        partial[(size_t)blockIdx.x * nout + o] = t;
+    }
+}
+
 static size_t ip_smem(int p, int q, size_t esz = sizeof(c128)) {
     const int nout = p * q;
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
@@ -96,8 +143,15 @@ static size_t ip_smem(int p, int q, size_t esz = sizeof(c128)) {
 template <typename TA, typename TB, typename ACC>
 int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, size_t N, int p, int q,
                       c128* partial, int max_blocks, cudaStream_t s) {
-    // rows per block: enough work per block to amortise the reduction over blocks
-    const size_t per = (size_t)p * q >= 256 ? 256 : 1024;
+    if (p * q <= 64) {
+        int grid = (int)((N + 63) / 64);
+        if (grid > max_blocks) grid = max_blocks;
+        if (grid < 1) grid = 1;
+        k_ip_skinny<TA, TB, ACC><<<grid, 256, 0, s>>>(A, lda, B, ldb, N, p, q, partial);
+        note_launch();
+        return grid;
+    }
+    const size_t per = 256;
     int grid = (int)((N + per - 1) / per);
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
@@ -116,12 +170,23 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
 // deterministic); optional out2 = Minv * out computed by the same (single) block.
 __global__ void __launch_bounds__(1024) k_ip_reduce(const c128* __restrict__ partial, int nblk, int p, int q,
                                                     c128* out, const c128* __restrict__ Minv, c128* out2) {
-    extern __shared__ c128 s_out[];
+    extern __shared__ c128 s_out[];          // [nout] sums, then [p*p] Minv when present
     const int nout = p * q;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    c128* s_m = s_out + nout;
+    if (Minv)
+        for (int t = threadIdx.x; t < p * p; t += blockDim.x) s_m[t] = Minv[t];
     for (int o = blockIdx.x * nw + (threadIdx.x >> 5); o < nout; o += gridDim.x * nw) {
-        c128 t = {0.0, 0.0};
-        for (int b = lane; b < nblk; b += 32) t = t + partial[(size_t)b * nout + o];
+        c128 t0 = {0.0, 0.0}, t1 = {0.0, 0.0}, t2 = {0.0, 0.0}, t3 = {0.0, 0.0};
+        int b = lane;
+        for (; b + 96 < nblk; b += 128) {
+            t0 = t0 + partial[(size_t)b * nout + o];
+            t1 = t1 + partial[(size_t)(b + 32) * nout + o];
+            t2 = t2 + partial[(size_t)(b + 64) * nout + o];
+            t3 = t3 + partial[(size_t)(b + 96) * nout + o];
+        }
+        for (; b < nblk; b += 32) t0 = t0 + partial[(size_t)b * nout + o];
+        c128 t = (t0 + t1) + (t2 + t3);
         t = warp_sum(t);
         if (lane == 0) {
             if (Minv) s_out[o] = t;
@@ -133,7 +198,7 @@ __global__ void __launch_bounds__(1024) k_ip_reduce(const c128* __restrict__ par
     for (int o = threadIdx.x; o < nout; o += blockDim.x) {
         const int i = o / q, j = o % q;
         c128 t = {0.0, 0.0};
-        for (int k = 0; k < p; ++k) cfma(t, Minv[i * p + k], s_out[k * q + j]);
+        for (int k = 0; k < p; ++k) cfma(t, s_m[i * p + k], s_out[k * q + j]);
         out2[o] = t;
     }
 }
@@ -146,7 +211,7 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
     }
     const int nout = p * q;
     if (Minv) {
-        k_ip_reduce<<<1, 1024, sizeof(c128) * nout, s>>>(partial, nblk, p, q, out, Minv, out2);
+        k_ip_reduce<<<1, 1024, sizeof(c128) * (nout + (size_t)p * p), s>>>(partial, nblk, p, q, out, Minv, out2);
     } else {
         int grid = (nout + 7) / 8;
         if (grid > 304) grid = 304;
@@ -274,132 +339,214 @@ void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scrat
     note_launch();
 }
 
-// -------------------------------------------------------------- Jacobi (FP64)
-// Cyclic Jacobi with round-robin ordering: each round applies m/2 disjoint unitary
-// plane rotations J = diag(1, e^{-i phi}) * [[c, s], [-s, c]] that annihilate G[p][q].
-__device__ __forceinline__ int rr_index(int i, int round, int n) {
-    return i == 0 ? 0 : 1 + (i - 1 + round) % (n - 1);
+// ------------------------------------------------------ Hermitian eigen (FP64)
+// Eigenvalues (all, descending) and the r leading eigenvectors of the m x m Hermitian
+// Gram matrix G = Z^H Z of the sketch, in FP64, one CTA per matrix:
+//  1. Householder reduction to tridiagonal form, H_k = I - tau v v^H applied on both
+//     sides of the trailing block (w = tau A v, q = w - (tau/2)(v^H w) v,
+//     A <- A - v q^H - q v^H);
+//  2. a diagonal unitary scaling makes the tridiagonal real symmetric;
+//  3. every eigenvalue by bisection on Sturm counts (one thread each);
+//  4. the r leading eigenvectors by inverse iteration on the tridiagonal (pivoted LU),
+//     mapped back through the scaling and the reflectors.
+static constexpr int HE_MAX = 64;
+
+__device__ int sturm_count(const double* d, const double* e2, int m, double x) {
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0.0) ++c;
+    for (int i = 1; i < m; ++i) {
+        if (q == 0.0) q = -1e-300;
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (q < 0.0) ++c;
+    }
+    return c;
 }
 
-__global__ void __launch_bounds__(256) k_jacobi(c128* const* Gp, c128* const* Up, double* const* lamp, int m) {
-    extern __shared__ c128 sj[];
-    const int n = m + (m & 1);          // padded to even
-    c128* G = sj;                       // m x m
-    c128* U = G + m * m;                // m x m
-    double* rot = (double*)(U + m * m); // per pair: c, s, cos(phi), sin(phi)
-    int* pq = (int*)(rot + 4 * (n / 2));
-    __shared__ double off_s, diag_s;
-    c128* Gg = Gp[blockIdx.x];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        G[e] = Gg[e];
-        U[e] = c128{(e / m == e % m) ? 1.0 : 0.0, 0.0};
-    }
+__global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, double* const* lamp, int m, int r) {
+    extern __shared__ __align__(16) unsigned char hsm[];
+    c128* A = (c128*)hsm;                    // m x m working matrix
+    c128* Vr = A + m * m;                    // reflector k stored in row k (length m-k-1)
+    c128* w = Vr + m * m;                    // m
+    double* tau = (double*)(w + m);          // m
+    double* d = tau + m;                     // m   diagonal of the real tridiagonal
+    double* eb = d + m;                      // m   |subdiagonal|
+    double* e2 = eb + m;                     // m   squared
+    c128* delta = (c128*)(e2 + m);           // m   diagonal unitary scaling
+    __shared__ c128 s_beta, s_K;
+    __shared__ double s_tau;
+    const c128* G = Gp[blockIdx.x];
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) A[t] = G[t];
     __syncthreads();
-    const int npair = n / 2;
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        // convergence test on the off-diagonal mass
-        if (threadIdx.x == 0) { off_s = 0.0; diag_s = 0.0; }
-        __syncthreads();
-        double off = 0.0, dg = 0.0;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            if (e / m == e % m) dg += abs2(G[e]); else off += abs2(G[e]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k + 2 < m; ++k) {
+        const int n = m - k - 1;             // length of the column below the diagonal
+        if (warp == 0) {
+            double a2 = 0.0;
+            for (int i = lane; i < n; i += 32) a2 += abs2(A[(k + 1 + i) * m + k]);
+            a2 = warp_sum(a2);
+            if (lane == 0) {
+                const double alpha = sqrt(a2);
+                const c128 x0 = A[(k + 1) * m + k];
+                const double ax0 = sqrt(abs2(x0));
+                const c128 ph = ax0 > 0.0 ? (1.0 / ax0) * x0 : c128{1.0, 0.0};
+                s_beta = (-alpha) * ph;
+                s_tau = alpha > 0.0 ? 1.0 / (alpha * (alpha + ax0)) : 0.0;   // 2 / ||v||^2
+            }
         }
-        off = warp_sum(off);
-        dg = warp_sum(dg);
-        if ((threadIdx.x & 31) == 0) { atomicAdd(&off_s, off); atomicAdd(&diag_s, dg); }
         __syncthreads();
-        if (off_s <= 1e-24 * diag_s || off_s == 0.0) break;   // off-diagonal <= 1e-12 relative
-        __syncthreads();
-        for (int round = 0; round < n - 1; ++round) {
-            if (threadIdx.x < npair) {
-                const int k = threadIdx.x;
-                int a = rr_index(k, round, n), b = rr_index(n - 1 - k, round, n);
-                if (a > b) { int t = a; a = b; b = t; }
-                pq[2 * k] = a;
-                pq[2 * k + 1] = b;
-                double c = 1.0, s = 0.0, cph = 1.0, sph = 0.0;
-                if (b < m) {
-                    const c128 g = G[a * m + b];
-                    const double ag = sqrt(abs2(g));
-                    const double app = G[a * m + a].re, aqq = G[b * m + b].re;
-                    if (ag > 1e-300 && ag > 1e-18 * sqrt(fabs(app * aqq))) {
-                        cph = g.re / ag;
-                        sph = g.im / ag;
-                        const double zeta = (aqq - app) / (2.0 * ag);
-                        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        s = t * c;
-                    }
-                }
-                rot[4 * k] = c; rot[4 * k + 1] = s; rot[4 * k + 2] = cph; rot[4 * k + 3] = sph;
-            }
-            __syncthreads();
-            // columns: (G J) and (U J): col_p' = c col_p - s e^{-i phi} col_q ; col_q' = s col_p + c e^{-i phi} col_q
-            for (int e = threadIdx.x; e < npair * m * 2; e += blockDim.x) {
-                const int which = e / (npair * m);
-                const int k = (e / m) % npair, r = e % m;
-                const int a = pq[2 * k], b = pq[2 * k + 1];
-                if (b >= m) continue;
-                const double c = rot[4 * k], s = rot[4 * k + 1];
-                const c128 em = {rot[4 * k + 2], -rot[4 * k + 3]};   // e^{-i phi}
-                c128* X = which ? U : G;
-                const c128 xp = X[r * m + a], xq = X[r * m + b];
-                const c128 eq = em * xq;
-                X[r * m + a] = c * xp - s * eq;
-                X[r * m + b] = s * xp + c * eq;
-            }
-            __syncthreads();
-            // rows: row_p' = c row_p - s e^{i phi} row_q ; row_q' = s row_p + c e^{i phi} row_q
-            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-                const int k = e / m, col = e % m;
-                const int a = pq[2 * k], b = pq[2 * k + 1];
-                if (b >= m) continue;
-                const double c = rot[4 * k], s = rot[4 * k + 1];
-                const c128 ep = {rot[4 * k + 2], rot[4 * k + 3]};
-                const c128 xp = G[a * m + col], xq = G[b * m + col];
-                const c128 eq = ep * xq;
-                G[a * m + col] = c * xp - s * eq;
-                G[b * m + col] = s * xp + c * eq;
-            }
-            __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            c128 v = A[(k + 1 + i) * m + k];
+            if (i == 0) v = v - s_beta;
+            Vr[k * m + i] = v;
         }
+        if (threadIdx.x == 0) tau[k] = s_tau;
+        __syncthreads();
+        const double tk = s_tau;
+        const c128* v = Vr + k * m;
+        // w = tau A' v
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            c128 acc = {0.0, 0.0};
+            const c128* row = A + (k + 1 + i) * m + (k + 1);
+            for (int j = 0; j < n; ++j) cfma(acc, row[j], v[j]);
+            w[i] = tk * acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            c128 acc = {0.0, 0.0};
+            for (int i = lane; i < n; i += 32) cfma_cj(acc, v[i], w[i]);
+            acc = warp_sum(acc);
+            if (lane == 0) s_K = (0.5 * tk) * acc;
+        }
+        __syncthreads();
+        const c128 K = s_K;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = w[i] - K * v[i];   // q
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = t / n, j = t - (t / n) * n;
+            c128& a = A[(k + 1 + i) * m + (k + 1 + j)];
+            a = a - v[i] * conj(w[j]) - w[i] * conj(v[j]);
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const c128 val = (i == 0) ? s_beta : c128{0.0, 0.0};
+            A[(k + 1 + i) * m + k] = val;
+            A[k * m + (k + 1 + i)] = conj(val);
+        }
+        __syncthreads();
     }
-    // sort eigenvalues descending (selection by one thread), permute U's columns
-    int* perm = pq;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < m; ++i) perm[i] = i;
+        c128 dl = {1.0, 0.0};
         for (int i = 0; i < m; ++i) {
-            int best = i;
-            for (int j = i + 1; j < m; ++j)
-                if (G[perm[j] * m + perm[j]].re > G[perm[best] * m + perm[best]].re) best = j;
-            int t = perm[i]; perm[i] = perm[best]; perm[best] = t;
+            d[i] = A[i * m + i].re;
+            delta[i] = dl;
+            if (i + 1 < m) {
+                const c128 e = A[(i + 1) * m + i];
+                const double ae = sqrt(abs2(e));
+                eb[i] = ae;
+                e2[i] = ae * ae;
+                if (ae > 0.0) dl = dl * ((1.0 / ae) * e);
+            }
         }
     }
     __syncthreads();
-    double* lam = lamp[blockIdx.x];
-    c128* Uo = Up[blockIdx.x];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int r = e / m, j = e % m;
-        Uo[e] = U[r * m + perm[j]];
+    // Gershgorin interval
+    double lo0 = 0.0, hi0 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const double rad = (i > 0 ? eb[i - 1] : 0.0) + (i + 1 < m ? eb[i] : 0.0);
+        lo0 = i ? fmin(lo0, d[i] - rad) : d[i] - rad;
+        hi0 = i ? fmax(hi0, d[i] + rad) : d[i] + rad;
     }
-    for (int j = threadIdx.x; j < m; j += blockDim.x) lam[j] = G[perm[j] * m + perm[j]].re;
+    const double span = fmax(hi0 - lo0, 1e-300);
+    lo0 -= 1e-12 * span;
+    hi0 += 1e-12 * span;
+    double* lam = lamp[blockIdx.x];
+    for (int kk = threadIdx.x; kk < m; kk += blockDim.x) {
+        const int j = m - 1 - kk;            // ascending index of the kk-th largest eigenvalue
+        double lo = lo0, hi = hi0;
+        for (int it = 0; it < 200 && hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)); ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (sturm_count(d, e2, m, mid) <= j) lo = mid;
+            else hi = mid;
+        }
+        lam[kk] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+    c128* U = Up[blockIdx.x];
+    for (int kk = threadIdx.x; kk < r; kk += blockDim.x) {
+        const double l = lam[kk];
+        const double mu = l + 1e-14 * fmax(fabs(l), span * 1e-3);
+        double dg[HE_MAX], up[HE_MAX], up2[HE_MAX], lo[HE_MAX], y[HE_MAX];
+        bool sw[HE_MAX];
+        for (int i = 0; i < m; ++i) {
+            dg[i] = d[i] - mu;
+            up[i] = i + 1 < m ? eb[i] : 0.0;
+            up2[i] = 0.0;
+            y[i] = 1.0 + 1e-3 * i;
+        }
+        for (int i = 0; i + 1 < m; ++i) {
+            const double sub = eb[i];
+            if (fabs(dg[i]) >= fabs(sub)) {
+                sw[i] = false;
+                const double f = dg[i] != 0.0 ? sub / dg[i] : 0.0;
+                lo[i] = f;
+                dg[i + 1] -= f * up[i];
+            } else {
+                sw[i] = true;
+                const double f = dg[i] / sub;
+                dg[i] = sub;
+                lo[i] = f;
+                const double t = up[i];
+                up[i] = dg[i + 1];
+                dg[i + 1] = t - f * dg[i + 1];
+                if (i + 2 < m) {
+                    up2[i] = up[i + 1];
+                    up[i + 1] = -f * up[i + 1];
+                }
+            }
+        }
+        for (int i = 0; i < m; ++i)
+            if (fabs(dg[i]) < 1e-300) dg[i] = 1e-300;
+        for (int it = 0; it < 3; ++it) {
+            for (int i = 0; i + 1 < m; ++i) {
+                if (!sw[i]) y[i + 1] -= lo[i] * y[i];
+                else { const double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t - lo[i] * y[i]; }
+            }
+            y[m - 1] /= dg[m - 1];
+            if (m > 1) y[m - 2] = (y[m - 2] - up[m - 2] * y[m - 1]) / dg[m - 2];
+            for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - up[i] * y[i + 1] - up2[i] * y[i + 2]) / dg[i];
+            double nr = 0.0;
+            for (int i = 0; i < m; ++i) nr += y[i] * y[i];
+            nr = nr > 0.0 ? 1.0 / sqrt(nr) : 1.0;
+            for (int i = 0; i < m; ++i) y[i] *= nr;
+        }
+        // u = Q D y with Q = H_0 ... H_{m-3}
+        c128 u[HE_MAX];
+        for (int i = 0; i < m; ++i) u[i] = y[i] * delta[i];
+        for (int k = m - 3; k >= 0; --k) {
+            const int n = m - k - 1;
+            const c128* v = Vr + k * m;
+            c128 s = {0.0, 0.0};
+            for (int i = 0; i < n; ++i) cfma_cj(s, v[i], u[k + 1 + i]);
+            s = tau[k] * s;
+            for (int i = 0; i < n; ++i) u[k + 1 + i] = u[k + 1 + i] - v[i] * s;
+        }
+        for (int i = 0; i < m; ++i) U[i * m + kk] = u[i];
+    }
 }
 
-void launch_jacobi(c128* const* G, c128* const* U, double* const* lam, int nq, int m, void** scratch,
-                   cudaStream_t s) {
-    // scratch holds 3*nq device pointers
+void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int m, int r, void** scratch,
+                 cudaStream_t s) {
     void* hp[3 * 64];
     for (int i = 0; i < nq; ++i) { hp[i] = G[i]; hp[nq + i] = U[i]; hp[2 * nq + i] = lam[i]; }
     cudaMemcpyAsync(scratch, hp, sizeof(void*) * 3 * nq, cudaMemcpyHostToDevice, s);
-    const int n = m + (m & 1);
-    const size_t sm = sizeof(c128) * 2 * m * m + sizeof(double) * 4 * (n / 2) + sizeof(int) * (n + 2);
+    const size_t sm = sizeof(c128) * (2 * (size_t)m * m + m) + sizeof(double) * 4 * m + sizeof(c128) * m + 64;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_heig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_jacobi<<<nq, 256, sm, s>>>((c128* const*)scratch, (c128* const*)(scratch + nq),
-                                 (double* const*)(scratch + 2 * nq), m);
+    k_heig<<<nq, 256, sm, s>>>((c128* const*)scratch, (c128* const*)(scratch + nq), (double* const*)(scratch + 2 * nq),
+                              m, r);
     note_launch();
 }
 

@@ -21,6 +21,8 @@
 // tridiagonal W^{-1/2} K W^{-1/2}; eigenvalues by the Aberth-Ehrlich simultaneous
 // iteration on its characteristic polynomial, eigenvectors by inverse iteration with a
 // pivoted tridiagonal LU, normalised q^T q = 1 (no conjugation).
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace hh {
@@ -244,11 +246,17 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
     for (int t = 0; t < GT_RPT; ++t) acc[t] = {0, 0};
     for (int k0 = 0; k0 < b; k0 += GT_K) {
         const int kc = min(GT_K, b - k0);
-        for (int e2 = threadIdx.x; e2 < b * GT_K; e2 += GT_THREADS) {
-            const int r = e2 / GT_K, k = e2 % GT_K;
-            cplx<T> v = {0, 0};
-            if (k < kc) v = TRANS ? V[(size_t)(k0 + k) * b + r] : V[(size_t)r * b + k0 + k];
-            Vs[e2] = v;
+        if (TRANS) {
+            // op(V)[r][k] = V[k][r]: read rows of V (consecutive r), store transposed
+            for (int e2 = threadIdx.x; e2 < b * GT_K; e2 += GT_THREADS) {
+                const int k = e2 / b, r = e2 - k * b;
+                Vs[r * GT_K + k] = k < kc ? V[(size_t)(k0 + k) * b + r] : cplx<T>{0, 0};
+            }
+        } else {
+            for (int e2 = threadIdx.x; e2 < b * GT_K; e2 += GT_THREADS) {
+                const int r = e2 / GT_K, k = e2 % GT_K;
+                Vs[e2] = k < kc ? V[(size_t)r * b + k0 + k] : cplx<T>{0, 0};
+            }
         }
         for (int e2 = threadIdx.x; e2 < GT_K * GT_N; e2 += GT_THREADS) {
             const int k = e2 / GT_N, j = e2 % GT_N;
@@ -277,9 +285,14 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
     }
 }
 
-// Scalar recursions, one thread per (mode, right-hand side), in place on Fh[m][i][c].
+// Scalar recursions, in place on Fh[m][i][c].  A CTA takes rm modes of one leaf with all
+// their right-hand sides: the modes' coefficients xi[i][m] and right-hand sides along the
+// whole line are staged in shared memory by all threads (coalesced), one thread per
+// (mode, right-hand side) runs the forward/backward recursion out of shared memory, and
+// the results are written back cooperatively.  Lines too long to stage use
+// k_eig_recur_global (one thread per (mode, right-hand side) straight from memory).
 template <typename T>
-__global__ void k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs) {
+__global__ void k_eig_recur_global(const EigTask* __restrict__ tasks, int Sx, int nrhs) {
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,33 +300,55 @@ __global__ void k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs)
     const int m = t / nrhs, c = t % nrhs;
     const cplx<T>* xi = (const cplx<T>*)tk.xi;
     cplx<T>* f = (cplx<T>*)tk.Fh + (size_t)m * Sx * nrhs + c;
-    constexpr int U = 8;
     cplx<T> y = {0, 0};
-    for (int i0 = 0; i0 < Sx; i0 += U) {
-        cplx<T> fv[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (i0 + u < Sx) { fv[u] = f[(size_t)(i0 + u) * nrhs]; xv[u] = xi[(size_t)(i0 + u) * b + m]; }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (i0 + u < Sx) {
-                y = xv[u] * (fv[u] + y);
-                f[(size_t)(i0 + u) * nrhs] = y;
-            }
+    for (int i = 0; i < Sx; ++i) {
+        y = xi[(size_t)i * b + m] * (f[(size_t)i * nrhs] + y);
+        f[(size_t)i * nrhs] = y;
     }
-    cplx<T> x = y;   // x_{n-1} = y_{n-1}
-    for (int i1 = Sx - 2; i1 >= 0; i1 -= U) {
-        cplx<T> yv[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (i1 - u >= 0) { yv[u] = f[(size_t)(i1 - u) * nrhs]; xv[u] = xi[(size_t)(i1 - u) * b + m]; }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (i1 - u >= 0) {
-                x = yv[u] + xv[u] * x;
-                f[(size_t)(i1 - u) * nrhs] = x;
-            }
+    cplx<T> x = y;
+    for (int i = Sx - 2; i >= 0; --i) {
+        x = f[(size_t)i * nrhs] + xi[(size_t)i * b + m] * x;
+        f[(size_t)i * nrhs] = x;
     }
+}
+
+static constexpr int RM_THREADS = 256;
+template <typename T>
+__global__ void __launch_bounds__(RM_THREADS) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs,
+                                                          int rm) {
+    const EigTask tk = tasks[blockIdx.y];
+    const int b = tk.b;
+    const int m0 = blockIdx.x * rm;
+    if (m0 >= b) return;
+    const int nm = min(rm, b - m0);
+    extern __shared__ __align__(16) unsigned char rsm[];
+    cplx<T>* xs = (cplx<T>*)rsm;                      // [Sx][nm]
+    cplx<T>* fs = xs + (size_t)Sx * nm;               // [nm][Sx][nrhs]
+    const cplx<T>* xi = (const cplx<T>*)tk.xi;
+    cplx<T>* fh = (cplx<T>*)tk.Fh;
+    const size_t line = (size_t)Sx * nrhs;
+    for (size_t e2 = threadIdx.x; e2 < (size_t)Sx * nm; e2 += blockDim.x) {
+        const int i = (int)(e2 / nm), mm = (int)(e2 - (size_t)i * nm);
+        xs[e2] = xi[(size_t)i * b + m0 + mm];
+    }
+    for (size_t e2 = threadIdx.x; e2 < (size_t)nm * line; e2 += blockDim.x) fs[e2] = fh[(size_t)m0 * line + e2];
+    __syncthreads();
+    for (int t = threadIdx.x; t < nm * nrhs; t += blockDim.x) {
+        const int mm = t / nrhs, c = t - (t / nrhs) * nrhs;
+        cplx<T>* f = fs + (size_t)mm * line + c;
+        cplx<T> y = {0, 0};
+        for (int i = 0; i < Sx; ++i) {
+            y = xs[(size_t)i * nm + mm] * (f[(size_t)i * nrhs] + y);
+            f[(size_t)i * nrhs] = y;
+        }
+        cplx<T> x = y;
+        for (int i = Sx - 2; i >= 0; --i) {
+            x = f[(size_t)i * nrhs] + xs[(size_t)i * nm + mm] * x;
+            f[(size_t)i * nrhs] = x;
+        }
+    }
+    __syncthreads();
+    for (size_t e2 = threadIdx.x; e2 < (size_t)nm * line; e2 += blockDim.x) fh[(size_t)m0 * line + e2] = fs[e2];
 }
 
 template <typename T>
@@ -327,8 +362,11 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
     note_launch();
 }
 
+// One leaf solve = three launches: f^ = V^T f, the scalar recursions, x = V x^.
+// stage 0: transform in, 1: recursions, 2: transform out.
 template <typename T>
-void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s) {
+void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
+                            cudaStream_t s) {
     const int J = Sx * nrhs;
     dim3 g1((J + GT_N - 1) / GT_N, ntasks);
     const size_t sm = sizeof(cplx<T>) * ((size_t)b_max * GT_K + GT_K * GT_N);
@@ -336,15 +374,33 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
     if (!attr) {
         cudaFuncSetAttribute(k_eig_gemm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         cudaFuncSetAttribute(k_eig_gemm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_eig_recur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0);
-    note_launch();
-    dim3 g2((b_max * nrhs + 127) / 128, ntasks);
-    k_eig_recur<T><<<g2, 128, 0, s>>>(d_tasks, Sx, nrhs);
-    note_launch();
-    k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1);
-    note_launch();
+    if (stage == 0) {
+        k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0);
+        note_launch();
+    } else if (stage == 2) {
+        k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1);
+        note_launch();
+    } else {
+        // modes per CTA: the staged line (Sx x (1 + nrhs) per mode) within ~96 KB
+        const size_t per_mode = sizeof(cplx<T>) * (size_t)Sx * (1 + nrhs);
+        if (per_mode > (200u << 10)) {
+            dim3 gg((b_max * nrhs + 127) / 128, ntasks);
+            k_eig_recur_global<T><<<gg, 128, 0, s>>>(d_tasks, Sx, nrhs);
+        } else {
+            const int rm = (int)std::max<size_t>(1, std::min<size_t>(32, (96u << 10) / per_mode));
+            dim3 g2((b_max + rm - 1) / rm, ntasks);
+            k_eig_recur<T><<<g2, RM_THREADS, per_mode * rm, s>>>(d_tasks, Sx, nrhs, rm);
+        }
+        note_launch();
+    }
+}
+
+template <typename T>
+void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s) {
+    for (int st = 0; st < 3; ++st) launch_eig_sweep_stage<T>(st, d_tasks, ntasks, b_max, Sx, nrhs, s);
 }
 
 int eig_bmax() { return GT_ROWS * GT_RPT < EIG_BMAX ? GT_ROWS * GT_RPT : EIG_BMAX; }
@@ -353,6 +409,8 @@ size_t eig_work_elems(int b) { return (size_t)b * 6 * b; }
 template void launch_eig_factor<float>(const EigTask*, int, int, int, double, int*, cudaStream_t);
 template void launch_eig_factor<double>(const EigTask*, int, int, int, double, int*, cudaStream_t);
 template void launch_eig_sweep<float>(const EigTask*, int, int, int, int, cudaStream_t);
+template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t);
+template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep<double>(const EigTask*, int, int, int, int, cudaStream_t);
 
 }  // namespace hh

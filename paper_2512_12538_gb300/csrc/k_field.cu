@@ -240,9 +240,33 @@ __global__ void k_coarse_update(const cplx<TC>* __restrict__ C, const c128* __re
         W[t] = W[t] + cvt<TW>(acc);
     }
 }
+// Single column (nc = 1): a warp per point, lanes across the p basis columns, so that
+// each row of C is read as one contiguous segment.
+template <typename TC, typename TW>
+__global__ void k_coarse_update1(const cplx<TC>* __restrict__ C, const c128* __restrict__ y,
+                                 cplx<TW>* __restrict__ W, size_t npts, int p) {
+    __shared__ cplx<TC> ys[128];
+    for (int t = threadIdx.x; t < p; t += blockDim.x) ys[t] = cvt<TC>(y[t]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const size_t nwarp = (size_t)gridDim.x * (blockDim.x >> 5);
+    for (size_t pt = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pt < npts; pt += nwarp) {
+        const cplx<TC>* cr = C + pt * p;
+        cplx<TC> acc = {0, 0};
+        for (int j = lane; j < p; j += 32) cfma(acc, cr[j], ys[j]);
+        acc = warp_sum(acc);
+        if (lane == 0) W[pt] = W[pt] + cvt<TW>(acc);
+    }
+}
+
 template <typename TC, typename TW>
 void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t npts, int p, int nc,
                           cudaStream_t s) {
+    if (nc == 1 && p <= 128) {
+        k_coarse_update1<TC, TW><<<grid_for(npts, 8), 256, 0, s>>>(C, y, W, npts, p);
+        note_launch();
+        return;
+    }
     const size_t total = npts * nc;
     k_coarse_update<TC, TW><<<grid_for(total, 256), 256, sizeof(c128) * p * nc, s>>>(C, y, W, npts, p, nc);
     note_launch();

@@ -73,10 +73,10 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
 // In-place QR (classical Gram-Schmidt, two passes) of nq independent Sx x m blocks.
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s);
-// Hermitian Jacobi eigensolver on nq m x m FP64 matrices: eigenvalues descending in
-// lam, eigenvectors (columns) in U.  G is overwritten.
-void launch_jacobi(c128* const* G, c128* const* U, double* const* lam, int nq, int m,
-                   void** dev_ptr_scratch, cudaStream_t s);
+// Hermitian eigenproblems of nq m x m FP64 matrices (m <= 64): all eigenvalues
+// descending in lam, the r leading eigenvectors in columns 0..r-1 of U (m x m).
+void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int m, int r,
+                 void** dev_ptr_scratch, cudaStream_t s);
 // V[x][j] = sum_k Z[x][k] U[k][j] / sqrt(lam_j)  for j < r
 template <typename T>
 void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* V, int Sx, int m, int r,
@@ -116,6 +116,10 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
                        cudaStream_t s);
 template <typename T>
 void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s);
+// stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^
+template <typename T>
+void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
+                            cudaStream_t s);
 int eig_bmax();
 size_t eig_work_elems(int b);
 

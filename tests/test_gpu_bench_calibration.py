@@ -60,7 +60,8 @@ def test_profiler_and_launch_counter(hh, case):
         st = hh.hh_solve(h, fd, gd, u)
         prof = hh.hh_profile_read(h)
         assert prof["factor"][1] == 1 and prof["factor"][0] > 0
-        assert prof["sweep"][1] == 6 + st.iters          # 3 sketch passes per level + 1 per iteration
+        for stage in ("sweep_in", "sweep_recur", "sweep_out"):
+            assert prof[stage][1] == 6 + st.iters        # 3 sketch passes per level + 1 per iteration
         assert prof["galerkin"][1] == 3 and prof["svd"][1] == 2 and prof["qr"][1] == 2
         assert hh.hh_launch_count() - n0 > 50
     finally:
