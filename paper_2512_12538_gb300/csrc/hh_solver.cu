@@ -156,6 +156,7 @@ static inline cudaError_t ck(cudaError_t e, cudaError_t& first) {
 }
 
 static const int MAX_PART_BLOCKS = 304;   // 2 x 152 SMs
+static const int COARSE_BLOCKS = 64;      // partial blocks of a one-column coarse projection
 
 struct SolverBase {
     hh_params P{};
@@ -261,6 +262,7 @@ struct Solver final : SolverBase {
     c128* partial = nullptr;
     double *npart = nullptr, *dnorm = nullptr;
     int* derr = nullptr;
+    unsigned* dcounter = nullptr;   // ticket counter of the last-block reductions (zero between launches)
     LeafTask *d_tasks_view = nullptr, *d_tasks_own = nullptr, *d_task_one = nullptr;
     // eigenbasis leaf path
     bool eig = false;
@@ -371,6 +373,7 @@ struct Solver final : SolverBase {
         npart = a.take<double>(2048);
         dnorm = a.take<double>(4);
         derr = a.take<int>(4);
+        dcounter = a.take<unsigned>(4);
         const int nleaf = 1 << L;
         d_tasks_view = a.take<LeafTask>(nleaf);
         d_tasks_own = a.take<LeafTask>(nleaf);
@@ -516,13 +519,21 @@ struct Solver final : SolverBase {
 
     // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
     void coarse_correct(int p, const CT* vin, int nc) {
+        if (nc == 1) {
+            pbeg(PC_COARSE);
+            launch_coarse_proj1<T, T, T>(C[p], vin, W[p], geom(p), 2 * r, partial, dcounter, Ainv[p], ycoef[p],
+                                         stream);
+            pend();
+            launch_coarse_upd1<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, stream);
+            return;
+        }
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
         pbeg(PC_COARSE);
-        const int nb = launch_ip_partial<T, T, T>(C[p], 2 * r, R[p], nc, pts(p), 2 * r, nc, partial,
-                                                  MAX_PART_BLOCKS, stream);
+        const int nb = launch_ip_partial_colA<T, T, T>(C[p], R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
+                                                       stream);
         pend();
         launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
-        launch_coarse_update<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
+        launch_coarse_updn<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
     }
 
     // ------------------------------------------------------------------ set-up
@@ -582,10 +593,9 @@ struct Solver final : SolverBase {
             for (int k = 0; k < 2; ++k) {
                 const int c = nodes[p].child[k];
                 const Node& cn = nodes[c];
-                ck(cudaMemcpy2DAsync(C[p] + row_off(p, cn.own_a, 2 * r) + k * r, sizeof(CT) * 2 * r,
-                                     W[c] + row_off(c, cn.own_a, r), sizeof(CT) * r, sizeof(CT) * r,
-                                     (size_t)(cn.own_b - cn.own_a) * Sx, cudaMemcpyDeviceToDevice, stream),
-                   cerr);
+                launch_build_basis<T>(W[c], (size_t)(cn.own_a - cn.ra) * Sx, r, C[p], pts(p), k * r,
+                                      (size_t)(cn.own_a - nodes[p].ra) * Sx, (size_t)(cn.own_b - cn.own_a) * Sx,
+                                      stream);
             }
             // A_c = C_p^H A~_p C_p, then its inverse
             pbeg(PC_GALERKIN);
@@ -599,6 +609,7 @@ struct Solver final : SolverBase {
 
     hh_status setup() override {
         zero(derr, sizeof(int) * 4);
+        zero(dcounter, sizeof(unsigned) * 4);
         for (int id = 1; id < nn; ++id) zero(Vs[id], sizeof(CT) * pts(id) * nmax);
         if (eig) {
             std::vector<EigTask> own;
@@ -651,12 +662,12 @@ struct Solver final : SolverBase {
             launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), ut + row_off(0, cn.own_a, 1),
                                    (size_t)(cn.own_b - cn.own_a) * Sx, true, false, stream);
         }
-        launch_apply<double, double, double>(ut, rhs, res, geom(0), 1, 1.0, nullptr, nullptr, stream);
-        const int nb = launch_ip_partial<T, double, T>(C[0], 2 * r, res, 1, N, 2 * r, 1, partial, MAX_PART_BLOCKS,
-                                                       stream);
-        launch_ip_reduce(partial, nb, 2 * r, 1, nullptr, Ainv[0], ycoef[0], stream);
+        pbeg(PC_COARSE);
+        launch_coarse_proj1<T, double, double>(C[0], rhs, ut, geom(0), 2 * r, partial, dcounter, Ainv[0], ycoef[0],
+                                               stream);
+        pend();
         if (out != ut) d2d(out, ut, sizeof(c128) * N);
-        launch_coarse_update<T, double>(C[0], ycoef[0], out, N, 2 * r, 1, stream);
+        launch_coarse_upd1<T, double>(C[0], ycoef[0], out, N, 2 * r, stream);
     }
 
     hh_status norm_sq(const c128* x, double* dst) {
@@ -954,11 +965,10 @@ struct Solver final : SolverBase {
 
     hh_status coarse_apply(int p, const c128* rr, c128* z) override {
         if (!valid_node(p) || nodes[p].leaf() || !rr || !z) return HH_EINVAL;
-        const int nb = launch_ip_partial<T, double>(C[p], 2 * r, rr, 1, pts(p), 2 * r, 1, partial, MAX_PART_BLOCKS,
-                                                    stream);
-        launch_ip_reduce(partial, nb, 2 * r, 1, nullptr, Ainv[p], ycoef[p], stream);
+        launch_coarse_proj1<T, double, double>(C[p], rr, nullptr, geom(p), 2 * r, partial, dcounter, Ainv[p],
+                                               ycoef[p], stream);
         zero(z, sizeof(c128) * pts(p));
-        launch_coarse_update<T, double>(C[p], ycoef[p], z, pts(p), 2 * r, 1, stream);
+        launch_coarse_upd1<T, double>(C[p], ycoef[p], z, pts(p), 2 * r, stream);
         hh_status st;
         sync_check(st);
         return st;

@@ -1,0 +1,231 @@
+// k_coarse.cu -- the coarse correction of Eq. (3), w <- w + C_p A_c^{-1} C_p^H (v - A~_p w),
+// with the coarse basis stored column-major: C[j * N + pt], j < p = 2r, pt < N points of
+// the node's band, so that every kernel below reads C with consecutive threads on
+// consecutive points.
+#include "kernels.h"
+
+namespace hh {
+
+static int blocks_for(size_t n, int threads, int cap) {
+    size_t g = (n + threads - 1) / threads;
+    if (g > (size_t)cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// C[(coff + j) * ldc + dst0 + q] = src[(src0 + q) * r + j], q < n, j < r
+// (scatter of a child's extension [points][r] into its block of the parent's basis).
+template <typename T>
+__global__ void k_build_basis(const cplx<T>* __restrict__ src, size_t src0, int r, cplx<T>* __restrict__ C,
+                              size_t ldc, int coff, size_t dst0, size_t n) {
+    const size_t total = n * r;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n);
+        const size_t q = t - (size_t)j * n;
+        C[(size_t)(coff + j) * ldc + dst0 + q] = src[(src0 + q) * r + j];
+    }
+}
+template <typename T>
+void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size_t ldc, int coff, size_t dst0,
+                        size_t n, cudaStream_t s) {
+    k_build_basis<T><<<blocks_for(n * r, 256, 152 * 8), 256, 0, s>>>(src, src0, r, C, ldc, coff, dst0, n);
+    note_launch();
+}
+
+// Warp reduce-scatter of 32 values per lane: afterwards lane l holds the warp sum of value
+// l.  Five butterfly stages; at the stage of width k each lane keeps the half of its
+// values selected by bit k of its lane index and adds its partner's copy of that half
+// (31 shuffles per component instead of 32 x 5 for separate reductions).
+template <typename T>
+__device__ __forceinline__ cplx<T> warp_reduce_scatter32(cplx<T> (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        const bool up = (lane & k) != 0;
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            const cplx<T> lo = v[i], hi = v[i + k];
+            const cplx<T> send = up ? lo : hi;
+            const cplx<T> keep = up ? hi : lo;
+            cplx<T> got;
+            got.re = __shfl_xor_sync(0xffffffffu, send.re, k);
+            got.im = __shfl_xor_sync(0xffffffffu, send.im, k);
+            v[i] = keep + got;
+        }
+    }
+    return v[0];
+}
+
+// One column.  Every thread forms r_pt = v_pt - (A~ w)_pt (w may be null: r = v) in the
+// precision of v and w, accumulates conj(C[j][pt]) r_pt for a chunk of PC columns in ACC,
+// and the block writes its partial sums.  The last block to finish (ticket counter) adds
+// the partials in block order (FP64), multiplies by the FP64 inverse Galerkin matrix and
+// writes y = A_c^{-1} C^H r, then resets the counter.
+template <typename TC, typename TV, typename TW, typename ACC, int PC>
+__global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict__ C, const cplx<TV>* __restrict__ v,
+                                                      const cplx<TW>* __restrict__ w, OpGeom g, int p,
+                                                      c128* __restrict__ partial, unsigned* counter,
+                                                      const c128* __restrict__ Minv, c128* __restrict__ y) {
+    using CA = cplx<ACC>;
+    using CW = cplx<decltype(TV() + TW())>;
+    __shared__ CA red[8][PC];
+    __shared__ unsigned ticket;
+    __shared__ c128 s_sum[64];
+    const size_t N = (size_t)g.b * g.Sx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int j0 = 0; j0 < p; j0 += PC) {
+        const int pc = min(PC, p - j0);
+        CA acc[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) acc[j] = {0, 0};
+        for (size_t pt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; pt < N; pt += stride) {
+            CW rv = cvt<decltype(TV() + TW())>(v[pt]);
+            if (w) {
+                const int i = (int)(pt % g.Sx), jr = (int)(pt / g.Sx);
+                using R = decltype(TV() + TW());
+                const c128 d = op_diag(jr, i, g);
+                const cplx<R> dg = {(R)d.re, (R)d.im};
+                cplx<R> ax = dg * cvt<R>(w[pt]);
+                const R wj = (R)wrow(jr, g.b), wi = (R)wcol(i, g.Sx);
+                if (g.Sx > 1) {
+                    if (i > 0) ax = ax - wj * cvt<R>(w[pt - 1]);
+                    if (i < g.Sx - 1) ax = ax - wj * cvt<R>(w[pt + 1]);
+                }
+                if (jr > 0) ax = ax - wi * cvt<R>(w[pt - g.Sx]);
+                if (jr < g.b - 1) ax = ax - wi * cvt<R>(w[pt + g.Sx]);
+                rv = rv - ax;
+            }
+            const CA ra = cvt<ACC>(rv);
+#pragma unroll
+            for (int jb = 0; jb < PC; jb += 16) {
+                cplx<TC> cv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    cv[u] = (jb + u < pc) ? C[(size_t)(j0 + jb + u) * N + pt] : cplx<TC>{0, 0};
+                asm volatile("" ::: "memory");
+#pragma unroll
+                for (int u = 0; u < 16; ++u) cfma_cj(acc[jb + u], cvt<ACC>(cv[u]), ra);
+            }
+        }
+        if (PC == 32) {
+            const CA t = warp_reduce_scatter32(*reinterpret_cast<CA(*)[32]>(&acc[0]));
+            red[warp][lane] = t;
+        } else {
+#pragma unroll
+            for (int j = 0; j < PC; ++j) {
+                const CA t = warp_sum(acc[j]);
+                if (lane == 0) red[warp][j] = t;
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < pc; j += blockDim.x) {
+            c128 t = {0.0, 0.0};
+            for (int q = 0; q < 8; ++q) t = t + cvt<double>(red[q][j]);
+            partial[(size_t)blockIdx.x * p + j0 + j] = t;
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        c128 t = {0.0, 0.0};
+        for (unsigned b = 0; b < gridDim.x; ++b) t = t + ((volatile c128*)partial)[(size_t)b * p + j];
+        s_sum[j] = t;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        c128 t = {0.0, 0.0};
+        for (int k = 0; k < p; ++k) cfma(t, Minv[j * p + k], s_sum[k]);
+        y[j] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <typename TC, typename TV, typename TW>
+void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
+                         unsigned* counter, const c128* Minv, c128* y, cudaStream_t s) {
+    const size_t N = (size_t)g.b * g.Sx;
+    const int grid = blocks_for(N, 256 * 2, 152 * 2);
+    // accumulate in the basis precision; 16 FP64 or 32 FP32 columns per pass
+    if (sizeof(TC) == 8) k_coarse_proj1<TC, TV, TW, TC, 16><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
+    else k_coarse_proj1<TC, TV, TW, TC, 32><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
+    note_launch();
+}
+
+// W[pt] += sum_j C[j][pt] y[j]  (one column; accumulated in the basis precision).
+// A block takes 64 consecutive points; its four groups of 64 threads each sum a quarter
+// of the p columns (coalesced reads of C along the points), combined in shared memory.
+template <typename TC, typename TW>
+__global__ void __launch_bounds__(256) k_coarse_upd1(const cplx<TC>* __restrict__ C, const c128* __restrict__ y,
+                                                     cplx<TW>* __restrict__ W, size_t N, int p) {
+    __shared__ cplx<TC> ys[64];
+    __shared__ cplx<TC> part[4][64];
+    for (int j = threadIdx.x; j < p; j += blockDim.x) ys[j] = cvt<TC>(y[j]);
+    __syncthreads();
+    const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;
+    const int per = (p + 3) / 4, ja = jg * per, jb = min(p, ja + per);
+    for (size_t base = (size_t)blockIdx.x * 64; base < N; base += (size_t)gridDim.x * 64) {
+        const size_t pt = base + q;
+        cplx<TC> acc = {0, 0};
+        if (pt < N) {
+            cplx<TC> cv[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cv[u] = (ja + u < jb) ? C[(size_t)(ja + u) * N + pt] : cplx<TC>{0, 0};
+            asm volatile("" ::: "memory");
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cfma(acc, cv[u], ys[(ja + u) & 63]);
+        }
+        part[jg][q] = acc;
+        __syncthreads();
+        if (jg == 0 && pt < N) W[pt] = W[pt] + cvt<TW>((part[0][q] + part[1][q]) + (part[2][q] + part[3][q]));
+        __syncthreads();
+    }
+}
+template <typename TC, typename TW>
+void launch_coarse_upd1(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, cudaStream_t s) {
+    k_coarse_upd1<TC, TW><<<blocks_for(N, 64, 152 * 16), 256, 0, s>>>(C, y, W, N, p);
+    note_launch();
+}
+
+// Several columns (set-up): W[pt][c] += sum_j C[j][pt] y[j][c]
+template <typename TC, typename TW>
+__global__ void k_coarse_updn(const cplx<TC>* __restrict__ C, const c128* __restrict__ y, cplx<TW>* __restrict__ W,
+                              size_t N, int p, int nc) {
+    extern __shared__ c128 ysn[];
+    for (int t = threadIdx.x; t < p * nc; t += blockDim.x) ysn[t] = y[t];
+    __syncthreads();
+    const size_t total = N * nc;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % nc);
+        const size_t pt = t / nc;
+        cplx<TC> acc = {0, 0};
+#pragma unroll 16
+        for (int j = 0; j < p; ++j) cfma(acc, C[(size_t)j * N + pt], cvt<TC>(ysn[j * nc + c]));
+        W[t] = W[t] + cvt<TW>(acc);
+    }
+}
+template <typename TC, typename TW>
+void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s) {
+    k_coarse_updn<TC, TW><<<blocks_for(N * nc, 256, 152 * 8), 256, sizeof(c128) * p * nc, s>>>(C, y, W, N, p, nc);
+    note_launch();
+}
+
+template void launch_build_basis<float>(const c64*, size_t, int, c64*, size_t, int, size_t, size_t, cudaStream_t);
+template void launch_build_basis<double>(const c128*, size_t, int, c128*, size_t, int, size_t, size_t, cudaStream_t);
+template void launch_coarse_proj1<float, float, float>(const c64*, const c64*, const c64*, OpGeom, int, c128*,
+                                                       unsigned*, const c128*, c128*, cudaStream_t);
+template void launch_coarse_proj1<float, double, double>(const c64*, const c128*, const c128*, OpGeom, int, c128*,
+                                                         unsigned*, const c128*, c128*, cudaStream_t);
+template void launch_coarse_proj1<double, double, double>(const c128*, const c128*, const c128*, OpGeom, int,
+                                                          c128*, unsigned*, const c128*, c128*, cudaStream_t);
+template void launch_coarse_upd1<float, float>(const c64*, const c128*, c64*, size_t, int, cudaStream_t);
+template void launch_coarse_upd1<float, double>(const c64*, const c128*, c128*, size_t, int, cudaStream_t);
+template void launch_coarse_upd1<double, double>(const c128*, const c128*, c128*, size_t, int, cudaStream_t);
+template void launch_coarse_updn<float, float>(const c64*, const c128*, c64*, size_t, int, int, cudaStream_t);
+template void launch_coarse_updn<double, double>(const c128*, const c128*, c128*, size_t, int, int, cudaStream_t);
+
+}  // namespace hh

@@ -60,8 +60,8 @@ __device__ __forceinline__ void ip_store_partial(cplx<ACC>* acc, int p, int q, i
     }
 }
 
-template <typename TA, typename TB, typename ACC>
-__global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __restrict__ A, int lda,
+template <typename TA, typename TB, typename ACC, bool ACOL>
+__global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __restrict__ A, size_t lda,
                                                            const cplx<TB>* __restrict__ B, int ldb,
                                                            size_t N, int p, int q, c128* partial) {
     extern __shared__ __align__(16) unsigned char ipsm[];
@@ -77,10 +77,26 @@ __global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __res
     const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
         const int rows = (int)min((size_t)IP_TILE, n1 - t0);
-        for (int e = threadIdx.x; e < rows * p; e += IP_THREADS)
-            As[e] = cvt<ACC>(A[(t0 + e / p) * lda + e % p]);
-        for (int e = threadIdx.x; e < rows * q; e += IP_THREADS)
-            Bs[e] = cvt<ACC>(B[(t0 + e / q) * ldb + e % q]);
+        {
+            // 8 loads in flight per thread before the shared-memory stores
+            const int na = rows * p, nbq = rows * q;
+            for (int base = threadIdx.x; base < na + nbq; base += 8 * IP_THREADS) {
+                cplx<ACC> tmp[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = base + u * IP_THREADS;
+                    if (e < na) tmp[u] = ACOL ? cvt<ACC>(A[(size_t)(e % p) * lda + t0 + e / p])
+                                              : cvt<ACC>(A[(t0 + e / p) * lda + e % p]);
+                    else if (e < na + nbq) { const int e2 = e - na; tmp[u] = cvt<ACC>(B[(t0 + e2 / q) * ldb + e2 % q]); }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = base + u * IP_THREADS;
+                    if (e < na) As[e] = tmp[u];
+                    else if (e < na + nbq) Bs[e - na] = tmp[u];
+                }
+            }
+        }
         __syncthreads();
         ip_tile_accumulate<ACC>(As, Bs, rows, p, q, split, acc, 0, 0);
         __syncthreads();
@@ -158,10 +174,28 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
     const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(k_ip_partial<TA, TB, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_ip_partial<TA, TB, ACC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    k_ip_partial<TA, TB, ACC><<<grid, IP_THREADS, sm, s>>>(A, lda, B, ldb, N, p, q, partial);
+    k_ip_partial<TA, TB, ACC, false><<<grid, IP_THREADS, sm, s>>>(A, lda, B, ldb, N, p, q, partial);
+    note_launch();
+    return grid;
+}
+
+// partial[blk][i][j] = sum conj(A[i * N + n]) B[n * ldb + j] with A column-major (p x N).
+template <typename TA, typename TB, typename ACC>
+int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t N, int p, int q, c128* partial,
+                           int max_blocks, cudaStream_t s) {
+    int grid = (int)((N + 255) / 256);
+    if (grid > max_blocks) grid = max_blocks;
+    if (grid < 1) grid = 1;
+    const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_ip_partial<TA, TB, ACC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    k_ip_partial<TA, TB, ACC, true><<<grid, IP_THREADS, sm, s>>>(A, N, B, ldb, N, p, q, partial);
     note_launch();
     return grid;
 }
@@ -234,7 +268,6 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
     c128 acc[IP_MAXOUT];
     for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = {0.0, 0.0};
     const size_t N = (size_t)g.b * g.Sx;
-    const size_t ldr = (size_t)g.Sx * p;
     const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
     const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
@@ -243,16 +276,16 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
             const size_t pt = t0 + e / p;
             const int l = e % p;
             const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
-            const size_t t = pt * p + l;
+            const size_t t = (size_t)l * N + pt;          // column-major basis
             const c128 cv = cvt<double>(C[t]);
             c128 ax = op_diag(j, i, g) * cv;
             const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
             if (g.Sx > 1) {
-                if (i > 0) ax = ax - wj * cvt<double>(C[t - p]);
-                if (i < g.Sx - 1) ax = ax - wj * cvt<double>(C[t + p]);
+                if (i > 0) ax = ax - wj * cvt<double>(C[t - 1]);
+                if (i < g.Sx - 1) ax = ax - wj * cvt<double>(C[t + 1]);
             }
-            if (j > 0) ax = ax - wi * cvt<double>(C[t - ldr]);
-            if (j < g.b - 1) ax = ax - wi * cvt<double>(C[t + ldr]);
+            if (j > 0) ax = ax - wi * cvt<double>(C[t - g.Sx]);
+            if (j < g.b - 1) ax = ax - wi * cvt<double>(C[t + g.Sx]);
             As[e] = cv;
             Bs[e] = ax;
         }
@@ -351,14 +384,24 @@ void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scrat
 //     mapped back through the scaling and the reflectors.
 static constexpr int HE_MAX = 64;
 
+// Number of eigenvalues below x: sign changes of the leading principal minors
+// p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2} (Sturm sequence), rescaled by
+// powers of ten to stay in range; a vanishing minor counts as a sign change.  Division
+// free (FP64 division is expensive here).
 __device__ int sturm_count(const double* d, const double* e2, int m, double x) {
     int c = 0;
-    double q = d[0] - x;
-    if (q < 0.0) ++c;
+    double pm = 1.0, p = d[0] - x;
+    if (p == 0.0) p = -1e-300;
+    if (p < 0.0) ++c;
     for (int i = 1; i < m; ++i) {
-        if (q == 0.0) q = -1e-300;
-        q = (d[i] - x) - e2[i - 1] / q;
-        if (q < 0.0) ++c;
+        double pn = (d[i] - x) * p - e2[i - 1] * pm;
+        if (pn == 0.0) pn = -copysign(1e-300, p);
+        if ((pn < 0.0) != (p < 0.0)) ++c;
+        pm = p;
+        p = pn;
+        const double mx = fmax(fabs(p), fabs(pm));
+        if (mx > 1e150) { p *= 1e-150; pm *= 1e-150; }
+        else if (mx < 1e-150) { p *= 1e150; pm *= 1e150; }
     }
     return c;
 }
@@ -669,6 +712,10 @@ template int launch_ip_partial<float, double, float>(const c64*, int, const c128
                                                      int, cudaStream_t);
 template int launch_ip_partial<float, double, double>(const c64*, int, const c128*, int, size_t, int, int, c128*,
                                                       int, cudaStream_t);
+template int launch_ip_partial_colA<float, float, float>(const c64*, const c64*, int, size_t, int, int, c128*, int,
+                                                        cudaStream_t);
+template int launch_ip_partial_colA<double, double, double>(const c128*, const c128*, int, size_t, int, int, c128*,
+                                                            int, cudaStream_t);
 template int launch_galerkin_partial<float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
 template int launch_galerkin_partial<double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t);
 template void launch_qr<float>(c64* const*, int, int, int, c64**, cudaStream_t);

@@ -218,18 +218,22 @@ __global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ 
             const C sdel = delta - prev;
             if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
             prev = cdiv_(C{1, 0}, sdel);
-            xi[(size_t)i * b + m] = prev;
+            xi[(size_t)m * Sx + i] = prev;
         }
     }
 }
 
 // --------------------------------------------------------------- contractions
-// C[r][j] = sum_k op(V)[r][k] B[k][j] for r, k < b and j < J; op = V (out) or V^T (in).
-// One CTA per 32 columns; V and B staged through shared memory in k-chunks of 32.
-static constexpr int GT_N = 32, GT_K = 32, GT_THREADS = 256, GT_ROWS = 8, GT_RPT = 17;
+// C[r][j] = sum_k op(V)[r][k] B[k][j] for r, k < b and j < J = Sx * nrhs; op = V^T (in)
+// or V (out).  Column j of the node layout is (i, c) = (j / nrhs, j % nrhs); the
+// transformed vectors are stored line by line, [m][c][i], so that each scalar recursion
+// reads one contiguous line.  One CTA per GT_N columns; V and B staged through shared
+// memory in k-chunks.
+static constexpr int GT_N = 8, GT_K = 32, GT_THREADS = 256, GT_ROWS = 32, GT_RPT = 5;
 
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restrict__ tasks, int J, int which) {
+__global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restrict__ tasks, int J, int which,
+                                                         int Sx, int nrhs, int kchunk) {
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
     const int j0 = blockIdx.x * GT_N;
@@ -238,31 +242,58 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
     const cplx<T>* B = (const cplx<T>*)(which == 0 ? tk.F : tk.Fh);
     cplx<T>* C = (cplx<T>*)(which == 0 ? tk.Fh : tk.W);
     extern __shared__ __align__(16) unsigned char gsm[];
-    cplx<T>* Vs = (cplx<T>*)gsm;              // [r][k-chunk], b x GT_K
-    cplx<T>* Bs = Vs + (size_t)b * GT_K;      // [k-chunk][j], GT_K x GT_N
+    cplx<T>* Vs = (cplx<T>*)gsm;              // [r][k-chunk], b x kchunk
+    cplx<T>* Bs = Vs + (size_t)b * kchunk;    // [k-chunk][j], kchunk x GT_N
     const int jj = threadIdx.x % GT_N, rg = threadIdx.x / GT_N;
     cplx<T> acc[GT_RPT];
 #pragma unroll
     for (int t = 0; t < GT_RPT; ++t) acc[t] = {0, 0};
-    for (int k0 = 0; k0 < b; k0 += GT_K) {
-        const int kc = min(GT_K, b - k0);
-        if (TRANS) {
-            // op(V)[r][k] = V[k][r]: read rows of V (consecutive r), store transposed
-            for (int e2 = threadIdx.x; e2 < b * GT_K; e2 += GT_THREADS) {
-                const int k = e2 / b, r = e2 - k * b;
-                Vs[r * GT_K + k] = k < kc ? V[(size_t)(k0 + k) * b + r] : cplx<T>{0, 0};
+    for (int k0 = 0; k0 < b; k0 += kchunk) {
+        const int kc = min(kchunk, b - k0);
+        // stage op(V)[r][k0 + k] (b x kc) and B[k0 + k][j0 .. j0 + GT_N) with 8 loads in
+        // flight per thread
+        const int nv = b * kc;
+        for (int base = threadIdx.x; base < nv; base += 8 * GT_THREADS) {
+            cplx<T> tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e2 = base + u * GT_THREADS;
+                if (e2 < nv) {
+                    if (TRANS) { const int k = e2 / b, r = e2 - k * b; tmp[u] = V[(size_t)(k0 + k) * b + r]; }
+                    else { const int r = e2 / kc, k = e2 - r * kc; tmp[u] = V[(size_t)r * b + k0 + k]; }
+                }
             }
-        } else {
-            for (int e2 = threadIdx.x; e2 < b * GT_K; e2 += GT_THREADS) {
-                const int r = e2 / GT_K, k = e2 % GT_K;
-                Vs[e2] = k < kc ? V[(size_t)r * b + k0 + k] : cplx<T>{0, 0};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e2 = base + u * GT_THREADS;
+                if (e2 < nv) {
+                    if (TRANS) { const int k = e2 / b, r = e2 - k * b; Vs[r * kchunk + k] = tmp[u]; }
+                    else { const int r = e2 / kc, k = e2 - r * kc; Vs[r * kchunk + k] = tmp[u]; }
+                }
             }
         }
-        for (int e2 = threadIdx.x; e2 < GT_K * GT_N; e2 += GT_THREADS) {
-            const int k = e2 / GT_N, j = e2 % GT_N;
-            cplx<T> v = {0, 0};
-            if (k < kc && j0 + j < J) v = B[(size_t)(k0 + k) * J + j0 + j];
-            Bs[e2] = v;
+        const int nb2 = kc * GT_N;
+        for (int base = threadIdx.x; base < nb2; base += 8 * GT_THREADS) {
+            cplx<T> tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e2 = base + u * GT_THREADS;
+                tmp[u] = {0, 0};
+                if (e2 < nb2) {
+                    const int k = e2 / GT_N, j = e2 - k * GT_N;
+                    if (j0 + j < J) {
+                        const int jj2 = j0 + j;
+                        // which == 1 reads the line-major transformed vectors
+                        const size_t col = which == 0 ? (size_t)jj2 : (size_t)(jj2 % nrhs) * Sx + jj2 / nrhs;
+                        tmp[u] = B[(size_t)(k0 + k) * J + col];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e2 = base + u * GT_THREADS;
+                if (e2 < nb2) Bs[e2] = tmp[u];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -270,85 +301,107 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
             const int r = rg + t * GT_ROWS;
             if (r < b) {
                 cplx<T> a = acc[t];
-                for (int k = 0; k < kc; ++k) cfma(a, Vs[r * GT_K + k], Bs[k * GT_N + jj]);
+                for (int k = 0; k < kc; ++k) cfma(a, Vs[r * kchunk + k], Bs[k * GT_N + jj]);
                 acc[t] = a;
             }
         }
         __syncthreads();
     }
     if (j0 + jj < J) {
+        const int jj2 = j0 + jj;
+        const size_t col = which == 0 ? (size_t)(jj2 % nrhs) * Sx + jj2 / nrhs : (size_t)jj2;
 #pragma unroll
         for (int t = 0; t < GT_RPT; ++t) {
             const int r = rg + t * GT_ROWS;
-            if (r < b) C[(size_t)r * J + j0 + jj] = acc[t];
+            if (r < b) C[(size_t)r * J + col] = acc[t];
         }
     }
 }
 
-// Scalar recursions, in place on Fh[m][i][c].  A CTA takes rm modes of one leaf with all
-// their right-hand sides: the modes' coefficients xi[i][m] and right-hand sides along the
-// whole line are staged in shared memory by all threads (coalesced), one thread per
-// (mode, right-hand side) runs the forward/backward recursion out of shared memory, and
-// the results are written back cooperatively.  Lines too long to stage use
-// k_eig_recur_global (one thread per (mode, right-hand side) straight from memory).
+// Scalar recursions along each line, in place on Fh[m][c][i]: one warp per line (mode m,
+// right-hand side c).  Both recursions are affine, y_i = xi_i y_{i-1} + xi_i f_i and
+// x_i = xi_i x_{i+1} + y_i (with x_{n-1} = y_{n-1}), so each lane composes the maps of a
+// contiguous chunk of the line, a warp scan (shuffles) composes the chunks, and each lane
+// then replays its chunk from its entering value.  The line is staged in shared memory.
 template <typename T>
-__global__ void k_eig_recur_global(const EigTask* __restrict__ tasks, int Sx, int nrhs) {
-    const EigTask tk = tasks[blockIdx.y];
-    const int b = tk.b;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= b * nrhs) return;
-    const int m = t / nrhs, c = t % nrhs;
-    const cplx<T>* xi = (const cplx<T>*)tk.xi;
-    cplx<T>* f = (cplx<T>*)tk.Fh + (size_t)m * Sx * nrhs + c;
-    cplx<T> y = {0, 0};
-    for (int i = 0; i < Sx; ++i) {
-        y = xi[(size_t)i * b + m] * (f[(size_t)i * nrhs] + y);
-        f[(size_t)i * nrhs] = y;
-    }
-    cplx<T> x = y;
-    for (int i = Sx - 2; i >= 0; --i) {
-        x = f[(size_t)i * nrhs] + xi[(size_t)i * b + m] * x;
-        f[(size_t)i * nrhs] = x;
+__device__ __forceinline__ void affine_shfl(cplx<T>& A, cplx<T>& B, int d, bool up, cplx<T>& A2, cplx<T>& B2) {
+    if (up) {
+        A2.re = __shfl_up_sync(0xffffffffu, A.re, d); A2.im = __shfl_up_sync(0xffffffffu, A.im, d);
+        B2.re = __shfl_up_sync(0xffffffffu, B.re, d); B2.im = __shfl_up_sync(0xffffffffu, B.im, d);
+    } else {
+        A2.re = __shfl_down_sync(0xffffffffu, A.re, d); A2.im = __shfl_down_sync(0xffffffffu, A.im, d);
+        B2.re = __shfl_down_sync(0xffffffffu, B.re, d); B2.im = __shfl_down_sync(0xffffffffu, B.im, d);
     }
 }
 
-static constexpr int RM_THREADS = 256;
 template <typename T>
-__global__ void __launch_bounds__(RM_THREADS) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs,
-                                                          int rm) {
+__global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs, int wpb) {
+    using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
-    const int m0 = blockIdx.x * rm;
-    if (m0 >= b) return;
-    const int nm = min(rm, b - m0);
-    extern __shared__ __align__(16) unsigned char rsm[];
-    cplx<T>* xs = (cplx<T>*)rsm;                      // [Sx][nm]
-    cplx<T>* fs = xs + (size_t)Sx * nm;               // [nm][Sx][nrhs]
-    const cplx<T>* xi = (const cplx<T>*)tk.xi;
-    cplx<T>* fh = (cplx<T>*)tk.Fh;
-    const size_t line = (size_t)Sx * nrhs;
-    for (size_t e2 = threadIdx.x; e2 < (size_t)Sx * nm; e2 += blockDim.x) {
-        const int i = (int)(e2 / nm), mm = (int)(e2 - (size_t)i * nm);
-        xs[e2] = xi[(size_t)i * b + m0 + mm];
-    }
-    for (size_t e2 = threadIdx.x; e2 < (size_t)nm * line; e2 += blockDim.x) fs[e2] = fh[(size_t)m0 * line + e2];
-    __syncthreads();
-    for (int t = threadIdx.x; t < nm * nrhs; t += blockDim.x) {
-        const int mm = t / nrhs, c = t - (t / nrhs) * nrhs;
-        cplx<T>* f = fs + (size_t)mm * line + c;
-        cplx<T> y = {0, 0};
-        for (int i = 0; i < Sx; ++i) {
-            y = xs[(size_t)i * nm + mm] * (f[(size_t)i * nrhs] + y);
-            f[(size_t)i * nrhs] = y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int line = blockIdx.x * wpb + warp;
+    if (warp >= wpb || line >= b * nrhs) return;
+    const int m = line / nrhs;
+    extern __shared__ __align__(16) unsigned char ssm[];
+    C* as = (C*)ssm + (size_t)warp * 2 * Sx;
+    C* fs = as + Sx;
+    const C* xi = (const C*)tk.xi + (size_t)m * Sx;
+    C* fh = (C*)tk.Fh + (size_t)line * Sx;     // line = m * nrhs + c
+    for (int i0 = lane; i0 < Sx; i0 += 32 * 8) {
+        C ta[8], tf[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 32 * u;
+            if (i < Sx) { ta[u] = xi[i]; tf[u] = fh[i]; }
         }
-        cplx<T> x = y;
-        for (int i = Sx - 2; i >= 0; --i) {
-            x = f[(size_t)i * nrhs] + xs[(size_t)i * nm + mm] * x;
-            f[(size_t)i * nrhs] = x;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 32 * u;
+            if (i < Sx) { as[i] = ta[u]; fs[i] = tf[u]; }
         }
     }
-    __syncthreads();
-    for (size_t e2 = threadIdx.x; e2 < (size_t)nm * line; e2 += blockDim.x) fh[(size_t)m0 * line + e2] = fs[e2];
+    __syncwarp();
+    const int L = (Sx + 31) / 32;
+    const int s = lane * L, e = min(Sx, s + L);
+    // forward: y_i = a_i (y_{i-1} + f_i)
+    C A = {1, 0}, B = {0, 0};
+    for (int i = s; i < e; ++i) { A = as[i] * A; B = as[i] * (B + fs[i]); }
+    for (int d = 1; d < 32; d <<= 1) {
+        C A2, B2;
+        affine_shfl(A, B, d, true, A2, B2);
+        if (lane >= d) { B = A * B2 + B; A = A * A2; }
+    }
+    C y;
+    y.re = __shfl_up_sync(0xffffffffu, B.re, 1);
+    y.im = __shfl_up_sync(0xffffffffu, B.im, 1);
+    if (lane == 0) y = {0, 0};
+    for (int i = s; i < e; ++i) { y = as[i] * (fs[i] + y); fs[i] = y; }
+    __syncwarp();
+    // backward: x_i = y_i + a'_i x_{i+1}, a'_{n-1} = 0
+    A = {1, 0};
+    B = {0, 0};
+    for (int i = e - 1; i >= s; --i) {
+        const C ap = (i == Sx - 1) ? C{0, 0} : as[i];
+        B = ap * B + fs[i];
+        A = ap * A;
+    }
+    for (int d = 1; d < 32; d <<= 1) {
+        C A2, B2;
+        affine_shfl(A, B, d, false, A2, B2);
+        if (lane + d < 32) { B = A * B2 + B; A = A * A2; }
+    }
+    C x;
+    x.re = __shfl_down_sync(0xffffffffu, B.re, 1);
+    x.im = __shfl_down_sync(0xffffffffu, B.im, 1);
+    if (lane == 31) x = {0, 0};
+    for (int i = e - 1; i >= s; --i) {
+        const C ap = (i == Sx - 1) ? C{0, 0} : as[i];
+        x = fs[i] + ap * x;
+        fs[i] = x;
+    }
+    __syncwarp();
+    for (int i = lane; i < Sx; i += 32) fh[i] = fs[i];
 }
 
 template <typename T>
@@ -369,7 +422,10 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
                             cudaStream_t s) {
     const int J = Sx * nrhs;
     dim3 g1((J + GT_N - 1) / GT_N, ntasks);
-    const size_t sm = sizeof(cplx<T>) * ((size_t)b_max * GT_K + GT_K * GT_N);
+    // stage as much of V as fits in ~96 KB (all of it for complex64 bands up to 136 rows)
+    int kchunk = (int)std::min<size_t>((size_t)b_max, (96u << 10) / (sizeof(cplx<T>) * (b_max + GT_N)));
+    kchunk = std::max(8, kchunk);
+    const size_t sm = sizeof(cplx<T>) * ((size_t)b_max * kchunk + (size_t)kchunk * GT_N);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_eig_gemm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -378,24 +434,17 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
         attr = true;
     }
     if (stage == 0) {
-        k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0);
-        note_launch();
+        k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0, Sx, nrhs, kchunk);
     } else if (stage == 2) {
-        k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1);
-        note_launch();
+        k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1, Sx, nrhs, kchunk);
     } else {
-        // modes per CTA: the staged line (Sx x (1 + nrhs) per mode) within ~96 KB
-        const size_t per_mode = sizeof(cplx<T>) * (size_t)Sx * (1 + nrhs);
-        if (per_mode > (200u << 10)) {
-            dim3 gg((b_max * nrhs + 127) / 128, ntasks);
-            k_eig_recur_global<T><<<gg, 128, 0, s>>>(d_tasks, Sx, nrhs);
-        } else {
-            const int rm = (int)std::max<size_t>(1, std::min<size_t>(32, (96u << 10) / per_mode));
-            dim3 g2((b_max + rm - 1) / rm, ntasks);
-            k_eig_recur<T><<<g2, RM_THREADS, per_mode * rm, s>>>(d_tasks, Sx, nrhs, rm);
-        }
-        note_launch();
+        const size_t per_warp = 2 * sizeof(cplx<T>) * (size_t)Sx;
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp));
+        const int lines = b_max * nrhs;
+        dim3 g2((lines + wpb - 1) / wpb, ntasks);
+        k_eig_recur<T><<<g2, 32 * wpb, per_warp * wpb, s>>>(d_tasks, Sx, nrhs, wpb);
     }
+    note_launch();
 }
 
 template <typename T>

@@ -343,6 +343,7 @@ HH_COPY(float, double)
 HH_PREC(float)
 HH_PREC(double)
 template void launch_coarse_update<float, float>(const c64*, const c128*, c64*, size_t, int, int, cudaStream_t);
+
 template void launch_coarse_update<float, double>(const c64*, const c128*, c128*, size_t, int, int, cudaStream_t);
 template void launch_coarse_update<double, double>(const c128*, const c128*, c128*, size_t, int, int,
                                                    cudaStream_t);

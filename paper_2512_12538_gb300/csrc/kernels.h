@@ -48,6 +48,24 @@ template <typename TC, typename TW>
 void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t npts, int p, int nc,
                           cudaStream_t s);
 
+// ---- coarse correction with a column-major basis C[j * N + pt] (k_coarse.cu) --------
+template <typename T>
+void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size_t ldc, int coff, size_t dst0,
+                        size_t n, cudaStream_t s);
+// y = Minv C^H (v - A~ w) for one column (w may be null); counter: a zeroed device word
+template <typename TC, typename TV, typename TW>
+void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
+                         unsigned* counter, const c128* Minv, c128* y, cudaStream_t s);
+// W += C y (one column) / W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
+template <typename TC, typename TW>
+void launch_coarse_upd1(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, cudaStream_t s);
+template <typename TC, typename TW>
+void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s);
+// tiled inner products with a column-major A (p x N)
+template <typename TA, typename TB, typename ACC>
+int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t N, int p, int q, c128* partial,
+                           int max_blocks, cudaStream_t s);
+
 // Krylov bases, point-major B[n * ld + j]:
 void launch_col_load(const c128* B, int ld, int col, c128* dst, size_t n, cudaStream_t s);
 void launch_col_store_normalised(c128* B, int ld, int col, const c128* src, const c128* nrm2, size_t n,
@@ -65,7 +83,8 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
 // out[i][j] = sum_blk partial; if Minv != null, out2 = Minv (p x p) * out  (p x q).
 void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, const c128* Minv,
                       c128* out2, cudaStream_t s);
-// Galerkin partials: partial[blk][a][l] = sum_pts conj(C[pt][a]) (A~ C)[pt][l]  (p = 2r).
+// Galerkin partials: partial[blk][a][l] = sum_pts conj(C[a][pt]) (A~ C)[l][pt]  (p = 2r,
+// C column-major).
 // split_row >= 0: columns [0, p/2) of C vanish on rows >= split_row and [p/2, p) below it.
 template <typename T>
 int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
