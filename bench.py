@@ -132,34 +132,20 @@ def leaf_bands(w):
     return [min(S, ob + e) - max(0, oa - e) for oa, ob in nodes]
 
 
-def sweep_columns(w, n_solves, iters_total):
-    """Right-hand-side counts of every leaf-sweep launch: per solve 3 sketch passes per
-    level (r + p, r + p and r columns), then one column per outer iteration."""
-    m = min(w.rank + w.oversample, w.S)
-    r = min(w.rank, m)
-    return [m, m, r] * w.levels * n_solves + [1] * iters_total
-
-
-def kernel_work(w, cat, n_solves, iters_total, esz=8):
-    """Algorithmic work of all launches of one profiler category over the timed solves:
-    (amount, unit, bound, kernel name).  Per launch and leaf of b rows, Sx = S columns,
-    nc right-hand sides:
-      transforms f^ = V^T f, x = V x^: 8 b^2 Sx nc flops (complex multiply-add = 8 flops);
-      recursions: read xi (Sx b), read and write f^ (2 b Sx nc) elements;
-      FP64 residual: 48 bytes per node (read u, read b, write r)."""
-    bands = leaf_bands(w)
-    S = w.S
-    cols = sweep_columns(w, n_solves, iters_total)
-    if cat in ("sweep_in", "sweep_out"):
-        fl = sum(8.0 * b * b * S * nc for nc in cols for b in bands)
-        name = "k_eig_gemm<float," + ("1> (f^ = V^T f)" if cat == "sweep_in" else "0> (x = V x^)")
-        return fl, "flop", "alu", name
-    if cat == "sweep_recur":
-        by = sum(esz * S * b * (1.0 + 2.0 * nc) for nc in cols for b in bands)
-        return by, "byte", "hbm", "k_eig_recur<float> (scalar Schur recursions along the line)"
-    if cat == "residual":
-        return 48.0 * S * S * (iters_total + n_solves), "byte", "hbm", "k_apply<double> (FP64 residual b - A u)"
-    return None, None, "latency", cat
+# Bound of each profiler category (the library reports each launch's algorithmic bytes
+# and flops; see hh_profile_read in include/hh.h).
+CATEGORY_BOUND = {
+    "factor": ("latency", "k_eig_factor (eigenpairs of the column pencil + scalar Schur recursions)"),
+    "sweep_in": ("alu", "k_eig_gemm<float,1> (f^ = V^T f, complex64 CUDA-core contraction)"),
+    "sweep_recur": ("hbm", "k_eig_recur<float> (scalar Schur recursions, warp scans)"),
+    "sweep_out": ("alu", "k_eig_gemm<float,0> (x = V x^)"),
+    "residual": ("hbm", "k_apply<double> (FP64 residual b - A u)"),
+    "coarse_project": ("hbm", "k_coarse_proj1 (fused residual + C^H r + A_c^-1, column-major C)"),
+    "galerkin": ("alu64", "k_galerkin_partial (A_c = C^H A~ C, FP64)"),
+    "qr": ("latency", "k_qr (sketch orthonormalisation)"),
+    "svd": ("latency", "k_heig (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
+}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure is available)
 
 
 # --------------------------------------------------------------------- our arm
@@ -193,7 +179,7 @@ def run_ours(args, rank, world):
         h, _ = hh.hh_setup(params(prec), stream)
         st = hh.hh_solve(h, fd, gd, u, stream)
         e1.record(stream)
-        prof = hh.hh_profile_read(h) if profile else None
+        prof = hh.hh_profile_read(h, work=True) if profile else None
         hh.hh_destroy(h)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), st, prof
@@ -221,9 +207,9 @@ def run_ours(args, rank, world):
             ms, st, prof = one("mixed", profile=True)
             step_ms.append(ms)
             iters.append(st.iters)
-            for k, (pms, cnt) in prof.items():
-                a, b = prof_total.get(k, (0.0, 0))
-                prof_total[k] = (a + pms, b + cnt)
+            for k, vals in prof.items():
+                old = prof_total.get(k, (0.0, 0, 0.0, 0.0))
+                prof_total[k] = tuple(x + y for x, y in zip(old, vals))
         barrier()
         wall = time.perf_counter() - t0
     hh.hh_profile_enable(None, False)
@@ -280,7 +266,8 @@ def run_ours(args, rank, world):
                       "ms_per_step": statistics.mean(fp64_ms)},
         "mixed_over_fp64": (value / world) / (len(fp64_ms) / (sum(fp64_ms) / 1e3)),
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
-        "kernel_ms": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof_total.items()},
+        "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
+                    for k, v in prof_total.items() if v[1] > 0},
         "wall_s_timed": wall,
     }
     if rank == 0:
@@ -297,30 +284,40 @@ def pct(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
+def rate(cat, ms, by, fl, pk, pk_kind):
+    """Achieved rate of one category against its peak."""
+    bound, kname = CATEGORY_BOUND.get(cat, ("latency", cat))
+    out = {"kernel": kname, "category": cat, "bound": bound}
+    if bound == "hbm" and by > 0:
+        a = by / (ms / 1e3) / 1e9
+        out.update({"achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": a / pk["hbm_gbs"],
+                    "peak_kind": f"{pk_kind} hbm_gbs"})
+    elif bound == "alu" and fl > 0:
+        peak = SM_COUNT * FP32_LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        a = fl / (ms / 1e3) / 1e12
+        out.update({"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                    "peak_kind": "FP32 FFMA derived: 152 SMs x 128 lanes x 2 flops x max SM clock"})
+    elif bound == "alu64" and fl > 0:
+        a = fl / (ms / 1e3) / 1e12
+        out.update({"achieved": a, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_NOMINAL_TFLOPS,
+                    "peak_kind": "FP64 nominal"})
+    else:
+        out.update({"achieved": None, "peak": None, "unit": None, "frac": None})
+    return out
+
+
 def roofline(w, prof, iters, pk, pk_kind):
-    """Dominant kernel (largest total device time in the timed solves, measured with CUDA
+    """Dominant kernel category (largest total device time over the timed solves, CUDA
     events on the launching stream) with its algorithmic rate against its peak."""
     if not prof:
         return None
     tot_ms = sum(v[0] for v in prof.values())
-    name = max(prof, key=lambda k: prof[k][0])
-    ms, launches = prof[name]
-    amount, unit, bound, kname = kernel_work(w, name, len(iters), sum(iters))
-    out = {"kernel": kname, "category": name, "bound": bound, "launches": launches,
-           "avg_launch_ms": ms / max(launches, 1), "share_of_profiled_ms": ms / tot_ms, "traffic": None}
-    if amount is None:
-        out.update({"achieved": None, "peak": None, "unit": None, "frac": None})
-        return out
-    if unit == "byte":
-        achieved = amount / (ms / 1e3) / 1e9
-        peak = pk["hbm_gbs"]
-        out.update({"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_kind": f"{pk_kind} hbm_gbs"})
-    else:
-        achieved = amount / (ms / 1e3) / 1e12
-        peak = SM_COUNT * FP32_LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        out.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock (derived)"})
+    cat = max(prof, key=lambda k: prof[k][0])
+    ms, launches, by, fl = prof[cat]
+    out = rate(cat, ms, by, fl, pk, pk_kind)
+    out.update({"launches": launches, "avg_launch_ms": ms / max(launches, 1), "share_of_profiled_ms": ms / tot_ms,
+                "traffic": None, "alg_bytes_per_launch": by / max(launches, 1),
+                "alg_flops_per_launch": fl / max(launches, 1)})
     return out
 
 

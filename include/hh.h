@@ -197,7 +197,12 @@ hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
 /* h != NULL: (re)start profiling of that handle, clearing its totals; h == NULL: set
  * whether handles created afterwards profile from their first set-up kernel. */
 hh_status hh_profile_enable(hh_handle* h, int enable);
-hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches);
+/* total_ms: summed event time; launches: timed launches; alg_bytes / alg_flops: the
+ * algorithmic memory traffic and floating-point work of those launches (formulas in the
+ * library: e.g. a band transform of b rows, S_x columns and nc right-hand sides counts
+ * 8 b^2 S_x nc flops and (b^2 + 2 b S_x nc) elements).  Any output may be NULL. */
+hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches,
+                          double* alg_bytes, double* alg_flops);
 /* Number of CUDA kernels this library has launched in the calling process. */
 unsigned long long hh_launch_count(void);
 

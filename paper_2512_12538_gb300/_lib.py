@@ -68,7 +68,7 @@ def _load():
         "hh_precondition": (i, [vp, vp, vp, vp]),
         "hh_sketch_samples": (i, [vp, i, vp, vp]),
         "hh_profile_enable": (i, [vp, i]),
-        "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong)]),
+        "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
         "hh_launch_count": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
@@ -241,14 +241,18 @@ def hh_profile_enable(h, enable=True) -> None:
     _check(LIB.hh_profile_enable(h, int(bool(enable))), "hh_profile_enable")
 
 
-def hh_profile_read(h) -> dict:
-    """{category: (total_ms, launches)} for every profiler category."""
+def hh_profile_read(h, work=False) -> dict:
+    """{category: (total_ms, launches)} for every profiler category; with work=True
+    (total_ms, launches, algorithmic_bytes, algorithmic_flops)."""
     out = {}
     for i, name in enumerate(PROFILE_CATEGORIES):
         ms = ctypes.c_double()
         n = ctypes.c_longlong()
-        _check(LIB.hh_profile_read(h, i, ctypes.byref(ms), ctypes.byref(n)), "hh_profile_read")
-        out[name] = (ms.value, n.value)
+        by = ctypes.c_double()
+        fl = ctypes.c_double()
+        _check(LIB.hh_profile_read(h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by), ctypes.byref(fl)),
+               "hh_profile_read")
+        out[name] = (ms.value, n.value, by.value, fl.value) if work else (ms.value, n.value)
     return out
 
 

@@ -166,12 +166,13 @@ struct SolverBase {
     cudaStream_t stream = nullptr;
     double t_setup_ms = 0.0, t_solve_ms = 0.0;
     // event profiler: pairs recorded around the kernels of one category
-    struct EvPair { cudaEvent_t a, b; int cat; };
+    struct EvPair { cudaEvent_t a, b; int cat; double bytes, flops; };
     bool prof_on = false;
     std::vector<EvPair> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[PC_NCAT] = {0};
     long long prof_n[PC_NCAT] = {0};
+    double prof_bytes[PC_NCAT] = {0}, prof_flops[PC_NCAT] = {0};   // algorithmic work
     cudaEvent_t prof_ev() {
         if (!prof_pool.empty()) { cudaEvent_t e = prof_pool.back(); prof_pool.pop_back(); return e; }
         cudaEvent_t e;
@@ -186,9 +187,10 @@ struct SolverBase {
         if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
         else cudaEventRecord(e, stream);
     }
-    void pbeg(int cat) {
+    // bytes / flops: algorithmic work of the kernels between pbeg and pend
+    void pbeg(int cat, double bytes = 0.0, double flops = 0.0) {
         if (!prof_on) return;
-        EvPair p{prof_ev(), nullptr, cat};
+        EvPair p{prof_ev(), nullptr, cat, bytes, flops};
         ev_record(p.a);
         prof_pending.push_back(p);
     }
@@ -221,7 +223,7 @@ struct SolverBase {
     }
     void prof_reset(bool on) {
         prof_on = on;
-        for (int i = 0; i < PC_NCAT; ++i) { prof_ms[i] = 0; prof_n[i] = 0; }
+        for (int i = 0; i < PC_NCAT; ++i) { prof_ms[i] = 0; prof_n[i] = 0; prof_bytes[i] = 0; prof_flops[i] = 0; }
     }
     virtual ~SolverBase() {
         for (auto& p : prof_pending) { prof_pool.push_back(p.a); if (p.b) prof_pool.push_back(p.b); }
@@ -472,7 +474,15 @@ struct Solver final : SolverBase {
         if (eig) {
             if (!own && view_nc != nc) { upload_eig_view_tasks(nc); view_nc = nc; }
             for (int stg = 0; stg < 3; ++stg) {
-                pbeg(PC_TIN + stg);
+                // per leaf b x Sx x nc: transforms 8 b^2 Sx nc flops and (b^2 + 2 b Sx nc)
+                // elements; recursions read xi (Sx b) and read/write the lines (2 b Sx nc)
+                double by = 0.0, fl = 0.0;
+                for (int id : lev[L]) {
+                    const double b = nodes[id].b(), sx = Sx;
+                    if (stg == 1) by += sizeof(CT) * (b * sx + 2.0 * b * sx * nc);
+                    else { fl += 8.0 * b * b * sx * nc; by += sizeof(CT) * (b * b + 2.0 * b * sx * nc); }
+                }
+                pbeg(PC_TIN + stg, by, fl);
                 launch_eig_sweep_stage<T>(stg, own ? d_etasks_own : d_etasks_view, nl, b_max, Sx, nc, stream);
                 pend();
             }
@@ -520,7 +530,8 @@ struct Solver final : SolverBase {
     // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
     void coarse_correct(int p, const CT* vin, int nc) {
         if (nc == 1) {
-            pbeg(PC_COARSE);
+            // reads C (2r x N), v and w (N each)
+            pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + 2.0) * sizeof(CT), 8.0 * 2 * r * pts(p));
             launch_coarse_proj1<T, T, T>(C[p], vin, W[p], geom(p), 2 * r, partial, dcounter, Ainv[p], ycoef[p],
                                          stream);
             pend();
@@ -528,7 +539,7 @@ struct Solver final : SolverBase {
             return;
         }
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
-        pbeg(PC_COARSE);
+        pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + nc) * sizeof(CT), 8.0 * 2 * r * nc * pts(p));
         const int nb = launch_ip_partial_colA<T, T, T>(C[p], R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
                                                        stream);
         pend();
@@ -598,7 +609,7 @@ struct Solver final : SolverBase {
                                       stream);
             }
             // A_c = C_p^H A~_p C_p, then its inverse
-            pbeg(PC_GALERKIN);
+            pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT), 8.0 * 2.0 * r * r * pts(p));
             const int split = nodes[nodes[p].child[1]].own_a - nodes[p].ra;
             const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS, stream);
             pend();
@@ -662,7 +673,7 @@ struct Solver final : SolverBase {
             launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), ut + row_off(0, cn.own_a, 1),
                                    (size_t)(cn.own_b - cn.own_a) * Sx, true, false, stream);
         }
-        pbeg(PC_COARSE);
+        pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 2.0 * sizeof(c128)), 8.0 * 2 * r * N);
         launch_coarse_proj1<T, double, double>(C[0], rhs, ut, geom(0), 2 * r, partial, dcounter, Ainv[0], ycoef[0],
                                                stream);
         pend();
@@ -725,7 +736,7 @@ struct Solver final : SolverBase {
     // ||b - A u||^2 into h_norm[0] (synchronises); ||b||^2 must be in dnorm[2].
     bool true_residual(c128* dst, hh_status& st) {
         int nb = 0;
-        pbeg(PC_SPMV);
+        pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
         launch_apply<double, double, double>(u, bvec, dst, geom(0), 1, 1.0, npart, &nb, stream);
         pend();
         launch_sum(npart, nb, dnorm, stream);
@@ -1153,10 +1164,13 @@ hh_status hh_profile_enable(hh_handle* h, int enable) {
     h->s->prof_reset(enable != 0);
     return HH_OK;
 }
-hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches) {
+hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches,
+                          double* alg_bytes, double* alg_flops) {
     if (!h || category < 0 || category >= hh::PC_NCAT) return HH_EINVAL;
     if (total_ms) *total_ms = h->s->prof_ms[category];
     if (launches) *launches = h->s->prof_n[category];
+    if (alg_bytes) *alg_bytes = h->s->prof_bytes[category];
+    if (alg_flops) *alg_flops = h->s->prof_flops[category];
     return HH_OK;
 }
 unsigned long long hh_launch_count(void) { return hh::g_launches.load(); }

@@ -59,6 +59,8 @@ def test_profiler_and_launch_counter(hh, case):
         u = torch.empty_like(fd)
         st = hh.hh_solve(h, fd, gd, u)
         prof = hh.hh_profile_read(h)
+        work = hh.hh_profile_read(h, work=True)
+        assert work["sweep_recur"][2] > 0 and work["sweep_in"][3] > 0 and work["coarse_project"][2] > 0
         assert prof["factor"][1] == 1 and prof["factor"][0] > 0
         for stage in ("sweep_in", "sweep_recur", "sweep_out"):
             assert prof[stage][1] == 6 + st.iters        # 3 sketch passes per level + 1 per iteration
