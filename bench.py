@@ -144,6 +144,7 @@ CATEGORY_BOUND = {
     "galerkin": ("alu64", "k_galerkin_partial (A_c = C^H A~ C, FP64)"),
     "qr": ("latency", "k_qr (sketch orthonormalisation)"),
     "svd": ("latency", "k_heig (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
+    "leaf_sweep": ("alu", "k_eig_sweep_fused<float> (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
 }
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure is available)
 

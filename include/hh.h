@@ -192,7 +192,8 @@ hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
  * 2 leaf sweep recursions along the line (scalar recursions, or the block substitution
  * of the explicit-inverse path), 3 leaf sweep transform back, 4 FP64 global residual,
  * 5 coarse projection C^H r, 6 Galerkin product, 7 sketch orthonormalisation, 8 sketch
- * SVD.
+ * SVD, 9 leaf sweep of a single right-hand side on the eigenbasis path (categories 1-3
+ * fused into one launch; 1-3 then count the multi-vector sweeps of the set-up).
  * -------------------------------------------------------------------------------- */
 /* h != NULL: (re)start profiling of that handle, clearing its totals; h == NULL: set
  * whether handles created afterwards profile from their first set-up kernel. */

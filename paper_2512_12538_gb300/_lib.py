@@ -234,7 +234,7 @@ def hh_sketch_samples(h, child, out, stream=None) -> None:
 
 
 PROFILE_CATEGORIES = ["factor", "sweep_in", "sweep_recur", "sweep_out", "residual", "coarse_project",
-                      "galerkin", "qr", "svd"]
+                      "galerkin", "qr", "svd", "leaf_sweep"]
 
 
 def hh_profile_enable(h, enable=True) -> None:

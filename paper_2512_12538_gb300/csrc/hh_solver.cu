@@ -45,6 +45,7 @@ enum ProfCat {
     PC_GALERKIN,     // Galerkin product
     PC_QR,           // sketch orthonormalisation
     PC_JACOBI,       // sketch SVD
+    PC_SWEEP,        // leaf sweep for one right-hand side, all three stages in one launch
     PC_NCAT
 };
 
@@ -200,22 +201,21 @@ struct SolverBase {
         ev_record(prof_pending.back().b);
     }
     // event pairs owned by captured graphs: read after every synchronised replay
-    void prof_read_pairs(const std::vector<EvPair>& v) {
-        for (auto& p : v) {
-            float ms = 0.f;
-            if (p.b && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                prof_ms[p.cat] += ms;
-                prof_n[p.cat] += 1;
-            }
+    void prof_account(const EvPair& p) {
+        float ms = 0.f;
+        if (p.b && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            prof_ms[p.cat] += ms;
+            prof_n[p.cat] += 1;
+            prof_bytes[p.cat] += p.bytes;
+            prof_flops[p.cat] += p.flops;
         }
+    }
+    void prof_read_pairs(const std::vector<EvPair>& v) {
+        for (auto& p : v) prof_account(p);
     }
     void prof_collect() {   // call after synchronising the stream
         for (auto& p : prof_pending) {
-            float ms = 0.f;
-            if (p.b && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                prof_ms[p.cat] += ms;
-                prof_n[p.cat] += 1;
-            }
+            prof_account(p);
             prof_pool.push_back(p.a);
             if (p.b) prof_pool.push_back(p.b);
         }
@@ -268,6 +268,7 @@ struct Solver final : SolverBase {
     LeafTask *d_tasks_view = nullptr, *d_tasks_own = nullptr, *d_task_one = nullptr;
     // eigenbasis leaf path
     bool eig = false;
+    bool eig_fused = false;     // one-launch sweep for single right-hand sides
     std::vector<CT*> EV, EXI, EFh;
     std::vector<c128*> ELAM, EWK;
     EigTask *d_etasks_view = nullptr, *d_etasks_own = nullptr, *d_etask_one = nullptr;
@@ -473,6 +474,21 @@ struct Solver final : SolverBase {
         const int nl = (int)lev[L].size();
         if (eig) {
             if (!own && view_nc != nc) { upload_eig_view_tasks(nc); view_nc = nc; }
+            const EigTask* tasks = own ? d_etasks_own : d_etasks_view;
+            if (nc == 1 && eig_fused) {
+                // both transforms (16 b^2 Sx flops) and the recursions; V, f, xi read and
+                // x written once: b^2 + 3 b Sx elements
+                double by = 0.0, fl = 0.0;
+                for (int id : lev[L]) {
+                    const double b = nodes[id].b(), sx = Sx;
+                    fl += 16.0 * b * b * sx;
+                    by += sizeof(CT) * (b * b + 3.0 * b * sx);
+                }
+                pbeg(PC_SWEEP, by, fl);
+                launch_eig_sweep_fused<T>(tasks, nl, b_max, Sx, stream);
+                pend();
+                return;
+            }
             for (int stg = 0; stg < 3; ++stg) {
                 // per leaf b x Sx x nc: transforms 8 b^2 Sx nc flops and (b^2 + 2 b Sx nc)
                 // elements; recursions read xi (Sx b) and read/write the lines (2 b Sx nc)
@@ -483,7 +499,7 @@ struct Solver final : SolverBase {
                     else { fl += 8.0 * b * b * sx * nc; by += sizeof(CT) * (b * b + 2.0 * b * sx * nc); }
                 }
                 pbeg(PC_TIN + stg, by, fl);
-                launch_eig_sweep_stage<T>(stg, own ? d_etasks_own : d_etasks_view, nl, b_max, Sx, nc, stream);
+                launch_eig_sweep_stage<T>(stg, tasks, nl, b_max, Sx, nc, stream);
                 pend();
             }
             return;
@@ -619,6 +635,7 @@ struct Solver final : SolverBase {
     }
 
     hh_status setup() override {
+        eig_fused = eig && eig_sweep_fused_ready<T>(b_max, Sx);
         zero(derr, sizeof(int) * 4);
         zero(dcounter, sizeof(unsigned) * 4);
         for (int id = 1; id < nn; ++id) zero(Vs[id], sizeof(CT) * pts(id) * nmax);

@@ -32,114 +32,106 @@ void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size
     note_launch();
 }
 
-// Warp reduce-scatter of 32 values per lane: afterwards lane l holds the warp sum of value
-// l.  Five butterfly stages; at the stage of width k each lane keeps the half of its
-// values selected by bit k of its lane index and adds its partner's copy of that half
-// (31 shuffles per component instead of 32 x 5 for separate reductions).
-template <typename T>
-__device__ __forceinline__ cplx<T> warp_reduce_scatter32(cplx<T> (&v)[32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
-        const bool up = (lane & k) != 0;
-#pragma unroll
-        for (int i = 0; i < k; ++i) {
-            const cplx<T> lo = v[i], hi = v[i + k];
-            const cplx<T> send = up ? lo : hi;
-            const cplx<T> keep = up ? hi : lo;
-            cplx<T> got;
-            got.re = __shfl_xor_sync(0xffffffffu, send.re, k);
-            got.im = __shfl_xor_sync(0xffffffffu, send.im, k);
-            v[i] = keep + got;
-        }
-    }
-    return v[0];
-}
-
-// One column.  Every thread forms r_pt = v_pt - (A~ w)_pt (w may be null: r = v) in the
-// precision of v and w, accumulates conj(C[j][pt]) r_pt for a chunk of PC columns in ACC,
-// and the block writes its partial sums.  The last block to finish (ticket counter) adds
-// the partials in block order (FP64), multiplies by the FP64 inverse Galerkin matrix and
-// writes y = A_c^{-1} C^H r, then resets the counter.
-template <typename TC, typename TV, typename TW, typename ACC, int PC>
+// One column.  A block takes 64 consecutive points per step; its four groups of 64
+// threads each accumulate a quarter of the p columns (coalesced reads of C along the
+// points), every thread forming r_pt = v_pt - (A~ w)_pt (w may be null: r = v) in the
+// precision of v and w.  Per-block partial sums go to `partial`; the last block to
+// finish (ticket counter) adds them in block order (FP64), multiplies by the FP64
+// inverse Galerkin matrix, writes y = A_c^{-1} C^H r and resets the counter.
+template <typename TC, typename TV, typename TW, typename ACC>
 __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict__ C, const cplx<TV>* __restrict__ v,
                                                       const cplx<TW>* __restrict__ w, OpGeom g, int p,
                                                       c128* __restrict__ partial, unsigned* counter,
                                                       const c128* __restrict__ Minv, c128* __restrict__ y) {
     using CA = cplx<ACC>;
-    using CW = cplx<decltype(TV() + TW())>;
-    __shared__ CA red[8][PC];
+    using R = decltype(TV() + TW());
+    __shared__ CA red[8][16];
     __shared__ unsigned ticket;
     __shared__ c128 s_sum[64];
+    __shared__ c128 s_m[64 * 64];
     const size_t N = (size_t)g.b * g.Sx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (int j0 = 0; j0 < p; j0 += PC) {
-        const int pc = min(PC, p - j0);
-        CA acc[PC];
+    const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;        // point in tile, column group
+    const int per = (p + 3) / 4, ja = jg * per, jb = min(p, ja + per);
+    CA acc[16];
 #pragma unroll
-        for (int j = 0; j < PC; ++j) acc[j] = {0, 0};
-        for (size_t pt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; pt < N; pt += stride) {
-            CW rv = cvt<decltype(TV() + TW())>(v[pt]);
-            if (w) {
-                const int i = (int)(pt % g.Sx), jr = (int)(pt / g.Sx);
-                using R = decltype(TV() + TW());
-                const c128 d = op_diag(jr, i, g);
-                const cplx<R> dg = {(R)d.re, (R)d.im};
-                cplx<R> ax = dg * cvt<R>(w[pt]);
-                const R wj = (R)wrow(jr, g.b), wi = (R)wcol(i, g.Sx);
-                if (g.Sx > 1) {
-                    if (i > 0) ax = ax - wj * cvt<R>(w[pt - 1]);
-                    if (i < g.Sx - 1) ax = ax - wj * cvt<R>(w[pt + 1]);
-                }
-                if (jr > 0) ax = ax - wi * cvt<R>(w[pt - g.Sx]);
-                if (jr < g.b - 1) ax = ax - wi * cvt<R>(w[pt + g.Sx]);
-                rv = rv - ax;
+    for (int j = 0; j < 16; ++j) acc[j] = {0, 0};
+    for (size_t base = (size_t)blockIdx.x * 64; base < N; base += (size_t)gridDim.x * 64) {
+        const size_t pt = base + q;
+        if (pt >= N) continue;
+        cplx<TC> cv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) cv[u] = (ja + u < jb) ? C[(size_t)(ja + u) * N + pt] : cplx<TC>{0, 0};
+        cplx<R> rv = cvt<R>(v[pt]);
+        if (w) {
+            const int i = (int)(pt % g.Sx), jr = (int)(pt / g.Sx);
+            const c128 d = op_diag(jr, i, g);
+            cplx<R> ax = cplx<R>{(R)d.re, (R)d.im} * cvt<R>(w[pt]);
+            const R wj = (R)wrow(jr, g.b), wi = (R)wcol(i, g.Sx);
+            if (g.Sx > 1) {
+                if (i > 0) ax = ax - wj * cvt<R>(w[pt - 1]);
+                if (i < g.Sx - 1) ax = ax - wj * cvt<R>(w[pt + 1]);
             }
-            const CA ra = cvt<ACC>(rv);
-#pragma unroll
-            for (int jb = 0; jb < PC; jb += 16) {
-                cplx<TC> cv[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    cv[u] = (jb + u < pc) ? C[(size_t)(j0 + jb + u) * N + pt] : cplx<TC>{0, 0};
-                asm volatile("" ::: "memory");
-#pragma unroll
-                for (int u = 0; u < 16; ++u) cfma_cj(acc[jb + u], cvt<ACC>(cv[u]), ra);
-            }
+            if (jr > 0) ax = ax - wi * cvt<R>(w[pt - g.Sx]);
+            if (jr < g.b - 1) ax = ax - wi * cvt<R>(w[pt + g.Sx]);
+            rv = rv - ax;
         }
-        if (PC == 32) {
-            const CA t = warp_reduce_scatter32(*reinterpret_cast<CA(*)[32]>(&acc[0]));
-            red[warp][lane] = t;
-        } else {
+        const CA ra = cvt<ACC>(rv);
 #pragma unroll
-            for (int j = 0; j < PC; ++j) {
-                const CA t = warp_sum(acc[j]);
-                if (lane == 0) red[warp][j] = t;
-            }
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < pc; j += blockDim.x) {
-            c128 t = {0.0, 0.0};
-            for (int q = 0; q < 8; ++q) t = t + cvt<double>(red[q][j]);
-            partial[(size_t)blockIdx.x * p + j0 + j] = t;
-        }
-        __syncthreads();
+        for (int u = 0; u < 16; ++u) cfma_cj(acc[u], cvt<ACC>(cv[u]), ra);
+    }
+    // both warps of a column group hold the group's columns: reduce over lanes, then over
+    // the two warps in shared memory
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const CA t = warp_sum(acc[u]);
+        if (lane == 0) red[warp][u] = t;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < p; t += blockDim.x) {
+        const int grp = t / per, u = t - grp * per;
+        const CA s = red[2 * grp][u] + red[2 * grp + 1][u];
+        partial[(size_t)blockIdx.x * p + t] = cvt<double>(s);
     }
     __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
     __syncthreads();
     if (ticket != gridDim.x - 1) return;
     __threadfence();
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        c128 t = {0.0, 0.0};
-        for (unsigned b = 0; b < gridDim.x; ++b) t = t + ((volatile c128*)partial)[(size_t)b * p + j];
-        s_sum[j] = t;
+    // last block: stage Minv, then 8 threads per output add the blocks' partials (fixed
+    // order within each thread, then a fixed shuffle tree), loads bypassing L1 (__ldcg)
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) s_m[t] = Minv[t];
+    // the loop bound is warp-uniform (every lane of a warp reaches the shuffles)
+    const int sub = threadIdx.x & 7;
+    for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
+        const int j = j0 + (threadIdx.x >> 3);
+        const bool ok = j < p;
+        c128 t0 = {0.0, 0.0}, t1 = {0.0, 0.0};
+        unsigned b = sub;
+        if (ok) {
+            for (; b + 8 < gridDim.x; b += 16) {
+                const double2 a0 = __ldcg((const double2*)(partial + (size_t)b * p + j));
+                const double2 a1 = __ldcg((const double2*)(partial + (size_t)(b + 8) * p + j));
+                t0 = t0 + c128{a0.x, a0.y};
+                t1 = t1 + c128{a1.x, a1.y};
+            }
+            if (b < gridDim.x) {
+                const double2 a0 = __ldcg((const double2*)(partial + (size_t)b * p + j));
+                t0 = t0 + c128{a0.x, a0.y};
+            }
+        }
+        c128 t = t0 + t1;
+        for (int o = 4; o > 0; o >>= 1) {
+            t.re += __shfl_xor_sync(0xffffffffu, t.re, o);
+            t.im += __shfl_xor_sync(0xffffffffu, t.im, o);
+        }
+        if (ok && sub == 0) s_sum[j] = t;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         c128 t = {0.0, 0.0};
-        for (int k = 0; k < p; ++k) cfma(t, Minv[j * p + k], s_sum[k]);
+        for (int k = 0; k < p; ++k) cfma(t, s_m[j * p + k], s_sum[k]);
         y[j] = t;
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -149,10 +141,8 @@ template <typename TC, typename TV, typename TW>
 void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
                          unsigned* counter, const c128* Minv, c128* y, cudaStream_t s) {
     const size_t N = (size_t)g.b * g.Sx;
-    const int grid = blocks_for(N, 256 * 2, 152 * 2);
-    // accumulate in the basis precision; 16 FP64 or 32 FP32 columns per pass
-    if (sizeof(TC) == 8) k_coarse_proj1<TC, TV, TW, TC, 16><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
-    else k_coarse_proj1<TC, TV, TW, TC, 32><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
+    const int grid = blocks_for(N, 64, 152 * 4);
+    k_coarse_proj1<TC, TV, TW, TC><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
     note_launch();
 }
 

@@ -236,6 +236,16 @@ __global__ void __launch_bounds__(1024) k_ip_reduce(const c128* __restrict__ par
         out2[o] = t;
     }
 }
+// y = M x for a p x p matrix and a p x q block (one thread per output)
+__global__ void k_small_matmul(const c128* __restrict__ M, const c128* __restrict__ x, int p, int q, c128* y) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= p * q) return;
+    const int i = o / q, j = o % q;
+    c128 t = {0.0, 0.0};
+    for (int k = 0; k < p; ++k) cfma(t, M[i * p + k], x[k * q + j]);
+    y[o] = t;
+}
+
 void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, const c128* Minv, c128* out2,
                       cudaStream_t s) {
     static bool attr = false;
@@ -244,6 +254,19 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
         attr = true;
     }
     const int nout = p * q;
+    if (Minv && nout > 64) {
+        // many outputs: reduce over blocks with the whole GPU, then apply Minv separately
+        // the sums go just past the partials (the scratch holds nblk * nout + nout values)
+        c128* sums = const_cast<c128*>(partial) + (size_t)nblk * nout;
+        int grid = (nout + 7) / 8;
+        if (grid > 304) grid = 304;
+        k_ip_reduce<<<grid, 256, 0, s>>>(partial, nblk, p, q, sums, nullptr, nullptr);
+        note_launch();
+        k_small_matmul<<<(nout + 255) / 256, 256, 0, s>>>(Minv, sums, p, q, out2);
+        note_launch();
+        if (out) cudaMemcpyAsync(out, sums, sizeof(c128) * nout, cudaMemcpyDeviceToDevice, s);
+        return;
+    }
     if (Minv) {
         k_ip_reduce<<<1, 1024, sizeof(c128) * (nout + (size_t)p * p), s>>>(partial, nblk, p, q, out, Minv, out2);
     } else {
@@ -447,12 +470,13 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
         __syncthreads();
         const double tk = s_tau;
         const c128* v = Vr + k * m;
-        // w = tau A' v
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        // w = tau A' v: a warp per row, lanes across the row
+        for (int i = warp; i < n; i += (blockDim.x >> 5)) {
             c128 acc = {0.0, 0.0};
             const c128* row = A + (k + 1 + i) * m + (k + 1);
-            for (int j = 0; j < n; ++j) cfma(acc, row[j], v[j]);
-            w[i] = tk * acc;
+            for (int j = lane; j < n; j += 32) cfma(acc, row[j], v[j]);
+            acc = warp_sum(acc);
+            if (lane == 0) w[i] = tk * acc;
         }
         __syncthreads();
         if (warp == 0) {
@@ -503,18 +527,38 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
     lo0 -= 1e-12 * span;
     hi0 += 1e-12 * span;
     double* lam = lamp[blockIdx.x];
-    for (int kk = threadIdx.x; kk < m; kk += blockDim.x) {
-        const int j = m - 1 - kk;            // ascending index of the kk-th largest eigenvalue
-        double lo = lo0, hi = hi0;
-        for (int it = 0; it < 200 && hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)); ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (sturm_count(d, e2, m, mid) <= j) lo = mid;
-            else hi = mid;
+    // multisection: 8 threads per eigenvalue probe 8 interior points of its bracket per
+    // round (Sturm counts), shrinking the bracket by a factor 9 per round
+    {
+        const int sub = threadIdx.x & 7;
+        for (int kk0 = 0; kk0 < m; kk0 += (int)(blockDim.x >> 3)) {
+            const int kk = kk0 + (threadIdx.x >> 3);
+            const bool act = kk < m;
+            const int j = m - 1 - (act ? kk : 0);   // ascending index of the kk-th largest
+            double lo = lo0, hi = hi0;
+            for (int it = 0; it < 40; ++it) {
+                const double x = lo + (hi - lo) * (sub + 1) / 9.0;
+                const bool above = act && sturm_count(d, e2, m, x) > j;   // eigenvalue below x
+                const unsigned mask = __ballot_sync(0xffffffffu, above);
+                const unsigned mine = (mask >> ((threadIdx.x & 31) & ~7)) & 0xffu;
+                // first probe with count > j bounds from above; the one before from below
+                const int first = mine ? __ffs(mine) - 1 : 8;
+                const double nlo = lo + (hi - lo) * first / 9.0;
+                const double nhi = first < 8 ? lo + (hi - lo) * (first + 1) / 9.0 : hi;
+                lo = nlo;
+                hi = nhi;
+                // every lane takes part in the ballot: leave together
+                // absolute accuracy eps * ||G|| is all the selection and the singular
+                // values need (the Gram matrix squares the sketch's dynamic range)
+                const bool done = !act || hi - lo <= 2e-16 * span;
+                if (__all_sync(0xffffffffu, done)) break;
+            }
+            if (act && sub == 0) lam[kk] = 0.5 * (lo + hi);
         }
-        lam[kk] = 0.5 * (lo + hi);
     }
     __syncthreads();
     c128* U = Up[blockIdx.x];
+    c128* Us = A;   // reuse the working matrix as U (m x r) during back-transformation
     for (int kk = threadIdx.x; kk < r; kk += blockDim.x) {
         const double l = lam[kk];
         const double mu = l + 1e-14 * fmax(fabs(l), span * 1e-3);
@@ -547,33 +591,44 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
                 }
             }
         }
-        for (int i = 0; i < m; ++i)
-            if (fabs(dg[i]) < 1e-300) dg[i] = 1e-300;
+        for (int i = 0; i < m; ++i) dg[i] = 1.0 / (fabs(dg[i]) < 1e-300 ? 1e-300 : dg[i]);   // reciprocals
         for (int it = 0; it < 3; ++it) {
             for (int i = 0; i + 1 < m; ++i) {
                 if (!sw[i]) y[i + 1] -= lo[i] * y[i];
                 else { const double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t - lo[i] * y[i]; }
             }
-            y[m - 1] /= dg[m - 1];
-            if (m > 1) y[m - 2] = (y[m - 2] - up[m - 2] * y[m - 1]) / dg[m - 2];
-            for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - up[i] * y[i + 1] - up2[i] * y[i + 2]) / dg[i];
+            y[m - 1] *= dg[m - 1];
+            if (m > 1) y[m - 2] = (y[m - 2] - up[m - 2] * y[m - 1]) * dg[m - 2];
+            for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - up[i] * y[i + 1] - up2[i] * y[i + 2]) * dg[i];
             double nr = 0.0;
             for (int i = 0; i < m; ++i) nr += y[i] * y[i];
-            nr = nr > 0.0 ? 1.0 / sqrt(nr) : 1.0;
+            nr = nr > 0.0 ? rsqrt(nr) : 1.0;
             for (int i = 0; i < m; ++i) y[i] *= nr;
         }
-        // u = Q D y with Q = H_0 ... H_{m-3}
-        c128 u[HE_MAX];
-        for (int i = 0; i < m; ++i) u[i] = y[i] * delta[i];
-        for (int k = m - 3; k >= 0; --k) {
-            const int n = m - k - 1;
-            const c128* v = Vr + k * m;
+        for (int i = 0; i < m; ++i) Us[i * r + kk] = y[i] * delta[i];
+    }
+    __syncthreads();
+    // u = Q D y with Q = H_0 ... H_{m-3}: reflectors applied in reverse, all vectors at
+    // once (a warp per vector for the projections)
+    for (int k = m - 3; k >= 0; --k) {
+        const int n = m - k - 1;
+        const c128* v = Vr + k * m;
+        for (int kk = warp; kk < r; kk += (blockDim.x >> 5)) {
             c128 s = {0.0, 0.0};
-            for (int i = 0; i < n; ++i) cfma_cj(s, v[i], u[k + 1 + i]);
-            s = tau[k] * s;
-            for (int i = 0; i < n; ++i) u[k + 1 + i] = u[k + 1 + i] - v[i] * s;
+            for (int i = lane; i < n; i += 32) cfma_cj(s, v[i], Us[(k + 1 + i) * r + kk]);
+            s = warp_sum(s);
+            if (lane == 0) w[kk] = tau[k] * s;
         }
-        for (int i = 0; i < m; ++i) U[i * m + kk] = u[i];
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * r; t += blockDim.x) {
+            const int i = t / r, kk = t - (t / r) * r;
+            Us[(k + 1 + i) * r + kk] = Us[(k + 1 + i) * r + kk] - v[i] * w[kk];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < m * r; t += blockDim.x) {
+        const int i = t / r, kk = t - (t / r) * r;
+        U[i * m + kk] = Us[i * r + kk];
     }
 }
 

@@ -23,7 +23,11 @@
 // pivoted tridiagonal LU, normalised q^T q = 1 (no conjugation).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace hh {
 
@@ -334,34 +338,11 @@ __device__ __forceinline__ void affine_shfl(cplx<T>& A, cplx<T>& B, int d, bool 
     }
 }
 
+// Both recursions of one line, in place: on entry fs = f^ (Sx values) and as = xi; on
+// exit fs = x^.  One warp; lane l owns the contiguous chunk [l L, (l + 1) L).
 template <typename T>
-__global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs, int wpb) {
+__device__ __forceinline__ void warp_line_solve(const cplx<T>* as, cplx<T>* fs, int Sx, int lane) {
     using C = cplx<T>;
-    const EigTask tk = tasks[blockIdx.y];
-    const int b = tk.b;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int line = blockIdx.x * wpb + warp;
-    if (warp >= wpb || line >= b * nrhs) return;
-    const int m = line / nrhs;
-    extern __shared__ __align__(16) unsigned char ssm[];
-    C* as = (C*)ssm + (size_t)warp * 2 * Sx;
-    C* fs = as + Sx;
-    const C* xi = (const C*)tk.xi + (size_t)m * Sx;
-    C* fh = (C*)tk.Fh + (size_t)line * Sx;     // line = m * nrhs + c
-    for (int i0 = lane; i0 < Sx; i0 += 32 * 8) {
-        C ta[8], tf[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + 32 * u;
-            if (i < Sx) { ta[u] = xi[i]; tf[u] = fh[i]; }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + 32 * u;
-            if (i < Sx) { as[i] = ta[u]; fs[i] = tf[u]; }
-        }
-    }
-    __syncwarp();
     const int L = (Sx + 31) / 32;
     const int s = lane * L, e = min(Sx, s + L);
     // forward: y_i = a_i (y_{i-1} + f_i)
@@ -401,6 +382,37 @@ __global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ t
         fs[i] = x;
     }
     __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs, int wpb) {
+    using C = cplx<T>;
+    const EigTask tk = tasks[blockIdx.y];
+    const int b = tk.b;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int line = blockIdx.x * wpb + warp;
+    if (warp >= wpb || line >= b * nrhs) return;
+    const int m = line / nrhs;
+    extern __shared__ __align__(16) unsigned char ssm[];
+    C* as = (C*)ssm + (size_t)warp * 2 * Sx;
+    C* fs = as + Sx;
+    const C* xi = (const C*)tk.xi + (size_t)m * Sx;
+    C* fh = (C*)tk.Fh + (size_t)line * Sx;     // line = m * nrhs + c
+    for (int i0 = lane; i0 < Sx; i0 += 32 * 8) {
+        C ta[8], tf[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 32 * u;
+            if (i < Sx) { ta[u] = xi[i]; tf[u] = fh[i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 32 * u;
+            if (i < Sx) { as[i] = ta[u]; fs[i] = tf[u]; }
+        }
+    }
+    __syncwarp();
+    warp_line_solve(as, fs, Sx, lane);
     for (int i = lane; i < Sx; i += 32) fh[i] = fs[i];
 }
 
@@ -452,6 +464,157 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
     for (int st = 0; st < 3; ++st) launch_eig_sweep_stage<T>(st, d_tasks, ntasks, b_max, Sx, nrhs, s);
 }
 
+// ------------------------------------------------------- fused one-vector sweep
+// The whole leaf solve for one right-hand side in one launch: one cluster of FS_CL CTAs
+// per leaf.  CTA q of the cluster owns the columns [q ncol, (q + 1) ncol) and the modes
+// [q nmode, (q + 1) nmode).
+//   1. f^[m][i] = sum_a V[a][m] f[a][i] for all m and the CTA's columns (V and f staged
+//      in shared memory);
+//   2. cluster barrier; each warp takes one owned mode, gathers its line f^[m][0..Sx)
+//      from the CTAs' shared memory (distributed shared memory), runs both recursions
+//      and writes x^[m][.] back in place; cluster barrier;
+//   3. x[a][i] = sum_m V[a][m] x^[m][i] for the CTA's columns, written to the leaf output.
+// V stays in shared memory between the two transforms and the transformed vectors never
+// leave the cluster.  2 x 2 register tiles: two 16-byte shared loads per four complex
+// multiply-adds (complex64).
+static constexpr int FS_CL = 8, FS_THREADS = 256, FS_WARPS = FS_THREADS / 32;
+
+struct FsGeom {
+    int ncol, nmode, ldv, ldf;
+    size_t elems;
+};
+HH_HD FsGeom fs_geom(int b, int Sx) {
+    FsGeom g;
+    g.ncol = (Sx + FS_CL - 1) / FS_CL;
+    g.nmode = (b + FS_CL - 1) / FS_CL;
+    g.ldv = b + (b & 1);
+    g.ldf = g.ncol + (g.ncol & 1);
+    const size_t fin = (size_t)b * g.ldf, lines = (size_t)FS_WARPS * 2 * Sx;
+    g.elems = (size_t)b * g.ldv + (size_t)b * g.ldf + (fin > lines ? fin : lines);
+    return g;
+}
+
+template <typename T>
+struct alignas(2 * sizeof(cplx<T>)) cpair {
+    cplx<T> x, y;
+};
+
+template <typename T>
+__global__ void __cluster_dims__(FS_CL, 1, 1) __launch_bounds__(FS_THREADS)
+    k_eig_sweep_fused(const EigTask* __restrict__ tasks, int Sx) {
+    using C = cplx<T>;
+    using C2 = cpair<T>;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const EigTask tk = tasks[blockIdx.y];
+    const int b = tk.b;
+    const FsGeom G = fs_geom(b, Sx);
+    const int c0 = q * G.ncol;
+    const int nown = max(0, min(Sx, c0 + G.ncol) - c0);
+    extern __shared__ __align__(16) unsigned char fsm[];
+    C* Vs = (C*)fsm;                              // [b][ldv], V[a][m]
+    C* Fs = Vs + (size_t)b * G.ldv;               // [b][ldf], f^ then x^ of own columns
+    C* Fin = Fs + (size_t)b * G.ldf;              // [b][ldf], f of own columns (phase 1)
+    C* lines = Fin;                               // per warp as[Sx], fs[Sx] (phase 2)
+    const C* V = (const C*)tk.V;
+    const C* F = (const C*)tk.F;
+    C* Wout = (C*)tk.W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int e = threadIdx.x; e < b * b; e += FS_THREADS) {
+        const int a = e / b, m = e - a * b;
+        Vs[a * G.ldv + m] = V[e];
+    }
+    for (int e = threadIdx.x; e < b * G.ldf; e += FS_THREADS) {
+        const int a = e / G.ldf, il = e - a * G.ldf;
+        Fin[e] = il < nown ? F[(size_t)a * Sx + c0 + il] : C{0, 0};
+    }
+    __syncthreads();
+
+    const int ntc = (nown + 1) / 2, ntm = (b + 1) / 2;
+    // phase 1: tiles (modes m0, m0 + 1) x (columns i0, i0 + 1)
+    for (int t = threadIdx.x; t < ntm * ntc; t += FS_THREADS) {
+        const int m0 = 2 * (t / ntc), i0 = 2 * (t % ntc);
+        C a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
+        for (int k = 0; k < b; ++k) {
+            const C2 v = *(const C2*)(Vs + k * G.ldv + m0);
+            const C2 f = *(const C2*)(Fin + k * G.ldf + i0);
+            cfma(a00, v.x, f.x);
+            cfma(a01, v.x, f.y);
+            cfma(a10, v.y, f.x);
+            cfma(a11, v.y, f.y);
+        }
+        *(C2*)(Fs + m0 * G.ldf + i0) = C2{a00, a01};
+        if (m0 + 1 < b) *(C2*)(Fs + (m0 + 1) * G.ldf + i0) = C2{a10, a11};
+    }
+    cluster.sync();
+
+    // phase 2: the owned modes' lines
+    {
+        C* as = lines + (size_t)warp * 2 * Sx;
+        C* fs = as + Sx;
+        const int mend = min(b, (q + 1) * G.nmode);
+        for (int m = q * G.nmode + warp; m < mend; m += FS_WARPS) {
+            const C* xi = (const C*)tk.xi + (size_t)m * Sx;
+            for (int i = lane; i < Sx; i += 32) {
+                const int r = i / G.ncol;
+                const C* rem = cluster.map_shared_rank(Fs, r);
+                fs[i] = rem[m * G.ldf + (i - r * G.ncol)];
+                as[i] = xi[i];
+            }
+            __syncwarp();
+            warp_line_solve(as, fs, Sx, lane);
+            for (int i = lane; i < Sx; i += 32) {
+                const int r = i / G.ncol;
+                C* rem = cluster.map_shared_rank(Fs, r);
+                rem[m * G.ldf + (i - r * G.ncol)] = fs[i];
+            }
+            __syncwarp();
+        }
+    }
+    cluster.sync();
+
+    // phase 3: tiles (rows a0, a0 + 1) x (columns i0, i0 + 1), written to the output
+    for (int t = threadIdx.x; t < ntm * ntc; t += FS_THREADS) {
+        const int a0 = 2 * (t / ntc), i0 = 2 * (t % ntc);
+        const int a1 = min(a0 + 1, b - 1);
+        C a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
+        for (int k = 0; k < b; ++k) {
+            const C v0 = Vs[a0 * G.ldv + k], v1 = Vs[a1 * G.ldv + k];
+            const C2 f = *(const C2*)(Fs + k * G.ldf + i0);
+            cfma(a00, v0, f.x);
+            cfma(a01, v0, f.y);
+            cfma(a10, v1, f.x);
+            cfma(a11, v1, f.y);
+        }
+        C* w0 = Wout + (size_t)a0 * Sx + c0 + i0;
+        w0[0] = a00;
+        if (i0 + 1 < nown) w0[1] = a01;
+        if (a0 + 1 < b) {
+            C* w1 = w0 + Sx;
+            w1[0] = a10;
+            if (i0 + 1 < nown) w1[1] = a11;
+        }
+    }
+}
+
+template <typename T>
+bool eig_sweep_fused_ready(int b_max, int Sx) {
+    if (Sx < FS_CL || sizeof(cplx<T>) * fs_geom(b_max, Sx).elems > (size_t)FS_SMEM_MAX) return false;
+    static bool attr = false;
+    if (!attr)
+        attr = cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    FS_SMEM_MAX) == cudaSuccess;
+    return attr;
+}
+
+template <typename T>
+void launch_eig_sweep_fused(const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s) {
+    const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx).elems;
+    k_eig_sweep_fused<T><<<dim3(FS_CL, ntasks), FS_THREADS, sm, s>>>(d_tasks, Sx);
+    note_launch();
+}
+
 int eig_bmax() { return GT_ROWS * GT_RPT < EIG_BMAX ? GT_ROWS * GT_RPT : EIG_BMAX; }
 size_t eig_work_elems(int b) { return (size_t)b * 6 * b; }
 
@@ -461,5 +624,9 @@ template void launch_eig_sweep<float>(const EigTask*, int, int, int, int, cudaSt
 template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep<double>(const EigTask*, int, int, int, int, cudaStream_t);
+template void launch_eig_sweep_fused<float>(const EigTask*, int, int, int, cudaStream_t);
+template void launch_eig_sweep_fused<double>(const EigTask*, int, int, int, cudaStream_t);
+template bool eig_sweep_fused_ready<float>(int, int);
+template bool eig_sweep_fused_ready<double>(int, int);
 
 }  // namespace hh

@@ -135,6 +135,15 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
                        cudaStream_t s);
 template <typename T>
 void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s);
+// One right-hand side (nrhs = 1, F/W [b][Sx]): the three stages in one launch, one
+// thread-block cluster per leaf.  eig_sweep_fused_ready (call outside stream capture)
+// says whether leaves of up to b_max rows fit the cluster's shared memory and prepares
+// the kernel; when it returns false the caller runs the three stages instead.
+constexpr int FS_SMEM_MAX = 220 * 1024;
+template <typename T>
+bool eig_sweep_fused_ready(int b_max, int Sx);
+template <typename T>
+void launch_eig_sweep_fused(const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s);
 // stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^
 template <typename T>
 void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,

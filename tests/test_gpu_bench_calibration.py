@@ -61,9 +61,11 @@ def test_profiler_and_launch_counter(hh, case):
         prof = hh.hh_profile_read(h)
         work = hh.hh_profile_read(h, work=True)
         assert work["sweep_recur"][2] > 0 and work["sweep_in"][3] > 0 and work["coarse_project"][2] > 0
+        assert work["leaf_sweep"][2] > 0 and work["leaf_sweep"][3] > 0
         assert prof["factor"][1] == 1 and prof["factor"][0] > 0
         for stage in ("sweep_in", "sweep_recur", "sweep_out"):
-            assert prof[stage][1] == 6 + st.iters        # 3 sketch passes per level + 1 per iteration
+            assert prof[stage][1] == 6                   # 3 multi-vector sketch passes per level
+        assert prof["leaf_sweep"][1] == st.iters         # one single-vector sweep per iteration
         assert prof["galerkin"][1] == 3 and prof["svd"][1] == 2 and prof["qr"][1] == 2
         assert hh.hh_launch_count() - n0 > 50
     finally:
