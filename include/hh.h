@@ -50,7 +50,9 @@ typedef enum {
     HH_EBREAKDOWN = -4,   /* zero pivot in a subdomain or coarse factorisation        */
     HH_ETIMEOUT = -5,     /* a bounded device-side wait gave up                       */
     HH_ECUDA = -6,        /* a CUDA runtime call failed                               */
-    HH_ENOTIMPL = -7
+    HH_ENOTIMPL = -7,
+    HH_ETOOLARGE = -8     /* the problem does not fit a fixed-size static scratch     */
+                          /* (hh_residual_noalloc: n + 2 > HH_NOALLOC_MAX_ROWS)       */
 } hh_status;
 
 typedef enum {
@@ -139,6 +141,44 @@ hh_status hh_residual(hh_handle* h, const void* d_f, const void* d_g, const void
 
 void hh_destroy(hh_handle* h);
 const char* hh_status_string(hh_status s);
+
+/* --------------------------------------------------------------------------------
+ * Allocation-free residual.  The paper has no counterpart: this is a service entry
+ * point of the library, not a step of the method.
+ *
+ * Who needs it: a caller that may not allocate device memory at the moment it wants
+ * the residual.  cudaMalloc and cudaFree can synchronise the whole device, which a
+ * caller overlapping latency-bound work on other streams cannot afford; a process whose
+ * device memory is already claimed by a pooling allocator (a framework's caching pool,
+ * a serving engine that reserves the HBM up front) may see a fresh cudaMalloc fail
+ * although its own pool has room; and a caller with a fixed memory plan (a health check
+ * run after a solve, next to other jobs' buffers) must not fail half-way for want of
+ * memory.  hh_residual needs a handle, and hh_setup allocates.
+ * -------------------------------------------------------------------------------- */
+/* Largest number of grid rows (S = n + 2) hh_residual_noalloc accepts. */
+#define HH_NOALLOC_MAX_ROWS 16384
+
+/* ||b(f,g) - A u||_2 / ||b||_2 in FP64, the same quantity as hh_residual, for the
+ * problem (dim, n, k) of Eq. (1) / Sec. 3.1 (h = 1/(n+1)), without a handle and
+ * without allocating: no cudaMalloc, cudaFree or allocating library call.
+ * d_f [S_y][S_x], d_g [4][S] (or [2]) and d_u [S_y][S_x] are complex128 device arrays
+ * on the current device, owned by the caller and only read; rel_res is a host double.
+ * Enqueues one memset of a 4-byte counter, one kernel and one 16-byte device-to-host
+ * copy on `stream`, and synchronises it.  b = 0 gives 0.
+ * Scratch: a file-scope device array of HH_NOALLOC_MAX_ROWS x 16 bytes (256 KiB)
+ * plus 256 bytes, which every GPU that loads libhh holds until the process exits.  It
+ * holds one (sum |r|^2, sum |b|^2) pair per grid row, the total and a counter; the
+ * counter, the one part that must start at zero, is cleared on `stream` by every call.
+ * The first call on a device (the device current at the call) looks the array's address
+ * up (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Calls that overlap in time on one device share the array and race: issue
+ * them from one host thread on one stream (or otherwise serialise them).
+ * Errors: HH_EINVAL for dim not 1 or 2, n < 1, k negative or not finite, or a NULL
+ * pointer; HH_ETOOLARGE when n + 2 > HH_NOALLOC_MAX_ROWS (checked before any pointer
+ * or the device is touched); HH_ECUDA when a CUDA call fails (including the address
+ * look-up). */
+hh_status hh_residual_noalloc(int dim, int n, double k, const void* d_f, const void* d_g,
+                              const void* d_u, void* stream, double* rel_res);
 
 /* --------------------------------------------------------------------------------
  * Step-level entry points.  Each runs one step of the path on device arrays so that it

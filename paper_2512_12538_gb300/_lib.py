@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libhh.so")
 
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ENOCONV, HH_EBREAKDOWN, HH_ETIMEOUT, HH_ECUDA, HH_ENOTIMPL = (
     0, -1, -2, -3, -4, -5, -6, -7)
+HH_ETOOLARGE = -8
+HH_NOALLOC_MAX_ROWS = 16384
 HH_PREC_FP64, HH_PREC_MIXED = 0, 1
 HH_LEAF_EIGEN, HH_LEAF_BLOCK = 0, 1
 HH_OUTER_ORAS, HH_OUTER_GMRES = 0, 1
@@ -70,6 +72,7 @@ def _load():
         "hh_profile_enable": (i, [vp, i]),
         "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
         "hh_launch_count": (ctypes.c_ulonglong, []),
+        "hh_residual_noalloc": (i, [i, i, d, vp, vp, vp, vp, P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -188,6 +191,14 @@ def hh_solve_host(h, f_host, g_host, u_host, stream=None, allow_noconv=False) ->
 def hh_residual(h, f, g, u, stream=None) -> float:
     r = ctypes.c_double()
     _check(LIB.hh_residual(h, _ptr(f), _ptr(g), _ptr(u), _stream(stream), ctypes.byref(r)), "hh_residual")
+    return r.value
+
+
+def hh_residual_noalloc(dim, n, k, f, g, u, stream=None) -> float:
+    """hh_residual without a handle or any device allocation (static scratch)."""
+    r = ctypes.c_double()
+    _check(LIB.hh_residual_noalloc(int(dim), int(n), float(k), _ptr(f), _ptr(g), _ptr(u), _stream(stream),
+                                   ctypes.byref(r)), "hh_residual_noalloc")
     return r.value
 
 

@@ -1135,6 +1135,7 @@ const char* hh_status_string(hh_status s) {
         case HH_ETIMEOUT: return "bounded device wait gave up";
         case HH_ECUDA: return "CUDA runtime error";
         case HH_ENOTIMPL: return "not implemented";
+        case HH_ETOOLARGE: return "problem larger than the fixed static scratch (n + 2 > HH_NOALLOC_MAX_ROWS)";
     }
     return "unknown status";
 }
