@@ -73,6 +73,22 @@ HH_HD c128 op_diag(int j, int i, const OpGeom& g) {
     const double im = -g.kh * (wj * bx + wi * (by ? 1.0 : 0.0));
     return {re, im};
 }
+// The same coefficient evaluated in precision R (the weights and stencil counts are
+// exact in any precision; R = float keeps single-precision kernels off the FP64 pipe).
+template <typename R> HH_HD cplx<R> op_diag_t(int j, int i, const OpGeom& g) {
+    const R wj = (j == 0 || j == g.b - 1) ? (R)0.5 : (R)1;
+    const R wi = g.Sx == 1 ? (R)1 : ((i == 0 || i == g.Sx - 1) ? (R)0.5 : (R)1);
+    const bool by = (j == 0 || j == g.b - 1);
+    const R cy = by ? (R)1 : (R)2;
+    R cx = 0, bx = 0;
+    if (g.Sx > 1) {
+        const bool xb = (i == 0 || i == g.Sx - 1);
+        cx = xb ? (R)1 : (R)2;
+        bx = xb ? (R)1 : (R)0;
+    }
+    const R kh = (R)g.kh;
+    return {wj * cx + wi * cy - kh * kh * wi * wj, -kh * (wj * bx + wi * (by ? (R)1 : (R)0))};
+}
 
 // ------------------------------------------------------------------ error reporting
 // Device-side status word (per process): kernels record the first failure here and

@@ -128,6 +128,7 @@ static hh_status validate(const hh_params* P) {
     if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
     if (P->levels > 6) return HH_EINVAL;
     const int Sx = P->dim == 2 ? P->n + 2 : 1;
+    if ((long long)(P->n + 2) * Sx >= (1ll << 31)) return HH_EINVAL;   // grid points index in 32 bits
     const int m = std::min(P->rank + P->oversample, Sx);
     if (2 * std::min(P->rank, m) > 64 || m > 64) return HH_EINVAL;   // dense coarse kernels
     std::vector<Node> nodes;
@@ -265,13 +266,19 @@ struct Solver final : SolverBase {
     double *npart = nullptr, *dnorm = nullptr;
     int* derr = nullptr;
     unsigned* dcounter = nullptr;   // ticket counter of the last-block reductions (zero between launches)
-    LeafTask *d_tasks_view = nullptr, *d_tasks_own = nullptr, *d_task_one = nullptr;
+    LeafTask *d_tasks_view = nullptr, *d_tasks_own = nullptr, *d_task_one = nullptr, *d_tasks_pre = nullptr;
+    // inputs of the nodes in the current apply (with n_i = 1 a child reads its parent's
+    // input directly: R_c of the parent's input, no copy into the parent's buffer)
+    std::vector<const CT*> cur_in;
+    bool in_pre = false;        // inside the preconditioner step (oras_step)
+    bool pre_direct = false;    // its leaf sweeps write the owned rows into the parents
+    std::vector<const void*> view_key, eview_key;
     // eigenbasis leaf path
     bool eig = false;
-    bool eig_fused = false;     // one-launch sweep for single right-hand sides
+    int eig_fused = 0;          // cluster size of the one-launch single-vector sweep (0: off)
     std::vector<CT*> EV, EXI, EFh;
     std::vector<c128*> ELAM, EWK;
-    EigTask *d_etasks_view = nullptr, *d_etasks_own = nullptr, *d_etask_one = nullptr;
+    EigTask *d_etasks_view = nullptr, *d_etasks_own = nullptr, *d_etask_one = nullptr, *d_etasks_pre = nullptr;
     // flexible GMRES
     int mk = 0;                                   // restart length
     c128 *Vb = nullptr, *Zb = nullptr, *gw = nullptr, *gv = nullptr, *gz = nullptr, *gdots = nullptr,
@@ -350,7 +357,7 @@ struct Solver final : SolverBase {
                 Om[id] = a.take<CT>((size_t)Sx * nmax);
                 Z[id] = a.take<CT>((size_t)Sx * nmax);
                 Vc[id] = a.take<CT>((size_t)Sx * std::max(r, 1));
-                Gm[id] = a.take<c128>((size_t)m * m);
+                Gm[id] = a.take<c128>((size_t)m * m + 4 * (size_t)m);   // + eigensolver workspace
                 U[id] = a.take<c128>((size_t)m * m);
                 lam[id] = a.take<double>(m);
             }
@@ -372,6 +379,8 @@ struct Solver final : SolverBase {
             }
         }
         R[0] = RT;
+        cur_in.assign(nn, nullptr);
+        cur_in[0] = RT;
         partial = a.take<c128>((size_t)MAX_PART_BLOCKS * 64 * 64);
         npart = a.take<double>(2048);
         dnorm = a.take<double>(4);
@@ -381,6 +390,8 @@ struct Solver final : SolverBase {
         d_tasks_view = a.take<LeafTask>(nleaf);
         d_tasks_own = a.take<LeafTask>(nleaf);
         d_task_one = a.take<LeafTask>(1);
+        d_tasks_pre = a.take<LeafTask>(nleaf);
+        d_etasks_pre = a.take<EigTask>(nleaf);
         d_etasks_view = a.take<EigTask>(nleaf);
         d_etasks_own = a.take<EigTask>(nleaf);
         d_etask_one = a.take<EigTask>(1);
@@ -431,8 +442,15 @@ struct Solver final : SolverBase {
         return t;
     }
     // The view tasks depend on the column count (row stride = Sx * nc).
+    // Leaf input of the current apply: R_leaf of the parent's input (n_i = 1) or of the
+    // parent's residual buffer.
+    const CT* leaf_input(int id, int nc) const {
+        const int p = nodes[id].parent;
+        return src_of(p) + row_off(p, nodes[id].ra, nc);
+    }
     void upload_view_tasks(int nc) {
         std::vector<LeafTask> t;
+        std::vector<const void*> key{(const void*)(size_t)nc};
         for (int id : lev[L]) {
             const Node& nd = nodes[id];
             LeafTask k;
@@ -440,14 +458,15 @@ struct Solver final : SolverBase {
             k.W = W[id];
             k.b = nd.b();
             k.ldx = ldx[id];
-            k.F = R[nd.parent] + row_off(nd.parent, nd.ra, nc);
+            k.F = leaf_input(id, nc);
+            key.push_back(k.F);
             t.push_back(k);
         }
+        if (key == view_key) return;
+        view_key = key;
         ck(cudaMemcpyAsync(d_tasks_view, t.data(), sizeof(LeafTask) * t.size(), cudaMemcpyHostToDevice, stream),
            cerr);
     }
-    int view_nc = -1;
-
     EigTask eig_task(int id, const void* F, void* Wout) const {
         EigTask k;
         k.V = EV[id];
@@ -458,23 +477,73 @@ struct Solver final : SolverBase {
         k.W = Wout;
         k.work = EWK[id];
         k.b = nodes[id].b();
+        k.w0 = 0;
+        k.w1 = k.b;
         return k;
     }
     void upload_eig_view_tasks(int nc) {
         std::vector<EigTask> t;
+        std::vector<const void*> key{(const void*)(size_t)nc};
         for (int id : lev[L]) {
-            const Node& nd = nodes[id];
-            t.push_back(eig_task(id, R[nd.parent] + row_off(nd.parent, nd.ra, nc), W[id]));
+            t.push_back(eig_task(id, leaf_input(id, nc), W[id]));
+            key.push_back(t.back().F);
         }
+        if (key == eview_key) return;
+        eview_key = key;
         ck(cudaMemcpyAsync(d_etasks_view, t.data(), sizeof(EigTask) * t.size(), cudaMemcpyHostToDevice, stream),
            cerr);
+    }
+    // Leaf tasks of the preconditioner step (one vector, from the root's residual RT),
+    // fixed after set-up so that captured graphs can read them.  With n_i = 1 and the
+    // one-launch sweep, each leaf writes its owned rows straight into its parent's
+    // solution (restricted prolongation without a copy).
+    void upload_pre_tasks() {
+        const bool direct_in = P.n_inner == 1;
+        pre_direct = eig && eig_fused && direct_in && L >= 2;
+        std::vector<EigTask> et;
+        std::vector<LeafTask> lt;
+        for (int id : lev[L]) {
+            const Node& nd = nodes[id];
+            const int p = nd.parent;
+            const CT* F = direct_in ? RT + row_off(0, nd.ra, 1) : R[p] + row_off(p, nd.ra, 1);
+            if (eig) {
+                EigTask k = eig_task(id, F, W[id]);
+                if (pre_direct) {
+                    k.W = W[p] + row_off(p, nd.own_a, 1);
+                    k.w0 = nd.own_a - nd.ra;
+                    k.w1 = nd.own_b - nd.ra;
+                }
+                et.push_back(k);
+            } else {
+                LeafTask k;
+                k.X = X[id];
+                k.W = W[id];
+                k.b = nd.b();
+                k.ldx = ldx[id];
+                k.F = F;
+                lt.push_back(k);
+            }
+        }
+        if (eig)
+            ck(cudaMemcpyAsync(d_etasks_pre, et.data(), sizeof(EigTask) * et.size(), cudaMemcpyHostToDevice, stream),
+               cerr);
+        else
+            ck(cudaMemcpyAsync(d_tasks_pre, lt.data(), sizeof(LeafTask) * lt.size(), cudaMemcpyHostToDevice, stream),
+               cerr);
     }
     // all leaves: W[leaf] = A~_leaf^{-1} F (F = own buffers or views into the parents)
     void leaf_sweep_all(int nc, bool own) {
         const int nl = (int)lev[L].size();
         if (eig) {
-            if (!own && view_nc != nc) { upload_eig_view_tasks(nc); view_nc = nc; }
-            const EigTask* tasks = own ? d_etasks_own : d_etasks_view;
+            const EigTask* tasks = d_etasks_own;
+            if (!own) {
+                if (in_pre && nc == 1) {
+                    tasks = d_etasks_pre;
+                } else {
+                    upload_eig_view_tasks(nc);
+                    tasks = d_etasks_view;
+                }
+            }
             if (nc == 1 && eig_fused) {
                 // both transforms (16 b^2 Sx flops) and the recursions; V, f, xi read and
                 // x written once: b^2 + 3 b Sx elements
@@ -485,7 +554,7 @@ struct Solver final : SolverBase {
                     by += sizeof(CT) * (b * b + 3.0 * b * sx);
                 }
                 pbeg(PC_SWEEP, by, fl);
-                launch_eig_sweep_fused<T>(tasks, nl, b_max, Sx, stream);
+                launch_eig_sweep_fused<T>(eig_fused, tasks, nl, b_max, Sx, stream);
                 pend();
                 return;
             }
@@ -504,18 +573,30 @@ struct Solver final : SolverBase {
             }
             return;
         }
-        if (!own && view_nc != nc) { upload_view_tasks(nc); view_nc = nc; }
+        const LeafTask* tasks = d_tasks_own;
+        if (!own) {
+            if (in_pre && nc == 1) {
+                tasks = d_tasks_pre;
+            } else {
+                upload_view_tasks(nc);
+                tasks = d_tasks_view;
+            }
+        }
         pbeg(PC_RECUR);
-        launch_sweep<T>(own ? d_tasks_own : d_tasks_view, nl, b_max, Sx, nc, derr, stream);
+        launch_sweep<T>(tasks, nl, b_max, Sx, nc, derr, stream);
         pend();
     }
 
-    // Input of node id at the top level of an apply: its own buffer or a view into
-    // the parent's residual.
+    // Buffer holding node p's input during the current apply: with n_i = 1 its input
+    // itself (nothing is subtracted from it), else its residual buffer R[p].
+    const CT* src_of(int p) const { return (P.n_inner == 1 && cur_in[p]) ? cur_in[p] : R[p]; }
+
+    // Input of node id in an apply: its own buffer (top level of a multi-vector apply)
+    // or its rows of the parent's input buffer.
     const CT* input(int id, int nc, bool own) const {
         if (own) return Vs[id];
         const int p = nodes[id].parent;
-        return R[p] + row_off(p, nodes[id].ra, nc);
+        return src_of(p) + row_off(p, nodes[id].ra, nc);
     }
 
     // ------------------------------------------------- sub-level solve M at level l
@@ -524,21 +605,29 @@ struct Solver final : SolverBase {
             leaf_sweep_all(nc, own);
             return;
         }
+        for (int p : lev[l]) cur_in[p] = input(p, nc, own);
+        // the leaves of the preconditioner step may have written their owned rows into
+        // the parents already
+        const bool leaves_direct = l + 1 == L && in_pre && pre_direct && nc == 1;
         for (int it = 0; it < P.n_inner; ++it) {
             for (int p : lev[l]) {
-                const CT* vin = input(p, nc, own);
-                if (it == 0) d2d(R[p], vin, sizeof(CT) * pts(p) * nc);
-                else launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
+                if (it == 0) {
+                    if (P.n_inner > 1) d2d(R[p], cur_in[p], sizeof(CT) * pts(p) * nc);
+                } else {
+                    launch_apply<T, T, T>(W[p], cur_in[p], R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
+                }
             }
             apply_M(l + 1, nc, false);
             for (int p : lev[l]) {
-                for (int c : nodes[p].child) {
-                    const Node& cn = nodes[c];
-                    const size_t n = (size_t)(cn.own_b - cn.own_a) * Sx * nc;
-                    launch_copy<T, T>(W[c] + row_off(c, cn.own_a, nc), W[p] + row_off(p, cn.own_a, nc), n, it > 0,
-                                      false, stream);
+                if (!leaves_direct) {
+                    for (int c : nodes[p].child) {
+                        const Node& cn = nodes[c];
+                        const size_t n = (size_t)(cn.own_b - cn.own_a) * Sx * nc;
+                        launch_copy<T, T>(W[c] + row_off(c, cn.own_a, nc), W[p] + row_off(p, cn.own_a, nc), n,
+                                          it > 0, false, stream);
+                    }
                 }
-                coarse_correct(p, input(p, nc, own), nc);
+                coarse_correct(p, cur_in[p], nc);
             }
         }
     }
@@ -630,12 +719,18 @@ struct Solver final : SolverBase {
             const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS, stream);
             pend();
             launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
-            launch_gj_inverse(Ainv[p], 2 * r, derr, stream);
         }
+        // the level's Galerkin matrices inverted together
+        GjBatch bt{};
+        bt.n = 2 * r;
+        bt.err = derr;
+        int cnt = 0;
+        for (int p : lev[l - 1]) bt.A[cnt++] = Ainv[p];
+        launch_gj_inverse(bt, cnt, stream);
     }
 
     hh_status setup() override {
-        eig_fused = eig && eig_sweep_fused_ready<T>(b_max, Sx);
+        eig_fused = eig ? eig_sweep_fused_ready<T>(b_max, Sx) : 0;
         zero(derr, sizeof(int) * 4);
         zero(dcounter, sizeof(unsigned) * 4);
         for (int id = 1; id < nn; ++id) zero(Vs[id], sizeof(CT) * pts(id) * nmax);
@@ -660,6 +755,7 @@ struct Solver final : SolverBase {
         else launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
         pend();
         for (int l = L; l >= 1; --l) sketch_level(l);
+        upload_pre_tasks();
         cudaEventRecord(e1, stream);
         hh_status st;
         const bool ok = sync_check(st);
@@ -676,25 +772,27 @@ struct Solver final : SolverBase {
     }
 
     // --------------------------------------------------------- the outer iteration
-    // One coarse-corrected ORAS step from the FP64 residual `rr` (kept in res):
-    // ut = base + sum_c P_c M_c R_c rr ; res <- b - A ut (or rr - A(ut - base));
-    // out = ut + C A_c^{-1} C^H res.
+    // One coarse-corrected ORAS step from the FP64 residual kept in res:
+    // out = base + sum_c P_c M_c R_c res (base null: zero; base may be out), then
+    // out += C A_c^{-1} C^H (rhs - A out).
     void oras_step(const c128* base, const c128* rhs, c128* out) {
         const size_t N = (size_t)Sy * Sx;
         launch_copy<double, T>(res, RT, N, false, false, stream);
+        in_pre = true;
         apply_M(1, 1, false);
-        if (base) d2d(ut, base, sizeof(c128) * N);
-        else zero(ut, sizeof(c128) * N);
+        in_pre = false;
+        // out = base + sum_c P_c W_c: the level-1 owned rows partition the grid, so with
+        // no base the copies initialise out
+        if (base && base != out) d2d(out, base, sizeof(c128) * N);
         for (int c : lev[1]) {
             const Node& cn = nodes[c];
-            launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), ut + row_off(0, cn.own_a, 1),
-                                   (size_t)(cn.own_b - cn.own_a) * Sx, true, false, stream);
+            launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), out + row_off(0, cn.own_a, 1),
+                                   (size_t)(cn.own_b - cn.own_a) * Sx, base != nullptr, false, stream);
         }
         pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 2.0 * sizeof(c128)), 8.0 * 2 * r * N);
-        launch_coarse_proj1<T, double, double>(C[0], rhs, ut, geom(0), 2 * r, partial, dcounter, Ainv[0], ycoef[0],
-                                               stream);
+        launch_coarse_proj1<T, double, double>(C[0], rhs, out, geom(0), 2 * r, partial, dcounter, Ainv[0],
+                                               ycoef[0], stream);
         pend();
-        if (out != ut) d2d(out, ut, sizeof(c128) * N);
         launch_coarse_upd1<T, double>(C[0], ycoef[0], out, N, 2 * r, stream);
     }
 
@@ -934,7 +1032,9 @@ struct Solver final : SolverBase {
         if (eig) {
             EigTask k = eig_task(id, Vs[id], W[id]);
             ck(cudaMemcpyAsync(d_etask_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
-            launch_eig_sweep<T>(d_etask_one, 1, nodes[id].b(), Sx, nc, stream);
+            // the same kernels as inside a solve: one launch for a single vector
+            if (nc == 1 && eig_fused) launch_eig_sweep_fused<T>(eig_fused, d_etask_one, 1, nodes[id].b(), Sx, stream);
+            else launch_eig_sweep<T>(d_etask_one, 1, nodes[id].b(), Sx, nc, stream);
         } else {
             LeafTask k;
             k.X = X[id];

@@ -32,12 +32,13 @@ void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size
     note_launch();
 }
 
-// One column.  A block takes 64 consecutive points per step; its four groups of 64
-// threads each accumulate a quarter of the p columns (coalesced reads of C along the
-// points), every thread forming r_pt = v_pt - (A~ w)_pt (w may be null: r = v) in the
-// precision of v and w.  Per-block partial sums go to `partial`; the last block to
-// finish (ticket counter) adds them in block order (FP64), multiplies by the FP64
-// inverse Galerkin matrix, writes y = A_c^{-1} C^H r and resets the counter.
+// One column.  A block takes 256 consecutive points per step: first every thread forms
+// r_pt = v_pt - (A~ w)_pt for one point (w may be null: r = v) in the precision of v and
+// w and leaves it in shared memory; then its four groups of 64 threads each accumulate a
+// quarter of the p columns over the 256 points (coalesced reads of C along the points).
+// Per-block partial sums go to `partial`; the last block to finish (ticket counter) adds
+// them in block order (FP64), multiplies by the FP64 inverse Galerkin matrix, writes
+// y = A_c^{-1} C^H r and resets the counter.
 template <typename TC, typename TV, typename TW, typename ACC>
 __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict__ C, const cplx<TV>* __restrict__ v,
                                                       const cplx<TW>* __restrict__ w, OpGeom g, int p,
@@ -46,39 +47,54 @@ __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict
     using CA = cplx<ACC>;
     using R = decltype(TV() + TW());
     __shared__ CA red[8][16];
+    __shared__ CA s_r[256];
     __shared__ unsigned ticket;
     __shared__ c128 s_sum[64];
     __shared__ c128 s_m[64 * 64];
-    const size_t N = (size_t)g.b * g.Sx;
+    const unsigned N = (unsigned)g.b * (unsigned)g.Sx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;        // point in tile, column group
+    const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;        // point in sub-tile, column group
     const int per = (p + 3) / 4, ja = jg * per, jb = min(p, ja + per);
     CA acc[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = {0, 0};
-    for (size_t base = (size_t)blockIdx.x * 64; base < N; base += (size_t)gridDim.x * 64) {
-        const size_t pt = base + q;
-        if (pt >= N) continue;
-        cplx<TC> cv[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) cv[u] = (ja + u < jb) ? C[(size_t)(ja + u) * N + pt] : cplx<TC>{0, 0};
-        cplx<R> rv = cvt<R>(v[pt]);
-        if (w) {
-            const int i = (int)(pt % g.Sx), jr = (int)(pt / g.Sx);
-            const c128 d = op_diag(jr, i, g);
-            cplx<R> ax = cplx<R>{(R)d.re, (R)d.im} * cvt<R>(w[pt]);
-            const R wj = (R)wrow(jr, g.b), wi = (R)wcol(i, g.Sx);
-            if (g.Sx > 1) {
-                if (i > 0) ax = ax - wj * cvt<R>(w[pt - 1]);
-                if (i < g.Sx - 1) ax = ax - wj * cvt<R>(w[pt + 1]);
+    for (unsigned base = blockIdx.x * 256u; base < N; base += gridDim.x * 256u) {
+        {
+            const unsigned pt = base + threadIdx.x;
+            CA ra = {0, 0};
+            if (pt < N) {
+                cplx<R> rv = cvt<R>(v[pt]);
+                if (w) {
+                    const int jr = (int)(pt / (unsigned)g.Sx), i = (int)(pt - (unsigned)jr * g.Sx);
+                    cplx<R> ax = op_diag_t<R>(jr, i, g) * cvt<R>(w[pt]);
+                    const R wj = (jr == 0 || jr == g.b - 1) ? (R)0.5 : (R)1;
+                    const R wi = g.Sx == 1 ? (R)1 : ((i == 0 || i == g.Sx - 1) ? (R)0.5 : (R)1);
+                    if (g.Sx > 1) {
+                        if (i > 0) ax = ax - wj * cvt<R>(w[pt - 1]);
+                        if (i < g.Sx - 1) ax = ax - wj * cvt<R>(w[pt + 1]);
+                    }
+                    if (jr > 0) ax = ax - wi * cvt<R>(w[pt - g.Sx]);
+                    if (jr < g.b - 1) ax = ax - wi * cvt<R>(w[pt + g.Sx]);
+                    rv = rv - ax;
+                }
+                ra = cvt<ACC>(rv);
             }
-            if (jr > 0) ax = ax - wi * cvt<R>(w[pt - g.Sx]);
-            if (jr < g.b - 1) ax = ax - wi * cvt<R>(w[pt + g.Sx]);
-            rv = rv - ax;
+            s_r[threadIdx.x] = ra;
         }
-        const CA ra = cvt<ACC>(rv);
+        __syncthreads();
+#pragma unroll 2
+        for (int sub = 0; sub < 4; ++sub) {
+            const unsigned pt = base + sub * 64 + q;
+            if (pt < N) {
+                cplx<TC> cv[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) cfma_cj(acc[u], cvt<ACC>(cv[u]), ra);
+                for (int u = 0; u < 16; ++u) cv[u] = (ja + u < jb) ? C[(size_t)(ja + u) * N + pt] : cplx<TC>{0, 0};
+                const CA ra = s_r[sub * 64 + q];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) cfma_cj(acc[u], cvt<ACC>(cv[u]), ra);
+            }
+        }
+        __syncthreads();
     }
     // both warps of a column group hold the group's columns: reduce over lanes, then over
     // the two warps in shared memory
@@ -107,18 +123,22 @@ __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict
     for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
         const int j = j0 + (threadIdx.x >> 3);
         const bool ok = j < p;
+        // partials b = sub, sub + 8, ...: eight loads in flight per thread, added in
+        // index order
         c128 t0 = {0.0, 0.0}, t1 = {0.0, 0.0};
-        unsigned b = sub;
         if (ok) {
-            for (; b + 8 < gridDim.x; b += 16) {
-                const double2 a0 = __ldcg((const double2*)(partial + (size_t)b * p + j));
-                const double2 a1 = __ldcg((const double2*)(partial + (size_t)(b + 8) * p + j));
-                t0 = t0 + c128{a0.x, a0.y};
-                t1 = t1 + c128{a1.x, a1.y};
-            }
-            if (b < gridDim.x) {
-                const double2 a0 = __ldcg((const double2*)(partial + (size_t)b * p + j));
-                t0 = t0 + c128{a0.x, a0.y};
+            for (unsigned b0 = sub; b0 < gridDim.x; b0 += 64) {
+                double2 a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const unsigned bb = b0 + 8u * u;
+                    a[u] = bb < gridDim.x ? __ldcg((const double2*)(partial + (size_t)bb * p + j)) : make_double2(0.0, 0.0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    t0 = t0 + c128{a[u].x, a[u].y};
+                    t1 = t1 + c128{a[u + 1].x, a[u + 1].y};
+                }
             }
         }
         c128 t = t0 + t1;
@@ -141,7 +161,8 @@ template <typename TC, typename TV, typename TW>
 void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
                          unsigned* counter, const c128* Minv, c128* y, cudaStream_t s) {
     const size_t N = (size_t)g.b * g.Sx;
-    const int grid = blocks_for(N, 64, 152 * 4);
+    // one block per SM at most: the last block's reduction reads grid x p partials
+    const int grid = blocks_for(N, 256, 152);
     k_coarse_proj1<TC, TV, TW, TC><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
     note_launch();
 }
@@ -154,7 +175,8 @@ __global__ void __launch_bounds__(256) k_coarse_upd1(const cplx<TC>* __restrict_
                                                      cplx<TW>* __restrict__ W, size_t N, int p) {
     __shared__ cplx<TC> ys[64];
     __shared__ cplx<TC> part[4][64];
-    for (int j = threadIdx.x; j < p; j += blockDim.x) ys[j] = cvt<TC>(y[j]);
+    // entries past p are multiplied by zero columns: they must be finite, so zero them
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) ys[j] = j < p ? cvt<TC>(y[j]) : cplx<TC>{0, 0};
     __syncthreads();
     const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;
     const int per = (p + 3) / 4, ja = jg * per, jb = min(p, ja + per);

@@ -349,12 +349,34 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
 // Classical Gram-Schmidt applied twice per column (orthogonal to working precision
 // for full-rank input); column j of Y becomes q_j with r_jj > 0 real.  One CTA per
 // block; the block stays in global memory (L2).
+// The block is staged in shared memory when it fits (every step of the sequential
+// column loop then waits on shared rather than global memory latency).
 template <typename T>
-__global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m) {
-    cplx<T>* Y = Yp[blockIdx.x];
+__global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, int staged) {
+    cplx<T>* Yg = Yp[blockIdx.x];
+    extern __shared__ __align__(16) unsigned char qsm[];
+    cplx<T>* Y = staged ? (cplx<T>*)qsm : Yg;
     __shared__ cplx<T> dots[128];
     __shared__ T red[32];
+    __shared__ T s_inv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t tot = (size_t)Sx * m;
+    if (staged) {
+        for (size_t e0 = threadIdx.x; e0 < tot; e0 += 4 * blockDim.x) {
+            cplx<T> t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const size_t e = e0 + (size_t)u * blockDim.x;
+                if (e < tot) t[u] = Yg[e];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const size_t e = e0 + (size_t)u * blockDim.x;
+                if (e < tot) Y[e] = t[u];
+            }
+        }
+        __syncthreads();
+    }
     for (int j = 0; j < m; ++j) {
         for (int pass = 0; pass < 2 && j > 0; ++pass) {
             for (int k = warp; k < j; k += nw) {
@@ -379,57 +401,82 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m) {
         if (warp == 0) {
             T v = lane < nw ? red[lane] : (T)0;
             v = warp_sum(v);
-            if (lane == 0) red[0] = v;
+            if (lane == 0) {
+                const T nrm = sqrt(v);
+                s_inv = nrm > (T)0 ? (T)1 / nrm : (T)0;
+            }
         }
         __syncthreads();
-        const T nrm = sqrt(red[0]);
-        const T inv = nrm > (T)0 ? (T)1 / nrm : (T)0;
+        const T inv = s_inv;
         for (int x = threadIdx.x; x < Sx; x += blockDim.x) Y[(size_t)x * m + j] = inv * Y[(size_t)x * m + j];
         __syncthreads();
     }
+    if (staged)
+        for (size_t e = threadIdx.x; e < tot; e += blockDim.x) Yg[e] = Y[e];
 }
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s) {
     cudaMemcpyAsync(dev_ptr_scratch, Y, sizeof(cplx<T>*) * nq, cudaMemcpyHostToDevice, s);
-    k_qr<T><<<nq, 512, 0, s>>>(dev_ptr_scratch, Sx, m);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    const size_t bytes = sizeof(cplx<T>) * (size_t)Sx * m;
+    const int staged = bytes <= (size_t)(200 * 1024) - 2048;
+    k_qr<T><<<nq, 512, staged ? bytes : 0, s>>>(dev_ptr_scratch, Sx, m, staged);
     note_launch();
 }
 
 // ------------------------------------------------------ Hermitian eigen (FP64)
 // Eigenvalues (all, descending) and the r leading eigenvectors of the m x m Hermitian
-// Gram matrix G = Z^H Z of the sketch, in FP64, one CTA per matrix:
-//  1. Householder reduction to tridiagonal form, H_k = I - tau v v^H applied on both
-//     sides of the trailing block (w = tau A v, q = w - (tau/2)(v^H w) v,
-//     A <- A - v q^H - q v^H);
-//  2. a diagonal unitary scaling makes the tridiagonal real symmetric;
-//  3. every eigenvalue by bisection on Sturm counts (one thread each);
-//  4. the r leading eigenvectors by inverse iteration on the tridiagonal (pivoted LU),
-//     mapped back through the scaling and the reflectors.
+// Gram matrix G = Z^H Z of the sketch, in FP64, in two launches:
+//  1. (one CTA per matrix) Householder reduction to tridiagonal form, H_k = I - tau v v^H
+//     applied on both sides of the trailing block (w = tau A v, q = w - (tau/2)(v^H w) v,
+//     A <- A - v q^H - q v^H); a diagonal unitary scaling makes the tridiagonal real
+//     symmetric;
+//  2. (one warp per eigenvalue and matrix, spread over the SMs: FP64 is throughput-bound
+//     per SM) each eigenvalue by multisection on Sturm counts; the r leading eigenvectors
+//     by inverse iteration on the tridiagonal (pivoted LU), mapped back through the
+//     scaling and the reflectors.
 static constexpr int HE_MAX = 64;
 
 // Number of eigenvalues below x: sign changes of the leading principal minors
-// p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2} (Sturm sequence), rescaled by
-// powers of ten to stay in range; a vanishing minor counts as a sign change.  Division
-// free (FP64 division is expensive here).
+// p_0 = 1, p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2} (Sturm sequence).  Three FP64
+// operations per step: the sign test and the range check read the sign and exponent
+// bits with integer instructions, and the pair (p_i, p_{i-1}) is rescaled by an exact
+// power of two when it leaves [2^-400, 2^400].  A vanishing minor needs no special
+// case: p_{i+1} = -e^2 p_{i-1} then has the opposite sign of p_{i-1}, so the triple
+// counts one change whichever sign the zero is given.
 __device__ int sturm_count(const double* d, const double* e2, int m, double x) {
-    int c = 0;
     double pm = 1.0, p = d[0] - x;
-    if (p == 0.0) p = -1e-300;
-    if (p < 0.0) ++c;
+    int hp = __double2hiint(p);
+    int c = hp < 0;
     for (int i = 1; i < m; ++i) {
-        double pn = (d[i] - x) * p - e2[i - 1] * pm;
-        if (pn == 0.0) pn = -copysign(1e-300, p);
-        if ((pn < 0.0) != (p < 0.0)) ++c;
+        const double pn = fma(d[i] - x, p, -(e2[i - 1] * pm));
+        const int hn = __double2hiint(pn);
+        c += (hn ^ hp) < 0;
         pm = p;
         p = pn;
-        const double mx = fmax(fabs(p), fabs(pm));
-        if (mx > 1e150) { p *= 1e-150; pm *= 1e-150; }
-        else if (mx < 1e-150) { p *= 1e150; pm *= 1e150; }
+        hp = hn;
+        const int ex = max((hn >> 20) & 0x7ff, (__double2hiint(pm) >> 20) & 0x7ff);
+        if (ex > 1023 + 400) {
+            p *= 0x1p-400;
+            pm *= 0x1p-400;
+        } else if (ex < 1023 - 400 && ex > 0) {
+            p *= 0x1p+400;
+            pm *= 0x1p+400;
+        }
     }
     return c;
 }
 
-__global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, double* const* lamp, int m, int r) {
+// Stage 1, one block per matrix: Householder reduction of the Hermitian G to a real
+// symmetric tridiagonal T = D^H Q^H G Q D (d diagonal, eb >= 0 off-diagonal, D = diag
+// of unit phases).  Overwrites G with the workspace read by stage 2: reflector k in
+// row k (tau_k = 2 / ||v_k||^2), then d, eb, eb^2, tau (m doubles each) and D (m
+// complex) from offset m^2.
+__global__ void __launch_bounds__(256) k_heig_tri(c128* const* Gp, int m) {
     extern __shared__ __align__(16) unsigned char hsm[];
     c128* A = (c128*)hsm;                    // m x m working matrix
     c128* Vr = A + m * m;                    // reflector k stored in row k (length m-k-1)
@@ -441,7 +488,7 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
     c128* delta = (c128*)(e2 + m);           // m   diagonal unitary scaling
     __shared__ c128 s_beta, s_K;
     __shared__ double s_tau;
-    const c128* G = Gp[blockIdx.x];
+    c128* G = Gp[blockIdx.x];
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) A[t] = G[t];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -516,54 +563,79 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
         }
     }
     __syncthreads();
-    // Gershgorin interval
-    double lo0 = 0.0, hi0 = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const double rad = (i > 0 ? eb[i - 1] : 0.0) + (i + 1 < m ? eb[i] : 0.0);
-        lo0 = i ? fmin(lo0, d[i] - rad) : d[i] - rad;
-        hi0 = i ? fmax(hi0, d[i] + rad) : d[i] + rad;
-    }
-    const double span = fmax(hi0 - lo0, 1e-300);
-    lo0 -= 1e-12 * span;
-    hi0 += 1e-12 * span;
-    double* lam = lamp[blockIdx.x];
-    // multisection: 8 threads per eigenvalue probe 8 interior points of its bracket per
-    // round (Sturm counts), shrinking the bracket by a factor 9 per round
-    {
-        const int sub = threadIdx.x & 7;
-        for (int kk0 = 0; kk0 < m; kk0 += (int)(blockDim.x >> 3)) {
-            const int kk = kk0 + (threadIdx.x >> 3);
-            const bool act = kk < m;
-            const int j = m - 1 - (act ? kk : 0);   // ascending index of the kk-th largest
-            double lo = lo0, hi = hi0;
-            for (int it = 0; it < 40; ++it) {
-                const double x = lo + (hi - lo) * (sub + 1) / 9.0;
-                const bool above = act && sturm_count(d, e2, m, x) > j;   // eigenvalue below x
-                const unsigned mask = __ballot_sync(0xffffffffu, above);
-                const unsigned mine = (mask >> ((threadIdx.x & 31) & ~7)) & 0xffu;
-                // first probe with count > j bounds from above; the one before from below
-                const int first = mine ? __ffs(mine) - 1 : 8;
-                const double nlo = lo + (hi - lo) * first / 9.0;
-                const double nhi = first < 8 ? lo + (hi - lo) * (first + 1) / 9.0 : hi;
-                lo = nlo;
-                hi = nhi;
-                // every lane takes part in the ballot: leave together
-                // absolute accuracy eps * ||G|| is all the selection and the singular
-                // values need (the Gram matrix squares the sketch's dynamic range)
-                const bool done = !act || hi - lo <= 2e-16 * span;
-                if (__all_sync(0xffffffffu, done)) break;
-            }
-            if (act && sub == 0) lam[kk] = 0.5 * (lo + hi);
+    // write the workspace (G is no longer needed)
+    double* ws = (double*)(G + (size_t)m * m);
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) G[t] = Vr[t];
+    if (threadIdx.x == 0) {
+        // Gershgorin interval of T
+        double lo0 = 0.0, hi0 = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double rad = (i > 0 ? eb[i - 1] : 0.0) + (i + 1 < m ? eb[i] : 0.0);
+            lo0 = i ? fmin(lo0, d[i] - rad) : d[i] - rad;
+            hi0 = i ? fmax(hi0, d[i] + rad) : d[i] + rad;
         }
+        ws[6 * m] = lo0;
+        ws[6 * m + 1] = hi0;
     }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        ws[i] = d[i];
+        ws[m + i] = eb[i];
+        ws[2 * m + i] = e2[i];
+        ws[3 * m + i] = tau[i];
+        ((c128*)(ws + 4 * m))[i] = delta[i];
+    }
+}
+
+// Stage 2, one block of four warps per (eigenvalue, matrix): the kk-th largest
+// eigenvalue of T by multisection (128 Sturm-count probes per round, one per thread, so
+// that each SM's four FP64 pipes work); for kk < r also its eigenvector (warp 0):
+// inverse iteration with a pivoted tridiagonal LU (three steps from a fixed start),
+// then u = Q D y by the reflectors in reverse.
+static constexpr int HV_THREADS = 128;
+__global__ void __launch_bounds__(HV_THREADS) k_heig_vec(c128* const* Gp, c128* const* Up, double* const* lamp,
+                                                         int m, int r) {
+    __shared__ double d[HE_MAX], eb[HE_MAX], e2[HE_MAX], tau[HE_MAX];
+    __shared__ c128 delta[HE_MAX], u[HE_MAX];
+    __shared__ double dg[HE_MAX], up[HE_MAX], up2[HE_MAX], lo[HE_MAX], y[HE_MAX];
+    __shared__ bool sw[HE_MAX];
+    __shared__ unsigned s_mask[HV_THREADS / 32];
+    const int kk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const c128* Vr = Gp[blockIdx.y];
+    const double* ws = (const double*)(Vr + (size_t)m * m);
+    for (int i = tid; i < m; i += HV_THREADS) {
+        d[i] = ws[i];
+        eb[i] = ws[m + i];
+        e2[i] = ws[2 * m + i];
+        tau[i] = ws[3 * m + i];
+        delta[i] = ((const c128*)(ws + 4 * m))[i];
+    }
+    const double lo0 = ws[6 * m], hi0 = ws[6 * m + 1];
     __syncthreads();
-    c128* U = Up[blockIdx.x];
-    c128* Us = A;   // reuse the working matrix as U (m x r) during back-transformation
-    for (int kk = threadIdx.x; kk < r; kk += blockDim.x) {
-        const double l = lam[kk];
+    const double span = fmax(hi0 - lo0, 1e-300);
+    double blo = lo0 - 1e-12 * span, bhi = hi0 + 1e-12 * span;
+    // thread t probes lo + (t + 1) (hi - lo) / 129; the bracket shrinks 129x per round.
+    // Absolute accuracy 2e-16 ||T|| is what the selection and the singular values need.
+    const int j = m - 1 - kk;                 // ascending index of the kk-th largest
+    for (int it = 0; it < 12 && bhi - blo > 2e-16 * span; ++it) {
+        const double step = (bhi - blo) * (1.0 / (HV_THREADS + 1));
+        const bool above = sturm_count(d, e2, m, blo + step * (tid + 1)) > j;   // eigenvalue below x
+        const unsigned mask = __ballot_sync(0xffffffffu, above);
+        if (lane == 0) s_mask[warp] = mask;
+        __syncthreads();
+        int first = HV_THREADS;
+        for (int w = HV_THREADS / 32 - 1; w >= 0; --w)
+            if (s_mask[w]) first = w * 32 + __ffs(s_mask[w]) - 1;
+        __syncthreads();
+        const double nlo = blo + step * first;
+        const double nhi = first < HV_THREADS ? blo + step * (first + 1) : bhi;
+        blo = nlo;
+        bhi = nhi;
+    }
+    const double l = 0.5 * (blo + bhi);
+    if (tid == 0) lamp[blockIdx.y][kk] = l;
+    if (kk >= r || warp != 0) return;
+    if (lane == 0) {
         const double mu = l + 1e-14 * fmax(fabs(l), span * 1e-3);
-        double dg[HE_MAX], up[HE_MAX], up2[HE_MAX], lo[HE_MAX], y[HE_MAX];
-        bool sw[HE_MAX];
         for (int i = 0; i < m; ++i) {
             dg[i] = d[i] - mu;
             up[i] = i + 1 < m ? eb[i] : 0.0;
@@ -574,12 +646,12 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
             const double sub = eb[i];
             if (fabs(dg[i]) >= fabs(sub)) {
                 sw[i] = false;
-                const double f = dg[i] != 0.0 ? sub / dg[i] : 0.0;
+                const double f = dg[i] != 0.0 ? sub * __drcp_rn(dg[i]) : 0.0;
                 lo[i] = f;
                 dg[i + 1] -= f * up[i];
             } else {
                 sw[i] = true;
-                const double f = dg[i] / sub;
+                const double f = dg[i] * __drcp_rn(sub);
                 dg[i] = sub;
                 lo[i] = f;
                 const double t = up[i];
@@ -591,7 +663,7 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
                 }
             }
         }
-        for (int i = 0; i < m; ++i) dg[i] = 1.0 / (fabs(dg[i]) < 1e-300 ? 1e-300 : dg[i]);   // reciprocals
+        for (int i = 0; i < m; ++i) dg[i] = __drcp_rn(fabs(dg[i]) < 1e-300 ? 1e-300 : dg[i]);   // reciprocals
         for (int it = 0; it < 3; ++it) {
             for (int i = 0; i + 1 < m; ++i) {
                 if (!sw[i]) y[i + 1] -= lo[i] * y[i];
@@ -605,31 +677,23 @@ __global__ void __launch_bounds__(256) k_heig(c128* const* Gp, c128* const* Up, 
             nr = nr > 0.0 ? rsqrt(nr) : 1.0;
             for (int i = 0; i < m; ++i) y[i] *= nr;
         }
-        for (int i = 0; i < m; ++i) Us[i * r + kk] = y[i] * delta[i];
     }
-    __syncthreads();
-    // u = Q D y with Q = H_0 ... H_{m-3}: reflectors applied in reverse, all vectors at
-    // once (a warp per vector for the projections)
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) u[i] = y[i] * delta[i];
+    __syncwarp();
+    // u = Q D y with Q = H_0 ... H_{m-3}: reflectors applied in reverse
     for (int k = m - 3; k >= 0; --k) {
         const int n = m - k - 1;
-        const c128* v = Vr + k * m;
-        for (int kk = warp; kk < r; kk += (blockDim.x >> 5)) {
-            c128 s = {0.0, 0.0};
-            for (int i = lane; i < n; i += 32) cfma_cj(s, v[i], Us[(k + 1 + i) * r + kk]);
-            s = warp_sum(s);
-            if (lane == 0) w[kk] = tau[k] * s;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < n * r; t += blockDim.x) {
-            const int i = t / r, kk = t - (t / r) * r;
-            Us[(k + 1 + i) * r + kk] = Us[(k + 1 + i) * r + kk] - v[i] * w[kk];
-        }
-        __syncthreads();
+        const c128* v = Vr + (size_t)k * m;
+        c128 s = {0.0, 0.0};
+        for (int i = lane; i < n; i += 32) cfma_cj(s, v[i], u[k + 1 + i]);
+        s = tau[k] * warp_sum(s);
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) u[k + 1 + i] = u[k + 1 + i] - v[i] * s;
+        __syncwarp();
     }
-    for (int t = threadIdx.x; t < m * r; t += blockDim.x) {
-        const int i = t / r, kk = t - (t / r) * r;
-        U[i * m + kk] = Us[i * r + kk];
-    }
+    c128* U = Up[blockIdx.y];
+    for (int i = lane; i < m; i += 32) U[(size_t)i * m + kk] = u[i];
 }
 
 void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int m, int r, void** scratch,
@@ -640,11 +704,13 @@ void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int
     const size_t sm = sizeof(c128) * (2 * (size_t)m * m + m) + sizeof(double) * 4 * m + sizeof(c128) * m + 64;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_heig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_heig_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_heig<<<nq, 256, sm, s>>>((c128* const*)scratch, (c128* const*)(scratch + nq), (double* const*)(scratch + 2 * nq),
-                              m, r);
+    k_heig_tri<<<nq, 256, sm, s>>>((c128* const*)scratch, m);
+    note_launch();
+    k_heig_vec<<<dim3(m, nq), HV_THREADS, 0, s>>>((c128* const*)scratch, (c128* const*)(scratch + nq),
+                                          (double* const*)(scratch + 2 * nq), m, r);
     note_launch();
 }
 
@@ -675,14 +741,18 @@ void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* 
 // ------------------------------------------------------- Gauss-Jordan (FP64)
 // In-place inverse with partial pivoting: row interchanges during elimination, the
 // inverse's columns unscrambled in reverse order at the end.
-__global__ void __launch_bounds__(256) k_gj_inverse(c128* A, int n, int* err) {
+// One block per matrix.  The pivot's reciprocal is formed once per step (thread 0) and
+// shared: FP64 division is a long instruction sequence on the narrow FP64 pipe.
+__global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
     extern __shared__ c128 sg[];
+    c128* A = bt.A[blockIdx.x];
+    const int n = bt.n;
     c128* M = sg;
     c128* col = M + n * n;
     c128* row = col + n;
     int* perm = (int*)(row + n);
     __shared__ int piv;
-    __shared__ c128 pv, akk;
+    __shared__ c128 pv, akk, s_ip;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = A[e];
     __syncthreads();
     for (int k = 0; k < n; ++k) {
@@ -701,17 +771,19 @@ __global__ void __launch_bounds__(256) k_gj_inverse(c128* A, int n, int* err) {
             if (threadIdx.x == 0) {
                 piv = bi;
                 perm[k] = bi;
-                pv = M[bi * n + k];
+                c128 pk = M[bi * n + k];
                 akk = M[k * n + k];
                 if (!(best > 0.0) || !isfinite(best)) {
-                    atomicExch(err, DEV_BREAKDOWN);
-                    pv = c128{1.0, 0.0};
+                    atomicExch(bt.err, DEV_BREAKDOWN);
+                    pk = c128{1.0, 0.0};
                 }
+                pv = pk;
+                s_ip = cinv(pk);
             }
         }
         __syncthreads();
         const int p = piv;
-        const c128 ip = cinv(pv);
+        const c128 ip = s_ip;
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             col[t] = (t == k) ? pv : (t == p ? akk : M[t * n + k]);
             const c128 rp = M[p * n + t];
@@ -720,7 +792,7 @@ __global__ void __launch_bounds__(256) k_gj_inverse(c128* A, int n, int* err) {
         }
         __syncthreads();
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int r = e / n, c = e % n;
+            const int r = e / n, c = e - r * n;
             if (r == k) {
                 M[e] = (c == k) ? ip : row[c];
             } else {
@@ -741,18 +813,20 @@ __global__ void __launch_bounds__(256) k_gj_inverse(c128* A, int n, int* err) {
     __syncthreads();
     const int* pos = perm + n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int r = e / n, c = e % n;
+        const int r = e / n, c = e - r * n;
         A[e] = M[r * n + pos[c]];
     }
 }
-void launch_gj_inverse(c128* A, int n, int* err, cudaStream_t s) {
+void launch_gj_inverse(const GjBatch& bt, int count, cudaStream_t s) {
+    if (count < 1) return;
+    const int n = bt.n;
     const size_t sm = sizeof(c128) * (n * n + 2 * n) + sizeof(int) * 2 * n;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_gj_inverse<<<1, 256, sm, s>>>(A, n, err);
+    k_gj_inverse<<<count, 256, sm, s>>>(bt);
     note_launch();
 }
 

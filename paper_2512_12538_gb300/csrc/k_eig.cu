@@ -465,29 +465,31 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
 }
 
 // ------------------------------------------------------- fused one-vector sweep
-// The whole leaf solve for one right-hand side in one launch: one cluster of FS_CL CTAs
-// per leaf.  CTA q of the cluster owns the columns [q ncol, (q + 1) ncol) and the modes
-// [q nmode, (q + 1) nmode).
+// The whole leaf solve for one right-hand side in one launch: one cluster of CL CTAs
+// per leaf (CL = 16 where the GPU schedules such clusters, else 8).  CTA q of the
+// cluster owns the columns [q ncol, (q + 1) ncol) and the modes [q nmode, (q + 1) nmode).
 //   1. f^[m][i] = sum_a V[a][m] f[a][i] for all m and the CTA's columns (V and f staged
 //      in shared memory);
 //   2. cluster barrier; each warp takes one owned mode, gathers its line f^[m][0..Sx)
 //      from the CTAs' shared memory (distributed shared memory), runs both recursions
 //      and writes x^[m][.] back in place; cluster barrier;
-//   3. x[a][i] = sum_m V[a][m] x^[m][i] for the CTA's columns, written to the leaf output.
+//   3. x[a][i] = sum_m V[a][m] x^[m][i] for the CTA's columns, written to the leaf output
+//      (only the rows [w0, w1) the caller asked for: the owned rows, when the output goes
+//      straight into the parent's prolongation).
 // V stays in shared memory between the two transforms and the transformed vectors never
-// leave the cluster.  2 x 2 register tiles: two 16-byte shared loads per four complex
-// multiply-adds (complex64).
-static constexpr int FS_CL = 8, FS_THREADS = 256, FS_WARPS = FS_THREADS / 32;
+// leave the cluster.  4 x 2 register tiles: three 16-byte shared loads per eight complex
+// multiply-adds (complex64) in phase 1, five loads in phase 3.
+static constexpr int FS_THREADS = 256, FS_WARPS = FS_THREADS / 32;
 
 struct FsGeom {
     int ncol, nmode, ldv, ldf;
     size_t elems;
 };
-HH_HD FsGeom fs_geom(int b, int Sx) {
+HH_HD FsGeom fs_geom(int b, int Sx, int cl) {
     FsGeom g;
-    g.ncol = (Sx + FS_CL - 1) / FS_CL;
-    g.nmode = (b + FS_CL - 1) / FS_CL;
-    g.ldv = b + (b & 1);
+    g.ncol = (Sx + cl - 1) / cl;
+    g.nmode = (b + cl - 1) / cl;
+    g.ldv = (b + 3) & ~3;
     g.ldf = g.ncol + (g.ncol & 1);
     const size_t fin = (size_t)b * g.ldf, lines = (size_t)FS_WARPS * 2 * Sx;
     g.elems = (size_t)b * g.ldv + (size_t)b * g.ldf + (fin > lines ? fin : lines);
@@ -500,18 +502,18 @@ struct alignas(2 * sizeof(cplx<T>)) cpair {
 };
 
 template <typename T>
-__global__ void __cluster_dims__(FS_CL, 1, 1) __launch_bounds__(FS_THREADS)
-    k_eig_sweep_fused(const EigTask* __restrict__ tasks, int Sx) {
+__global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* __restrict__ tasks, int Sx) {
     using C = cplx<T>;
     using C2 = cpair<T>;
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
+    const int cl = (int)cluster.num_blocks();
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
-    const FsGeom G = fs_geom(b, Sx);
+    const FsGeom G = fs_geom(b, Sx, cl);
     const int c0 = q * G.ncol;
     const int nown = max(0, min(Sx, c0 + G.ncol) - c0);
-    extern __shared__ __align__(16) unsigned char fsm[];
+    extern __shared__ __align__(128) unsigned char fsm[];
     C* Vs = (C*)fsm;                              // [b][ldv], V[a][m]
     C* Fs = Vs + (size_t)b * G.ldv;               // [b][ldf], f^ then x^ of own columns
     C* Fin = Fs + (size_t)b * G.ldf;              // [b][ldf], f of own columns (phase 1)
@@ -521,31 +523,57 @@ __global__ void __cluster_dims__(FS_CL, 1, 1) __launch_bounds__(FS_THREADS)
     C* Wout = (C*)tk.W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (int e = threadIdx.x; e < b * b; e += FS_THREADS) {
-        const int a = e / b, m = e - a * b;
-        Vs[a * G.ldv + m] = V[e];
-    }
-    for (int e = threadIdx.x; e < b * G.ldf; e += FS_THREADS) {
-        const int a = e / G.ldf, il = e - a * G.ldf;
-        Fin[e] = il < nown ? F[(size_t)a * Sx + c0 + il] : C{0, 0};
+    // stage V and the own columns of f: eight loads in flight per thread
+    const int nv = b * b, nf = b * G.ldf;
+    for (int e0 = threadIdx.x; e0 < nv + nf; e0 += 8 * FS_THREADS) {
+        C tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * FS_THREADS;
+            tmp[u] = C{0, 0};
+            if (e < nv) {
+                tmp[u] = V[e];
+            } else if (e < nv + nf) {
+                const int a = (e - nv) / G.ldf, il = (e - nv) - a * G.ldf;
+                if (il < nown) tmp[u] = F[(size_t)a * Sx + c0 + il];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * FS_THREADS;
+            if (e < nv) {
+                const int a = e / b, m = e - a * b;
+                Vs[a * G.ldv + m] = tmp[u];
+            } else if (e < nv + nf) {
+                Fin[e - nv] = tmp[u];
+            }
+        }
     }
     __syncthreads();
 
-    const int ntc = (nown + 1) / 2, ntm = (b + 1) / 2;
-    // phase 1: tiles (modes m0, m0 + 1) x (columns i0, i0 + 1)
+    const int ntc = (nown + 1) / 2, ntm = (b + 3) / 4;
+    // phase 1: tiles (modes m0 .. m0 + 3) x (columns i0, i0 + 1)
     for (int t = threadIdx.x; t < ntm * ntc; t += FS_THREADS) {
-        const int m0 = 2 * (t / ntc), i0 = 2 * (t % ntc);
-        C a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
+        const int m0 = 4 * (t / ntc), i0 = 2 * (t % ntc);
+        C acc[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = C{0, 0};
         for (int k = 0; k < b; ++k) {
-            const C2 v = *(const C2*)(Vs + k * G.ldv + m0);
+            const C2 v01 = *(const C2*)(Vs + k * G.ldv + m0);
+            const C2 v23 = *(const C2*)(Vs + k * G.ldv + m0 + 2);
             const C2 f = *(const C2*)(Fin + k * G.ldf + i0);
-            cfma(a00, v.x, f.x);
-            cfma(a01, v.x, f.y);
-            cfma(a10, v.y, f.x);
-            cfma(a11, v.y, f.y);
+            cfma(acc[0][0], v01.x, f.x);
+            cfma(acc[0][1], v01.x, f.y);
+            cfma(acc[1][0], v01.y, f.x);
+            cfma(acc[1][1], v01.y, f.y);
+            cfma(acc[2][0], v23.x, f.x);
+            cfma(acc[2][1], v23.x, f.y);
+            cfma(acc[3][0], v23.y, f.x);
+            cfma(acc[3][1], v23.y, f.y);
         }
-        *(C2*)(Fs + m0 * G.ldf + i0) = C2{a00, a01};
-        if (m0 + 1 < b) *(C2*)(Fs + (m0 + 1) * G.ldf + i0) = C2{a10, a11};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (m0 + u < b) *(C2*)(Fs + (m0 + u) * G.ldf + i0) = C2{acc[u][0], acc[u][1]};
     }
     cluster.sync();
 
@@ -574,44 +602,83 @@ __global__ void __cluster_dims__(FS_CL, 1, 1) __launch_bounds__(FS_THREADS)
     }
     cluster.sync();
 
-    // phase 3: tiles (rows a0, a0 + 1) x (columns i0, i0 + 1), written to the output
+    // phase 3: tiles (rows a0 .. a0 + 3) x (columns i0, i0 + 1), written to the output
     for (int t = threadIdx.x; t < ntm * ntc; t += FS_THREADS) {
-        const int a0 = 2 * (t / ntc), i0 = 2 * (t % ntc);
-        const int a1 = min(a0 + 1, b - 1);
-        C a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
+        const int a0 = 4 * (t / ntc), i0 = 2 * (t % ntc);
+        const C* vr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vr[u] = Vs + min(a0 + u, b - 1) * G.ldv;
+        C acc[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = C{0, 0};
         for (int k = 0; k < b; ++k) {
-            const C v0 = Vs[a0 * G.ldv + k], v1 = Vs[a1 * G.ldv + k];
             const C2 f = *(const C2*)(Fs + k * G.ldf + i0);
-            cfma(a00, v0, f.x);
-            cfma(a01, v0, f.y);
-            cfma(a10, v1, f.x);
-            cfma(a11, v1, f.y);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const C v = vr[u][k];
+                cfma(acc[u][0], v, f.x);
+                cfma(acc[u][1], v, f.y);
+            }
         }
-        C* w0 = Wout + (size_t)a0 * Sx + c0 + i0;
-        w0[0] = a00;
-        if (i0 + 1 < nown) w0[1] = a01;
-        if (a0 + 1 < b) {
-            C* w1 = w0 + Sx;
-            w1[0] = a10;
-            if (i0 + 1 < nown) w1[1] = a11;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (a0 + u >= tk.w0 && a0 + u < tk.w1) {
+                C* wr = Wout + (size_t)(a0 + u - tk.w0) * Sx + c0 + i0;
+                wr[0] = acc[u][0];
+                if (i0 + 1 < nown) wr[1] = acc[u][1];
+            }
         }
     }
 }
 
 template <typename T>
-bool eig_sweep_fused_ready(int b_max, int Sx) {
-    if (Sx < FS_CL || sizeof(cplx<T>) * fs_geom(b_max, Sx).elems > (size_t)FS_SMEM_MAX) return false;
-    static bool attr = false;
-    if (!attr)
-        attr = cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    FS_SMEM_MAX) == cudaSuccess;
-    return attr;
+static cudaLaunchConfig_t fs_config(int cl, int ntasks, size_t sm, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl, ntasks);
+    cfg.blockDim = dim3(FS_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
 template <typename T>
-void launch_eig_sweep_fused(const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s) {
-    const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx).elems;
-    k_eig_sweep_fused<T><<<dim3(FS_CL, ntasks), FS_THREADS, sm, s>>>(d_tasks, Sx);
+int eig_sweep_fused_ready(int b_max, int Sx) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_SMEM_MAX) !=
+            cudaSuccess)
+            return 0;
+        // clusters of 16 are beyond the portable size; allowed where the GPU supports them
+        if (cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+            cudaGetLastError();
+        attr_set = true;
+    }
+    for (int cl : {16, 8}) {
+        if (Sx < cl) continue;
+        const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx, cl).elems;
+        if (sm > (size_t)FS_SMEM_MAX) continue;
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = fs_config<T>(cl, 1, sm, nullptr, at);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_eig_sweep_fused<T>, &cfg) == cudaSuccess && n > 0) return cl;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+template <typename T>
+void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s) {
+    const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx, cl).elems;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = fs_config<T>(cl, ntasks, sm, s, at);
+    cudaLaunchKernelEx(&cfg, k_eig_sweep_fused<T>, d_tasks, Sx);
     note_launch();
 }
 
@@ -624,9 +691,9 @@ template void launch_eig_sweep<float>(const EigTask*, int, int, int, int, cudaSt
 template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep<double>(const EigTask*, int, int, int, int, cudaStream_t);
-template void launch_eig_sweep_fused<float>(const EigTask*, int, int, int, cudaStream_t);
-template void launch_eig_sweep_fused<double>(const EigTask*, int, int, int, cudaStream_t);
-template bool eig_sweep_fused_ready<float>(int, int);
-template bool eig_sweep_fused_ready<double>(int, int);
+template void launch_eig_sweep_fused<float>(int, const EigTask*, int, int, int, cudaStream_t);
+template void launch_eig_sweep_fused<double>(int, const EigTask*, int, int, int, cudaStream_t);
+template int eig_sweep_fused_ready<float>(int, int);
+template int eig_sweep_fused_ready<double>(int, int);
 
 }  // namespace hh

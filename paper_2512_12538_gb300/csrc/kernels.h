@@ -93,15 +93,23 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s);
 // Hermitian eigenproblems of nq m x m FP64 matrices (m <= 64): all eigenvalues
-// descending in lam, the r leading eigenvectors in columns 0..r-1 of U (m x m).
+// descending in lam, the r leading eigenvectors in columns 0..r-1 of U (m x m).  Each G
+// holds m^2 + 4m complex entries; the matrix is destroyed (used as workspace).
 void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int m, int r,
                  void** dev_ptr_scratch, cudaStream_t s);
 // V[x][j] = sum_k Z[x][k] U[k][j] / sqrt(lam_j)  for j < r
 template <typename T>
 void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* V, int Sx, int m, int r,
                    cudaStream_t s);
-// In-place Gauss-Jordan inverse with partial pivoting of an n x n FP64 matrix.
-void launch_gj_inverse(c128* A, int n, int* err, cudaStream_t s);
+// In-place Gauss-Jordan inverses with partial pivoting of `count` n x n FP64 matrices
+// A[0..count) (count <= GJ_MAX_BATCH), one launch.
+constexpr int GJ_MAX_BATCH = 32;
+struct GjBatch {
+    c128* A[GJ_MAX_BATCH];
+    int n;
+    int* err;
+};
+void launch_gj_inverse(const GjBatch& bt, int count, cudaStream_t s);
 
 // ---- leaf kernels (k_leaf.cu) ------------------------------------------------------
 struct LeafTask {
@@ -129,6 +137,8 @@ struct EigTask {
     void* W;          // solutions [b][Sx][nrhs]
     void* work;       // set-up workspace, eig_work_elems(b) complex128 (used as complex<T>)
     int b;
+    int w0, w1;       // the one-launch sweep writes local rows [w0, w1) only, row a to
+                      // W + (a - w0) Sx (the three-stage sweep: all rows, w0 = 0, w1 = b)
 };
 template <typename T>
 void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,
@@ -137,13 +147,14 @@ template <typename T>
 void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s);
 // One right-hand side (nrhs = 1, F/W [b][Sx]): the three stages in one launch, one
 // thread-block cluster per leaf.  eig_sweep_fused_ready (call outside stream capture)
-// says whether leaves of up to b_max rows fit the cluster's shared memory and prepares
-// the kernel; when it returns false the caller runs the three stages instead.
+// prepares the kernel and returns the cluster size to launch with (16 or 8), or 0 when
+// leaves of up to b_max rows do not fit a cluster's shared memory; the caller then runs
+// the three stages instead.
 constexpr int FS_SMEM_MAX = 220 * 1024;
 template <typename T>
-bool eig_sweep_fused_ready(int b_max, int Sx);
+int eig_sweep_fused_ready(int b_max, int Sx);
 template <typename T>
-void launch_eig_sweep_fused(const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s);
+void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s);
 // stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^
 template <typename T>
 void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
