@@ -258,6 +258,7 @@ struct Solver final : SolverBase {
     // device buffers
     std::vector<CT*> W, R, Vs, C, X, Om, Z, Vc;
     std::vector<c128*> Ainv, ycoef, Gm, U;
+    std::vector<CT*> AinvT;      // A_c^{-1} in the basis precision (the one-column correction)
     std::vector<double*> lam;
     std::vector<int> ldx;
     c128 *u = nullptr, *ut = nullptr, *bvec = nullptr, *res = nullptr, *gbuf = nullptr;
@@ -341,6 +342,7 @@ struct Solver final : SolverBase {
         W.assign(nn, nullptr); R.assign(nn, nullptr); Vs.assign(nn, nullptr); C.assign(nn, nullptr);
         X.assign(nn, nullptr); Om.assign(nn, nullptr); Z.assign(nn, nullptr); Vc.assign(nn, nullptr);
         Ainv.assign(nn, nullptr); ycoef.assign(nn, nullptr); Gm.assign(nn, nullptr); U.assign(nn, nullptr);
+        AinvT.assign(nn, nullptr);
         lam.assign(nn, nullptr); ldx.assign(nn, 0);
         EV.assign(nn, nullptr); EXI.assign(nn, nullptr); EFh.assign(nn, nullptr);
         ELAM.assign(nn, nullptr); EWK.assign(nn, nullptr);
@@ -365,6 +367,7 @@ struct Solver final : SolverBase {
                 if (id != 0) R[id] = a.take<CT>(np * nmax);
                 C[id] = a.take<CT>(np * 2 * r);
                 Ainv[id] = a.take<c128>((size_t)4 * r * r);
+                AinvT[id] = sizeof(CT) == sizeof(c128) ? (CT*)Ainv[id] : a.take<CT>((size_t)4 * r * r);
                 ycoef[id] = a.take<c128>((size_t)2 * r * nmax);
             } else if (eig) {
                 const int b = nd.b();
@@ -635,12 +638,11 @@ struct Solver final : SolverBase {
     // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
     void coarse_correct(int p, const CT* vin, int nc) {
         if (nc == 1) {
-            // reads C (2r x N), v and w (N each)
-            pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + 2.0) * sizeof(CT), 8.0 * 2 * r * pts(p));
-            launch_coarse_proj1<T, T, T>(C[p], vin, W[p], geom(p), 2 * r, partial, dcounter, Ainv[p], ycoef[p],
-                                         stream);
+            // algorithmic: C (2r x N) once, v and w read, w written; C^H r and C y
+            pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT), 2.0 * 8.0 * 2 * r * pts(p));
+            launch_coarse_fused<T, T, T>(C[p], vin, W[p], W[p], true, geom(p), 2 * r, partial, dcounter + 2, derr,
+                                         AinvT[p], ycoef[p], stream);
             pend();
-            launch_coarse_upd1<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, stream);
             return;
         }
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
@@ -727,6 +729,8 @@ struct Solver final : SolverBase {
         int cnt = 0;
         for (int p : lev[l - 1]) bt.A[cnt++] = Ainv[p];
         launch_gj_inverse(bt, cnt, stream);
+        if (sizeof(CT) != sizeof(c128))
+            for (int p : lev[l - 1]) launch_copy<double, T>(Ainv[p], AinvT[p], (size_t)4 * r * r, false, false, stream);
     }
 
     hh_status setup() override {
@@ -789,11 +793,10 @@ struct Solver final : SolverBase {
             launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), out + row_off(0, cn.own_a, 1),
                                    (size_t)(cn.own_b - cn.own_a) * Sx, base != nullptr, false, stream);
         }
-        pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 2.0 * sizeof(c128)), 8.0 * 2 * r * N);
-        launch_coarse_proj1<T, double, double>(C[0], rhs, out, geom(0), 2 * r, partial, dcounter, Ainv[0],
-                                               ycoef[0], stream);
+        pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
+        launch_coarse_fused<T, double, double>(C[0], rhs, out, out, true, geom(0), 2 * r, partial, dcounter + 2, derr,
+                                               AinvT[0], ycoef[0], stream);
         pend();
-        launch_coarse_upd1<T, double>(C[0], ycoef[0], out, N, 2 * r, stream);
     }
 
     hh_status norm_sq(const c128* x, double* dst) {
@@ -1093,10 +1096,8 @@ struct Solver final : SolverBase {
 
     hh_status coarse_apply(int p, const c128* rr, c128* z) override {
         if (!valid_node(p) || nodes[p].leaf() || !rr || !z) return HH_EINVAL;
-        launch_coarse_proj1<T, double, double>(C[p], rr, nullptr, geom(p), 2 * r, partial, dcounter, Ainv[p],
-                                               ycoef[p], stream);
-        zero(z, sizeof(c128) * pts(p));
-        launch_coarse_upd1<T, double>(C[p], ycoef[p], z, pts(p), 2 * r, stream);
+        launch_coarse_fused<T, double, double>(C[p], rr, nullptr, z, false, geom(p), 2 * r, partial, dcounter + 2, derr,
+                                               AinvT[p], ycoef[p], stream);
         hh_status st;
         sync_check(st);
         return st;

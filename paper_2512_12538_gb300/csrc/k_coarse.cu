@@ -2,6 +2,8 @@
 // with the coarse basis stored column-major: C[j * N + pt], j < p = 2r, pt < N points of
 // the node's band, so that every kernel below reads C with consecutive threads on
 // consecutive points.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace hh {
@@ -55,6 +57,10 @@ __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;        // point in sub-tile, column group
     const int per = (p + 3) / 4, ja = jg * per, jb = min(p, ja + per);
+    // the last block needs A_c^{-1}: every block starts its copy into shared memory now,
+    // so that it has long arrived when the last block gets there
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) cp_async16(s_m + t, Minv + t);
+    cp_async_commit();
     CA acc[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = {0, 0};
@@ -110,14 +116,14 @@ __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict
         partial[(size_t)blockIdx.x * p + t] = cvt<double>(s);
     }
     __threadfence();
+    cp_async_wait_all();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
     __syncthreads();
     if (ticket != gridDim.x - 1) return;
     __threadfence();
-    // last block: stage Minv, then 8 threads per output add the blocks' partials (fixed
-    // order within each thread, then a fixed shuffle tree), loads bypassing L1 (__ldcg)
-    for (int t = threadIdx.x; t < p * p; t += blockDim.x) s_m[t] = Minv[t];
+    // last block: 8 threads per output add the blocks' partials (fixed order within each
+    // thread, then a fixed shuffle tree), loads bypassing L1 (__ldcg)
     // the loop bound is warp-uniform (every lane of a warp reaches the shuffles)
     const int sub = threadIdx.x & 7;
     for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
@@ -149,10 +155,17 @@ __global__ void __launch_bounds__(256) k_coarse_proj1(const cplx<TC>* __restrict
         if (ok && sub == 0) s_sum[j] = t;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    // y = A_c^{-1} s: 8 threads per output (k = sub, sub + 8, ...), fixed shuffle tree
+    for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
+        const int j = j0 + (threadIdx.x >> 3);
         c128 t = {0.0, 0.0};
-        for (int k = 0; k < p; ++k) cfma(t, s_m[j * p + k], s_sum[k]);
-        y[j] = t;
+        if (j < p)
+            for (int k = sub; k < p; k += 8) cfma(t, s_m[j * p + k], s_sum[k]);
+        for (int o = 4; o > 0; o >>= 1) {
+            t.re += __shfl_xor_sync(0xffffffffu, t.re, o);
+            t.im += __shfl_xor_sync(0xffffffffu, t.im, o);
+        }
+        if (j < p && sub == 0) y[j] = t;
     }
     if (threadIdx.x == 0) *counter = 0u;
 }
@@ -164,6 +177,220 @@ void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w
     // one block per SM at most: the last block's reduction reads grid x p partials
     const int grid = blocks_for(N, 256, 152);
     k_coarse_proj1<TC, TV, TW, TC><<<grid, 256, 0, s>>>(C, v, w, g, p, partial, counter, Minv, y);
+    note_launch();
+}
+
+// ------------------------------------------------------- fused one-column correction
+// Barrier over a cooperative grid (all blocks resident): arrive on a counter, the last
+// arriver resets it and advances the generation; the others wait on the generation with
+// a bounded spin (DEV_TIMEOUT and false after about a second).
+__device__ bool grid_barrier(unsigned* bar, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;            // no block touches the counter again before the generation moves
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g0) {
+                if (++it > (1ll << 24)) {
+                    atomicExch(err, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// w_out (+)= C A_c^{-1} C^H (v - A~ w_in) for one column in one cooperative launch
+// (Eq. (3)): phase 1 as the projection above (residual once per point in shared memory,
+// four column groups, per-block partial sums of C^H r in the basis precision); grid
+// barrier; phase 2: every block adds all blocks' partials in the same fixed order and
+// multiplies by A_c^{-1} (basis precision; the inverse was copied to shared memory while
+// phase 1 ran), so all blocks hold the same y; phase 3: each block updates the points it
+// projected (C re-read while still in cache).  w_in may be null (r = v); w_in may equal
+// w_out (the barrier separates every read of w_in from the writes).
+template <typename TC, typename TV, typename TW>
+__global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict__ C, const cplx<TV>* __restrict__ v,
+                                                      const cplx<TW>* w_in, cplx<TW>* w_out, int accumulate,
+                                                      OpGeom g, int p, cplx<TC>* partial, unsigned* bar, int* err,
+                                                      const cplx<TC>* __restrict__ Minv, c128* __restrict__ y) {
+    using CA = cplx<TC>;
+    using R = decltype(TV() + TW());
+    __shared__ CA red[8][16];
+    __shared__ CA s_r[256];
+    __shared__ CA s_sum[64];
+    __shared__ CA s_y[64];
+    __shared__ __align__(16) CA s_m[64 * 64];
+    const unsigned N = (unsigned)g.b * (unsigned)g.Sx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;
+    const int per = (p + 3) / 4, ja = jg * per, jb = min(p, ja + per);
+    {
+        const int chunks = (int)(sizeof(CA) * p * p / 16);
+        for (int t = threadIdx.x; t < chunks; t += blockDim.x)
+            cp_async16((char*)s_m + 16 * t, (const char*)Minv + 16 * t);
+        cp_async_commit();
+    }
+    CA acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = {0, 0};
+    for (unsigned base = blockIdx.x * 256u; base < N; base += gridDim.x * 256u) {
+        {
+            const unsigned pt = base + threadIdx.x;
+            CA ra = {0, 0};
+            if (pt < N) {
+                cplx<R> rv = cvt<R>(v[pt]);
+                if (w_in) {
+                    const int jr = (int)(pt / (unsigned)g.Sx), i = (int)(pt - (unsigned)jr * g.Sx);
+                    cplx<R> ax = op_diag_t<R>(jr, i, g) * cvt<R>(w_in[pt]);
+                    const R wj = (jr == 0 || jr == g.b - 1) ? (R)0.5 : (R)1;
+                    const R wi = g.Sx == 1 ? (R)1 : ((i == 0 || i == g.Sx - 1) ? (R)0.5 : (R)1);
+                    if (g.Sx > 1) {
+                        if (i > 0) ax = ax - wj * cvt<R>(w_in[pt - 1]);
+                        if (i < g.Sx - 1) ax = ax - wj * cvt<R>(w_in[pt + 1]);
+                    }
+                    if (jr > 0) ax = ax - wi * cvt<R>(w_in[pt - g.Sx]);
+                    if (jr < g.b - 1) ax = ax - wi * cvt<R>(w_in[pt + g.Sx]);
+                    rv = rv - ax;
+                }
+                ra = cvt<TC>(rv);
+            }
+            s_r[threadIdx.x] = ra;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int sub = 0; sub < 4; ++sub) {
+            const unsigned pt = base + sub * 64 + q;
+            if (pt < N) {
+                cplx<TC> cv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) cv[u] = (ja + u < jb) ? C[(size_t)(ja + u) * N + pt] : cplx<TC>{0, 0};
+                const CA ra = s_r[sub * 64 + q];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) cfma_cj(acc[u], cv[u], ra);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const CA t = warp_sum(acc[u]);
+        if (lane == 0) red[warp][u] = t;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < p; t += blockDim.x) {
+        const int grp = t / per, u = t - grp * per;
+        partial[(size_t)blockIdx.x * p + t] = red[2 * grp][u] + red[2 * grp + 1][u];
+    }
+    cp_async_wait_all();
+    if (!grid_barrier(bar, err)) return;
+    // phase 2: the same sums in every block: 8 threads per output, partials
+    // b = sub, sub + 8, ... in order, then a fixed shuffle tree
+    const int sub = threadIdx.x & 7;
+    for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
+        const int j = j0 + (threadIdx.x >> 3);
+        CA t0 = {0, 0}, t1 = {0, 0};
+        if (j < p) {
+            for (unsigned b0 = sub; b0 < gridDim.x; b0 += 64) {
+                CA a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const unsigned bb = b0 + 8u * u;
+                    a[u] = bb < gridDim.x ? partial[(size_t)bb * p + j] : CA{0, 0};
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    t0 = t0 + a[u];
+                    t1 = t1 + a[u + 1];
+                }
+            }
+        }
+        CA t = t0 + t1;
+        for (int o = 4; o > 0; o >>= 1) {
+            t.re += __shfl_xor_sync(0xffffffffu, t.re, o);
+            t.im += __shfl_xor_sync(0xffffffffu, t.im, o);
+        }
+        if (j < p && sub == 0) s_sum[j] = t;
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
+        const int j = j0 + (threadIdx.x >> 3);
+        CA t = {0, 0};
+        if (j < p)
+            for (int k = sub; k < p; k += 8) cfma(t, s_m[j * p + k], s_sum[k]);
+        for (int o = 4; o > 0; o >>= 1) {
+            t.re += __shfl_xor_sync(0xffffffffu, t.re, o);
+            t.im += __shfl_xor_sync(0xffffffffu, t.im, o);
+        }
+        if (j < p && sub == 0) {
+            s_y[j] = t;
+            if (blockIdx.x == 0) y[j] = cvt<double>(t);
+        }
+    }
+    __syncthreads();
+    // phase 3: one point per thread, all p columns (coalesced along the points)
+    for (unsigned base = blockIdx.x * 256u; base < N; base += gridDim.x * 256u) {
+        const unsigned pt = base + threadIdx.x;
+        if (pt >= N) continue;
+        CA a = {0, 0};
+        int j = 0;
+        for (; j + 8 <= p; j += 8) {
+            cplx<TC> cv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cv[u] = C[(size_t)(j + u) * N + pt];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cfma(a, cv[u], s_y[j + u]);
+        }
+        for (; j < p; ++j) cfma(a, C[(size_t)j * N + pt], s_y[j]);
+        const cplx<TW> add = cvt<TW>(a);
+        w_out[pt] = accumulate ? w_out[pt] + add : add;
+    }
+}
+
+template <typename TC, typename TV, typename TW>
+int coarse_fused_max_grid() {
+    static int mg = 0;
+    if (!mg) {
+        int dev = 0, sms = 0, nb = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_fused<TC, TV, TW>, 256, 0);
+        mg = std::max(1, std::min(nb, 1) * sms);   // one block per SM: phase 2 reads grid x p partials
+    }
+    return mg;
+}
+
+template <typename TC, typename TV, typename TW>
+void launch_coarse_fused(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w_in, cplx<TW>* w_out, bool accumulate,
+                         OpGeom g, int p, void* partial, unsigned* bar, int* err, const cplx<TC>* Minv, c128* y,
+                         cudaStream_t s) {
+    const size_t N = (size_t)g.b * g.Sx;
+    const int grid = blocks_for(N, 256, coarse_fused_max_grid<TC, TV, TW>());
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_coarse_fused<TC, TV, TW>, C, v, w_in, w_out, (int)accumulate, g, p, (cplx<TC>*)partial,
+                       bar, err, Minv, y);
     note_launch();
 }
 
@@ -234,6 +461,13 @@ template void launch_coarse_proj1<float, double, double>(const c64*, const c128*
                                                          unsigned*, const c128*, c128*, cudaStream_t);
 template void launch_coarse_proj1<double, double, double>(const c128*, const c128*, const c128*, OpGeom, int,
                                                           c128*, unsigned*, const c128*, c128*, cudaStream_t);
+template void launch_coarse_fused<float, float, float>(const c64*, const c64*, const c64*, c64*, bool, OpGeom, int,
+                                                       void*, unsigned*, int*, const c64*, c128*, cudaStream_t);
+template void launch_coarse_fused<float, double, double>(const c64*, const c128*, const c128*, c128*, bool, OpGeom, int,
+                                                         void*, unsigned*, int*, const c64*, c128*, cudaStream_t);
+template void launch_coarse_fused<double, double, double>(const c128*, const c128*, const c128*, c128*, bool, OpGeom,
+                                                          int, void*, unsigned*, int*, const c128*, c128*,
+                                                          cudaStream_t);
 template void launch_coarse_upd1<float, float>(const c64*, const c128*, c64*, size_t, int, cudaStream_t);
 template void launch_coarse_upd1<float, double>(const c64*, const c128*, c128*, size_t, int, cudaStream_t);
 template void launch_coarse_upd1<double, double>(const c128*, const c128*, c128*, size_t, int, cudaStream_t);

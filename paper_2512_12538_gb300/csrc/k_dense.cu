@@ -279,13 +279,18 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 
 // ------------------------------------------------------------------- Galerkin
 // partial[blk][a][l] = sum over the block's points of conj(C[pt][a]) * (A~ C)[pt][l].
+// The products and the stencil run in the basis precision T: FP64 for the FP64 form;
+// FP32 for the complex64 form, whose basis is itself rounded to FP32 (each 32-point
+// tile is summed in FP32 and added to FP64 accumulators, so the FP32 rounding stays at
+// the level of one tile's sum; FP64 on this GPU runs at 1/64 of the FP32 rate).
 template <typename T>
 __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* __restrict__ C, OpGeom g, int p,
                                                                  int split_row, c128* partial) {
-    extern __shared__ c128 sm[];
-    c128* As = sm;
-    c128* Bs = As + IP_TILE * p;
-    c128* red = Bs + IP_TILE * p;
+    using CT = cplx<T>;
+    extern __shared__ __align__(16) unsigned char gsm_[];
+    CT* As = (CT*)gsm_;
+    CT* Bs = As + IP_TILE * p;
+    c128* red = (c128*)(Bs + IP_TILE * p);
     const int nout = p * p;
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
     c128 acc[IP_MAXOUT];
@@ -300,15 +305,16 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
             const int l = e % p;
             const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
             const size_t t = (size_t)l * N + pt;          // column-major basis
-            const c128 cv = cvt<double>(C[t]);
-            c128 ax = op_diag(j, i, g) * cv;
-            const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+            const CT cv = C[t];
+            CT ax = op_diag_t<T>(j, i, g) * cv;
+            const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
+            const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
             if (g.Sx > 1) {
-                if (i > 0) ax = ax - wj * cvt<double>(C[t - 1]);
-                if (i < g.Sx - 1) ax = ax - wj * cvt<double>(C[t + 1]);
+                if (i > 0) ax = ax - wj * C[t - 1];
+                if (i < g.Sx - 1) ax = ax - wj * C[t + 1];
             }
-            if (j > 0) ax = ax - wi * cvt<double>(C[t - g.Sx]);
-            if (j < g.b - 1) ax = ax - wi * cvt<double>(C[t + g.Sx]);
+            if (j > 0) ax = ax - wi * C[t - g.Sx];
+            if (j < g.b - 1) ax = ax - wi * C[t + g.Sx];
             As[e] = cv;
             Bs[e] = ax;
         }
@@ -321,7 +327,14 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
             if (j1 < split_row) { ilo = 0; ihi = p / 2; }
             else if (j0 >= split_row) { ilo = p / 2; ihi = p; }
         }
-        ip_tile_accumulate<double>(As, Bs, rows, p, p, split, acc, ilo, ihi);
+        if (sizeof(T) == sizeof(double)) {
+            ip_tile_accumulate<double>((const c128*)As, (const c128*)Bs, rows, p, p, split, acc, ilo, ihi);
+        } else {
+            CT tacc[IP_MAXOUT];
+            for (int k = 0; k < IP_MAXOUT; ++k) tacc[k] = {0, 0};
+            ip_tile_accumulate<T>(As, Bs, rows, p, p, split, tacc, ilo, ihi);
+            for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = acc[k] + cvt<double>(tacc[k]);
+        }
         __syncthreads();
     }
     ip_store_partial<double>(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
@@ -334,7 +347,9 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
     int grid = (int)((N + 127) / 128);
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
-    const size_t sm = ip_smem(p, p);
+    const int nout = p * p;
+    const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
+    const size_t sm = sizeof(cplx<T>) * (size_t)IP_TILE * 2 * p + (split > 1 ? sizeof(c128) * split * nout : 0);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_galerkin_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

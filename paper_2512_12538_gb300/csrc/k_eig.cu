@@ -57,6 +57,13 @@ template <typename R> struct Eps;
 template <> struct Eps<float> { static constexpr float v = 1.1920929e-07f; static constexpr float tiny = 1e-5f; };
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; static constexpr double tiny = 1e-12; };
 
+// 1 / z as conj(z) / |z|^2 (one real reciprocal); the arguments here are differences of
+// eigenvalue estimates and Sturm ratios of moderate size, far from over- or underflow.
+template <typename R> __device__ __forceinline__ cplx<R> crcp_(cplx<R> z) {
+    const R s = (R)1 / (z.re * z.re + z.im * z.im);
+    return {z.re * s, -z.im * s};
+}
+
 // Complex symmetric tridiagonal line operator of a band (b rows), scaled
 // W^{-1/2} K W^{-1/2}: diagonal d_a and coupling e_a between rows a and a+1.
 template <typename R>
@@ -77,17 +84,17 @@ template <typename R>
 __device__ cplx<R> newton_step(const cplx<R>* d, const cplx<R>* e2, int b, cplx<R> z) {
     const R tiny = Eps<R>::tiny;
     cplx<R> r = d[0] - z;
-    if (cabs_(r) < tiny) r = {tiny, 0};
+    if (abs2(r) < tiny * tiny) r = {tiny, 0};
     cplx<R> rp = {(R)-1, 0};
-    cplx<R> ir = cdiv_(cplx<R>{1, 0}, r);
+    cplx<R> ir = crcp_(r);
     cplx<R> s = rp * ir;
     for (int j = 1; j < b; ++j) {
         const cplx<R> q = e2[j - 1] * ir;          // e^2 / r
         cplx<R> rn = d[j] - z - q;
-        if (cabs_(rn) < tiny) rn = {tiny, 0};
+        if (abs2(rn) < tiny * tiny) rn = {tiny, 0};
         rp = cplx<R>{(R)-1, 0} + q * (rp * ir);
         r = rn;
-        ir = cdiv_(cplx<R>{1, 0}, r);
+        ir = crcp_(r);
         s = s + rp * ir;
     }
     return cdiv_(cplx<R>{1, 0}, s);
@@ -96,8 +103,10 @@ __device__ cplx<R> newton_step(const cplx<R>* d, const cplx<R>* e2, int b, cplx<
 // Inverse iteration for the eigenvector of eigenvalue mu: (T - mu) x = x_prev with a
 // pivoted tridiagonal LU (row interchanges between neighbours), three iterations,
 // normalised q^T q = 1 (complex symmetric, no conjugation).
+// dd, ee: the band's tridiagonal (band_tridiag), staged once per leaf.
 template <typename R>
-__device__ void inverse_iteration(int b, double kh, cplx<R> mu, cplx<R>* x, cplx<R>* ws) {
+__device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, cplx<R> mu, cplx<R>* x,
+                                  cplx<R>* ws) {
     using C = cplx<R>;
     C* dg = ws;
     C* up = ws + b;
@@ -105,16 +114,13 @@ __device__ void inverse_iteration(int b, double kh, cplx<R> mu, cplx<R>* x, cplx
     C* lo = ws + 3 * b;
     R* sw = (R*)(ws + 4 * b);   // interchange flags
     for (int a = 0; a < b; ++a) {
-        C d, e;
-        band_tridiag<R>(b, kh, a, d, e);
-        dg[a] = d - mu;
-        up[a] = e;
+        dg[a] = dd[a] - mu;
+        up[a] = ee[a];
         up2[a] = {0, 0};
-        x[a] = {(R)(1.0 + 1e-3 * a), (R)(1e-3 * (a % 7))};
+        x[a] = {(R)1 + (R)1e-3 * (R)a, (R)1e-3 * (R)(a % 7)};
     }
     for (int j = 0; j < b - 1; ++j) {
-        C dsub, esub;
-        band_tridiag<R>(b, kh, j, dsub, esub);   // esub = sub-diagonal entry (j+1, j)
+        const C esub = ee[j];   // sub-diagonal entry (j+1, j)
         if (cabs_(dg[j]) >= cabs_(esub)) {
             sw[j] = 0;
             const C fact = cabs_(dg[j]) > (R)0 ? cdiv_(esub, dg[j]) : C{0, 0};
@@ -173,12 +179,15 @@ __global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ 
     using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.x];
     const int b = tk.b;
-    __shared__ C d[EIG_BMAX], e2[EIG_BMAX], z[EIG_BMAX];
+    __shared__ C d[EIG_BMAX], e[EIG_BMAX], e2[EIG_BMAX], z[EIG_BMAX];
+    __shared__ T rw[EIG_BMAX];     // 1 / sqrt(w_a)
     for (int a = threadIdx.x; a < b; a += blockDim.x) {
         C dd, ee;
         band_tridiag<T>(b, kh, a, dd, ee);
         d[a] = dd;
+        e[a] = ee;
         e2[a] = ee * ee;
+        rw[a] = (T)(1.0 / sqrt(wrow(a, b)));
         const double mu = 2.0 - 2.0 * cos(M_PI * a / (b - 1)) - kh * kh;
         z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 4.0) / (b - 1))};
     }
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ 
             const C w = newton_step<T>(d, e2, b, zj);
             C s = {0, 0};
             for (int k = 0; k < b; ++k)
-                if (k != j) s = s + cdiv_(C{1, 0}, zj - z[k]);
+                if (k != j) s = s + crcp_(zj - z[k]);
             const C dz = cdiv_(w, C{1, 0} - w * s);
             zn = zj - dz;
             small = cabs_(dz) <= (T)64 * Eps<T>::v * fmax(cabs_(zj), (T)1);
@@ -211,14 +220,15 @@ __global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ 
         C* ws = (C*)tk.work + (size_t)m * 6 * b;
         C* q = ws + 5 * b;
         const C mu = lm + C{(T)(8 * Eps<T>::v) * fmax(cabs_(lm), (T)1), (T)0};
-        inverse_iteration<T>(b, kh, mu, q, ws);
-        for (int a = 0; a < b; ++a) V[a * b + m] = ((T)(1.0 / sqrt(wrow(a, b)))) * q[a];
-        // scalar Schur recursions along the columns
+        inverse_iteration<T>(b, d, e, mu, q, ws);
+        for (int a = 0; a < b; ++a) V[a * b + m] = rw[a] * q[a];
+        // scalar Schur recursions along the columns (in T: the FP64 pipe is slow here)
+        const T khT = (T)kh;
         C prev = {0, 0};
         for (int i = 0; i < Sx; ++i) {
-            const T wi = (T)wcol(i, Sx);
             const bool xb = (i == 0 || i == Sx - 1);
-            const C delta = C{(T)(xb ? 1.0 : 2.0), (T)(xb ? -kh : 0.0)} + wi * lm;
+            const T wi = (Sx > 1 && xb) ? (T)0.5 : (T)1;
+            const C delta = C{xb ? (T)1 : (T)2, xb ? -khT : (T)0} + wi * lm;
             const C sdel = delta - prev;
             if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
             prev = cdiv_(C{1, 0}, sdel);
@@ -478,7 +488,8 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
 //      straight into the parent's prolongation).
 // V stays in shared memory between the two transforms and the transformed vectors never
 // leave the cluster.  4 x 2 register tiles: three 16-byte shared loads per eight complex
-// multiply-adds (complex64) in phase 1, five loads in phase 3.
+// multiply-adds (complex64) in phase 1, five loads in phase 3 (rows strided by b/4 so
+// that a warp's V reads fall in distinct banks).
 static constexpr int FS_THREADS = 256, FS_WARPS = FS_THREADS / 32;
 
 struct FsGeom {
@@ -602,12 +613,14 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
     }
     cluster.sync();
 
-    // phase 3: tiles (rows a0 .. a0 + 3) x (columns i0, i0 + 1), written to the output
+    // phase 3: tiles (rows g, g + ntm, g + 2 ntm, g + 3 ntm) x (columns i0, i0 + 1): the
+    // lanes of a warp read V rows g .. g + 3, which fall in different shared-memory banks
+    // (consecutive rows four apart would share one), written to the output
     for (int t = threadIdx.x; t < ntm * ntc; t += FS_THREADS) {
-        const int a0 = 4 * (t / ntc), i0 = 2 * (t % ntc);
+        const int g = t / ntc, i0 = 2 * (t % ntc);
         const C* vr[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) vr[u] = Vs + min(a0 + u, b - 1) * G.ldv;
+        for (int u = 0; u < 4; ++u) vr[u] = Vs + min(g + u * ntm, b - 1) * G.ldv;
         C acc[4][2];
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = C{0, 0};
@@ -622,8 +635,9 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (a0 + u >= tk.w0 && a0 + u < tk.w1) {
-                C* wr = Wout + (size_t)(a0 + u - tk.w0) * Sx + c0 + i0;
+            const int a = g + u * ntm;
+            if (a >= tk.w0 && a < tk.w1) {
+                C* wr = Wout + (size_t)(a - tk.w0) * Sx + c0 + i0;
                 wr[0] = acc[u][0];
                 if (i0 + 1 < nown) wr[1] = acc[u][1];
             }

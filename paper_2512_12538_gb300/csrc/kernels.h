@@ -56,6 +56,14 @@ void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size
 template <typename TC, typename TV, typename TW>
 void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
                          unsigned* counter, const c128* Minv, c128* y, cudaStream_t s);
+// One column in one cooperative launch: w_out (+)= C Minv C^H (v - A~ w_in), y = the
+// coefficients (FP64 copy).  Minv in the basis precision; partial: grid x p scratch
+// entries of the basis precision; bar: two zeroed words (grid barrier); err: the
+// device status word (DEV_TIMEOUT if the barrier wait gives up).
+template <typename TC, typename TV, typename TW>
+void launch_coarse_fused(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w_in, cplx<TW>* w_out, bool accumulate,
+                         OpGeom g, int p, void* partial, unsigned* bar, int* err, const cplx<TC>* Minv, c128* y,
+                         cudaStream_t s);
 // W += C y (one column) / W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
 template <typename TC, typename TW>
 void launch_coarse_upd1(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, cudaStream_t s);
