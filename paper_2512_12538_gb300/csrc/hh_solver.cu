@@ -272,6 +272,8 @@ struct Solver final : SolverBase {
     // input directly: R_c of the parent's input, no copy into the parent's buffer)
     std::vector<const CT*> cur_in;
     bool in_pre = false;        // inside the preconditioner step (oras_step)
+    c128* root_out = nullptr;   // with n_i = 1 the level-1 corrections write into the root's
+    bool root_acc = false;      // output directly (accumulating onto a base iterate)
     bool pre_direct = false;    // its leaf sweeps write the owned rows into the parents
     std::vector<const void*> view_key, eview_key;
     // eigenbasis leaf path
@@ -386,8 +388,8 @@ struct Solver final : SolverBase {
         cur_in[0] = RT;
         partial = a.take<c128>((size_t)MAX_PART_BLOCKS * 64 * 64);
         npart = a.take<double>(2048);
-        dnorm = a.take<double>(4);
-        derr = a.take<int>(4);
+        dnorm = a.take<double>(8);          // [0..4) norms, then the device status words
+        derr = (int*)(dnorm + 4);
         dcounter = a.take<unsigned>(4);
         const int nleaf = 1 << L;
         d_tasks_view = a.take<LeafTask>(nleaf);
@@ -609,9 +611,10 @@ struct Solver final : SolverBase {
             return;
         }
         for (int p : lev[l]) cur_in[p] = input(p, nc, own);
-        // the leaves of the preconditioner step may have written their owned rows into
-        // the parents already
-        const bool leaves_direct = l + 1 == L && in_pre && pre_direct && nc == 1;
+        // preconditioner step with n_i = 1: every level's corrections in one launch, each
+        // node writing its owned rows straight into its parent's solution
+        const bool batch = in_pre && nc == 1 && P.n_inner == 1;
+        const bool children_direct = batch && (l + 1 < L || pre_direct);
         for (int it = 0; it < P.n_inner; ++it) {
             for (int p : lev[l]) {
                 if (it == 0) {
@@ -621,8 +624,8 @@ struct Solver final : SolverBase {
                 }
             }
             apply_M(l + 1, nc, false);
-            for (int p : lev[l]) {
-                if (!leaves_direct) {
+            if (!children_direct) {
+                for (int p : lev[l]) {
                     for (int c : nodes[p].child) {
                         const Node& cn = nodes[c];
                         const size_t n = (size_t)(cn.own_b - cn.own_a) * Sx * nc;
@@ -630,9 +633,64 @@ struct Solver final : SolverBase {
                                           it > 0, false, stream);
                     }
                 }
-                coarse_correct(p, cur_in[p], nc);
             }
+            if (batch) coarse_level_direct(l);
+            else
+                for (int p : lev[l]) coarse_correct(p, cur_in[p], nc);
         }
+    }
+
+    // The one-column corrections of all level-l nodes of the preconditioner step, each
+    // written (owned rows, plus the node's own solution) into the parent: the root's
+    // output for level 1, else the parent's W.
+    void coarse_level_direct(int l) {
+        const std::vector<int>& ps = lev[l];
+        for (size_t k0 = 0; k0 < ps.size(); k0 += CB_MAX_JOBS) {
+            CoarseBatch bt{};
+            double by = 0.0, fl = 0.0;
+            for (size_t k = k0; k < ps.size() && k < k0 + CB_MAX_JOBS; ++k) {
+                const int p = ps[k];
+                const Node& nd = nodes[p];
+                CoarseJob& j = bt.job[bt.njobs++];
+                j.C = C[p];
+                j.v = cur_in[p];
+                j.w_in = W[p];
+                j.out = l == 1 ? (void*)(root_out + row_off(0, nd.own_a, 1))
+                               : (void*)(W[nd.parent] + row_off(nd.parent, nd.own_a, 1));
+                j.Minv = AinvT[p];
+                j.y = ycoef[p];
+                j.g = geom(p);
+                j.r0 = nd.own_a - nd.ra;
+                j.r1 = nd.own_b - nd.ra;
+                j.acc_out = l == 1 && root_acc;
+                j.add_w = 1;
+                by += (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT);
+                fl += 2.0 * 8.0 * 2 * r * pts(p);
+            }
+            pbeg(PC_COARSE, by, fl);
+            if (l == 1) launch_coarse_batch<T, T, T, double>(bt, 2 * r, partial, dcounter + 2, derr, stream);
+            else launch_coarse_batch<T, T, T, T>(bt, 2 * r, partial, dcounter + 2, derr, stream);
+            pend();
+        }
+    }
+
+    // out (+)= C_p A_c^{-1} C_p^H (v - A~_p w) over node p's band, one column
+    CoarseBatch one_job(int p, const void* v, const void* w, void* out, bool acc) const {
+        CoarseBatch bt{};
+        CoarseJob& j = bt.job[0];
+        j.C = C[p];
+        j.v = v;
+        j.w_in = w;
+        j.out = out;
+        j.Minv = AinvT[p];
+        j.y = ycoef[p];
+        j.g = geom(p);
+        j.r0 = 0;
+        j.r1 = nodes[p].b();
+        j.acc_out = acc;
+        j.add_w = 0;
+        bt.njobs = 1;
+        return bt;
     }
 
     // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
@@ -640,8 +698,8 @@ struct Solver final : SolverBase {
         if (nc == 1) {
             // algorithmic: C (2r x N) once, v and w read, w written; C^H r and C y
             pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT), 2.0 * 8.0 * 2 * r * pts(p));
-            launch_coarse_fused<T, T, T>(C[p], vin, W[p], W[p], true, geom(p), 2 * r, partial, dcounter + 2, derr,
-                                         AinvT[p], ycoef[p], stream);
+            launch_coarse_batch<T, T, T, T>(one_job(p, vin, W[p], W[p], true), 2 * r, partial, dcounter + 2, derr,
+                                            stream);
             pend();
             return;
         }
@@ -770,32 +828,40 @@ struct Solver final : SolverBase {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (!ok) return st;
-        ck(cudaMallocHost(&h_norm, 4 * sizeof(double)), cerr);
+        ck(cudaMallocHost(&h_norm, 8 * sizeof(double)), cerr);
         if (mk > 0) ck(cudaMallocHost(&h_dots, 4 * 80 * sizeof(c128)), cerr);
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
 
     // --------------------------------------------------------- the outer iteration
-    // One coarse-corrected ORAS step from the FP64 residual kept in res:
+    // One coarse-corrected ORAS step from the FP64 residual kept in res (and already in
+    // RT, the leaf precision, when rt_ready):
     // out = base + sum_c P_c M_c R_c res (base null: zero; base may be out), then
     // out += C A_c^{-1} C^H (rhs - A out).
-    void oras_step(const c128* base, const c128* rhs, c128* out) {
+    void oras_step(const c128* base, const c128* rhs, c128* out, bool rt_ready = false) {
         const size_t N = (size_t)Sy * Sx;
-        launch_copy<double, T>(res, RT, N, false, false, stream);
+        if (!rt_ready) launch_copy<double, T>(res, RT, N, false, false, stream);
+        // with n_i = 1 (and a level below the root's children) the level-1 corrections
+        // write out = base + sum_c P_c M_c R_c res themselves
+        const bool direct = P.n_inner == 1 && L >= 2;
+        if (base && base != out) d2d(out, base, sizeof(c128) * N);
+        root_out = out;
+        root_acc = base != nullptr;
         in_pre = true;
         apply_M(1, 1, false);
         in_pre = false;
-        // out = base + sum_c P_c W_c: the level-1 owned rows partition the grid, so with
-        // no base the copies initialise out
-        if (base && base != out) d2d(out, base, sizeof(c128) * N);
-        for (int c : lev[1]) {
-            const Node& cn = nodes[c];
-            launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), out + row_off(0, cn.own_a, 1),
-                                   (size_t)(cn.own_b - cn.own_a) * Sx, base != nullptr, false, stream);
+        if (!direct) {
+            // the level-1 owned rows partition the grid, so with no base the copies
+            // initialise out
+            for (int c : lev[1]) {
+                const Node& cn = nodes[c];
+                launch_copy<T, double>(W[c] + row_off(c, cn.own_a, 1), out + row_off(0, cn.own_a, 1),
+                                       (size_t)(cn.own_b - cn.own_a) * Sx, base != nullptr, false, stream);
+            }
         }
         pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
-        launch_coarse_fused<T, double, double>(C[0], rhs, out, out, true, geom(0), 2 * r, partial, dcounter + 2, derr,
-                                               AinvT[0], ycoef[0], stream);
+        launch_coarse_batch<T, double, double, double>(one_job(0, rhs, out, out, true), 2 * r, partial, dcounter + 2,
+                                                       derr, stream);
         pend();
     }
 
@@ -852,14 +918,25 @@ struct Solver final : SolverBase {
     }
 
     // ||b - A u||^2 into h_norm[0] (synchronises); ||b||^2 must be in dnorm[2].
-    bool true_residual(c128* dst, hh_status& st) {
+    bool true_residual(c128* dst, hh_status& st, CT* dst_t = nullptr) {
         int nb = 0;
         pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
-        launch_apply<double, double, double>(u, bvec, dst, geom(0), 1, 1.0, npart, &nb, stream);
+        if (dst_t) launch_residual_cast<T>(u, bvec, dst, dst_t, geom(0), npart, &nb, stream);
+        else launch_apply<double, double, double>(u, bvec, dst, geom(0), 1, 1.0, npart, &nb, stream);
         pend();
         launch_sum(npart, nb, dnorm, stream);
-        ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
-        const bool ok = sync_check(st);
+        // the norms and the device status words in one copy
+        ck(cudaMemcpyAsync(h_norm, dnorm, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaGetLastError(), cerr);
+        ck(cudaStreamSynchronize(stream), cerr);
+        bool ok = cerr == cudaSuccess;
+        if (!ok) st = HH_ECUDA;
+        else {
+            const int e2 = *(const int*)(h_norm + 4);
+            st = e2 == DEV_BREAKDOWN ? HH_EBREAKDOWN : e2 == DEV_TIMEOUT ? HH_ETIMEOUT : e2 == DEV_BADARG ? HH_EINVAL
+                                                                                                     : HH_OK;
+            ok = st == HH_OK;
+        }
         graphs_collect();
         return ok;
     }
@@ -868,12 +945,12 @@ struct Solver final : SolverBase {
     hh_status loop_oras(int& it, double& rel) {
         hh_status st = HH_OK;
         for (;;) {
-            if (!true_residual(res, st)) return st;
+            if (!true_residual(res, st, RT)) return st;
             rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
             if (!std::isfinite(rel)) return HH_ENOCONV;
             if (rel < P.tol) return HH_OK;
             if (it >= P.max_iter) return HH_ENOCONV;
-            via_graph(1, [&] { oras_step(u, bvec, u); });
+            via_graph(1, [&] { oras_step(u, bvec, u, true); });
             ++it;
         }
     }
@@ -1096,8 +1173,8 @@ struct Solver final : SolverBase {
 
     hh_status coarse_apply(int p, const c128* rr, c128* z) override {
         if (!valid_node(p) || nodes[p].leaf() || !rr || !z) return HH_EINVAL;
-        launch_coarse_fused<T, double, double>(C[p], rr, nullptr, z, false, geom(p), 2 * r, partial, dcounter + 2, derr,
-                                               AinvT[p], ycoef[p], stream);
+        launch_coarse_batch<T, double, double, double>(one_job(p, rr, nullptr, z, false), 2 * r, partial, dcounter + 2,
+                                                       derr, stream);
         hh_status st;
         sync_check(st);
         return st;

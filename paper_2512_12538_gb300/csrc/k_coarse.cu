@@ -214,19 +214,23 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
     return s_ok != 0;
 }
 
-// w_out (+)= C A_c^{-1} C^H (v - A~ w_in) for one column in one cooperative launch
-// (Eq. (3)): phase 1 as the projection above (residual once per point in shared memory,
-// four column groups, per-block partial sums of C^H r in the basis precision); grid
-// barrier; phase 2: every block adds all blocks' partials in the same fixed order and
-// multiplies by A_c^{-1} (basis precision; the inverse was copied to shared memory while
-// phase 1 ran), so all blocks hold the same y; phase 3: each block updates the points it
-// projected (C re-read while still in cache).  w_in may be null (r = v); w_in may equal
-// w_out (the barrier separates every read of w_in from the writes).
-template <typename TC, typename TV, typename TW>
-__global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict__ C, const cplx<TV>* __restrict__ v,
-                                                      const cplx<TW>* w_in, cplx<TW>* w_out, int accumulate,
-                                                      OpGeom g, int p, cplx<TC>* partial, unsigned* bar, int* err,
-                                                      const cplx<TC>* __restrict__ Minv, c128* __restrict__ y) {
+// One-column coarse corrections of several nodes (Eq. (3)) in one cooperative launch;
+// job k owns blocks [blk0, blk0 + nblk).  For each job:
+//   phase 1: r = v - A~ w_in (w_in may be null: r = v), formed once per point in shared
+//            memory, and per-block partial sums of C^H r in the basis precision (four
+//            column groups, coalesced reads of C along the points);
+//   grid barrier;
+//   phase 2: every block of the job adds the job's partials in the same fixed order and
+//            multiplies by A_c^{-1} (basis precision; copied to shared memory with
+//            cp.async while phase 1 ran), so all of them hold the same y;
+//   phase 3: for the points it projected whose rows lie in [r0, r1):
+//            out[pt - r0 Sx] = (acc_out ? out : 0) + (add_w ? w_in[pt] : 0) + (C y)[pt]
+//            (in place: out = w_in, acc_out; straight into the parent's solution: the
+//            owned rows, add_w).  The barrier separates every read of w_in from the
+//            writes.
+template <typename TC, typename TV, typename TW, typename TO>
+__global__ void __launch_bounds__(256) k_coarse_batch(CoarseBatch bt, int p, cplx<TC>* partial, unsigned* bar,
+                                                      int* err) {
     using CA = cplx<TC>;
     using R = decltype(TV() + TW());
     __shared__ CA red[8][16];
@@ -234,6 +238,14 @@ __global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict
     __shared__ CA s_sum[64];
     __shared__ CA s_y[64];
     __shared__ __align__(16) CA s_m[64 * 64];
+    int jb_ = 0;
+    while (jb_ + 1 < bt.njobs && blockIdx.x >= bt.job[jb_ + 1].blk0) ++jb_;
+    const CoarseJob& J = bt.job[jb_];
+    const cplx<TC>* __restrict__ C = (const cplx<TC>*)J.C;
+    const cplx<TV>* __restrict__ v = (const cplx<TV>*)J.v;
+    const cplx<TW>* w_in = (const cplx<TW>*)J.w_in;
+    const OpGeom g = J.g;
+    const unsigned lb = blockIdx.x - J.blk0, nblk = J.nblk;
     const unsigned N = (unsigned)g.b * (unsigned)g.Sx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = threadIdx.x & 63, jg = threadIdx.x >> 6;
@@ -241,13 +253,13 @@ __global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict
     {
         const int chunks = (int)(sizeof(CA) * p * p / 16);
         for (int t = threadIdx.x; t < chunks; t += blockDim.x)
-            cp_async16((char*)s_m + 16 * t, (const char*)Minv + 16 * t);
+            cp_async16((char*)s_m + 16 * t, (const char*)J.Minv + 16 * t);
         cp_async_commit();
     }
     CA acc[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = {0, 0};
-    for (unsigned base = blockIdx.x * 256u; base < N; base += gridDim.x * 256u) {
+    for (unsigned base = lb * 256u; base < N; base += nblk * 256u) {
         {
             const unsigned pt = base + threadIdx.x;
             CA ra = {0, 0};
@@ -297,19 +309,20 @@ __global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict
     }
     cp_async_wait_all();
     if (!grid_barrier(bar, err)) return;
-    // phase 2: the same sums in every block: 8 threads per output, partials
+    // phase 2: the same sums in every block of the job: 8 threads per output, partials
     // b = sub, sub + 8, ... in order, then a fixed shuffle tree
     const int sub = threadIdx.x & 7;
+    const CA* jp = partial + (size_t)J.blk0 * p;
     for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
         const int j = j0 + (threadIdx.x >> 3);
         CA t0 = {0, 0}, t1 = {0, 0};
         if (j < p) {
-            for (unsigned b0 = sub; b0 < gridDim.x; b0 += 64) {
+            for (unsigned b0 = sub; b0 < nblk; b0 += 64) {
                 CA a[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const unsigned bb = b0 + 8u * u;
-                    a[u] = bb < gridDim.x ? partial[(size_t)bb * p + j] : CA{0, 0};
+                    a[u] = bb < nblk ? jp[(size_t)bb * p + j] : CA{0, 0};
                 }
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
@@ -337,14 +350,16 @@ __global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict
         }
         if (j < p && sub == 0) {
             s_y[j] = t;
-            if (blockIdx.x == 0) y[j] = cvt<double>(t);
+            if (lb == 0 && J.y) J.y[j] = cvt<double>(t);
         }
     }
     __syncthreads();
     // phase 3: one point per thread, all p columns (coalesced along the points)
-    for (unsigned base = blockIdx.x * 256u; base < N; base += gridDim.x * 256u) {
+    cplx<TO>* out = (cplx<TO>*)J.out;
+    const unsigned lo = (unsigned)J.r0 * g.Sx, hi = (unsigned)J.r1 * g.Sx;
+    for (unsigned base = lb * 256u; base < N; base += nblk * 256u) {
         const unsigned pt = base + threadIdx.x;
-        if (pt >= N) continue;
+        if (pt < lo || pt >= hi) continue;
         CA a = {0, 0};
         int j = 0;
         for (; j + 8 <= p; j += 8) {
@@ -355,33 +370,43 @@ __global__ void __launch_bounds__(256) k_coarse_fused(const cplx<TC>* __restrict
             for (int u = 0; u < 8; ++u) cfma(a, cv[u], s_y[j + u]);
         }
         for (; j < p; ++j) cfma(a, C[(size_t)j * N + pt], s_y[j]);
-        const cplx<TW> add = cvt<TW>(a);
-        w_out[pt] = accumulate ? w_out[pt] + add : add;
+        cplx<TO> val = cvt<TO>(a);
+        if (J.add_w) val = val + cvt<TO>(w_in[pt]);
+        cplx<TO>& o = out[pt - lo];
+        o = J.acc_out ? o + val : val;
     }
 }
 
-template <typename TC, typename TV, typename TW>
-int coarse_fused_max_grid() {
+template <typename TC, typename TV, typename TW, typename TO>
+int coarse_batch_max_grid() {
     static int mg = 0;
     if (!mg) {
         int dev = 0, sms = 0, nb = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_fused<TC, TV, TW>, 256, 0);
-        mg = std::max(1, std::min(nb, 1) * sms);   // one block per SM: phase 2 reads grid x p partials
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_batch<TC, TV, TW, TO>, 256, 0);
+        mg = std::max(1, std::min(nb, 2) * sms);
     }
     return mg;
 }
 
-template <typename TC, typename TV, typename TW>
-void launch_coarse_fused(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w_in, cplx<TW>* w_out, bool accumulate,
-                         OpGeom g, int p, void* partial, unsigned* bar, int* err, const cplx<TC>* Minv, c128* y,
-                         cudaStream_t s) {
-    const size_t N = (size_t)g.b * g.Sx;
-    const int grid = blocks_for(N, 256, coarse_fused_max_grid<TC, TV, TW>());
+template <typename TC, typename TV, typename TW, typename TO>
+void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s) {
+    if (bt.njobs < 1) return;
+    // blocks per job: one per 256 points, at most 152 per job (phase 2 reads every partial
+    // of the job), within the co-resident total
+    const int mg = coarse_batch_max_grid<TC, TV, TW, TO>();
+    const int cap = std::max(1, std::min(152, mg / bt.njobs));
+    unsigned blk = 0;
+    for (int k = 0; k < bt.njobs; ++k) {
+        const size_t N = (size_t)bt.job[k].g.b * bt.job[k].g.Sx;
+        bt.job[k].blk0 = blk;
+        bt.job[k].nblk = (unsigned)blocks_for(N, 256, cap);
+        blk += bt.job[k].nblk;
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = dim3(blk);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -389,8 +414,7 @@ void launch_coarse_fused(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_coarse_fused<TC, TV, TW>, C, v, w_in, w_out, (int)accumulate, g, p, (cplx<TC>*)partial,
-                       bar, err, Minv, y);
+    cudaLaunchKernelEx(&cfg, k_coarse_batch<TC, TV, TW, TO>, bt, p, (cplx<TC>*)partial, bar, err);
     note_launch();
 }
 
@@ -461,13 +485,12 @@ template void launch_coarse_proj1<float, double, double>(const c64*, const c128*
                                                          unsigned*, const c128*, c128*, cudaStream_t);
 template void launch_coarse_proj1<double, double, double>(const c128*, const c128*, const c128*, OpGeom, int,
                                                           c128*, unsigned*, const c128*, c128*, cudaStream_t);
-template void launch_coarse_fused<float, float, float>(const c64*, const c64*, const c64*, c64*, bool, OpGeom, int,
-                                                       void*, unsigned*, int*, const c64*, c128*, cudaStream_t);
-template void launch_coarse_fused<float, double, double>(const c64*, const c128*, const c128*, c128*, bool, OpGeom, int,
-                                                         void*, unsigned*, int*, const c64*, c128*, cudaStream_t);
-template void launch_coarse_fused<double, double, double>(const c128*, const c128*, const c128*, c128*, bool, OpGeom,
-                                                          int, void*, unsigned*, int*, const c128*, c128*,
-                                                          cudaStream_t);
+template void launch_coarse_batch<float, float, float, float>(CoarseBatch, int, void*, unsigned*, int*, cudaStream_t);
+template void launch_coarse_batch<float, float, float, double>(CoarseBatch, int, void*, unsigned*, int*, cudaStream_t);
+template void launch_coarse_batch<float, double, double, double>(CoarseBatch, int, void*, unsigned*, int*,
+                                                                 cudaStream_t);
+template void launch_coarse_batch<double, double, double, double>(CoarseBatch, int, void*, unsigned*, int*,
+                                                                  cudaStream_t);
 template void launch_coarse_upd1<float, float>(const c64*, const c128*, c64*, size_t, int, cudaStream_t);
 template void launch_coarse_upd1<float, double>(const c64*, const c128*, c128*, size_t, int, cudaStream_t);
 template void launch_coarse_upd1<double, double>(const c128*, const c128*, c128*, size_t, int, cudaStream_t);

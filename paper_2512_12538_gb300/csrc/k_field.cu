@@ -68,6 +68,52 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
     if (nblk_out) *nblk_out = grid;
 }
 
+// Global residual y = v - A x in FP64 with per-block partial sums of |y|^2, and the
+// same residual rounded to the leaf precision (yt), the input of the next ORAS step.
+template <typename T>
+__global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restrict__ v, c128* __restrict__ y,
+                                cplx<T>* __restrict__ yt, OpGeom g, double* part) {
+    const size_t total = (size_t)g.b * g.Sx;
+    double acc2 = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.Sx);
+        const int j = (int)(t / g.Sx);
+        c128 ax = op_diag(j, i, g) * x[t];
+        const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+        if (g.Sx > 1) {
+            if (i > 0) ax = ax - wj * x[t - 1];
+            if (i < g.Sx - 1) ax = ax - wj * x[t + 1];
+        }
+        if (j > 0) ax = ax - wi * x[t - g.Sx];
+        if (j < g.b - 1) ax = ax - wi * x[t + g.Sx];
+        const c128 out = v[t] - ax;
+        y[t] = out;
+        yt[t] = cvt<T>(out);
+        acc2 += abs2(out);
+    }
+    __shared__ double red[32];
+    acc2 = warp_sum(acc2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s2 = warp_sum(s2);
+        if (threadIdx.x == 0) part[blockIdx.x] = s2;
+    }
+}
+template <typename T>
+void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, int* nblk_out,
+                          cudaStream_t s) {
+    const size_t total = (size_t)g.b * g.Sx;
+    const int grid = grid_for(total, 256, 152 * 8);
+    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part);
+    note_launch();
+    if (nblk_out) *nblk_out = grid;
+}
+template void launch_residual_cast<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, int*, cudaStream_t);
+template void launch_residual_cast<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, int*,
+                                           cudaStream_t);
+
 __global__ void k_sum(const double* part, int n, double* out) {
     double a = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];

@@ -16,6 +16,11 @@ template <typename TX, typename TV, typename TY>
 void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, int nc, double sgn,
                   double* part, int* nblk_out, cudaStream_t s);
 
+// y = v - A x (FP64, one column) with per-block |y|^2 partials, and yt = y rounded to T.
+template <typename T>
+void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, int* nblk_out,
+                          cudaStream_t s);
+
 // out = sum of n doubles (deterministic single-block reduction)
 void launch_sum(const double* part, int n, double* out, cudaStream_t s);
 
@@ -56,14 +61,32 @@ void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size
 template <typename TC, typename TV, typename TW>
 void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
                          unsigned* counter, const c128* Minv, c128* y, cudaStream_t s);
-// One column in one cooperative launch: w_out (+)= C Minv C^H (v - A~ w_in), y = the
-// coefficients (FP64 copy).  Minv in the basis precision; partial: grid x p scratch
-// entries of the basis precision; bar: two zeroed words (grid barrier); err: the
-// device status word (DEV_TIMEOUT if the barrier wait gives up).
-template <typename TC, typename TV, typename TW>
-void launch_coarse_fused(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w_in, cplx<TW>* w_out, bool accumulate,
-                         OpGeom g, int p, void* partial, unsigned* bar, int* err, const cplx<TC>* Minv, c128* y,
-                         cudaStream_t s);
+// One-column coarse corrections of up to CB_MAX_JOBS nodes in one cooperative launch
+// (k_coarse.cu).  Per job: basis C [p][N] (TC), right-hand side v (TV), iterate w_in
+// (TW, may be null), output out (TO) for the rows [r0, r1) of the node:
+//   out[pt - r0 Sx] = (acc_out ? out : 0) + (add_w ? w_in[pt] : 0) + (C y)[pt],
+//   y = Minv C^H (v - A~ w_in)  (Minv in TC; y also stored in FP64 when non-null).
+// partial: (total blocks) x p scratch entries of TC; bar: two zeroed words (grid
+// barrier); err: the device status word (DEV_TIMEOUT if the barrier wait gives up).
+constexpr int CB_MAX_JOBS = 16;
+struct CoarseJob {
+    const void* C;
+    const void* v;
+    const void* w_in;
+    void* out;
+    const void* Minv;
+    c128* y;
+    OpGeom g;
+    int r0, r1;
+    int acc_out, add_w;
+    unsigned blk0, nblk;   // set by the launcher
+};
+struct CoarseBatch {
+    CoarseJob job[CB_MAX_JOBS];
+    int njobs;
+};
+template <typename TC, typename TV, typename TW, typename TO>
+void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s);
 // W += C y (one column) / W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
 template <typename TC, typename TW>
 void launch_coarse_upd1(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, cudaStream_t s);
