@@ -748,7 +748,9 @@ struct Solver final : SolverBase {
             launch_copy<T, T>(W[c] + row_off(c, nodes[c].ifrow, m), Z[c], (size_t)Sx * m, false, true, stream);
         // SVD of Z^H = Q^H T: Gram Z^H Z (FP64), its Hermitian eigenproblem, V = Z U Sigma^{-1}
         for (int c : cs) {
-            const int nb = launch_ip_partial<T, T>(Z[c], m, Z[c], m, Sx, m, m, partial, MAX_PART_BLOCKS, stream);
+            // Gram matrix in the sketch precision (FP32 products for the complex64 sketch:
+            // their rounding matches that of the sketch itself), partial sums in FP64
+            const int nb = launch_ip_partial<T, T, T>(Z[c], m, Z[c], m, Sx, m, m, partial, MAX_PART_BLOCKS, stream);
             launch_ip_reduce(partial, nb, m, m, Gm[c], nullptr, nullptr, stream);
         }
         std::vector<c128*> gs, us;

@@ -454,26 +454,45 @@ void launch_coarse_upd1(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N,
     note_launch();
 }
 
-// Several columns (set-up): W[pt][c] += sum_j C[j][pt] y[j][c]
+// Several columns (set-up): W[pt][c] += sum_j C[j][pt] y[j][c].  One thread per point
+// and 16 columns at a time: each C[j][pt] is read once per chunk (coalesced along the
+// points) and used for all the chunk's columns; y staged in shared memory in the basis
+// precision.
 template <typename TC, typename TW>
-__global__ void k_coarse_updn(const cplx<TC>* __restrict__ C, const c128* __restrict__ y, cplx<TW>* __restrict__ W,
-                              size_t N, int p, int nc) {
-    extern __shared__ c128 ysn[];
-    for (int t = threadIdx.x; t < p * nc; t += blockDim.x) ysn[t] = y[t];
+__global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict__ C, const c128* __restrict__ y,
+                                                     cplx<TW>* __restrict__ W, size_t N, int p, int nc) {
+    extern __shared__ __align__(16) unsigned char ysm[];
+    cplx<TC>* ys = (cplx<TC>*)ysm;   // [p][nc]
+    for (int t = threadIdx.x; t < p * nc; t += blockDim.x) ys[t] = cvt<TC>(y[t]);
     __syncthreads();
-    const size_t total = N * nc;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(t % nc);
-        const size_t pt = t / nc;
-        cplx<TC> acc = {0, 0};
-#pragma unroll 16
-        for (int j = 0; j < p; ++j) cfma(acc, C[(size_t)j * N + pt], cvt<TC>(ysn[j * nc + c]));
-        W[t] = W[t] + cvt<TW>(acc);
+    for (size_t pt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; pt < N; pt += (size_t)gridDim.x * blockDim.x) {
+        for (int c0 = 0; c0 < nc; c0 += 16) {
+            const int cn = min(16, nc - c0);
+            cplx<TC> acc[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = {0, 0};
+            for (int j = 0; j < p; ++j) {
+                const cplx<TC> cv = C[(size_t)j * N + pt];
+                const cplx<TC>* yr = ys + j * nc + c0;
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c < cn) cfma(acc[c], cv, yr[c]);
+            }
+            cplx<TW>* wr = W + pt * nc + c0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < cn) wr[c] = wr[c] + cvt<TW>(acc[c]);
+        }
     }
 }
 template <typename TC, typename TW>
 void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s) {
-    k_coarse_updn<TC, TW><<<blocks_for(N * nc, 256, 152 * 8), 256, sizeof(c128) * p * nc, s>>>(C, y, W, N, p, nc);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_coarse_updn<TC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr = true;
+    }
+    k_coarse_updn<TC, TW><<<blocks_for(N, 256, 152 * 8), 256, sizeof(cplx<TC>) * p * nc, s>>>(C, y, W, N, p, nc);
     note_launch();
 }
 

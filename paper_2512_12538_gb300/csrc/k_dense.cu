@@ -167,8 +167,10 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
         note_launch();
         return grid;
     }
-    const size_t per = 256;
-    int grid = (int)((N + per - 1) / per);
+    // one block per IP_TILE rows up to one per SM: the outputs are many and the rows few
+    // (Gram matrices of sketch blocks), so the work per row is what needs spreading
+    int grid = (int)((N + IP_TILE - 1) / IP_TILE);
+    if (grid > 152) grid = 152;
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
     const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));

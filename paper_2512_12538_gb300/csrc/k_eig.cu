@@ -332,6 +332,84 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
     }
 }
 
+// Register-tiled form of the same contraction for leaves whose V fits in shared memory:
+// one CTA per GN columns (GN = 16 CV), V staged once in [k][r] order (op applied) and the
+// CTA's B block [k][GN]; thread (rg, cg) accumulates rows rg + 16 u (u < RU) times columns
+// cg + 16 v (v < CV): RU + CV shared loads per RU x CV complex multiply-adds.
+template <typename T> struct Gemm2Cols { static constexpr int CV = 4; };
+template <> struct Gemm2Cols<double> { static constexpr int CV = 2; };
+
+template <typename T, bool TRANS, int RU>
+__global__ void __launch_bounds__(256) k_eig_gemm2(const EigTask* __restrict__ tasks, int J, int which, int Sx,
+                                                   int nrhs) {
+    constexpr int CV = Gemm2Cols<T>::CV, GN = 16 * CV;
+    using C = cplx<T>;
+    const EigTask tk = tasks[blockIdx.y];
+    const int b = tk.b;
+    const int j0 = blockIdx.x * GN;
+    if (j0 >= J) return;
+    const C* V = (const C*)tk.V;
+    const C* B = (const C*)(which == 0 ? tk.F : tk.Fh);
+    C* Cout = (C*)(which == 0 ? tk.Fh : tk.W);
+    extern __shared__ __align__(16) unsigned char g2sm[];
+    C* Vs = (C*)g2sm;                  // [k][r], ld = b
+    C* Bs = Vs + (size_t)b * b;        // [k][GN]
+    // stage: eight loads in flight per thread
+    const int nv = b * b, nb2 = b * GN;
+    for (int e0 = threadIdx.x; e0 < nv + nb2; e0 += 8 * 256) {
+        C tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256;
+            tmp[u] = C{0, 0};
+            if (e < nv) {
+                const int k = e / b, r = e - k * b;
+                tmp[u] = TRANS ? V[(size_t)k * b + r] : V[(size_t)r * b + k];
+            } else if (e < nv + nb2) {
+                const int e2 = e - nv, k = e2 / GN, c = e2 - k * GN, jj = j0 + c;
+                if (jj < J) {
+                    const size_t col = which == 0 ? (size_t)jj : (size_t)(jj % nrhs) * Sx + jj / nrhs;
+                    tmp[u] = B[(size_t)k * J + col];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256;
+            if (e < nv + nb2) Vs[e] = tmp[u];   // Vs and Bs are contiguous
+        }
+    }
+    __syncthreads();
+    const int rg = threadIdx.x >> 4, cg = threadIdx.x & 15;
+    C acc[RU][CV];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+        for (int v = 0; v < CV; ++v) acc[u][v] = C{0, 0};
+    for (int k = 0; k < b; ++k) {
+        C vr[RU], bc[CV];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) vr[u] = Vs[k * b + min(rg + 16 * u, b - 1)];
+#pragma unroll
+        for (int v = 0; v < CV; ++v) bc[v] = Bs[k * GN + cg + 16 * v];
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+#pragma unroll
+            for (int v = 0; v < CV; ++v) cfma(acc[u][v], vr[u], bc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < CV; ++v) {
+        const int jj = j0 + cg + 16 * v;
+        if (jj >= J) continue;
+        const size_t col = which == 0 ? (size_t)(jj % nrhs) * Sx + jj / nrhs : (size_t)jj;
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int r = rg + 16 * u;
+            if (r < b) Cout[(size_t)r * J + col] = acc[u][v];
+        }
+    }
+}
+
 // Scalar recursions along each line, in place on Fh[m][c][i]: one warp per line (mode m,
 // right-hand side c).  Both recursions are affine, y_i = xi_i y_{i-1} + xi_i f_i and
 // x_i = xi_i x_{i+1} + y_i (with x_{n-1} = y_{n-1}), so each lane composes the maps of a
@@ -455,7 +533,29 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
         cudaFuncSetAttribute(k_eig_recur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    if (stage == 0) {
+    // register-tiled contraction where V and the column block fit in shared memory
+    constexpr int GN2 = 16 * Gemm2Cols<T>::CV;
+    const size_t sm2 = sizeof(cplx<T>) * ((size_t)b_max * b_max + (size_t)b_max * GN2);
+    const bool tiled = stage != 1 && b_max <= 144 && sm2 <= (size_t)(200 * 1024);
+    if (tiled) {
+        static bool attr2 = false;
+        if (!attr2) {
+            cudaFuncSetAttribute(k_eig_gemm2<T, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr2 = true;
+        }
+        dim3 g2((J + GN2 - 1) / GN2, ntasks);
+        const bool small = b_max <= 80;
+        if (stage == 0) {
+            if (small) k_eig_gemm2<T, true, 5><<<g2, 256, sm2, s>>>(d_tasks, J, 0, Sx, nrhs);
+            else k_eig_gemm2<T, true, 9><<<g2, 256, sm2, s>>>(d_tasks, J, 0, Sx, nrhs);
+        } else {
+            if (small) k_eig_gemm2<T, false, 5><<<g2, 256, sm2, s>>>(d_tasks, J, 1, Sx, nrhs);
+            else k_eig_gemm2<T, false, 9><<<g2, 256, sm2, s>>>(d_tasks, J, 1, Sx, nrhs);
+        }
+    } else if (stage == 0) {
         k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0, Sx, nrhs, kchunk);
     } else if (stage == 2) {
         k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1, Sx, nrhs, kchunk);
@@ -492,9 +592,12 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
 // that a warp's V reads fall in distinct banks).
 static constexpr int FS_THREADS = 256, FS_WARPS = FS_THREADS / 32;
 
+// Shared memory, in elements: V [b][ldv] | f^ / x^ [b][ldf] | xi of the owned modes
+// [nmode][Sx] | f of the own columns [b][ldf] (phase 1), reused as one line per warp
+// (phase 2).
 struct FsGeom {
     int ncol, nmode, ldv, ldf;
-    size_t elems;
+    size_t off_xi, off_in, elems;
 };
 HH_HD FsGeom fs_geom(int b, int Sx, int cl) {
     FsGeom g;
@@ -502,9 +605,20 @@ HH_HD FsGeom fs_geom(int b, int Sx, int cl) {
     g.nmode = (b + cl - 1) / cl;
     g.ldv = (b + 3) & ~3;
     g.ldf = g.ncol + (g.ncol & 1);
-    const size_t fin = (size_t)b * g.ldf, lines = (size_t)FS_WARPS * 2 * Sx;
-    g.elems = (size_t)b * g.ldv + (size_t)b * g.ldf + (fin > lines ? fin : lines);
+    g.off_xi = (size_t)b * g.ldv + (size_t)b * g.ldf;
+    g.off_in = g.off_xi + (((size_t)g.nmode * Sx + 1) & ~(size_t)1);
+    const size_t fin = (size_t)b * g.ldf, lines = (size_t)FS_WARPS * Sx;
+    g.elems = g.off_in + (fin > lines ? fin : lines);
     return g;
+}
+
+// Asynchronous copy of one complex element into shared memory.
+template <typename T> __device__ __forceinline__ void cp_async_elem(cplx<T>* smem, const cplx<T>* gmem);
+template <> __device__ __forceinline__ void cp_async_elem<float>(c64* smem, const c64* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+template <> __device__ __forceinline__ void cp_async_elem<double>(c128* smem, const c128* gmem) {
+    cp_async16(smem, gmem);
 }
 
 template <typename T>
@@ -527,39 +641,30 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
     extern __shared__ __align__(128) unsigned char fsm[];
     C* Vs = (C*)fsm;                              // [b][ldv], V[a][m]
     C* Fs = Vs + (size_t)b * G.ldv;               // [b][ldf], f^ then x^ of own columns
-    C* Fin = Fs + (size_t)b * G.ldf;              // [b][ldf], f of own columns (phase 1)
-    C* lines = Fin;                               // per warp as[Sx], fs[Sx] (phase 2)
+    C* XI = (C*)fsm + G.off_xi;                   // [nmode][Sx], xi of the owned modes
+    C* Fin = (C*)fsm + G.off_in;                  // [b][ldf], f of own columns (phase 1)
+    C* lines = Fin;                               // per warp one line of Sx (phase 2)
     const C* V = (const C*)tk.V;
     const C* F = (const C*)tk.F;
     C* Wout = (C*)tk.W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int mb = q * G.nmode, me = min(b, mb + G.nmode);
 
-    // stage V and the own columns of f: eight loads in flight per thread
-    const int nv = b * b, nf = b * G.ldf;
-    for (int e0 = threadIdx.x; e0 < nv + nf; e0 += 8 * FS_THREADS) {
-        C tmp[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * FS_THREADS;
-            tmp[u] = C{0, 0};
-            if (e < nv) {
-                tmp[u] = V[e];
-            } else if (e < nv + nf) {
-                const int a = (e - nv) / G.ldf, il = (e - nv) - a * G.ldf;
-                if (il < nown) tmp[u] = F[(size_t)a * Sx + c0 + il];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * FS_THREADS;
-            if (e < nv) {
-                const int a = e / b, m = e - a * b;
-                Vs[a * G.ldv + m] = tmp[u];
-            } else if (e < nv + nf) {
-                Fin[e - nv] = tmp[u];
-            }
-        }
+    // stage V, the own columns of f and the owned modes' xi, all copies in flight at once
+    for (int e = threadIdx.x; e < b * b; e += FS_THREADS) {
+        const int a = e / b, m = e - a * b;
+        cp_async_elem<T>(Vs + a * G.ldv + m, V + e);
     }
+    for (int e = threadIdx.x; e < b * G.ldf; e += FS_THREADS) {
+        const int a = e / G.ldf, il = e - a * G.ldf;
+        if (il < nown) cp_async_elem<T>(Fin + e, F + (size_t)a * Sx + c0 + il);
+        else Fin[e] = C{0, 0};
+    }
+    if (me > mb)
+        for (int e = threadIdx.x; e < (me - mb) * Sx; e += FS_THREADS)
+            cp_async_elem<T>(XI + e, (const C*)tk.xi + (size_t)mb * Sx + e);
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
 
     const int ntc = (nown + 1) / 2, ntm = (b + 3) / 4;
@@ -590,16 +695,13 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
 
     // phase 2: the owned modes' lines
     {
-        C* as = lines + (size_t)warp * 2 * Sx;
-        C* fs = as + Sx;
-        const int mend = min(b, (q + 1) * G.nmode);
-        for (int m = q * G.nmode + warp; m < mend; m += FS_WARPS) {
-            const C* xi = (const C*)tk.xi + (size_t)m * Sx;
+        C* fs = lines + (size_t)warp * Sx;
+        for (int m = mb + warp; m < me; m += FS_WARPS) {
+            const C* as = XI + (size_t)(m - mb) * Sx;
             for (int i = lane; i < Sx; i += 32) {
                 const int r = i / G.ncol;
                 const C* rem = cluster.map_shared_rank(Fs, r);
                 fs[i] = rem[m * G.ldf + (i - r * G.ncol)];
-                as[i] = xi[i];
             }
             __syncwarp();
             warp_line_solve(as, fs, Sx, lane);
