@@ -136,17 +136,23 @@ def leaf_bands(w):
 # and flops; see hh_profile_read in include/hh.h).
 CATEGORY_BOUND = {
     "factor": ("latency", "k_eig_factor (eigenpairs of the column pencil + scalar Schur recursions)"),
-    "sweep_in": ("alu", "k_eig_gemm<float,1> (f^ = V^T f, complex64 CUDA-core contraction)"),
-    "sweep_recur": ("hbm", "k_eig_recur<float> (scalar Schur recursions, warp scans)"),
-    "sweep_out": ("alu", "k_eig_gemm<float,0> (x = V x^)"),
-    "residual": ("hbm", "k_apply<double> (FP64 residual b - A u)"),
-    "coarse_project": ("hbm", "k_coarse_proj1 (fused residual + C^H r + A_c^-1, column-major C)"),
-    "galerkin": ("alu64", "k_galerkin_partial (A_c = C^H A~ C, FP64)"),
-    "qr": ("latency", "k_qr (sketch orthonormalisation)"),
-    "svd": ("latency", "k_heig (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
+    "sweep_in": ("alu", "k_eig_gemm2<float,true> (f^ = V^T f over the sketch columns, register-tiled)"),
+    "sweep_recur": ("hbm", "k_eig_recur<float> (scalar Schur recursions of the sketch columns, warp scans)"),
+    "sweep_out": ("alu", "k_eig_gemm2<float,false> (x = V x^ over the sketch columns)"),
+    "residual": ("hbm", "k_residual_cast<float> (FP64 residual b - A u, its norm partials and complex64 copy)"),
+    "coarse_project": ("hbm", "k_coarse_batch (one-column coarse corrections: residual, C^H r, A_c^-1, C y; "
+                              "one cooperative launch per level)"),
+    "galerkin": ("alu", "k_galerkin_partial<float> (A_c = C^H A~ C: FP32 products, FP64 tile sums)"),
+    "qr": ("latency", "k_qr (sketch orthonormalisation, shared-memory CGS2)"),
+    "svd": ("latency", "k_heig_tri + k_heig_vec (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
     "leaf_sweep": ("alu", "k_eig_sweep_fused<float> (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
 }
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure is available)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel, from one ncu capture of this bench (warm cache, as inside a solve); the
+# capture and its command are in profiles/coarse_batch_helm2d_n255_k40_L2.md.  To be
+# reset to None whenever k_coarse_batch changes.
+TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 71808.0}
 
 
 # --------------------------------------------------------------------- our arm
@@ -317,7 +323,7 @@ def roofline(w, prof, iters, pk, pk_kind):
     ms, launches, by, fl = prof[cat]
     out = rate(cat, ms, by, fl, pk, pk_kind)
     out.update({"launches": launches, "avg_launch_ms": ms / max(launches, 1), "share_of_profiled_ms": ms / tot_ms,
-                "traffic": None, "alg_bytes_per_launch": by / max(launches, 1),
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(cat), "alg_bytes_per_launch": by / max(launches, 1),
                 "alg_flops_per_launch": fl / max(launches, 1)})
     return out
 
