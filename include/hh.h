@@ -139,6 +139,29 @@ hh_status hh_solve_host(hh_handle* h, const void* h_f, const void* h_g, void* h_
 hh_status hh_residual(hh_handle* h, const void* d_f, const void* d_g, const void* d_u,
                       void* stream, double* rel_res);
 
+/* --------------------------------------------------------------------------------
+ * Batching form: many independent problems (each with its own parameters and grid
+ * size) set up and solved together.
+ * -------------------------------------------------------------------------------- */
+/* Sets up count problems (params[k] for out[k]): the set-ups run concurrently, up to
+ * eight at a time, each on a stream and host thread of its own; returns when all are
+ * done.  On any failure every handle created so far is destroyed, out[] is NULL and the
+ * first failing status is returned.  The handles are ordinary handles (hh_solve,
+ * hh_destroy, ...); their stream is set to `stream`. */
+hh_status hh_setup_batch(const hh_params* params, int count, void* stream, hh_handle** out);
+
+/* Solves count set-up problems: u[k] = solution of problem h[k] for d_f[k], d_g[k]
+ * (layouts as hh_solve).  When every handle uses the stationary outer iteration with
+ * n_inner = 1, the eigenbasis leaf path and at least two levels, in one precision, the
+ * problems iterate in lockstep: each iteration is one residual launch, one leaf-sweep
+ * launch, one coarse-correction launch per hierarchy height and one for the roots, for
+ * all problems together, and a problem drops out when its residual meets its own tol.
+ * Otherwise the problems are solved one after another.  stats[k] (may be NULL) gets
+ * problem k's iterations and residual; t_solve_ms is the time of the whole batch.
+ * Synchronises.  Returns HH_OK if all converged, else the first failing status. */
+hh_status hh_solve_batch(hh_handle* const* h, const void* const* d_f, const void* const* d_g, void* const* d_u,
+                         int count, void* stream, hh_stats* stats);
+
 void hh_destroy(hh_handle* h);
 const char* hh_status_string(hh_status s);
 

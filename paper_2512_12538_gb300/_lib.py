@@ -73,6 +73,8 @@ def _load():
         "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
         "hh_launch_count": (ctypes.c_ulonglong, []),
         "hh_residual_noalloc": (i, [i, i, d, vp, vp, vp, vp, P(d)]),
+        "hh_setup_batch": (i, [P(hh_params), i, vp, P(vp)]),
+        "hh_solve_batch": (i, [P(vp), P(vp), P(vp), P(vp), i, vp, P(hh_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -166,6 +168,28 @@ def hh_setup(params: hh_params, stream=None):
     fp = ctypes.c_size_t()
     _check(LIB.hh_setup(ctypes.byref(params), _stream(stream), ctypes.byref(h), ctypes.byref(fp)), "hh_setup")
     return h, fp.value
+
+
+def hh_setup_batch(params_list, stream=None) -> list:
+    """Sets up len(params_list) problems concurrently; returns their handles."""
+    n = len(params_list)
+    arr = (hh_params * n)(*params_list)
+    hs = (ctypes.c_void_p * n)()
+    _check(LIB.hh_setup_batch(arr, n, _stream(stream), hs), "hh_setup_batch")
+    return [ctypes.c_void_p(x) for x in hs]
+
+
+def hh_solve_batch(handles, fs, gs, us, stream=None, allow_noconv=False) -> list:
+    """Solves the set-up problems together (lockstep where possible); returns hh_stats
+    per problem.  fs, gs, us: device tensors (or pointers), one per handle."""
+    n = len(handles)
+    VP = ctypes.c_void_p * n
+    st = (hh_stats * n)()
+    ok = (HH_OK, HH_ENOCONV) if allow_noconv else (HH_OK,)
+    _check(LIB.hh_solve_batch(VP(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles]),
+                              VP(*[_ptr(x) for x in fs]), VP(*[_ptr(x) for x in gs]), VP(*[_ptr(x) for x in us]),
+                              n, _stream(stream), st), "hh_solve_batch", ok)
+    return list(st)
 
 
 def hh_solve(h, f, g, u, stream=None, allow_noconv=False) -> hh_stats:

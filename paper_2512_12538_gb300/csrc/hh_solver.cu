@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "../../include/hh.h"
@@ -276,6 +277,7 @@ struct Solver final : SolverBase {
     bool root_acc = false;      // output directly (accumulating onto a base iterate)
     bool pre_direct = false;    // its leaf sweeps write the owned rows into the parents
     std::vector<const void*> view_key, eview_key;
+    std::vector<EigTask> h_pre;   // host copy of the preconditioner's leaf tasks (batched solves)
     // eigenbasis leaf path
     bool eig = false;
     int eig_fused = 0;          // cluster size of the one-launch single-vector sweep (0: off)
@@ -482,6 +484,7 @@ struct Solver final : SolverBase {
         k.W = Wout;
         k.work = EWK[id];
         k.b = nodes[id].b();
+        k.Sx = Sx;
         k.w0 = 0;
         k.w1 = k.b;
         return k;
@@ -529,9 +532,11 @@ struct Solver final : SolverBase {
                 lt.push_back(k);
             }
         }
-        if (eig)
+        if (eig) {
+            h_pre = et;
             ck(cudaMemcpyAsync(d_etasks_pre, et.data(), sizeof(EigTask) * et.size(), cudaMemcpyHostToDevice, stream),
                cerr);
+        }
         else
             ck(cudaMemcpyAsync(d_tasks_pre, lt.data(), sizeof(LeafTask) * lt.size(), cudaMemcpyHostToDevice, stream),
                cerr);
@@ -1222,6 +1227,324 @@ static SolverBase* make_solver(const hh_params* P) {
     return s;
 }
 
+// A solver set up in one call (validation, allocation through the hook, set-up).
+static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out) {
+    *out = nullptr;
+    const hh_status v = validate(p);
+    if (v != HH_OK) return v;
+    std::unique_ptr<SolverBase> sb(make_solver(p));
+    sb->stream = s;
+    sb->hook = g_alloc;
+    sb->footprint = sb->plan(nullptr);
+    sb->block = dev_alloc(sb->footprint, sb->stream, sb->hook);
+    if (!sb->block) return HH_ENOMEM;
+    sb->plan((char*)sb->block);
+    sb->prof_reset(g_prof_default);
+    const hh_status st = sb->setup();
+    if (st != HH_OK) return st;
+    *out = sb.release();
+    return HH_OK;
+}
+
+// ------------------------------------------------------------------ batched solves
+// Several set-up problems solved together in lockstep (the batching form): per iteration
+// one residual launch and one norm launch for all of them, one one-launch leaf sweep over
+// all their leaves, one cooperative coarse launch per height of the hierarchy over all
+// their nodes, and one for all roots; a problem leaves the batch when it converges.
+// Requires the stationary outer iteration, n_i = 1, the eigenbasis leaf path with the
+// one-launch sweep and at least two levels, for every problem, in one precision.
+template <typename T>
+static bool batchable(const Solver<T>* p) {
+    return p->eig && p->eig_fused && p->pre_direct && p->P.n_inner == 1 && p->P.outer == HH_OUTER_ORAS && p->L >= 2;
+}
+
+template <typename T>
+static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, const c128* const* g,
+                             c128* const* uo, cudaStream_t stream, hh_stats* stats, std::vector<hh_status>& res) {
+    using CT = cplx<T>;
+    const int np = (int)ps.size();
+    // fused-sweep cluster size and shared memory for all leaves together
+    int bmax = 0, sxmax = 0, sxmin = 1 << 30, nleaf = 0;
+    for (auto* p : ps) {
+        bmax = std::max(bmax, p->b_max);
+        sxmax = std::max(sxmax, p->Sx);
+        sxmin = std::min(sxmin, p->Sx);
+        nleaf += (int)p->h_pre.size();
+    }
+    const int cl = eig_sweep_fused_ready<T>(bmax, sxmax);
+    if (!cl || cl > sxmin) return HH_ENOTIMPL;
+    // scratch: leaf tasks, residual partials and norms, coarse partials, barrier, status
+    const int part_cap = RB_MAX_JOBS * 304;
+    const size_t bytes = align_up(sizeof(EigTask) * nleaf, 256) + align_up(sizeof(double) * part_cap, 256) +
+                         align_up(sizeof(double) * (np + 8), 256) + align_up(sizeof(c128) * 304 * 64, 256) + 256;
+    AllocHook hook = g_alloc;
+    char* base = (char*)dev_alloc(bytes, stream, hook);
+    if (!base) return HH_ENOMEM;
+    size_t off = 0;
+    auto take = [&](size_t b) { char* q = base + off; off += align_up(b, 256); return q; };
+    EigTask* d_tasks = (EigTask*)take(sizeof(EigTask) * nleaf);
+    double* part = (double*)take(sizeof(double) * part_cap);
+    double* norms = (double*)take(sizeof(double) * (np + 8));
+    c128* cpart = (c128*)take(sizeof(c128) * 304 * 64);
+    unsigned* bar = (unsigned*)take(256);
+    int* berr = (int*)(bar + 4);
+    double* h_norms = nullptr;
+    cudaError_t cerr = cudaSuccess;
+    ck(cudaMallocHost(&h_norms, sizeof(double) * (np + 8)), cerr);
+    ck(cudaMemsetAsync(bar, 0, 256, stream), cerr);
+    std::vector<double> b2(np, 0.0);
+    std::vector<int> it(np, 0);
+    std::vector<double> rel(np, 0.0), best(np, 0.0), chk(np, 0.0);
+    std::vector<int> chk_it(np, 0);
+    res.assign(np, HH_OK);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, stream);
+    // right-hand sides, ||b||^2, u = 0
+    for (int k = 0; k < np; ++k) {
+        Solver<T>* p = ps[k];
+        p->stream = stream;
+        p->zero(p->derr, sizeof(int) * 4);
+        launch_rhs(f[k], g[k], p->bvec, p->P.dim, p->S, p->h, stream);
+        p->norm_sq(p->bvec, p->dnorm + 2);
+        ck(cudaMemcpyAsync(h_norms + k, p->dnorm + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        p->zero(p->u, sizeof(c128) * (size_t)p->Sy * p->Sx);
+    }
+    ck(cudaStreamSynchronize(stream), cerr);
+    for (int k = 0; k < np; ++k) b2[k] = h_norms[k];
+    std::vector<int> active(np);
+    for (int k = 0; k < np; ++k) active[k] = k;
+    std::vector<int> uploaded;
+    hh_status st = cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+    while (st == HH_OK && !active.empty()) {
+        // residuals of the active problems (FP64, plus the leaf-precision copy)
+        const int na = (int)active.size();
+        for (int c0 = 0; c0 < na; c0 += RB_MAX_JOBS) {
+            ResidBatch rb{};
+            for (int k = c0; k < na && k < c0 + RB_MAX_JOBS; ++k) {
+                Solver<T>* p = ps[active[k]];
+                ResidJob& j = rb.job[rb.njobs++];
+                j.x = p->u;
+                j.v = p->bvec;
+                j.y = p->res;
+                j.yt = p->RT;
+                j.g = p->geom(0);
+            }
+            launch_residual_batch<T>(rb, part, part_cap, norms + c0, stream);
+        }
+        ck(cudaMemcpyAsync(h_norms, norms, sizeof(double) * na, cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaMemcpyAsync(h_norms + np, berr, sizeof(int), cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaStreamSynchronize(stream), cerr);
+        if (cerr != cudaSuccess) { st = HH_ECUDA; break; }
+        if (*(const int*)(h_norms + np) == DEV_TIMEOUT) { st = HH_ETIMEOUT; break; }
+        std::vector<int> still;
+        for (int k = 0; k < na; ++k) {
+            const int q = active[k];
+            const double r2 = h_norms[k];
+            rel[q] = b2[q] > 0 ? std::sqrt(r2 / b2[q]) : 0.0;
+            if (it[q] == 0) best[q] = chk[q] = rel[q];
+            best[q] = std::min(best[q], rel[q]);
+            // the stationary iteration is not a contraction for every problem: one whose
+            // residual has grown a hundredfold past its best, or fell less than tenfold over
+            // the last 25 steps, leaves the batch early (the caller solves it by GMRES)
+            bool slow = false;
+            if (it[q] - chk_it[q] >= 25) {
+                slow = rel[q] > 0.1 * chk[q];
+                chk[q] = rel[q];
+                chk_it[q] = it[q];
+            }
+            if (!std::isfinite(rel[q]) || rel[q] > 100.0 * best[q] || (slow && rel[q] >= ps[q]->P.tol))
+                res[q] = HH_ENOCONV;
+            else if (rel[q] < ps[q]->P.tol) res[q] = HH_OK;
+            else if (it[q] >= ps[q]->P.max_iter) res[q] = HH_ENOCONV;
+            else still.push_back(q);
+        }
+        active.swap(still);
+        if (active.empty()) break;
+        // one preconditioner step for every active problem
+        if (active != uploaded) {
+            std::vector<EigTask> tk;
+            for (int q : active) tk.insert(tk.end(), ps[q]->h_pre.begin(), ps[q]->h_pre.end());
+            ck(cudaMemcpyAsync(d_tasks, tk.data(), sizeof(EigTask) * tk.size(), cudaMemcpyHostToDevice, stream), cerr);
+            uploaded = active;
+        }
+        int nt = 0, lmax = 0;
+        for (int q : active) {
+            nt += (int)ps[q]->h_pre.size();
+            lmax = std::max(lmax, ps[q]->L);
+        }
+        launch_eig_sweep_fused<T>(cl, d_tasks, nt, bmax, sxmax, stream);
+        // internal nodes, deepest first: height = L - level; level 1 writes into u (FP64)
+        for (int hgt = 1; hgt < lmax; ++hgt) {
+            for (int to64 = 0; to64 < 2; ++to64) {
+                std::vector<std::pair<int, int>> jobs;   // (problem, node)
+                for (int q : active) {
+                    const Solver<T>* p = ps[q];
+                    const int l = p->L - hgt;
+                    if (l < 1 || (l == 1) != (to64 == 1)) continue;
+                    for (int id : p->lev[l]) jobs.push_back({q, id});
+                }
+                // one launch per basis width and per CB_MAX_JOBS nodes
+                std::vector<int> widths;
+                for (auto& jn : jobs) {
+                    const int w = 2 * ps[jn.first]->r;
+                    if (std::find(widths.begin(), widths.end(), w) == widths.end()) widths.push_back(w);
+                }
+                for (int w : widths) {
+                    CoarseBatch bt{};
+                    auto flush = [&]() {
+                        if (!bt.njobs) return;
+                        if (to64) launch_coarse_batch<T, T, T, double>(bt, w, cpart, bar, berr, stream);
+                        else launch_coarse_batch<T, T, T, T>(bt, w, cpart, bar, berr, stream);
+                        bt = CoarseBatch{};
+                    };
+                    for (auto& jn : jobs) {
+                        Solver<T>* p = ps[jn.first];
+                        if (2 * p->r != w) continue;
+                        const Node& nd = p->nodes[jn.second];
+                        const int id = jn.second;
+                        CoarseJob& j = bt.job[bt.njobs++];
+                        j.C = p->C[id];
+                        j.v = p->RT + p->row_off(0, nd.ra, 1);
+                        j.w_in = p->W[id];
+                        j.out = to64 ? (void*)(p->u + p->row_off(0, nd.own_a, 1))
+                                     : (void*)(p->W[nd.parent] + p->row_off(nd.parent, nd.own_a, 1));
+                        j.Minv = p->AinvT[id];
+                        j.y = p->ycoef[id];
+                        j.g = p->geom(id);
+                        j.r0 = nd.own_a - nd.ra;
+                        j.r1 = nd.own_b - nd.ra;
+                        j.acc_out = to64;
+                        j.add_w = 1;
+                        if (bt.njobs == CB_MAX_JOBS) flush();
+                    }
+                    flush();
+                }
+            }
+        }
+        // the roots: u += C A_c^{-1} C^H (b - A u)
+        std::vector<int> widths;
+        for (int q : active)
+            if (std::find(widths.begin(), widths.end(), 2 * ps[q]->r) == widths.end()) widths.push_back(2 * ps[q]->r);
+        for (int w : widths) {
+            CoarseBatch bt{};
+            for (int q : active) {
+                Solver<T>* p = ps[q];
+                if (2 * p->r != w) continue;
+                bt.job[bt.njobs++] = p->one_job(0, p->bvec, p->u, p->u, true).job[0];
+                if (bt.njobs == CB_MAX_JOBS) {
+                    launch_coarse_batch<T, double, double, double>(bt, w, cpart, bar, berr, stream);
+                    bt = CoarseBatch{};
+                }
+            }
+            if (bt.njobs) launch_coarse_batch<T, double, double, double>(bt, w, cpart, bar, berr, stream);
+        }
+        for (int q : active) ++it[q];
+        ck(cudaGetLastError(), cerr);
+        if (cerr != cudaSuccess) st = HH_ECUDA;
+    }
+    for (int k = 0; k < np; ++k)
+        ck(cudaMemcpyAsync(uo[k], ps[k]->u, sizeof(c128) * (size_t)ps[k]->Sy * ps[k]->Sx, cudaMemcpyDeviceToDevice,
+                           stream),
+           cerr);
+    cudaEventRecord(e1, stream);
+    ck(cudaStreamSynchronize(stream), cerr);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeHost(h_norms);
+    dev_free(base, bytes, stream, hook);
+    if (stats)
+        for (int k = 0; k < np; ++k) {
+            stats[k].iters = it[k];
+            stats[k].rel_res = rel[k];
+            stats[k].t_setup_ms = ps[k]->t_setup_ms;
+            stats[k].t_solve_ms = ms;
+            stats[k].footprint_bytes = ps[k]->footprint;
+        }
+    if (st == HH_OK && cerr != cudaSuccess) st = HH_ECUDA;
+    if (st != HH_OK) return st;
+    for (int k = 0; k < np; ++k)
+        if (res[k] != HH_OK) return res[k];
+    return HH_OK;
+}
+
+// All handles in one precision and batchable: solve them together in lockstep.  Problems
+// the stationary iteration does not converge are then solved by flexible GMRES (the
+// paper's outer solver) on handles set up for it, several at a time from host threads.
+// Handles that cannot join the lockstep batch are solved one by one.
+static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out);
+
+static hh_status solve_many(SolverBase* const* hs, const c128* const* f, const c128* const* g, c128* const* u, int n,
+                            cudaStream_t stream, hh_stats* stats) {
+    std::vector<Solver<float>*> pf;
+    std::vector<Solver<double>*> pd;
+    for (int k = 0; k < n; ++k) {
+        if (auto* a = dynamic_cast<Solver<float>*>(hs[k])) { if (batchable(a)) pf.push_back(a); }
+        else if (auto* b = dynamic_cast<Solver<double>*>(hs[k])) { if (batchable(b)) pd.push_back(b); }
+    }
+    std::vector<hh_status> per;
+    hh_status st = HH_ENOTIMPL;
+    if ((int)pf.size() == n) st = batch_solve<float>(pf, f, g, u, stream, stats, per);
+    else if ((int)pd.size() == n) st = batch_solve<double>(pd, f, g, u, stream, stats, per);
+    if (st == HH_ENOTIMPL) {
+        hh_status first = HH_OK;
+        for (int k = 0; k < n; ++k) {
+            hs[k]->stream = stream;
+            const hh_status s1 = hs[k]->solve(f[k], g[k], u[k], stats ? stats + k : nullptr);
+            if (s1 != HH_OK && first == HH_OK) first = s1;
+        }
+        return first;
+    }
+    if (st != HH_OK && st != HH_ENOCONV) return st;
+    std::vector<int> rescue;
+    for (int k = 0; k < n; ++k)
+        if (per[k] == HH_ENOCONV) rescue.push_back(k);
+    if (rescue.empty()) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HH_ECUDA;
+    std::vector<hh_status> rs(rescue.size(), HH_OK);
+    const int nw = std::min((int)rescue.size(), 8);
+    auto worker = [&](int w) {
+        cudaSetDevice(dev);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            for (size_t i = w; i < rescue.size(); i += nw) rs[i] = HH_ECUDA;
+            return;
+        }
+        for (size_t i = w; i < rescue.size(); i += nw) {
+            const int k = rescue[i];
+            hh_params q = hs[k]->P;
+            q.outer = HH_OUTER_GMRES;
+            if (q.restart < 1 || q.restart > 64) q.restart = 40;
+            SolverBase* g2 = nullptr;
+            rs[i] = setup_one(&q, ws, &g2);
+            if (rs[i] != HH_OK) continue;
+            hh_stats s2{};
+            rs[i] = g2->solve(f[k], g[k], u[k], &s2);
+            if (stats) {
+                stats[k].iters += s2.iters;
+                stats[k].rel_res = s2.rel_res;
+            }
+            cudaStreamSynchronize(ws);
+            delete g2;
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    // the batch wrote its last iterates on `stream`: the rescues overwrite them on theirs
+    cudaStreamSynchronize(stream);
+    std::vector<std::thread> th;
+    for (int w = 1; w < nw; ++w) th.emplace_back(worker, w);
+    worker(0);
+    for (auto& t : th) t.join();
+    for (auto s1 : rs)
+        if (s1 != HH_OK) return s1;
+    return HH_OK;
+}
+
 }  // namespace hh
 
 // ============================================================================= C-ABI
@@ -1267,6 +1590,61 @@ hh_status hh_setup(const hh_params* params, void* stream, hh_handle** out, size_
     if (st != HH_OK) return st;
     *out = new hh_handle{s.release()};
     return HH_OK;
+}
+
+hh_status hh_setup_batch(const hh_params* params, int count, void* stream, hh_handle** out) {
+    if (!params || !out || count < 1) return HH_EINVAL;
+    for (int k = 0; k < count; ++k) {
+        out[k] = nullptr;
+        const hh_status v = hh::validate(params + k);
+        if (v != HH_OK) return v;
+    }
+    // set-ups are latency-bound chains of small kernels: run several at once, each on its
+    // own stream from its own host thread
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HH_ECUDA;
+    const int nw = std::min(count, 8);
+    std::vector<hh_status> st(count, HH_OK);
+    auto worker = [&](int w) {
+        cudaSetDevice(dev);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int k = w; k < count; k += nw) st[k] = HH_ECUDA;
+            return;
+        }
+        for (int k = w; k < count; k += nw) {
+            size_t fp = 0;
+            st[k] = hh_setup(params + k, ws, &out[k], &fp);
+            if (out[k]) out[k]->s->stream = (cudaStream_t)stream;
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> th;
+    for (int w = 1; w < nw; ++w) th.emplace_back(worker, w);
+    worker(0);
+    for (auto& t : th) t.join();
+    for (int k = 0; k < count; ++k)
+        if (st[k] != HH_OK) {
+            for (int j = 0; j < count; ++j) {
+                hh_destroy(out[j]);
+                out[j] = nullptr;
+            }
+            return st[k];
+        }
+    return HH_OK;
+}
+
+hh_status hh_solve_batch(hh_handle* const* h, const void* const* d_f, const void* const* d_g, void* const* d_u,
+                         int count, void* stream, hh_stats* stats) {
+    if (!h || !d_f || !d_g || !d_u || count < 1) return HH_EINVAL;
+    std::vector<hh::SolverBase*> hs(count);
+    for (int k = 0; k < count; ++k) {
+        if (!h[k] || !d_f[k] || !d_g[k] || !d_u[k]) return HH_EINVAL;
+        hs[k] = h[k]->s;
+    }
+    return hh::solve_many(hs.data(), (const c128* const*)d_f, (const c128* const*)d_g, (c128* const*)d_u, count,
+                          (cudaStream_t)stream, stats);
 }
 
 hh_status hh_solve(hh_handle* h, const void* d_f, const void* d_g, void* d_u, void* stream, hh_stats* stats) {

@@ -627,7 +627,7 @@ struct alignas(2 * sizeof(cplx<T>)) cpair {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* __restrict__ tasks, int Sx) {
+__global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* __restrict__ tasks) {
     using C = cplx<T>;
     using C2 = cpair<T>;
     cg::cluster_group cluster = cg::this_cluster();
@@ -635,6 +635,7 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
     const int cl = (int)cluster.num_blocks();
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
+    const int Sx = tk.Sx;
     const FsGeom G = fs_geom(b, Sx, cl);
     const int c0 = q * G.ncol;
     const int nown = max(0, min(Sx, c0 + G.ncol) - c0);
@@ -794,7 +795,7 @@ void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_ma
     const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx, cl).elems;
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = fs_config<T>(cl, ntasks, sm, s, at);
-    cudaLaunchKernelEx(&cfg, k_eig_sweep_fused<T>, d_tasks, Sx);
+    cudaLaunchKernelEx(&cfg, k_eig_sweep_fused<T>, d_tasks);
     note_launch();
 }
 

@@ -2,6 +2,8 @@
 // (Eqs. (2)-(3) need f - A u at every level), right-hand-side assembly (Eq. (1),
 // Sec. 3.1), precision casts and restricted prolongation (Sec. 1), the interface
 // traces B_s A~_s (Sec. 2), the counter-based sketch and the coarse update C y.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace hh {
@@ -113,6 +115,77 @@ void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
 template void launch_residual_cast<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, int*, cudaStream_t);
 template void launch_residual_cast<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, int*,
                                            cudaStream_t);
+
+// Residuals of several problems in one launch (the batched solver): job k owns blocks
+// [blk0, blk0 + nblk) and computes y = v - A x, its complex64/128 copy yt and per-block
+// |y|^2 partials at part[blockIdx.x]; then one block per job adds its partials in order.
+template <typename T>
+__global__ void k_residual_batch(ResidBatch bt, double* part) {
+    int jb = 0;
+    while (jb + 1 < bt.njobs && blockIdx.x >= bt.job[jb + 1].blk0) ++jb;
+    const ResidJob& J = bt.job[jb];
+    const OpGeom g = J.g;
+    const size_t total = (size_t)g.b * g.Sx;
+    const unsigned lb = blockIdx.x - J.blk0;
+    double acc2 = 0.0;
+    for (size_t t = lb * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)J.nblk * blockDim.x) {
+        const int i = (int)(t % g.Sx);
+        const int j = (int)(t / g.Sx);
+        c128 ax = op_diag(j, i, g) * J.x[t];
+        const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+        if (g.Sx > 1) {
+            if (i > 0) ax = ax - wj * J.x[t - 1];
+            if (i < g.Sx - 1) ax = ax - wj * J.x[t + 1];
+        }
+        if (j > 0) ax = ax - wi * J.x[t - g.Sx];
+        if (j < g.b - 1) ax = ax - wi * J.x[t + g.Sx];
+        const c128 out = J.v[t] - ax;
+        J.y[t] = out;
+        ((cplx<T>*)J.yt)[t] = cvt<T>(out);
+        acc2 += abs2(out);
+    }
+    __shared__ double red[32];
+    acc2 = warp_sum(acc2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s2 = warp_sum(s2);
+        if (threadIdx.x == 0) part[blockIdx.x] = s2;
+    }
+}
+__global__ void k_sum_batch(ResidBatch bt, const double* part, double* norms) {
+    const ResidJob& J = bt.job[blockIdx.x];
+    double a = 0.0;
+    for (unsigned i = threadIdx.x; i < J.nblk; i += blockDim.x) a += part[J.blk0 + i];
+    __shared__ double red[32];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s2 = warp_sum(s2);
+        if (threadIdx.x == 0) norms[blockIdx.x] = s2;
+    }
+}
+template <typename T>
+void launch_residual_batch(ResidBatch bt, double* part, int part_cap, double* norms, cudaStream_t s) {
+    if (bt.njobs < 1) return;
+    const int cap = std::max(1, std::min(152 * 2, part_cap / bt.njobs));
+    unsigned blk = 0;
+    for (int k = 0; k < bt.njobs; ++k) {
+        const size_t n = (size_t)bt.job[k].g.b * bt.job[k].g.Sx;
+        bt.job[k].blk0 = blk;
+        bt.job[k].nblk = (unsigned)grid_for(n, 256, cap);
+        blk += bt.job[k].nblk;
+    }
+    k_residual_batch<T><<<blk, 256, 0, s>>>(bt, part);
+    note_launch();
+    k_sum_batch<<<bt.njobs, 256, 0, s>>>(bt, part, norms);
+    note_launch();
+}
+template void launch_residual_batch<float>(ResidBatch, double*, int, double*, cudaStream_t);
+template void launch_residual_batch<double>(ResidBatch, double*, int, double*, cudaStream_t);
 
 __global__ void k_sum(const double* part, int n, double* out) {
     double a = 0.0;

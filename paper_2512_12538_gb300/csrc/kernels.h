@@ -21,6 +21,24 @@ template <typename T>
 void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, int* nblk_out,
                           cudaStream_t s);
 
+// Residuals of up to RB_MAX_JOBS problems in one launch: per job y = v - A x (FP64) and
+// yt = y in T; norms[k] = ||y_k||^2 (fixed-order sums).  part: scratch of part_cap doubles.
+constexpr int RB_MAX_JOBS = 32;
+struct ResidJob {
+    const c128* x;
+    const c128* v;
+    c128* y;
+    void* yt;
+    OpGeom g;
+    unsigned blk0, nblk;   // set by the launcher
+};
+struct ResidBatch {
+    ResidJob job[RB_MAX_JOBS];
+    int njobs;
+};
+template <typename T>
+void launch_residual_batch(ResidBatch bt, double* part, int part_cap, double* norms, cudaStream_t s);
+
 // out = sum of n doubles (deterministic single-block reduction)
 void launch_sum(const double* part, int n, double* out, cudaStream_t s);
 
@@ -168,6 +186,7 @@ struct EigTask {
     void* W;          // solutions [b][Sx][nrhs]
     void* work;       // set-up workspace, eig_work_elems(b) complex128 (used as complex<T>)
     int b;
+    int Sx;           // columns of the leaf's problem (tasks of several problems may share a launch)
     int w0, w1;       // the one-launch sweep writes local rows [w0, w1) only, row a to
                       // W + (a - w0) Sx (the three-stage sweep: all rows, w0 = 0, w1 = b)
 };
@@ -184,6 +203,7 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
 constexpr int FS_SMEM_MAX = 220 * 1024;
 template <typename T>
 int eig_sweep_fused_ready(int b_max, int Sx);
+// b_max, Sx: the largest band and column count among the tasks (shared-memory size).
 template <typename T>
 void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s);
 // stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^

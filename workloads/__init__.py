@@ -6,6 +6,7 @@ solver's arithmetic lives here (see ``generators`` for what each input is).
 from .generators import (  # noqa: F401
     WORKLOADS,
     Workload,
+    batch_problems,
     random_complex,
     point_source_rhs,
     plane_wave_2d,

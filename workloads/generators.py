@@ -130,3 +130,25 @@ def problem_inputs(w: Workload, index: int = 0):
         f = point_source_rhs(w.n, seed)
     g = np.zeros((4, w.S), dtype=np.complex128)
     return f, g
+
+
+def batch_problems(count: int, seed: int = BASE_SEED + 7, sides=(63, 127, 191, 255), kh=(0.3, 0.6),
+                   levels: int = 2, overlap: int = 2, rank: int = 16, oversample: int = 8):
+    """The batching-form workload: ``count`` independent 2D problems.
+
+    Grid sides n drawn uniformly from ``sides``, k such that k h is uniform in ``kh``
+    (h = 1/(n+1)), a ``levels``-level strip hierarchy, overlap, rank and oversampling as
+    given (512 problems with these defaults is the batch configuration).  Each problem
+    gets its own seeded point-source right-hand side and zero impedance data.  Returns a
+    list of (Workload, f, g).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(sides[int(rng.integers(len(sides)))])
+        k = float(rng.uniform(kh[0], kh[1]) * (n + 1))
+        w = Workload(f"batch{i}_n{n}", 2, n, k, levels, overlap, rank, oversample)
+        f = point_source_rhs(n, seed + 17 * (i + 1))
+        g = np.zeros((4, n + 2), dtype=np.complex128)
+        out.append((w, f, g))
+    return out
