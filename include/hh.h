@@ -51,8 +51,9 @@ typedef enum {
     HH_ETIMEOUT = -5,     /* a bounded device-side wait gave up                       */
     HH_ECUDA = -6,        /* a CUDA runtime call failed                               */
     HH_ENOTIMPL = -7,
-    HH_ETOOLARGE = -8     /* the problem does not fit a fixed-size static scratch     */
+    HH_ETOOLARGE = -8,    /* the problem does not fit a fixed-size static scratch     */
                           /* (hh_residual_noalloc: n + 2 > HH_NOALLOC_MAX_ROWS)       */
+    HH_EPENDING = -9      /* hh_server_poll: the request has not finished yet         */
 } hh_status;
 
 typedef enum {
@@ -99,6 +100,8 @@ typedef struct {
     double t_setup_ms;    /* device time of hh_setup (CUDA events)                       */
     double t_solve_ms;    /* device time of the last hh_solve                            */
     size_t footprint_bytes;
+    double t_queue_ms;    /* served requests: submission to admission (host clock)       */
+    double t_total_ms;    /* served requests: submission to completion (host clock)      */
 } hh_stats;
 
 typedef struct hh_handle hh_handle;
@@ -161,6 +164,42 @@ hh_status hh_setup_batch(const hh_params* params, int count, void* stream, hh_ha
  * Synchronises.  Returns HH_OK if all converged, else the first failing status. */
 hh_status hh_solve_batch(hh_handle* const* h, const void* const* d_f, const void* const* d_g, void* const* d_u,
                          int count, void* stream, hh_stats* stats);
+
+/* --------------------------------------------------------------------------------
+ * Serving form: a request loop with continuous batching.  Requests (any grid size,
+ * wavenumber and hierarchy) are admitted while the sum of their footprints
+ * (hh_footprint) stays within hbm_budget bytes and fewer than max_slots are in flight.
+ * Four set-up workers set admitted requests up concurrently, each on a stream of its own;
+ * one engine thread iterates all set-up requests together (the lockstep iteration of
+ * hh_solve_batch), taking new ones in between iterations and retiring each as soon as
+ * its residual meets its tol.  Requests the lockstep iteration cannot take are solved by
+ * their worker; requests whose stationary iteration does not converge are re-solved by
+ * flexible GMRES.  Server problems allocate from the CUDA runtime's stream-ordered pool,
+ * not through hh_set_allocator.
+ * -------------------------------------------------------------------------------- */
+typedef struct hh_server hh_server;
+
+/* Starts the server threads on the current device.  HH_EINVAL for max_slots outside
+ * [1, 4096] or a zero budget. */
+hh_status hh_server_create(size_t hbm_budget, int max_slots, hh_server** out);
+
+/* Queues one request and returns at once with its ticket.  d_f, d_g (read) and d_u
+ * (written) are device arrays laid out as for hh_solve; they must stay valid, and d_f,
+ * d_g unchanged, until the ticket has finished, and must hold their data (the caller's
+ * stream synchronised) before the call.  HH_EINVAL for invalid parameters, HH_ENOMEM
+ * when the request's footprint alone exceeds the budget. */
+hh_status hh_server_submit(hh_server* srv, const hh_params* params, const void* d_f, const void* d_g, void* d_u,
+                           unsigned long long* ticket);
+
+/* Non-blocking.  HH_EPENDING while the request is queued or in flight; HH_OK once it has
+ * finished, with *result its status (as hh_solve's) and *stats (may be NULL) its
+ * iterations, residual, set-up and solve times, footprint, queueing and total latency;
+ * d_u then holds the solution.  A finished ticket is forgotten after it has been polled
+ * (polling it again gives HH_EINVAL). */
+hh_status hh_server_poll(hh_server* srv, unsigned long long ticket, hh_status* result, hh_stats* stats);
+
+/* Stops the threads (queued and in-flight requests are abandoned) and frees everything. */
+void hh_server_destroy(hh_server* srv);
 
 void hh_destroy(hh_handle* h);
 const char* hh_status_string(hh_status s);

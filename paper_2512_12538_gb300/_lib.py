@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libhh.so")
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ENOCONV, HH_EBREAKDOWN, HH_ETIMEOUT, HH_ECUDA, HH_ENOTIMPL = (
     0, -1, -2, -3, -4, -5, -6, -7)
 HH_ETOOLARGE = -8
+HH_EPENDING = -9
 HH_NOALLOC_MAX_ROWS = 16384
 HH_PREC_FP64, HH_PREC_MIXED = 0, 1
 HH_LEAF_EIGEN, HH_LEAF_BLOCK = 0, 1
@@ -34,7 +35,8 @@ class hh_params(ctypes.Structure):
 class hh_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
-                ("footprint_bytes", ctypes.c_size_t)]
+                ("footprint_bytes", ctypes.c_size_t), ("t_queue_ms", ctypes.c_double),
+                ("t_total_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -74,6 +76,10 @@ def _load():
         "hh_launch_count": (ctypes.c_ulonglong, []),
         "hh_residual_noalloc": (i, [i, i, d, vp, vp, vp, vp, P(d)]),
         "hh_setup_batch": (i, [P(hh_params), i, vp, P(vp)]),
+        "hh_server_create": (i, [sz, i, P(vp)]),
+        "hh_server_submit": (i, [vp, P(hh_params), vp, vp, vp, P(ctypes.c_ulonglong)]),
+        "hh_server_poll": (i, [vp, ctypes.c_ulonglong, P(i), P(hh_stats)]),
+        "hh_server_destroy": (None, [vp]),
         "hh_solve_batch": (i, [P(vp), P(vp), P(vp), P(vp), i, vp, P(hh_stats)]),
     }
     for name, (res, args) in sig.items():
@@ -190,6 +196,35 @@ def hh_solve_batch(handles, fs, gs, us, stream=None, allow_noconv=False) -> list
                               VP(*[_ptr(x) for x in fs]), VP(*[_ptr(x) for x in gs]), VP(*[_ptr(x) for x in us]),
                               n, _stream(stream), st), "hh_solve_batch", ok)
     return list(st)
+
+
+def hh_server_create(hbm_budget: int, max_slots: int):
+    srv = ctypes.c_void_p()
+    _check(LIB.hh_server_create(int(hbm_budget), int(max_slots), ctypes.byref(srv)), "hh_server_create")
+    return srv
+
+
+def hh_server_submit(srv, params: hh_params, f, g, u) -> int:
+    """Queues one request; f, g, u device tensors that must stay alive until it finishes."""
+    t = ctypes.c_ulonglong()
+    _check(LIB.hh_server_submit(srv, ctypes.byref(params), _ptr(f), _ptr(g), _ptr(u), ctypes.byref(t)),
+           "hh_server_submit")
+    return t.value
+
+
+def hh_server_poll(srv, ticket: int):
+    """None while pending, else (status, hh_stats)."""
+    res = ctypes.c_int()
+    st = hh_stats()
+    r = LIB.hh_server_poll(srv, ctypes.c_ulonglong(ticket), ctypes.byref(res), ctypes.byref(st))
+    if r == HH_EPENDING:
+        return None
+    _check(r, "hh_server_poll")
+    return res.value, st
+
+
+def hh_server_destroy(srv) -> None:
+    LIB.hh_server_destroy(srv)
 
 
 def hh_solve(h, f, g, u, stream=None, allow_noconv=False) -> hh_stats:

@@ -19,9 +19,14 @@
 // contiguous row window of its parent's residual buffer.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -1228,13 +1233,13 @@ static SolverBase* make_solver(const hh_params* P) {
 }
 
 // A solver set up in one call (validation, allocation through the hook, set-up).
-static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out) {
+static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out, const AllocHook& hook) {
     *out = nullptr;
     const hh_status v = validate(p);
     if (v != HH_OK) return v;
     std::unique_ptr<SolverBase> sb(make_solver(p));
     sb->stream = s;
-    sb->hook = g_alloc;
+    sb->hook = hook;
     sb->footprint = sb->plan(nullptr);
     sb->block = dev_alloc(sb->footprint, sb->stream, sb->hook);
     if (!sb->block) return HH_ENOMEM;
@@ -1258,72 +1263,110 @@ static bool batchable(const Solver<T>* p) {
     return p->eig && p->eig_fused && p->pre_direct && p->P.n_inner == 1 && p->P.outer == HH_OUTER_ORAS && p->L >= 2;
 }
 
+// Lockstep iteration of several set-up problems: the engine of the batching and serving
+// forms.  Problems are added with their right-hand sides and leave when they converge (or
+// when the stationary iteration stops contracting for them); each step() is one
+// iteration for all current problems: one residual launch and one norm launch, one
+// one-launch leaf sweep over all their leaves, one cooperative coarse launch per
+// hierarchy height and one for the roots.
 template <typename T>
-static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, const c128* const* g,
-                             c128* const* uo, cudaStream_t stream, hh_stats* stats, std::vector<hh_status>& res) {
-    using CT = cplx<T>;
-    const int np = (int)ps.size();
-    // fused-sweep cluster size and shared memory for all leaves together
-    int bmax = 0, sxmax = 0, sxmin = 1 << 30, nleaf = 0;
-    for (auto* p : ps) {
-        bmax = std::max(bmax, p->b_max);
-        sxmax = std::max(sxmax, p->Sx);
-        sxmin = std::min(sxmin, p->Sx);
-        nleaf += (int)p->h_pre.size();
-    }
-    const int cl = eig_sweep_fused_ready<T>(bmax, sxmax);
-    if (!cl || cl > sxmin) return HH_ENOTIMPL;
-    // scratch: leaf tasks, residual partials and norms, coarse partials, barrier, status
-    const int part_cap = RB_MAX_JOBS * 304;
-    const size_t bytes = align_up(sizeof(EigTask) * nleaf, 256) + align_up(sizeof(double) * part_cap, 256) +
-                         align_up(sizeof(double) * (np + 8), 256) + align_up(sizeof(c128) * 304 * 64, 256) + 256;
-    AllocHook hook = g_alloc;
-    char* base = (char*)dev_alloc(bytes, stream, hook);
-    if (!base) return HH_ENOMEM;
-    size_t off = 0;
-    auto take = [&](size_t b) { char* q = base + off; off += align_up(b, 256); return q; };
-    EigTask* d_tasks = (EigTask*)take(sizeof(EigTask) * nleaf);
-    double* part = (double*)take(sizeof(double) * part_cap);
-    double* norms = (double*)take(sizeof(double) * (np + 8));
-    c128* cpart = (c128*)take(sizeof(c128) * 304 * 64);
-    unsigned* bar = (unsigned*)take(256);
-    int* berr = (int*)(bar + 4);
-    double* h_norms = nullptr;
+struct BatchEngine {
+    struct Prob {
+        Solver<T>* p = nullptr;
+        c128* uo = nullptr;          // where the solution goes when the problem leaves
+        void* tag = nullptr;
+        int it = 0, chk_it = 0;
+        double rel = 0.0, best = 0.0, chk = 0.0;
+        hh_status st = HH_OK;
+    };
+    cudaStream_t stream = nullptr;
+    int cap_probs = 0, cap_tasks = 0;
+    AllocHook hook;
+    char* base = nullptr;
+    size_t bytes = 0;
+    EigTask* d_tasks = nullptr;
+    double* part = nullptr;
+    double* norms = nullptr;
+    c128* cpart = nullptr;
+    unsigned* bar = nullptr;
+    int* berr = nullptr;
+    double* h_norms = nullptr;       // pinned
+    int part_cap = RB_MAX_JOBS * 304;
+    std::vector<Prob> act;
+    std::vector<Solver<T>*> uploaded;
+    int cl = 0, bmax = 0, sxmax = 0;
     cudaError_t cerr = cudaSuccess;
-    ck(cudaMallocHost(&h_norms, sizeof(double) * (np + 8)), cerr);
-    ck(cudaMemsetAsync(bar, 0, 256, stream), cerr);
-    std::vector<double> b2(np, 0.0);
-    std::vector<int> it(np, 0);
-    std::vector<double> rel(np, 0.0), best(np, 0.0), chk(np, 0.0);
-    std::vector<int> chk_it(np, 0);
-    res.assign(np, HH_OK);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, stream);
-    // right-hand sides, ||b||^2, u = 0
-    for (int k = 0; k < np; ++k) {
-        Solver<T>* p = ps[k];
+
+    hh_status init(cudaStream_t s, int probs, int tasks, const AllocHook& h) {
+        stream = s;
+        cap_probs = std::max(probs, 1);
+        cap_tasks = std::max(tasks, 1);
+        hook = h;
+        bytes = align_up(sizeof(EigTask) * cap_tasks, 256) + align_up(sizeof(double) * part_cap, 256) +
+                align_up(sizeof(double) * (cap_probs + 8), 256) + align_up(sizeof(c128) * 304 * 64, 256) + 256;
+        base = (char*)dev_alloc(bytes, stream, hook);
+        if (!base) return HH_ENOMEM;
+        size_t off = 0;
+        auto take = [&](size_t b) { char* q = base + off; off += align_up(b, 256); return q; };
+        d_tasks = (EigTask*)take(sizeof(EigTask) * cap_tasks);
+        part = (double*)take(sizeof(double) * part_cap);
+        norms = (double*)take(sizeof(double) * (cap_probs + 8));
+        cpart = (c128*)take(sizeof(c128) * 304 * 64);
+        bar = (unsigned*)take(256);
+        berr = (int*)(bar + 4);
+        ck(cudaMallocHost(&h_norms, sizeof(double) * (cap_probs + 8)), cerr);
+        ck(cudaMemsetAsync(bar, 0, 256, stream), cerr);
+        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+    }
+    void release() {
+        if (h_norms) cudaFreeHost(h_norms);
+        h_norms = nullptr;
+        if (base) dev_free(base, bytes, stream, hook);
+        base = nullptr;
+    }
+    int tasks_in_use() const {
+        int n = 0;
+        for (auto& q : act) n += (int)q.p->h_pre.size();
+        return n;
+    }
+    // whether p can join: lockstep-able, room left, and a fused-sweep cluster size that
+    // serves every member
+    bool can_add(Solver<T>* p) const {
+        if (!batchable(p) || (int)act.size() >= cap_probs) return false;
+        if (tasks_in_use() + (int)p->h_pre.size() > cap_tasks) return false;
+        int bm = p->b_max, sx = p->Sx, smin = p->Sx;
+        for (auto& q : act) {
+            bm = std::max(bm, q.p->b_max);
+            sx = std::max(sx, q.p->Sx);
+            smin = std::min(smin, q.p->Sx);
+        }
+        const int c = eig_sweep_fused_ready<T>(bm, sx);
+        return c && c <= smin;
+    }
+    // enqueue the right-hand side, ||b||^2 and u = 0 of a problem that joins
+    void add(Solver<T>* p, const c128* f, const c128* g, c128* uo, void* tag) {
         p->stream = stream;
         p->zero(p->derr, sizeof(int) * 4);
-        launch_rhs(f[k], g[k], p->bvec, p->P.dim, p->S, p->h, stream);
+        launch_rhs(f, g, p->bvec, p->P.dim, p->S, p->h, stream);
         p->norm_sq(p->bvec, p->dnorm + 2);
-        ck(cudaMemcpyAsync(h_norms + k, p->dnorm + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaMemcpyAsync(p->h_norm + 2, p->dnorm + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
         p->zero(p->u, sizeof(c128) * (size_t)p->Sy * p->Sx);
+        Prob q;
+        q.p = p;
+        q.uo = uo;
+        q.tag = tag;
+        q.it = -1;   // the first step reads ||b||^2
+        act.push_back(q);
     }
-    ck(cudaStreamSynchronize(stream), cerr);
-    for (int k = 0; k < np; ++k) b2[k] = h_norms[k];
-    std::vector<int> active(np);
-    for (int k = 0; k < np; ++k) active[k] = k;
-    std::vector<int> uploaded;
-    hh_status st = cerr == cudaSuccess ? HH_OK : HH_ECUDA;
-    while (st == HH_OK && !active.empty()) {
-        // residuals of the active problems (FP64, plus the leaf-precision copy)
-        const int na = (int)active.size();
+    // One iteration for every current problem; problems that leave are appended to `done`
+    // (their solution already copied to uo, the copy complete).
+    hh_status step(std::vector<Prob>& done) {
+        if (act.empty()) return HH_OK;
+        const int na = (int)act.size();
         for (int c0 = 0; c0 < na; c0 += RB_MAX_JOBS) {
             ResidBatch rb{};
             for (int k = c0; k < na && k < c0 + RB_MAX_JOBS; ++k) {
-                Solver<T>* p = ps[active[k]];
+                Solver<T>* p = act[k].p;
                 ResidJob& j = rb.job[rb.njobs++];
                 j.x = p->u;
                 j.v = p->bvec;
@@ -1334,63 +1377,86 @@ static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, 
             launch_residual_batch<T>(rb, part, part_cap, norms + c0, stream);
         }
         ck(cudaMemcpyAsync(h_norms, norms, sizeof(double) * na, cudaMemcpyDeviceToHost, stream), cerr);
-        ck(cudaMemcpyAsync(h_norms + np, berr, sizeof(int), cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaMemcpyAsync(h_norms + cap_probs, berr, sizeof(int), cudaMemcpyDeviceToHost, stream), cerr);
         ck(cudaStreamSynchronize(stream), cerr);
-        if (cerr != cudaSuccess) { st = HH_ECUDA; break; }
-        if (*(const int*)(h_norms + np) == DEV_TIMEOUT) { st = HH_ETIMEOUT; break; }
-        std::vector<int> still;
+        if (cerr != cudaSuccess) return HH_ECUDA;
+        if (*(const int*)(h_norms + cap_probs) == DEV_TIMEOUT) return HH_ETIMEOUT;
+        std::vector<Prob> still;
+        bool left = false;
         for (int k = 0; k < na; ++k) {
-            const int q = active[k];
-            const double r2 = h_norms[k];
-            rel[q] = b2[q] > 0 ? std::sqrt(r2 / b2[q]) : 0.0;
-            if (it[q] == 0) best[q] = chk[q] = rel[q];
-            best[q] = std::min(best[q], rel[q]);
+            Prob& q = act[k];
+            if (q.it < 0) q.it = 0;
+            const double b2 = q.p->h_norm[2];
+            q.rel = b2 > 0 ? std::sqrt(h_norms[k] / b2) : 0.0;
+            if (q.it == 0) q.best = q.chk = q.rel;
+            q.best = std::min(q.best, q.rel);
             // the stationary iteration is not a contraction for every problem: one whose
             // residual has grown a hundredfold past its best, or fell less than tenfold over
-            // the last 25 steps, leaves the batch early (the caller solves it by GMRES)
+            // the last 25 steps, leaves early (its owner solves it by GMRES)
             bool slow = false;
-            if (it[q] - chk_it[q] >= 25) {
-                slow = rel[q] > 0.1 * chk[q];
-                chk[q] = rel[q];
-                chk_it[q] = it[q];
+            if (q.it - q.chk_it >= 25) {
+                slow = q.rel > 0.1 * q.chk;
+                q.chk = q.rel;
+                q.chk_it = q.it;
             }
-            if (!std::isfinite(rel[q]) || rel[q] > 100.0 * best[q] || (slow && rel[q] >= ps[q]->P.tol))
-                res[q] = HH_ENOCONV;
-            else if (rel[q] < ps[q]->P.tol) res[q] = HH_OK;
-            else if (it[q] >= ps[q]->P.max_iter) res[q] = HH_ENOCONV;
-            else still.push_back(q);
+            bool out = true;
+            if (!std::isfinite(q.rel) || q.rel > 100.0 * q.best || (slow && q.rel >= q.p->P.tol)) q.st = HH_ENOCONV;
+            else if (q.rel < q.p->P.tol) q.st = HH_OK;
+            else if (q.it >= q.p->P.max_iter) q.st = HH_ENOCONV;
+            else out = false;
+            if (out) {
+                ck(cudaMemcpyAsync(q.uo, q.p->u, sizeof(c128) * (size_t)q.p->Sy * q.p->Sx, cudaMemcpyDeviceToDevice,
+                                   stream),
+                   cerr);
+                done.push_back(q);
+                left = true;
+            } else {
+                still.push_back(q);
+            }
         }
-        active.swap(still);
-        if (active.empty()) break;
-        // one preconditioner step for every active problem
-        if (active != uploaded) {
+        if (left) ck(cudaStreamSynchronize(stream), cerr);
+        act.swap(still);
+        if (act.empty()) return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+        // one preconditioner step for every current problem
+        std::vector<Solver<T>*> ids;
+        for (auto& q : act) ids.push_back(q.p);
+        if (ids != uploaded) {
             std::vector<EigTask> tk;
-            for (int q : active) tk.insert(tk.end(), ps[q]->h_pre.begin(), ps[q]->h_pre.end());
-            ck(cudaMemcpyAsync(d_tasks, tk.data(), sizeof(EigTask) * tk.size(), cudaMemcpyHostToDevice, stream), cerr);
-            uploaded = active;
+            bmax = sxmax = 0;
+            int smin = 1 << 30;
+            for (auto* p : ids) {
+                tk.insert(tk.end(), p->h_pre.begin(), p->h_pre.end());
+                bmax = std::max(bmax, p->b_max);
+                sxmax = std::max(sxmax, p->Sx);
+                smin = std::min(smin, p->Sx);
+            }
+            cl = eig_sweep_fused_ready<T>(bmax, sxmax);
+            if (!cl || cl > smin) return HH_ENOTIMPL;
+            ck(cudaMemcpyAsync(d_tasks, tk.data(), sizeof(EigTask) * tk.size(), cudaMemcpyHostToDevice, stream),
+               cerr);
+            // the pageable source must stay alive until the copy has read it
+            ck(cudaStreamSynchronize(stream), cerr);
+            uploaded = ids;
         }
         int nt = 0, lmax = 0;
-        for (int q : active) {
-            nt += (int)ps[q]->h_pre.size();
-            lmax = std::max(lmax, ps[q]->L);
+        for (auto* p : ids) {
+            nt += (int)p->h_pre.size();
+            lmax = std::max(lmax, p->L);
         }
         launch_eig_sweep_fused<T>(cl, d_tasks, nt, bmax, sxmax, stream);
         // internal nodes, deepest first: height = L - level; level 1 writes into u (FP64)
         for (int hgt = 1; hgt < lmax; ++hgt) {
             for (int to64 = 0; to64 < 2; ++to64) {
-                std::vector<std::pair<int, int>> jobs;   // (problem, node)
-                for (int q : active) {
-                    const Solver<T>* p = ps[q];
+                std::vector<std::pair<Solver<T>*, int>> jobs;   // (problem, node)
+                for (auto* p : ids) {
                     const int l = p->L - hgt;
                     if (l < 1 || (l == 1) != (to64 == 1)) continue;
-                    for (int id : p->lev[l]) jobs.push_back({q, id});
+                    for (int id : p->lev[l]) jobs.push_back({p, id});
                 }
-                // one launch per basis width and per CB_MAX_JOBS nodes
-                std::vector<int> widths;
-                for (auto& jn : jobs) {
-                    const int w = 2 * ps[jn.first]->r;
-                    if (std::find(widths.begin(), widths.end(), w) == widths.end()) widths.push_back(w);
-                }
+                std::vector<int> widths;   // one launch per basis width and per CB_MAX_JOBS nodes
+                for (auto& jn : jobs)
+                    if (std::find(widths.begin(), widths.end(), 2 * jn.first->r) == widths.end())
+                        widths.push_back(2 * jn.first->r);
                 for (int w : widths) {
                     CoarseBatch bt{};
                     auto flush = [&]() {
@@ -1400,10 +1466,10 @@ static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, 
                         bt = CoarseBatch{};
                     };
                     for (auto& jn : jobs) {
-                        Solver<T>* p = ps[jn.first];
+                        Solver<T>* p = jn.first;
                         if (2 * p->r != w) continue;
-                        const Node& nd = p->nodes[jn.second];
                         const int id = jn.second;
+                        const Node& nd = p->nodes[id];
                         CoarseJob& j = bt.job[bt.njobs++];
                         j.C = p->C[id];
                         j.v = p->RT + p->row_off(0, nd.ra, 1);
@@ -1425,12 +1491,11 @@ static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, 
         }
         // the roots: u += C A_c^{-1} C^H (b - A u)
         std::vector<int> widths;
-        for (int q : active)
-            if (std::find(widths.begin(), widths.end(), 2 * ps[q]->r) == widths.end()) widths.push_back(2 * ps[q]->r);
+        for (auto* p : ids)
+            if (std::find(widths.begin(), widths.end(), 2 * p->r) == widths.end()) widths.push_back(2 * p->r);
         for (int w : widths) {
             CoarseBatch bt{};
-            for (int q : active) {
-                Solver<T>* p = ps[q];
+            for (auto* p : ids) {
                 if (2 * p->r != w) continue;
                 bt.job[bt.njobs++] = p->one_job(0, p->bvec, p->u, p->u, true).job[0];
                 if (bt.njobs == CB_MAX_JOBS) {
@@ -1440,34 +1505,61 @@ static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, 
             }
             if (bt.njobs) launch_coarse_batch<T, double, double, double>(bt, w, cpart, bar, berr, stream);
         }
-        for (int q : active) ++it[q];
+        for (auto& q : act) ++q.it;
         ck(cudaGetLastError(), cerr);
-        if (cerr != cudaSuccess) st = HH_ECUDA;
+        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
-    for (int k = 0; k < np; ++k)
-        ck(cudaMemcpyAsync(uo[k], ps[k]->u, sizeof(c128) * (size_t)ps[k]->Sy * ps[k]->Sx, cudaMemcpyDeviceToDevice,
-                           stream),
-           cerr);
+};
+
+template <typename T>
+static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, const c128* const* g,
+                             c128* const* uo, cudaStream_t stream, hh_stats* stats, std::vector<hh_status>& res) {
+    const int np = (int)ps.size();
+    int nleaf = 0;
+    for (auto* p : ps) nleaf += (int)p->h_pre.size();
+    BatchEngine<T> eng;
+    eng.cap_probs = np;
+    eng.cap_tasks = nleaf;
+    for (auto* p : ps) {
+        if (!eng.can_add(p)) return HH_ENOTIMPL;
+        eng.act.push_back({});   // capacity and cluster checks against the members so far
+        eng.act.back().p = p;
+    }
+    eng.act.clear();
+    hh_status st = eng.init(stream, np, nleaf, g_alloc);
+    if (st != HH_OK) {
+        eng.release();
+        return st;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, stream);
+    for (int k = 0; k < np; ++k) eng.add(ps[k], f[k], g[k], uo[k], (void*)(size_t)k);
+    std::vector<typename BatchEngine<T>::Prob> done;
+    while (st == HH_OK && !eng.act.empty()) st = eng.step(done);
     cudaEventRecord(e1, stream);
-    ck(cudaStreamSynchronize(stream), cerr);
+    cudaStreamSynchronize(stream);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFreeHost(h_norms);
-    dev_free(base, bytes, stream, hook);
-    if (stats)
-        for (int k = 0; k < np; ++k) {
-            stats[k].iters = it[k];
-            stats[k].rel_res = rel[k];
+    eng.release();
+    res.assign(np, HH_ECUDA);
+    for (auto& q : done) {
+        const int k = (int)(size_t)q.tag;
+        res[k] = q.st;
+        if (stats) {
+            stats[k].iters = q.it;
+            stats[k].rel_res = q.rel;
             stats[k].t_setup_ms = ps[k]->t_setup_ms;
             stats[k].t_solve_ms = ms;
             stats[k].footprint_bytes = ps[k]->footprint;
         }
-    if (st == HH_OK && cerr != cudaSuccess) st = HH_ECUDA;
+    }
     if (st != HH_OK) return st;
-    for (int k = 0; k < np; ++k)
-        if (res[k] != HH_OK) return res[k];
+    for (auto s1 : res)
+        if (s1 != HH_OK) return s1;
     return HH_OK;
 }
 
@@ -1475,7 +1567,7 @@ static hh_status batch_solve(std::vector<Solver<T>*>& ps, const c128* const* f, 
 // the stationary iteration does not converge are then solved by flexible GMRES (the
 // paper's outer solver) on handles set up for it, several at a time from host threads.
 // Handles that cannot join the lockstep batch are solved one by one.
-static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out);
+static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out, const AllocHook& hook);
 
 static hh_status solve_many(SolverBase* const* hs, const c128* const* f, const c128* const* g, c128* const* u, int n,
                             cudaStream_t stream, hh_stats* stats) {
@@ -1520,7 +1612,7 @@ static hh_status solve_many(SolverBase* const* hs, const c128* const* f, const c
             q.outer = HH_OUTER_GMRES;
             if (q.restart < 1 || q.restart > 64) q.restart = 40;
             SolverBase* g2 = nullptr;
-            rs[i] = setup_one(&q, ws, &g2);
+            rs[i] = setup_one(&q, ws, &g2, g_alloc);
             if (rs[i] != HH_OK) continue;
             hh_stats s2{};
             rs[i] = g2->solve(f[k], g[k], u[k], &s2);
@@ -1544,6 +1636,239 @@ static hh_status solve_many(SolverBase* const* hs, const c128* const* f, const c
         if (s1 != HH_OK) return s1;
     return HH_OK;
 }
+
+// ------------------------------------------------------------------ serving form
+// Continuous batching: requests are admitted while the sum of their footprints stays
+// within the HBM budget and a slot is free; set-up workers set them up concurrently; an
+// engine thread iterates every set-up problem in lockstep (BatchEngine), taking in new
+// problems between iterations and retiring converged ones at once.  Problems the
+// lockstep iteration cannot take (other outer solvers, n_i > 1, one level, 1D, the
+// explicit-inverse leaf path) are solved by the worker that set them up; problems whose
+// stationary iteration does not converge go back to a worker for flexible GMRES.
+struct ServerReq {
+    unsigned long long ticket = 0;
+    hh_params P{};
+    const c128* f = nullptr;
+    const c128* g = nullptr;
+    c128* u = nullptr;
+    size_t fp = 0;
+    hh_status st = HH_OK;
+    hh_stats stats{};
+    bool done = false, rescued = false;
+    std::chrono::steady_clock::time_point t_submit, t_admit, t_join;
+    SolverBase* s = nullptr;
+};
+
+static double ms_since(std::chrono::steady_clock::time_point a) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+}
+
+struct Server {
+    size_t budget = 0, used = 0;
+    int max_slots = 0, slots = 0, dev = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_engine;
+    std::deque<ServerReq*> pending, ready, rescue;
+    std::map<unsigned long long, ServerReq*> all;
+    unsigned long long next = 1;
+    bool stop = false;
+    std::vector<std::thread> threads;
+
+    // called with the lock held
+    void finish(ServerReq* r) {
+        r->done = true;
+        used -= r->fp;
+        --slots;
+        cv_work.notify_all();
+    }
+    void complete(ServerReq* r, hh_status st, cudaStream_t s) {
+        if (r->s) {
+            r->s->stream = s;
+            delete r->s;
+            r->s = nullptr;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        r->st = st;
+        r->stats.t_total_ms = ms_since(r->t_submit);
+        r->stats.t_queue_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+        finish(r);
+    }
+
+    void worker() {
+        cudaSetDevice(dev);
+        cudaStream_t ws = nullptr;
+        cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+        const AllocHook rt{};   // server problems allocate from the runtime's pool on this stream
+        for (;;) {
+            ServerReq* r = nullptr;
+            bool is_rescue = false;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                for (;;) {
+                    if (stop) break;
+                    if (!rescue.empty()) {
+                        r = rescue.front();
+                        rescue.pop_front();
+                        is_rescue = true;
+                        break;
+                    }
+                    if (!pending.empty() && slots < max_slots && used + pending.front()->fp <= budget) {
+                        r = pending.front();
+                        pending.pop_front();
+                        used += r->fp;
+                        ++slots;
+                        r->t_admit = std::chrono::steady_clock::now();
+                        break;
+                    }
+                    cv_work.wait(lk);
+                }
+            }
+            if (!r) break;
+            if (is_rescue) {
+                hh_params q = r->P;
+                q.outer = HH_OUTER_GMRES;
+                if (q.restart < 1 || q.restart > 64) q.restart = 40;
+                SolverBase* g2 = nullptr;
+                hh_status st = setup_one(&q, ws, &g2, rt);
+                hh_stats s2{};
+                if (st == HH_OK) {
+                    st = g2->solve(r->f, r->g, r->u, &s2);
+                    cudaStreamSynchronize(ws);
+                    delete g2;
+                }
+                r->stats.iters += s2.iters;
+                r->stats.rel_res = s2.rel_res;
+                complete(r, st, ws);
+                continue;
+            }
+            SolverBase* sb = nullptr;
+            hh_status st = setup_one(&r->P, ws, &sb, rt);
+            r->s = sb;
+            if (st != HH_OK) {
+                complete(r, st, ws);
+                continue;
+            }
+            r->stats.t_setup_ms = sb->t_setup_ms;
+            r->stats.footprint_bytes = sb->footprint;
+            bool lock = false;
+            if (auto* a = dynamic_cast<Solver<float>*>(sb)) lock = batchable(a);
+            else if (auto* b = dynamic_cast<Solver<double>*>(sb)) lock = batchable(b);
+            if (lock) {
+                cudaStreamSynchronize(ws);
+                std::lock_guard<std::mutex> lk(mu);
+                ready.push_back(r);
+                cv_engine.notify_one();
+                continue;
+            }
+            const auto t0 = std::chrono::steady_clock::now();
+            st = sb->solve(r->f, r->g, r->u, &r->stats);
+            cudaStreamSynchronize(ws);
+            r->stats.t_solve_ms = ms_since(t0);
+            complete(r, st, ws);
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    }
+
+    template <typename T>
+    void retire(BatchEngine<T>& eng, std::vector<typename BatchEngine<T>::Prob>& done) {
+        for (auto& q : done) {
+            ServerReq* r = (ServerReq*)q.tag;
+            r->stats.iters = q.it;
+            r->stats.rel_res = q.rel;
+            r->stats.t_solve_ms = ms_since(r->t_join);
+            if (q.st == HH_ENOCONV && !r->rescued) {
+                // hand to a worker for GMRES; the handle of the stationary run goes now
+                r->s->stream = eng.stream;
+                delete r->s;
+                r->s = nullptr;
+                r->rescued = true;
+                std::lock_guard<std::mutex> lk(mu);
+                rescue.push_back(r);
+                cv_work.notify_all();
+            } else {
+                complete(r, q.st, eng.stream);
+            }
+        }
+        done.clear();
+    }
+
+    void engine() {
+        cudaSetDevice(dev);
+        cudaStream_t es = nullptr;
+        cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking);
+        BatchEngine<float> e32;
+        BatchEngine<double> e64;
+        const AllocHook rt{};
+        const bool ok = e32.init(es, max_slots, max_slots * 64, rt) == HH_OK &&
+                        e64.init(es, max_slots, max_slots * 64, rt) == HH_OK;
+        std::vector<BatchEngine<float>::Prob> d32;
+        std::vector<BatchEngine<double>::Prob> d64;
+        for (;;) {
+            std::vector<ServerReq*> take;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (e32.act.empty() && e64.act.empty())
+                    cv_engine.wait(lk, [&] { return stop || !ready.empty(); });
+                if (stop) break;
+                while (!ready.empty()) {
+                    take.push_back(ready.front());
+                    ready.pop_front();
+                }
+            }
+            std::vector<ServerReq*> later;
+            for (ServerReq* r : take) {
+                bool added = false;
+                if (ok) {
+                    r->t_join = std::chrono::steady_clock::now();
+                    if (auto* a = dynamic_cast<Solver<float>*>(r->s)) {
+                        if (e32.can_add(a)) { e32.add(a, r->f, r->g, r->u, r); added = true; }
+                    } else if (auto* b = dynamic_cast<Solver<double>*>(r->s)) {
+                        if (e64.can_add(b)) { e64.add(b, r->f, r->g, r->u, r); added = true; }
+                    }
+                }
+                if (!added) {
+                    if (!ok || (e32.act.empty() && e64.act.empty())) {
+                        // cannot join even an empty engine: solve it here on its own
+                        r->s->stream = es;
+                        const auto t0 = std::chrono::steady_clock::now();
+                        const hh_status st = r->s->solve(r->f, r->g, r->u, &r->stats);
+                        cudaStreamSynchronize(es);
+                        r->stats.t_solve_ms = ms_since(t0);
+                        complete(r, st, es);
+                    } else {
+                        later.push_back(r);
+                    }
+                }
+            }
+            if (!later.empty()) {
+                std::lock_guard<std::mutex> lk(mu);
+                for (auto it2 = later.rbegin(); it2 != later.rend(); ++it2) ready.push_front(*it2);
+            }
+            hh_status st32 = e32.step(d32);
+            retire(e32, d32);
+            hh_status st64 = e64.step(d64);
+            retire(e64, d64);
+            if (st32 != HH_OK) {
+                for (auto& q : e32.act) complete((ServerReq*)q.tag, st32, es);
+                e32.act.clear();
+                e32.uploaded.clear();
+            }
+            if (st64 != HH_OK) {
+                for (auto& q : e64.act) complete((ServerReq*)q.tag, st64, es);
+                e64.act.clear();
+                e64.uploaded.clear();
+            }
+        }
+        // shutting down: requests still iterating are dropped (their handles freed)
+        for (auto& q : e32.act) complete((ServerReq*)q.tag, HH_ECUDA, es);
+        for (auto& q : e64.act) complete((ServerReq*)q.tag, HH_ECUDA, es);
+        cudaStreamSynchronize(es);
+        e32.release();
+        e64.release();
+        cudaStreamDestroy(es);
+    }
+};
 
 }  // namespace hh
 
@@ -1647,6 +1972,87 @@ hh_status hh_solve_batch(hh_handle* const* h, const void* const* d_f, const void
                           (cudaStream_t)stream, stats);
 }
 
+struct hh_server {
+    hh::Server* sv;
+};
+
+hh_status hh_server_create(size_t hbm_budget, int max_slots, hh_server** out) {
+    if (!out || max_slots < 1 || max_slots > 4096 || hbm_budget == 0) return HH_EINVAL;
+    *out = nullptr;
+    auto* sv = new hh::Server();
+    sv->budget = hbm_budget;
+    sv->max_slots = max_slots;
+    if (cudaGetDevice(&sv->dev) != cudaSuccess) {
+        delete sv;
+        return HH_ECUDA;
+    }
+    sv->threads.emplace_back([sv] { sv->engine(); });
+    for (int w = 0; w < 4; ++w) sv->threads.emplace_back([sv] { sv->worker(); });
+    *out = new hh_server{sv};
+    return HH_OK;
+}
+
+hh_status hh_server_submit(hh_server* srv, const hh_params* params, const void* d_f, const void* d_g, void* d_u,
+                           unsigned long long* ticket) {
+    if (!srv || !params || !d_f || !d_g || !d_u || !ticket) return HH_EINVAL;
+    const hh_status v = hh::validate(params);
+    if (v != HH_OK) return v;
+    size_t fp = 0;
+    {
+        std::unique_ptr<hh::SolverBase> s(hh::make_solver(params));
+        fp = s->plan(nullptr);
+    }
+    hh::Server* sv = srv->sv;
+    if (fp > sv->budget) return HH_ENOMEM;
+    auto* r = new hh::ServerReq();
+    r->P = *params;
+    r->f = (const c128*)d_f;
+    r->g = (const c128*)d_g;
+    r->u = (c128*)d_u;
+    r->fp = fp;
+    r->t_submit = r->t_admit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->ticket = sv->next++;
+    sv->all[r->ticket] = r;
+    sv->pending.push_back(r);
+    sv->cv_work.notify_all();
+    *ticket = r->ticket;
+    return HH_OK;
+}
+
+hh_status hh_server_poll(hh_server* srv, unsigned long long ticket, hh_status* result, hh_stats* stats) {
+    if (!srv || !result) return HH_EINVAL;
+    hh::Server* sv = srv->sv;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return HH_EINVAL;
+    hh::ServerReq* r = it->second;
+    if (!r->done) return HH_EPENDING;
+    *result = r->st;
+    if (stats) *stats = r->stats;
+    sv->all.erase(it);
+    delete r;
+    return HH_OK;
+}
+
+void hh_server_destroy(hh_server* srv) {
+    if (!srv) return;
+    hh::Server* sv = srv->sv;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->cv_work.notify_all();
+        sv->cv_engine.notify_all();
+    }
+    for (auto& t : sv->threads) t.join();
+    for (auto& kv : sv->all) {
+        if (kv.second->s) delete kv.second->s;
+        delete kv.second;
+    }
+    delete sv;
+    delete srv;
+}
+
 hh_status hh_solve(hh_handle* h, const void* d_f, const void* d_g, void* d_u, void* stream, hh_stats* stats) {
     if (!h || !d_f || !d_g || !d_u) return HH_EINVAL;
     h->s->stream = (cudaStream_t)stream;
@@ -1694,6 +2100,7 @@ const char* hh_status_string(hh_status s) {
         case HH_ECUDA: return "CUDA runtime error";
         case HH_ENOTIMPL: return "not implemented";
         case HH_ETOOLARGE: return "problem larger than the fixed static scratch (n + 2 > HH_NOALLOC_MAX_ROWS)";
+        case HH_EPENDING: return "request not finished yet";
     }
     return "unknown status";
 }
