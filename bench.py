@@ -255,6 +255,8 @@ def run_ours(args, rank, world):
     e2e = {"value": world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": 16 * (N + 4 * w.S), "d2h_bytes_per_step": 16 * N}
 
+    batch = run_batch_form(hh, torch) if rank == 0 else None
+
     pk, pk_kind = peaks()
     roof = roofline(w, prof_total, prof_iters, pk, pk_kind)
     clocks = clk.summary()
@@ -277,9 +279,110 @@ def run_ours(args, rank, world):
                     for k, v in prof_total.items() if v[1] > 0},
         "wall_s_timed": wall,
     }
+    if batch is not None:
+        out["batch_form"] = batch
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(w, f, g)
     return out
+
+
+BATCH_PROBLEMS = 512
+
+
+def run_batch_form(hh, torch, count=BATCH_PROBLEMS):
+    """The batching form: `count` independent problems (grid sides 63..255, k h in
+    [0.3, 0.6], 2 levels, r = 16, p = 8) set up together (hh_setup_batch) and solved
+    together (hh_solve_batch), one warm-up and one timed pass; solves/s over set-up and
+    solve."""
+    from workloads import batch_problems
+    probs = batch_problems(count)
+    params = [hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, 1, TOL, MAX_ITER, "mixed",
+                             1 + i) for i, (w, f, g) in enumerate(probs)]
+    fs = [torch.from_numpy(f).cuda() for (w, f, g) in probs]
+    gs = [torch.from_numpy(g).cuda() for (w, f, g) in probs]
+    us = [torch.empty((w.S, w.S), dtype=torch.complex128, device="cuda") for (w, f, g) in probs]
+    res = None
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = hh.hh_setup_batch(params)
+        t1 = time.perf_counter()
+        sts = hh.hh_solve_batch(hs, fs, gs, us)
+        t2 = time.perf_counter()
+        for h in hs:
+            hh.hh_destroy(h)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        its = [st.iters for st in sts]
+        res = {"problems": count, "value": count / (t3 - t0), "unit": UNIT, "setup_ms": 1e3 * (t1 - t0),
+               "solve_ms": 1e3 * (t2 - t1), "iterations": {"median": statistics.median(its), "max": max(its)},
+               "max_rel_res": max(st.rel_res for st in sts),
+               "workload": "batch: grid sides U{63,127,191,255}, k h U[0.3,0.6], L=2, overlap 2, r=16, p=8, "
+                           "mixed form, tol 1e-10"}
+    return res
+
+
+def run_serving(args):
+    """The serving form: a Poisson stream of requests (mean args.rate per second for
+    args.serve_seconds seconds), grid sides U{127,255,511,1023}, k ~ U[20, min(150, 0.6/h)],
+    2 levels (r=16, p=10, overlap 2) up to 255 and 3 levels (r=32, p=10, overlap 4) above,
+    submitted to one hh_server; reports served solves/s and p50/p99 latency (submission
+    to completion)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_12538_gb300 as hh
+    from workloads import point_source_rhs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.Generator(np.random.PCG64(2512_12538 + 5))
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / args.rate)
+        if t > args.serve_seconds:
+            break
+        n = int(rng.choice([127, 255, 511, 1023]))
+        k = float(rng.uniform(20.0, min(150.0, 0.6 * (n + 1))))
+        lv, ov, r = (2, 2, 16) if n <= 255 else (3, 4, 32)
+        p = hh.make_params(2, n, k, lv, ov, r, 10, 1, TOL, MAX_ITER, "mixed", len(reqs) + 1)
+        f = torch.from_numpy(point_source_rhs(n, 2512_12538 + 31 * len(reqs))).cuda()
+        g = torch.zeros((4, n + 2), dtype=torch.complex128, device="cuda")
+        u = torch.empty_like(f)
+        reqs.append((t, n, p, f, g, u))
+    torch.cuda.synchronize()
+    srv = hh.hh_server_create(160 << 30, 64)
+    lat, done, fails, codes = [], {}, 0, {}
+    t0 = time.perf_counter()
+    tickets = []
+    i = 0
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            _, n, p, f, g, u = reqs[i]
+            tickets.append(hh.hh_server_submit(srv, p, f, g, u))
+            i += 1
+        for j, tk in enumerate(tickets):
+            if j in done:
+                continue
+            res = hh.hh_server_poll(srv, tk)
+            if res is not None:
+                st, stats = res
+                done[j] = time.perf_counter() - t0
+                lat.append(stats.t_total_ms)
+                fails += st != hh.HH_OK
+                codes[hh.status_string(st)] = codes.get(hh.status_string(st), 0) + 1
+        time.sleep(0.0002)
+    wall = max(done.values())
+    hh.hh_server_destroy(srv)
+    return {"metric": "served Helmholtz solves/sec (Poisson stream) at rel err 1e-8; p50/p99 latency",
+            "value": len(reqs) / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "requests": len(reqs), "failed": fails, "statuses": codes, "offered_rate": args.rate,
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)}, "wall_s": wall,
+            "config": {"workload": "serving: sides U{127,255,511,1023}, k U[20, min(150, 0.6/h)], L=2 (r=16,p=10) "
+                                   "up to 255, L=3 (r=32,p=10) above; budget 160 GB, 64 slots", "precision": "mixed"},
+            "data": "synthetic"}
 
 
 def pct(xs, q):
@@ -379,7 +482,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="single", choices=["single", "serve"],
+                    help="serve: the serving-form stream instead of the headline workload")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: length of the arrival stream")
     args = ap.parse_args()
+    if args.form == "serve":
+        print(json.dumps(run_serving(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -1275,6 +1275,7 @@ struct BatchEngine {
         Solver<T>* p = nullptr;
         c128* uo = nullptr;          // where the solution goes when the problem leaves
         void* tag = nullptr;
+        unsigned long long serial = 0;   // unique per add(): the key of the task upload
         int it = 0, chk_it = 0;
         double rel = 0.0, best = 0.0, chk = 0.0;
         hh_status st = HH_OK;
@@ -1293,7 +1294,10 @@ struct BatchEngine {
     double* h_norms = nullptr;       // pinned
     int part_cap = RB_MAX_JOBS * 304;
     std::vector<Prob> act;
-    std::vector<Solver<T>*> uploaded;
+    // serials of the problems whose leaf tasks are in d_tasks (a freed solver's address
+    // can come back for a new problem, so addresses are no key)
+    std::vector<unsigned long long> uploaded;
+    unsigned long long next_serial = 1;
     int cl = 0, bmax = 0, sxmax = 0;
     cudaError_t cerr = cudaSuccess;
 
@@ -1355,6 +1359,7 @@ struct BatchEngine {
         q.p = p;
         q.uo = uo;
         q.tag = tag;
+        q.serial = next_serial++;
         q.it = -1;   // the first step reads ||b||^2
         act.push_back(q);
     }
@@ -1419,8 +1424,12 @@ struct BatchEngine {
         if (act.empty()) return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
         // one preconditioner step for every current problem
         std::vector<Solver<T>*> ids;
-        for (auto& q : act) ids.push_back(q.p);
-        if (ids != uploaded) {
+        std::vector<unsigned long long> key;
+        for (auto& q : act) {
+            ids.push_back(q.p);
+            key.push_back(q.serial);
+        }
+        if (key != uploaded) {
             std::vector<EigTask> tk;
             bmax = sxmax = 0;
             int smin = 1 << 30;
@@ -1436,7 +1445,7 @@ struct BatchEngine {
                cerr);
             // the pageable source must stay alive until the copy has read it
             ck(cudaStreamSynchronize(stream), cerr);
-            uploaded = ids;
+            uploaded = key;
         }
         int nt = 0, lmax = 0;
         for (auto* p : ids) {
@@ -1725,20 +1734,7 @@ struct Server {
             }
             if (!r) break;
             if (is_rescue) {
-                hh_params q = r->P;
-                q.outer = HH_OUTER_GMRES;
-                if (q.restart < 1 || q.restart > 64) q.restart = 40;
-                SolverBase* g2 = nullptr;
-                hh_status st = setup_one(&q, ws, &g2, rt);
-                hh_stats s2{};
-                if (st == HH_OK) {
-                    st = g2->solve(r->f, r->g, r->u, &s2);
-                    cudaStreamSynchronize(ws);
-                    delete g2;
-                }
-                r->stats.iters += s2.iters;
-                r->stats.rel_res = s2.rel_res;
-                complete(r, st, ws);
+                gmres_rescue(r, ws, rt);
                 continue;
             }
             SolverBase* sb = nullptr;
@@ -1764,10 +1760,50 @@ struct Server {
             st = sb->solve(r->f, r->g, r->u, &r->stats);
             cudaStreamSynchronize(ws);
             r->stats.t_solve_ms = ms_since(t0);
+            if (st == HH_ENOCONV && r->P.outer == HH_OUTER_ORAS) {
+                sb->stream = ws;
+                delete sb;
+                r->s = nullptr;
+                gmres_rescue(r, ws, rt);
+                continue;
+            }
             complete(r, st, ws);
         }
         cudaStreamSynchronize(ws);
         cudaStreamDestroy(ws);
+    }
+
+    // Re-solves a request by flexible GMRES on a handle set up for it.  Its footprint
+    // replaces the request's in the budget (waiting until it fits, unless nothing else is
+    // in flight).
+    void gmres_rescue(ServerReq* r, cudaStream_t ws, const AllocHook& rt) {
+        r->rescued = true;
+        hh_params q = r->P;
+        q.outer = HH_OUTER_GMRES;
+        if (q.restart < 1 || q.restart > 64) q.restart = 40;
+        size_t fpg = 0;
+        {
+            std::unique_ptr<SolverBase> tmp(make_solver(&q));
+            fpg = tmp->plan(nullptr);
+        }
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] { return stop || used - r->fp + fpg <= budget || slots == 1; });
+            used = used - r->fp + fpg;
+            r->fp = fpg;
+        }
+        SolverBase* g2 = nullptr;
+        hh_status st = setup_one(&q, ws, &g2, rt);
+        hh_stats s2{};
+        if (st == HH_OK) {
+            st = g2->solve(r->f, r->g, r->u, &s2);
+            cudaStreamSynchronize(ws);
+            g2->stream = ws;
+            delete g2;
+        }
+        r->stats.iters += s2.iters;
+        r->stats.rel_res = s2.rel_res;
+        complete(r, st, ws);
     }
 
     template <typename T>
@@ -1782,7 +1818,6 @@ struct Server {
                 r->s->stream = eng.stream;
                 delete r->s;
                 r->s = nullptr;
-                r->rescued = true;
                 std::lock_guard<std::mutex> lk(mu);
                 rescue.push_back(r);
                 cv_work.notify_all();

@@ -114,3 +114,26 @@ def test_admission_keeps_footprints_within_budget(hh):
     assert all(st == hh.HH_OK for st, _ in res)
     # admitted one after another: the last waited for the first two
     assert res[2][1].t_queue_ms > 0.0
+
+
+@pytest.mark.gpu
+def test_requests_cycling_through_few_slots(hh):
+    # more requests than slots: problems join the lockstep iteration while others leave
+    probs = batch_problems(20, sides=(63, 127), kh=(0.3, 0.35))
+    params = [_params(hh, w, i) for i, (w, f, g) in enumerate(probs)]
+    fs = [torch.from_numpy(f).cuda() for (w, f, g) in probs]
+    gs = [torch.from_numpy(g).cuda() for (w, f, g) in probs]
+    us = [torch.zeros((w.S, w.S), dtype=torch.complex128, device="cuda") for (w, f, g) in probs]
+    torch.cuda.synchronize()
+    srv = hh.hh_server_create(8 << 30, 3)
+    try:
+        tickets = [hh.hh_server_submit(srv, params[i], fs[i], gs[i], us[i]) for i in range(len(probs))]
+        res = _wait(hh, srv, tickets)
+    finally:
+        hh.hh_server_destroy(srv)
+    for i, (w, f, g) in enumerate(probs):
+        st, stats = res[i]
+        assert st == hh.HH_OK, (w.name, st)
+        ud = direct.solve(Problem(2, w.n, w.k), f, g).reshape(w.S, w.S)
+        got = us[i].cpu().numpy()
+        assert np.linalg.norm(got - ud) / np.linalg.norm(ud) < 1e-8
