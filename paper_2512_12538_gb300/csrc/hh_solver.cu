@@ -674,6 +674,7 @@ struct Solver final : SolverBase {
                 j.r1 = nd.own_b - nd.ra;
                 j.acc_out = l == 1 && root_acc;
                 j.add_w = 1;
+                j.split = split_row(p);
                 by += (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT);
                 fl += 2.0 * 8.0 * 2 * r * pts(p);
             }
@@ -683,6 +684,9 @@ struct Solver final : SolverBase {
             pend();
         }
     }
+
+    // local row of node p where its second child's owned rows (and basis columns) begin
+    int split_row(int p) const { return nodes[nodes[p].child[1]].own_a - nodes[p].ra; }
 
     // out (+)= C_p A_c^{-1} C_p^H (v - A~_p w) over node p's band, one column
     CoarseBatch one_job(int p, const void* v, const void* w, void* out, bool acc) const {
@@ -699,6 +703,7 @@ struct Solver final : SolverBase {
         j.r1 = nodes[p].b();
         j.acc_out = acc;
         j.add_w = 0;
+        j.split = split_row(p);
         bt.njobs = 1;
         return bt;
     }
@@ -1492,6 +1497,7 @@ struct BatchEngine {
                         j.r1 = nd.own_b - nd.ra;
                         j.acc_out = to64;
                         j.add_w = 1;
+                        j.split = p->split_row(id);
                         if (bt.njobs == CB_MAX_JOBS) flush();
                     }
                     flush();

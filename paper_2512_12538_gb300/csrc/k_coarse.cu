@@ -287,9 +287,15 @@ __global__ void __launch_bounds__(256) k_coarse_batch(CoarseBatch bt, int p, cpl
         for (int sub = 0; sub < 4; ++sub) {
             const unsigned pt = base + sub * 64 + q;
             if (pt < N) {
+                // a column whose child does not own this row is zero there: not read
+                const int half = J.split < 0 ? -1 : ((int)(pt / (unsigned)g.Sx) < J.split ? 0 : 1);
                 cplx<TC> cv[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) cv[u] = (ja + u < jb) ? C[(size_t)(ja + u) * N + pt] : cplx<TC>{0, 0};
+                for (int u = 0; u < 16; ++u) {
+                    const int j = ja + u;
+                    const bool need = j < jb && (half < 0 || (j < (p >> 1)) == (half == 0));
+                    cv[u] = need ? C[(size_t)j * N + pt] : cplx<TC>{0, 0};
+                }
                 const CA ra = s_r[sub * 64 + q];
 #pragma unroll
                 for (int u = 0; u < 16; ++u) cfma_cj(acc[u], cv[u], ra);
@@ -361,15 +367,20 @@ __global__ void __launch_bounds__(256) k_coarse_batch(CoarseBatch bt, int p, cpl
         const unsigned pt = base + threadIdx.x;
         if (pt < lo || pt >= hi) continue;
         CA a = {0, 0};
-        int j = 0;
-        for (; j + 8 <= p; j += 8) {
+        // only the columns of the child that owns this row are nonzero
+        int j = 0, je = p;
+        if (J.split >= 0) {
+            if ((int)(pt / (unsigned)g.Sx) < J.split) je = p >> 1;
+            else j = p >> 1;
+        }
+        for (; j + 8 <= je; j += 8) {
             cplx<TC> cv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) cv[u] = C[(size_t)(j + u) * N + pt];
 #pragma unroll
             for (int u = 0; u < 8; ++u) cfma(a, cv[u], s_y[j + u]);
         }
-        for (; j < p; ++j) cfma(a, C[(size_t)j * N + pt], s_y[j]);
+        for (; j < je; ++j) cfma(a, C[(size_t)j * N + pt], s_y[j]);
         cplx<TO> val = cvt<TO>(a);
         if (J.add_w) val = val + cvt<TO>(w_in[pt]);
         cplx<TO>& o = out[pt - lo];

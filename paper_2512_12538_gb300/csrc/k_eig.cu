@@ -536,14 +536,14 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
     // register-tiled contraction where V and the column block fit in shared memory
     constexpr int GN2 = 16 * Gemm2Cols<T>::CV;
     const size_t sm2 = sizeof(cplx<T>) * ((size_t)b_max * b_max + (size_t)b_max * GN2);
-    const bool tiled = stage != 1 && b_max <= 144 && sm2 <= (size_t)(200 * 1024);
+    const bool tiled = stage != 1 && b_max <= 144 && sm2 <= (size_t)(220 * 1024);
     if (tiled) {
         static bool attr2 = false;
         if (!attr2) {
-            cudaFuncSetAttribute(k_eig_gemm2<T, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            cudaFuncSetAttribute(k_eig_gemm2<T, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            cudaFuncSetAttribute(k_eig_gemm2<T, true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            cudaFuncSetAttribute(k_eig_gemm2<T, false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(k_eig_gemm2<T, false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
             attr2 = true;
         }
         dim3 g2((J + GN2 - 1) / GN2, ntasks);

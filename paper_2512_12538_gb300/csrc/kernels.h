@@ -97,6 +97,8 @@ struct CoarseJob {
     OpGeom g;
     int r0, r1;
     int acc_out, add_w;
+    int split;             // >= 0: columns [0, p/2) vanish on rows >= split, [p/2, p) on rows
+                           // below (each child's basis lives on its owned rows); -1: dense
     unsigned blk0, nblk;   // set by the launcher
 };
 struct CoarseBatch {
