@@ -197,6 +197,8 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
+            // spin without sleeping first (the release is usually a few microseconds
+            // away), then back off; give up after about a second
             long long it = 0;
             while (*gen == g0) {
                 if (++it > (1ll << 24)) {
@@ -204,7 +206,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if (it > 4096) __nanosleep(64);
             }
         }
         __threadfence();
@@ -321,17 +323,20 @@ __global__ void __launch_bounds__(256) k_coarse_batch(CoarseBatch bt, int p, cpl
     const CA* jp = partial + (size_t)J.blk0 * p;
     for (int j0 = 0; j0 < p; j0 += blockDim.x >> 3) {
         const int j = j0 + (threadIdx.x >> 3);
+        // all of a thread's partials requested at once (one round trip for up to
+        // 8 PU blocks), then added in index order
+        constexpr int PU = sizeof(TC) == 4 ? 24 : 12;
         CA t0 = {0, 0}, t1 = {0, 0};
         if (j < p) {
-            for (unsigned b0 = sub; b0 < nblk; b0 += 64) {
-                CA a[8];
+            for (unsigned b0 = sub; b0 < nblk; b0 += 8 * PU) {
+                CA a[PU];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < PU; ++u) {
                     const unsigned bb = b0 + 8u * u;
                     a[u] = bb < nblk ? jp[(size_t)bb * p + j] : CA{0, 0};
                 }
 #pragma unroll
-                for (int u = 0; u < 8; u += 2) {
+                for (int u = 0; u < PU; u += 2) {
                     t0 = t0 + a[u];
                     t1 = t1 + a[u + 1];
                 }
