@@ -802,10 +802,13 @@ struct Solver final : SolverBase {
         bt.n = 2 * r;
         bt.err = derr;
         int cnt = 0;
-        for (int p : lev[l - 1]) bt.A[cnt++] = Ainv[p];
-        launch_gj_inverse(bt, cnt, stream);
-        if (sizeof(CT) != sizeof(c128))
-            for (int p : lev[l - 1]) launch_copy<double, T>(Ainv[p], AinvT[p], (size_t)4 * r * r, false, false, stream);
+        // the complex64 form eliminates in FP32 and writes its complex64 copy directly
+        const bool fp32 = sizeof(CT) != sizeof(c128);
+        for (int p : lev[l - 1]) {
+            bt.A[cnt] = Ainv[p];
+            bt.AT[cnt++] = fp32 ? (void*)AinvT[p] : nullptr;
+        }
+        launch_gj_inverse(bt, cnt, fp32, stream);
     }
 
     hh_status setup() override {

@@ -758,41 +758,46 @@ void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* 
 // ------------------------------------------------------- Gauss-Jordan (FP64)
 // In-place inverse with partial pivoting: row interchanges during elimination, the
 // inverse's columns unscrambled in reverse order at the end.
-// One block per matrix.  The pivot's reciprocal is formed once per step (thread 0) and
-// shared: FP64 division is a long instruction sequence on the narrow FP64 pipe.
+// One block per matrix, in arithmetic R: FP64 for the FP64 form; FP32 for the complex64
+// form, whose one-column corrections apply the inverse in FP32 anyway (the outer FP64
+// refinement absorbs the difference; FP64 runs at 1/64 of the FP32 rate here).  The
+// pivot's reciprocal is formed once per step (thread 0) and shared.  The inverse is
+// written back to A in complex128 and, where AT is given, in complex64.
+template <typename R>
 __global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
-    extern __shared__ c128 sg[];
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char gjs[];
     c128* A = bt.A[blockIdx.x];
     const int n = bt.n;
-    c128* M = sg;
-    c128* col = M + n * n;
-    c128* row = col + n;
+    C* M = (C*)gjs;
+    C* col = M + n * n;
+    C* row = col + n;
     int* perm = (int*)(row + n);
     __shared__ int piv;
-    __shared__ c128 pv, akk, s_ip;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = A[e];
+    __shared__ C pv, akk, s_ip;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = cvt<R>(A[e]);
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (threadIdx.x < 32) {
-            double best = -1.0;
+            R best = -1;
             int bi = k;
             for (int r = k + threadIdx.x; r < n; r += 32) {
-                const double a = abs2(M[r * n + k]);
+                const R a = abs2(M[r * n + k]);
                 if (a > best) { best = a; bi = r; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const R ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
             if (threadIdx.x == 0) {
                 piv = bi;
                 perm[k] = bi;
-                c128 pk = M[bi * n + k];
+                C pk = M[bi * n + k];
                 akk = M[k * n + k];
-                if (!(best > 0.0) || !isfinite(best)) {
+                if (!(best > 0) || !isfinite(best)) {
                     atomicExch(bt.err, DEV_BREAKDOWN);
-                    pk = c128{1.0, 0.0};
+                    pk = C{1, 0};
                 }
                 pv = pk;
                 s_ip = cinv(pk);
@@ -800,10 +805,10 @@ __global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
         }
         __syncthreads();
         const int p = piv;
-        const c128 ip = s_ip;
+        const C ip = s_ip;
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             col[t] = (t == k) ? pv : (t == p ? akk : M[t * n + k]);
-            const c128 rp = M[p * n + t];
+            const C rp = M[p * n + t];
             if (p != k) { M[p * n + t] = M[k * n + t]; M[k * n + t] = rp; }
             row[t] = rp * ip;
         }
@@ -813,7 +818,7 @@ __global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
             if (r == k) {
                 M[e] = (c == k) ? ip : row[c];
             } else {
-                const c128 f = col[r];
+                const C f = col[r];
                 M[e] = (c == k) ? -(f * ip) : M[e] - f * row[c];
             }
         }
@@ -829,21 +834,27 @@ __global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
     }
     __syncthreads();
     const int* pos = perm + n;
+    c64* AT = (c64*)bt.AT[blockIdx.x];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int r = e / n, c = e - r * n;
-        A[e] = M[r * n + pos[c]];
+        const C v = M[r * n + pos[c]];
+        A[e] = cvt<double>(v);
+        if (AT) AT[e] = cvt<float>(v);
     }
 }
-void launch_gj_inverse(const GjBatch& bt, int count, cudaStream_t s) {
+void launch_gj_inverse(const GjBatch& bt, int count, bool fp32, cudaStream_t s) {
     if (count < 1) return;
     const int n = bt.n;
-    const size_t sm = sizeof(c128) * (n * n + 2 * n) + sizeof(int) * 2 * n;
+    const size_t es = fp32 ? sizeof(c64) : sizeof(c128);
+    const size_t sm = es * (n * n + 2 * n) + sizeof(int) * 2 * n;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_gj_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_gj_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_gj_inverse<<<count, 256, sm, s>>>(bt);
+    if (fp32) k_gj_inverse<float><<<count, 256, sm, s>>>(bt);
+    else k_gj_inverse<double><<<count, 256, sm, s>>>(bt);
     note_launch();
 }
 

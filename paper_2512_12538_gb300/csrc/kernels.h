@@ -157,10 +157,12 @@ void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* 
 constexpr int GJ_MAX_BATCH = 32;
 struct GjBatch {
     c128* A[GJ_MAX_BATCH];
+    void* AT[GJ_MAX_BATCH];   // complex64 copies of the inverses (entries may be NULL)
     int n;
     int* err;
 };
-void launch_gj_inverse(const GjBatch& bt, int count, cudaStream_t s);
+// fp32: eliminate in FP32 (the complex64 form), else FP64.
+void launch_gj_inverse(const GjBatch& bt, int count, bool fp32, cudaStream_t s);
 
 // ---- leaf kernels (k_leaf.cu) ------------------------------------------------------
 struct LeafTask {
