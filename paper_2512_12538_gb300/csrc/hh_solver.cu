@@ -38,7 +38,11 @@ namespace hh {
 // ------------------------------------------------------------------ launch counter
 static std::atomic<unsigned long long> g_launches{0};
 static bool g_prof_default = false;   // profiling state of newly created handles
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local unsigned long long t_launches = 0;   // this thread's launches (captures)
+void note_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
 
 // Kernel categories timed by the optional event profiler (hh_profile_*).
 enum ProfCat {
@@ -281,6 +285,7 @@ struct Solver final : SolverBase {
     c128* root_out = nullptr;   // with n_i = 1 the level-1 corrections write into the root's
     bool root_acc = false;      // output directly (accumulating onto a base iterate)
     bool pre_direct = false;    // its leaf sweeps write the owned rows into the parents
+    const int* step_gate = nullptr;   // gate of the launches of the step being enqueued
     std::vector<const void*> view_key, eview_key;
     std::vector<EigTask> h_pre;   // host copy of the preconditioner's leaf tasks (batched solves)
     // eigenbasis leaf path
@@ -295,14 +300,22 @@ struct Solver final : SolverBase {
          *gy = nullptr;
     c128* h_dots = nullptr;                       // pinned host copy of the dot products
     // captured graphs of the preconditioner step (slot 0: gv -> gz for GMRES, slot 1:
-    // the stationary update of u)
+    // the stationary update of u, slot 2: one step of the device-tested loop, update and
+    // residual)
     struct Graph {
+        cudaGraph_t graph = nullptr;   // kept: its event-record nodes address the exec's
         cudaGraphExec_t exec = nullptr;
         bool failed = false;
         bool replayed = false;
-        std::vector<EvPair> prof;
+        unsigned long long nkern = 0;  // kernels in the graph
+        std::vector<EvPair> prof;      // pairs stamped by the captured event-record nodes
+        // event-record nodes of the profiler pairs: (node, 2 * pair + (0: a, 1: b))
+        std::vector<std::pair<cudaGraphNode_t, int>> evnode;
+        // replays launched with fresh events (replay_fresh), in launch order
+        std::vector<std::vector<EvPair>> runs;
     };
-    Graph graphs[2];
+    Graph graphs[3];
+    cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
     void** d_ptrs = nullptr;
     double* h_norm = nullptr;   // pinned host
     int b_max = 0;
@@ -311,8 +324,11 @@ struct Solver final : SolverBase {
     ~Solver() override {
         for (auto& g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
             for (auto& p : g.prof) { prof_pool.push_back(p.a); if (p.b) prof_pool.push_back(p.b); }
+            runs_release(g, 0);
         }
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         if (h_norm) cudaFreeHost(h_norm);
         if (h_dots) cudaFreeHost(h_dots);
         if (block) dev_free(block, footprint, stream, hook);
@@ -569,7 +585,7 @@ struct Solver final : SolverBase {
                     by += sizeof(CT) * (b * b + 3.0 * b * sx);
                 }
                 pbeg(PC_SWEEP, by, fl);
-                launch_eig_sweep_fused<T>(eig_fused, tasks, nl, b_max, Sx, stream);
+                launch_eig_sweep_fused<T>(eig_fused, tasks, nl, b_max, Sx, stream, step_gate);
                 pend();
                 return;
             }
@@ -657,6 +673,7 @@ struct Solver final : SolverBase {
         const std::vector<int>& ps = lev[l];
         for (size_t k0 = 0; k0 < ps.size(); k0 += CB_MAX_JOBS) {
             CoarseBatch bt{};
+            bt.gate = step_gate;
             double by = 0.0, fl = 0.0;
             for (size_t k = k0; k < ps.size() && k < k0 + CB_MAX_JOBS; ++k) {
                 const int p = ps[k];
@@ -858,8 +875,9 @@ struct Solver final : SolverBase {
     // RT, the leaf precision, when rt_ready):
     // out = base + sum_c P_c M_c R_c res (base null: zero; base may be out), then
     // out += C A_c^{-1} C^H (rhs - A out).
-    void oras_step(const c128* base, const c128* rhs, c128* out, bool rt_ready = false) {
+    void oras_step(const c128* base, const c128* rhs, c128* out, bool rt_ready = false, const int* gate = nullptr) {
         const size_t N = (size_t)Sy * Sx;
+        step_gate = gate;
         if (!rt_ready) launch_copy<double, T>(res, RT, N, false, false, stream);
         // with n_i = 1 (and a level below the root's children) the level-1 corrections
         // write out = base + sum_c P_c M_c R_c res themselves
@@ -880,9 +898,11 @@ struct Solver final : SolverBase {
             }
         }
         pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
-        launch_coarse_batch<T, double, double, double>(one_job(0, rhs, out, out, true), 2 * r, partial, dcounter + 2,
-                                                       derr, stream);
+        CoarseBatch rb = one_job(0, rhs, out, out, true);
+        rb.gate = gate;
+        launch_coarse_batch<T, double, double, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
         pend();
+        step_gate = nullptr;
     }
 
     hh_status norm_sq(const c128* x, double* dst) {
@@ -905,6 +925,7 @@ struct Solver final : SolverBase {
         Graph& g = graphs[slot];
         if (g.exec) {
             cudaGraphLaunch(g.exec, stream);
+            g_launches.fetch_add(g.nkern, std::memory_order_relaxed);
             g.replayed = true;
             return;
         }
@@ -912,22 +933,104 @@ struct Solver final : SolverBase {
         if (g.failed) return;
         cudaGraph_t graph = nullptr;
         const size_t npend = prof_pending.size();
+        const unsigned long long l0 = t_launches;
+        // captured on a private stream (the caller's may be the legacy default stream,
+        // which cannot be captured); replays go to the caller's stream
+        if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            cap_stream = nullptr;
+            g.failed = true;
+            return;
+        }
+        const cudaStream_t user = stream;
+        stream = cap_stream;
         if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
+            stream = user;
             g.failed = true;
             return;
         }
         body();
         const cudaError_t e1 = cudaStreamEndCapture(stream, &graph);
+        stream = user;
         if (e1 != cudaSuccess || !graph || cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
             cudaGetLastError();
             g.failed = true;
             g.exec = nullptr;
         }
-        if (graph) cudaGraphDestroy(graph);
+        // the captured body launched nothing: its kernels count at each replay
+        g.nkern = t_launches - l0;
+        g_launches.fetch_sub(g.nkern, std::memory_order_relaxed);
         // the pairs recorded during capture belong to the graph
         g.prof.assign(prof_pending.begin() + npend, prof_pending.end());
         prof_pending.resize(npend);
+        if (g.exec && !g.prof.empty()) {
+            // find the event-record nodes, so that replays can stamp fresh events
+            size_t cnt = 0;
+            cudaGraphGetNodes(graph, nullptr, &cnt);
+            std::vector<cudaGraphNode_t> nd(cnt);
+            if (cnt && cudaGraphGetNodes(graph, nd.data(), &cnt) == cudaSuccess) {
+                for (size_t i = 0; i < cnt; ++i) {
+                    cudaGraphNodeType ty;
+                    cudaEvent_t ev = nullptr;
+                    if (cudaGraphNodeGetType(nd[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord ||
+                        cudaGraphEventRecordNodeGetEvent(nd[i], &ev) != cudaSuccess)
+                        continue;
+                    for (size_t k = 0; k < g.prof.size(); ++k) {
+                        if (g.prof[k].a == ev) g.evnode.push_back({nd[i], (int)(2 * k)});
+                        else if (g.prof[k].b == ev) g.evnode.push_back({nd[i], (int)(2 * k + 1)});
+                    }
+                }
+            }
+            cudaGetLastError();
+        }
+        if (g.exec) g.graph = graph;
+        else if (graph) cudaGraphDestroy(graph);
+    }
+
+    // Replay of graph slot `slot` whose profiler pairs get fresh events (several replays
+    // may then be in flight before the host reads them); the pairs are kept in g.runs.
+    // The first call for a slot runs `body` and captures it, as via_graph does.
+    template <class F> void replay_fresh(int slot, F body) {
+        Graph& g = graphs[slot];
+        if (!g.exec) {
+            via_graph(slot, body);
+            return;
+        }
+        if (prof_on && !g.prof.empty() && g.evnode.size() == 2 * g.prof.size()) {
+            std::vector<EvPair> v = g.prof;
+            for (auto& p : v) {
+                p.a = prof_ev();
+                p.b = prof_ev();
+            }
+            bool ok = true;
+            for (auto& [node, k] : g.evnode)
+                ok = ok && cudaGraphExecEventRecordNodeSetEvent(g.exec, node, (k & 1) ? v[k >> 1].b : v[k >> 1].a) ==
+                               cudaSuccess;
+            if (ok) {
+                g.runs.push_back(std::move(v));
+            } else {
+                // not settable: replays keep stamping the captured events (only the last
+                // replay before a read is then timed)
+                cudaGetLastError();
+                g.evnode.clear();
+                for (auto& p : v) { prof_pool.push_back(p.a); prof_pool.push_back(p.b); }
+            }
+        }
+        cudaGraphLaunch(g.exec, stream);
+        g_launches.fetch_add(g.nkern, std::memory_order_relaxed);
+    }
+    // after a synchronisation: account the first `keep` replays of g.runs (those that
+    // did work) and return every event of g.runs to the pool
+    void runs_release(Graph& g, size_t keep) {
+        for (size_t i = 0; i < g.runs.size(); ++i) {
+            for (auto& p : g.runs[i]) {
+                if (i < keep) prof_account(p);
+                prof_pool.push_back(p.a);
+                if (p.b) prof_pool.push_back(p.b);
+            }
+        }
+        g.runs.clear();
     }
     // after a synchronisation: account the graphs' profiler events of the last replay
     void graphs_collect() {
@@ -961,8 +1064,85 @@ struct Solver final : SolverBase {
         return ok;
     }
 
+    // The launches of one stationary step on the fast path (n_i = 1, fused eigenbasis
+    // leaf sweeps writing into the parents, L >= 2) are the leaf sweep and the batched
+    // coarse corrections: all of them, and the residual that follows, take a gate.
+    bool device_test_path() const {
+        return eig && eig_fused && pre_direct && P.n_inner == 1 && L >= 2 && P.outer == HH_OUTER_ORAS;
+    }
+
+    // residual b - A u into res and RT, its norm and the device stopping test (ctl)
+    void gated_residual(int* ctl) {
+        int nb = 0;
+        pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
+        launch_residual_cast<T>(u, bvec, res, RT, geom(0), npart, &nb, stream, ctl);
+        pend();
+        launch_sum_stop(npart, nb, dnorm, ctl, P.tol, stream);
+    }
+
+    // the norms, the status words and the stop words (dnorm[0..8)) to the host
+    bool read_norms(hh_status& st) {
+        ck(cudaMemcpyAsync(h_norm, dnorm, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaGetLastError(), cerr);
+        ck(cudaStreamSynchronize(stream), cerr);
+        if (cerr != cudaSuccess) { st = HH_ECUDA; return false; }
+        const int e2 = *(const int*)(h_norm + 4);
+        st = e2 == DEV_BREAKDOWN ? HH_EBREAKDOWN : e2 == DEV_TIMEOUT ? HH_ETIMEOUT : e2 == DEV_BADARG ? HH_EINVAL
+                                                                                                 : HH_OK;
+        return st == HH_OK;
+    }
+
+    // Stationary iteration u <- u + M (b - A u) (Eqs. (2)-(3)) with the stopping test on
+    // the device.  Each step (update, residual, test) is gated by the stop word the
+    // previous test sets, so the host queues several steps per synchronisation: a step
+    // queued after the test passed does nothing, and u, the iteration count and the
+    // final residual are those of the loop that tests after every step.  The number of
+    // steps queued follows the contraction observed so far.
+    hh_status loop_oras_device_test(int& it, double& rel) {
+        int* ctl = (int*)(dnorm + 6);   // [0] stop (1 converged, 2 not finite), [1] tests run
+        const int* hctl = (const int*)(h_norm + 6);
+        hh_status st = HH_OK;
+        zero(ctl, 2 * sizeof(int));
+        gated_residual(ctl);
+        if (!read_norms(st)) return st;
+        double rel_prev = -1.0;
+        int it_prev = 0, chunk = 8;
+        for (;;) {
+            rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
+            if (hctl[0] == 2 || !std::isfinite(rel)) return HH_ENOCONV;
+            if (hctl[0] == 1) return HH_OK;
+            if (it >= P.max_iter) return HH_ENOCONV;
+            // steps still needed at the observed contraction rate, and two to spare
+            if (rel_prev > 0 && it > it_prev && rel < rel_prev && rel > 0) {
+                const double rho = std::pow(rel / rel_prev, 1.0 / (it - it_prev));
+                const double need = std::log(P.tol / rel) / std::log(rho);
+                chunk = need < 62.0 ? (int)std::ceil(need) + 2 : 64;
+            } else if (rel_prev > 0) {
+                chunk = 8;
+            }
+            rel_prev = rel;
+            it_prev = it;
+            const int n = std::max(1, std::min(chunk, P.max_iter - it));
+            const int tests0 = hctl[1];
+            const bool fresh = graphs[2].exec == nullptr;
+            for (int k = 0; k < n; ++k)
+                replay_fresh(2, [&] {
+                    oras_step(u, bvec, u, true, ctl);
+                    gated_residual(ctl);
+                });
+            const bool ok = read_norms(st);
+            const int ran = hctl[1] - tests0;
+            // the first step of a new handle ran directly (its pairs are pending); the
+            // replays that did work are the next ran - 1
+            runs_release(graphs[2], (size_t)std::max(0, ran - (fresh ? 1 : 0)));
+            if (!ok) return st;
+            it += ran;
+        }
+    }
+
     // Stationary iteration u <- u + M (b - A u)  (Eqs. (2)-(3)).
     hh_status loop_oras(int& it, double& rel) {
+        if (device_test_path()) return loop_oras_device_test(it, rel);
         hh_status st = HH_OK;
         for (;;) {
             if (!true_residual(res, st, RT)) return st;

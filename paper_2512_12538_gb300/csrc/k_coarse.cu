@@ -233,6 +233,9 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
 template <typename TC, typename TV, typename TW, typename TO>
 __global__ void __launch_bounds__(256) k_coarse_batch(CoarseBatch bt, int p, cplx<TC>* partial, unsigned* bar,
                                                       int* err) {
+    // a set stop word (written by an earlier launch: the same for every block) skips the
+    // launch before the grid barrier
+    if (bt.gate && *bt.gate) return;
     using CA = cplx<TC>;
     using R = decltype(TV() + TW());
     __shared__ CA red[8][16];

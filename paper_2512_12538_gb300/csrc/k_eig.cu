@@ -627,7 +627,11 @@ struct alignas(2 * sizeof(cplx<T>)) cpair {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* __restrict__ tasks,
+                                                                 const int* __restrict__ gate) {
+    // a set stop word (written by an earlier launch, so the same for every CTA) skips
+    // the launch before any cluster barrier
+    if (gate && *gate) return;
     using C = cplx<T>;
     using C2 = cpair<T>;
     cg::cluster_group cluster = cg::this_cluster();
@@ -791,11 +795,12 @@ int eig_sweep_fused_ready(int b_max, int Sx) {
 }
 
 template <typename T>
-void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s) {
+void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s,
+                            const int* gate) {
     const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx, cl).elems;
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = fs_config<T>(cl, ntasks, sm, s, at);
-    cudaLaunchKernelEx(&cfg, k_eig_sweep_fused<T>, d_tasks);
+    cudaLaunchKernelEx(&cfg, k_eig_sweep_fused<T>, d_tasks, gate);
     note_launch();
 }
 
@@ -808,8 +813,8 @@ template void launch_eig_sweep<float>(const EigTask*, int, int, int, int, cudaSt
 template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep<double>(const EigTask*, int, int, int, int, cudaStream_t);
-template void launch_eig_sweep_fused<float>(int, const EigTask*, int, int, int, cudaStream_t);
-template void launch_eig_sweep_fused<double>(int, const EigTask*, int, int, int, cudaStream_t);
+template void launch_eig_sweep_fused<float>(int, const EigTask*, int, int, int, cudaStream_t, const int*);
+template void launch_eig_sweep_fused<double>(int, const EigTask*, int, int, int, cudaStream_t, const int*);
 template int eig_sweep_fused_ready<float>(int, int);
 template int eig_sweep_fused_ready<double>(int, int);
 

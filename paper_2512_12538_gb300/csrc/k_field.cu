@@ -74,7 +74,8 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
 // same residual rounded to the leaf precision (yt), the input of the next ORAS step.
 template <typename T>
 __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restrict__ v, c128* __restrict__ y,
-                                cplx<T>* __restrict__ yt, OpGeom g, double* part) {
+                                cplx<T>* __restrict__ yt, OpGeom g, double* part, const int* gate) {
+    if (gate && *gate) return;
     const size_t total = (size_t)g.b * g.Sx;
     double acc2 = 0.0;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -105,16 +106,17 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
 }
 template <typename T>
 void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, int* nblk_out,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int* gate) {
     const size_t total = (size_t)g.b * g.Sx;
     const int grid = grid_for(total, 256, 152 * 8);
-    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part);
+    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate);
     note_launch();
     if (nblk_out) *nblk_out = grid;
 }
-template void launch_residual_cast<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, int*, cudaStream_t);
+template void launch_residual_cast<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, int*, cudaStream_t,
+                                          const int*);
 template void launch_residual_cast<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, int*,
-                                           cudaStream_t);
+                                           cudaStream_t, const int*);
 
 // Residuals of several problems in one launch (the batched solver): job k owns blocks
 // [blk0, blk0 + nblk) and computes y = v - A x, its complex64/128 copy yt and per-block
@@ -202,6 +204,35 @@ __global__ void k_sum(const double* part, int n, double* out) {
 }
 void launch_sum(const double* part, int n, double* out, cudaStream_t s) {
     k_sum<<<1, 256, 0, s>>>(part, n, out);
+    note_launch();
+}
+
+// k_sum's reduction (same order, so the same ||r||^2) followed by the stopping test the
+// host would take: IEEE division and square root in FP64 on both sides give the same
+// decision.
+__global__ void k_sum_stop(const double* part, int n, double* nrm, int* ctl, double tol) {
+    if (*(volatile int*)ctl) return;
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+    __shared__ double red[32];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s2 = warp_sum(s2);
+        if (threadIdx.x == 0) {
+            nrm[0] = s2;
+            ctl[1] += 1;
+            const double b2 = nrm[2];
+            const double rel = b2 > 0 ? sqrt(s2 / b2) : 0.0;
+            if (!isfinite(rel)) ctl[0] = 2;
+            else if (rel < tol) ctl[0] = 1;
+        }
+    }
+}
+void launch_sum_stop(const double* part, int n, double* nrm, int* ctl, double tol, cudaStream_t s) {
+    k_sum_stop<<<1, 256, 0, s>>>(part, n, nrm, ctl, tol);
     note_launch();
 }
 

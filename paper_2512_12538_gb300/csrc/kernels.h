@@ -17,9 +17,10 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
                   double* part, int* nblk_out, cudaStream_t s);
 
 // y = v - A x (FP64, one column) with per-block |y|^2 partials, and yt = y rounded to T.
+// gate (may be null): when the device word is nonzero at launch, nothing is done.
 template <typename T>
 void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, int* nblk_out,
-                          cudaStream_t s);
+                          cudaStream_t s, const int* gate = nullptr);
 
 // Residuals of up to RB_MAX_JOBS problems in one launch: per job y = v - A x (FP64) and
 // yt = y in T; norms[k] = ||y_k||^2 (fixed-order sums).  part: scratch of part_cap doubles.
@@ -41,6 +42,11 @@ void launch_residual_batch(ResidBatch bt, double* part, int part_cap, double* no
 
 // out = sum of n doubles (deterministic single-block reduction)
 void launch_sum(const double* part, int n, double* out, cudaStream_t s);
+// The stopping test of the stationary iteration kept on the device.  Unless ctl[0] is
+// already set: nrm[0] = sum of the n partials (||r||^2, same order as launch_sum),
+// ctl[1] += 1, and with rel = sqrt(nrm[0] / nrm[2]) (0 when nrm[2] <= 0) ctl[0] = 2 if
+// rel is not finite, 1 if rel < tol.  ctl[0] is the gate of the next step's launches.
+void launch_sum_stop(const double* part, int n, double* nrm, int* ctl, double tol, cudaStream_t s);
 
 // b = h^2 w_i w_j f + h (w_j gx + w_i gy) for the global problem.
 void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s);
@@ -104,6 +110,7 @@ struct CoarseJob {
 struct CoarseBatch {
     CoarseJob job[CB_MAX_JOBS];
     int njobs;
+    const int* gate;       // may be null: when the word is nonzero at launch, nothing is done
 };
 template <typename TC, typename TV, typename TW, typename TO>
 void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s);
@@ -208,8 +215,10 @@ constexpr int FS_SMEM_MAX = 220 * 1024;
 template <typename T>
 int eig_sweep_fused_ready(int b_max, int Sx);
 // b_max, Sx: the largest band and column count among the tasks (shared-memory size).
+// gate (may be null): a device word; when it is nonzero at launch the launch does nothing.
 template <typename T>
-void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s);
+void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s,
+                            const int* gate = nullptr);
 // stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^
 template <typename T>
 void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
