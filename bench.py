@@ -35,6 +35,7 @@ UNIT = "solves/s"
 WORKLOAD = "helm2d_n255_k40_L2"
 # FP64 relative-residual stopping tolerance giving relative error <= 1e-8 against the
 # direct solution on this workload (checked by tests/test_gpu_bench_calibration.py).
+PROFILED_PASS_STEPS = 2      # untimed steps with every kernel category timed
 TOL = 1e-10
 MAX_ITER = 400
 OUTER = "oras"                      # stationary ORAS iteration (GMRES: outer="gmres")
@@ -201,13 +202,24 @@ def run_ours(args, rank, world):
         one("mixed")
     one("fp64")
 
-    # timed: mixed form, headline.  The library's event profiler is on for these handles:
-    # it records CUDA events on `stream` around its kernels, which gives the dominant
-    # kernel's average launch duration over the timed region.
+    # untimed profiled pass: every kernel category timed with CUDA events on `stream`
+    # (the per-category table, and which category dominates)
+    prof_all = {}
+    hh.hh_profile_enable(None, True)
+    for _ in range(PROFILED_PASS_STEPS):
+        _, _, prof = one("mixed", profile=True)
+        for k, vals in prof.items():
+            old = prof_all.get(k, (0.0, 0, 0.0, 0.0))
+            prof_all[k] = tuple(x + y for x, y in zip(old, vals))
+    dominant = max(prof_all, key=lambda k: prof_all[k][0])
+
+    # timed: mixed form, headline.  The library's event profiler times the dominant
+    # category alone here (CUDA events on `stream` around its launches), which gives its
+    # average launch duration over the timed region at the cost of two events per step.
+    hh.hh_profile_categories(None, [dominant])
     barrier()
     launches0 = hh.hh_launch_count()
     step_ms, iters, prof_total = [], [], {}
-    hh.hh_profile_enable(None, True)
     with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -220,8 +232,8 @@ def run_ours(args, rank, world):
         barrier()
         wall = time.perf_counter() - t0
     hh.hh_profile_enable(None, False)
+    hh.hh_profile_categories(None, None)
     launches = hh.hh_launch_count() - launches0
-    prof_iters = iters
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -258,7 +270,7 @@ def run_ours(args, rank, world):
     batch = run_batch_form(hh, torch) if rank == 0 else None
 
     pk, pk_kind = peaks()
-    roof = roofline(w, prof_total, prof_iters, pk, pk_kind)
+    roof = roofline(w, prof_total, prof_all, dominant, pk, pk_kind)
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -276,7 +288,8 @@ def run_ours(args, rank, world):
         "mixed_over_fp64": (value / world) / (len(fp64_ms) / (sum(fp64_ms) / 1e3)),
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
         "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
-                    for k, v in prof_total.items() if v[1] > 0},
+                    for k, v in prof_all.items() if v[1] > 0},
+        "kernels_from": f"untimed profiled pass of {PROFILED_PASS_STEPS} steps, every category timed",
         "wall_s_timed": wall,
     }
     if batch is not None:
@@ -416,16 +429,16 @@ def rate(cat, ms, by, fl, pk, pk_kind):
     return out
 
 
-def roofline(w, prof, iters, pk, pk_kind):
-    """Dominant kernel category (largest total device time over the timed solves, CUDA
-    events on the launching stream) with its algorithmic rate against its peak."""
-    if not prof:
+def roofline(w, prof, prof_all, cat, pk, pk_kind):
+    """The dominant kernel category (largest total device time in the untimed profiled
+    pass) with its algorithmic rate against its peak; the rate from its CUDA-event times
+    over the timed solves (`prof`, that category alone timed)."""
+    if not prof or cat not in prof or prof[cat][1] == 0:
         return None
-    tot_ms = sum(v[0] for v in prof.values())
-    cat = max(prof, key=lambda k: prof[k][0])
     ms, launches, by, fl = prof[cat]
     out = rate(cat, ms, by, fl, pk, pk_kind)
-    out.update({"launches": launches, "avg_launch_ms": ms / max(launches, 1), "share_of_profiled_ms": ms / tot_ms,
+    out.update({"launches": launches, "avg_launch_ms": ms / max(launches, 1),
+                "share_of_profiled_ms": prof_all[cat][0] / sum(v[0] for v in prof_all.values()),
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(cat), "alg_bytes_per_launch": by / max(launches, 1),
                 "alg_flops_per_launch": fl / max(launches, 1)})
     return out

@@ -300,6 +300,12 @@ hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
 /* h != NULL: (re)start profiling of that handle, clearing its totals; h == NULL: set
  * whether handles created afterwards profile from their first set-up kernel. */
 hh_status hh_profile_enable(hh_handle* h, int enable);
+/* Which categories the profiler times: bit c of mask for category c (default: all).
+ * Each timed category costs events on the stream, so a caller timing one kernel family
+ * selects only that one.  h != NULL: that handle, from its next launch; h == NULL:
+ * handles created afterwards.  Within one outer step the coarse corrections of all
+ * levels run back to back and share one event pair (counted as that many launches). */
+hh_status hh_profile_categories(hh_handle* h, unsigned mask);
 /* total_ms: summed event time; launches: timed launches; alg_bytes / alg_flops: the
  * algorithmic memory traffic and floating-point work of those launches (formulas in the
  * library: e.g. a band transform of b rows, S_x columns and nc right-hand sides counts

@@ -18,7 +18,7 @@ _BINDING = {
     "hh_coarse_apply", "hh_destroy", "hh_footprint", "hh_get_basis", "hh_interface_map", "hh_leaf_solve",
     "hh_node_info", "hh_params", "hh_precondition", "hh_residual", "hh_set_allocator", "hh_setup",
     "hh_sketch_samples", "hh_solve", "hh_solve_host", "hh_stats", "make_params", "status_string",
-    "use_torch_allocator", "hh_profile_enable", "hh_profile_read", "hh_launch_count", "PROFILE_CATEGORIES",
+    "use_torch_allocator", "hh_profile_enable", "hh_profile_categories", "hh_profile_read", "hh_launch_count", "PROFILE_CATEGORIES",
     "HH_LEAF_EIGEN", "HH_LEAF_BLOCK", "HH_OUTER_ORAS", "HH_OUTER_GMRES",
     "hh_residual_noalloc", "HH_ETOOLARGE", "HH_NOALLOC_MAX_ROWS", "hh_setup_batch", "hh_solve_batch", "hh_server_create", "hh_server_submit",
     "hh_server_poll", "hh_server_destroy", "HH_EPENDING",

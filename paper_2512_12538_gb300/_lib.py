@@ -72,6 +72,7 @@ def _load():
         "hh_precondition": (i, [vp, vp, vp, vp]),
         "hh_sketch_samples": (i, [vp, i, vp, vp]),
         "hh_profile_enable": (i, [vp, i]),
+        "hh_profile_categories": (i, [vp, ctypes.c_uint]),
         "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
         "hh_launch_count": (ctypes.c_ulonglong, []),
         "hh_residual_noalloc": (i, [i, i, d, vp, vp, vp, vp, P(d)]),
@@ -309,6 +310,12 @@ PROFILE_CATEGORIES = ["factor", "sweep_in", "sweep_recur", "sweep_out", "residua
 
 def hh_profile_enable(h, enable=True) -> None:
     _check(LIB.hh_profile_enable(h, int(bool(enable))), "hh_profile_enable")
+
+
+def hh_profile_categories(h, names=None) -> None:
+    """Time only the named categories (PROFILE_CATEGORIES); None: all of them."""
+    mask = 0xFFFFFFFF if names is None else sum(1 << PROFILE_CATEGORIES.index(n) for n in names)
+    _check(LIB.hh_profile_categories(h, ctypes.c_uint(mask)), "hh_profile_categories")
 
 
 def hh_profile_read(h, work=False) -> dict:

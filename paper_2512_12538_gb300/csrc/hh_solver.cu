@@ -38,6 +38,7 @@ namespace hh {
 // ------------------------------------------------------------------ launch counter
 static std::atomic<unsigned long long> g_launches{0};
 static bool g_prof_default = false;   // profiling state of newly created handles
+static unsigned g_prof_mask_default = ~0u;   // their timed categories
 static thread_local unsigned long long t_launches = 0;   // this thread's launches (captures)
 void note_launch() {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -178,8 +179,10 @@ struct SolverBase {
     cudaStream_t stream = nullptr;
     double t_setup_ms = 0.0, t_solve_ms = 0.0;
     // event profiler: pairs recorded around the kernels of one category
-    struct EvPair { cudaEvent_t a, b; int cat; double bytes, flops; };
+    // nl: launches between a and b (adjacent launches of one category share a pair)
+    struct EvPair { cudaEvent_t a, b; int cat; double bytes, flops; int nl; };
     bool prof_on = false;
+    unsigned prof_mask = ~0u;   // categories timed while prof_on
     std::vector<EvPair> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[PC_NCAT] = {0};
@@ -200,14 +203,28 @@ struct SolverBase {
         else cudaEventRecord(e, stream);
     }
     // bytes / flops: algorithmic work of the kernels between pbeg and pend
+    bool prof_cat(int cat) const { return prof_on && ((prof_mask >> cat) & 1u); }
     void pbeg(int cat, double bytes = 0.0, double flops = 0.0) {
-        if (!prof_on) return;
-        EvPair p{prof_ev(), nullptr, cat, bytes, flops};
+        if (!prof_cat(cat)) return;
+        EvPair p{prof_ev(), nullptr, cat, bytes, flops, 1};
         ev_record(p.a);
         prof_pending.push_back(p);
     }
-    void pend() {
-        if (!prof_on || prof_pending.empty() || prof_pending.back().b) return;
+    // like pbeg, but a launch that directly follows an open pair of the same category
+    // joins it (one pair, two events, for a run of adjacent launches)
+    void pjoin(int cat, double bytes, double flops) {
+        if (!prof_cat(cat)) return;
+        if (!prof_pending.empty() && !prof_pending.back().b && prof_pending.back().cat == cat) {
+            EvPair& p = prof_pending.back();
+            p.bytes += bytes;
+            p.flops += flops;
+            p.nl += 1;
+            return;
+        }
+        pbeg(cat, bytes, flops);
+    }
+    void pend(int cat) {
+        if (!prof_cat(cat) || prof_pending.empty() || prof_pending.back().b || prof_pending.back().cat != cat) return;
         prof_pending.back().b = prof_ev();
         ev_record(prof_pending.back().b);
     }
@@ -216,7 +233,7 @@ struct SolverBase {
         float ms = 0.f;
         if (p.b && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             prof_ms[p.cat] += ms;
-            prof_n[p.cat] += 1;
+            prof_n[p.cat] += p.nl;
             prof_bytes[p.cat] += p.bytes;
             prof_flops[p.cat] += p.flops;
         }
@@ -232,8 +249,9 @@ struct SolverBase {
         }
         prof_pending.clear();
     }
-    void prof_reset(bool on) {
+    void prof_reset(bool on, unsigned mask) {
         prof_on = on;
+        prof_mask = mask;
         for (int i = 0; i < PC_NCAT; ++i) { prof_ms[i] = 0; prof_n[i] = 0; prof_bytes[i] = 0; prof_flops[i] = 0; }
     }
     virtual ~SolverBase() {
@@ -586,7 +604,7 @@ struct Solver final : SolverBase {
                 }
                 pbeg(PC_SWEEP, by, fl);
                 launch_eig_sweep_fused<T>(eig_fused, tasks, nl, b_max, Sx, stream, step_gate);
-                pend();
+                pend(PC_SWEEP);
                 return;
             }
             for (int stg = 0; stg < 3; ++stg) {
@@ -600,7 +618,7 @@ struct Solver final : SolverBase {
                 }
                 pbeg(PC_TIN + stg, by, fl);
                 launch_eig_sweep_stage<T>(stg, tasks, nl, b_max, Sx, nc, stream);
-                pend();
+                pend(PC_TIN + stg);
             }
             return;
         }
@@ -615,7 +633,7 @@ struct Solver final : SolverBase {
         }
         pbeg(PC_RECUR);
         launch_sweep<T>(tasks, nl, b_max, Sx, nc, derr, stream);
-        pend();
+        pend(PC_RECUR);
     }
 
     // Buffer holding node p's input during the current apply: with n_i = 1 its input
@@ -695,10 +713,11 @@ struct Solver final : SolverBase {
                 by += (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT);
                 fl += 2.0 * 8.0 * 2 * r * pts(p);
             }
-            pbeg(PC_COARSE, by, fl);
+            // the pair stays open: the step's next launches are the coarse corrections of
+            // the levels above and the root's, which closes it (oras_step)
+            pjoin(PC_COARSE, by, fl);
             if (l == 1) launch_coarse_batch<T, T, T, double>(bt, 2 * r, partial, dcounter + 2, derr, stream);
             else launch_coarse_batch<T, T, T, T>(bt, 2 * r, partial, dcounter + 2, derr, stream);
-            pend();
         }
     }
 
@@ -732,14 +751,14 @@ struct Solver final : SolverBase {
             pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT), 2.0 * 8.0 * 2 * r * pts(p));
             launch_coarse_batch<T, T, T, T>(one_job(p, vin, W[p], W[p], true), 2 * r, partial, dcounter + 2, derr,
                                             stream);
-            pend();
+            pend(PC_COARSE);
             return;
         }
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
         pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + nc) * sizeof(CT), 8.0 * 2 * r * nc * pts(p));
         const int nb = launch_ip_partial_colA<T, T, T>(C[p], R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
                                                        stream);
-        pend();
+        pend(PC_COARSE);
         launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
         launch_coarse_updn<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
     }
@@ -766,7 +785,7 @@ struct Solver final : SolverBase {
         for (int c : cs) ys.push_back(Om[c]);
         pbeg(PC_QR);
         launch_qr<T>(ys.data(), (int)ys.size(), Sx, m, (CT**)d_ptrs, stream);
-        pend();
+        pend(PC_QR);
         // Z = T_c^* Q = B_c conj(M_c conj(A~_s B_s^T ... )) ; here as conj(M_c(A~_s B_s^T conj Q))
         for (int c : cs) {
             const Node& cn = nodes[c];
@@ -790,7 +809,7 @@ struct Solver final : SolverBase {
         for (int c : cs) { gs.push_back(Gm[c]); us.push_back(U[c]); ls.push_back(lam[c]); }
         pbeg(PC_JACOBI);
         launch_heig(gs.data(), us.data(), ls.data(), (int)cs.size(), m, r, d_ptrs, stream);
-        pend();
+        pend(PC_JACOBI);
         for (int c : cs) launch_form_v<T>(Z[c], U[c], lam[c], Vc[c], Sx, m, r, stream);
         // C_c = P_c M_c B_c^T V_c
         for (int c : cs) {
@@ -811,7 +830,7 @@ struct Solver final : SolverBase {
             pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT), 8.0 * 2.0 * r * r * pts(p));
             const int split = nodes[nodes[p].child[1]].own_a - nodes[p].ra;
             const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS, stream);
-            pend();
+            pend(PC_GALERKIN);
             launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
         }
         // the level's Galerkin matrices inverted together
@@ -852,7 +871,7 @@ struct Solver final : SolverBase {
         pbeg(PC_FACTOR);
         if (eig) launch_eig_factor<T>(d_etasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
         else launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
-        pend();
+        pend(PC_FACTOR);
         for (int l = L; l >= 1; --l) sketch_level(l);
         upload_pre_tasks();
         cudaEventRecord(e1, stream);
@@ -897,11 +916,11 @@ struct Solver final : SolverBase {
                                        (size_t)(cn.own_b - cn.own_a) * Sx, base != nullptr, false, stream);
             }
         }
-        pbeg(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
+        pjoin(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
         CoarseBatch rb = one_job(0, rhs, out, out, true);
         rb.gate = gate;
         launch_coarse_batch<T, double, double, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
-        pend();
+        pend(PC_COARSE);
         step_gate = nullptr;
     }
 
@@ -1046,7 +1065,7 @@ struct Solver final : SolverBase {
         pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
         if (dst_t) launch_residual_cast<T>(u, bvec, dst, dst_t, geom(0), npart, &nb, stream);
         else launch_apply<double, double, double>(u, bvec, dst, geom(0), 1, 1.0, npart, &nb, stream);
-        pend();
+        pend(PC_SPMV);
         launch_sum(npart, nb, dnorm, stream);
         // the norms and the device status words in one copy
         ck(cudaMemcpyAsync(h_norm, dnorm, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
@@ -1076,7 +1095,7 @@ struct Solver final : SolverBase {
         int nb = 0;
         pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
         launch_residual_cast<T>(u, bvec, res, RT, geom(0), npart, &nb, stream, ctl);
-        pend();
+        pend(PC_SPMV);
         launch_sum_stop(npart, nb, dnorm, ctl, P.tol, stream);
     }
 
@@ -1432,7 +1451,7 @@ static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out,
     sb->block = dev_alloc(sb->footprint, sb->stream, sb->hook);
     if (!sb->block) return HH_ENOMEM;
     sb->plan((char*)sb->block);
-    sb->prof_reset(g_prof_default);
+    sb->prof_reset(g_prof_default, g_prof_mask_default);
     const hh_status st = sb->setup();
     if (st != HH_OK) return st;
     *out = sb.release();
@@ -2133,7 +2152,7 @@ hh_status hh_setup(const hh_params* params, void* stream, hh_handle** out, size_
     s->block = hh::dev_alloc(s->footprint, s->stream, s->hook);
     if (!s->block) return HH_ENOMEM;
     s->plan((char*)s->block);
-    s->prof_reset(hh::g_prof_default);
+    s->prof_reset(hh::g_prof_default, hh::g_prof_mask_default);
     const hh_status st = s->setup();
     if (footprint_out) *footprint_out = s->footprint;
     if (st != HH_OK) return st;
@@ -2368,7 +2387,15 @@ hh_status hh_profile_enable(hh_handle* h, int enable) {
         hh::g_prof_default = enable != 0;
         return HH_OK;
     }
-    h->s->prof_reset(enable != 0);
+    h->s->prof_reset(enable != 0, h->s->prof_mask);
+    return HH_OK;
+}
+hh_status hh_profile_categories(hh_handle* h, unsigned mask) {
+    if (!h) {
+        hh::g_prof_mask_default = mask;
+        return HH_OK;
+    }
+    h->s->prof_mask = mask;
     return HH_OK;
 }
 hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches,

@@ -111,3 +111,30 @@ def test_profiler_counts_only_steps_that_ran(hh):
             assert prof["leaf_sweep"][0] > 0 and prof["residual"][0] > 0
     finally:
         hh.hh_destroy(h)
+
+
+def test_profiler_category_mask(hh):
+    n = 45
+    S = n + 2
+    f = torch.from_numpy(random_complex((S, S), 45)).cuda()
+    g = torch.from_numpy(random_complex((4, S), 46)).cuda()
+    p = hh.make_params(2, n, 12.0, 2, 2, 6, 4, 1, 1e-9, 300, "mixed", 0)
+    h, _ = hh.hh_setup(p)
+    try:
+        u = torch.empty((S, S), dtype=torch.complex128, device="cuda")
+        hh.hh_profile_categories(h, ["coarse_project"])
+        hh.hh_profile_enable(h, True)
+        st = hh.hh_solve(h, f, g, u)
+        prof = hh.hh_profile_read(h, work=True)
+        # two coarse launches per step (both level-1 nodes together, then the root),
+        # sharing one event pair; nothing else timed
+        assert prof["coarse_project"][1] == 2 * st.iters
+        assert prof["coarse_project"][0] > 0 and prof["coarse_project"][2] > 0
+        assert all(prof[c][1] == 0 for c in hh.PROFILE_CATEGORIES if c != "coarse_project")
+        hh.hh_profile_categories(h, None)
+        hh.hh_profile_enable(h, True)
+        st = hh.hh_solve(h, f, g, u)
+        prof = hh.hh_profile_read(h)
+        assert prof["leaf_sweep"][1] == st.iters and prof["coarse_project"][1] == 2 * st.iters
+    finally:
+        hh.hh_destroy(h)
