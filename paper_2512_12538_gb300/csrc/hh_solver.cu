@@ -258,6 +258,16 @@ struct SolverBase {
         for (auto& p : prof_pending) { prof_pool.push_back(p.a); if (p.b) prof_pool.push_back(p.b); }
         for (auto e : prof_pool) cudaEventDestroy(e);
     }
+    // forget captured graphs (their event-record nodes follow the profiler settings of
+    // the capture); the next step captures again
+    virtual void drop_graphs() {}
+    // profiler settings of this handle; captured graphs are dropped when they change
+    void prof_configure(bool on, unsigned mask, bool clear) {
+        if (on != prof_on || mask != prof_mask) drop_graphs();
+        if (clear) prof_reset(on, mask);
+        prof_on = on;
+        prof_mask = mask;
+    }
     virtual size_t plan(char* base) = 0;
     virtual hh_status setup() = 0;
     virtual hh_status solve(const c128* f, const c128* g, c128* u, hh_stats* st) = 0;
@@ -1038,6 +1048,16 @@ struct Solver final : SolverBase {
         }
         cudaGraphLaunch(g.exec, stream);
         g_launches.fetch_add(g.nkern, std::memory_order_relaxed);
+    }
+    void drop_graphs() override {
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto& g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+            for (auto& p : g.prof) { prof_pool.push_back(p.a); if (p.b) prof_pool.push_back(p.b); }
+            runs_release(g, 0);
+            g = Graph{};
+        }
     }
     // after a synchronisation: account the first `keep` replays of g.runs (those that
     // did work) and return every event of g.runs to the pool
@@ -2387,7 +2407,7 @@ hh_status hh_profile_enable(hh_handle* h, int enable) {
         hh::g_prof_default = enable != 0;
         return HH_OK;
     }
-    h->s->prof_reset(enable != 0, h->s->prof_mask);
+    h->s->prof_configure(enable != 0, h->s->prof_mask, true);
     return HH_OK;
 }
 hh_status hh_profile_categories(hh_handle* h, unsigned mask) {
@@ -2395,7 +2415,8 @@ hh_status hh_profile_categories(hh_handle* h, unsigned mask) {
         hh::g_prof_mask_default = mask;
         return HH_OK;
     }
-    h->s->prof_mask = mask;
+    // the totals so far stay; graphs captured under the old selection are dropped
+    h->s->prof_configure(h->s->prof_on, mask, false);
     return HH_OK;
 }
 hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches,
