@@ -275,6 +275,8 @@ def run_ours(args, rank, world):
 
     pk, pk_kind = peaks()
     roof = roofline(w, prof_total, prof_all, dominant, pk, pk_kind)
+    if roof is not None:
+        roof["event_steps"] = f"{len(range(0, args.steps, PROFILE_EVERY))} of {args.steps} timed steps"
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
