@@ -33,9 +33,13 @@ if ROOT not in sys.path:
 METRIC = "Helmholtz solves/sec at rel err 1e-8 (mixed vs FP64 GPU); p50/p99 latency"
 UNIT = "solves/s"
 WORKLOAD = "helm2d_n255_k40_L2"
-# FP64 relative-residual stopping tolerance giving relative error <= 1e-8 against the
-# direct solution on this workload (checked by tests/test_gpu_bench_calibration.py).
-TOL = 1e-10
+# FP64 relative-residual stopping tolerance for relative error <= 1e-8 against the
+# direct solution on this workload, with a margin of at least 10x (the error is checked
+# to be <= 1e-9 in both forms by tests/test_gpu_bench_calibration.py).
+TOL = 1e-9
+# The batching and serving forms mix grid sizes and wavenumbers that this calibration
+# does not cover: they stop at the tighter 1e-10.
+TOL_FORMS = 1e-10
 MAX_ITER = 400
 PROFILED_PASS_STEPS = 2      # untimed steps with every kernel category timed
 PROFILE_EVERY = 5            # timed steps per step whose dominant-kernel launches carry events
@@ -315,7 +319,7 @@ def run_batch_form(hh, torch, count=BATCH_PROBLEMS):
     solve."""
     from workloads import batch_problems
     probs = batch_problems(count)
-    params = [hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, 1, TOL, MAX_ITER, "mixed",
+    params = [hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, 1, TOL_FORMS, MAX_ITER, "mixed",
                              1 + i) for i, (w, f, g) in enumerate(probs)]
     fs = [torch.from_numpy(f).cuda() for (w, f, g) in probs]
     gs = [torch.from_numpy(g).cuda() for (w, f, g) in probs]
@@ -337,7 +341,7 @@ def run_batch_form(hh, torch, count=BATCH_PROBLEMS):
                "solve_ms": 1e3 * (t2 - t1), "iterations": {"median": statistics.median(its), "max": max(its)},
                "max_rel_res": max(st.rel_res for st in sts),
                "workload": "batch: grid sides U{63,127,191,255}, k h U[0.3,0.6], L=2, overlap 2, r=16, p=8, "
-                           "mixed form, tol 1e-10"}
+                           f"mixed form, tol {TOL_FORMS}"}
     return res
 
 
@@ -365,7 +369,7 @@ def run_serving(args):
         n = int(rng.choice([127, 255, 511, 1023]))
         k = float(rng.uniform(20.0, min(150.0, 0.6 * (n + 1))))
         lv, ov, r = (2, 2, 16) if n <= 255 else (3, 4, 32)
-        p = hh.make_params(2, n, k, lv, ov, r, 10, 1, TOL, MAX_ITER, "mixed", len(reqs) + 1)
+        p = hh.make_params(2, n, k, lv, ov, r, 10, 1, TOL_FORMS, MAX_ITER, "mixed", len(reqs) + 1)
         f = torch.from_numpy(point_source_rhs(n, 2512_12538 + 31 * len(reqs))).cuda()
         g = torch.zeros((4, n + 2), dtype=torch.complex128, device="cuda")
         u = torch.empty_like(f)

@@ -1110,13 +1110,12 @@ struct Solver final : SolverBase {
         return eig && eig_fused && pre_direct && P.n_inner == 1 && L >= 2 && P.outer == HH_OUTER_ORAS;
     }
 
-    // residual b - A u into res and RT, its norm and the device stopping test (ctl)
+    // residual b - A u into res and RT, its norm and the device stopping test (ctl), one
+    // launch; dcounter[0] is its ticket
     void gated_residual(int* ctl) {
-        int nb = 0;
         pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
-        launch_residual_cast<T>(u, bvec, res, RT, geom(0), npart, &nb, stream, ctl);
+        launch_residual_stop<T>(u, bvec, res, RT, geom(0), npart, dnorm, ctl, dcounter, P.tol, stream);
         pend(PC_SPMV);
-        launch_sum_stop(npart, nb, dnorm, ctl, P.tol, stream);
     }
 
     // the norms, the status words and the stop words (dnorm[0..8)) to the host
@@ -1142,6 +1141,7 @@ struct Solver final : SolverBase {
         const int* hctl = (const int*)(h_norm + 6);
         hh_status st = HH_OK;
         zero(ctl, 2 * sizeof(int));
+        zero(dcounter, sizeof(unsigned));   // the residual's ticket
         gated_residual(ctl);
         if (!read_norms(st)) return st;
         double rel_prev = -1.0;

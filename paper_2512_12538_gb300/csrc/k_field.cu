@@ -72,9 +72,18 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
 
 // Global residual y = v - A x in FP64 with per-block partial sums of |y|^2, and the
 // same residual rounded to the leaf precision (yt), the input of the next ORAS step.
+// With stop (the device-tested loop) the last block to finish also adds the partials in
+// block order and takes the stopping test (the same as k_sum_stop), so no second launch
+// is needed: ctl doubles as the gate, stop->ticket is zero between launches.
+struct ResidStop {
+    double* nrm;
+    int* ctl;
+    unsigned* ticket;
+    double tol;
+};
 template <typename T>
 __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restrict__ v, c128* __restrict__ y,
-                                cplx<T>* __restrict__ yt, OpGeom g, double* part, const int* gate) {
+                                cplx<T>* __restrict__ yt, OpGeom g, double* part, const int* gate, ResidStop stop) {
     if (gate && *gate) return;
     const size_t total = (size_t)g.b * g.Sx;
     double acc2 = 0.0;
@@ -95,13 +104,45 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
         acc2 += abs2(out);
     }
     __shared__ double red[32];
+    __shared__ unsigned s_last;
     acc2 = warp_sum(acc2);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
     __syncthreads();
     if (threadIdx.x < 32) {
         double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         s2 = warp_sum(s2);
-        if (threadIdx.x == 0) part[blockIdx.x] = s2;
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = s2;
+            if (stop.ctl) {
+                __threadfence();
+                s_last = atomicAdd(stop.ticket, 1u) == gridDim.x - 1;
+            }
+        }
+    }
+    if (!stop.ctl) return;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block: k_sum's order (thread t adds t, t + 256, ..., then the warp and
+    // block trees), so ||r||^2 is the value launch_sum would give
+    double a = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) a += __ldcg(part + i);
+    a = warp_sum(a);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s2 = warp_sum(s2);
+        if (threadIdx.x == 0) {
+            *stop.ticket = 0u;
+            stop.nrm[0] = s2;
+            stop.ctl[1] += 1;
+            const double b2 = stop.nrm[2];
+            const double rel = b2 > 0 ? sqrt(s2 / b2) : 0.0;
+            if (!isfinite(rel)) stop.ctl[0] = 2;
+            else if (rel < stop.tol) stop.ctl[0] = 1;
+        }
     }
 }
 template <typename T>
@@ -109,10 +150,22 @@ void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
                           cudaStream_t s, const int* gate) {
     const size_t total = (size_t)g.b * g.Sx;
     const int grid = grid_for(total, 256, 152 * 8);
-    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate);
+    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, ResidStop{});
     note_launch();
     if (nblk_out) *nblk_out = grid;
 }
+template <typename T>
+void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, double* nrm,
+                          int* ctl, unsigned* ticket, double tol, cudaStream_t s) {
+    const size_t total = (size_t)g.b * g.Sx;
+    const int grid = grid_for(total, 256, 152 * 8);
+    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, ResidStop{nrm, ctl, ticket, tol});
+    note_launch();
+}
+template void launch_residual_stop<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, double*, int*,
+                                          unsigned*, double, cudaStream_t);
+template void launch_residual_stop<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, double*, int*,
+                                           unsigned*, double, cudaStream_t);
 template void launch_residual_cast<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, int*, cudaStream_t,
                                           const int*);
 template void launch_residual_cast<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, int*,
@@ -207,34 +260,6 @@ void launch_sum(const double* part, int n, double* out, cudaStream_t s) {
     note_launch();
 }
 
-// k_sum's reduction (same order, so the same ||r||^2) followed by the stopping test the
-// host would take: IEEE division and square root in FP64 on both sides give the same
-// decision.
-__global__ void k_sum_stop(const double* part, int n, double* nrm, int* ctl, double tol) {
-    if (*(volatile int*)ctl) return;
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
-    __shared__ double red[32];
-    a = warp_sum(a);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double s2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        s2 = warp_sum(s2);
-        if (threadIdx.x == 0) {
-            nrm[0] = s2;
-            ctl[1] += 1;
-            const double b2 = nrm[2];
-            const double rel = b2 > 0 ? sqrt(s2 / b2) : 0.0;
-            if (!isfinite(rel)) ctl[0] = 2;
-            else if (rel < tol) ctl[0] = 1;
-        }
-    }
-}
-void launch_sum_stop(const double* part, int n, double* nrm, int* ctl, double tol, cudaStream_t s) {
-    k_sum_stop<<<1, 256, 0, s>>>(part, n, nrm, ctl, tol);
-    note_launch();
-}
 
 // --------------------------------------------------------------------------- rhs
 __global__ void k_rhs(const c128* __restrict__ f, const c128* __restrict__ g, c128* __restrict__ b,

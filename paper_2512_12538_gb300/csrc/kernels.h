@@ -42,11 +42,15 @@ void launch_residual_batch(ResidBatch bt, double* part, int part_cap, double* no
 
 // out = sum of n doubles (deterministic single-block reduction)
 void launch_sum(const double* part, int n, double* out, cudaStream_t s);
-// The stopping test of the stationary iteration kept on the device.  Unless ctl[0] is
-// already set: nrm[0] = sum of the n partials (||r||^2, same order as launch_sum),
-// ctl[1] += 1, and with rel = sqrt(nrm[0] / nrm[2]) (0 when nrm[2] <= 0) ctl[0] = 2 if
-// rel is not finite, 1 if rel < tol.  ctl[0] is the gate of the next step's launches.
-void launch_sum_stop(const double* part, int n, double* nrm, int* ctl, double tol, cudaStream_t s);
+// launch_residual_cast with the stopping test of the stationary iteration kept on the
+// device, in the same launch.  Unless ctl[0] is already set (then nothing is done):
+// y, yt and the partials as launch_residual_cast, then nrm[0] = ||y||^2 (launch_sum's
+// order), ctl[1] += 1, and with rel = sqrt(nrm[0] / nrm[2]) (0 when nrm[2] <= 0)
+// ctl[0] = 2 if rel is not finite, 1 if rel < tol.  ctl[0] is the gate of the next
+// step's launches; ticket is a device counter that is zero between launches.
+template <typename T>
+void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, double* nrm,
+                          int* ctl, unsigned* ticket, double tol, cudaStream_t s);
 
 // b = h^2 w_i w_j f + h (w_j gx + w_i gy) for the global problem.
 void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s);

@@ -1,5 +1,5 @@
 """The bench's stopping tolerance reaches relative error 1e-8 on the bench workload, in
-both precision forms, and the tracing hooks the bench relies on work."""
+both precision forms and with a 10x margin, and the tracing hooks the bench relies on work."""
 import numpy as np
 import pytest
 
@@ -29,7 +29,7 @@ def case():
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_bench_tolerance_gives_rel_err_1e8(hh, case, precision):
+def test_bench_tolerance_gives_rel_err_1e8_with_margin(hh, case, precision):
     bench, w, f, g, us = case
     p = hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, w.n_inner, bench.TOL,
                        bench.MAX_ITER, precision, 1, outer=bench.OUTER, restart=bench.RESTART)
@@ -39,7 +39,8 @@ def test_bench_tolerance_gives_rel_err_1e8(hh, case, precision):
         st = hh.hh_solve(h, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), u)
         err = direct.rel_err(u.cpu().numpy(), us)
         print(f"{precision}: iters={st.iters} rel_res={st.rel_res:.2e} err={err:.2e}")
-        assert err <= 1e-8
+        # the metric asks for 1e-8; the bench's tolerance must keep a 10x margin
+        assert err <= 1e-9
     finally:
         hh.hh_destroy(h)
 
