@@ -252,7 +252,7 @@ def run_ours(args, rank, world):
     # FP64 GPU form of the same method on the same workload
     fp64_ms = []
     fp64_iters = []
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(max(3, args.steps // 2)):
         ms, st, _ = one("fp64")
         fp64_ms.append(ms)
         fp64_iters.append(st.iters)
@@ -294,7 +294,8 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
         "iterations": {"mixed": statistics.median(iters), "fp64": statistics.median(fp64_iters)},
         "fp64_form": {"value": world * len(fp64_ms) / (sum(fp64_ms) / 1e3), "unit": UNIT,
-                      "ms_per_step": statistics.mean(fp64_ms)},
+                      "ms_per_step": statistics.mean(fp64_ms), "median_ms_per_step": statistics.median(fp64_ms),
+                      "step_ms": [round(x, 3) for x in fp64_ms]},
         "mixed_over_fp64": (value / world) / (len(fp64_ms) / (sum(fp64_ms) / 1e3)),
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
         "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
