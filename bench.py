@@ -275,7 +275,7 @@ def run_ours(args, rank, world):
     e2e = {"value": world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": 16 * (N + 4 * w.S), "d2h_bytes_per_step": 16 * N}
 
-    batch = run_batch_form(hh, torch) if rank == 0 else None
+    batch = run_batch_form(hh, torch) if rank == 0 and args.batch_form == "on" else None
 
     pk, pk_kind = peaks()
     roof = roofline(w, prof_total, prof_all, dominant, pk, pk_kind)
@@ -508,6 +508,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="single", choices=["single", "serve"],
                     help="serve: the serving-form stream instead of the headline workload")
+    ap.add_argument("--batch-form", default="on", choices=["on", "off"],
+                    help="also measure the batching form (512 problems) after the headline")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: length of the arrival stream")
     args = ap.parse_args()
