@@ -1145,20 +1145,23 @@ struct Solver final : SolverBase {
         gated_residual(ctl);
         if (!read_norms(st)) return st;
         double rel_prev = -1.0;
-        int it_prev = 0, chunk = 8;
+        int it_prev = 0, chunks = 0;
         for (;;) {
             rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
             if (hctl[0] == 2 || !std::isfinite(rel)) return HH_ENOCONV;
             if (hctl[0] == 1) return HH_OK;
             if (it >= P.max_iter) return HH_ENOCONV;
-            // steps still needed at the observed contraction rate, and two to spare
-            if (rel_prev > 0 && it > it_prev && rel < rel_prev && rel > 0) {
+            // Two chunks of 8 first: the residual of the first steps may grow before it
+            // settles into its asymptotic rate, so a rate measured from step 0 overshoots.
+            // Then the steps still needed at the rate of the last chunk, none to spare (a
+            // short estimate costs one more synchronisation, a long one gated steps).
+            int chunk = 8;
+            if (chunks >= 2 && it > it_prev && rel < rel_prev && rel > 0) {
                 const double rho = std::pow(rel / rel_prev, 1.0 / (it - it_prev));
                 const double need = std::log(P.tol / rel) / std::log(rho);
-                chunk = need < 62.0 ? (int)std::ceil(need) + 2 : 64;
-            } else if (rel_prev > 0) {
-                chunk = 8;
+                chunk = need < 64.0 ? std::max(1, (int)std::ceil(need)) : 64;
             }
+            ++chunks;
             rel_prev = rel;
             it_prev = it;
             const int n = std::max(1, std::min(chunk, P.max_iter - it));
