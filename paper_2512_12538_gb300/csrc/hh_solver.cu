@@ -320,7 +320,7 @@ struct Solver final : SolverBase {
     bool eig = false;
     int eig_fused = 0;          // cluster size of the one-launch single-vector sweep (0: off)
     std::vector<CT*> EV, EXI, EFh;
-    std::vector<c128*> ELAM, EWK;
+    std::vector<c128*> ELAM;
     EigTask *d_etasks_view = nullptr, *d_etasks_own = nullptr, *d_etask_one = nullptr, *d_etasks_pre = nullptr;
     // flexible GMRES
     int mk = 0;                                   // restart length
@@ -398,7 +398,7 @@ struct Solver final : SolverBase {
         AinvT.assign(nn, nullptr);
         lam.assign(nn, nullptr); ldx.assign(nn, 0);
         EV.assign(nn, nullptr); EXI.assign(nn, nullptr); EFh.assign(nn, nullptr);
-        ELAM.assign(nn, nullptr); EWK.assign(nn, nullptr);
+        ELAM.assign(nn, nullptr);
         const size_t N = (size_t)Sy * Sx;
         u = a.take<c128>(N); ut = a.take<c128>(N); bvec = a.take<c128>(N); res = a.take<c128>(N);
         gbuf = a.take<c128>(4 * (size_t)S);
@@ -428,7 +428,6 @@ struct Solver final : SolverBase {
                 EXI[id] = a.take<CT>((size_t)Sx * b);
                 ELAM[id] = a.take<c128>(b);
                 EFh[id] = a.take<CT>(np * nmax);
-                EWK[id] = a.take<c128>(eig_work_elems(b));
             } else {
                 ldx[id] = leaf_ldx(nd.b(), (int)sizeof(CT));
                 X[id] = a.take<CT>(Sx == 1 ? (size_t)nd.b() : (size_t)Sx * nd.b() * ldx[id]);
@@ -531,7 +530,6 @@ struct Solver final : SolverBase {
         k.F = F;
         k.Fh = EFh[id];
         k.W = Wout;
-        k.work = EWK[id];
         k.b = nodes[id].b();
         k.Sx = Sx;
         k.w0 = 0;

@@ -166,28 +166,26 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
     for (int a = 0; a < b; ++a) x[a] = cdiv_(x[a], nr);
 }
 
-// Set-up of one leaf per CTA, in the precision of the leaf path (FP32 for the mixed
-// form, FP64 for the FP64 form).
+// Set-up of the leaves, in the precision of the leaf path (FP32 for the mixed form, FP64
+// for the FP64 form), in two launches: the eigenvalues (one CTA per leaf) and then the
+// eigenvectors and recursions (k_eig_modes).
 // Eigenvalues: Aberth-Ehrlich simultaneous iteration, one thread per eigenvalue,
 //   z_j <- z_j - w_j / (1 - w_j sum_{k != j} 1/(z_j - z_k)),  w_j = p(z_j)/p'(z_j),
 // started from the closed-form spectrum of the real part, 2 - 2cos(j pi/(b-1)) - (kh)^2
 // (the halved-end second difference has the cosine eigenvectors), shifted by the
 // first-order effect of the two impedance corners.
 template <typename T>
-__global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ tasks, int Sx, double kh,
-                                                    int* err) {
+__global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ tasks, double kh, int* err) {
     using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.x];
     const int b = tk.b;
     __shared__ C d[EIG_BMAX], e[EIG_BMAX], e2[EIG_BMAX], z[EIG_BMAX];
-    __shared__ T rw[EIG_BMAX];     // 1 / sqrt(w_a)
     for (int a = threadIdx.x; a < b; a += blockDim.x) {
         C dd, ee;
         band_tridiag<T>(b, kh, a, dd, ee);
         d[a] = dd;
         e[a] = ee;
         e2[a] = ee * ee;
-        rw[a] = (T)(1.0 / sqrt(wrow(a, b)));
         const double mu = 2.0 - 2.0 * cos(M_PI * a / (b - 1)) - kh * kh;
         z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 4.0) / (b - 1))};
     }
@@ -211,29 +209,64 @@ __global__ void __launch_bounds__(256) k_eig_factor(const EigTask* __restrict__ 
         if (__syncthreads_and(small) && it >= 3) break;
     }
     c128* lam = (c128*)tk.lam;
-    C* V = (C*)tk.V;
-    C* xi = (C*)tk.xi;
     for (int m = threadIdx.x; m < b; m += blockDim.x) {
         const C lm = z[m];
         if (!(isfinite(lm.re) && isfinite(lm.im))) atomicExch(err, DEV_BREAKDOWN);
         lam[m] = cvt<double>(lm);
-        C* ws = (C*)tk.work + (size_t)m * 6 * b;
-        C* q = ws + 5 * b;
+    }
+}
+
+// Eigenvectors and the scalar recursions, one warp per mode m of one leaf (grid: modes
+// in groups of EM_WARPS, leaves): lane 0 runs the inverse iteration with its workspace
+// in shared memory (the chains of dependent accesses stay on chip), the warp writes the
+// W-orthonormal column V[.][m], then lane 0 runs the chain xi_{m,i} along the columns.
+static constexpr int EM_WARPS = 4;
+template <typename T>
+__global__ void __launch_bounds__(32 * EM_WARPS) k_eig_modes(const EigTask* __restrict__ tasks, int Sx, double kh,
+                                                            int* err) {
+    using C = cplx<T>;
+    const EigTask tk = tasks[blockIdx.y];
+    const int b = tk.b;
+    extern __shared__ __align__(16) unsigned char emsm[];
+    C* dd = (C*)emsm;                          // [b] tridiagonal of the band
+    C* ee = dd + b;                            // [b]
+    C* wsall = ee + b;                         // [EM_WARPS][6 b] per-warp workspace
+    T* rw = (T*)(wsall + (size_t)EM_WARPS * 6 * b);   // [b] 1 / sqrt(w_a)
+    for (int a = threadIdx.x; a < b; a += blockDim.x) {
+        C d1, e1;
+        band_tridiag<T>(b, kh, a, d1, e1);
+        dd[a] = d1;
+        ee[a] = e1;
+        rw[a] = (T)(1.0 / sqrt(wrow(a, b)));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x * EM_WARPS + warp;
+    if (m >= b) return;
+    C* ws = wsall + (size_t)warp * 6 * b;
+    C* q = ws + 5 * b;
+    const c128 l64 = ((const c128*)tk.lam)[m];
+    const C lm = {(T)l64.re, (T)l64.im};
+    if (lane == 0) {
         const C mu = lm + C{(T)(8 * Eps<T>::v) * fmax(cabs_(lm), (T)1), (T)0};
-        inverse_iteration<T>(b, d, e, mu, q, ws);
-        for (int a = 0; a < b; ++a) V[a * b + m] = rw[a] * q[a];
-        // scalar Schur recursions along the columns (in T: the FP64 pipe is slow here)
-        const T khT = (T)kh;
-        C prev = {0, 0};
-        for (int i = 0; i < Sx; ++i) {
-            const bool xb = (i == 0 || i == Sx - 1);
-            const T wi = (Sx > 1 && xb) ? (T)0.5 : (T)1;
-            const C delta = C{xb ? (T)1 : (T)2, xb ? -khT : (T)0} + wi * lm;
-            const C sdel = delta - prev;
-            if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
-            prev = cdiv_(C{1, 0}, sdel);
-            xi[(size_t)m * Sx + i] = prev;
-        }
+        inverse_iteration<T>(b, dd, ee, mu, q, ws);
+    }
+    __syncwarp();
+    C* V = (C*)tk.V;
+    for (int a = lane; a < b; a += 32) V[a * b + m] = rw[a] * q[a];
+    if (lane != 0) return;
+    // scalar Schur recursions along the columns (in T: the FP64 pipe is slow here)
+    C* xi = (C*)tk.xi;
+    const T khT = (T)kh;
+    C prev = {0, 0};
+    for (int i = 0; i < Sx; ++i) {
+        const bool xb = (i == 0 || i == Sx - 1);
+        const T wi = (Sx > 1 && xb) ? (T)0.5 : (T)1;
+        const C delta = C{xb ? (T)1 : (T)2, xb ? -khT : (T)0} + wi * lm;
+        const C sdel = delta - prev;
+        if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
+        prev = cdiv_(C{1, 0}, sdel);
+        xi[(size_t)m * Sx + i] = prev;
     }
 }
 
@@ -511,7 +544,15 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
         cudaMemcpyAsync(err, &one, sizeof(int), cudaMemcpyHostToDevice, s);
         return;
     }
-    k_eig_factor<T><<<ntasks, 160, 0, s>>>(d_tasks, Sx, kh, err);
+    k_eig_roots<T><<<ntasks, 160, 0, s>>>(d_tasks, kh, err);
+    note_launch();
+    const size_t sm = sizeof(cplx<T>) * (size_t)b_max * (2 + 6 * EM_WARPS) + sizeof(T) * (size_t)b_max;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_eig_modes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    k_eig_modes<T><<<dim3((b_max + EM_WARPS - 1) / EM_WARPS, ntasks), 32 * EM_WARPS, sm, s>>>(d_tasks, Sx, kh, err);
     note_launch();
 }
 
@@ -805,7 +846,6 @@ void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_ma
 }
 
 int eig_bmax() { return GT_ROWS * GT_RPT < EIG_BMAX ? GT_ROWS * GT_RPT : EIG_BMAX; }
-size_t eig_work_elems(int b) { return (size_t)b * 6 * b; }
 
 template void launch_eig_factor<float>(const EigTask*, int, int, int, double, int*, cudaStream_t);
 template void launch_eig_factor<double>(const EigTask*, int, int, int, double, int*, cudaStream_t);

@@ -199,7 +199,6 @@ struct EigTask {
     const void* F;    // right-hand sides [b][Sx][nrhs]
     void* Fh;         // transformed right-hand sides / solutions [b][Sx][nrhs]
     void* W;          // solutions [b][Sx][nrhs]
-    void* work;       // set-up workspace, eig_work_elems(b) complex128 (used as complex<T>)
     int b;
     int Sx;           // columns of the leaf's problem (tasks of several problems may share a launch)
     int w0, w1;       // the one-launch sweep writes local rows [w0, w1) only, row a to
@@ -228,6 +227,5 @@ template <typename T>
 void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
                             cudaStream_t s);
 int eig_bmax();
-size_t eig_work_elems(int b);
 
 }  // namespace hh
