@@ -45,6 +45,37 @@ void note_launch() {
     ++t_launches;
 }
 
+// ------------------------------------------------------------ pinned host blocks
+// The per-handle host copies of norms and dot products live in 8 KiB pinned blocks kept
+// in a process-wide free list: page-locking memory per handle (and releasing it, which
+// synchronises the device) cost more than a whole set-up's kernels on small problems.
+// Blocks are returned only once nothing can still copy into them, and are held until
+// the process exits.
+static constexpr size_t PIN_BLOCK = 8192;
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+static void* pinned_get() {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free.empty()) {
+            void* p = g_pin_free.back();
+            g_pin_free.pop_back();
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, PIN_BLOCK, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+static void pinned_put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 // Kernel categories timed by the optional event profiler (hh_profile_*).
 enum ProfCat {
     PC_FACTOR = 0,   // leaf factorisation (eigen set-up or explicit block inverses)
@@ -345,6 +376,7 @@ struct Solver final : SolverBase {
     Graph graphs[3];
     cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
     void** d_ptrs = nullptr;
+    void* h_pin = nullptr;      // pinned block holding h_norm and h_dots
     double* h_norm = nullptr;   // pinned host
     int b_max = 0;
     cudaError_t cerr = cudaSuccess;
@@ -357,10 +389,9 @@ struct Solver final : SolverBase {
             runs_release(g, 0);
         }
         if (cap_stream) cudaStreamDestroy(cap_stream);
-        if (h_norm) cudaFreeHost(h_norm);
-        if (h_dots) cudaFreeHost(h_dots);
         if (block) dev_free(block, footprint, stream, hook);
         if (stream) cudaStreamSynchronize(stream);
+        pinned_put(h_pin);   // nothing copies into it any more
     }
 
     OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh}; }
@@ -892,8 +923,12 @@ struct Solver final : SolverBase {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (!ok) return st;
-        ck(cudaMallocHost(&h_norm, 8 * sizeof(double)), cerr);
-        if (mk > 0) ck(cudaMallocHost(&h_dots, 4 * 80 * sizeof(c128)), cerr);
+        // one pinned block: the norms (8 doubles) at 0, the dot products (320 complex) at 256
+        static_assert(256 + 4 * 80 * sizeof(c128) <= PIN_BLOCK, "pinned block too small");
+        h_pin = pinned_get();
+        if (!h_pin) return HH_ENOMEM;
+        h_norm = (double*)h_pin;
+        if (mk > 0) h_dots = (c128*)((char*)h_pin + 256);
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
 

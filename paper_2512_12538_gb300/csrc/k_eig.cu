@@ -22,6 +22,9 @@
 // iteration on its characteristic polynomial, eigenvectors by inverse iteration with a
 // pivoted tridiagonal LU, normalised q^T q = 1 (no conjugation).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cooperative_groups.h>
 
@@ -809,8 +812,26 @@ static cudaLaunchConfig_t fs_config(int cl, int ntasks, size_t sm, cudaStream_t 
     return cfg;
 }
 
+// The answer depends only on (device, b_max, Sx, T): cached, so that a set-up does not
+// pay an occupancy query.
+template <typename T>
+int eig_sweep_fused_ready_query(int b_max, int Sx);
 template <typename T>
 int eig_sweep_fused_ready(int b_max, int Sx) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, int> memo;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, b_max, Sx);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    const int cl = eig_sweep_fused_ready_query<T>(b_max, Sx);
+    memo[key] = cl;
+    return cl;
+}
+template <typename T>
+int eig_sweep_fused_ready_query(int b_max, int Sx) {
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_SMEM_MAX) !=
