@@ -108,7 +108,9 @@ typedef struct hh_handle hh_handle;
 
 /* Device allocator hook.  alloc(bytes, stream, ctx) returns device memory usable on
  * `stream` or NULL; free_(ptr, bytes, stream, ctx) returns it.  Passing alloc = NULL
- * restores the default.  Affects handles created afterwards. */
+ * restores the default: a stream-ordered memory pool of the library's own per device,
+ * which keeps memory freed by hh_destroy for later handles (until the process exits).
+ * Affects handles created afterwards. */
 hh_status hh_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
                            void (*free_)(void* ptr, size_t bytes, void* stream, void* ctx),
                            void* ctx);

@@ -99,10 +99,43 @@ struct AllocHook {
 };
 static AllocHook g_alloc;
 
+// Without a hook, handles draw from a stream-ordered memory pool of the library's own,
+// one per device, that keeps freed memory for later set-ups. (The device's default pool
+// returns freed memory to the driver at every synchronisation, so each set-up mapped its
+// block afresh.) The memory stays with the pool until the process exits.
+static cudaMemPool_t lib_pool(int dev) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pools[dev] = pool;
+    return pool;
+}
 static void* dev_alloc(size_t bytes, cudaStream_t s, const AllocHook& a) {
     if (a.alloc) return a.alloc(bytes, (void*)s, a.ctx);
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    const cudaMemPool_t pool = lib_pool(dev);
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
     return p;
 }
 static void dev_free(void* p, size_t bytes, cudaStream_t s, const AllocHook& a) {
