@@ -172,7 +172,6 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    hh.use_torch_allocator()
     stream = torch.cuda.current_stream()
     w, f, g = workload_inputs()
     fd = torch.from_numpy(f).cuda()

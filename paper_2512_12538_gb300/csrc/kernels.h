@@ -85,10 +85,6 @@ void launch_coarse_update(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t 
 template <typename T>
 void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size_t ldc, int coff, size_t dst0,
                         size_t n, cudaStream_t s);
-// y = Minv C^H (v - A~ w) for one column (w may be null); counter: a zeroed device word
-template <typename TC, typename TV, typename TW>
-void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w, OpGeom g, int p, c128* partial,
-                         unsigned* counter, const c128* Minv, c128* y, cudaStream_t s);
 // One-column coarse corrections of up to CB_MAX_JOBS nodes in one cooperative launch
 // (k_coarse.cu).  Per job: basis C [p][N] (TC), right-hand side v (TV), iterate w_in
 // (TW, may be null), output out (TO) for the rows [r0, r1) of the node:
@@ -97,6 +93,7 @@ void launch_coarse_proj1(const cplx<TC>* C, const cplx<TV>* v, const cplx<TW>* w
 // partial: (total blocks) x p scratch entries of TC; bar: two zeroed words (grid
 // barrier); err: the device status word (DEV_TIMEOUT if the barrier wait gives up).
 constexpr int CB_MAX_JOBS = 16;
+constexpr int CB_COLS = 16;   // basis columns one block of k_coarse_batch projects on (p <= 64)
 struct CoarseJob {
     const void* C;
     const void* v;
@@ -110,6 +107,8 @@ struct CoarseJob {
     int split;             // >= 0: columns [0, p/2) vanish on rows >= split, [p/2, p) on rows
                            // below (each child's basis lives on its owned rows); -1: dense
     unsigned blk0, nblk;   // set by the launcher
+    int ngrp;              // set by the launcher: column groups per half (p/2 / CB_COLS, rounded up)
+    unsigned sb[5];        // set by the launcher: blocks of set s are [sb[s], sb[s + 1])
 };
 struct CoarseBatch {
     CoarseJob job[CB_MAX_JOBS];
@@ -118,9 +117,7 @@ struct CoarseBatch {
 };
 template <typename TC, typename TV, typename TW, typename TO>
 void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s);
-// W += C y (one column) / W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
-template <typename TC, typename TW>
-void launch_coarse_upd1(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, cudaStream_t s);
+// W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
 template <typename TC, typename TW>
 void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s);
 // tiled inner products with a column-major A (p x N)

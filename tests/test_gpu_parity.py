@@ -304,3 +304,28 @@ def test_noconvergence_reports_last_iterate(hh):
         assert np.isfinite(host(u)).all() and np.abs(host(u)).max() > 0
     finally:
         hh.hh_destroy(h)
+
+
+def test_torch_allocator_hook_and_library_pool_agree(hh):
+    """Handles whose memory comes from torch's caching allocator (the hook) and from the
+    library's own pool (the default) solve the same problem to the same bits."""
+    P = Problem(2, 45, 12.0)
+    f = point_source_rhs(45, 4)
+    g = random_complex((4, P.S), 5)
+    us = direct.solve(P, f, g)
+    p = hh.make_params(2, 45, 12.0, 2, 2, 6, 4, 1, 1e-12, 300, "mixed", 2)
+    out = []
+    for hook in (True, False):
+        if hook:
+            hh.use_torch_allocator()
+        try:
+            h, _ = hh.hh_setup(p)
+            u = torch.empty((P.S, P.S), dtype=torch.complex128, device="cuda")
+            st = hh.hh_solve(h, dev(f), dev(g), u)
+            hh.hh_destroy(h)
+            out.append((st.iters, host(u)))
+        finally:
+            hh.hh_set_allocator(None, None, None)
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+    assert rel(out[1][1], us) < 1e-8
