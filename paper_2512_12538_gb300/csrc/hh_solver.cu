@@ -365,6 +365,7 @@ struct Solver final : SolverBase {
     std::vector<int> ldx;
     c128 *u = nullptr, *ut = nullptr, *bvec = nullptr, *res = nullptr, *gbuf = nullptr;
     CT* RT = nullptr;
+    CT* dlt = nullptr;          // the level-1 update of the current step (leaf precision)
     c128* partial = nullptr;
     double *npart = nullptr, *dnorm = nullptr;
     int* derr = nullptr;
@@ -465,6 +466,7 @@ struct Solver final : SolverBase {
         ELAM.assign(nn, nullptr);
         const size_t N = (size_t)Sy * Sx;
         u = a.take<c128>(N); ut = a.take<c128>(N); bvec = a.take<c128>(N); res = a.take<c128>(N);
+        dlt = a.take<CT>(N);
         gbuf = a.take<c128>(4 * (size_t)S);
         RT = a.take<CT>(N * nmax);
         for (auto& nd : nodes) {
@@ -782,6 +784,8 @@ struct Solver final : SolverBase {
                 j.acc_out = l == 1 && root_acc;
                 j.add_w = 1;
                 j.split = split_row(p);
+                // level 1 also keeps its update delta_1 for the root's correction
+                j.dout = l == 1 ? (void*)(dlt + row_off(0, nd.own_a, 1)) : nullptr;
                 by += (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT);
                 fl += 2.0 * 8.0 * 2 * r * pts(p);
             }
@@ -992,10 +996,23 @@ struct Solver final : SolverBase {
                                        (size_t)(cn.own_b - cn.own_a) * Sx, base != nullptr, false, stream);
             }
         }
-        pjoin(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
-        CoarseBatch rb = one_job(0, rhs, out, out, true);
-        rb.gate = gate;
-        launch_coarse_batch<T, double, double, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
+        if (direct) {
+            // The root corrects on the residual after the level-1 update, rhs - A(base +
+            // delta_1) = res - A delta_1: the step's input residual (RT, in the leaf
+            // precision) less A applied to the update the level-1 kernel kept in dlt.
+            // Both terms are in the leaf precision, like the correction computed from them;
+            // the FP64 residual of the new iterate is formed afterwards as before.
+            pjoin(PC_COARSE, (double)N * (2.0 * r + 3.0) * sizeof(CT) + (double)N * 2.0 * sizeof(c128),
+                  2.0 * 8.0 * 2 * r * N);
+            CoarseBatch rb = one_job(0, RT, dlt, out, true);
+            rb.gate = gate;
+            launch_coarse_batch<T, T, T, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
+        } else {
+            pjoin(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
+            CoarseBatch rb = one_job(0, rhs, out, out, true);
+            rb.gate = gate;
+            launch_coarse_batch<T, double, double, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
+        }
         pend(PC_COARSE);
         step_gate = nullptr;
     }

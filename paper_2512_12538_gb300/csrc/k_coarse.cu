@@ -88,8 +88,8 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
 //   phase 3: for the points whose rows lie in [r0, r1):
 //            out[pt - r0 Sx] = (acc_out ? out : 0) + (add_w ? w_in[pt] : 0) + (C y)[pt]
 //            (in place: out = w_in, acc_out; straight into the parent's solution: the
-//            owned rows, add_w).  The barrier separates every read of w_in from the
-//            writes.
+//            owned rows, add_w), and the added value alone into dout when given.  The
+//            barrier separates every read of w_in from the writes.
 template <typename TC, typename TV, typename TW, typename TO>
 __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(CoarseBatch bt, int p, cplx<TC>* partial, unsigned* bar,
                                                       int* err) {
@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
         for (; j < je; ++j) cfma(a, C[(size_t)j * N + pt], s_y[j]);
         cplx<TO> val = cvt<TO>(a);
         if (J.add_w) val = val + cvt<TO>(w_in[pt]);
+        if (J.dout) ((cplx<TC>*)J.dout)[pt - lo] = J.add_w ? a + cvt<TC>(w_in[pt]) : a;
         cplx<TO>& o = out[pt - lo];
         o = J.acc_out ? o + val : val;
     }

@@ -107,6 +107,8 @@ struct CoarseJob {
     int split;             // >= 0: columns [0, p/2) vanish on rows >= split, [p/2, p) on rows
                            // below (each child's basis lives on its owned rows); -1: dense
     unsigned blk0, nblk;   // set by the launcher
+    void* dout;            // may be null: also receives the correction added to out (without
+                           // out's old value), in the basis precision, at out's index
     int ngrp;              // set by the launcher: column groups per half (p/2 / CB_COLS, rounded up)
     unsigned sb[5];        // set by the launcher: blocks of set s are [sb[s], sb[s + 1])
 };
