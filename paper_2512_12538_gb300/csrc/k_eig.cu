@@ -124,9 +124,9 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
     }
     for (int j = 0; j < b - 1; ++j) {
         const C esub = ee[j];   // sub-diagonal entry (j+1, j)
-        if (cabs_(dg[j]) >= cabs_(esub)) {
+        if (abs2(dg[j]) >= abs2(esub)) {
             sw[j] = 0;
-            const C fact = cabs_(dg[j]) > (R)0 ? cdiv_(esub, dg[j]) : C{0, 0};
+            const C fact = abs2(dg[j]) > (R)0 ? cdiv_(esub, dg[j]) : C{0, 0};
             lo[j] = fact;
             dg[j + 1] = dg[j + 1] - fact * up[j];
         } else {
@@ -143,8 +143,12 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
             }
         }
     }
-    for (int a = 0; a < b; ++a)
-        if (cabs_(dg[a]) < Eps<R>::tiny * Eps<R>::v) dg[a] = {Eps<R>::tiny * Eps<R>::v, 0};
+    // the pivots, guarded, then replaced by their reciprocals (the three solves multiply)
+    for (int a = 0; a < b; ++a) {
+        const R g0 = Eps<R>::tiny * Eps<R>::v;
+        const C dv = abs2(dg[a]) < g0 * g0 ? C{g0, 0} : dg[a];
+        dg[a] = cdiv_(C{1, 0}, dv);
+    }
     for (int it = 0; it < 3; ++it) {
         for (int j = 0; j < b - 1; ++j) {
             if (sw[j] == (R)0) {
@@ -155,12 +159,12 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
                 x[j + 1] = t - lo[j] * x[j];
             }
         }
-        x[b - 1] = cdiv_(x[b - 1], dg[b - 1]);
-        if (b > 1) x[b - 2] = cdiv_(x[b - 2] - up[b - 2] * x[b - 1], dg[b - 2]);
-        for (int j = b - 3; j >= 0; --j) x[j] = cdiv_(x[j] - up[j] * x[j + 1] - up2[j] * x[j + 2], dg[j]);
-        R mx = 0;
-        for (int a = 0; a < b; ++a) mx = fmax(mx, cabs_(x[a]));
-        const R inv = mx > (R)0 ? (R)1 / mx : (R)1;
+        x[b - 1] = x[b - 1] * dg[b - 1];
+        if (b > 1) x[b - 2] = (x[b - 2] - up[b - 2] * x[b - 1]) * dg[b - 2];
+        for (int j = b - 3; j >= 0; --j) x[j] = (x[j] - up[j] * x[j + 1] - up2[j] * x[j + 2]) * dg[j];
+        R mx2 = 0;
+        for (int a = 0; a < b; ++a) mx2 = fmax(mx2, abs2(x[a]));
+        const R inv = mx2 > (R)0 ? (R)1 / sqrt(mx2) : (R)1;
         for (int a = 0; a < b; ++a) x[a] = inv * x[a];
     }
     C qq = {0, 0};
@@ -193,6 +197,11 @@ __global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ t
         z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 4.0) / (b - 1))};
     }
     __syncthreads();
+    // A root is done when its correction is below 64 eps |z|, or when, already below
+    // 4096 eps |z|, it no longer halves from one sweep to the next: the correction then
+    // measures rounding noise of the recurrences in T, which the strict bound may never
+    // pass.  The iteration converges cubically, so this ends it in a few sweeps.
+    T dz_prev2 = (T)INFINITY;
     for (int it = 0; it < 48; ++it) {
         C zn = {0, 0};
         bool small = true;
@@ -205,7 +214,11 @@ __global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ t
                 if (k != j) s = s + crcp_(zj - z[k]);
             const C dz = cdiv_(w, C{1, 0} - w * s);
             zn = zj - dz;
-            small = cabs_(dz) <= (T)64 * Eps<T>::v * fmax(cabs_(zj), (T)1);
+            const T sc = fmax(abs2(zj), (T)1);
+            const T dz2 = abs2(dz);
+            const T tight = (T)64 * Eps<T>::v, loose = (T)4096 * Eps<T>::v;
+            small = dz2 <= tight * tight * sc || (it >= 3 && dz2 <= loose * loose * sc && dz2 > (T)0.25 * dz_prev2);
+            dz_prev2 = dz2;
         }
         __syncthreads();
         if (threadIdx.x < b) z[threadIdx.x] = zn;
@@ -268,7 +281,7 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_eig_modes(const EigTask* __re
         const C delta = C{xb ? (T)1 : (T)2, xb ? -khT : (T)0} + wi * lm;
         const C sdel = delta - prev;
         if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
-        prev = cdiv_(C{1, 0}, sdel);
+        prev = crcp_(sdel);   // |sdel| is of order one here: no scaling needed
         xi[(size_t)m * Sx + i] = prev;
     }
 }
