@@ -13,6 +13,7 @@ namespace hh {
 static constexpr int IP_TILE = 32;
 static constexpr int IP_THREADS = 256;
 static constexpr int IP_MAXOUT = 16;   // outputs per thread when p*q >= IP_THREADS
+static constexpr int GAL_FLUSH = 4;     // Galerkin tiles summed in FP32 before the FP64 add
 
 // Accumulate conj(As[n][i]) * Bs[n][j] over a tile of `rows` rows held in shared memory.
 // Rows i outside [ilo, ihi) contribute nothing for this tile (ihi = 0: no restriction).
@@ -21,8 +22,12 @@ __device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cp
                                                    int split, cplx<ACC>* acc, int ilo, int ihi) {
     const int nout = p * q;
     if (split == 1) {
-        int k = 0;
-        for (int o = threadIdx.x; o < nout; o += IP_THREADS, ++k) {
+        // output o = threadIdx.x + k IP_THREADS; k is a compile-time index, so acc stays
+        // in registers
+#pragma unroll
+        for (int k = 0; k < IP_MAXOUT; ++k) {
+            const int o = threadIdx.x + k * IP_THREADS;
+            if (o >= nout) continue;
             const int i = o / q, j = o % q;
             if (ihi > 0 && (i < ilo || i >= ihi)) continue;
             cplx<ACC> a = acc[k];
@@ -46,8 +51,11 @@ __device__ __forceinline__ void ip_store_partial(cplx<ACC>* acc, int p, int q, i
                                                  c128* out) {
     const int nout = p * q;
     if (split == 1) {
-        int k = 0;
-        for (int o = threadIdx.x; o < nout; o += IP_THREADS, ++k) out[o] = cvt<double>(acc[k]);
+#pragma unroll
+        for (int k = 0; k < IP_MAXOUT; ++k) {
+            const int o = threadIdx.x + k * IP_THREADS;
+            if (o < nout) out[o] = cvt<double>(acc[k]);
+        }
     } else {
         const int s = threadIdx.x / nout, o = threadIdx.x % nout;
         if (s < split) red[s * nout + o] = acc[0];
@@ -282,9 +290,10 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 // ------------------------------------------------------------------- Galerkin
 // partial[blk][a][l] = sum over the block's points of conj(C[pt][a]) * (A~ C)[pt][l].
 // The products and the stencil run in the basis precision T: FP64 for the FP64 form;
-// FP32 for the complex64 form, whose basis is itself rounded to FP32 (each 32-point
-// tile is summed in FP32 and added to FP64 accumulators, so the FP32 rounding stays at
-// the level of one tile's sum; FP64 on this GPU runs at 1/64 of the FP32 rate).
+// FP32 for the complex64 form, whose basis is itself rounded to FP32 (the products of
+// GAL_FLUSH 32-point tiles are summed in FP32, then added to FP64 accumulators, so the
+// FP32 rounding stays at the level of 128 points' sum; FP64 on this GPU runs at 1/64
+// of the FP32 rate, so only the outputs a thread owns are flushed).
 template <typename T>
 __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* __restrict__ C, OpGeom g, int p,
                                                                  int split_row, c128* partial) {
@@ -297,6 +306,10 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
     c128 acc[IP_MAXOUT];
     for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = {0.0, 0.0};
+    CT tacc[IP_MAXOUT];
+    for (int k = 0; k < IP_MAXOUT; ++k) tacc[k] = {0, 0};
+    const int nk = split > 1 ? 1 : (nout + IP_THREADS - 1) / IP_THREADS;   // outputs owned
+    int ntile = 0;
     const size_t N = (size_t)g.b * g.Sx;
     const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
     const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
@@ -332,10 +345,16 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
         if (sizeof(T) == sizeof(double)) {
             ip_tile_accumulate<double>((const c128*)As, (const c128*)Bs, rows, p, p, split, acc, ilo, ihi);
         } else {
-            CT tacc[IP_MAXOUT];
-            for (int k = 0; k < IP_MAXOUT; ++k) tacc[k] = {0, 0};
             ip_tile_accumulate<T>(As, Bs, rows, p, p, split, tacc, ilo, ihi);
-            for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = acc[k] + cvt<double>(tacc[k]);
+            if (++ntile == GAL_FLUSH || t0 + IP_TILE >= n1) {
+#pragma unroll
+                for (int k = 0; k < IP_MAXOUT; ++k)
+                    if (k < nk) {
+                        acc[k] = acc[k] + cvt<double>(tacc[k]);
+                        tacc[k] = {0, 0};
+                    }
+                ntile = 0;
+            }
         }
         __syncthreads();
     }
