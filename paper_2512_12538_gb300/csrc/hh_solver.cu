@@ -366,6 +366,8 @@ struct Solver final : SolverBase {
     c128 *u = nullptr, *ut = nullptr, *bvec = nullptr, *res = nullptr, *gbuf = nullptr;
     CT* RT = nullptr;
     CT* dlt = nullptr;          // the level-1 update of the current step (leaf precision)
+    CT* AC0 = nullptr;          // A~_0 C_0: the root's operator on its basis (column-major)
+    CT* RP = nullptr;           // r' of the current step (the root's input residual)
     c128* partial = nullptr;
     double *npart = nullptr, *dnorm = nullptr;
     int* derr = nullptr;
@@ -467,6 +469,10 @@ struct Solver final : SolverBase {
         const size_t N = (size_t)Sy * Sx;
         u = a.take<c128>(N); ut = a.take<c128>(N); bvec = a.take<c128>(N); res = a.take<c128>(N);
         dlt = a.take<CT>(N);
+        if (recur_possible()) {
+            AC0 = a.take<CT>(N * 2 * (size_t)r);
+            RP = a.take<CT>(N);
+        }
         gbuf = a.take<c128>(4 * (size_t)S);
         RT = a.take<CT>(N * nmax);
         for (auto& nd : nodes) {
@@ -504,7 +510,9 @@ struct Solver final : SolverBase {
         cur_in[0] = RT;
         partial = a.take<c128>((size_t)MAX_PART_BLOCKS * 64 * 64);
         npart = a.take<double>(2048);
-        dnorm = a.take<double>(8);          // [0..4) norms, then the device status words
+        // [0] ||r||^2 (FP64 residual), [1] ||r||^2 (recursive residual), [2..4) ||b||^2,
+        // [4..6) the device status words, [6..10) the device-tested loop's control words
+        dnorm = a.take<double>(10);
         derr = (int*)(dnorm + 4);
         dcounter = a.take<unsigned>(4);
         const int nleaf = 1 << L;
@@ -950,6 +958,7 @@ struct Solver final : SolverBase {
         pend(PC_FACTOR);
         for (int l = L; l >= 1; --l) sketch_level(l);
         upload_pre_tasks();
+        if (device_test_path() && recur_possible()) launch_apply_cols<T>(C[0], AC0, geom(0), 2 * r, stream);
         cudaEventRecord(e1, stream);
         hh_status st;
         const bool ok = sync_check(st);
@@ -974,7 +983,9 @@ struct Solver final : SolverBase {
     // RT, the leaf precision, when rt_ready):
     // out = base + sum_c P_c M_c R_c res (base null: zero; base may be out), then
     // out += C A_c^{-1} C^H (rhs - A out).
-    void oras_step(const c128* base, const c128* rhs, c128* out, bool rt_ready = false, const int* gate = nullptr) {
+    // recur: the root's extras forming the next residual recursively (null: none)
+    void oras_step(const c128* base, const c128* rhs, c128* out, bool rt_ready = false, const int* gate = nullptr,
+                   const CoarseRecur* recur = nullptr) {
         const size_t N = (size_t)Sy * Sx;
         step_gate = gate;
         if (!rt_ready) launch_copy<double, T>(res, RT, N, false, false, stream);
@@ -1002,10 +1013,14 @@ struct Solver final : SolverBase {
             // precision) less A applied to the update the level-1 kernel kept in dlt.
             // Both terms are in the leaf precision, like the correction computed from them;
             // the FP64 residual of the new iterate is formed afterwards as before.
-            pjoin(PC_COARSE, (double)N * (2.0 * r + 3.0) * sizeof(CT) + (double)N * 2.0 * sizeof(c128),
-                  2.0 * 8.0 * 2 * r * N);
+            // with the recursive residual also r' kept, the r columns of A C_0 at each point
+            // read and the next residual written; r complex multiply-adds per point
+            const double rby = recur ? (double)N * (r + 2.0) * sizeof(CT) : 0.0;
+            pjoin(PC_COARSE, (double)N * (2.0 * r + 3.0) * sizeof(CT) + (double)N * 2.0 * sizeof(c128) + rby,
+                  2.0 * 8.0 * 2 * r * N + (recur ? 8.0 * r * N : 0.0));
             CoarseBatch rb = one_job(0, RT, dlt, out, true);
             rb.gate = gate;
+            if (recur) rb.rr = *recur;
             launch_coarse_batch<T, T, T, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
         } else {
             pjoin(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
@@ -1195,15 +1210,15 @@ struct Solver final : SolverBase {
 
     // residual b - A u into res and RT, its norm and the device stopping test (ctl), one
     // launch; dcounter[0] is its ticket
-    void gated_residual(int* ctl) {
+    void gated_residual(int* ctl, const int* need = nullptr, const int* anchor = nullptr) {
         pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
-        launch_residual_stop<T>(u, bvec, res, RT, geom(0), npart, dnorm, ctl, dcounter, P.tol, stream);
+        launch_residual_stop<T>(u, bvec, res, RT, geom(0), npart, dnorm, ctl, dcounter, P.tol, stream, need, anchor);
         pend(PC_SPMV);
     }
 
     // the norms, the status words and the stop words (dnorm[0..8)) to the host
     bool read_norms(hh_status& st) {
-        ck(cudaMemcpyAsync(h_norm, dnorm, 8 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
+        ck(cudaMemcpyAsync(h_norm, dnorm, 10 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
         ck(cudaGetLastError(), cerr);
         ck(cudaStreamSynchronize(stream), cerr);
         if (cerr != cudaSuccess) { st = HH_ECUDA; return false; }
@@ -1219,44 +1234,83 @@ struct Solver final : SolverBase {
     // queued after the test passed does nothing, and u, the iteration count and the
     // final residual are those of the loop that tests after every step.  The number of
     // steps queued follows the contraction observed so far.
+    //
+    // In the complex64 form the residual that drives the steps is formed recursively by
+    // the root's correction, r_{k+1} = (r_k - A delta_1) - (A C_0) y_0 in the leaf
+    // precision, and replaced by the FP64 residual b - A u every RECUR_ANCHOR steps.  The FP64 residual is formed at those
+    // steps and wherever the recursive one comes within 2 tol: the stopping test always
+    // takes the FP64 residual, and the anchors depend on the step count only, so the
+    // iterates do not depend on when the test ran.
+    static constexpr int RECUR_ANCHOR = 8;
+    // The recursive residual serves the complex64 form: the FP64 form's residual is already
+    // in its working precision, and there the recursion's extra FP64 work costs more than
+    // the residual launch it saves.
+    bool recur_possible() const {
+        return sizeof(T) == sizeof(float) && eig && L >= 2 && P.n_inner == 1 && P.outer == HH_OUTER_ORAS;
+    }
     hh_status loop_oras_device_test(int& it, double& rel) {
-        int* ctl = (int*)(dnorm + 6);   // [0] stop (1 converged, 2 not finite), [1] tests run
+        // [0] stop (1 converged, 2 not finite), [1] FP64 tests run, [2] FP64 residual due,
+        // [3] steps done, [4] anchor step
+        int* ctl = (int*)(dnorm + 6);
         const int* hctl = (const int*)(h_norm + 6);
         hh_status st = HH_OK;
-        zero(ctl, 2 * sizeof(int));
-        zero(dcounter, sizeof(unsigned));   // the residual's ticket
+        zero(ctl, 8 * sizeof(int));
+        zero(dcounter, 2 * sizeof(unsigned));   // the residual's and the root's tickets
         gated_residual(ctl);
         if (!read_norms(st)) return st;
+        const bool recur = recur_possible();
+        CoarseRecur rr{};
+        rr.AC = recur ? AC0 : nullptr;
+        rr.rp = RP;
+        rr.rt = RT;
+        rr.part = npart;
+        rr.ticket = dcounter + 1;
+        rr.nrm = dnorm;
+        rr.ctl = ctl;
+        rr.tol = P.tol;
+        rr.anchor = RECUR_ANCHOR;
         double rel_prev = -1.0;
         int it_prev = 0, chunks = 0;
         for (;;) {
-            rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
+            rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;   // last FP64 residual
             if (hctl[0] == 2 || !std::isfinite(rel)) return HH_ENOCONV;
             if (hctl[0] == 1) return HH_OK;
-            if (it >= P.max_iter) return HH_ENOCONV;
+            if (it >= P.max_iter) {
+                // the FP64 residual of the last iterate, for the report
+                gated_residual(ctl);
+                if (!read_norms(st)) return st;
+                rel = h_norm[2] > 0 ? std::sqrt(h_norm[0] / h_norm[2]) : 0.0;
+                return hctl[0] == 1 ? HH_OK : HH_ENOCONV;
+            }
+            // the current residual: the recursive one once steps have run
+            const double relc =
+                (it == 0 || !recur) ? rel : (h_norm[2] > 0 ? std::sqrt(h_norm[1] / h_norm[2]) : 0.0);
             // Two chunks of 8 first: the residual of the first steps may grow before it
             // settles into its asymptotic rate, so a rate measured from step 0 overshoots.
             // Then the steps still needed at the rate of the last chunk, none to spare (a
             // short estimate costs one more synchronisation, a long one gated steps).
             int chunk = 8;
-            if (chunks >= 2 && it > it_prev && rel < rel_prev && rel > 0) {
-                const double rho = std::pow(rel / rel_prev, 1.0 / (it - it_prev));
-                const double need = std::log(P.tol / rel) / std::log(rho);
+            if (chunks >= 2 && it > it_prev && relc < rel_prev && relc > 0) {
+                const double rho = std::pow(relc / rel_prev, 1.0 / (it - it_prev));
+                const double need = std::log(P.tol / relc) / std::log(rho);
                 chunk = need < 64.0 ? std::max(1, (int)std::ceil(need)) : 64;
             }
             ++chunks;
-            rel_prev = rel;
+            rel_prev = relc;
             it_prev = it;
             const int n = std::max(1, std::min(chunk, P.max_iter - it));
-            const int tests0 = hctl[1];
+            // steps done: counted by the root's correction (recursive residual), else by
+            // the FP64 tests, one per step
+            const int count0 = recur ? hctl[3] : hctl[1];
             const bool fresh = graphs[2].exec == nullptr;
             for (int k = 0; k < n; ++k)
                 replay_fresh(2, [&] {
-                    oras_step(u, bvec, u, true, ctl);
-                    gated_residual(ctl);
+                    oras_step(u, bvec, u, true, ctl, recur ? &rr : nullptr);
+                    if (recur) gated_residual(ctl, ctl + 2, ctl + 4);
+                    else gated_residual(ctl);
                 });
             const bool ok = read_norms(st);
-            const int ran = hctl[1] - tests0;
+            const int ran = (recur ? hctl[3] : hctl[1]) - count0;
             // the first step of a new handle ran directly (its pairs are pending); the
             // replays that did work are the next ran - 1
             runs_release(graphs[2], (size_t)std::max(0, ran - (fresh ? 1 : 0)));

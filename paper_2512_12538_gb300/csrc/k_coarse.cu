@@ -70,6 +70,46 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
     return s_ok != 0;
 }
 
+// CoarseRecur's end of phase 3: the block's |next residual|^2, then in the last block to
+// finish the fixed-order sum and the control words.  The norm only decides when the FP64
+// residual is formed, so it is summed in FP32 (the FP64 pipe is slow here).
+__device__ __forceinline__ void coarse_recur_tail(const CoarseRecur& R, float rr2, unsigned lb, unsigned nblk) {
+    __shared__ float rred[8];
+    __shared__ unsigned s_last;
+    rr2 = warp_sum(rr2);
+    if ((threadIdx.x & 31) == 0) rred[threadIdx.x >> 5] = rr2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += rred[w];
+        ((float*)R.part)[lb] = t;
+        __threadfence();
+        s_last = atomicAdd(R.ticket, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    float a = 0.f;
+    for (unsigned k = threadIdx.x; k < nblk; k += blockDim.x) a += __ldcg((const float*)R.part + k);
+    a = warp_sum(a);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) rred[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += rred[w];
+        *R.ticket = 0u;
+        R.nrm[1] = (double)t;
+        const int steps = R.ctl[3] + 1;
+        R.ctl[3] = steps;
+        const int anchor = (steps % R.anchor) == 0;
+        const float b2 = (float)R.nrm[2];
+        const float rel = b2 > 0.f ? sqrtf(t / b2) : 0.f;
+        R.ctl[4] = anchor;
+        R.ctl[2] = (anchor || !isfinite(rel) || rel < 2.f * (float)R.tol) ? 1 : 0;
+    }
+}
+
 // One-column coarse corrections of several nodes (Eq. (3)) in one cooperative launch;
 // job k owns blocks [blk0, blk0 + nblk).  A node's basis has p = 2r columns: those of its
 // first child [0, p/2) vanish on the rows at and below `split`, the second child's
@@ -150,6 +190,7 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
             rv = rv - ax;
         }
         const CA ra = cvt<TC>(rv);
+        if (bt.rr.AC && gi == 0) ((CA*)bt.rr.rp)[pt] = ra;   // r' for the next residual
 #pragma unroll
         for (int u = 0; u < CB_COLS; ++u) cfma_cj(acc[u], cv[u], ra);
     }
@@ -222,6 +263,7 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
     // phase 3: one point per thread, all p columns (coalesced along the points)
     cplx<TO>* out = (cplx<TO>*)J.out;
     const unsigned lo = (unsigned)J.r0 * g.Sx, hi = (unsigned)J.r1 * g.Sx;
+    float rr2 = 0.f;   // |next residual|^2 of the thread's points (CoarseRecur)
     for (unsigned base = lb * 256u; base < N; base += nblk * 256u) {
         const unsigned pt = base + threadIdx.x;
         if (pt < lo || pt >= hi) continue;
@@ -245,7 +287,30 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
         if (J.dout) ((cplx<TC>*)J.dout)[pt - lo] = J.add_w ? a + cvt<TC>(w_in[pt]) : a;
         cplx<TO>& o = out[pt - lo];
         o = J.acc_out ? o + val : val;
+        if (bt.rr.AC) {
+            // the next residual r' - (A C) y; A C's columns of one child reach one row into
+            // the other child's rows (the stencil), so both halves count next to the split
+            const int jr = (int)(pt / (unsigned)g.Sx);
+            int k0 = 0, k1 = p;
+            if (J.split >= 0) {
+                if (jr < J.split - 1) k1 = p >> 1;
+                else if (jr > J.split) k0 = p >> 1;
+            }
+            const CA* AC = (const CA*)bt.rr.AC;
+            CA rn = ((const CA*)bt.rr.rp)[pt];
+            for (; k0 + 8 <= k1; k0 += 8) {
+                CA av[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) av[u] = AC[(size_t)(k0 + u) * N + pt];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) rn = rn - av[u] * s_y[k0 + u];
+            }
+            for (; k0 < k1; ++k0) rn = rn - AC[(size_t)k0 * N + pt] * s_y[k0];
+            ((CA*)bt.rr.rt)[pt] = rn;
+            rr2 += (float)abs2(rn);
+        }
     }
+    if (bt.rr.AC) coarse_recur_tail(bt.rr, rr2, lb, nblk);
 }
 
 template <typename TC, typename TV, typename TW, typename TO>

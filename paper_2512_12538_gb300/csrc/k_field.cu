@@ -80,11 +80,15 @@ struct ResidStop {
     int* ctl;
     unsigned* ticket;
     double tol;
+    const int* need;     // may be null: else the launch does nothing while *need is zero
+    const int* anchor;   // may be null: else yt is written only while *anchor is nonzero
 };
 template <typename T>
 __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restrict__ v, c128* __restrict__ y,
                                 cplx<T>* __restrict__ yt, OpGeom g, double* part, const int* gate, ResidStop stop) {
     if (gate && *gate) return;
+    if (stop.need && !*stop.need) return;
+    const bool wt = !stop.anchor || *stop.anchor;
     const size_t total = (size_t)g.b * g.Sx;
     double acc2 = 0.0;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -100,7 +104,7 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
         if (j < g.b - 1) ax = ax - wi * x[t + g.Sx];
         const c128 out = v[t] - ax;
         y[t] = out;
-        yt[t] = cvt<T>(out);
+        if (wt) yt[t] = cvt<T>(out);
         acc2 += abs2(out);
     }
     __shared__ double red[32];
@@ -150,22 +154,52 @@ void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
                           cudaStream_t s, const int* gate) {
     const size_t total = (size_t)g.b * g.Sx;
     const int grid = grid_for(total, 256, 152 * 8);
-    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, ResidStop{});
+    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, ResidStop{nullptr, nullptr, nullptr, 0.0,
+                                                                                nullptr, nullptr});
     note_launch();
     if (nblk_out) *nblk_out = grid;
 }
 template <typename T>
 void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, double* nrm,
-                          int* ctl, unsigned* ticket, double tol, cudaStream_t s) {
+                          int* ctl, unsigned* ticket, double tol, cudaStream_t s, const int* need,
+                          const int* anchor) {
     const size_t total = (size_t)g.b * g.Sx;
     const int grid = grid_for(total, 256, 152 * 8);
-    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, ResidStop{nrm, ctl, ticket, tol});
+    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, ResidStop{nrm, ctl, ticket, tol, need, anchor});
     note_launch();
 }
 template void launch_residual_stop<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, double*, int*,
-                                          unsigned*, double, cudaStream_t);
+                                          unsigned*, double, cudaStream_t, const int*, const int*);
 template void launch_residual_stop<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, double*, int*,
-                                           unsigned*, double, cudaStream_t);
+                                           unsigned*, double, cudaStream_t, const int*, const int*);
+
+// y[j N + pt] = (A~ x_j)[pt] for p column-major columns (one thread per (column, point))
+template <typename T>
+__global__ void k_apply_cols(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y, OpGeom g, int p) {
+    const size_t N = (size_t)g.b * g.Sx, total = N * p;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t pt = t % N;
+        const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
+        cplx<T> ax = op_diag_t<T>(j, i, g) * x[t];
+        const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
+        const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
+        if (g.Sx > 1) {
+            if (i > 0) ax = ax - wj * x[t - 1];
+            if (i < g.Sx - 1) ax = ax - wj * x[t + 1];
+        }
+        if (j > 0) ax = ax - wi * x[t - g.Sx];
+        if (j < g.b - 1) ax = ax - wi * x[t + g.Sx];
+        y[t] = ax;
+    }
+}
+template <typename T>
+void launch_apply_cols(const cplx<T>* x, cplx<T>* y, OpGeom g, int p, cudaStream_t s) {
+    const size_t total = (size_t)g.b * g.Sx * p;
+    k_apply_cols<T><<<grid_for(total, 256), 256, 0, s>>>(x, y, g, p);
+    note_launch();
+}
+template void launch_apply_cols<float>(const c64*, c64*, OpGeom, int, cudaStream_t);
+template void launch_apply_cols<double>(const c128*, c128*, OpGeom, int, cudaStream_t);
 template void launch_residual_cast<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, int*, cudaStream_t,
                                           const int*);
 template void launch_residual_cast<double>(const c128*, const c128*, c128*, c128*, OpGeom, double*, int*,

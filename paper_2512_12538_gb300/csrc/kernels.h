@@ -42,15 +42,21 @@ void launch_residual_batch(ResidBatch bt, double* part, int part_cap, double* no
 
 // out = sum of n doubles (deterministic single-block reduction)
 void launch_sum(const double* part, int n, double* out, cudaStream_t s);
+// A~ applied to p column-major columns of a node's band: y[j N + pt] = (A~ x_j)[pt].
+template <typename T>
+void launch_apply_cols(const cplx<T>* x, cplx<T>* y, OpGeom g, int p, cudaStream_t s);
+
 // launch_residual_cast with the stopping test of the stationary iteration kept on the
-// device, in the same launch.  Unless ctl[0] is already set (then nothing is done):
+// device, in the same launch.  Unless ctl[0] is already set, or need is given and zero
+// (then nothing is done); yt is written only when anchor is null or nonzero:
 // y, yt and the partials as launch_residual_cast, then nrm[0] = ||y||^2 (launch_sum's
 // order), ctl[1] += 1, and with rel = sqrt(nrm[0] / nrm[2]) (0 when nrm[2] <= 0)
 // ctl[0] = 2 if rel is not finite, 1 if rel < tol.  ctl[0] is the gate of the next
 // step's launches; ticket is a device counter that is zero between launches.
 template <typename T>
 void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, double* nrm,
-                          int* ctl, unsigned* ticket, double tol, cudaStream_t s);
+                          int* ctl, unsigned* ticket, double tol, cudaStream_t s, const int* need = nullptr,
+                          const int* anchor = nullptr);
 
 // b = h^2 w_i w_j f + h (w_j gx + w_i gy) for the global problem.
 void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s);
@@ -112,10 +118,31 @@ struct CoarseJob {
     int ngrp;              // set by the launcher: column groups per half (p/2 / CB_COLS, rounded up)
     unsigned sb[5];        // set by the launcher: blocks of set s are [sb[s], sb[s + 1])
 };
+// Optional extras of a one-job launch on the root in the device-tested stationary loop.
+// Phase 1 keeps r' = v - A~ w (the residual after the level-1 update) in rp; phase 3
+// forms the next residual r' - (A C) y (AC: A applied to the basis, laid out as C) into
+// rt, with its |.|^2 per block in part, and the last block to finish (ticket: zero
+// between launches) adds those in block order and sets the loop's control words:
+//   ctl[3] += 1 (steps done); ctl[4] = 1 when ctl[3] is a multiple of `anchor` (the FP64
+//   residual then replaces rt), else 0; ctl[2] = 1 when the FP64 residual must be formed
+//   (an anchor step, or sqrt(sum / nrm[2]) < 2 tol, or the sum not finite), else 0;
+//   nrm[1] = the sum.
+struct CoarseRecur {
+    const void* AC;        // null: none of this
+    void* rp;
+    void* rt;
+    double* part;
+    unsigned* ticket;
+    double* nrm;
+    int* ctl;
+    double tol;
+    int anchor;
+};
 struct CoarseBatch {
     CoarseJob job[CB_MAX_JOBS];
     int njobs;
     const int* gate;       // may be null: when the word is nonzero at launch, nothing is done
+    CoarseRecur rr;
 };
 template <typename TC, typename TV, typename TW, typename TO>
 void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s);
