@@ -158,7 +158,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure is a
 # kernel, from one ncu capture of this bench (warm cache, as inside a solve); the
 # capture and its command are in profiles/coarse_batch_helm2d_n255_k40_L2.md.  To be
 # reset to None whenever k_coarse_batch changes.
-TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": None}
+TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 89637}
 
 
 # --------------------------------------------------------------------- our arm
