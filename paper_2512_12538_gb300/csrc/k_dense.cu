@@ -17,7 +17,7 @@ static constexpr int GAL_FLUSH = 4;     // Galerkin tiles summed in FP32 before 
 
 // Accumulate conj(As[n][i]) * Bs[n][j] over a tile of `rows` rows held in shared memory.
 // Rows i outside [ilo, ihi) contribute nothing for this tile (ihi = 0: no restriction).
-template <typename ACC>
+template <typename ACC, int KMAX = IP_MAXOUT>
 __device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cplx<ACC>* Bs, int rows, int p, int q,
                                                    int split, cplx<ACC>* acc, int ilo, int ihi) {
     const int nout = p * q;
@@ -25,7 +25,7 @@ __device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cp
         // output o = threadIdx.x + k IP_THREADS; k is a compile-time index, so acc stays
         // in registers
 #pragma unroll
-        for (int k = 0; k < IP_MAXOUT; ++k) {
+        for (int k = 0; k < KMAX; ++k) {
             const int o = threadIdx.x + k * IP_THREADS;
             if (o >= nout) continue;
             const int i = o / q, j = o % q;
@@ -46,13 +46,13 @@ __device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cp
     }
 }
 
-template <typename ACC>
+template <typename ACC, int KMAX = IP_MAXOUT>
 __device__ __forceinline__ void ip_store_partial(cplx<ACC>* acc, int p, int q, int split, cplx<ACC>* red,
                                                  c128* out) {
     const int nout = p * q;
     if (split == 1) {
 #pragma unroll
-        for (int k = 0; k < IP_MAXOUT; ++k) {
+        for (int k = 0; k < KMAX; ++k) {
             const int o = threadIdx.x + k * IP_THREADS;
             if (o < nout) out[o] = cvt<double>(acc[k]);
         }
@@ -294,7 +294,7 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 // GAL_FLUSH 32-point tiles are summed in FP32, then added to FP64 accumulators, so the
 // FP32 rounding stays at the level of 128 points' sum; FP64 on this GPU runs at 1/64
 // of the FP32 rate, so only the outputs a thread owns are flushed).
-template <typename T>
+template <typename T, int KMAX>
 __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* __restrict__ C, OpGeom g, int p,
                                                                  int split_row, c128* partial) {
     using CT = cplx<T>;
@@ -304,10 +304,10 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
     c128* red = (c128*)(Bs + IP_TILE * p);
     const int nout = p * p;
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
-    c128 acc[IP_MAXOUT];
-    for (int k = 0; k < IP_MAXOUT; ++k) acc[k] = {0.0, 0.0};
-    CT tacc[IP_MAXOUT];
-    for (int k = 0; k < IP_MAXOUT; ++k) tacc[k] = {0, 0};
+    c128 acc[KMAX];
+    for (int k = 0; k < KMAX; ++k) acc[k] = {0.0, 0.0};
+    CT tacc[KMAX];
+    for (int k = 0; k < KMAX; ++k) tacc[k] = {0, 0};
     const int nk = split > 1 ? 1 : (nout + IP_THREADS - 1) / IP_THREADS;   // outputs owned
     int ntile = 0;
     const size_t N = (size_t)g.b * g.Sx;
@@ -343,12 +343,12 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
             else if (j0 >= split_row) { ilo = p / 2; ihi = p; }
         }
         if (sizeof(T) == sizeof(double)) {
-            ip_tile_accumulate<double>((const c128*)As, (const c128*)Bs, rows, p, p, split, acc, ilo, ihi);
+            ip_tile_accumulate<double, KMAX>((const c128*)As, (const c128*)Bs, rows, p, p, split, acc, ilo, ihi);
         } else {
-            ip_tile_accumulate<T>(As, Bs, rows, p, p, split, tacc, ilo, ihi);
+            ip_tile_accumulate<T, KMAX>(As, Bs, rows, p, p, split, tacc, ilo, ihi);
             if (++ntile == GAL_FLUSH || t0 + IP_TILE >= n1) {
 #pragma unroll
-                for (int k = 0; k < IP_MAXOUT; ++k)
+                for (int k = 0; k < KMAX; ++k)
                     if (k < nk) {
                         acc[k] = acc[k] + cvt<double>(tacc[k]);
                         tacc[k] = {0, 0};
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
         }
         __syncthreads();
     }
-    ip_store_partial<double>(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
+    ip_store_partial<double, KMAX>(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
 }
 
 template <typename T>
@@ -373,10 +373,15 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
     const size_t sm = sizeof(cplx<T>) * (size_t)IP_TILE * 2 * p + (split > 1 ? sizeof(c128) * split * nout : 0);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_galerkin_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_galerkin_partial<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_galerkin_partial<T, IP_MAXOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
         attr_set = true;
     }
-    k_galerkin_partial<T><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
+    // accumulators sized to the outputs a thread owns (p <= 32: at most 4), so that the
+    // registers allow two blocks per SM and the grid runs in one wave
+    if (nout <= 4 * IP_THREADS) k_galerkin_partial<T, 4><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
+    else k_galerkin_partial<T, IP_MAXOUT><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
     note_launch();
     return grid;
 }
