@@ -402,6 +402,9 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, i
     __shared__ T s_inv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t tot = (size_t)Sx * m;
+    // the staged copy's rows are m + 1 apart: a warp reading one column of consecutive
+    // rows then spreads over the shared-memory banks
+    const int ld = staged ? m + 1 : m;
     if (staged) {
         for (size_t e0 = threadIdx.x; e0 < tot; e0 += 4 * blockDim.x) {
             cplx<T> t[4];
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, i
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const size_t e = e0 + (size_t)u * blockDim.x;
-                if (e < tot) Y[e] = t[u];
+                if (e < tot) Y[(e / m) * ld + e % m] = t[u];
             }
         }
         __syncthreads();
@@ -422,20 +425,20 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, i
         for (int pass = 0; pass < 2 && j > 0; ++pass) {
             for (int k = warp; k < j; k += nw) {
                 cplx<T> a = {0, 0};
-                for (int x = lane; x < Sx; x += 32) cfma_cj(a, Y[(size_t)x * m + k], Y[(size_t)x * m + j]);
+                for (int x = lane; x < Sx; x += 32) cfma_cj(a, Y[(size_t)x * ld + k], Y[(size_t)x * ld + j]);
                 a = warp_sum(a);
                 if (lane == 0) dots[k] = a;
             }
             __syncthreads();
             for (int x = threadIdx.x; x < Sx; x += blockDim.x) {
-                cplx<T> v = Y[(size_t)x * m + j];
-                for (int k = 0; k < j; ++k) v = v - Y[(size_t)x * m + k] * dots[k];
-                Y[(size_t)x * m + j] = v;
+                cplx<T> v = Y[(size_t)x * ld + j];
+                for (int k = 0; k < j; ++k) v = v - Y[(size_t)x * ld + k] * dots[k];
+                Y[(size_t)x * ld + j] = v;
             }
             __syncthreads();
         }
         T a2 = 0;
-        for (int x = threadIdx.x; x < Sx; x += blockDim.x) a2 += abs2(Y[(size_t)x * m + j]);
+        for (int x = threadIdx.x; x < Sx; x += blockDim.x) a2 += abs2(Y[(size_t)x * ld + j]);
         a2 = warp_sum(a2);
         if (lane == 0) red[warp] = a2;
         __syncthreads();
@@ -449,11 +452,11 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, i
         }
         __syncthreads();
         const T inv = s_inv;
-        for (int x = threadIdx.x; x < Sx; x += blockDim.x) Y[(size_t)x * m + j] = inv * Y[(size_t)x * m + j];
+        for (int x = threadIdx.x; x < Sx; x += blockDim.x) Y[(size_t)x * ld + j] = inv * Y[(size_t)x * ld + j];
         __syncthreads();
     }
     if (staged)
-        for (size_t e = threadIdx.x; e < tot; e += blockDim.x) Yg[e] = Y[e];
+        for (size_t e = threadIdx.x; e < tot; e += blockDim.x) Yg[e] = Y[(e / m) * ld + e % m];
 }
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s) {
@@ -463,7 +466,7 @@ void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scrat
         cudaFuncSetAttribute(k_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    const size_t bytes = sizeof(cplx<T>) * (size_t)Sx * m;
+    const size_t bytes = sizeof(cplx<T>) * (size_t)Sx * (m + 1);   // padded rows
     const int staged = bytes <= (size_t)(200 * 1024) - 2048;
     k_qr<T><<<nq, 512, staged ? bytes : 0, s>>>(dev_ptr_scratch, Sx, m, staged);
     note_launch();
@@ -630,7 +633,7 @@ __global__ void __launch_bounds__(256) k_heig_tri(c128* const* Gp, int m) {
 // Stage 2, one block of four warps per (eigenvalue, matrix): the kk-th largest
 // eigenvalue of T by multisection (128 Sturm-count probes per round, one per thread, so
 // that each SM's four FP64 pipes work); for kk < r also its eigenvector (warp 0):
-// inverse iteration with a pivoted tridiagonal LU (three steps from a fixed start),
+// inverse iteration with a pivoted tridiagonal LU (two steps from a fixed start),
 // then u = Q D y by the reflectors in reverse.
 static constexpr int HV_THREADS = 128;
 __global__ void __launch_bounds__(HV_THREADS) k_heig_vec(c128* const* Gp, c128* const* Up, double* const* lamp,
@@ -705,7 +708,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_heig_vec(c128* const* Gp, c128* 
             }
         }
         for (int i = 0; i < m; ++i) dg[i] = __drcp_rn(fabs(dg[i]) < 1e-300 ? 1e-300 : dg[i]);   // reciprocals
-        for (int it = 0; it < 3; ++it) {
+        for (int it = 0; it < 2; ++it) {
             for (int i = 0; i + 1 < m; ++i) {
                 if (!sw[i]) y[i + 1] -= lo[i] * y[i];
                 else { const double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t - lo[i] * y[i]; }
