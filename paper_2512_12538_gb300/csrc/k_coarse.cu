@@ -373,44 +373,42 @@ void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, in
 
 
 // Several columns (set-up): W[pt][c] += sum_j C[j][pt] y[j][c].  One thread per point
-// and 16 columns at a time: each C[j][pt] is read once per chunk (coalesced along the
-// points) and used for all the chunk's columns; y staged in shared memory in the basis
-// precision.
+// and per chunk of UPD_COLS columns (chunk = blockIdx.y): each C[j][pt] is read once per
+// chunk (coalesced along the points) and used for all the chunk's columns; y staged in
+// shared memory in the basis precision.  The chunks in separate blocks keep several blocks
+// per SM in flight (the loop over j waits on L2 loads).
+static constexpr int UPD_COLS = 8;
 template <typename TC, typename TW>
 __global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict__ C, const c128* __restrict__ y,
                                                      cplx<TW>* __restrict__ W, size_t N, int p, int nc) {
     extern __shared__ __align__(16) unsigned char ysm[];
-    cplx<TC>* ys = (cplx<TC>*)ysm;   // [p][nc]
-    for (int t = threadIdx.x; t < p * nc; t += blockDim.x) ys[t] = cvt<TC>(y[t]);
+    cplx<TC>* ys = (cplx<TC>*)ysm;   // [p][UPD_COLS]: this chunk's columns of y
+    const int c0 = blockIdx.y * UPD_COLS, cn = min(UPD_COLS, nc - c0);
+    for (int t = threadIdx.x; t < p * UPD_COLS; t += blockDim.x) {
+        const int j = t / UPD_COLS, c = t - j * UPD_COLS;
+        ys[t] = c < cn ? cvt<TC>(y[j * nc + c0 + c]) : cplx<TC>{0, 0};
+    }
     __syncthreads();
     for (size_t pt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; pt < N; pt += (size_t)gridDim.x * blockDim.x) {
-        for (int c0 = 0; c0 < nc; c0 += 16) {
-            const int cn = min(16, nc - c0);
-            cplx<TC> acc[16];
+        cplx<TC> acc[UPD_COLS];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c] = {0, 0};
-            for (int j = 0; j < p; ++j) {
-                const cplx<TC> cv = C[(size_t)j * N + pt];
-                const cplx<TC>* yr = ys + j * nc + c0;
+        for (int c = 0; c < UPD_COLS; ++c) acc[c] = {0, 0};
+        for (int j = 0; j < p; ++j) {
+            const cplx<TC> cv = C[(size_t)j * N + pt];
+            const cplx<TC>* yr = ys + j * UPD_COLS;
 #pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c < cn) cfma(acc[c], cv, yr[c]);
-            }
-            cplx<TW>* wr = W + pt * nc + c0;
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (c < cn) wr[c] = wr[c] + cvt<TW>(acc[c]);
+            for (int c = 0; c < UPD_COLS; ++c) cfma(acc[c], cv, yr[c]);
         }
+        cplx<TW>* wr = W + pt * nc + c0;
+#pragma unroll
+        for (int c = 0; c < UPD_COLS; ++c)
+            if (c < cn) wr[c] = wr[c] + cvt<TW>(acc[c]);
     }
 }
 template <typename TC, typename TW>
 void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_coarse_updn<TC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr = true;
-    }
-    k_coarse_updn<TC, TW><<<blocks_for(N, 256, 152 * 8), 256, sizeof(cplx<TC>) * p * nc, s>>>(C, y, W, N, p, nc);
+    const dim3 grid(blocks_for(N, 256, 152 * 8), (nc + UPD_COLS - 1) / UPD_COLS);
+    k_coarse_updn<TC, TW><<<grid, 256, sizeof(cplx<TC>) * p * UPD_COLS, s>>>(C, y, W, N, p, nc);
     note_launch();
 }
 
