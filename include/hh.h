@@ -58,9 +58,10 @@ typedef enum {
 
 typedef enum {
     HH_PREC_FP64 = 0,     /* complex128 everywhere, FP64 CUDA-core arithmetic          */
-    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches and bases;  */
-                          /* FP64 residual, Galerkin matrices, their inverse and the   */
-                          /* sketch SVD; the outer iteration refines in FP64           */
+    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches, bases and  */
+                          /* the Galerkin inverses (eliminated in FP32 from matrices   */
+                          /* summed in FP64); FP64 residual and sketch SVD; the outer  */
+                          /* iteration refines against the FP64 residual               */
 } hh_precision;
 
 typedef struct {
