@@ -161,6 +161,19 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure is a
 TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 89637}
 
 
+def whole_job_rate(local_ms, units_per_rank, world, device="cuda"):
+    """Whole-job throughput over `world` ranks that each processed `units_per_rank`
+    units in `local_ms`: the units of all ranks over the slowest rank's time (a MAX
+    all-reduce of the times when world > 1).  Returns (units/s, max ms)."""
+    ms = float(local_ms)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 # --------------------------------------------------------------------- our arm
 def run_ours(args, rank, world):
     import numpy as np
@@ -241,12 +254,7 @@ def run_ours(args, rank, world):
     hh.hh_profile_enable(None, False)
     hh.hh_profile_categories(None, None)
     launches = hh.hh_launch_count() - launches0
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(sum(step_ms), args.steps, world)
 
     # FP64 GPU form of the same method on the same workload
     fp64_ms = []
@@ -255,6 +263,7 @@ def run_ours(args, rank, world):
         ms, st, _ = one("fp64")
         fp64_ms.append(ms)
         fp64_iters.append(st.iters)
+    fp64_value = whole_job_rate(sum(fp64_ms), len(fp64_ms), world)[0]
 
     # end to end through the C-ABI with host buffers (pinned): H2D f, g and D2H u inside
     fh = torch.from_numpy(f).pin_memory()
@@ -271,7 +280,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
     N = w.S * w.S
-    e2e = {"value": world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
+    e2e = {"value": whole_job_rate(sum(e2e_ms), len(e2e_ms), world)[0], "unit": UNIT,
            "h2d_bytes_per_step": 16 * (N + 4 * w.S), "d2h_bytes_per_step": 16 * N}
 
     batch = run_batch_form(hh, torch) if rank == 0 and args.batch_form == "on" else None
@@ -292,10 +301,10 @@ def run_ours(args, rank, world):
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
         "iterations": {"mixed": statistics.median(iters), "fp64": statistics.median(fp64_iters)},
-        "fp64_form": {"value": world * len(fp64_ms) / (sum(fp64_ms) / 1e3), "unit": UNIT,
+        "fp64_form": {"value": fp64_value, "unit": UNIT,
                       "ms_per_step": statistics.mean(fp64_ms), "median_ms_per_step": statistics.median(fp64_ms),
                       "step_ms": [round(x, 3) for x in fp64_ms]},
-        "mixed_over_fp64": (value / world) / (len(fp64_ms) / (sum(fp64_ms) / 1e3)),
+        "mixed_over_fp64": value / fp64_value,
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
         "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
                     for k, v in prof_all.items() if v[1] > 0},
