@@ -16,23 +16,23 @@ static int grid_for(size_t n, int threads, int cap = 152 * 16) {
 }
 
 // ------------------------------------------------------------------ operator apply
-// One thread per (point, column); grid-stride.  Compute type = TY.
-template <typename TX, typename TV, typename TY>
+// One thread per (point, column); grid-stride.  Compute type = TY (the coefficients too,
+// so that a complex64 apply stays off the FP64 pipe).  I: the index type, 32-bit when
+// the launch's element count fits (the divisions by the sizes are then far shorter).
+template <typename TX, typename TV, typename TY, typename I>
 __global__ void k_apply(const cplx<TX>* __restrict__ x, const cplx<TV>* __restrict__ v,
                         cplx<TY>* __restrict__ y, OpGeom g, int nc, TY sgn, double* part) {
-    const size_t total = (size_t)g.b * g.Sx * nc;
-    const size_t ldr = (size_t)g.Sx * nc;
+    const I total = (I)g.b * (I)g.Sx * (I)nc;
+    const I ldr = (I)g.Sx * (I)nc;
     double acc2 = 0.0;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(t % nc);
-        const size_t pt = t / nc;
-        const int i = (int)(pt % g.Sx);
-        const int j = (int)(pt / g.Sx);
-        const c128 d = op_diag(j, i, g);
-        const cplx<TY> dg = {(TY)d.re, (TY)d.im};
-        cplx<TY> ax = dg * cvt<TY>(x[t]);
-        const TY wj = (TY)wrow(j, g.b), wi = (TY)wcol(i, g.Sx);
+    for (I t = blockIdx.x * (I)blockDim.x + threadIdx.x; t < total; t += (I)gridDim.x * blockDim.x) {
+        const I pt = t / (I)nc;
+        const I jr = pt / (I)g.Sx;
+        const int i = (int)(pt - jr * (I)g.Sx);
+        const int j = (int)jr;
+        cplx<TY> ax = op_diag_t<TY>(j, i, g) * cvt<TY>(x[t]);
+        const TY wj = (j == 0 || j == g.b - 1) ? (TY)0.5 : (TY)1;
+        const TY wi = g.Sx == 1 ? (TY)1 : ((i == 0 || i == g.Sx - 1) ? (TY)0.5 : (TY)1);
         // x-neighbours: coefficient -w_j
         if (g.Sx > 1) {
             if (i > 0) ax = ax - wj * cvt<TY>(x[t - nc]);
@@ -65,7 +65,10 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
     const size_t total = (size_t)g.b * g.Sx * nc;
     const int th = 256;
     const int grid = grid_for(total, th, 152 * 8);
-    k_apply<TX, TV, TY><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    if (total + (size_t)grid * th < (1ull << 32))
+        k_apply<TX, TV, TY, unsigned><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    else
+        k_apply<TX, TV, TY, size_t><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
     note_launch();
     if (nblk_out) *nblk_out = grid;
 }
