@@ -246,14 +246,22 @@ __global__ void __launch_bounds__(1024) k_ip_reduce(const c128* __restrict__ par
         out2[o] = t;
     }
 }
-// y = M x for a p x p matrix and a p x q block (one thread per output)
+// y = M x for a p x p matrix and a p x q block.  Eight threads per output, each adding
+// every eighth term, then a fixed shuffle tree: the FP64 products spread over eight
+// times the SMs of one thread per output.
 __global__ void k_small_matmul(const c128* __restrict__ M, const c128* __restrict__ x, int p, int q, c128* y) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= p * q) return;
-    const int i = o / q, j = o % q;
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, sub = threadIdx.x & 7;
+    const bool ok = o < p * q;
     c128 t = {0.0, 0.0};
-    for (int k = 0; k < p; ++k) cfma(t, M[i * p + k], x[k * q + j]);
-    y[o] = t;
+    if (ok) {
+        const int i = o / q, j = o - (o / q) * q;
+        for (int k = sub; k < p; k += 8) cfma(t, M[i * p + k], x[k * q + j]);
+    }
+    for (int d = 4; d > 0; d >>= 1) {
+        t.re += __shfl_xor_sync(0xffffffffu, t.re, d);
+        t.im += __shfl_xor_sync(0xffffffffu, t.im, d);
+    }
+    if (ok && sub == 0) y[o] = t;
 }
 
 void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, const c128* Minv, c128* out2,
@@ -272,7 +280,7 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
         if (grid > 304) grid = 304;
         k_ip_reduce<<<grid, 256, 0, s>>>(partial, nblk, p, q, sums, nullptr, nullptr);
         note_launch();
-        k_small_matmul<<<(nout + 255) / 256, 256, 0, s>>>(Minv, sums, p, q, out2);
+        k_small_matmul<<<(8 * nout + 255) / 256, 256, 0, s>>>(Minv, sums, p, q, out2);
         note_launch();
         if (out) cudaMemcpyAsync(out, sums, sizeof(c128) * nout, cudaMemcpyDeviceToDevice, s);
         return;
@@ -758,26 +766,41 @@ void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int
     note_launch();
 }
 
-// V[x][j] = sum_k Z[x][k] U[k][j] / sqrt(lam_j)
+// V[x][j] = sum_k Z[x][k] U[k][j] / sqrt(lam_j), in FP64.  Eight threads per output,
+// each adding every eighth term, then a fixed shuffle tree (the FP64 products spread over
+// the SMs); the r scales 1 / sqrt(lam_j) formed once per block.
 template <typename T>
 __global__ void k_form_v(const cplx<T>* __restrict__ Z, const c128* __restrict__ U, const double* lam,
                          cplx<T>* __restrict__ V, int Sx, int m, int r) {
-    const size_t total = (size_t)Sx * r;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(t % r);
-        const size_t x = t / r;
-        c128 a = {0.0, 0.0};
-        for (int k = 0; k < m; ++k) cfma(a, cvt<double>(Z[x * m + k]), U[k * m + j]);
+    __shared__ double sc[64];
+    for (int j = threadIdx.x; j < r && j < 64; j += blockDim.x) {
         const double l = lam[j];
-        const double sc = l > 0.0 ? 1.0 / sqrt(l) : 0.0;
-        V[t] = cvt<T>(sc * a);
+        sc[j] = l > 0.0 ? 1.0 / sqrt(l) : 0.0;
     }
+    __syncthreads();
+    const unsigned total = (unsigned)Sx * (unsigned)r;
+    const unsigned t = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    const bool ok = t < total;
+    c128 a = {0.0, 0.0};
+    unsigned x = 0;
+    int j = 0;
+    if (ok) {
+        x = t / (unsigned)r;
+        j = (int)(t - x * (unsigned)r);
+        for (int k = sub; k < m; k += 8) cfma(a, cvt<double>(Z[(size_t)x * m + k]), U[k * m + j]);
+    }
+    for (int d = 4; d > 0; d >>= 1) {
+        a.re += __shfl_xor_sync(0xffffffffu, a.re, d);
+        a.im += __shfl_xor_sync(0xffffffffu, a.im, d);
+    }
+    if (ok && sub == 0) V[t] = cvt<T>(sc[j] * a);
 }
 template <typename T>
 void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* V, int Sx, int m, int r,
                    cudaStream_t s) {
-    const size_t total = (size_t)Sx * r;
-    int grid = (int)((total + 255) / 256);
+    const size_t total = (size_t)Sx * r;   // r <= 64 (the basis width)
+    const int grid = (int)((8 * total + 255) / 256);
     k_form_v<T><<<grid, 256, 0, s>>>(Z, U, lam, V, Sx, m, r);
     note_launch();
 }
