@@ -76,8 +76,9 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
 // Global residual y = v - A x in FP64 with per-block partial sums of |y|^2, and the
 // same residual rounded to the leaf precision (yt), the input of the next ORAS step.
 // With stop (the device-tested loop) the last block to finish also adds the partials in
-// block order and takes the stopping test (the same as k_sum_stop), so no second launch
-// is needed: ctl doubles as the gate, stop->ticket is zero between launches.
+// block order and takes the stopping test the host would take (IEEE division and square
+// root in FP64 on both sides), so no second launch is needed: ctl doubles as the gate,
+// stop->ticket is zero between launches.
 struct ResidStop {
     double* nrm;
     int* ctl;
