@@ -528,107 +528,163 @@ __device__ int sturm_count(const double* d, const double* e2, int m, double x) {
 // of unit phases).  Overwrites G with the workspace read by stage 2: reflector k in
 // row k (tau_k = 2 / ||v_k||^2), then d, eb, eb^2, tau (m doubles each) and D (m
 // complex) from offset m^2.
+//
+// FP64 issue on one SM bounds this kernel, so each column's step is laid out by FP64
+// instruction count. Only the lower triangle of the trailing matrix is kept, and the
+// rank-2 update touches only that triangle. The product A'v reads an upper entry as
+// the conjugate of its mirror, with the sign of the imaginary part flipped by an
+// integer operation. The product is formed as four column-interleaved partial sums
+// per row, one warp per SM sub-partition, then added in a fixed order. The scalar
+// work of a column (the reflector, K and q) runs in warp 0 alone, with four block
+// barriers per column.
 __global__ void __launch_bounds__(256) k_heig_tri(c128* const* Gp, int m) {
     extern __shared__ __align__(16) unsigned char hsm[];
-    c128* A = (c128*)hsm;                    // m x m working matrix
+    c128* A = (c128*)hsm;                    // m x m working matrix (lower triangle)
     c128* Vr = A + m * m;                    // reflector k stored in row k (length m-k-1)
-    c128* w = Vr + m * m;                    // m
+    c128* w = Vr + m * m;                    // m: q = tau A'v - K v
     double* tau = (double*)(w + m);          // m
     double* d = tau + m;                     // m   diagonal of the real tridiagonal
     double* eb = d + m;                      // m   |subdiagonal|
     double* e2 = eb + m;                     // m   squared
     c128* delta = (c128*)(e2 + m);           // m   diagonal unitary scaling
-    __shared__ c128 s_beta, s_K;
-    __shared__ double s_tau;
+    c128* part = delta + m;                  // 4 x m partial sums of A'v; phases at the end
+    __shared__ c128 s_beta;
     c128* G = Gp[blockIdx.x];
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) A[t] = G[t];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k + 2 < m; ++k) {
         const int n = m - k - 1;             // length of the column below the diagonal
+        c128* v = Vr + k * m;
+        const c128* a0 = A + (k + 1) * m + (k + 1);   // trailing block, row stride m
+        // v = x - beta e_1 with beta = -|x| x_0 / |x_0|, and tau = 2 / ||v||^2; every lane
+        // of warp 0 forms the same scalars
         if (warp == 0) {
             double a2 = 0.0;
             for (int i = lane; i < n; i += 32) a2 += abs2(A[(k + 1 + i) * m + k]);
             a2 = warp_sum(a2);
+            const c128 x0 = A[(k + 1) * m + k];
+            const double alpha = sqrt(a2);
+            const double ax02 = abs2(x0);
+            double ax0 = 0.0;
+            c128 ph = {1.0, 0.0};
+            if (ax02 > 0.0) {
+                const double r0 = rsqrt(ax02);
+                ax0 = ax02 * r0;
+                ph = r0 * x0;
+            }
+            const c128 beta = (-alpha) * ph;
+            const double tk = alpha > 0.0 ? 1.0 / (alpha * (alpha + ax0)) : 0.0;
+            for (int i = lane; i < n; i += 32) {
+                c128 x = A[(k + 1 + i) * m + k];
+                if (i == 0) x = x - beta;
+                v[i] = x;
+            }
             if (lane == 0) {
-                const double alpha = sqrt(a2);
-                const c128 x0 = A[(k + 1) * m + k];
-                const double ax0 = sqrt(abs2(x0));
-                const c128 ph = ax0 > 0.0 ? (1.0 / ax0) * x0 : c128{1.0, 0.0};
-                s_beta = (-alpha) * ph;
-                s_tau = alpha > 0.0 ? 1.0 / (alpha * (alpha + ax0)) : 0.0;   // 2 / ||v||^2
+                tau[k] = tk;
+                s_beta = beta;
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            c128 v = A[(k + 1 + i) * m + k];
-            if (i == 0) v = v - s_beta;
-            Vr[k * m + i] = v;
-        }
-        if (threadIdx.x == 0) tau[k] = s_tau;
-        __syncthreads();
-        const double tk = s_tau;
-        const c128* v = Vr + k * m;
-        // w = tau A' v: a warp per row, lanes across the row
-        for (int i = warp; i < n; i += (blockDim.x >> 5)) {
+        const double tk = tau[k];
+        // thread (q, i) adds columns q, q + 4, ... of row i of A'v (4 n <= 252 threads)
+        for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) {
+            const int q = t / n, i = t - q * n;
             c128 acc = {0.0, 0.0};
-            const c128* row = A + (k + 1 + i) * m + (k + 1);
-            for (int j = lane; j < n; j += 32) cfma(acc, row[j], v[j]);
-            acc = warp_sum(acc);
-            if (lane == 0) w[i] = tk * acc;
+            for (int j = q; j < n; j += 4) {
+                const bool lo = j <= i;
+                c128 a = a0[lo ? i * m + j : j * m + i];
+                a.im = __hiloint2double(__double2hiint(a.im) ^ (lo ? 0 : (int)0x80000000), __double2loint(a.im));
+                cfma(acc, a, v[j]);
+            }
+            part[q * m + i] = acc;
         }
         __syncthreads();
+        // warp 0: w = tau A'v, K = (tau / 2) v^H w, q = w - K v (rows lane and lane + 32)
         if (warp == 0) {
-            c128 acc = {0.0, 0.0};
-            for (int i = lane; i < n; i += 32) cfma_cj(acc, v[i], w[i]);
-            acc = warp_sum(acc);
-            if (lane == 0) s_K = (0.5 * tk) * acc;
+            c128 wl[2];
+            c128 kp = {0.0, 0.0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                c128 s = {0.0, 0.0};
+                if (i < n) {
+                    s = tk * (((part[i] + part[m + i]) + part[2 * m + i]) + part[3 * m + i]);
+                    cfma_cj(kp, v[i], s);
+                }
+                wl[h] = s;
+            }
+            const c128 K = (0.5 * tk) * warp_sum(kp);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i < n) w[i] = wl[h] - K * v[i];
+            }
         }
         __syncthreads();
-        const c128 K = s_K;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = w[i] - K * v[i];   // q
-        __syncthreads();
-        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-            const int i = t / n, j = t - (t / n) * n;
+        // A' -= v q^H + q v^H on the lower triangle; thread t takes element t of the
+        // row-major triangle, i from the triangular root and two exact integer corrections
+        const int nt = n * (n + 1) / 2;
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+            int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while (i * (i + 1) / 2 > t) --i;
+            while ((i + 1) * (i + 2) / 2 <= t) ++i;
+            const int j = t - i * (i + 1) / 2;
             c128& a = A[(k + 1 + i) * m + (k + 1 + j)];
-            a = a - v[i] * conj(w[j]) - w[i] * conj(v[j]);
+            const c128 vi = v[i], vj = v[j], wi = w[i], wj = w[j];
+            a.re = fma(-vi.re, wj.re, fma(-vi.im, wj.im, fma(-wi.re, vj.re, fma(-wi.im, vj.im, a.re))));
+            a.im = fma(-vi.im, wj.re, fma(vi.re, wj.im, fma(-wi.im, vj.re, fma(wi.re, vj.im, a.im))));
         }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const c128 val = (i == 0) ? s_beta : c128{0.0, 0.0};
-            A[(k + 1 + i) * m + k] = val;
-            A[k * m + (k + 1 + i)] = conj(val);
-        }
+        const c128 beta = s_beta;
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            A[(k + 1 + i) * m + k] = (i == 0) ? beta : c128{0.0, 0.0};
         __syncthreads();
     }
+    // d, eb, eb^2 and the unit phases of the subdiagonal, one thread per index; the
+    // phases' prefix product (D) by thread 0
+    c128* phs = part;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        d[i] = A[i * m + i].re;
+        if (i + 1 < m) {
+            const c128 e = A[(i + 1) * m + i];
+            const double ae = sqrt(abs2(e));
+            eb[i] = ae;
+            e2[i] = ae * ae;
+            phs[i] = ae > 0.0 ? (1.0 / ae) * e : c128{1.0, 0.0};
+        }
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         c128 dl = {1.0, 0.0};
         for (int i = 0; i < m; ++i) {
-            d[i] = A[i * m + i].re;
             delta[i] = dl;
-            if (i + 1 < m) {
-                const c128 e = A[(i + 1) * m + i];
-                const double ae = sqrt(abs2(e));
-                eb[i] = ae;
-                e2[i] = ae * ae;
-                if (ae > 0.0) dl = dl * ((1.0 / ae) * e);
-            }
+            if (i + 1 < m) dl = dl * phs[i];
+        }
+    }
+    // the Gershgorin interval of T, warp 1
+    double* ws = (double*)(G + (size_t)m * m);
+    if (warp == 1) {
+        double lo0 = 0.0, hi0 = 0.0;
+        bool any = false;
+        for (int i = lane; i < m; i += 32) {
+            const double rad = (i > 0 ? eb[i - 1] : 0.0) + (i + 1 < m ? eb[i] : 0.0);
+            lo0 = any ? fmin(lo0, d[i] - rad) : d[i] - rad;
+            hi0 = any ? fmax(hi0, d[i] + rad) : d[i] + rad;
+            any = true;
+        }
+        if (!any) { lo0 = 1e300; hi0 = -1e300; }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo0 = fmin(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+            hi0 = fmax(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+        }
+        if (lane == 0) {
+            ws[6 * m] = lo0;
+            ws[6 * m + 1] = hi0;
         }
     }
     __syncthreads();
     // write the workspace (G is no longer needed)
-    double* ws = (double*)(G + (size_t)m * m);
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) G[t] = Vr[t];
-    if (threadIdx.x == 0) {
-        // Gershgorin interval of T
-        double lo0 = 0.0, hi0 = 0.0;
-        for (int i = 0; i < m; ++i) {
-            const double rad = (i > 0 ? eb[i - 1] : 0.0) + (i + 1 < m ? eb[i] : 0.0);
-            lo0 = i ? fmin(lo0, d[i] - rad) : d[i] - rad;
-            hi0 = i ? fmax(hi0, d[i] + rad) : d[i] + rad;
-        }
-        ws[6 * m] = lo0;
-        ws[6 * m + 1] = hi0;
-    }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         ws[i] = d[i];
         ws[m + i] = eb[i];
@@ -753,7 +809,7 @@ void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int
     void* hp[3 * 64];
     for (int i = 0; i < nq; ++i) { hp[i] = G[i]; hp[nq + i] = U[i]; hp[2 * nq + i] = lam[i]; }
     cudaMemcpyAsync(scratch, hp, sizeof(void*) * 3 * nq, cudaMemcpyHostToDevice, s);
-    const size_t sm = sizeof(c128) * (2 * (size_t)m * m + m) + sizeof(double) * 4 * m + sizeof(c128) * m + 64;
+    const size_t sm = sizeof(c128) * (2 * (size_t)m * m + m) + sizeof(double) * 4 * m + sizeof(c128) * 5 * m + 64;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_heig_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
