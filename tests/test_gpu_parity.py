@@ -137,19 +137,32 @@ def _proj_dist(V1, V2):
     return np.linalg.norm(P1 - P2, 2)
 
 
+def _check_bases(hh, h, P, O, tol):
+    for c in range(1, 7):
+        V = np.zeros((P.Sx, O.r), dtype=np.complex128)
+        sig = np.zeros(O.m)
+        hh.hh_get_basis(h, c, V, sig)
+        assert np.allclose(V.conj().T @ V, np.eye(O.r), atol=10 * tol)
+        np.testing.assert_allclose(sig, O.sigma[c][:O.m], rtol=tol, atol=tol * O.sigma[c][0])
+        gap = O.sigma[c][O.r - 1] / max(O.sigma[c][O.r], 1e-300)
+        if gap > 1.05:   # subspace well defined only across a spectral gap
+            assert _proj_dist(V, O.V[c]) < 50 * tol / (gap - 1.0), (c, gap)
+
+
+def _check_coarse(hh, h, P, O, tol):
+    for p in (0, 1, 2):
+        nd = O.tree[p]
+        rr = random_complex((nd.b, P.Sx, 1), 55 + p)
+        z = torch.empty_like(dev(rr))
+        hh.hh_coarse_apply(h, p, dev(rr), z)
+        assert rel(host(z), O.coarse(p, rr)) < tol, p
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-7), ("mixed", 1e-3)])
 def test_sketch_basis_subspace_and_singular_values(hh, precision, tol):
     P, O, h = make_pair(hh, precision)
     try:
-        for c in range(1, 7):
-            V = np.zeros((P.Sx, O.r), dtype=np.complex128)
-            sig = np.zeros(O.m)
-            hh.hh_get_basis(h, c, V, sig)
-            assert np.allclose(V.conj().T @ V, np.eye(O.r), atol=10 * tol)
-            np.testing.assert_allclose(sig, O.sigma[c][:O.m], rtol=tol, atol=tol * O.sigma[c][0])
-            gap = O.sigma[c][O.r - 1] / max(O.sigma[c][O.r], 1e-300)
-            if gap > 1.05:   # subspace well defined only across a spectral gap
-                assert _proj_dist(V, O.V[c]) < 50 * tol / (gap - 1.0), (c, gap)
+        _check_bases(hh, h, P, O, tol)
     finally:
         hh.hh_destroy(h)
 
@@ -158,12 +171,40 @@ def test_sketch_basis_subspace_and_singular_values(hh, precision, tol):
 def test_coarse_correction_operator(hh, precision, tol):
     P, O, h = make_pair(hh, precision)
     try:
-        for p in (0, 1, 2):
-            nd = O.tree[p]
-            rr = random_complex((nd.b, P.Sx, 1), 55 + p)
-            z = torch.empty_like(dev(rr))
-            hh.hh_coarse_apply(h, p, dev(rr), z)
-            assert rel(host(z), O.coarse(p, rr)) < tol, p
+        _check_coarse(hh, h, P, O, tol)
+    finally:
+        hh.hh_destroy(h)
+
+
+# The largest sketch the dense kernels take: r + p = 64 samples per child (64 x 64 Gram
+# matrices) and 2r = 64 (the coarse matrices and their inverses). S = 80 columns, so no
+# clamping to the interface dimension. The singular values stay above 0.15 sigma_0 here,
+# so every one of the 64 is compared at the relative tolerance.
+LARGEST_SKETCH = dict(n=78, k=30.0, rank=32, oversample=32, seed=5)
+
+
+@pytest.mark.parametrize("precision,tol,tol_coarse,tol_solve", [("fp64", 1e-7, 1e-8, 1e-10),
+                                                                  ("mixed", 1e-3, 1e-3, 1e-8)])
+def test_largest_sketch_bases_coarse_operator_and_solve(hh, precision, tol, tol_coarse, tol_solve):
+    P, O, h = make_pair(hh, precision, **LARGEST_SKETCH)
+    try:
+        assert (O.m, O.r) == (64, 32)
+        _check_bases(hh, h, P, O, tol)
+        _check_coarse(hh, h, P, O, tol_coarse)
+    finally:
+        hh.hh_destroy(h)
+    cfg = dict(SMALL)
+    cfg.update(LARGEST_SKETCH)
+    f = point_source_rhs(cfg["n"], 21)
+    g = random_complex((4, P.S), 22)
+    us = direct.solve(P, f, g)
+    params = hh.make_params(2, cfg["n"], cfg["k"], cfg["levels"], cfg["overlap"], cfg["rank"], cfg["oversample"], 1,
+                            1e-12, 400, precision, cfg["seed"])
+    h, _ = hh.hh_setup(params)
+    try:
+        u = torch.empty((P.S, P.S), dtype=torch.complex128, device="cuda")
+        hh.hh_solve(h, dev(f), dev(g), u)
+        assert rel(host(u), us) < tol_solve
     finally:
         hh.hh_destroy(h)
 
