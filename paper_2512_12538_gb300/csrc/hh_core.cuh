@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #define HH_HD __host__ __device__ __forceinline__
 
 // ------------------------------------------------------------------ complex numbers
@@ -157,3 +159,27 @@ template <typename T> __device__ __forceinline__ cplx<T> warp_sum(cplx<T> v) {
 }
 
 HH_HD size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------ one-time steps per device
+// Kernel attributes (the dynamic shared-memory limit, non-portable cluster sizes) belong
+// to a device's context, so a process that drives several devices sets them on each.
+// `bits` holds one bit per device (ordinals 0..63); f() runs until it succeeds once on
+// the current device.  Two threads may both run f() the first time, which is harmless.
+inline int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+template <typename F> inline bool once_per_device(std::atomic<unsigned long long>& bits, F&& f) {
+    const unsigned long long bit = 1ull << (current_device() & 63);
+    if (bits.load(std::memory_order_acquire) & bit) return true;
+    if (!f()) return false;
+    bits.fetch_or(bit, std::memory_order_release);
+    return true;
+}
+// Raises `fn`'s dynamic shared-memory limit to `bytes` on the current device, once.
+template <typename K> inline void smem_limit_once(std::atomic<unsigned long long>& bits, K* fn, int bytes) {
+    once_per_device(bits, [&] {
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    });
+}

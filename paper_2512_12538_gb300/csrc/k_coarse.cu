@@ -315,15 +315,17 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
 
 template <typename TC, typename TV, typename TW, typename TO>
 int coarse_batch_max_grid() {
-    static int mg = 0;
-    if (!mg) {
-        int dev = 0, sms = 0, nb = 0;
-        cudaGetDevice(&dev);
+    static std::atomic<int> mg[64];   // per device ordinal; 0 until queried
+    const int dev = current_device();
+    int g = mg[dev & 63].load(std::memory_order_relaxed);
+    if (!g) {
+        int sms = 0, nb = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_batch<TC, TV, TW, TO>, 256, 0);
-        mg = std::max(1, std::min(nb, 2) * sms);
+        g = std::max(1, std::min(nb, 2) * sms);
+        mg[dev & 63].store(g, std::memory_order_relaxed);
     }
-    return mg;
+    return g;
 }
 
 template <typename TC, typename TV, typename TW, typename TO>

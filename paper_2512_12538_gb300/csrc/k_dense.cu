@@ -182,11 +182,8 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
     const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_ip_partial<TA, TB, ACC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr{0};   // per instantiation
+    smem_limit_once(attr, k_ip_partial<TA, TB, ACC, false>, 200 * 1024);
     k_ip_partial<TA, TB, ACC, false><<<grid, IP_THREADS, sm, s>>>(A, lda, B, ldb, N, p, q, partial);
     note_launch();
     return grid;
@@ -200,11 +197,8 @@ int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
     const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_ip_partial<TA, TB, ACC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(attr, k_ip_partial<TA, TB, ACC, true>, 200 * 1024);
     k_ip_partial<TA, TB, ACC, true><<<grid, IP_THREADS, sm, s>>>(A, N, B, ldb, N, p, q, partial);
     note_launch();
     return grid;
@@ -266,11 +260,8 @@ __global__ void k_small_matmul(const c128* __restrict__ M, const c128* __restric
 
 void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, const c128* Minv, c128* out2,
                       cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ip_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(attr, k_ip_reduce, 200 * 1024);
     const int nout = p * q;
     if (Minv && nout > 64) {
         // many outputs: reduce over blocks with the whole GPU, then apply Minv separately
@@ -379,13 +370,9 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
     const int nout = p * p;
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
     const size_t sm = sizeof(cplx<T>) * (size_t)IP_TILE * 2 * p + (split > 1 ? sizeof(c128) * split * nout : 0);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_galerkin_partial<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_galerkin_partial<T, IP_MAXOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr4{0}, attrmax{0};
+    smem_limit_once(attr4, k_galerkin_partial<T, 4>, 200 * 1024);
+    smem_limit_once(attrmax, k_galerkin_partial<T, IP_MAXOUT>, 200 * 1024);
     // accumulators sized to the outputs a thread owns (p <= 32: at most 4), so that the
     // registers allow two blocks per SM and the grid runs in one wave
     if (nout <= 4 * IP_THREADS) k_galerkin_partial<T, 4><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
@@ -469,11 +456,8 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, i
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s) {
     cudaMemcpyAsync(dev_ptr_scratch, Y, sizeof(cplx<T>*) * nq, cudaMemcpyHostToDevice, s);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(attr, k_qr<T>, 200 * 1024);
     const size_t bytes = sizeof(cplx<T>) * (size_t)Sx * (m + 1);   // padded rows
     const int staged = bytes <= (size_t)(200 * 1024) - 2048;
     k_qr<T><<<nq, 512, staged ? bytes : 0, s>>>(dev_ptr_scratch, Sx, m, staged);
@@ -810,11 +794,8 @@ void launch_heig(c128* const* G, c128* const* U, double* const* lam, int nq, int
     for (int i = 0; i < nq; ++i) { hp[i] = G[i]; hp[nq + i] = U[i]; hp[2 * nq + i] = lam[i]; }
     cudaMemcpyAsync(scratch, hp, sizeof(void*) * 3 * nq, cudaMemcpyHostToDevice, s);
     const size_t sm = sizeof(c128) * (2 * (size_t)m * m + m) + sizeof(double) * 4 * m + sizeof(c128) * 5 * m + 64;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_heig_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(attr, k_heig_tri, 200 * 1024);
     k_heig_tri<<<nq, 256, sm, s>>>((c128* const*)scratch, m);
     note_launch();
     k_heig_vec<<<dim3(m, nq), HV_THREADS, 0, s>>>((c128* const*)scratch, (c128* const*)(scratch + nq),
@@ -953,12 +934,9 @@ void launch_gj_inverse(const GjBatch& bt, int count, bool fp32, cudaStream_t s) 
     const int n = bt.n;
     const size_t es = fp32 ? sizeof(c64) : sizeof(c128);
     const size_t sm = es * (n * n + 2 * n) + sizeof(int) * 2 * n;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gj_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_gj_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr64{0}, attr32{0};
+    smem_limit_once(attr64, k_gj_inverse<double>, 200 * 1024);
+    smem_limit_once(attr32, k_gj_inverse<float>, 200 * 1024);
     if (fp32) k_gj_inverse<float><<<count, 256, sm, s>>>(bt);
     else k_gj_inverse<double><<<count, 256, sm, s>>>(bt);
     note_launch();

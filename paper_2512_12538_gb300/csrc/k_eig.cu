@@ -563,11 +563,8 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
     k_eig_roots<T><<<ntasks, 160, 0, s>>>(d_tasks, kh, err);
     note_launch();
     const size_t sm = sizeof(cplx<T>) * (size_t)b_max * (2 + 6 * EM_WARPS) + sizeof(T) * (size_t)b_max;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_eig_modes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(attr, k_eig_modes<T>, 200 * 1024);
     k_eig_modes<T><<<dim3((b_max + EM_WARPS - 1) / EM_WARPS, ntasks), 32 * EM_WARPS, sm, s>>>(d_tasks, Sx, kh, err);
     note_launch();
 }
@@ -583,26 +580,20 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
     int kchunk = (int)std::min<size_t>((size_t)b_max, (96u << 10) / (sizeof(cplx<T>) * (b_max + GT_N)));
     kchunk = std::max(8, kchunk);
     const size_t sm = sizeof(cplx<T>) * ((size_t)b_max * kchunk + (size_t)kchunk * GT_N);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_eig_gemm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        cudaFuncSetAttribute(k_eig_gemm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        cudaFuncSetAttribute(k_eig_recur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr_t{0}, attr_f{0}, attr_r{0};
+    smem_limit_once(attr_t, k_eig_gemm<T, true>, 160 * 1024);
+    smem_limit_once(attr_f, k_eig_gemm<T, false>, 160 * 1024);
+    smem_limit_once(attr_r, k_eig_recur<T>, 200 * 1024);
     // register-tiled contraction where V and the column block fit in shared memory
     constexpr int GN2 = 16 * Gemm2Cols<T>::CV;
     const size_t sm2 = sizeof(cplx<T>) * ((size_t)b_max * b_max + (size_t)b_max * GN2);
     const bool tiled = stage != 1 && b_max <= 144 && sm2 <= (size_t)(220 * 1024);
     if (tiled) {
-        static bool attr2 = false;
-        if (!attr2) {
-            cudaFuncSetAttribute(k_eig_gemm2<T, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            cudaFuncSetAttribute(k_eig_gemm2<T, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            cudaFuncSetAttribute(k_eig_gemm2<T, true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            cudaFuncSetAttribute(k_eig_gemm2<T, false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            attr2 = true;
-        }
+        static std::atomic<unsigned long long> a_t5{0}, a_f5{0}, a_t9{0}, a_f9{0};
+        smem_limit_once(a_t5, k_eig_gemm2<T, true, 5>, 220 * 1024);
+        smem_limit_once(a_f5, k_eig_gemm2<T, false, 5>, 220 * 1024);
+        smem_limit_once(a_t9, k_eig_gemm2<T, true, 9>, 220 * 1024);
+        smem_limit_once(a_f9, k_eig_gemm2<T, false, 9>, 220 * 1024);
         dim3 g2((J + GN2 - 1) / GN2, ntasks);
         const bool small = b_max <= 80;
         if (stage == 0) {
@@ -845,17 +836,18 @@ int eig_sweep_fused_ready(int b_max, int Sx) {
 }
 template <typename T>
 int eig_sweep_fused_ready_query(int b_max, int Sx) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr{0};
+    const bool ok = once_per_device(attr, [] {
         if (cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_SMEM_MAX) !=
             cudaSuccess)
-            return 0;
+            return false;
         // clusters of 16 are beyond the portable size; allowed where the GPU supports them
         if (cudaFuncSetAttribute(k_eig_sweep_fused<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess)
             cudaGetLastError();
-        attr_set = true;
-    }
+        return true;
+    });
+    if (!ok) return 0;
     for (int cl : {16, 8}) {
         if (Sx < cl) continue;
         const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx, cl).elems;
