@@ -27,8 +27,9 @@
  * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue their
  *   work on it and return; calls that return host scalars or hh_stats synchronise it.
  * - The library owns its factors, bases and work buffers.  It obtains them in one
- *   block per handle from the allocator set by hh_set_allocator (default:
- *   cudaMallocAsync/cudaFreeAsync on the handle's stream) and returns it in hh_destroy.
+ *   block per handle from the allocator set by hh_set_allocator (default: a
+ *   stream-ordered memory pool of the library's own per device, on the handle's
+ *   stream) and returns it in hh_destroy.
  * - Errors are returned as hh_status; no call exits, traps or prints.  A handle is not
  *   thread-safe: use one host thread and one stream per handle.
  */
@@ -177,8 +178,9 @@ hh_status hh_solve_batch(hh_handle* const* h, const void* const* d_f, const void
  * hh_solve_batch), taking new ones in between iterations and retiring each as soon as
  * its residual meets its tol.  Requests the lockstep iteration cannot take are solved by
  * their worker; requests whose stationary iteration does not converge are re-solved by
- * flexible GMRES.  Server problems allocate from the CUDA runtime's stream-ordered pool,
- * not through hh_set_allocator.
+ * flexible GMRES.  Server problems allocate from the library's own stream-ordered pool
+ * on the current device (the default of hh_set_allocator), never through an installed
+ * hook.
  * -------------------------------------------------------------------------------- */
 typedef struct hh_server hh_server;
 

@@ -2075,7 +2075,7 @@ struct Server {
         cudaSetDevice(dev);
         cudaStream_t ws = nullptr;
         cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
-        const AllocHook rt{};   // server problems allocate from the runtime's pool on this stream
+        const AllocHook rt{};   // no hook: server problems allocate from the library's pool, on this stream
         for (;;) {
             ServerReq* r = nullptr;
             bool is_rescue = false;
