@@ -130,10 +130,12 @@ hh_status hh_footprint(const hh_params* params, size_t* bytes);
 hh_status hh_setup(const hh_params* params, void* stream, hh_handle** out,
                    size_t* footprint_out);
 
-/* Solve A u = b(f, g) by the coarse-corrected ORAS iteration of Eqs. (2)-(3) from
- * u = 0 until the FP64 relative residual is below params.tol.  d_f [S_y][S_x],
- * d_g [4][S] (or [2]), d_u [S_y][S_x] complex128 device arrays.  Synchronises.
- * Returns HH_ENOCONV (u = last iterate) if max_iter is reached. */
+/* Solve A u = b(f, g) from u = 0 until the FP64 relative residual is below params.tol,
+ * by the outer iteration params.outer selects: the coarse-corrected ORAS iteration of
+ * Eqs. (2)-(3), or flexible GMRES preconditioned by one step of it (Sec. 3).  d_f
+ * [S_y][S_x], d_g [4][S] (or [2]), d_u [S_y][S_x] complex128 device arrays.
+ * Synchronises.  Returns HH_ENOCONV (u = last iterate, stats->rel_res its residual) if
+ * max_iter is reached or the residual stops being finite. */
 hh_status hh_solve(hh_handle* h, const void* d_f, const void* d_g, void* d_u,
                    void* stream, hh_stats* stats);
 
