@@ -707,8 +707,11 @@ __global__ void __launch_bounds__(HV_THREADS) k_heig_vec(c128* const* Gp, c128* 
     double blo = lo0 - 1e-12 * span, bhi = hi0 + 1e-12 * span;
     // thread t probes lo + (t + 1) (hi - lo) / 129; the bracket shrinks 129x per round.
     // Absolute accuracy 2e-16 ||T|| is what the selection and the singular values need.
+    // Rounds also stop once the bracket is within two ulps of its end points: for the
+    // largest eigenvalues 2e-16 ||T|| is below one ulp, and further rounds cannot narrow
+    // the bracket.
     const int j = m - 1 - kk;                 // ascending index of the kk-th largest
-    for (int it = 0; it < 12 && bhi - blo > 2e-16 * span; ++it) {
+    for (int it = 0; it < 12 && bhi - blo > fmax(2e-16 * span, 0x1p-51 * fmax(fabs(blo), fabs(bhi))); ++it) {
         const double step = (bhi - blo) * (1.0 / (HV_THREADS + 1));
         const bool above = sturm_count(d, e2, m, blo + step * (tid + 1)) > j;   // eigenvalue below x
         const unsigned mask = __ballot_sync(0xffffffffu, above);
