@@ -13,6 +13,8 @@ formulas:
   the interface map formed column by column.
 * T7 (Sec. 2): <T x, y> = <x, T^* y> for the Euclidean inner product.
 * T8 (Sec. 1): Galerkin orthogonality C^H (f - A u) = 0 after the coarse step.
+* T10 (Sec. 3, n_i): the n_i sub-level iterations of an internal node are a stationary
+  iteration for A~_c x = v, so as n_i grows they converge to the band's exact solve.
 """
 import numpy as np
 import pytest
@@ -162,3 +164,22 @@ def test_hierarchy_layout():
         build_tree(20, 3, 4)
     with pytest.raises(ValueError):
         build_tree(100, 1, 3)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_T10_sub_level_iterations_converge_to_the_band_solve(levels):
+    """M_c with n_i sub-level iterations (each a coarse-corrected ORAS sweep over c's
+    children on the refreshed residual) tends to A~_c^{-1} v geometrically.  A slip in the
+    inner loop (a residual not refreshed, the global A in place of A~_c, a sign) stalls,
+    diverges or converges to another vector."""
+    P = Problem(2, 60, 10.0)
+    M = OMethod(P, levels, 2, 4, 4, n_inner=1, seed=7)
+    nd = M.tree[1]
+    V = random_complex((nd.b, P.Sx, 1), 31)
+    X = spla.spsolve(P.band_operator(nd.ra, nd.rb).tocsc(), V.reshape(-1)).reshape(V.shape)
+    errs = []
+    for ni in (1, 2, 4, 8, 16, 32):
+        M.n_inner = ni
+        errs.append(np.linalg.norm(M.M(1, V) - X) / np.linalg.norm(X))
+    assert all(b < 0.5 * a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-7, errs
