@@ -11,6 +11,7 @@ formulas:
 * T3/T9: manufactured solutions are recovered; the iteration's fixed point is A^{-1}b.
 * T6 (Sec. 2): with enough samples the randomised SVD reproduces the dense SVD of
   the interface map formed column by column.
+  With fewer samples, its values interlace below the dense ones.
 * T7 (Sec. 2): <T x, y> = <x, T^* y> for the Euclidean inner product.
 * T8 (Sec. 1): Galerkin orthogonality C^H (f - A u) = 0 after the coarse step.
 * T10 (Sec. 3, n_i): the n_i sub-level iterations of an internal node are a stationary
@@ -121,6 +122,23 @@ def test_T6_rsvd_equals_dense_svd_when_samples_cover(dim):
     v = Vh.conj().T[:, :1]
     proj = M2.V[1] @ (M2.V[1].conj().T @ v)
     assert np.linalg.norm(proj - v) < 1e-8
+
+
+def test_T6_rsvd_values_interlace_with_the_dense_ones_when_samples_do_not_cover():
+    """With m < S_x samples, Q has orthonormal columns, so the singular values of
+    Z^H = Q^H T_c are bounded by those of T_c, one by one (Cauchy interlacing for a
+    compression).  Leaf and internal children (whose T_c uses n_i sub-level iterations).
+    A sketch left unorthonormalised breaks the bound by the scale of Y."""
+    P = Problem(2, 40, 12.0)
+    M = OMethod(P, 2, 2, 6, 4, seed=3)
+    assert M.m == 10 < P.Sx
+    for c in range(1, 7):
+        s_dense = np.linalg.svd(_explicit_T(M, c), compute_uv=False)
+        s = M.sigma[c]
+        assert len(s) == M.m and np.all(np.diff(s) <= 1e-14 * s[0])
+        assert np.all(s <= s_dense[:M.m] * (1 + 1e-10) + 1e-13 * s_dense[0]), c
+        # the leading value of a sketch with oversampling is close to the dense one
+        assert s[0] > 0.5 * s_dense[0], c
 
 
 def test_T7_adjoint_identity_and_explicit_adjoint():
