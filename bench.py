@@ -5,14 +5,15 @@ factorisation, interface sketches, coarse bases, Galerkin matrices and their inv
 followed by the outer iteration to the calibrated FP64 residual tolerance, then the
 handle is released.  Default workload: 255 x 255 interior grid (257^2 unknowns), k = 40,
 2-level binary band hierarchy (4 leaves), overlap 2 rows, r = 16, p = 10, seeded
-Gaussian point sources.  The headline runs the mixed form (complex64 subdomain work,
-FP64 residual / Galerkin / coarse inverse / sketch SVD); the FP64 GPU form runs the
-same workload for comparison.
+Gaussian point sources.  The headline runs the mixed form: complex64 subdomain work,
+sketches, bases and coarse inverses; Galerkin and Gram matrices from FP32 products with
+FP64 sums; an FP64 residual and sketch eigenproblem.  The FP64 GPU form runs the same
+workload for comparison.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this project) on the
-same workload.  Under torchrun (N > 1) every rank solves its own independent problems
+same workload and `config`, on rank 0 only.  Under torchrun (N > 1) every rank solves its own independent problems
 (weak scaling, no collective on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
@@ -294,11 +295,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": f"{w.S}x{w.S} nodes ({w.n}^2 interior)", "k": w.k,
-                   "levels": w.levels, "leaves": 2 ** w.levels, "overlap": w.overlap, "rank": w.rank,
-                   "oversample": w.oversample, "n_inner": w.n_inner, "tol_rel_residual": TOL,
-                   "precision": "mixed", "step": "setup+solve+release of one problem per rank",
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "config": workload_config(w, "mixed", "flushed between steps (256 MB write)", f"replicas x{world}"),
         "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
         "iterations": {"mixed": statistics.median(iters), "fp64": statistics.median(fp64_iters)},
         "fp64_form": {"value": fp64_value, "unit": UNIT,
@@ -463,6 +460,15 @@ def roofline(w, prof, prof_all, cat, pk, pk_kind):
     return out
 
 
+def workload_config(w, precision, l2, parallelism):
+    """The JSON line's `config`: the workload and the step, shared by both arms."""
+    return {"workload": WORKLOAD, "grid": f"{w.S}x{w.S} nodes ({w.n}^2 interior)", "k": w.k,
+            "levels": w.levels, "leaves": 2 ** w.levels, "overlap": w.overlap, "rank": w.rank,
+            "oversample": w.oversample, "n_inner": w.n_inner, "tol_rel_residual": TOL,
+            "precision": precision, "step": "setup+solve+release of one problem per rank", "l2": l2,
+            "parallelism": parallelism}
+
+
 # ------------------------------------------------------------------ CPU baseline
 def cpu_baseline(w, f, g, n_solves=1):
     """The FP64 oracle, as it stands, on the same workload: n one-shot solves."""
@@ -502,9 +508,10 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "tol_rel_residual": TOL, "precision": "fp64 (CPU oracle)"},
+            "config": workload_config(w, "fp64 (CPU oracle)", "host run", "rank 0 only"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} one-shot solves of {WORKLOAD}"},
+                             "sample": f"{args.steps} one-shot solve(s) (set-up + iteration to tol {TOL}) of "
+                                       f"{WORKLOAD}; numpy/scipy, BLAS threads up to the core count"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
