@@ -10,9 +10,13 @@ the matrix complex symmetric (A = A^T), which the adjoint solves rely on.
 
 Row (i, j) (i along x, j along y):
 
-    (A u)_ij = w_j X_i(u_.j) + w_i Y_j(u_i.) - (kh)^2 w_i w_j u_ij
-               - i kh (w_j bx_i + w_i by_j) u_ij
+    (A u)_ij = w_j X_i(u_.j) + w_i Y_j(u_i.) - (k_j h)^2 w_i w_j u_ij
+               - i k_j h (w_j bx_i + w_i by_j) u_ij
     b_ij     = h^2 w_i w_j f_ij + h (w_j gx_ij + w_i gy_ij)
+
+k_j is the wavenumber of grid row j: the constant k, or, for the layered media of
+Sec. 3.3 (k = omega / c(y), piecewise constant in y), its value at y_j.  It enters
+only the diagonal, so A stays complex symmetric.
 
 X is the second difference along x (2u_i - u_{i-1} - u_{i+1} inside, u_0 - u_1 and
 u_{S-1} - u_{S-2} at the ends), bx_i flags the two x-boundary nodes, and gx is the
@@ -51,18 +55,21 @@ def direction(n: int, present: bool = True):
     return X, w, bnd
 
 
-def operator(kh: float, xdir, ydir) -> sp.csr_matrix:
+def operator(kh, xdir, ydir) -> sp.csr_matrix:
     """Assemble the weighted 5-point operator for a rectangle of nodes.
 
-    Unknowns are ordered row-major, index = j * Sx + i (x fastest), so Kronecker
-    products read kron(y-part, x-part).
+    kh is k h, one value or one per y node (row).  Unknowns are ordered row-major,
+    index = j * Sx + i (x fastest), so Kronecker products read kron(y-part, x-part).
     """
     Xx, wx, bx = xdir
     Yy, wy, by = ydir
+    khy = np.broadcast_to(np.asarray(kh, dtype=np.float64), wy.shape)
     Wx, Wy = sp.diags(wx), sp.diags(wy)
+    # the weights are 1/2 or 1 and the flags 0 or 1, so with a constant kh every entry
+    # equals (kh kh) w_j w_i and kh (w_j bx_i + by_j w_i) to the last bit
     A = (sp.kron(Wy, Xx) + sp.kron(Yy, Wx)
-         - (kh * kh) * sp.kron(Wy, Wx)
-         - 1j * kh * (sp.kron(Wy, sp.diags(bx)) + sp.kron(sp.diags(by), Wx)))
+         - sp.kron(sp.diags(wy * (khy * khy)), Wx)
+         - 1j * (sp.kron(sp.diags(wy * khy), sp.diags(bx)) + sp.kron(sp.diags(by * khy), Wx)))
     return sp.csr_matrix(A, dtype=np.complex128)
 
 
@@ -73,7 +80,9 @@ class Problem:
     Vectors are flattened row-major [S_y][S_x]; S_x = 1 in 1D.
     """
 
-    def __init__(self, dim: int, n: int, k: float):
+    def __init__(self, dim: int, n: int, k: float, k_rows=None):
+        """k_rows (optional): the wavenumber of each grid row j = 0..S-1 (layered media,
+        Sec. 3.3); k is then only a label.  Without it every row has k."""
         if dim not in (1, 2):
             raise ValueError("dim must be 1 or 2")
         self.dim, self.n, self.k = dim, n, float(k)
@@ -82,6 +91,13 @@ class Problem:
         self.kh = self.k * self.h
         self.Sy = self.S
         self.Sx = self.S if dim == 2 else 1
+        if k_rows is None:
+            self.k_rows = np.full(self.Sy, self.k)
+        else:
+            self.k_rows = np.asarray(k_rows, dtype=np.float64).copy()
+            if self.k_rows.shape != (self.Sy,) or not np.all(np.isfinite(self.k_rows)) or np.any(self.k_rows < 0):
+                raise ValueError("k_rows must hold one finite k >= 0 per grid row")
+        self.kh_rows = self.k_rows * self.h
         self._xdir = direction(self.Sx, present=(dim == 2))
 
     @property
@@ -90,7 +106,7 @@ class Problem:
 
     def band_operator(self, ra: int, rb: int) -> sp.csr_matrix:
         """A~ on rows [ra, rb): impedance (Robin, zero data) rows at both band ends."""
-        return operator(self.kh, self._xdir, direction(rb - ra))
+        return operator(self.kh_rows[ra:rb], self._xdir, direction(rb - ra))
 
     def A(self) -> sp.csr_matrix:
         """The global operator A (the band covering every row)."""

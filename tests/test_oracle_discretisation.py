@@ -13,7 +13,7 @@ import pytest
 
 from oracle import direct
 from oracle.problem import Problem
-from workloads import plane_wave_2d, random_complex
+from workloads import layered_wavenumber, plane_wave_2d, random_complex
 
 
 def _err_1d_plane_wave(n, k):
@@ -124,3 +124,78 @@ def test_rhs_weights_corner():
     b = P.rhs(f, g).reshape(P.S, P.S)
     # corner weights w_i = w_j = 1/2: h^2/4 f + h (g_x/2 + g_y/2)
     assert b[0, 0] == pytest.approx(P.h ** 2 / 4 + P.h * (1.0 + 2.0))
+
+
+# ------------------------------------------------------- layered media (Sec. 3.3)
+def test_constant_row_wavenumbers_give_the_scalar_operator_bit_for_bit():
+    for dim in (1, 2):
+        P = Problem(dim, 30, 7.0)
+        Q = Problem(dim, 30, 7.0, k_rows=np.full(32, 7.0))
+        assert abs(P.A() - Q.A()).max() == 0.0
+        assert abs(P.band_operator(4, 17) - Q.band_operator(4, 17)).max() == 0.0
+
+
+def _err_two_layers(n, k1=20.0, k2=8.0):
+    """1D, c = 1 on (0, 1/2) and c0 = k1 / k2 on (1/2, 1): an incoming wave from y = 0
+    is partly reflected and transmitted.  With u and u' continuous at 1/2 the exact
+    solution is e^{i k1 y} + R e^{-i k1 y} below and T e^{i k2 (y - 1/2)} above, with
+    R = e^{i k1} (k1 - k2) / (k1 + k2) and T = e^{i k1 / 2} 2 k1 / (k1 + k2)."""
+    P = Problem(1, n, k1, k_rows=layered_wavenumber(n, k1, k1 / k2, layers=2))
+    y = np.arange(P.S) * P.h
+    R = np.exp(1j * k1) * (k1 - k2) / (k1 + k2)
+    T = np.exp(0.5j * k1) * 2 * k1 / (k1 + k2)
+    U = np.where(y <= 0.5, np.exp(1j * k1 * y) + R * np.exp(-1j * k1 * y), T * np.exp(1j * k2 * (y - 0.5)))
+    u = direct.solve(P, np.zeros(P.S), np.array([-2j * k1, 0.0]))
+    return np.max(np.abs(u - U))
+
+
+@pytest.mark.parametrize("ns", [(99, 199, 399), (100, 200, 400)], ids=["interface_on_a_node", "between_nodes"])
+def test_two_layer_transmission_second_order(ns):
+    """Second order whether the interface falls on a node (that row takes the mean of k^2
+    over its two layers) or midway between two.  A wavenumber profile shifted by a row,
+    or one-sided at an interface node, converges at first order only."""
+    e = [_err_two_layers(n) for n in ns]
+    assert e[0] < 0.05
+    for a, b in zip(e, e[1:]):
+        assert 3.6 < a / b < 4.4, e
+
+
+def _err_2d_variable_k(n, k0=6.0, a=4.0, b=-3.0):
+    """u = e^{i(a x + b y)} with k(y) = k0 (1 + 0.3 sin 2 pi y): f = (a^2 + b^2 - k(y)^2) u,
+    g = d_n u - i k u on each side with the local k."""
+    h = 1.0 / (n + 1)
+    x = np.arange(n + 2) * h
+    ky = k0 * (1 + 0.3 * np.sin(2 * math.pi * x))
+    P = Problem(2, n, k0, k_rows=ky)
+    X, Y = np.meshgrid(x, x)                     # [row=y][col=x]
+    U = np.exp(1j * (a * X + b * Y))
+    f = (a * a + b * b - ky[:, None] ** 2) * U
+    g = np.zeros((4, P.S), dtype=complex)
+    g[0] = (-1j * a - 1j * ky) * U[:, 0]        # x = 0, along y
+    g[1] = (1j * a - 1j * ky) * U[:, -1]        # x = 1, along y
+    g[2] = (-1j * b - 1j * ky[0]) * U[0, :]     # y = 0, along x
+    g[3] = (1j * b - 1j * ky[-1]) * U[-1, :]    # y = 1, along x
+    u = direct.solve(P, f, g).reshape(P.S, P.S)
+    return np.max(np.abs(u - U))
+
+
+def test_2d_variable_wavenumber_manufactured_second_order():
+    e = [_err_2d_variable_k(n) for n in (31, 63, 127)]
+    assert e[0] < 0.05
+    for a, b in zip(e, e[1:]):
+        assert 3.5 < a / b < 4.5, e
+
+
+def test_layered_operator_complex_symmetric_and_band_rows():
+    """Each band operator carries its own rows' wavenumbers: away from its artificial
+    boundary it equals A on those rows (a band reading another band's k would not)."""
+    n = 30
+    P = Problem(2, n, n + 1.0, k_rows=layered_wavenumber(n, n + 1.0, 5.0))   # omega h = 1
+    A = P.A()
+    assert abs(A - A.T).max() == 0.0
+    Ad = A.toarray()
+    for ra, rb in ((3, 12), (9, 25), (20, 32)):
+        At = P.band_operator(ra, rb).toarray()
+        rows = np.arange(ra * P.Sx, rb * P.Sx)
+        inner = np.arange(P.Sx, (rb - ra - 1) * P.Sx)
+        assert np.array_equal(At[inner], Ad[np.ix_(rows, rows)][inner]), (ra, rb)

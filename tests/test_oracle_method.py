@@ -25,7 +25,7 @@ from oracle import direct
 from oracle.hierarchy import build_tree, interface_row, owned_in_parent
 from oracle.method import OMethod
 from oracle.problem import Problem
-from workloads import WORKLOADS, problem_inputs, random_complex
+from workloads import WORKLOADS, layered_wavenumber, problem_inputs, random_complex
 
 
 def test_T1_1d_two_subdomains_one_step_exact():
@@ -51,6 +51,19 @@ def test_T1_2d_full_interface_space_one_step_exact(levels, exact):
     M = OMethod(P, levels, 2, P.S, 0, seed=9, exact_subsolves=exact)
     u1 = M.precondition(P.rhs(f, g))
     assert direct.rel_err(u1, direct.solve(P, f, g)) < 1e-10
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_T1_layered_medium_one_step_exact(levels):
+    """T1 in the layered medium of Sec. 3.3 (omega h = 1, c0 = 5, 8 layers): with the full
+    interface space and exact sub-solves the coarse-corrected step is still exact, which
+    needs every band's operator to carry its own rows' wavenumbers."""
+    n = 46
+    P = Problem(2, n, n + 1.0, k_rows=layered_wavenumber(n, n + 1.0, 5.0))
+    f = random_complex((P.S, P.S), 15)
+    g = random_complex((4, P.S), 16)
+    M = OMethod(P, levels, 2, P.S, 0, seed=9, exact_subsolves=True)
+    assert direct.rel_err(M.precondition(P.rhs(f, g)), direct.solve(P, f, g)) < 1e-10
 
 
 def _flat_oras_step(P, tree, r):

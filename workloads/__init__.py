@@ -7,6 +7,7 @@ from .generators import (  # noqa: F401
     WORKLOADS,
     Workload,
     batch_problems,
+    layered_wavenumber,
     random_complex,
     point_source_rhs,
     plane_wave_2d,

@@ -55,6 +55,24 @@ def point_source_rhs(n: int, seed: int, n_src: int = 8, width_h: float = 2.0) ->
     return f
 
 
+def layered_wavenumber(n: int, omega: float, c0: float, layers: int = 8, c1: float = 1.0) -> np.ndarray:
+    """Wavenumber of each grid row for the layered medium of Sec. 3.3: k(y) = omega / c(y)
+    with c alternating c1, c0, c1, ... over `layers` equal layers of y in [0, 1], from
+    y = 0 up.  A row inside a layer takes that layer's k.  A row on a layer boundary
+    (y_j = l / layers) takes the mean of k^2 over its two layers: its nodal control volume
+    straddles both, and the mean keeps the scheme second order there.  Returns S = n + 2
+    values."""
+    h = 1.0 / (n + 1)
+    t = np.arange(n + 2) * h * layers
+    kl = omega / np.where(np.arange(layers) % 2 == 0, c1, c0)
+    nearest = np.rint(t).astype(int)
+    on_boundary = (np.abs(t - nearest) < 1e-9) & (nearest > 0) & (nearest < layers)
+    inside = np.minimum(np.floor(t + 1e-9).astype(int), layers - 1)
+    k = kl[inside]
+    below, above = kl[np.clip(nearest - 1, 0, layers - 1)], kl[np.clip(nearest, 0, layers - 1)]
+    return np.where(on_boundary, np.sqrt(0.5 * (below * below + above * above)), k)
+
+
 def plane_wave_2d(n: int, k: float, theta: float):
     """Continuous plane wave u = exp(i k (cos t x + sin t y)) with matching data.
 
