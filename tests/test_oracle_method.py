@@ -16,6 +16,10 @@ formulas:
 * T8 (Sec. 1): Galerkin orthogonality C^H (f - A u) = 0 after the coarse step.
 * T10 (Sec. 3, n_i): the n_i sub-level iterations of an internal node are a stationary
   iteration for A~_c x = v, so as n_i grows they converge to the band's exact solve.
+* T11 (Sec. 2, Fig. 4 discussion): the spectrum of the interface map follows the trends
+  the paper reports.  At hk = 1 the number of singular values above a fixed level grows
+  about linearly with k.  At fixed k it grows like 1/h when the overlap is a fixed number
+  of rows, and stays bounded when the overlap is a fixed width.
 """
 import numpy as np
 import pytest
@@ -214,3 +218,20 @@ def test_T10_sub_level_iterations_converge_to_the_band_solve(levels):
         errs.append(np.linalg.norm(M.M(1, V) - X) / np.linalg.norm(X))
     assert all(b < 0.5 * a for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-7, errs
+
+
+def _count_above(n, k, overlap, level=1e-2):
+    M = OMethod(Problem(2, n, k), 1, overlap, 1, 0, seed=1)
+    s = np.linalg.svd(_explicit_T(M, 1), compute_uv=False)
+    return int((s > level).sum())
+
+
+def test_T11_interface_map_spectrum_trends():
+    ns = (31, 63, 127)
+    hk1 = [_count_above(n, n + 1.0, 4) for n in ns]              # h k = 1
+    rows4 = [_count_above(n, 20.0, 4) for n in ns]               # overlap 4 rows = 4h
+    width = [_count_above(n, 20.0, 4 * (n + 1) // 32) for n in ns]   # overlap 4/32 of the domain
+    for c in (hk1, rows4):
+        for a, b in zip(c, c[1:]):
+            assert 1.6 < b / a < 2.4, (hk1, rows4)
+    assert max(width) == width[0] and width[-1] < 0.25 * rows4[-1], (width, rows4)
