@@ -33,12 +33,17 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def direction(n: int, present: bool = True):
+def direction(n: int, present: bool = True, scheme: str = "fd"):
     """Line operator pieces for one direction of ``n`` nodes: (X, w, boundary flags).
 
     X is the (halved-at-the-ends) second difference, w the nodal weights and the
     flags mark the two end nodes.  An absent direction (1D problems) contributes
     X = 0, w = 1 and no boundary term.
+
+    scheme "q1" (the bilinear elements of Sec. 3): X is the same (h times the 1D
+    stiffness matrix) and w becomes the consistent 1D mass matrix over h,
+    tridiag(1, 4, 1) / 6 with 2/6 at the two ends.  Its row sums are the FD weights:
+    the FD scheme is Q1 with lumped masses.
     """
     if not present:
         return sp.csr_matrix((1, 1), dtype=np.float64), np.ones(1), np.zeros(1)
@@ -48,10 +53,17 @@ def direction(n: int, present: bool = True):
     main[0] = main[-1] = 1.0
     off = -np.ones(n - 1)
     X = sp.diags([off, main, off], [-1, 0, 1], format="csr")
-    w = np.ones(n)
-    w[0] = w[-1] = 0.5
     bnd = np.zeros(n)
     bnd[0] = bnd[-1] = 1.0
+    if scheme == "q1":
+        d = np.full(n, 4.0 / 6.0)
+        d[0] = d[-1] = 2.0 / 6.0
+        o = np.full(n - 1, 1.0 / 6.0)
+        return X, sp.diags([o, d, o], [-1, 0, 1], format="csr"), bnd
+    if scheme != "fd":
+        raise ValueError("scheme must be 'fd' or 'q1'")
+    w = np.ones(n)
+    w[0] = w[-1] = 0.5
     return X, w, bnd
 
 
@@ -63,6 +75,17 @@ def operator(kh, xdir, ydir) -> sp.csr_matrix:
     """
     Xx, wx, bx = xdir
     Yy, wy, by = ydir
+    if sp.issparse(wy):
+        # Q1: consistent masses; the element wavenumber is one constant
+        khs = np.unique(np.asarray(kh, dtype=np.float64))
+        if khs.size != 1:
+            raise ValueError("the Q1 scheme takes one constant wavenumber")
+        q = float(khs[0])
+        Wx = wx if sp.issparse(wx) else sp.diags(wx)
+        A = (sp.kron(wy, Xx) + sp.kron(Yy, Wx)
+             - (q * q) * sp.kron(wy, Wx)
+             - 1j * q * (sp.kron(wy, sp.diags(bx)) + sp.kron(sp.diags(by), Wx)))
+        return sp.csr_matrix(A, dtype=np.complex128)
     khy = np.broadcast_to(np.asarray(kh, dtype=np.float64), wy.shape)
     Wx, Wy = sp.diags(wx), sp.diags(wy)
     # the weights are 1/2 or 1 and the flags 0 or 1, so with a constant kh every entry
@@ -80,11 +103,15 @@ class Problem:
     Vectors are flattened row-major [S_y][S_x]; S_x = 1 in 1D.
     """
 
-    def __init__(self, dim: int, n: int, k: float, k_rows=None):
+    def __init__(self, dim: int, n: int, k: float, k_rows=None, scheme: str = "fd"):
         """k_rows (optional): the wavenumber of each grid row j = 0..S-1 (layered media,
-        Sec. 3.3); k is then only a label.  Without it every row has k."""
+        Sec. 3.3); k is then only a label.  Without it every row has k.  scheme: "fd"
+        (the weighted 5-point scheme) or "q1" (bilinear elements, one constant k)."""
         if dim not in (1, 2):
             raise ValueError("dim must be 1 or 2")
+        if scheme not in ("fd", "q1"):
+            raise ValueError("scheme must be 'fd' or 'q1'")
+        self.scheme = scheme
         self.dim, self.n, self.k = dim, n, float(k)
         self.S = n + 2
         self.h = 1.0 / (n + 1)
@@ -98,7 +125,9 @@ class Problem:
             if self.k_rows.shape != (self.Sy,) or not np.all(np.isfinite(self.k_rows)) or np.any(self.k_rows < 0):
                 raise ValueError("k_rows must hold one finite k >= 0 per grid row")
         self.kh_rows = self.k_rows * self.h
-        self._xdir = direction(self.Sx, present=(dim == 2))
+        if scheme == "q1" and np.unique(self.k_rows).size != 1:
+            raise ValueError("the Q1 scheme takes one constant wavenumber")
+        self._xdir = direction(self.Sx, present=(dim == 2), scheme=scheme)
 
     @property
     def N(self) -> int:
@@ -106,14 +135,18 @@ class Problem:
 
     def band_operator(self, ra: int, rb: int) -> sp.csr_matrix:
         """A~ on rows [ra, rb): impedance (Robin, zero data) rows at both band ends."""
-        return operator(self.kh_rows[ra:rb], self._xdir, direction(rb - ra))
+        return operator(self.kh_rows[ra:rb], self._xdir, direction(rb - ra, scheme=self.scheme))
 
     def A(self) -> sp.csr_matrix:
         """The global operator A (the band covering every row)."""
         return self.band_operator(0, self.Sy)
 
     def rhs(self, f: np.ndarray, g: np.ndarray) -> np.ndarray:
-        """b = h^2 w_i w_j f + h (w_j gx + w_i gy), flattened row-major."""
+        """b = h^2 w_i w_j f + h (w_j gx + w_i gy), flattened row-major.  For Q1 the
+        weights are the consistent mass matrices: b = h^2 (M_y F M_x^T) + h (edge masses
+        applied to g)."""
+        if self.scheme == "q1":
+            return self._rhs_q1(f, g)
         h = self.h
         _, wx, _ = self._xdir
         _, wy, _ = direction(self.Sy)
@@ -129,4 +162,23 @@ class Problem:
             b[:, -1] += h * wy * g[1]       # side x = 1
             b[0, :] += h * wx * g[2]        # side y = 0, indexed along x
             b[-1, :] += h * wx * g[3]       # side y = 1
+        return b.reshape(-1)
+
+    def _rhs_q1(self, f: np.ndarray, g: np.ndarray) -> np.ndarray:
+        h = self.h
+        _, mx, _ = self._xdir
+        _, my, _ = direction(self.Sy, scheme="q1")
+        f = np.asarray(f, dtype=np.complex128).reshape(self.Sy, self.Sx)
+        g = np.asarray(g, dtype=np.complex128)
+        if self.dim == 1:
+            b = (h * h) * (my @ f)
+            b[0, 0] += h * g[0]                 # a boundary point carries no edge mass
+            b[-1, 0] += h * g[1]
+            return b.reshape(-1)
+        b = (h * h) * (my @ (mx @ f.T).T)
+        g = g.reshape(4, self.S)
+        b[:, 0] += h * (my @ g[0])              # side x = 0, indexed along y
+        b[:, -1] += h * (my @ g[1])             # side x = 1
+        b[0, :] += h * (mx @ g[2])              # side y = 0, indexed along x
+        b[-1, :] += h * (mx @ g[3])             # side y = 1
         return b.reshape(-1)

@@ -199,3 +199,69 @@ def test_layered_operator_complex_symmetric_and_band_rows():
         rows = np.arange(ra * P.Sx, rb * P.Sx)
         inner = np.arange(P.Sx, (rb - ra - 1) * P.Sx)
         assert np.array_equal(At[inner], Ad[np.ix_(rows, rows)][inner]), (ra, rb)
+
+
+# ------------------------------------------------- Q1 bilinear elements (Sec. 3, row f2)
+def test_q1_plane_waves_second_order():
+    def e1(n, k=10.0):
+        P = Problem(1, n, k, scheme="q1")
+        x = np.arange(P.S) * P.h
+        u = direct.solve(P, np.zeros(P.S), np.array([-2j * k, 0.0]))
+        return np.max(np.abs(u - np.exp(1j * k * x)))
+
+    def e2(n, k=6.0, th=0.37):
+        P = Problem(2, n, k, scheme="q1")
+        U, f, g = plane_wave_2d(n, k, th)
+        return np.max(np.abs(direct.solve(P, f, g).reshape(P.S, P.S) - U))
+
+    for e in ([e1(n) for n in (99, 199, 399)], [e2(n) for n in (31, 63, 127)]):
+        assert e[0] < 0.05
+        for a, b in zip(e, e[1:]):
+            assert 3.6 < a / b < 4.4, e
+
+
+def test_q1_discrete_plane_wave_annihilated_by_interior_rows():
+    """Bilinear-element dispersion (Ihlenburg and Babuska): e^{i(tx i + ty j)} solves the
+    interior rows when a (4 + 2 cy) / 6 + px (2 - 2 cy) = (kh)^2 px (4 + 2 cy) / 6 with
+    a = 2 - 2 cos tx, px = (4 + 2 cos tx) / 6, cy = cos ty.  A wrong mass or stiffness
+    entry breaks it; the FD relation does not satisfy it."""
+    n, k = 40, 17.0
+    P = Problem(2, n, k, scheme="q1")
+    kh = k * P.h
+    tx = 0.6 * kh
+    a, px = 2 - 2 * math.cos(tx), (4 + 2 * math.cos(tx)) / 6
+    c0 = a * 4 / 6 + 2 * px - kh * kh * px * 4 / 6
+    c1 = a * 2 / 6 - 2 * px - kh * kh * px * 2 / 6
+    ty = math.acos(-c0 / c1)
+    j = np.arange(P.S)
+    U = np.exp(1j * (tx * j[None, :] + ty * j[:, None]))
+    r = (P.A() @ U.reshape(-1)).reshape(P.S, P.S)
+    assert np.max(np.abs(r[1:-1, 1:-1])) < 1e-12
+    r_fd = (Problem(2, n, k).A() @ U.reshape(-1)).reshape(P.S, P.S)
+    assert np.max(np.abs(r_fd[1:-1, 1:-1])) > 1e-4
+
+
+def test_q1_with_lumped_masses_is_the_fd_operator():
+    """Replacing each consistent 1D mass matrix by the diagonal of its row sums (mass
+    lumping) turns the Q1 operator into the weighted 5-point operator."""
+    from oracle.problem import direction, operator
+    for dim, n in ((1, 30), (2, 20)):
+        P, Q = Problem(dim, n, 9.0, scheme="q1"), Problem(dim, n, 9.0)
+
+        def lump(d):
+            X, w, b = d
+            return (X, np.asarray(w.sum(axis=1)).reshape(-1), b) if hasattr(w, "tocsr") else d
+        A_lumped = operator(P.kh, lump(P._xdir), lump(direction(P.Sy, scheme="q1")))
+        assert abs(A_lumped - Q.A()).max() < 1e-15
+
+
+def test_q1_operator_complex_symmetric_and_band_rows():
+    for dim in (1, 2):
+        P = Problem(dim, 20, 9.0, scheme="q1")
+        A = P.A()
+        assert abs(A - A.T).max() == 0.0
+        ra, rb = 5, 14
+        At = P.band_operator(ra, rb).toarray()
+        rows = np.arange(ra * P.Sx, rb * P.Sx)
+        inner = np.arange(P.Sx, (rb - ra - 1) * P.Sx)
+        assert np.array_equal(At[inner], A.toarray()[np.ix_(rows, rows)][inner])

@@ -70,6 +70,17 @@ def test_T1_layered_medium_one_step_exact(levels):
     assert direct.rel_err(M.precondition(P.rhs(f, g)), direct.solve(P, f, g)) < 1e-10
 
 
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_T1_q1_elements_one_step_exact(levels):
+    """T1 for the bilinear elements of Sec. 3 (9-point coupling between bands)."""
+    n = 26 if levels < 3 else 46
+    P = Problem(2, n, 11.0, scheme="q1")
+    f = random_complex((P.S, P.S), 5)
+    g = random_complex((4, P.S), 6)
+    M = OMethod(P, levels, 2, P.S, 0, seed=9, exact_subsolves=levels > 1)
+    assert direct.rel_err(M.precondition(P.rhs(f, g)), direct.solve(P, f, g)) < 1e-10
+
+
 def _flat_oras_step(P, tree, r):
     """Flat ORAS (no coarse space) over the leaves, by brute force per strip."""
     u = np.zeros_like(r).reshape(P.Sy, P.Sx)
