@@ -207,6 +207,52 @@ class OMethod:
             W = W + self.coarse(0, R - self.apply(0, W))
         return W.reshape(-1)
 
+    def solve_gmres(self, b: np.ndarray, tol: float = 1e-12, restart: int = 40, maxit: int = 400, M=None):
+        """GMRES on the Schwarz-preconditioned system (Sec. 3), right-preconditioned by
+        M (default: `precondition`, one coarse-corrected ORAS step from zero) and
+        restarted every `restart` steps.  Each cycle minimises ||b - A u|| over
+        u_0 + M K(A M, r_0): Arnoldi with modified Gram-Schmidt, the small least-squares
+        problem by a library solve.  The preconditioned vectors are kept (flexible
+        form), so u = u_0 + Z y needs no second application of M.  A cycle ends at the
+        restart length, at a residual estimate below tol, or at a breakdown; the true
+        residual then decides.  Returns (u, steps, history of relative residual
+        estimates, one per step, after the initial 1)."""
+        M = self.precondition if M is None else M
+        u = np.zeros_like(b)
+        nb = np.linalg.norm(b)
+        if nb == 0.0:
+            return u, 0, [0.0]
+        hist = [1.0]
+        steps = 0
+        while steps < maxit:
+            r = b - self.A @ u
+            beta = np.linalg.norm(r)
+            if beta / nb < tol:
+                break
+            V = [r / beta]
+            Z = []
+            H = np.zeros((restart + 1, restart), dtype=np.complex128)
+            y = np.zeros(0, dtype=np.complex128)
+            for j in range(restart):
+                z = M(V[j])
+                Z.append(z)
+                w = self.A @ z
+                for i in range(j + 1):
+                    H[i, j] = np.vdot(V[i], w)
+                    w = w - H[i, j] * V[i]
+                H[j + 1, j] = np.linalg.norm(w)
+                e1 = np.zeros(j + 2, dtype=np.complex128)
+                e1[0] = beta
+                y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+                est = np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y) / nb
+                steps += 1
+                hist.append(est)
+                if est < tol or H[j + 1, j] == 0.0 or steps >= maxit:
+                    break
+                V.append(w / H[j + 1, j])
+            u = u + sum(Z[i] * y[i] for i in range(len(y)))
+        return u, steps, hist
+
     def solve(self, b: np.ndarray, tol: float = 1e-12, maxit: int = 200, u0=None):
         """u^(n) = u^(n-1) + precondition(b - A u^(n-1)) until ||b - Au|| < tol ||b||."""
         u = np.zeros_like(b) if u0 is None else u0.copy()

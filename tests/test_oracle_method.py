@@ -16,6 +16,10 @@ formulas:
 * T8 (Sec. 1): Galerkin orthogonality C^H (f - A u) = 0 after the coarse step.
 * T10 (Sec. 3, n_i): the n_i sub-level iterations of an internal node are a stationary
   iteration for A~_c x = v, so as n_i grows they converge to the band's exact solve.
+* T12 (Sec. 3, GMRES): restarted GMRES right-preconditioned by the hierarchical step.
+  With the identity preconditioner it ends in at most N steps with A^{-1} b.  Its
+  residual estimates never increase.  In a layered medium where the stationary
+  iteration diverges, it reaches A^{-1} b.
 * T11 (Sec. 2, Fig. 4 discussion): the spectrum of the interface map follows the trends
   the paper reports.  At hk = 1 the number of singular values above a fixed level grows
   about linearly with k.  At fixed k it grows like 1/h when the overlap is a fixed number
@@ -246,3 +250,26 @@ def test_T11_interface_map_spectrum_trends():
         for a, b in zip(c, c[1:]):
             assert 1.6 < b / a < 2.4, (hk1, rows4)
     assert max(width) == width[0] and width[-1] < 0.25 * rows4[-1], (width, rows4)
+
+
+def test_T12_gmres_identity_preconditioner_ends_within_n_steps():
+    P = Problem(1, 28, 9.0)
+    M = OMethod(P, 1, 4, 1, 0, seed=1)
+    f, g = random_complex((P.S,), 3), random_complex((2,), 4)
+    u, steps, _ = M.solve_gmres(P.rhs(f, g), tol=1e-13, restart=P.N + 5, maxit=P.N + 5, M=lambda v: v)
+    assert steps <= P.N
+    assert direct.rel_err(u, direct.solve(P, f, g)) < 1e-12
+
+
+def test_T12_gmres_solves_the_layered_medium_where_the_stationary_iteration_diverges():
+    n = 63
+    P = Problem(2, n, n + 1.0, k_rows=layered_wavenumber(n, n + 1.0, 5.0))   # omega h = 1, c0 = 5
+    f, g = random_complex((P.S, P.S), 17), np.zeros((4, P.S), complex)
+    b = P.rhs(f, g)
+    M = OMethod(P, 2, 2, 16, 10, seed=1)
+    _, _, hist_s = M.solve(b, tol=1e-8, maxit=12)
+    assert hist_s[-1] > 10.0                                   # stationary: diverges
+    u, steps, hist = M.solve_gmres(b, tol=1e-9, restart=40, maxit=120)
+    assert all(y <= x * (1 + 1e-10) for x, y in zip(hist, hist[1:]))
+    assert hist[-1] < 1e-9 and steps < 120
+    assert direct.rel_err(u, direct.solve(P, f, g)) < 1e-7
