@@ -265,3 +265,24 @@ def test_q1_operator_complex_symmetric_and_band_rows():
         rows = np.arange(ra * P.Sx, rb * P.Sx)
         inner = np.arange(P.Sx, (rb - ra - 1) * P.Sx)
         assert np.array_equal(At[inner], A.toarray()[np.ix_(rows, rows)][inner])
+
+
+def test_layered_wavenumber_profile():
+    """c alternates 1, c0, 1, ... from y = 0 over equal layers; a row on a layer boundary
+    takes the mean of k^2 over its two layers; the top row belongs to the last layer."""
+    omega, c0 = 32.0, 5.0
+    k = layered_wavenumber(31, omega, c0)          # h = 1/32: four rows per layer
+    kb = math.sqrt(0.5 * (omega ** 2 + (omega / c0) ** 2))
+    assert k.shape == (33,)
+    for j in range(33):
+        if j % 4 == 0 and 0 < j < 32:
+            assert k[j] == pytest.approx(kb, rel=1e-15), j
+        else:
+            layer = min(j // 4, 7)
+            assert k[j] == (omega if layer % 2 == 0 else omega / c0), j
+    # rows that miss the layer boundaries take their layer's value only
+    k2 = layered_wavenumber(40, 41.0, 2.0)           # h = 1/41: no row on a boundary
+    assert set(np.round(k2, 12)) == {41.0, 20.5}
+    # y_j = j h rounds below the boundary for some n; the profile still sees the boundary
+    k3 = layered_wavenumber(39, 40.0, 3.0)           # h = 1/40: rows 5, 10, ... on boundaries
+    assert all(k3[j] == pytest.approx(math.sqrt(0.5 * (40.0 ** 2 + (40.0 / 3) ** 2))) for j in range(5, 40, 5))
