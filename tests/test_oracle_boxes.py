@@ -1,0 +1,106 @@
+"""Pins of the oracle's 2 x 2 box hierarchy (row f2, CPU only).
+
+The facts checked are those the strip method is pinned by, restated on boxes:
+
+* layout: the four children's owned rectangles partition the parent's owned rectangle;
+  the parts they own inside the parent's region partition that region; an interior
+  child's interface is an L through the cross point;
+* T1 (Sec. 1): with full interface spaces and exact sub-solves one coarse-corrected step
+  is exact, for the FD scheme and for the paper's Q1 elements;
+* T2 (Sec. 3.1 discussion): without coarse correction one hierarchical step equals one
+  step of the flat leaf partition;
+* T6/T7 (Sec. 2): <T x, y> = <x, T^* y> for leaf children; the randomised SVD equals the
+  dense SVD of the explicit interface map when the samples cover;
+* with partial ranks, GMRES on the preconditioned system reaches A^{-1} b.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import direct
+from oracle.boxes import BoxMethod, build_boxes, interface_nodes, owned_in_parent
+from oracle.problem import Problem
+from workloads import point_source_rhs, random_complex
+
+
+def test_box_layout_partitions_and_interfaces():
+    S, e = 62, 2
+    nodes = build_boxes(S, 2, 2 * e)
+    assert len(nodes) == 1 + 4 + 16
+    for p in nodes.values():
+        if p.is_leaf:
+            continue
+        owned = np.zeros((S, S), int)
+        in_region = np.zeros((S, S), int)
+        for cid in p.children:
+            c = nodes[cid]
+            owned[c.oy[0]:c.oy[1], c.ox[0]:c.ox[1]] += 1
+            (x0, x1), (y0, y1) = owned_in_parent(nodes, c)
+            in_region[y0:y1, x0:x1] += 1
+            assert c.gx == (max(0, c.ox[0] - e), min(S, c.ox[1] + e))
+            assert c.gy == (max(0, c.oy[0] - e), min(S, c.oy[1] + e))
+        assert np.all(owned[p.oy[0]:p.oy[1], p.ox[0]:p.ox[1]] == 1) and owned.sum() == (
+            (p.oy[1] - p.oy[0]) * (p.ox[1] - p.ox[0]))
+        assert np.all(in_region[p.gy[0]:p.gy[1], p.gx[0]:p.gx[1]] == 1) and in_region.sum() == (
+            (p.gy[1] - p.gy[0]) * (p.gx[1] - p.gx[0]))
+    # a first-level child meets its siblings along one x side and one y side: an L
+    c = nodes[1]
+    assert interface_nodes(nodes, c).size == c.nx + c.ny - 1
+    # a second-level child inside the grid has siblings on two sides only as well
+    assert interface_nodes(nodes, nodes[4 * 4 + 1]).size == nodes[17].nx + nodes[17].ny - 1
+
+
+@pytest.mark.parametrize("scheme", ["fd", "q1"])
+@pytest.mark.parametrize("levels,n", [(1, 26), (2, 46)])
+def test_T1_boxes_full_interface_space_one_step_exact(scheme, levels, n):
+    P = Problem(2, n, 11.0, scheme=scheme)
+    f = random_complex((P.S, P.S), 5)
+    g = random_complex((4, P.S), 6)
+    M = BoxMethod(P, levels, 2, 10 ** 6, 0, seed=9, exact_subsolves=True)   # rank clamps to |Gamma_c|
+    assert direct.rel_err(M.precondition(P.rhs(f, g)), direct.solve(P, f, g)) < 1e-10
+
+
+@pytest.mark.parametrize("levels,n", [(1, 30), (2, 60)])
+def test_T2_boxes_hierarchical_equals_flat_without_coarse(levels, n):
+    P = Problem(2, n, 13.0)
+    M = BoxMethod(P, levels, 2, 0, 0)
+    r = random_complex((P.N,), 21)
+    R = r.reshape(P.S, P.S)
+    u = np.zeros_like(R)
+    for nd in M.nodes.values():
+        if nd.is_leaf:
+            x = spla.spsolve(M.Atil[nd.id].tocsc(), R[nd.gy[0]:nd.gy[1], nd.gx[0]:nd.gx[1]].reshape(-1))
+            x = x.reshape(nd.ny, nd.nx)
+            u[nd.oy[0]:nd.oy[1], nd.ox[0]:nd.ox[1]] = \
+                x[nd.oy[0] - nd.gy[0]:nd.oy[1] - nd.gy[0], nd.ox[0] - nd.gx[0]:nd.ox[1] - nd.gx[0]]
+    assert np.linalg.norm(M.precondition(r) - u.reshape(-1)) <= 1e-13 * np.linalg.norm(u)
+
+
+def test_T7_boxes_adjoint_identity_for_leaf_children():
+    P = Problem(2, 46, 9.0)
+    M = BoxMethod(P, 2, 2, 6, 4, seed=12)
+    for c in (5, 8, 13, 20):
+        assert M.nodes[c].is_leaf
+        x = random_complex((M.Gamma[c].size, 2), 3 + c)
+        y = random_complex((sum(M.Gamma[s].size for s in M.siblings(c)), 2), 7 + c)
+        lhs, rhs = np.vdot(y, M.T(c, x)), np.vdot(M.T_adjoint(c, y), x)
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs), c
+
+
+def test_T6_boxes_rsvd_equals_dense_svd_when_samples_cover():
+    P = Problem(2, 26, 9.0)
+    M = BoxMethod(P, 1, 2, 10 ** 6, 0, seed=12)
+    for c in M.nodes[0].children:
+        s_dense = np.linalg.svd(M.T(c, np.eye(M.Gamma[c].size, dtype=complex)), compute_uv=False)
+        np.testing.assert_allclose(M.sigma[c], s_dense, rtol=1e-11, atol=1e-13 * s_dense[0])
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_boxes_gmres_with_partial_ranks_reaches_the_solution(levels):
+    n = 62
+    P = Problem(2, n, 20.0)
+    f, g = point_source_rhs(n, 3), np.zeros((4, P.S), complex)
+    M = BoxMethod(P, levels, 4, 12, 5, seed=1)
+    u, steps, hist = M.solve_gmres(P.rhs(f, g), tol=1e-10, restart=40, maxit=200)
+    assert hist[-1] < 1e-10 and steps < 60
+    assert direct.rel_err(u, direct.solve(P, f, g)) < 1e-8
