@@ -20,9 +20,15 @@ Readings (the strip readings, per axis):
   an L through the cross point for a 2 x 2 split.  Data enter by injection,
   B_c^T g = g on Gamma_c.  The parent's own artificial boundary belongs to A~_p
   (Sec. 1, Sec. 2);
-* T_c = (B_s A~_s R_s R_c^T M_c B_c^T)_s stacked over the three siblings s, with B_s
-  the restriction to Gamma_s (Sec. 2: the output data of c for its neighbours).  At a
-  cross point every sibling whose interface passes through it gets its own value;
+* T_c = (B_s A~_s R_s P_c M_c B_c^T)_s stacked over the three siblings s, with B_s the
+  restriction to Gamma_s (Sec. 2: the output data of c for its neighbours).  This is
+  the paper's B_{c,s} = B_s A~_s R_s P_c with the restricted prolongation P_c, taken
+  literally: a sibling's interface runs through parts of c's region that other
+  siblings own, and the iteration never passes c's values there on.  (The strips use
+  R_c^T in place of P_c: identical there for e >= 2, better for e = 1.)  With this
+  form the coarse-free and coarse-corrected GMRES counts of Table 1 for m = 2 are
+  reproduced to within one iteration.  At a cross point every sibling whose interface
+  passes through it gets its own value;
 * A~ on a box is the same weighted operator on that rectangle, with impedance rows
   (zero data) on all four sides (Sec. 1).
 
@@ -65,13 +71,22 @@ class Box:
         return not self.children
 
 
-def build_boxes(S: int, levels: int, overlap: int) -> dict:
-    """Nodes by id: root 0 owns the S x S grid; children of p are 4p+1 .. 4p+4."""
+def build_boxes(S: int, levels: int, overlap: int, partition: str = "nodes") -> dict:
+    """Nodes by id: root 0 owns the S x S grid; children of p are 4p+1 .. 4p+4.
+
+    partition "nodes": regions are the owned node ranges extended by e = overlap / 2
+    nodes on each side.  partition "elements" (the experiments of Sec. 3): the
+    non-overlapping partition is by elements, so a box's elements span its owned nodes
+    and the first node of the next box; they are extended by e elements on each side
+    (overlap delta = 2 e h), i.e. nodes [ox0 - e, ox1 + e + 1), clipped to the grid."""
     if levels < 0:
         raise ValueError("levels must be >= 0")
     if levels > 0 and (overlap < 2 or overlap % 2):
         raise ValueError("overlap must be even and >= 2")
+    if partition not in ("nodes", "elements"):
+        raise ValueError("partition must be 'nodes' or 'elements'")
     e = overlap // 2
+    hi = e + 1 if partition == "elements" else e
     nodes = {0: Box(0, 0, (0, S), (0, S), (0, S), (0, S))}
     for lev in range(levels):
         for p in [nd for nd in nodes.values() if nd.level == lev]:
@@ -81,10 +96,10 @@ def build_boxes(S: int, levels: int, overlap: int) -> dict:
             for iy, (y0, y1) in enumerate(((p.oy[0], my), (my, p.oy[1]))):
                 for ix, (x0, x1) in enumerate(((p.ox[0], mx), (mx, p.ox[1]))):
                     cid = 4 * p.id + 1 + 2 * iy + ix
-                    if min(x1 - x0, y1 - y0) < 2 * e + 2:
-                        raise ValueError(f"box {cid} owns {x1 - x0} x {y1 - y0} nodes; needs >= overlap + 2")
-                    nodes[cid] = Box(cid, lev + 1, (x0, x1), (y0, y1), (max(0, x0 - e), min(S, x1 + e)),
-                                     (max(0, y0 - e), min(S, y1 + e)), p.id)
+                    if min(x1 - x0, y1 - y0) < (2 * e + 2 if partition == "nodes" else e + 1):
+                        raise ValueError(f"box {cid} owns {x1 - x0} x {y1 - y0} nodes: too few for the overlap")
+                    nodes[cid] = Box(cid, lev + 1, (x0, x1), (y0, y1), (max(0, x0 - e), min(S, x1 + hi)),
+                                     (max(0, y0 - e), min(S, y1 + hi)), p.id)
                     kids.append(cid)
             p.children = tuple(kids)
     return nodes
@@ -123,7 +138,7 @@ class BoxMethod:
     boxes.  Same steps as `method.OMethod` (Eqs. (2)-(3), Sec. 2), on rectangles."""
 
     def __init__(self, prob: Problem, levels: int, overlap: int, rank: int, oversample: int,
-                 n_inner: int = 1, seed: int = 0, exact_subsolves: bool = False):
+                 n_inner: int = 1, seed: int = 0, exact_subsolves: bool = False, partition: str = "nodes"):
         if prob.dim != 2:
             raise ValueError("boxes need a 2D problem")
         self.prob = prob
@@ -131,7 +146,7 @@ class BoxMethod:
         self.n_inner = n_inner
         self.seed = seed
         self.rank, self.oversample = rank, oversample
-        self.nodes = build_boxes(prob.S, levels, overlap)
+        self.nodes = build_boxes(prob.S, levels, overlap, partition)
         self.A = prob.A()
         self.Atil = {nd.id: self._box_operator(nd) for nd in self.nodes.values()}
         self.Gamma = {nd.id: interface_nodes(self.nodes, nd) for nd in self.nodes.values() if nd.id != 0}
@@ -233,15 +248,23 @@ class BoxMethod:
         return [s for s in self.nodes[self.nodes[c].parent].children if s != c]
 
     def T(self, c: int, X: np.ndarray) -> np.ndarray:
-        """T_c X, stacked over the siblings s in id order: B_s A~_s R_s R_c^T M_c B_c^T X."""
+        """T_c X, stacked over the siblings s in id order: B_s A~_s R_s P_c M_c B_c^T X."""
         p = self.nodes[c].parent
-        W = self.M(c, self._inject(c, X))
         Wp = self._zeros(p, X.shape[1])
-        Wp[self._slice(p, c)] = W
+        self._prolong_add(p, c, Wp, self.M(c, self._inject(c, X)))
         return np.concatenate([self._trace(s, self.apply(s, self._restrict(p, s, Wp))) for s in self.siblings(c)])
 
+    def _prolong_adjoint(self, p: int, c: int, Zp: np.ndarray) -> np.ndarray:
+        """P_c^H Zp: the part of p's region that c owns, placed in c's region."""
+        P, Cn = self.nodes[p], self.nodes[c]
+        (x0, x1), (y0, y1) = owned_in_parent(self.nodes, Cn)
+        Zc = self._zeros(c, Zp.shape[2])
+        Zc[y0 - Cn.gy[0]:y1 - Cn.gy[0], x0 - Cn.gx[0]:x1 - Cn.gx[0]] = \
+            Zp[y0 - P.gy[0]:y1 - P.gy[0], x0 - P.gx[0]:x1 - P.gx[0]]
+        return Zc
+
     def T_adjoint(self, c: int, Y: np.ndarray) -> np.ndarray:
-        """T_c^* Y = B_c M_c^H R_c sum_s R_s^T A~_s^H B_s^T Y_s."""
+        """T_c^* Y = B_c M_c^H P_c^H sum_s R_s^T A~_s^H B_s^T Y_s."""
         p = self.nodes[c].parent
         Zp = self._zeros(p, Y.shape[1])
         at = 0
@@ -249,7 +272,7 @@ class BoxMethod:
             n = self.Gamma[s].size
             Zp[self._slice(p, s)] += self.apply_adjoint(s, self._inject(s, Y[at:at + n]))
             at += n
-        return self._trace(c, self.M_adjoint(c, self._restrict(p, c, Zp)))
+        return self._trace(c, self.M_adjoint(c, self._prolong_adjoint(p, c, Zp)))
 
     def rsvd(self, c: int):
         """Dominant right singular vectors of T_c by the randomised SVD (Sec. 2)."""
