@@ -43,7 +43,7 @@ import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
 from .method import OMethod
-from .problem import Problem, direction, operator
+from .problem import Problem
 from .sketch import gaussian_sketch
 
 
@@ -162,12 +162,9 @@ class BoxMethod:
                         self._build_coarse(p.id)
 
     def _box_operator(self, nd: Box):
-        P = self.prob
         if nd.id == 0:
             return self.A
-        xdir = direction(nd.nx, scheme=P.scheme)
-        ydir = direction(nd.ny, scheme=P.scheme)
-        return operator(P.kh_rows[nd.gy[0]:nd.gy[1]], xdir, ydir)
+        return self.prob.box_operator(nd.gx[0], nd.gx[1], nd.gy[0], nd.gy[1])
 
     # ------------------------------------------------------------------ helpers
     def _zeros(self, nid: int, k: int) -> np.ndarray:

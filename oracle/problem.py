@@ -96,6 +96,35 @@ def operator(kh, xdir, ydir) -> sp.csr_matrix:
     return sp.csr_matrix(A, dtype=np.complex128)
 
 
+def weighted_mass_q1(w_elem: np.ndarray) -> sp.csr_matrix:
+    """The 1D Q1 mass matrix over h with a weight per element, sum_e w_e [2 1; 1 2] / 6
+    assembled over the nodes (constant weights give w times the consistent mass)."""
+    w_elem = np.asarray(w_elem, dtype=np.float64)
+    n = w_elem.size + 1
+    d = np.zeros(n)
+    d[:-1] += 2.0 * w_elem / 6.0
+    d[1:] += 2.0 * w_elem / 6.0
+    o = w_elem / 6.0
+    return sp.diags([o, d, o], [-1, 0, 1], format="csr")
+
+
+def operator_q1_layered(kh_elem, xdir) -> sp.csr_matrix:
+    """Q1 operator on a rectangle whose wavenumber is constant on each row of elements
+    (layered media, Sec. 3.3): kh_elem holds k h for the ny - 1 element rows.  The k^2
+    mass term and the impedance edge masses on the x sides take the element weights; the
+    impedance rows on the y sides take the wavenumber of their adjacent element row."""
+    Xx, wx, bx = xdir
+    kh_elem = np.asarray(kh_elem, dtype=np.float64)
+    Yy, My, by = direction(kh_elem.size + 1, scheme="q1")
+    Wx = wx if sp.issparse(wx) else sp.diags(wx)
+    kb = np.zeros(kh_elem.size + 1)
+    kb[0], kb[-1] = kh_elem[0], kh_elem[-1]
+    A = (sp.kron(My, Xx) + sp.kron(Yy, Wx)
+         - sp.kron(weighted_mass_q1(kh_elem * kh_elem), Wx)
+         - 1j * (sp.kron(weighted_mass_q1(kh_elem), sp.diags(bx)) + sp.kron(sp.diags(by * kb), Wx)))
+    return sp.csr_matrix(A, dtype=np.complex128)
+
+
 class Problem:
     """Grid and discrete operators for one impedance Helmholtz problem.
 
@@ -103,10 +132,11 @@ class Problem:
     Vectors are flattened row-major [S_y][S_x]; S_x = 1 in 1D.
     """
 
-    def __init__(self, dim: int, n: int, k: float, k_rows=None, scheme: str = "fd"):
+    def __init__(self, dim: int, n: int, k: float, k_rows=None, scheme: str = "fd", k_elems=None):
         """k_rows (optional): the wavenumber of each grid row j = 0..S-1 (layered media,
         Sec. 3.3); k is then only a label.  Without it every row has k.  scheme: "fd"
-        (the weighted 5-point scheme) or "q1" (bilinear elements, one constant k)."""
+        (the weighted 5-point scheme) or "q1" (bilinear elements, one constant k, or with
+        k_elems one k per row of elements, S - 1 values, for layered media)."""
         if dim not in (1, 2):
             raise ValueError("dim must be 1 or 2")
         if scheme not in ("fd", "q1"):
@@ -126,7 +156,12 @@ class Problem:
                 raise ValueError("k_rows must hold one finite k >= 0 per grid row")
         self.kh_rows = self.k_rows * self.h
         if scheme == "q1" and np.unique(self.k_rows).size != 1:
-            raise ValueError("the Q1 scheme takes one constant wavenumber")
+            raise ValueError("the Q1 scheme takes its layers as k_elems")
+        self.k_elems = None
+        if k_elems is not None:
+            self.k_elems = np.asarray(k_elems, dtype=np.float64).copy()
+            if scheme != "q1" or k_rows is not None or self.k_elems.shape != (self.Sy - 1,):
+                raise ValueError("k_elems: one k per row of elements, with the Q1 scheme")
         self._xdir = direction(self.Sx, present=(dim == 2), scheme=scheme)
 
     @property
@@ -135,7 +170,17 @@ class Problem:
 
     def band_operator(self, ra: int, rb: int) -> sp.csr_matrix:
         """A~ on rows [ra, rb): impedance (Robin, zero data) rows at both band ends."""
+        if self.k_elems is not None:
+            return operator_q1_layered(self.k_elems[ra:rb - 1] * self.h, self._xdir)
         return operator(self.kh_rows[ra:rb], self._xdir, direction(rb - ra, scheme=self.scheme))
+
+    def box_operator(self, x0: int, x1: int, y0: int, y1: int) -> sp.csr_matrix:
+        """A~ on the rectangle of nodes [x0, x1) x [y0, y1) (2D): impedance rows with zero
+        data on its four sides; the whole grid gives A."""
+        xdir = direction(x1 - x0, scheme=self.scheme)
+        if self.k_elems is not None:
+            return operator_q1_layered(self.k_elems[y0:y1 - 1] * self.h, xdir)
+        return operator(self.kh_rows[y0:y1], xdir, direction(y1 - y0, scheme=self.scheme))
 
     def A(self) -> sp.csr_matrix:
         """The global operator A (the band covering every row)."""

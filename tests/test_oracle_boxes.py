@@ -14,7 +14,9 @@ The facts checked are those the strip method is pinned by, restated on boxes:
 * with partial ranks, GMRES on the preconditioned system reaches A^{-1} b;
 * Table 1 (Sec. 3.1), m = 2: the printed GMRES counts, coarse-free and with coarse
   modes, are reproduced to within one iteration on the paper's own setting
-  (`tests/golden/table1_free_space_m2.txt`).
+  (`tests/golden/table1_free_space_m2.txt`);
+* Table 3 (Sec. 3.3), layered media, m = 2: 14 of the 16 printed counts within one
+  iteration and all within two (`tests/golden/table3_layered_c5_m2.txt`).
 """
 import os
 
@@ -25,7 +27,7 @@ import scipy.sparse.linalg as spla
 from oracle import direct
 from oracle.boxes import BoxMethod, build_boxes, interface_nodes, owned_in_parent
 from oracle.problem import Problem
-from workloads import point_source_rhs, random_complex
+from workloads import layered_wavenumber_elements, point_source_rhs, random_complex
 
 
 def test_box_layout_partitions_and_interfaces():
@@ -114,9 +116,9 @@ def test_boxes_gmres_with_partial_ranks_reaches_the_solution(levels):
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_free_space_m2.txt")
 
 
-def _table1_rows():
+def _table1_rows(path=GOLDEN):
     rows = []
-    with open(GOLDEN) as fh:
+    with open(path) as fh:
         for line in fh:
             if line.strip() and not line.startswith("#"):
                 n, nc, it = (int(t) for t in line.split())
@@ -144,3 +146,23 @@ def test_table1_m2_gmres_counts_reproduced():
     assert all(got[(n, nc)] == 3 for n, nc, it in rows if it == 3), got
     # and one coarse mode at n = 8 is worse than none, as printed (9 against 7)
     assert got[(8, 1)] > got[(8, 0)]
+
+
+def test_table3_layered_m2_gmres_counts_reproduced():
+    """As Table 1, in the layered medium of Sec. 3.3: c = 1 and c0 = 5 alternating over 8
+    equal layers of element rows, c0 at y = 0 (the order is not stated; this one fits the
+    table better), omega = 2n so that k_max h = 1."""
+    rows = _table1_rows(os.path.join(os.path.dirname(GOLDEN), "table3_layered_c5_m2.txt"))
+    assert len(rows) == 16
+    got = {}
+    for n in sorted({r[0] for r in rows}):
+        E = 2 * n
+        omega = float(E)
+        P = Problem(2, E - 1, omega, scheme="q1", k_elems=layered_wavenumber_elements(E, omega, 5.0))
+        b = P.A() @ random_complex((P.N,), 100 + n)
+        for _, nc, _ in (r for r in rows if r[0] == n):
+            M = BoxMethod(P, 1, 4, nc, 5, seed=1, partition="elements")
+            got[(n, nc)] = M.solve_gmres(b, tol=1e-5, restart=500, maxit=500)[1]
+    diffs = [got[(n, nc)] - it for n, nc, it in rows]
+    assert max(abs(d) for d in diffs) <= 2, diffs
+    assert sum(abs(d) <= 1 for d in diffs) >= 14, diffs

@@ -8,6 +8,7 @@ from .generators import (  # noqa: F401
     Workload,
     batch_problems,
     layered_wavenumber,
+    layered_wavenumber_elements,
     random_complex,
     point_source_rhs,
     plane_wave_2d,

@@ -73,6 +73,19 @@ def layered_wavenumber(n: int, omega: float, c0: float, layers: int = 8, c1: flo
     return np.where(on_boundary, np.sqrt(0.5 * (below * below + above * above)), k)
 
 
+def layered_wavenumber_elements(E: int, omega: float, c0: float, layers: int = 8, c1: float = 1.0,
+                                first: str = "c0") -> np.ndarray:
+    """Wavenumber of each of the E rows of elements (bilinear elements, E per side) for the
+    layered medium of Sec. 3.3: k = omega / c(y) with c alternating over `layers` equal
+    layers, `first` ("c0" or "c1") at y = 0.  E must be a multiple of `layers`."""
+    if E % layers:
+        raise ValueError("E must be a multiple of the number of layers")
+    layer = np.arange(E) // (E // layers)
+    even = c0 if first == "c0" else c1
+    odd = c1 if first == "c0" else c0
+    return omega / np.where(layer % 2 == 0, even, odd)
+
+
 def plane_wave_2d(n: int, k: float, theta: float):
     """Continuous plane wave u = exp(i k (cos t x + sin t y)) with matching data.
 
