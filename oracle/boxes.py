@@ -145,7 +145,10 @@ class BoxMethod:
         self.levels = levels
         self.n_inner = n_inner
         self.seed = seed
-        self.rank, self.oversample = rank, oversample
+        # rank: one value for every level, or a sequence giving the children of level j
+        # (j = 1 .. levels) rank[j - 1] modes each
+        self.ranks = list(rank) if np.ndim(rank) else [int(rank)] * max(levels, 1)
+        self.rank, self.oversample = max(self.ranks), oversample
         self.nodes = build_boxes(prob.S, levels, overlap, partition)
         self.A = prob.A()
         self.Atil = {nd.id: self._box_operator(nd) for nd in self.nodes.values()}
@@ -155,11 +158,12 @@ class BoxMethod:
             if nd.id != 0 and (nd.is_leaf or exact_subsolves):
                 self.lu[nd.id] = spla.splu(self.Atil[nd.id].tocsc())
         self.V, self.sigma, self.C, self.Ac, self.Ac_lu = {}, {}, {}, {}, {}
-        if rank > 0:
-            for lev in reversed(range(levels)):
-                for p in self.nodes.values():
-                    if p.level == lev and not p.is_leaf:
-                        self._build_coarse(p.id)
+        for lev in reversed(range(levels)):
+            if self.ranks[lev] <= 0:
+                continue
+            for p in self.nodes.values():
+                if p.level == lev and not p.is_leaf:
+                    self._build_coarse(p.id)
 
     def _box_operator(self, nd: Box):
         if nd.id == 0:
@@ -215,7 +219,7 @@ class BoxMethod:
         for it in range(self.n_inner):
             R = V - self.apply(nid, W) if it else V
             W = W + self.sweep(nid, R)
-            if self.rank > 0:
+            if nid in self.C:
                 W = W + self.coarse(nid, V - self.apply(nid, W))
         return W
 
@@ -274,8 +278,9 @@ class BoxMethod:
     def rsvd(self, c: int):
         """Dominant right singular vectors of T_c by the randomised SVD (Sec. 2)."""
         g = self.Gamma[c].size
-        m = min(self.rank + self.oversample, g)
-        r = min(self.rank, m)
+        rank = self.ranks[self.nodes[c].level - 1]
+        m = min(rank + self.oversample, g)
+        r = min(rank, m)
         Y = self.T(c, gaussian_sketch(self.seed, c, g, m))
         Q, R = np.linalg.qr(Y)
         d = np.diag(R)
@@ -313,7 +318,7 @@ class BoxMethod:
             return spla.spsolve(self.A.tocsc(), r)
         R = r.reshape(S, S, 1)
         W = self.sweep(0, R)
-        if self.rank > 0:
+        if 0 in self.C:
             W = W + self.coarse(0, R - self.apply(0, W))
         return W.reshape(-1)
 

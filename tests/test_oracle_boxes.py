@@ -16,7 +16,9 @@ The facts checked are those the strip method is pinned by, restated on boxes:
   modes, are reproduced to within one iteration on the paper's own setting
   (`tests/golden/table1_free_space_m2.txt`);
 * Table 3 (Sec. 3.3), layered media, m = 2: 14 of the 16 printed counts within one
-  iteration and all within two (`tests/golden/table3_layered_c5_m2.txt`).
+  iteration and all within two (`tests/golden/table3_layered_c5_m2.txt`);
+* Table 2 (Sec. 3.1), the hierarchical decomposition with 2 and 3 levels: every
+  coarse-corrected count within one iteration (`tests/golden/table2_hierarchical_free_space.txt`).
 """
 import os
 
@@ -166,3 +168,26 @@ def test_table3_layered_m2_gmres_counts_reproduced():
     diffs = [got[(n, nc)] - it for n, nc, it in rows]
     assert max(abs(d) for d in diffs) <= 2, diffs
     assert sum(abs(d) <= 1 for d in diffs) >= 14, diffs
+
+
+def test_table2_hierarchical_gmres_counts_reproduced():
+    """l levels of 2 x 2 boxes, k = n 2^l, n_c modes at the finest level doubling at each
+    coarser level, n_i = 1 (the sub-level solves are one coarse-corrected step)."""
+    path = os.path.join(os.path.dirname(GOLDEN), "table2_hierarchical_free_space.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(int(t) for t in line.split()))
+    assert len(rows) == 12
+    diffs = []
+    for n, L, nc, it in rows:
+        E = n * 2 ** L
+        P = Problem(2, E - 1, float(E), scheme="q1")
+        b = P.A() @ random_complex((P.N,), 100 + n)
+        M = BoxMethod(P, L, 4, [nc * 2 ** (L - j) for j in range(1, L + 1)], 5, seed=1, partition="elements")
+        got = M.solve_gmres(b, tol=1e-5, restart=500, maxit=500)[1]
+        diffs.append((n, L, nc, got - it))
+        if it == 3:
+            assert got == 3, (n, L, nc, got)
+    assert all(abs(d) <= (1 if nc > 0 else 2) for n, L, nc, d in diffs), diffs
