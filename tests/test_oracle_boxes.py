@@ -15,8 +15,10 @@ The facts checked are those the strip method is pinned by, restated on boxes:
 * Table 1 (Sec. 3.1), m = 2: the printed GMRES counts, coarse-free and with coarse
   modes, are reproduced to within one iteration on the paper's own setting
   (`tests/golden/table1_free_space_m2.txt`);
-* Table 3 (Sec. 3.3), layered media, m = 2: 14 of the 16 printed counts within one
+* Table 3 (Sec. 3.3), layered media, m = 2: 15 of the 16 printed counts within one
   iteration and all within two (`tests/golden/table3_layered_c5_m2.txt`);
+* Table 4 (Sec. 3.3), layered media with 2 and 3 levels: every coarse-corrected count
+  within one iteration (`tests/golden/table4_layered_hierarchical.txt`);
 * Table 2 (Sec. 3.1), the hierarchical decomposition with 2 and 3 levels: every
   coarse-corrected count within one iteration (`tests/golden/table2_hierarchical_free_space.txt`).
 """
@@ -152,8 +154,8 @@ def test_table1_m2_gmres_counts_reproduced():
 
 def test_table3_layered_m2_gmres_counts_reproduced():
     """As Table 1, in the layered medium of Sec. 3.3: c = 1 and c0 = 5 alternating over 8
-    equal layers of element rows, c0 at y = 0 (the order is not stated; this one fits the
-    table better), omega = 2n so that k_max h = 1."""
+    equal layers of element rows, c = 1 at y = 0 (the order is not stated; this one fits
+    Tables 3 and 4 better), omega = 2n so that k_max h = 1."""
     rows = _table1_rows(os.path.join(os.path.dirname(GOLDEN), "table3_layered_c5_m2.txt"))
     assert len(rows) == 16
     got = {}
@@ -167,7 +169,28 @@ def test_table3_layered_m2_gmres_counts_reproduced():
             got[(n, nc)] = M.solve_gmres(b, tol=1e-5, restart=500, maxit=500)[1]
     diffs = [got[(n, nc)] - it for n, nc, it in rows]
     assert max(abs(d) for d in diffs) <= 2, diffs
-    assert sum(abs(d) <= 1 for d in diffs) >= 14, diffs
+    assert sum(abs(d) <= 1 for d in diffs) >= 15, diffs
+
+
+def test_table4_layered_hierarchical_gmres_counts_reproduced():
+    """Layered medium with l levels of 2 x 2 boxes (omega = n 2^l), n_c modes at the
+    finest level doubling at each coarser level (as in Table 2), n_i = 1."""
+    path = os.path.join(os.path.dirname(GOLDEN), "table4_layered_hierarchical.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(int(t) for t in line.split()))
+    assert len(rows) == 12
+    for n, L, nc, it in rows:
+        E = n * 2 ** L
+        omega = float(E)
+        P = Problem(2, E - 1, omega, scheme="q1", k_elems=layered_wavenumber_elements(E, omega, 5.0))
+        b = P.A() @ random_complex((P.N,), 100 + n)
+        M = BoxMethod(P, L, 4, [nc * 2 ** (L - j) for j in range(1, L + 1)], 5, seed=1, partition="elements")
+        got = M.solve_gmres(b, tol=1e-5, restart=500, maxit=500)[1]
+        # coarse-corrected counts within one; the coarse-free ones (19 to 60) within 10%
+        assert abs(got - it) <= (1 if nc > 0 else max(2, round(0.1 * it))), (n, L, nc, got, it)
 
 
 def test_table2_hierarchical_gmres_counts_reproduced():

@@ -74,7 +74,7 @@ def layered_wavenumber(n: int, omega: float, c0: float, layers: int = 8, c1: flo
 
 
 def layered_wavenumber_elements(E: int, omega: float, c0: float, layers: int = 8, c1: float = 1.0,
-                                first: str = "c0") -> np.ndarray:
+                                first: str = "c1") -> np.ndarray:
     """Wavenumber of each of the E rows of elements (bilinear elements, E per side) for the
     layered medium of Sec. 3.3: k = omega / c(y) with c alternating over `layers` equal
     layers, `first` ("c0" or "c1") at y = 0.  E must be a multiple of `layers`."""
