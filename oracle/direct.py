@@ -13,8 +13,14 @@ from .problem import Problem
 
 
 def solve(prob: Problem, f: np.ndarray, g: np.ndarray) -> np.ndarray:
-    """u* with A u* = b(f, g), flattened row-major [S_y][S_x]."""
-    return spla.spsolve(prob.A().tocsc(), prob.rhs(f, g))
+    """u* with A u* = b(f, g), flattened row-major [S_y][S_x].
+
+    The column ordering (minimum degree on A^T + A) only limits the fill of the LU
+    factors; it is not part of the method.  With it the 1023 x 1023 interior grid
+    (1,050,625 unknowns) factors in seconds rather than minutes.
+    """
+    lu = spla.splu(prob.A().tocsc(), permc_spec="MMD_AT_PLUS_A")
+    return lu.solve(prob.rhs(f, g))
 
 
 def rel_err(u: np.ndarray, u_star: np.ndarray) -> float:
