@@ -88,7 +88,9 @@ typedef enum {
     HH_LEAF_EIGEN = 0,    /* 2D leaves: the block Schur recursion evaluated in the eigenbasis */
                           /* of the column pencil (scalar recursions + two b x b transforms)  */
     HH_LEAF_BLOCK = 1     /* 2D leaves: the block Schur recursion with explicit b x b inverses */
-                          /* S_j^{-1} (Gauss-Jordan, partial pivoting) and block substitution  */
+                          /* S_j^{-1} (Gauss-Jordan, partial pivoting) and block substitution; */
+                          /* bands of at most 119 rows (FP64) or 169 rows (mixed), else       */
+                          /* hh_setup returns HH_EINVAL                                       */
 } hh_leaf_solver;         /* 1D leaves always use the scalar recursion along the line         */
 
 typedef enum {
@@ -239,8 +241,11 @@ const char* hh_status_string(hh_status s);
  * holds one (sum |r|^2, sum |b|^2) pair per grid row, the total and a counter; the
  * counter, the one part that must start at zero, is cleared on `stream` by every call.
  * The first call on a device (the device current at the call) looks the array's address
- * up (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  Calls that overlap in time on one device share the array and race: issue
+ * up (cudaGetSymbolAddress) and caches it.  Under CUDA's lazy module loading that first
+ * call may also be the moment the library's device code is loaded on that device and the
+ * array's memory reserved, so the promise of no allocation is firm only from the second
+ * call on: a caller that must not allocate later makes one warm-up call at start-up (any
+ * small problem), before any stream capture.  Calls that overlap in time on one device share the array and race: issue
  * them from one host thread on one stream (or otherwise serialise them).
  * Errors: HH_EINVAL for dim not 1 or 2, n < 1, k negative or not finite, or a NULL
  * pointer; HH_ETOOLARGE when n + 2 > HH_NOALLOC_MAX_ROWS (checked before any pointer

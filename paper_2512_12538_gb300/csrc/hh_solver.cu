@@ -212,6 +212,11 @@ static hh_status validate(const hh_params* P) {
     if (P->dim == 2 && P->leaf_solver == HH_LEAF_EIGEN)
         for (auto& nd : nodes)
             if (nd.leaf() && nd.b() > eig_bmax()) return HH_EINVAL;   // band too tall for this path
+    if (P->dim == 2 && P->leaf_solver == HH_LEAF_BLOCK) {
+        const int bmax = leaf_block_bmax(P->precision == HH_PREC_FP64 ? 16 : 8);
+        for (auto& nd : nodes)
+            if (nd.leaf() && nd.b() > bmax) return HH_EINVAL;         // inverse does not fit shared memory
+    }
     return HH_OK;
 }
 

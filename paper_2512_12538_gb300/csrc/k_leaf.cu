@@ -146,6 +146,15 @@ __global__ void k_factor1d(const LeafTask* __restrict__ tasks, int ntasks, doubl
     }
 }
 
+// Tallest band whose b x b inverse and pivot workspace fit one block's shared memory
+// (227 KiB) in k_factor2d: 119 rows in complex128, 169 in complex64.
+int leaf_block_bmax(int elem_bytes) {
+    const long long cap = 227 * 1024;
+    int b = 1;
+    while ((long long)elem_bytes * ((long long)(b + 1) * (b + 1) + 2 * (b + 1)) + 4ll * (b + 1) <= cap) ++b;
+    return b;
+}
+
 template <typename T>
 void launch_factor(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err, cudaStream_t s) {
     if (Sx == 1) {

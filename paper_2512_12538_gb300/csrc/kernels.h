@@ -216,6 +216,8 @@ template <typename T>
 void launch_sweep(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, int* err,
                   cudaStream_t s);
 int leaf_ldx(int b, int elem_bytes);
+// tallest band the explicit-inverse path factors (shared-memory bound of k_factor2d)
+int leaf_block_bmax(int elem_bytes);
 
 // ---- eigenbasis leaf path (k_eig.cu) -------------------------------------------------
 struct EigTask {

@@ -49,7 +49,7 @@ def _solve_alone(hh, w, f, g, p):
     h, _ = hh.hh_setup(p)
     try:
         u = torch.empty((w.S, w.S), dtype=torch.complex128, device="cuda")
-        st = hh.hh_solve(h, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), u)
+        st = hh.hh_solve(h, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), u, allow_noconv=True)
         return u.cpu().numpy(), st
     finally:
         hh.hh_destroy(h)
@@ -60,21 +60,32 @@ def _rel(a, b):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,tol", [("mixed", 1e-8), ("fp64", 1e-10)])
-def test_batch_matches_direct_and_solo(hh, precision, tol):
-    # mixed grid sides with k h in [0.3, 0.35], where the stationary iteration contracts for
-    # every draw, so that each problem's lockstep run can be compared with its solo run
-    probs = batch_problems(5, sides=(63, 127, 191, 255) if precision == "mixed" else (63, 127), kh=(0.3, 0.35))
+@pytest.mark.parametrize("precision,tol,count", [("mixed", 1e-8, 16), ("fp64", 1e-10, 8)])
+def test_batch_matches_direct_and_solo(hh, precision, tol, count):
+    """The batch configuration's whole range: grid sides 63 to 255 and k h drawn from
+    [0.3, 0.6].  Every problem's result is compared with u*.  Each problem is also solved
+    alone by the stationary iteration: where that converges in as many steps as the
+    problem took in the batch, the lockstep arithmetic is the same per problem, so the
+    two iterates agree up to the order of the partial sums (1e-12).  Problems whose
+    stationary iteration stalls or diverges are handed to GMRES inside the batch, so
+    their batch and solo runs differ; for those the comparison with u* decides."""
+    sides = (63, 127, 191, 255) if precision == "mixed" else (63, 127, 191)
+    probs = batch_problems(count, sides=sides, kh=(0.3, 0.6))
     params = _params(hh, probs, precision)
     got, sts = _solve_batch(hh, probs, params)
+    same = 0
     for i, (w, f, g) in enumerate(probs):
         us = direct.solve(Problem(2, w.n, w.k), f, g).reshape(w.S, w.S)
-        assert _rel(got[i], us) < tol, (w.name, sts[i].iters)
+        err = _rel(got[i], us)
+        kh = w.k / (w.n + 1)
+        print(f"{w.name} kh={kh:.3f}: iters {sts[i].iters}, err {err:.2e}")
+        assert sts[i].rel_res < 1e-10
+        assert err < tol, (w.name, sts[i].iters)
         alone, st1 = _solve_alone(hh, w, f, g, params[i])
-        # the same arithmetic per problem in lockstep: the same iterations, the same
-        # iterate up to the order of the partial sums
-        assert sts[i].iters == st1.iters
-        assert _rel(got[i], alone) < 1e-12
+        if st1.rel_res < 1e-10 and st1.iters == sts[i].iters:
+            assert _rel(got[i], alone) < 1e-12
+            same += 1
+    assert same >= count // 2, same
 
 
 @pytest.mark.gpu

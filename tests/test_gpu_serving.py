@@ -51,19 +51,27 @@ def _alone(hh, w, f, g, p):
     h, _ = hh.hh_setup(p)
     try:
         u = torch.empty((w.S, w.S), dtype=torch.complex128, device="cuda")
-        hh.hh_solve(h, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), u)
-        return u.cpu().numpy()
+        st = hh.hh_solve(h, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), u, allow_noconv=True)
+        return u.cpu().numpy(), st
     finally:
         hh.hh_destroy(h)
 
 
 @pytest.mark.gpu
 def test_served_results_equal_solo_results(hh):
-    probs = batch_problems(6, sides=(63, 127, 255), kh=(0.3, 0.35))
+    """Requests of every serving size (sides 63 to 1023; k h from 0.3 to 0.6 on the small
+    ones, the 3-level hierarchy with r = 32 on 511 and 1023) arriving while others are in
+    flight.  Each result is compared with u*; where the request's stationary iteration
+    alone converges in as many steps as it took in the server, the served result equals
+    the solo one to 1e-12 (the same arithmetic, summed in another order)."""
+    probs = batch_problems(8, sides=(63, 127, 255), kh=(0.3, 0.6))
     # one request the lockstep iteration does not take (GMRES outer) and one whose
     # stationary iteration diverges (handed to GMRES)
     w = Workload("div", 2, 63, 0.47 * 64, 2, 2, 16, 8)
     probs.append((w, point_source_rhs(63, 123), np.zeros((4, 65), dtype=np.complex128)))
+    for n, k in ((511, 150.0), (1023, 100.0)):
+        w = Workload(f"big{n}", 2, n, k, 3, 4, 32, 10)
+        probs.append((w, point_source_rhs(n, 7 + n), np.zeros((4, n + 2), dtype=np.complex128)))
     outers = ["oras"] * len(probs)
     outers[2] = "gmres"
     params = [_params(hh, w, i, outers[i]) for i, (w, f, g) in enumerate(probs)]
@@ -71,7 +79,7 @@ def test_served_results_equal_solo_results(hh):
     gs = [torch.from_numpy(g).cuda() for (w, f, g) in probs]
     us = [torch.zeros((w.S, w.S), dtype=torch.complex128, device="cuda") for (w, f, g) in probs]
     torch.cuda.synchronize()
-    srv = hh.hh_server_create(8 << 30, 16)
+    srv = hh.hh_server_create(16 << 30, 16)
     try:
         tickets = []
         for i in range(len(probs)):
@@ -80,16 +88,22 @@ def test_served_results_equal_solo_results(hh):
         res = _wait(hh, srv, tickets)
     finally:
         hh.hh_server_destroy(srv)
+    same = 0
     for i, (w, f, g) in enumerate(probs):
         st, stats = res[i]
         assert st == hh.HH_OK and stats.rel_res < 1e-10, (w.name, st)
         got = us[i].cpu().numpy()
         ud = direct.solve(Problem(2, w.n, w.k), f, g).reshape(w.S, w.S)
-        assert np.linalg.norm(got - ud) / np.linalg.norm(ud) < 1e-8
-        if outers[i] == "oras" and w.name != "div":
-            alone = _alone(hh, w, f, g, params[i])
-            assert np.linalg.norm(got - alone) / np.linalg.norm(alone) < 1e-12
+        err = np.linalg.norm(got - ud) / np.linalg.norm(ud)
+        print(f"{w.name} kh={w.k / (w.n + 1):.3f} {outers[i]}: iters {stats.iters}, err {err:.2e}")
+        assert err < 1e-8
+        if outers[i] == "oras":
+            alone, st1 = _alone(hh, w, f, g, params[i])
+            if st1.rel_res < 1e-10 and st1.iters == stats.iters:
+                assert np.linalg.norm(got - alone) / np.linalg.norm(alone) < 1e-12
+                same += 1
         assert stats.t_total_ms >= stats.t_queue_ms >= 0.0
+    assert same >= len(probs) // 2, same
 
 
 @pytest.mark.gpu

@@ -1,4 +1,5 @@
-"""hh_residual_noalloc (the allocation-free relative residual) against hh_residual.
+"""hh_residual_noalloc (the allocation-free relative residual) against hh_residual and
+against the oracle's ||b - A u|| / ||b|| (its sparse operator and right-hand side, FP64).
 
 Collected last on purpose: it must pass both in a fresh process, where its first call
 also does the per-device set-up, and after every other test has run.
@@ -6,6 +7,7 @@ also does the per-device set-up, and after every other test has run.
 import numpy as np
 import pytest
 
+from oracle.problem import Problem
 from workloads.generators import random_complex
 
 torch = pytest.importorskip("torch")
@@ -80,3 +82,28 @@ def test_noalloc_zero_rhs_and_exact_solution(hh):
     f, g, _ = _inputs(13, S, S, 4)
     assert hh.hh_residual_noalloc(2, n, k, z, gz, f) == 0.0
     assert hh.hh_residual_noalloc(2, n, k, f, g, z) == pytest.approx(1.0, abs=1e-15)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dim,n,k", [(2, 45, 12.0), (2, 1023, 100.0), (1, 1000, 62.83),
+                                     (1, 16382, 500.0), (1, 16381, 500.0)],
+                         ids=["d2n45", "d2n1023", "d1n1000", "d1_at_cap", "d1_below_cap"])
+def test_noalloc_matches_the_oracle_residual(hh, dim, n, k):
+    """The oracle's residual of random data, up to the largest size the static scratch
+    takes (n + 2 = HH_NOALLOC_MAX_ROWS grid rows: more rows than the launch has warps, so
+    the kernel's grid-stride loop runs).  Both sides sum in FP64 in different orders:
+    1e-12 relative."""
+    S = n + 2
+    assert S <= hh.HH_NOALLOC_MAX_ROWS
+    Sx = S if dim == 2 else 1
+    f = random_complex((S, Sx), 21)
+    g = random_complex((4, S) if dim == 2 else (2,), 22)
+    u = random_complex((S, Sx), 23)
+    P = Problem(dim, n, k)
+    b = P.rhs(f.reshape(-1) if dim == 1 else f, g)
+    want = float(np.linalg.norm(b - P.A() @ u.reshape(-1)) / np.linalg.norm(b))
+    d = [torch.from_numpy(x).cuda() for x in (f, g, u)]
+    got = [hh.hh_residual_noalloc(dim, n, k, *d) for _ in range(2)]
+    for a in got:
+        assert abs(a - want) <= 1e-12 * want, (a, want)
+    assert got[0] == got[1]
