@@ -59,10 +59,23 @@ def test_footprint_host_only_and_validation(hh):
         assert ei.value.status == hh.HH_EINVAL, kw
 
 
-def test_block_leaf_path_accepts_tall_bands(hh):
-    # the explicit-inverse leaf path has no eigenbasis band limit
-    p = hh.make_params(dim=2, n=1023, k=100.0, levels=2, overlap=4, rank=16, oversample=8, leaf_solver="block")
-    assert hh.hh_footprint(p) > 0
+def test_block_leaf_path_band_limits(hh):
+    # host-side validation only.  The explicit-inverse leaf path takes bands taller than
+    # the eigenbasis path's 136 rows, up to what one b x b inverse in shared memory
+    # allows: 169 rows in complex64, 119 in complex128.  n = 1200 with 3 levels gives
+    # bands of about 154 rows; n = 1023 with 2 levels about 260.
+    def fp(n, levels, precision, leaf_solver):
+        p = hh.make_params(dim=2, n=n, k=100.0, levels=levels, overlap=4, rank=16, oversample=8,
+                           precision=precision, leaf_solver=leaf_solver)
+        return hh.hh_footprint(p)
+
+    assert fp(1200, 3, "mixed", "block") > 0
+    for n, levels, precision, leaf_solver in ((1200, 3, "mixed", "eigen"), (1200, 3, "fp64", "block"),
+                                              (1023, 2, "mixed", "block")):
+        with pytest.raises(hh.HHError) as ei:
+            fp(n, levels, precision, leaf_solver)
+        assert ei.value.status == hh.HH_EINVAL
+    assert fp(1023, 3, "mixed", "block") > 0 and fp(1023, 3, "fp64", "eigen") > 0
 
 
 def test_footprint_1d(hh):
