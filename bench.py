@@ -3,12 +3,13 @@
 A step is one pass of the whole path for one problem: set-up (hierarchy, leaf
 factorisation, interface sketches, coarse bases, Galerkin matrices and their inverses)
 followed by the outer iteration to the calibrated FP64 residual tolerance, then the
-handle is released.  Default workload: 255 x 255 interior grid (257^2 unknowns), k = 40,
-2-level binary band hierarchy (4 leaves), overlap 2 rows, r = 16, p = 10, seeded
-Gaussian point sources.  The headline runs the mixed form: complex64 subdomain work,
-sketches, bases and coarse inverses; Galerkin and Gram matrices from FP32 products with
-FP64 sums; an FP64 residual and sketch eigenproblem.  The FP64 GPU form runs the same
-workload for comparison.
+handle is released.  Workload: the precision form, a 1023 x 1023 interior grid
+(1025^2 = 1,050,625 unknowns), k = 100, 3-level binary band hierarchy (8 leaves of 130
+to 132 rows), overlap 4 rows, r = 32, p = 10, seeded Gaussian point sources.  The
+headline runs the mixed form: complex64 subdomain factors, sweeps, sketches and bases;
+FP64 residual, Galerkin matrices (FP64 products of the complex64 basis), their
+elimination and the sketch eigenproblem.  The FP64 GPU form runs the same workload on
+the same line, and the errors of both against the oracle's direct solution are stated.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,11 +34,12 @@ if ROOT not in sys.path:
 
 METRIC = "Helmholtz solves/sec at rel err 1e-8 (mixed vs FP64 GPU); p50/p99 latency"
 UNIT = "solves/s"
-WORKLOAD = "helm2d_n255_k40_L2"
+WORKLOAD = "helm2d_n1023_k100_L3"
 # FP64 relative-residual stopping tolerance for relative error <= 1e-8 against the
 # direct solution on this workload, with a margin of at least 10x (the error is checked
-# to be <= 1e-9 in both forms by tests/test_gpu_bench_calibration.py).
-TOL = 1e-9
+# to be <= 1e-9 in both forms by tests/test_gpu_bench_calibration.py; measured about
+# 0.13 times the residual on this workload).
+TOL = 3e-9
 # The batching and serving forms mix grid sizes and wavenumbers that this calibration
 # does not cover: they stop at the tighter 1e-10.
 TOL_FORMS = 1e-10
@@ -142,24 +144,26 @@ def leaf_bands(w):
 # Bound of each profiler category (the library reports each launch's algorithmic bytes
 # and flops; see hh_profile_read in include/hh.h).
 CATEGORY_BOUND = {
-    "factor": ("latency", "k_eig_factor (eigenpairs of the column pencil + scalar Schur recursions)"),
-    "sweep_in": ("alu", "k_eig_gemm2<float,true> (f^ = V^T f over the sketch columns, register-tiled)"),
-    "sweep_recur": ("hbm", "k_eig_recur<float> (scalar Schur recursions of the sketch columns, warp scans)"),
-    "sweep_out": ("alu", "k_eig_gemm2<float,false> (x = V x^ over the sketch columns)"),
-    "residual": ("hbm", "k_residual_cast<float> (FP64 residual b - A u, its norm partials and complex64 copy)"),
-    "coarse_project": ("hbm", "k_coarse_batch (one-column coarse corrections: residual, C^H r, A_c^-1, C y; "
+    "factor": ("latency", "k_eig_roots + k_eig_modes (eigenpairs of the column pencil, scalar Schur recursions)"),
+    "sweep_in": ("alu", "k_eig_gemm2 (f^ = V^T f, register-tiled complex contraction)"),
+    "sweep_recur": ("hbm", "k_eig_recur (scalar Schur recursions along the line, warp scans)"),
+    "sweep_out": ("alu", "k_eig_gemm2 (x = V x^, register-tiled complex contraction)"),
+    "residual": ("hbm", "k_residual_cast (FP64 residual b - A u, its norm partials and complex64 copy)"),
+    "coarse_project": ("hbm", "k_coarse_batch (one-column coarse corrections: C^H r, A_c^-1, C y; "
                               "one cooperative launch per level)"),
-    "galerkin": ("alu", "k_galerkin_partial<float> (A_c = C^H A~ C: FP32 products, FP64 tile sums)"),
+    "galerkin": ("alu64", "k_galerkin_partial (A_c = C^H A~ C: FP64 stencil and products of the stored basis)"),
     "qr": ("latency", "k_qr (sketch orthonormalisation, shared-memory CGS2)"),
     "svd": ("latency", "k_heig_tri + k_heig_vec (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
-    "leaf_sweep": ("alu", "k_eig_sweep_fused<float> (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
+    "leaf_sweep": ("alu", "k_eig_sweep_fused (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
+    "coarse_multi": ("hbm", "k_ip_partial (multi-column coarse projections of the set-up's sub-level solves)"),
 }
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure is available)
+# FP64 peak derived from the DFMA issue rate (2 per SM per cycle, the peak ncu reports for
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum): 152 SMs x 2 x 2 flops x max SM clock.
+DFMA_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel, from one ncu capture of this bench (warm cache, as inside a solve); the
-# capture and its command are in profiles/coarse_batch_helm2d_n255_k40_L2.md.  To be
-# reset to None whenever k_coarse_batch changes.
-TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 89637}
+# kernel from one ncu capture of this workload; None until a capture of the current
+# kernel on this workload is summarised under profiles/.
+TRAFFIC_BYTES_PER_LAUNCH = {}
 
 
 def whole_job_rate(local_ms, units_per_rank, world, device="cuda"):
@@ -256,6 +260,8 @@ def run_ours(args, rank, world):
     hh.hh_profile_categories(None, None)
     launches = hh.hh_launch_count() - launches0
     value, total_ms = whole_job_rate(sum(step_ms), args.steps, world)
+    u_mixed = u.cpu().numpy()
+    setup_split = one("mixed")[1]
 
     # FP64 GPU form of the same method on the same workload
     fp64_ms = []
@@ -265,6 +271,7 @@ def run_ours(args, rank, world):
         fp64_ms.append(ms)
         fp64_iters.append(st.iters)
     fp64_value = whole_job_rate(sum(fp64_ms), len(fp64_ms), world)[0]
+    u_fp64 = u.cpu().numpy()
 
     # end to end through the C-ABI with host buffers (pinned): H2D f, g and D2H u inside
     fh = torch.from_numpy(f).pin_memory()
@@ -286,7 +293,8 @@ def run_ours(args, rank, world):
            "ms_per_step": statistics.mean(e2e_ms), "timing": "host wall clock around set-up, "
            "hh_solve_host (pinned buffers) and release, no profiler events"}
 
-    batch = run_batch_form(hh, torch) if rank == 0 and args.batch_form == "on" else None
+    batch, batch_u = run_batch_form(hh, torch) if rank == 0 and args.batch_form == "on" else (None, None)
+    serving = run_serving(args, hh, torch) if rank == 0 and args.serving_form == "on" else None
 
     pk, pk_kind = peaks()
     roof = roofline(w, prof_total, prof_all, dominant, pk, pk_kind)
@@ -297,12 +305,14 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
-        "config": workload_config(w, "mixed", "flushed between steps (256 MB write)", f"replicas x{world}"),
+        "config": workload_config(w, "mixed", "inputs larger than L2 (16.8 MB vectors, 2.3 GB factors and bases); "
+                                             "L2 also flushed between steps (256 MB write)", f"replicas x{world}"),
         "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
         "iterations": {"mixed": statistics.median(iters), "fp64": statistics.median(fp64_iters)},
-        "fp64_form": {"value": fp64_value, "unit": UNIT,
+        "setup_ms": {"mixed": setup_split.t_setup_ms, "solve_mixed": setup_split.t_solve_ms},
+        "fp64_form": {"value": fp64_value, "unit": UNIT, "dtype": "c128/f64",
                       "ms_per_step": statistics.mean(fp64_ms), "median_ms_per_step": statistics.median(fp64_ms),
-                      "step_ms": [round(x, 3) for x in fp64_ms]},
+                      "iterations": statistics.median(fp64_iters), "step_ms": [round(x, 3) for x in fp64_ms]},
         "mixed_over_fp64": value / fp64_value,
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
         "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
@@ -312,19 +322,50 @@ def run_ours(args, rank, world):
     }
     if batch is not None:
         out["batch_form"] = batch
-    if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(w, f, g)
+    if serving is not None:
+        out["serving_form"] = serving
+    if rank == 0 and world == 1 and args.cpu_baseline == "on":
+        base, refs = cpu_baseline_leg(w, batch_u)
+        out["cpu_baseline"] = base
+        # relative errors against the oracle's direct solution u* = A^{-1} b
+        out["rel_err"] = {"mixed": rel_err(u_mixed, refs["u_star"]), "fp64": rel_err(u_fp64, refs["u_star"]),
+                          "against": "oracle direct solve (sparse LU) of the same system"}
+        if batch is not None and refs.get("batch"):
+            errs = [rel_err(batch_u[i], us) for i, us in refs["batch"].items()]
+            batch["rel_err_sample"] = {"problems": sorted(refs["batch"]), "max": max(errs),
+                                       "against": "oracle direct solves of a seeded subset incl. the largest k h"}
     return out
 
 
+def rel_err(u, u_star):
+    import numpy as np
+    u = np.asarray(u).reshape(-1)
+    u_star = np.asarray(u_star).reshape(-1)
+    return float(np.linalg.norm(u - u_star) / np.linalg.norm(u_star))
+
+
 BATCH_PROBLEMS = 512
+BATCH_ERR_SAMPLE = 8      # problems of the batch compared with the oracle's direct solution
+
+
+def batch_error_sample(probs):
+    """Indices of the batch problems whose errors the line states: the problems with the
+    largest k h and a seeded draw of the rest."""
+    import numpy as np
+    kh = [w.k / (w.n + 1) for (w, f, g) in probs]
+    order = sorted(range(len(probs)), key=lambda i: -kh[i])
+    pick = order[:BATCH_ERR_SAMPLE // 2]
+    rng = np.random.Generator(np.random.PCG64(2512_12538 + 4))
+    rest = [i for i in range(len(probs)) if i not in pick]
+    pick += [int(i) for i in rng.choice(rest, size=min(len(rest), BATCH_ERR_SAMPLE - len(pick)), replace=False)]
+    return sorted(pick)
 
 
 def run_batch_form(hh, torch, count=BATCH_PROBLEMS):
     """The batching form: `count` independent problems (grid sides 63..255, k h in
     [0.3, 0.6], 2 levels, r = 16, p = 8) set up together (hh_setup_batch) and solved
     together (hh_solve_batch), one warm-up and one timed pass; solves/s over set-up and
-    solve."""
+    solve.  Returns (result, the solutions of the error sample on the host)."""
     from workloads import batch_problems
     probs = batch_problems(count)
     params = [hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, 1, TOL_FORMS, MAX_ITER, "mixed",
@@ -349,30 +390,25 @@ def run_batch_form(hh, torch, count=BATCH_PROBLEMS):
                "solve_ms": 1e3 * (t2 - t1), "iterations": {"median": statistics.median(its), "max": max(its)},
                "max_rel_res": max(st.rel_res for st in sts),
                "workload": "batch: grid sides U{63,127,191,255}, k h U[0.3,0.6], L=2, overlap 2, r=16, p=8, "
-                           f"mixed form, tol {TOL_FORMS}"}
-    return res
+                           f"mixed form, tol {TOL_FORMS}", "timing": "host wall clock, warm second pass"}
+    sample = {i: us[i].cpu().numpy() for i in batch_error_sample(probs)}
+    return res, sample
 
 
-def run_serving(args):
-    """The serving form: a Poisson stream of requests (mean args.rate per second for
-    args.serve_seconds seconds), grid sides U{127,255,511,1023}, k ~ U[20, min(150, 0.6/h)],
-    2 levels (r=16, p=10, overlap 2) up to 255 and 3 levels (r=32, p=10, overlap 4) above,
-    submitted to one hh_server; reports served solves/s and p50/p99 latency (submission
-    to completion)."""
+SERVE_SECONDS = 0.5       # length of the serving stream in the default line
+
+
+def serving_requests(hh, torch, rate, seconds):
+    """The serving form's request stream: Poisson arrivals (mean `rate` per second for
+    `seconds` seconds), grid sides U{127,255,511,1023}, k ~ U[20, min(150, 0.6/h)], 2 levels
+    (r=16, p=10, overlap 2) up to 255 and 3 levels (r=32, p=10, overlap 4) above."""
     import numpy as np
-    import torch
-
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2512_12538_gb300 as hh
     from workloads import point_source_rhs
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rng = np.random.Generator(np.random.PCG64(2512_12538 + 5))
     t, reqs = 0.0, []
     while True:
-        t += rng.exponential(1.0 / args.rate)
-        if t > args.serve_seconds:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
             break
         n = int(rng.choice([127, 255, 511, 1023]))
         k = float(rng.uniform(20.0, min(150.0, 0.6 * (n + 1))))
@@ -382,6 +418,14 @@ def run_serving(args):
         g = torch.zeros((4, n + 2), dtype=torch.complex128, device="cuda")
         u = torch.empty_like(f)
         reqs.append((t, n, p, f, g, u))
+    return reqs
+
+
+def run_serving(args, hh, torch, seconds=None):
+    """The serving form: the request stream submitted to one hh_server as the requests
+    arrive; served solves/s and p50/p99 latency (submission to completion)."""
+    seconds = args.serve_seconds if seconds is None else seconds
+    reqs = serving_requests(hh, torch, args.rate, seconds)
     torch.cuda.synchronize()
     srv = hh.hh_server_create(160 << 30, 64)
     lat, done, fails, codes = [], {}, 0, {}
@@ -408,12 +452,26 @@ def run_serving(args):
     wall = max(done.values())
     hh.hh_server_destroy(srv)
     return {"metric": "served Helmholtz solves/sec (Poisson stream) at rel err 1e-8; p50/p99 latency",
-            "value": len(reqs) / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "value": len(reqs) / wall, "unit": UNIT, "higher_is_better": True,
             "requests": len(reqs), "failed": fails, "statuses": codes, "offered_rate": args.rate,
-            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)}, "wall_s": wall,
+            "stream_s": seconds, "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)}, "wall_s": wall,
             "config": {"workload": "serving: sides U{127,255,511,1023}, k U[20, min(150, 0.6/h)], L=2 (r=16,p=10) "
-                                   "up to 255, L=3 (r=32,p=10) above; budget 160 GB, 64 slots", "precision": "mixed"},
+                                   "up to 255, L=3 (r=32,p=10) above; budget 160 GB, 64 slots", "precision": "mixed",
+                       "tol_rel_residual": TOL_FORMS},
             "data": "synthetic"}
+
+
+def run_serving_line(args):
+    """--form serve: a longer serving stream on its own line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_12538_gb300 as hh
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = run_serving(args, hh, torch)
+    out["n_gpus"] = 1
+    return out
 
 
 def pct(xs, q):
@@ -439,9 +497,10 @@ def rate(cat, ms, by, fl, pk, pk_kind):
         out.update({"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                     "peak_kind": "FP32 FFMA derived: 152 SMs x 128 lanes x 2 flops x max SM clock"})
     elif bound == "alu64" and fl > 0:
+        peak = SM_COUNT * DFMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         a = fl / (ms / 1e3) / 1e12
-        out.update({"achieved": a, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_NOMINAL_TFLOPS,
-                    "peak_kind": "FP64 nominal"})
+        out.update({"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                    "peak_kind": "FP64 DFMA derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"})
     else:
         out.update({"achieved": None, "peak": None, "unit": None, "frac": None})
     return out
@@ -472,48 +531,117 @@ def workload_config(w, precision, l2, parallelism):
 
 
 # ------------------------------------------------------------------ CPU baseline
-def cpu_baseline(w, f, g, n_solves=1):
-    """The FP64 oracle, as it stands, on the same workload: n one-shot solves."""
-    from oracle.method import OMethod
+# The oracle (oracle/, FP64 CPU) runs only here: the CPU baseline leg of the GPU arm and
+# the reference arm.  Its direct solve u* = A^{-1} b (sparse LU) is the oracle's fastest
+# way to a solution of the workload at the metric's accuracy (exact), so it is the timed
+# sample; its solutions also state the GPU results' errors.  Workers are spawned (fresh
+# interpreters, no CUDA state), single-threaded each.
+def _oracle_worker_init():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+
+
+def _oracle_direct(job):
+    """(seconds, u*) of one direct solve; job = (workload name or batch index, keep u*)."""
+    from oracle import direct
     from oracle.problem import Problem
-    P = Problem(2, w.n, w.k)
+    from workloads import WORKLOADS, batch_problems, problem_inputs
+    what, keep = job
+    if isinstance(what, str):
+        w = WORKLOADS[what]
+        f, g = problem_inputs(w)
+    else:
+        w, f, g = batch_problems(what + 1)[what]
     t0 = time.perf_counter()
-    for _ in range(n_solves):
-        M = OMethod(P, w.levels, w.overlap, w.rank, w.oversample, n_inner=w.n_inner, seed=1)
-        M.solve(P.rhs(f, g), tol=TOL, maxit=MAX_ITER)
-    dt = time.perf_counter() - t0
-    return {"value": n_solves / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n_solves} one-shot solve(s) (set-up + iteration to tol {TOL}) of {WORKLOAD}; "
-                      "numpy/scipy, BLAS threads up to the core count"}
+    u = direct.solve(Problem(2, w.n, w.k), f, g)
+    return time.perf_counter() - t0, (u if keep else None)
+
+
+def _oracle_pool(workers):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers, initializer=_oracle_worker_init)
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+ORACLE_POOL_MAX = 16
+
+
+def cpu_baseline_leg(w, batch_u=None):
+    """The oracle on the host cores: one direct solve single-threaded (its u* also gives
+    the GPU results' errors), then one solve per core on all cores at once (throughput).
+    With `batch_u`, the direct solutions of those batch problems as well.  Returns
+    (cpu_baseline object, {"u_star": u*, "batch": {index: u*}})."""
+    cores, model = host_cpu()
+    nw = max(1, min(cores, ORACLE_POOL_MAX))
+    with _oracle_pool(nw) as pool:
+        t1, u_star = pool.apply(_oracle_direct, ((WORKLOAD, True),))
+        t0 = time.perf_counter()
+        pool.map(_oracle_direct, [(WORKLOAD, False)] * nw, chunksize=1)
+        t_all = time.perf_counter() - t0
+        batch = {}
+        if batch_u:
+            idx = sorted(batch_u)
+            for i, (_, ub) in zip(idx, pool.map(_oracle_direct, [(i, True) for i in idx], chunksize=1)):
+                batch[i] = ub
+    base = {"value": nw / t_all, "unit": UNIT, "cores": nw, "kind": "oracle",
+            "sample": f"{nw} direct solves (oracle sparse LU, minimum-degree ordering; exact, so within the metric's "
+                      f"1e-8) of {WORKLOAD}, one per core at once, single-threaded each",
+            "single_thread": {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "seconds_per_solve": t1},
+            "cpu_model": model, "host_logical_cores": cores,
+            "note": "the oracle's stepwise method (O-method) on this workload is slower than its direct solve"}
+    return base, {"u_star": u_star, "batch": batch}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (FP64 CPU) on this workload, timed on the host cores.
+    A step is one direct solve of the workload; the steps run one per core at once
+    (single-threaded each), warm-up steps first."""
     if rank != 0:
         return None
     w, f, g = workload_inputs()
-    from oracle.method import OMethod
-    from oracle.problem import Problem
-    P = Problem(2, w.n, w.k)
-    b = P.rhs(f, g)
-
-    def step():
-        M = OMethod(P, w.levels, w.overlap, w.rank, w.oversample, n_inner=w.n_inner, seed=1)
-        M.solve(b, tol=TOL, maxit=MAX_ITER)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
+    cores, model = host_cpu()
+    nw = max(1, min(cores, ORACLE_POOL_MAX, max(args.steps, args.warmup, 1)))
+    with _oracle_pool(nw) as pool:
+        if args.warmup > 0:
+            pool.map(_oracle_direct, [(WORKLOAD, False)] * args.warmup, chunksize=1)
+        t0 = time.perf_counter()
+        times = pool.map(_oracle_direct, [(WORKLOAD, False)] * args.steps, chunksize=1)
+        dt = time.perf_counter() - t0
     value = args.steps / dt
+    per = [t for t, _ in times]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(w, "fp64 (CPU oracle)", "host run", "rank 0 only"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} one-shot solve(s) (set-up + iteration to tol {TOL}) of "
-                                       f"{WORKLOAD}; numpy/scipy, BLAS threads up to the core count"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(nw, args.steps), "kind": "oracle",
+                             "sample": f"{args.steps} direct solves (oracle sparse LU, minimum-degree ordering) of "
+                                       f"{WORKLOAD}, up to {nw} at once, single-threaded each",
+                             "seconds_per_solve": statistics.mean(per), "cpu_model": model,
+                             "host_logical_cores": cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -527,11 +655,16 @@ def main():
                     help="serve: the serving-form stream instead of the headline workload")
     ap.add_argument("--batch-form", default="on", choices=["on", "off"],
                     help="also measure the batching form (512 problems) after the headline")
+    ap.add_argument("--serving-form", default="on", choices=["on", "off"],
+                    help="also run a short serving stream after the headline")
+    ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"],
+                    help="time the oracle on the host cores and state the errors against its solution")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving: length of the arrival stream")
+    ap.add_argument("--serve-seconds", type=float, default=SERVE_SECONDS,
+                    help="serving: length of the arrival stream")
     args = ap.parse_args()
     if args.form == "serve":
-        print(json.dumps(run_serving(args)), flush=True)
+        print(json.dumps(run_serving_line(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -59,10 +59,12 @@ typedef enum {
 
 typedef enum {
     HH_PREC_FP64 = 0,     /* complex128 everywhere, FP64 CUDA-core arithmetic          */
-    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches, bases and  */
-                          /* the Galerkin inverses (eliminated in FP32 from matrices   */
-                          /* summed in FP64); FP64 residual and sketch SVD; the outer  */
-                          /* iteration refines against the FP64 residual               */
+    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches and bases; */
+                          /* FP64 residual, Galerkin matrices A_c (FP64 products of   */
+                          /* the complex64 basis), their elimination and the sketch   */
+                          /* SVD; the outer iteration refines against the FP64        */
+                          /* residual (HH_FLAG_COARSE_FP32: A_c from FP32 products,   */
+                          /* eliminated in FP32)                                      */
 } hh_precision;
 
 typedef struct {
@@ -82,7 +84,13 @@ typedef struct {
     int leaf_solver;      /* hh_leaf_solver                                              */
     int outer;            /* hh_outer                                                    */
     int restart;          /* Krylov vectors per GMRES cycle (outer = HH_OUTER_GMRES), 1..64 */
+    unsigned flags;       /* HH_FLAG_* bits; 0 for the defaults                           */
 } hh_params;
+
+/* hh_params.flags: the mixed form forms the Galerkin matrices A_c = C^H A~ C from FP32
+ * products (FP64 partial sums) and inverts them in FP32, instead of FP64 products and
+ * FP64 elimination.  Ignored by the FP64 form. */
+#define HH_FLAG_COARSE_FP32 1u
 
 typedef enum {
     HH_LEAF_EIGEN = 0,    /* 2D leaves: the block Schur recursion evaluated in the eigenbasis */
@@ -305,9 +313,11 @@ hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream);
  * Categories: 0 leaf factorisation, 1 leaf sweep transform into the column eigenbasis,
  * 2 leaf sweep recursions along the line (scalar recursions, or the block substitution
  * of the explicit-inverse path), 3 leaf sweep transform back, 4 FP64 global residual,
- * 5 coarse projection C^H r, 6 Galerkin product, 7 sketch orthonormalisation, 8 sketch
- * SVD, 9 leaf sweep of a single right-hand side on the eigenbasis path (categories 1-3
- * fused into one launch; 1-3 then count the multi-vector sweeps of the set-up).
+ * 5 one-column coarse corrections (C^H r, A_c^{-1}, C y: one launch per level), 6 Galerkin
+ * product, 7 sketch orthonormalisation, 8 sketch SVD, 9 leaf sweep of a single
+ * right-hand side on the eigenbasis path (categories 1-3 fused into one launch; 1-3 then
+ * count the multi-vector sweeps of the set-up), 10 multi-column coarse projections of the
+ * set-up's sub-level solves.
  * -------------------------------------------------------------------------------- */
 /* h != NULL: (re)start profiling of that handle, clearing its totals; h == NULL: set
  * whether handles created afterwards profile from their first set-up kernel. */
@@ -321,7 +331,9 @@ hh_status hh_profile_categories(hh_handle* h, unsigned mask);
 /* total_ms: summed event time; launches: timed launches; alg_bytes / alg_flops: the
  * algorithmic memory traffic and floating-point work of those launches (formulas in the
  * library: e.g. a band transform of b rows, S_x columns and nc right-hand sides counts
- * 8 b^2 S_x nc flops and (b^2 + 2 b S_x nc) elements).  Any output may be NULL. */
+ * 8 b^2 S_x nc flops and (b^2 + 2 b S_x nc) elements; a one-column coarse correction of
+ * a node of n points and rank r counts 2 r n elements of the basis: its r basis columns
+ * read once for C^H r and once for C y).  Any output may be NULL. */
 hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, long long* launches,
                           double* alg_bytes, double* alg_flops);
 /* Number of CUDA kernels this library has launched in the calling process. */

@@ -21,6 +21,7 @@ HH_NOALLOC_MAX_ROWS = 16384
 HH_PREC_FP64, HH_PREC_MIXED = 0, 1
 HH_LEAF_EIGEN, HH_LEAF_BLOCK = 0, 1
 HH_OUTER_ORAS, HH_OUTER_GMRES = 0, 1
+HH_FLAG_COARSE_FP32 = 1
 
 
 class hh_params(ctypes.Structure):
@@ -29,7 +30,7 @@ class hh_params(ctypes.Structure):
                 ("oversample", ctypes.c_int), ("n_inner", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("leaf_solver", ctypes.c_int), ("outer", ctypes.c_int),
-                ("restart", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("flags", ctypes.c_uint)]
 
 
 class hh_stats(ctypes.Structure):
@@ -122,7 +123,7 @@ def _check(st: int, where: str, ok=(HH_OK,)):
 
 def make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, n_inner=1,
                 tol=1e-10, max_iter=200, precision=HH_PREC_FP64, seed=0, leaf_solver=HH_LEAF_EIGEN,
-                outer=HH_OUTER_ORAS, restart=40) -> hh_params:
+                outer=HH_OUTER_ORAS, restart=40, flags=0) -> hh_params:
     if isinstance(precision, str):
         precision = {"fp64": HH_PREC_FP64, "mixed": HH_PREC_MIXED}[precision]
     if isinstance(leaf_solver, str):
@@ -130,7 +131,7 @@ def make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=1
     if isinstance(outer, str):
         outer = {"oras": HH_OUTER_ORAS, "gmres": HH_OUTER_GMRES}[outer]
     return hh_params(dim, n, float(k), levels, overlap, rank, oversample, n_inner, float(tol), max_iter,
-                     precision, seed, leaf_solver, outer, restart)
+                     precision, seed, leaf_solver, outer, restart, flags)
 
 
 # ------------------------------------------------------------------ allocator hook
@@ -305,7 +306,7 @@ def hh_sketch_samples(h, child, out, stream=None) -> None:
 
 
 PROFILE_CATEGORIES = ["factor", "sweep_in", "sweep_recur", "sweep_out", "residual", "coarse_project",
-                      "galerkin", "qr", "svd", "leaf_sweep"]
+                      "galerkin", "qr", "svd", "leaf_sweep", "coarse_multi"]
 
 
 def hh_profile_enable(h, enable=True) -> None:

@@ -83,11 +83,12 @@ enum ProfCat {
     PC_RECUR,        // leaf sweep: recursions along the line (scalar, or the block substitution)
     PC_TOUT,         // leaf sweep: transform back
     PC_SPMV,         // FP64 global residual
-    PC_COARSE,       // coarse projection C^H r
+    PC_COARSE,       // one-column coarse corrections (C^H r, A_c^{-1}, C y; one launch per level)
     PC_GALERKIN,     // Galerkin product
     PC_QR,           // sketch orthonormalisation
     PC_JACOBI,       // sketch SVD
     PC_SWEEP,        // leaf sweep for one right-hand side, all three stages in one launch
+    PC_COARSE_MC,    // multi-column coarse projections C^H r of the set-up's sub-level solves
     PC_NCAT
 };
 
@@ -201,6 +202,7 @@ static hh_status validate(const hh_params* P) {
     if (P->leaf_solver != HH_LEAF_EIGEN && P->leaf_solver != HH_LEAF_BLOCK) return HH_EINVAL;
     if (P->outer != HH_OUTER_ORAS && P->outer != HH_OUTER_GMRES) return HH_EINVAL;
     if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
+    if (P->flags & ~HH_FLAG_COARSE_FP32) return HH_EINVAL;
     if (P->levels > 6) return HH_EINVAL;
     const int Sx = P->dim == 2 ? P->n + 2 : 1;
     if ((long long)(P->n + 2) * Sx >= (1ll << 31)) return HH_EINVAL;   // grid points index in 32 bits
@@ -435,6 +437,8 @@ struct Solver final : SolverBase {
         pinned_put(h_pin);   // nothing copies into it any more
     }
 
+    // the mixed form's opt-in FP32 Galerkin products and coarse elimination
+    bool coarse_fp32() const { return sizeof(CT) != sizeof(c128) && (P.flags & HH_FLAG_COARSE_FP32); }
     OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh}; }
     size_t pts(int id) const { return (size_t)nodes[id].b() * Sx; }
     size_t row_off(int id, int grow, int nc) const { return (size_t)(grow - nodes[id].ra) * Sx * nc; }
@@ -799,7 +803,7 @@ struct Solver final : SolverBase {
                 j.split = split_row(p);
                 // level 1 also keeps its update delta_1 for the root's correction
                 j.dout = l == 1 ? (void*)(dlt + row_off(0, nd.own_a, 1)) : nullptr;
-                by += (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT);
+                by += coarse_bytes(p);
                 fl += 2.0 * 8.0 * 2 * r * pts(p);
             }
             // the pair stays open: the step's next launches are the coarse corrections of
@@ -809,6 +813,12 @@ struct Solver final : SolverBase {
             else launch_coarse_batch<T, T, T, T>(bt, 2 * r, partial, dcounter + 2, derr, stream);
         }
     }
+
+    // Algorithmic bytes of one one-column coarse correction of node p: each point of its
+    // band lies in one child's owned rows and carries that child's r basis columns, read
+    // once for C^H r and once for C y: 2 r n c bytes (n points, c bytes per element of the
+    // basis precision).  The residual and update vectors are not counted.
+    double coarse_bytes(int p) const { return 2.0 * r * (double)pts(p) * sizeof(CT); }
 
     // local row of node p where its second child's owned rows (and basis columns) begin
     int split_row(int p) const { return nodes[nodes[p].child[1]].own_a - nodes[p].ra; }
@@ -836,18 +846,17 @@ struct Solver final : SolverBase {
     // W[p] += C_p A_c^{-1} C_p^H (v - A~_p W[p])
     void coarse_correct(int p, const CT* vin, int nc) {
         if (nc == 1) {
-            // algorithmic: C (2r x N) once, v and w read, w written; C^H r and C y
-            pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + 3.0) * sizeof(CT), 2.0 * 8.0 * 2 * r * pts(p));
+            pbeg(PC_COARSE, coarse_bytes(p), 2.0 * 8.0 * 2 * r * pts(p));
             launch_coarse_batch<T, T, T, T>(one_job(p, vin, W[p], W[p], true), 2 * r, partial, dcounter + 2, derr,
                                             stream);
             pend(PC_COARSE);
             return;
         }
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
-        pbeg(PC_COARSE, (double)pts(p) * (2.0 * r + nc) * sizeof(CT), 8.0 * 2 * r * nc * pts(p));
+        pbeg(PC_COARSE_MC, (double)pts(p) * (2.0 * r + nc) * sizeof(CT), 8.0 * 2 * r * nc * pts(p));
         const int nb = launch_ip_partial_colA<T, T, T>(C[p], R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
                                                        stream);
-        pend(PC_COARSE);
+        pend(PC_COARSE_MC);
         launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
         launch_coarse_updn<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
     }
@@ -918,7 +927,13 @@ struct Solver final : SolverBase {
             // A_c = C_p^H A~_p C_p, then its inverse
             pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT), 8.0 * 2.0 * r * r * pts(p));
             const int split = nodes[nodes[p].child[1]].own_a - nodes[p].ra;
-            const int nb = launch_galerkin_partial<T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS, stream);
+            // FP64 products from the stored basis, or FP32 ones in the opt-in FP32 coarse
+            // variant of the mixed form
+            const int nb = coarse_fp32()
+                               ? launch_galerkin_partial<T, T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS,
+                                                               stream)
+                               : launch_galerkin_partial<T, double>(C[p], geom(p), 2 * r, split, partial,
+                                                                    MAX_PART_BLOCKS, stream);
             pend(PC_GALERKIN);
             launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
         }
@@ -927,13 +942,15 @@ struct Solver final : SolverBase {
         bt.n = 2 * r;
         bt.err = derr;
         int cnt = 0;
-        // the complex64 form eliminates in FP32 and writes its complex64 copy directly
-        const bool fp32 = sizeof(CT) != sizeof(c128);
+        // FP64 elimination in both forms (the opt-in FP32 coarse variant eliminates in
+        // FP32); the complex64 form also gets the inverse rounded to complex64 for its
+        // one-column corrections
+        const bool c64 = sizeof(CT) != sizeof(c128);
         for (int p : lev[l - 1]) {
             bt.A[cnt] = Ainv[p];
-            bt.AT[cnt++] = fp32 ? (void*)AinvT[p] : nullptr;
+            bt.AT[cnt++] = c64 ? (void*)AinvT[p] : nullptr;
         }
-        launch_gj_inverse(bt, cnt, fp32, stream);
+        launch_gj_inverse(bt, cnt, coarse_fp32(), stream);
     }
 
     hh_status setup() override {
@@ -1020,15 +1037,13 @@ struct Solver final : SolverBase {
             // the FP64 residual of the new iterate is formed afterwards as before.
             // with the recursive residual also r' kept, the r columns of A C_0 at each point
             // read and the next residual written; r complex multiply-adds per point
-            const double rby = recur ? (double)N * (r + 2.0) * sizeof(CT) : 0.0;
-            pjoin(PC_COARSE, (double)N * (2.0 * r + 3.0) * sizeof(CT) + (double)N * 2.0 * sizeof(c128) + rby,
-                  2.0 * 8.0 * 2 * r * N + (recur ? 8.0 * r * N : 0.0));
+            pjoin(PC_COARSE, coarse_bytes(0), 2.0 * 8.0 * 2 * r * N + (recur ? 8.0 * r * N : 0.0));
             CoarseBatch rb = one_job(0, RT, dlt, out, true);
             rb.gate = gate;
             if (recur) rb.rr = *recur;
             launch_coarse_batch<T, T, T, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);
         } else {
-            pjoin(PC_COARSE, (double)N * (2.0 * r * sizeof(CT) + 3.0 * sizeof(c128)), 2.0 * 8.0 * 2 * r * N);
+            pjoin(PC_COARSE, coarse_bytes(0), 2.0 * 8.0 * 2 * r * N);
             CoarseBatch rb = one_job(0, rhs, out, out, true);
             rb.gate = gate;
             launch_coarse_batch<T, double, double, double>(rb, 2 * r, partial, dcounter + 2, derr, stream);

@@ -288,13 +288,15 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 
 // ------------------------------------------------------------------- Galerkin
 // partial[blk][a][l] = sum over the block's points of conj(C[pt][a]) * (A~ C)[pt][l].
-// The products and the stencil run in the basis precision T: FP64 for the FP64 form;
-// FP32 for the complex64 form, whose basis is itself rounded to FP32 (the products of
-// GAL_FLUSH 32-point tiles are summed in FP32, then added to FP64 accumulators, so the
-// FP32 rounding stays at the level of 128 points' sum; FP64 on this GPU runs at 1/64
-// of the FP32 rate, so only the outputs a thread owns are flushed).
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* __restrict__ C, OpGeom g, int p,
+// C is stored in TI (complex64 in the mixed form); the stencil and the products run in
+// T.  T = double: FP64 arithmetic on the basis values (a complex64 basis widens exactly),
+// so A_c = C^H A~ C is the FP64 Galerkin matrix of the stored basis.  T = float (the
+// opt-in FP32 coarse variant of the mixed form): the products of GAL_FLUSH 32-point
+// tiles are summed in FP32, then added to FP64 accumulators, so the FP32 rounding stays
+// at the level of 128 points' sum (only the outputs a thread owns are flushed; FP64 on
+// this GPU runs at 1/64 of the FP32 rate).
+template <typename TI, typename T, int KMAX>
+__global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<TI>* __restrict__ C, OpGeom g, int p,
                                                                  int split_row, c128* partial) {
     using CT = cplx<T>;
     extern __shared__ __align__(16) unsigned char gsm_[];
@@ -319,16 +321,16 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
             const int l = e % p;
             const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
             const size_t t = (size_t)l * N + pt;          // column-major basis
-            const CT cv = C[t];
+            const CT cv = cvt<T>(C[t]);
             CT ax = op_diag_t<T>(j, i, g) * cv;
             const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
             const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
             if (g.Sx > 1) {
-                if (i > 0) ax = ax - wj * C[t - 1];
-                if (i < g.Sx - 1) ax = ax - wj * C[t + 1];
+                if (i > 0) ax = ax - wj * cvt<T>(C[t - 1]);
+                if (i < g.Sx - 1) ax = ax - wj * cvt<T>(C[t + 1]);
             }
-            if (j > 0) ax = ax - wi * C[t - g.Sx];
-            if (j < g.b - 1) ax = ax - wi * C[t + g.Sx];
+            if (j > 0) ax = ax - wi * cvt<T>(C[t - g.Sx]);
+            if (j < g.b - 1) ax = ax - wi * cvt<T>(C[t + g.Sx]);
             As[e] = cv;
             Bs[e] = ax;
         }
@@ -360,8 +362,8 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<T>* 
     ip_store_partial<double, KMAX>(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
 }
 
-template <typename T>
-int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
+template <typename TI, typename T>
+int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
                             cudaStream_t s) {
     const size_t N = (size_t)g.b * g.Sx;
     int grid = (int)((N + 127) / 128);
@@ -371,12 +373,14 @@ int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c1
     const int split = nout >= IP_THREADS ? 1 : IP_THREADS / nout;
     const size_t sm = sizeof(cplx<T>) * (size_t)IP_TILE * 2 * p + (split > 1 ? sizeof(c128) * split * nout : 0);
     static std::atomic<unsigned long long> attr4{0}, attrmax{0};
-    smem_limit_once(attr4, k_galerkin_partial<T, 4>, 200 * 1024);
-    smem_limit_once(attrmax, k_galerkin_partial<T, IP_MAXOUT>, 200 * 1024);
+    smem_limit_once(attr4, k_galerkin_partial<TI, T, 4>, 200 * 1024);
+    smem_limit_once(attrmax, k_galerkin_partial<TI, T, IP_MAXOUT>, 200 * 1024);
     // accumulators sized to the outputs a thread owns (p <= 32: at most 4), so that the
     // registers allow two blocks per SM and the grid runs in one wave
-    if (nout <= 4 * IP_THREADS) k_galerkin_partial<T, 4><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
-    else k_galerkin_partial<T, IP_MAXOUT><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
+    if (nout <= 4 * IP_THREADS)
+        k_galerkin_partial<TI, T, 4><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
+    else
+        k_galerkin_partial<TI, T, IP_MAXOUT><<<grid, IP_THREADS, sm, s>>>(C, g, p, split_row, partial);
     note_launch();
     return grid;
 }
@@ -960,8 +964,9 @@ template int launch_ip_partial_colA<float, float, float>(const c64*, const c64*,
                                                         cudaStream_t);
 template int launch_ip_partial_colA<double, double, double>(const c128*, const c128*, int, size_t, int, int, c128*,
                                                             int, cudaStream_t);
-template int launch_galerkin_partial<float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
-template int launch_galerkin_partial<double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t);
+template int launch_galerkin_partial<float, float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
+template int launch_galerkin_partial<float, double>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
+template int launch_galerkin_partial<double, double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t);
 template void launch_qr<float>(c64* const*, int, int, int, c64**, cudaStream_t);
 template void launch_qr<double>(c128* const*, int, int, int, c128**, cudaStream_t);
 template void launch_form_v<float>(const c64*, const c128*, const double*, c64*, int, int, int, cudaStream_t);

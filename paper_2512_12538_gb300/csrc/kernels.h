@@ -174,8 +174,9 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 // Galerkin partials: partial[blk][a][l] = sum_pts conj(C[a][pt]) (A~ C)[l][pt]  (p = 2r,
 // C column-major).
 // split_row >= 0: columns [0, p/2) of C vanish on rows >= split_row and [p/2, p) below it.
-template <typename T>
-int launch_galerkin_partial(const cplx<T>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
+// Galerkin partial sums of A_c = C^H A~ C: basis stored in TI, stencil and products in T
+template <typename TI, typename T>
+int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
                             cudaStream_t s);
 // In-place QR (classical Gram-Schmidt, two passes) of nq independent Sx x m blocks.
 template <typename T>

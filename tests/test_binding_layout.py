@@ -45,6 +45,8 @@ def test_enum_constants_match_the_header(hh):
         assert getattr(_lib, name) == v, name
     macro = re.search(r"#define\s+HH_NOALLOC_MAX_ROWS\s+(\d+)", _header())
     assert macro and _lib.HH_NOALLOC_MAX_ROWS == int(macro.group(1))
+    flag = re.search(r"#define\s+HH_FLAG_COARSE_FP32\s+(\d+)u", _header())
+    assert flag and _lib.HH_FLAG_COARSE_FP32 == int(flag.group(1))
 
 
 def test_every_status_has_its_own_message(hh):

@@ -377,3 +377,28 @@ def test_torch_allocator_hook_and_library_pool_agree(hh):
     assert out[0][0] == out[1][0]
     assert np.array_equal(out[0][1], out[1][1])
     assert rel(out[1][1], us) < 1e-8
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_mixed_form_coarse_precision_variants(hh, flags):
+    """The mixed form's Galerkin matrices and their elimination: FP64 products of the
+    complex64 basis with FP64 elimination (default), or the opt-in FP32 variant
+    (HH_FLAG_COARSE_FP32).  Both give the oracle's coarse operator C A_c^{-1} C^H to the
+    complex64 tolerance and solve to 1e-8 against u*."""
+    cfg = dict(SMALL)
+    P = Problem(2, cfg["n"], cfg["k"])
+    O = OMethod(P, cfg["levels"], cfg["overlap"], cfg["rank"], cfg["oversample"], seed=cfg["seed"])
+    params = hh.make_params(2, cfg["n"], cfg["k"], cfg["levels"], cfg["overlap"], cfg["rank"], cfg["oversample"], 1,
+                            1e-12, 400, "mixed", cfg["seed"], flags=flags)
+    h, _ = hh.hh_setup(params)
+    try:
+        _check_coarse(hh, h, P, O, 1e-3)
+        f = point_source_rhs(cfg["n"], 8)
+        g = random_complex((4, P.S), 9)
+        u = torch.empty((P.S, P.S), dtype=torch.complex128, device="cuda")
+        st = hh.hh_solve(h, dev(f), dev(g), u)
+        err = rel(host(u), direct.solve(P, f, g))
+        print(f"flags={flags}: iters {st.iters}, err {err:.2e}")
+        assert err < 1e-8
+    finally:
+        hh.hh_destroy(h)
