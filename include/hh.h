@@ -59,7 +59,8 @@ typedef enum {
 
 typedef enum {
     HH_PREC_FP64 = 0,     /* complex128 everywhere, FP64 CUDA-core arithmetic          */
-    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches and bases; */
+    HH_PREC_MIXED = 1     /* complex64 subdomain factors, sweeps, sketches and bases  */
+                          /* (the sweeps' multi-vector transforms on the tensor cores);*/
                           /* FP64 residual, Galerkin matrices A_c (FP64 products of   */
                           /* the complex64 basis), their elimination and the sketch   */
                           /* SVD; the outer iteration refines against the FP64        */
@@ -91,6 +92,11 @@ typedef struct {
  * products (FP64 partial sums) and inverts them in FP32, instead of FP64 products and
  * FP64 elimination.  Ignored by the FP64 form. */
 #define HH_FLAG_COARSE_FP32 1u
+/* hh_params.flags: the mixed form runs its leaf sweeps' dense transforms (f^ = V^T f,
+ * x = V x^ over several right-hand sides) on the CUDA cores (FP32 FMA) instead of the
+ * tensor cores (TF32 with a three-term split, FP32 accumulation).  Ignored by the FP64
+ * form, which always uses the CUDA cores. */
+#define HH_FLAG_CUDA_CORE_SWEEPS 2u
 
 typedef enum {
     HH_LEAF_EIGEN = 0,    /* 2D leaves: the block Schur recursion evaluated in the eigenbasis */

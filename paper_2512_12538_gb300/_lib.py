@@ -22,6 +22,7 @@ HH_PREC_FP64, HH_PREC_MIXED = 0, 1
 HH_LEAF_EIGEN, HH_LEAF_BLOCK = 0, 1
 HH_OUTER_ORAS, HH_OUTER_GMRES = 0, 1
 HH_FLAG_COARSE_FP32 = 1
+HH_FLAG_CUDA_CORE_SWEEPS = 2
 
 
 class hh_params(ctypes.Structure):

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhh.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["k_field.cu", "k_dense.cu", "k_leaf.cu", "k_eig.cu", "k_coarse.cu", "hh_solver.cu", "hh_noalloc.cu"]
+SOURCES = ["k_field.cu", "k_dense.cu", "k_leaf.cu", "k_eig.cu", "k_tc.cu", "k_coarse.cu", "hh_solver.cu",
+           "hh_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]

@@ -202,7 +202,7 @@ static hh_status validate(const hh_params* P) {
     if (P->leaf_solver != HH_LEAF_EIGEN && P->leaf_solver != HH_LEAF_BLOCK) return HH_EINVAL;
     if (P->outer != HH_OUTER_ORAS && P->outer != HH_OUTER_GMRES) return HH_EINVAL;
     if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
-    if (P->flags & ~HH_FLAG_COARSE_FP32) return HH_EINVAL;
+    if (P->flags & ~(HH_FLAG_COARSE_FP32 | HH_FLAG_CUDA_CORE_SWEEPS)) return HH_EINVAL;
     if (P->levels > 6) return HH_EINVAL;
     const int Sx = P->dim == 2 ? P->n + 2 : 1;
     if ((long long)(P->n + 2) * Sx >= (1ll << 31)) return HH_EINVAL;   // grid points index in 32 bits
@@ -395,6 +395,9 @@ struct Solver final : SolverBase {
     int eig_fused = 0;          // cluster size of the one-launch single-vector sweep (0: off)
     std::vector<CT*> EV, EXI, EFh;
     std::vector<c128*> ELAM;
+    // complex64 form: the sweep transforms' B operands for the tensor cores (V^T and V)
+    bool tc = false;
+    std::vector<void*> EVT, EVN;
     EigTask *d_etasks_view = nullptr, *d_etasks_own = nullptr, *d_etask_one = nullptr, *d_etasks_pre = nullptr;
     // flexible GMRES
     int mk = 0;                                   // restart length
@@ -462,6 +465,7 @@ struct Solver final : SolverBase {
         for (auto& nd : nodes)
             if (nd.leaf()) b_max = std::max(b_max, nd.b());
         eig = (Sx > 1 && P.leaf_solver == HH_LEAF_EIGEN);
+        tc = eig && sizeof(CT) == sizeof(c64) && !(P.flags & HH_FLAG_CUDA_CORE_SWEEPS);
         mk = P.outer == HH_OUTER_GMRES ? P.restart : 0;
     }
 
@@ -474,6 +478,7 @@ struct Solver final : SolverBase {
         AinvT.assign(nn, nullptr);
         lam.assign(nn, nullptr); ldx.assign(nn, 0);
         EV.assign(nn, nullptr); EXI.assign(nn, nullptr); EFh.assign(nn, nullptr);
+        EVT.assign(nn, nullptr); EVN.assign(nn, nullptr);
         ELAM.assign(nn, nullptr);
         const size_t N = (size_t)Sy * Sx;
         u = a.take<c128>(N); ut = a.take<c128>(N); bvec = a.take<c128>(N); res = a.take<c128>(N);
@@ -509,6 +514,10 @@ struct Solver final : SolverBase {
                 EXI[id] = a.take<CT>((size_t)Sx * b);
                 ELAM[id] = a.take<c128>(b);
                 EFh[id] = a.take<CT>(np * nmax);
+                if (tc) {
+                    EVT[id] = a.take<unsigned char>(tc_vemb_bytes(b_max));
+                    EVN[id] = a.take<unsigned char>(tc_vemb_bytes(b_max));
+                }
             } else {
                 ldx[id] = leaf_ldx(nd.b(), (int)sizeof(CT));
                 X[id] = a.take<CT>(Sx == 1 ? (size_t)nd.b() : (size_t)Sx * nd.b() * ldx[id]);
@@ -617,7 +626,15 @@ struct Solver final : SolverBase {
         k.Sx = Sx;
         k.w0 = 0;
         k.w1 = k.b;
+        k.vt_emb = EVT[id];
+        k.vn_emb = EVN[id];
         return k;
+    }
+    // The three-stage sweep of several right-hand sides: transforms on the tensor cores
+    // in the complex64 form, else on the CUDA cores; the line recursions in between.
+    void eig_sweep_stage(int stg, const EigTask* tasks, int ntasks, int nc) {
+        if (tc && stg != 1) launch_tc_transform(stg == 0 ? 0 : 1, tasks, ntasks, b_max, Sx, nc, derr, stream);
+        else launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream);
     }
     void upload_eig_view_tasks(int nc) {
         std::vector<EigTask> t;
@@ -708,7 +725,7 @@ struct Solver final : SolverBase {
                     else { fl += 8.0 * b * b * sx * nc; by += sizeof(CT) * (b * b + 2.0 * b * sx * nc); }
                 }
                 pbeg(PC_TIN + stg, by, fl);
-                launch_eig_sweep_stage<T>(stg, tasks, nl, b_max, Sx, nc, stream);
+                eig_sweep_stage(stg, tasks, nl, nc);
                 pend(PC_TIN + stg);
             }
             return;
@@ -955,6 +972,7 @@ struct Solver final : SolverBase {
 
     hh_status setup() override {
         eig_fused = eig ? eig_sweep_fused_ready<T>(b_max, Sx) : 0;
+        if (tc && !tc_transform_ready()) return HH_ECUDA;
         zero(derr, sizeof(int) * 4);
         zero(dcounter, sizeof(unsigned) * 4);
         for (int id = 1; id < nn; ++id) zero(Vs[id], sizeof(CT) * pts(id) * nmax);
@@ -977,6 +995,7 @@ struct Solver final : SolverBase {
         pbeg(PC_FACTOR);
         if (eig) launch_eig_factor<T>(d_etasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
         else launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
+        if (tc) launch_tc_prepare_v(d_etasks_own, (int)lev[L].size(), b_max, stream);
         pend(PC_FACTOR);
         for (int l = L; l >= 1; --l) sketch_level(l);
         upload_pre_tasks();
@@ -1513,7 +1532,8 @@ struct Solver final : SolverBase {
             ck(cudaMemcpyAsync(d_etask_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
             // the same kernels as inside a solve: one launch for a single vector
             if (nc == 1 && eig_fused) launch_eig_sweep_fused<T>(eig_fused, d_etask_one, 1, nodes[id].b(), Sx, stream);
-            else launch_eig_sweep<T>(d_etask_one, 1, nodes[id].b(), Sx, nc, stream);
+            else
+                for (int stg = 0; stg < 3; ++stg) eig_sweep_stage(stg, d_etask_one, 1, nc);
         } else {
             LeafTask k;
             k.X = X[id];

@@ -232,7 +232,22 @@ struct EigTask {
     int Sx;           // columns of the leaf's problem (tasks of several problems may share a launch)
     int w0, w1;       // the one-launch sweep writes local rows [w0, w1) only, row a to
                       // W + (a - w0) Sx (the three-stage sweep: all rows, w0 = 0, w1 = b)
+    const void* vt_emb;   // complex64 form: V^T and V as the tensor-core transforms' B operand
+    const void* vn_emb;   // (tc_prepare_v layout; null where the transforms run on CUDA cores)
 };
+
+// ---- tensor-core transforms (k_tc.cu) -----------------------------------------------
+// Bytes of one B operand (one leaf, one transform) for bands of up to b_max rows.
+size_t tc_vemb_bytes(int b_max);
+// Fills every task's vt_emb / vn_emb from its V (complex64).
+void launch_tc_prepare_v(const EigTask* d_tasks, int ntasks, int b_max, cudaStream_t s);
+// 1 when the transform kernel can run on the current device (its shared-memory limit set).
+int tc_transform_ready();
+// The complex64 sweep transforms on the tensor cores: which = 0, Fh = V^T F; which = 1,
+// W = V Fh (layouts as the three-stage sweep).  err: device status word (DEV_TIMEOUT on a
+// bounded wait that gave up).
+void launch_tc_transform(int which, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, int* err,
+                         cudaStream_t s);
 template <typename T>
 void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,
                        cudaStream_t s);

@@ -45,8 +45,9 @@ def test_enum_constants_match_the_header(hh):
         assert getattr(_lib, name) == v, name
     macro = re.search(r"#define\s+HH_NOALLOC_MAX_ROWS\s+(\d+)", _header())
     assert macro and _lib.HH_NOALLOC_MAX_ROWS == int(macro.group(1))
-    flag = re.search(r"#define\s+HH_FLAG_COARSE_FP32\s+(\d+)u", _header())
-    assert flag and _lib.HH_FLAG_COARSE_FP32 == int(flag.group(1))
+    for name in ("HH_FLAG_COARSE_FP32", "HH_FLAG_CUDA_CORE_SWEEPS"):
+        flag = re.search(r"#define\s+" + name + r"\s+(\d+)u", _header())
+        assert flag and getattr(_lib, name) == int(flag.group(1)), name
 
 
 def test_every_status_has_its_own_message(hh):

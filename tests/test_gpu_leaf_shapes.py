@@ -55,10 +55,14 @@ def _oracle(name):
     return _oracles[name]
 
 
+# mixed form, eigenbasis path: the multi-vector transforms on the tensor cores (default)
+# or on the CUDA cores (HH_FLAG_CUDA_CORE_SWEEPS)
+CASES = [(ls, pr, 0) for ls in ("eigen", "block") for pr in ("fp64", "mixed")] + [("eigen", "mixed", 2)]
+
+
 @pytest.mark.parametrize("name", ["n255", "n1023"])
-@pytest.mark.parametrize("leaf_solver", ["eigen", "block"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_leaf_solve_at_full_size_shapes(hh, name, leaf_solver, precision):
+@pytest.mark.parametrize("leaf_solver,precision,flags", CASES, ids=lambda c: str(c))
+def test_leaf_solve_at_full_size_shapes(hh, name, leaf_solver, precision, flags):
     w = SHAPES[name]
     if leaf_solver == "block" and precision == "fp64" and name == "n1023":
         # a 132 x 132 complex128 inverse does not fit one block's shared memory: the
@@ -71,7 +75,7 @@ def test_leaf_solve_at_full_size_shapes(hh, name, leaf_solver, precision):
         return
     P, O = _oracle(name)
     p = hh.make_params(2, w.n, w.k, w.levels, w.overlap, w.rank, w.oversample, 1, 1e-10, 10, precision, 1,
-                       leaf_solver)
+                       leaf_solver, flags=flags)
     h, _ = hh.hh_setup(p)
     m = w.rank + w.oversample
     try:
@@ -87,7 +91,7 @@ def test_leaf_solve_at_full_size_shapes(hh, name, leaf_solver, precision):
                 torch.cuda.synchronize()
                 want = O.leaf_solve(leaf, v)
                 err = float(np.linalg.norm(x.cpu().numpy() - want) / np.linalg.norm(want))
-                print(f"{name} {leaf_solver} {precision} leaf {leaf} (b={nd.b}) nc={nc}: {err:.2e}")
+                print(f"{name} {leaf_solver} {precision} flags={flags} leaf {leaf} (b={nd.b}) nc={nc}: {err:.2e}")
                 assert err < TOL[precision], (leaf, nc, err)
     finally:
         hh.hh_destroy(h)
