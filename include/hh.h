@@ -345,6 +345,20 @@ hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, lo
 /* Number of CUDA kernels this library has launched in the calling process. */
 unsigned long long hh_launch_count(void);
 
+/* --------------------------------------------------------------------------------
+ * Failure detection (testing aid; the paper has no counterpart).  Every device-side
+ * wait of the library is bounded: a wait that runs out records HH_ETIMEOUT, its kernel
+ * stops issuing work, drains what it has in flight and returns, and the call that
+ * synchronises reports HH_ETIMEOUT with the context still usable.
+ * -------------------------------------------------------------------------------- */
+/* Caps the polls of the give-up waits of the kernels launched from now on in this
+ * process: the coarse corrections' cooperative grid barrier and the tensor-core
+ * transforms' waits for their operands and MMAs.  polls = 0 makes every such wait give
+ * up at once (how a test makes a wait run out without a fault); polls < 0 restores the
+ * defaults (about a second).  CUDA graphs captured meanwhile keep the value of their
+ * capture, so a test sets it before creating the handle it checks.  Process-wide. */
+hh_status hh_debug_set_wait_limit(long long polls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ def _load():
         "hh_profile_read": (i, [vp, i, P(d), P(ctypes.c_longlong), P(d), P(d)]),
         "hh_launch_count": (ctypes.c_ulonglong, []),
         "hh_residual_noalloc": (i, [i, i, d, vp, vp, vp, vp, P(d)]),
+        "hh_debug_set_wait_limit": (i, [ctypes.c_longlong]),
         "hh_setup_batch": (i, [P(hh_params), i, vp, P(vp)]),
         "hh_server_create": (i, [sz, i, P(vp)]),
         "hh_server_submit": (i, [vp, P(hh_params), vp, vp, vp, P(ctypes.c_ulonglong)]),
@@ -337,3 +338,8 @@ def hh_profile_read(h, work=False) -> dict:
 
 def hh_launch_count() -> int:
     return int(LIB.hh_launch_count())
+
+
+def hh_debug_set_wait_limit(polls: int) -> None:
+    """Cap the polls of the library's give-up waits (0: give up at once; < 0: defaults)."""
+    _check(LIB.hh_debug_set_wait_limit(int(polls)), "hh_debug_set_wait_limit")

@@ -2610,6 +2610,11 @@ hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, lo
 }
 unsigned long long hh_launch_count(void) { return hh::g_launches.load(); }
 
+hh_status hh_debug_set_wait_limit(long long polls) {
+    hh::set_wait_polls(polls < 0 ? -1 : polls);
+    return HH_OK;
+}
+
 hh_status hh_sketch_samples(hh_handle* h, int child, void* d_out, void* stream) {
     if (!h) return HH_EINVAL;
     h->s->stream = (cudaStream_t)stream;

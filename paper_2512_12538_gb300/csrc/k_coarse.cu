@@ -4,6 +4,8 @@
 // consecutive points.
 #include <algorithm>
 
+#include <atomic>
+
 #include "kernels.h"
 
 namespace hh {
@@ -34,11 +36,19 @@ void launch_build_basis(const cplx<T>* src, size_t src0, int r, cplx<T>* C, size
     note_launch();
 }
 
+// ------------------------------------------------------------- bounded waits
+static std::atomic<long long> g_wait_polls{-1};
+void set_wait_polls(long long polls) { g_wait_polls.store(polls); }
+long long wait_polls(long long dflt) {
+    const long long v = g_wait_polls.load();
+    return v < 0 ? dflt : v;
+}
+
 // ------------------------------------------------------- fused one-column correction
 // Barrier over a cooperative grid (all blocks resident): arrive on a counter, the last
 // arriver resets it and advances the generation; the others wait on the generation with
-// a bounded spin (DEV_TIMEOUT and false after about a second).
-__device__ bool grid_barrier(unsigned* bar, int* err) {
+// a bounded spin (DEV_TIMEOUT and false after `limit` polls, by default about a second).
+__device__ bool grid_barrier(unsigned* bar, int* err, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -47,6 +57,8 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
         const unsigned g0 = *gen;
         __threadfence();
         if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            // the last arriver releases the others (also when some have given up: the
+            // counter and generation are consistent again for the next launch)
             bar[0] = 0u;            // no block touches the counter again before the generation moves
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -54,8 +66,8 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
             // spin without sleeping first (the release is usually a few microseconds
             // away), then back off; give up after about a second
             long long it = 0;
-            while (*gen == g0) {
-                if (++it > (1ll << 24)) {
+            while (limit == 0 || *gen == g0) {   // limit 0: give up at once (testing form)
+                if (++it > limit) {
                     atomicExch(err, DEV_TIMEOUT);
                     ok = 0;
                     break;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
         partial[(size_t)blockIdx.x * CB_COLS + threadIdx.x] = t;
     }
     cp_async_wait_all();
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(bar, err, bt.wait_polls)) return;
     // phase 2: the same sums in every block of the job: 8 threads per column, the
     // partials of the column's set b = sub, sub + 8, ... in order, then a fixed shuffle
     // tree
@@ -331,6 +343,7 @@ int coarse_batch_max_grid() {
 template <typename TC, typename TV, typename TW, typename TO>
 void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s) {
     if (bt.njobs < 1) return;
+    bt.wait_polls = wait_polls(1ll << 24);
     // blocks per job: one per 256 points, at most 152 per job (phase 2 reads every partial
     // of the job), within the co-resident total
     const int mg = coarse_batch_max_grid<TC, TV, TW, TO>();

@@ -30,6 +30,7 @@
 // Every wait is bounded: a wait that gives up records DEV_TIMEOUT, the CTA stops
 // issuing work, waits (bounded) for its tensor-core operations in flight, frees its
 // tensor memory and returns.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 
@@ -113,9 +114,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Bounded wait shared by all threads: false (and the error word set) on timeout.
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err) {
-    if (mbar_wait_bounded(bar, parity, TC_WAIT_LIMIT)) return true;
+// Bounded wait (thread 0): false, and the error word set, after `limit` polls (limit 0:
+// give up at once, the testing form of a wait that runs out).
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, uint32_t limit, int* err) {
+    if (limit > 0 && mbar_wait_bounded(bar, parity, limit)) return true;
     atomicCAS(err, DEV_OK, DEV_TIMEOUT);
     return false;
 }
@@ -184,7 +186,7 @@ void launch_tc_prepare_v(const EigTask* d_tasks, int ntasks, int b_max, cudaStre
 // along the input's contiguous column index p.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* __restrict__ tasks, int ntasks,
                                                                 int which, int Sx, int nrhs, int b_max,
-                                                                int tiles_per_task, int* err) {
+                                                                int tiles_per_task, uint32_t limit, int* err) {
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
     unsigned char* tsm = (unsigned char*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(tsm + 2 * TC_STAGE_BYTES);       // bulk copy of B landed, per stage
@@ -224,11 +226,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
     // Only thread 0 waits on the barriers (and issues the MMAs); the others learn the
     // outcome through the shared abort word after a block barrier, so every thread takes
     // the same path and the block barriers stay matched.
+    //
+    // Each thread stages column j = tid % 64 of the tile and the K quads kq = tid / 64,
+    // tid / 64 + 2, ...: 16 complex values per chunk, loaded into registers one chunk
+    // ahead (the loads of chunk q + 1, or of the next tile's first chunk, are in flight
+    // while chunk q's MMAs are issued and run).
+    const int jcol = tid & 63, kq0 = tid >> 6;
+    c64 pre[TC_KC / 8][4];
+    auto load_chunk = [&](int t, int q) {
+        const EigTask& tq = tasks[t / tiles_per_task];
+        const int p = (t % tiles_per_task) * TC_COLS + jcol;
+        const c64* src = (const c64*)(which == 0 ? tq.F : tq.Fh);
+        const int bb = tq.b;
+#pragma unroll
+        for (int u = 0; u < TC_KC / 8; ++u)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = q * TC_KC + (kq0 + 2 * u) * 4 + i;
+                float2 v = make_float2(0.f, 0.f);
+                if (p < J && k < bb) v = __ldg((const float2*)(src + (size_t)k * J + p));
+                pre[u][i] = c64{v.x, v.y};
+            }
+    };
+    if (blockIdx.x < ntiles) load_chunk(blockIdx.x, 0);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const EigTask tk = tasks[tile / tiles_per_task];
         const int p0 = (tile % tiles_per_task) * TC_COLS;
         const int b = tk.b;
-        const c64* in = (const c64*)(which == 0 ? tk.F : tk.Fh);
         c64* outp = (c64*)(which == 0 ? tk.Fh : tk.W);
         const unsigned char* bsrc = (const unsigned char*)(which == 0 ? tk.vt_emb : tk.vn_emb);
 
@@ -238,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
             unsigned char* Bs = As + TC_A_BYTES;
             if (tid == 0) {
                 // the stage's previous MMAs must have finished reading it
-                if (use[s] > 0 && !tc_wait(&done[s], (use[s] - 1) & 1, err)) *abort_flag = 1;
+                if (use[s] > 0 && !tc_wait(&done[s], (use[s] - 1) & 1, limit, err)) *abort_flag = 1;
                 else {
                     mbar_arrive_expect_tx(&full[s], g.b_bytes);
                     bulk_g2s(Bs, bsrc + (size_t)q * g.b_bytes, g.b_bytes, &full[s]);
@@ -247,40 +271,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
             }
             __syncthreads();
             if (*abort_flag) { ok = false; break; }
-            // A tile chunk: rows 2j + c, k in [32q, 32q + 32): split and transposed
-            {
-                const int j = tid & 63;
-                const int p = p0 + j;
-                for (int kq = tid >> 6; kq < TC_KC / 4; kq += TC_THREADS / 64) {
-                    float re[4], im[4];
+            // A tile chunk from the registers: rows 2j + c, split and transposed
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int k = q * TC_KC + kq * 4 + i;
-                        c64 v = {0.f, 0.f};
-                        if (p < J && k < b) v = in[(size_t)k * J + p];
-                        re[i] = v.re;
-                        im[i] = v.im;
-                    }
-                    uint4 hr, lr, hm, lm;
-                    tf32_split(re[0], hr.x, lr.x);
-                    tf32_split(re[1], hr.y, lr.y);
-                    tf32_split(re[2], hr.z, lr.z);
-                    tf32_split(re[3], hr.w, lr.w);
-                    tf32_split(im[0], hm.x, lm.x);
-                    tf32_split(im[1], hm.y, lm.y);
-                    tf32_split(im[2], hm.z, lm.z);
-                    tf32_split(im[3], hm.w, lm.w);
-                    const uint32_t o_re = kmaj_off(2 * j, kq * 4), o_im = kmaj_off(2 * j + 1, kq * 4);
-                    *(uint4*)(As + o_re) = hr;
-                    *(uint4*)(As + o_im) = hm;
-                    *(uint4*)(As + TC_A_BYTES / 2 + o_re) = lr;
-                    *(uint4*)(As + TC_A_BYTES / 2 + o_im) = lm;
-                }
+            for (int u = 0; u < TC_KC / 8; ++u) {
+                uint4 hr, lr, hm, lm;
+                tf32_split(pre[u][0].re, hr.x, lr.x);
+                tf32_split(pre[u][1].re, hr.y, lr.y);
+                tf32_split(pre[u][2].re, hr.z, lr.z);
+                tf32_split(pre[u][3].re, hr.w, lr.w);
+                tf32_split(pre[u][0].im, hm.x, lm.x);
+                tf32_split(pre[u][1].im, hm.y, lm.y);
+                tf32_split(pre[u][2].im, hm.z, lm.z);
+                tf32_split(pre[u][3].im, hm.w, lm.w);
+                const int kq = kq0 + 2 * u;
+                const uint32_t o_re = kmaj_off(2 * jcol, kq * 4), o_im = kmaj_off(2 * jcol + 1, kq * 4);
+                *(uint4*)(As + o_re) = hr;
+                *(uint4*)(As + o_im) = hm;
+                *(uint4*)(As + TC_A_BYTES / 2 + o_re) = lr;
+                *(uint4*)(As + TC_A_BYTES / 2 + o_im) = lm;
             }
+            // prefetch the next chunk (this tile's next, or the next tile's first)
+            if (q + 1 < g.nq) load_chunk(tile, q + 1);
+            else if (tile + (int)gridDim.x < ntiles) load_chunk(tile + gridDim.x, 0);
             fence_async_smem();
             __syncthreads();
             if (tid == 0) {
-                if (tc_wait(&full[s], use[s] & 1, err)) {
+                if (tc_wait(&full[s], use[s] & 1, limit, err)) {
                     copy_pending[s] = false;
                     tc_fence_after();
                     const uint32_t a_hi = smem_u32(As), a_lo = a_hi + TC_A_BYTES / 2;
@@ -312,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         // of each warp pair up
         if (tid == 0) {
             const int sl = (chunk - 1) & 1;
-            if (!tc_wait(&done[sl], (use[sl] - 1) & 1, err)) *abort_flag = 1;
+            if (!tc_wait(&done[sl], (use[sl] - 1) & 1, limit, err)) *abort_flag = 1;
         }
         __syncthreads();
         if (*abort_flag) { ok = false; break; }
@@ -378,7 +394,9 @@ void launch_tc_transform(int which, const EigTask* d_tasks, int ntasks, int b_ma
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int grid = ntasks * tiles_per_task;
     if (grid > sms) grid = sms > 0 ? sms : 1;     // one block per SM (shared and tensor memory)
-    k_tc_transform<<<grid, TC_THREADS, TC_SMEM, s>>>(d_tasks, ntasks, which, Sx, nrhs, b_max, tiles_per_task, err);
+    const uint32_t limit = (uint32_t)std::min<long long>(wait_polls(TC_WAIT_LIMIT), 0xFFFFFFFFll);
+    k_tc_transform<<<grid, TC_THREADS, TC_SMEM, s>>>(d_tasks, ntasks, which, Sx, nrhs, b_max, tiles_per_task, limit,
+                                                     err);
     note_launch();
 }
 

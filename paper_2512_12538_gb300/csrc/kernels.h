@@ -143,7 +143,16 @@ struct CoarseBatch {
     int njobs;
     const int* gate;       // may be null: when the word is nonzero at launch, nothing is done
     CoarseRecur rr;
+    long long wait_polls;  // polls of the grid barrier's wait before it gives up (set by the launcher)
 };
+
+// Polls a bounded device-side wait makes before giving up with DEV_TIMEOUT: the
+// cooperative grid barrier of the coarse corrections and the tensor-core transforms'
+// waits for their operands and MMAs.  Negative: each wait's default (about a second).
+// Read when a kernel is launched (a captured graph keeps the value of its capture).
+// The drains after a wait gave up always use the default.
+void set_wait_polls(long long polls);
+long long wait_polls(long long dflt);
 template <typename TC, typename TV, typename TW, typename TO>
 void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s);
 // W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
