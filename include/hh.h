@@ -71,7 +71,7 @@ typedef enum {
 typedef struct {
     int dim;              /* 1 or 2                                                      */
     int n;                /* interior nodes per side; S = n + 2, h = 1/(n+1); n >= 4     */
-    double k;             /* wavenumber k > 0 (Eq. (1))                                  */
+    double k;             /* wavenumber k > 0 (Eq. (1)); see k_rows for layered media     */
     int levels;           /* hierarchy depth L >= 1: 2^L leaf bands (Sec. 1)             */
     int overlap;          /* rows shared by two siblings; even, >= 2; e = overlap/2 rows */
                           /* added on each side of a non-overlapping split (Sec. 3)      */
@@ -86,6 +86,12 @@ typedef struct {
     int outer;            /* hh_outer                                                    */
     int restart;          /* Krylov vectors per GMRES cycle (outer = HH_OUTER_GMRES), 1..64 */
     unsigned flags;       /* HH_FLAG_* bits; 0 for the defaults                           */
+    const double* k_rows; /* layered media (Sec. 3.3): HOST array of S = n + 2 wavenumbers, */
+                          /* one per grid row (k = omega / c(y)), or NULL for the constant k; */
+                          /* copied by hh_setup (hh_server_submit: keep it valid until the    */
+                          /* request has finished).  Each k_rows[j] > 0 and finite.  2D      */
+                          /* problems then need leaf_solver = HH_LEAF_BLOCK (the eigenbasis  */
+                          /* path takes one k per band); the paper solves them with GMRES    */
 } hh_params;
 
 /* hh_params.flags: the mixed form forms the Galerkin matrices A_c = C^H A~ C from FP32

@@ -31,7 +31,7 @@ class hh_params(ctypes.Structure):
                 ("oversample", ctypes.c_int), ("n_inner", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("leaf_solver", ctypes.c_int), ("outer", ctypes.c_int),
-                ("restart", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("restart", ctypes.c_int), ("flags", ctypes.c_uint), ("k_rows", ctypes.c_void_p)]
 
 
 class hh_stats(ctypes.Structure):
@@ -125,15 +125,23 @@ def _check(st: int, where: str, ok=(HH_OK,)):
 
 def make_params(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10, n_inner=1,
                 tol=1e-10, max_iter=200, precision=HH_PREC_FP64, seed=0, leaf_solver=HH_LEAF_EIGEN,
-                outer=HH_OUTER_ORAS, restart=40, flags=0) -> hh_params:
+                outer=HH_OUTER_ORAS, restart=40, flags=0, k_rows=None) -> hh_params:
     if isinstance(precision, str):
         precision = {"fp64": HH_PREC_FP64, "mixed": HH_PREC_MIXED}[precision]
     if isinstance(leaf_solver, str):
         leaf_solver = {"eigen": HH_LEAF_EIGEN, "block": HH_LEAF_BLOCK}[leaf_solver]
     if isinstance(outer, str):
         outer = {"oras": HH_OUTER_ORAS, "gmres": HH_OUTER_GMRES}[outer]
-    return hh_params(dim, n, float(k), levels, overlap, rank, oversample, n_inner, float(tol), max_iter,
-                     precision, seed, leaf_solver, outer, restart, flags)
+    kr = None
+    if k_rows is not None:
+        import numpy as np
+        kr = np.ascontiguousarray(k_rows, dtype=np.float64)
+        if kr.shape != (n + 2,):
+            raise ValueError("k_rows needs one wavenumber per grid row (n + 2 values)")
+    p = hh_params(dim, n, float(k), levels, overlap, rank, oversample, n_inner, float(tol), max_iter,
+                  precision, seed, leaf_solver, outer, restart, flags, None if kr is None else kr.ctypes.data)
+    p._k_rows = kr      # the host array must outlive the calls that read it
+    return p
 
 
 # ------------------------------------------------------------------ allocator hook

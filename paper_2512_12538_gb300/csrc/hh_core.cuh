@@ -45,8 +45,9 @@ template <typename D, typename S> HH_HD cplx<D> cvt(cplx<S> a) { return {(D)a.re
 
 // ------------------------------------------------------------- discrete operator
 // Weighted 5-point operator on a band of `b` rows and Sx columns (Sx == 1: 1D):
-//   (A u)_ij = w_j X_i(u_.j) + w_i Y_j(u_i.) - (kh)^2 w_i w_j u_ij
-//              - i kh (w_j bx_i + w_i by_j) u_ij,
+//   (A u)_ij = w_j X_i(u_.j) + w_i Y_j(u_i.) - (k_j h)^2 w_i w_j u_ij
+//              - i k_j h (w_j bx_i + w_i by_j) u_ij,
+// with k_j = k, or the wavenumber of row j in a layered medium (Sec. 3.3),
 // with w = 1/2 on the band's first/last row and on x = 0, Sx-1 (1 elsewhere), X and Y
 // the second differences halved at the ends, bx/by the boundary flags.  A 1D band has
 // no x-direction: X = 0, w_i = 1, bx = 0.  Every band edge carries the impedance row
@@ -55,6 +56,7 @@ struct OpGeom {
     int b;        // rows in the band
     int Sx;       // columns
     double kh;    // k * h
+    const double* khr;   // k h per row of the band (device; layered media, Sec. 3.3) or null: kh
 };
 
 HH_HD double wrow(int j, int b) { return (j == 0 || j == b - 1) ? 0.5 : 1.0; }
@@ -71,8 +73,9 @@ HH_HD c128 op_diag(int j, int i, const OpGeom& g) {
         cx = xb ? 1.0 : 2.0;
         bx = xb ? 1.0 : 0.0;
     }
-    const double re = wj * cx + wi * cy - g.kh * g.kh * wi * wj;
-    const double im = -g.kh * (wj * bx + wi * (by ? 1.0 : 0.0));
+    const double kh = g.khr ? g.khr[j] : g.kh;
+    const double re = wj * cx + wi * cy - kh * kh * wi * wj;
+    const double im = -kh * (wj * bx + wi * (by ? 1.0 : 0.0));
     return {re, im};
 }
 // The same coefficient evaluated in precision R (the weights and stencil counts are
@@ -88,7 +91,7 @@ template <typename R> HH_HD cplx<R> op_diag_t(int j, int i, const OpGeom& g) {
         cx = xb ? (R)1 : (R)2;
         bx = xb ? (R)1 : (R)0;
     }
-    const R kh = (R)g.kh;
+    const R kh = (R)(g.khr ? g.khr[j] : g.kh);
     return {wj * cx + wi * cy - kh * kh * wi * wj, -kh * (wj * bx + wi * (by ? (R)1 : (R)0))};
 }
 

@@ -203,6 +203,13 @@ static hh_status validate(const hh_params* P) {
     if (P->outer != HH_OUTER_ORAS && P->outer != HH_OUTER_GMRES) return HH_EINVAL;
     if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
     if (P->flags & ~(HH_FLAG_COARSE_FP32 | HH_FLAG_CUDA_CORE_SWEEPS)) return HH_EINVAL;
+    if (P->k_rows) {
+        // layered media: the wavenumber varies across the rows of a band, which the
+        // column-pencil eigenbasis of the 2D leaves does not take (explicit inverses do)
+        if (P->dim == 2 && P->leaf_solver == HH_LEAF_EIGEN) return HH_EINVAL;
+        for (int j = 0; j < P->n + 2; ++j)
+            if (!(P->k_rows[j] > 0.0) || !std::isfinite(P->k_rows[j])) return HH_EINVAL;
+    }
     if (P->levels > 6) return HH_EINVAL;
     const int Sx = P->dim == 2 ? P->n + 2 : 1;
     if ((long long)(P->n + 2) * Sx >= (1ll << 31)) return HH_EINVAL;   // grid points index in 32 bits
@@ -371,6 +378,7 @@ struct Solver final : SolverBase {
     std::vector<double*> lam;
     std::vector<int> ldx;
     c128 *u = nullptr, *ut = nullptr, *bvec = nullptr, *res = nullptr, *gbuf = nullptr;
+    double* khr_dev = nullptr;  // layered media: k h per grid row (device), else null
     CT* RT = nullptr;
     CT* dlt = nullptr;          // the level-1 update of the current step (leaf precision)
     CT* AC0 = nullptr;          // A~_0 C_0: the root's operator on its basis (column-major)
@@ -442,7 +450,8 @@ struct Solver final : SolverBase {
 
     // the mixed form's opt-in FP32 Galerkin products and coarse elimination
     bool coarse_fp32() const { return sizeof(CT) != sizeof(c128) && (P.flags & HH_FLAG_COARSE_FP32); }
-    OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh}; }
+    OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh, khr_at(nodes[id].ra)}; }
+    const double* khr_at(int grow) const { return khr_dev ? khr_dev + grow : nullptr; }
     size_t pts(int id) const { return (size_t)nodes[id].b() * Sx; }
     size_t row_off(int id, int grow, int nc) const { return (size_t)(grow - nodes[id].ra) * Sx * nc; }
 
@@ -488,6 +497,7 @@ struct Solver final : SolverBase {
             RP = a.take<CT>(N);
         }
         gbuf = a.take<c128>(4 * (size_t)S);
+        khr_dev = P.k_rows ? a.take<double>(S) : nullptr;
         RT = a.take<CT>(N * nmax);
         for (auto& nd : nodes) {
             const int id = nd.id;
@@ -582,6 +592,7 @@ struct Solver final : SolverBase {
             k.W = W[id];
             k.b = nd.b();
             k.ldx = ldx[id];
+            k.khr = khr_at(nd.ra);
             if (own) k.F = Vs[id];
             else k.F = R[nd.parent] + (size_t)(nd.ra - nodes[nd.parent].ra) * Sx * 0;  // fixed per call
             t.push_back(k);
@@ -605,6 +616,7 @@ struct Solver final : SolverBase {
             k.W = W[id];
             k.b = nd.b();
             k.ldx = ldx[id];
+            k.khr = khr_at(nd.ra);
             k.F = leaf_input(id, nc);
             key.push_back(k.F);
             t.push_back(k);
@@ -675,6 +687,7 @@ struct Solver final : SolverBase {
                 k.W = W[id];
                 k.b = nd.b();
                 k.ldx = ldx[id];
+                k.khr = khr_at(nd.ra);
                 k.F = F;
                 lt.push_back(k);
             }
@@ -893,7 +906,7 @@ struct Solver final : SolverBase {
             const Node& cn = nodes[c];
             const Node& sn = nodes[cn.sib];
             launch_robin_trace<T>(W[c] + row_off(c, sn.ifrow, m), W[c] + row_off(c, sn.inward, m), Om[c], sn.b(), Sx,
-                                  m, kh, stream);
+                                  m, kh, khr_at(sn.ifrow), stream);
         }
         // Q = orth(Y)
         std::vector<CT*> ys;
@@ -907,7 +920,7 @@ struct Solver final : SolverBase {
             const Node& sn = nodes[cn.sib];
             zero(Vs[c], sizeof(CT) * pts(c) * m);
             launch_adjoint_place<T>(Om[c], Vs[c] + row_off(c, sn.ifrow, m), Vs[c] + row_off(c, sn.inward, m), sn.b(),
-                                    Sx, m, kh, stream);
+                                    Sx, m, kh, khr_at(sn.ifrow), stream);
         }
         apply_M(l, m, true);
         for (int c : cs)
@@ -971,6 +984,13 @@ struct Solver final : SolverBase {
     }
 
     hh_status setup() override {
+        if (khr_dev) {
+            // layered media: k h per grid row (the caller's k_rows times h)
+            std::vector<double> khr(S);
+            for (int j = 0; j < S; ++j) khr[j] = P.k_rows[j] * h;
+            ck(cudaMemcpyAsync(khr_dev, khr.data(), sizeof(double) * S, cudaMemcpyHostToDevice, stream), cerr);
+            ck(cudaStreamSynchronize(stream), cerr);
+        }
         eig_fused = eig ? eig_sweep_fused_ready<T>(b_max, Sx) : 0;
         if (tc && !tc_transform_ready()) return HH_ECUDA;
         zero(derr, sizeof(int) * 4);
@@ -1541,6 +1561,7 @@ struct Solver final : SolverBase {
             k.W = W[id];
             k.b = nodes[id].b();
             k.ldx = ldx[id];
+            k.khr = khr_at(nodes[id].ra);
             ck(cudaMemcpyAsync(d_task_one, &k, sizeof(k), cudaMemcpyHostToDevice, stream), cerr);
             launch_sweep<T>(d_task_one, 1, nodes[id].b(), Sx, nc, derr, stream);
         }
@@ -1560,12 +1581,12 @@ struct Solver final : SolverBase {
             launch_copy<double, T>(in, Vs[c] + row_off(c, cn.ifrow, nc), (size_t)Sx * nc, false, false, stream);
             apply_M(l, nc, true);
             launch_robin_trace<T>(W[c] + row_off(c, sn.ifrow, nc), W[c] + row_off(c, sn.inward, nc), Om[c], sn.b(), Sx,
-                                  nc, kh, stream);
+                                  nc, kh, khr_at(sn.ifrow), stream);
             launch_copy<T, double>(Om[c], out, (size_t)Sx * nc, false, false, stream);
         } else {
             launch_copy<double, T>(in, Om[c], (size_t)Sx * nc, false, false, stream);
             launch_adjoint_place<T>(Om[c], Vs[c] + row_off(c, sn.ifrow, nc), Vs[c] + row_off(c, sn.inward, nc), sn.b(),
-                                    Sx, nc, kh, stream);
+                                    Sx, nc, kh, khr_at(sn.ifrow), stream);
             apply_M(l, nc, true);
             launch_copy<T, double>(W[c] + row_off(c, cn.ifrow, nc), out, (size_t)Sx * nc, false, true, stream);
         }

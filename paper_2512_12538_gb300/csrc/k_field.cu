@@ -351,8 +351,9 @@ void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, 
 // row (X halved by w_j = 1/2), -w_i to the inward row.
 template <typename T>
 __global__ void k_robin_trace(const cplx<T>* __restrict__ uif, const cplx<T>* __restrict__ uin,
-                              cplx<T>* __restrict__ Y, int b_s, int Sx, int nc, double kh) {
-    const OpGeom g{b_s, Sx, kh};
+                              cplx<T>* __restrict__ Y, int b_s, int Sx, int nc, double kh,
+                              const double* khr_row) {
+    const OpGeom g{b_s, Sx, kh, khr_row};
     const size_t total = (size_t)Sx * nc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
@@ -369,16 +370,17 @@ __global__ void k_robin_trace(const cplx<T>* __restrict__ uif, const cplx<T>* __
 }
 template <typename T>
 void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, int b_s, int Sx, int nc,
-                        double kh, cudaStream_t s) {
+                        double kh, const double* khr_row, cudaStream_t s) {
     const size_t total = (size_t)Sx * nc;
-    k_robin_trace<T><<<grid_for(total, 256), 256, 0, s>>>(u_if, u_in, Y, b_s, Sx, nc, kh);
+    k_robin_trace<T><<<grid_for(total, 256), 256, 0, s>>>(u_if, u_in, Y, b_s, Sx, nc, kh, khr_row);
     note_launch();
 }
 
 template <typename T>
 __global__ void k_adjoint_place(const cplx<T>* __restrict__ Q, cplx<T>* __restrict__ vif,
-                                cplx<T>* __restrict__ vin, int b_s, int Sx, int nc, double kh) {
-    const OpGeom g{b_s, Sx, kh};
+                                cplx<T>* __restrict__ vin, int b_s, int Sx, int nc, double kh,
+                                const double* khr_row) {
+    const OpGeom g{b_s, Sx, kh, khr_row};
     const size_t total = (size_t)Sx * nc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
@@ -396,9 +398,9 @@ __global__ void k_adjoint_place(const cplx<T>* __restrict__ Q, cplx<T>* __restri
 }
 template <typename T>
 void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_s, int Sx, int nc,
-                          double kh, cudaStream_t s) {
+                          double kh, const double* khr_row, cudaStream_t s) {
     const size_t total = (size_t)Sx * nc;
-    k_adjoint_place<T><<<grid_for(total, 256), 256, 0, s>>>(Q, v_if, v_in, b_s, Sx, nc, kh);
+    k_adjoint_place<T><<<grid_for(total, 256), 256, 0, s>>>(Q, v_if, v_in, b_s, Sx, nc, kh, khr_row);
     note_launch();
 }
 
@@ -547,9 +549,9 @@ HH_COPY(double, float)
 HH_COPY(float, double)
 
 #define HH_PREC(T)                                                                                    \
-    template void launch_robin_trace<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, int, int, int, double, \
+    template void launch_robin_trace<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, int, int, int, double, const double*, \
                                         cudaStream_t);                                                \
-    template void launch_adjoint_place<T>(const cplx<T>*, cplx<T>*, cplx<T>*, int, int, int, double,   \
+    template void launch_adjoint_place<T>(const cplx<T>*, cplx<T>*, cplx<T>*, int, int, int, double, const double*,   \
                                           cudaStream_t);                                              \
     template void launch_sketch<T>(cplx<T>*, int, int, int, unsigned long long, cudaStream_t);
 

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_factor2d(const LeafTask* __restrict__ t
     cplx<T>* col = M + b * b;
     cplx<T>* row = col + b;
     int* perm = (int*)(row + b);
-    const OpGeom g{b, Sx, kh};
+    const OpGeom g{b, Sx, kh, tk.khr};
     const size_t step = (size_t)b * ldx;
     for (int i = 0; i < Sx; ++i) {
         // S_i = D_i - W X_{i-1} W, built in place over X_{i-1}
@@ -135,7 +135,7 @@ __global__ void k_factor1d(const LeafTask* __restrict__ tasks, int ntasks, doubl
     if (t >= ntasks) return;
     const LeafTask tk = tasks[t];
     cplx<T>* X = (cplx<T>*)tk.X;
-    const OpGeom g{tk.b, 1, kh};
+    const OpGeom g{tk.b, 1, kh, tk.khr};
     cplx<double> prev_inv = {0.0, 0.0};
     for (int j = 0; j < tk.b; ++j) {
         // S_j = D_j - (-1) S_{j-1}^{-1} (-1)

@@ -70,13 +70,13 @@ void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, 
 // boundary, u_in = the next row inward (both rows of the child's solution).
 template <typename T>
 void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, int b_s, int Sx, int nc,
-                        double kh, cudaStream_t s);
+                        double kh, const double* khr_row, cudaStream_t s);
 
 // v_if/v_in = rows of A~_s B_s^T conj(Q) (the adjoint trace, conjugated for the
 // conj o solve o conj adjoint); other rows untouched.
 template <typename T>
 void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_s, int Sx, int nc,
-                          double kh, cudaStream_t s);
+                          double kh, const double* khr_row, cudaStream_t s);
 
 // Omega[x][j] (Sx x m) for child `node`: SplitMix64 + Box-Muller, re/im ~ N(0,1/2).
 template <typename T>
@@ -218,6 +218,7 @@ struct LeafTask {
     void* W;          // solutions [b][Sx][nrhs]
     int b;
     int ldx;
+    const double* khr;   // k h per row of the band (layered media) or null: the launch's kh
 };
 template <typename T>
 void launch_factor(const LeafTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,

@@ -81,3 +81,21 @@ def test_block_leaf_path_band_limits(hh):
 def test_footprint_1d(hh):
     p = hh.make_params(dim=1, n=1000, k=62.83, levels=1, overlap=4, rank=1, oversample=0)
     assert 0 < hh.hh_footprint(p) < 64 << 20
+
+
+def test_layered_media_parameters(hh):
+    # host-side validation only: one positive finite wavenumber per grid row, and 2D
+    # leaves on the explicit-inverse path
+    import numpy as np
+    kr = np.full(65, 64.0)
+    assert hh.hh_footprint(hh.make_params(2, 63, 64.0, 2, 2, 16, 10, leaf_solver="block", k_rows=kr)) > 0
+    assert hh.hh_footprint(hh.make_params(1, 63, 64.0, 1, 4, 1, 0, k_rows=kr)) > 0
+    bad = kr.copy()
+    bad[7] = -1.0
+    for p in (hh.make_params(2, 63, 64.0, 2, 2, 16, 10, leaf_solver="eigen", k_rows=kr),
+              hh.make_params(2, 63, 64.0, 2, 2, 16, 10, leaf_solver="block", k_rows=bad)):
+        with pytest.raises(hh.HHError) as ei:
+            hh.hh_footprint(p)
+        assert ei.value.status == hh.HH_EINVAL
+    with pytest.raises(ValueError):
+        hh.make_params(2, 63, 64.0, 2, 2, 16, 10, leaf_solver="block", k_rows=kr[:-1])
