@@ -885,10 +885,10 @@ struct Solver final : SolverBase {
         launch_apply<T, T, T>(W[p], vin, R[p], geom(p), nc, 1.0, nullptr, nullptr, stream);
         pbeg(PC_COARSE_MC, (double)pts(p) * (2.0 * r + nc) * sizeof(CT), 8.0 * 2 * r * nc * pts(p));
         const int nb = launch_ip_partial_colA<T, T, T>(C[p], R[p], nc, pts(p), 2 * r, nc, partial, MAX_PART_BLOCKS,
-                                                       stream);
+                                                       stream, (long long)split_row(p) * Sx);
         pend(PC_COARSE_MC);
         launch_ip_reduce(partial, nb, 2 * r, nc, nullptr, Ainv[p], ycoef[p], stream);
-        launch_coarse_updn<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream);
+        launch_coarse_updn<T, T>(C[p], ycoef[p], W[p], pts(p), 2 * r, nc, stream, (long long)split_row(p) * Sx);
     }
 
     // ------------------------------------------------------------------ set-up

@@ -286,6 +286,14 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
             if ((int)(pt / (unsigned)g.Sx) < J.split) je = p >> 1;
             else j = p >> 1;
         }
+        // sixteen basis loads in flight per thread (the columns are far apart in memory)
+        for (; j + 16 <= je; j += 16) {
+            cplx<TC> cv[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cv[u] = C[(size_t)(j + u) * N + pt];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cfma(a, cv[u], s_y[j + u]);
+        }
         for (; j + 8 <= je; j += 8) {
             cplx<TC> cv[8];
 #pragma unroll
@@ -347,7 +355,12 @@ void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, in
     // blocks per job: one per 256 points, at most 152 per job (phase 2 reads every partial
     // of the job), within the co-resident total
     const int mg = coarse_batch_max_grid<TC, TV, TW, TO>();
-    const int cap = std::max(1, std::min(152, mg / bt.njobs));
+    // jobs too large for the L2 (the basis streams from HBM) take every co-resident block:
+    // there the launch is bound by memory parallelism, not by phase 2's reads
+    size_t nmax = 0;
+    for (int k = 0; k < bt.njobs; ++k) nmax = std::max(nmax, (size_t)bt.job[k].g.b * bt.job[k].g.Sx);
+    const int per_job = nmax * (size_t)p * sizeof(cplx<TC>) > ((size_t)64 << 20) ? 1 << 30 : 152;
+    const int cap = std::max(1, std::min(per_job, mg / bt.njobs));
     // each job's blocks shared out among its (half, column group) sets in proportion to
     // the points each set covers, at least one block per set
     const int ph = p / 2, G = (ph + CB_COLS - 1) / CB_COLS, nsets = 2 * G;
@@ -392,10 +405,13 @@ void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, in
 // chunk (coalesced along the points) and used for all the chunk's columns; y staged in
 // shared memory in the basis precision.  The chunks in separate blocks keep several blocks
 // per SM in flight (the loop over j waits on L2 loads).
-static constexpr int UPD_COLS = 8;
+// split_pt >= 0: the basis's first p/2 columns vanish from point split_pt on and the
+// others before it (a node's two children), so each point reads only its child's half.
+static constexpr int UPD_COLS = 16;
 template <typename TC, typename TW>
 __global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict__ C, const c128* __restrict__ y,
-                                                     cplx<TW>* __restrict__ W, size_t N, int p, int nc) {
+                                                     cplx<TW>* __restrict__ W, size_t N, int p, int nc,
+                                                     long long split_pt) {
     extern __shared__ __align__(16) unsigned char ysm[];
     cplx<TC>* ys = (cplx<TC>*)ysm;   // [p][UPD_COLS]: this chunk's columns of y
     const int c0 = blockIdx.y * UPD_COLS, cn = min(UPD_COLS, nc - c0);
@@ -408,7 +424,12 @@ __global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict_
         cplx<TC> acc[UPD_COLS];
 #pragma unroll
         for (int c = 0; c < UPD_COLS; ++c) acc[c] = {0, 0};
-        for (int j = 0; j < p; ++j) {
+        int j = 0, je = p;
+        if (split_pt >= 0) {
+            if ((long long)pt < split_pt) je = p / 2;
+            else j = p / 2;
+        }
+        for (; j < je; ++j) {
             const cplx<TC> cv = C[(size_t)j * N + pt];
             const cplx<TC>* yr = ys + j * UPD_COLS;
 #pragma unroll
@@ -421,9 +442,10 @@ __global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict_
     }
 }
 template <typename TC, typename TW>
-void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s) {
+void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s,
+                        long long split_pt) {
     const dim3 grid(blocks_for(N, 256, 152 * 8), (nc + UPD_COLS - 1) / UPD_COLS);
-    k_coarse_updn<TC, TW><<<grid, 256, sizeof(cplx<TC>) * p * UPD_COLS, s>>>(C, y, W, N, p, nc);
+    k_coarse_updn<TC, TW><<<grid, 256, sizeof(cplx<TC>) * p * UPD_COLS, s>>>(C, y, W, N, p, nc, split_pt);
     note_launch();
 }
 
@@ -435,7 +457,7 @@ template void launch_coarse_batch<float, double, double, double>(CoarseBatch, in
                                                                  cudaStream_t);
 template void launch_coarse_batch<double, double, double, double>(CoarseBatch, int, void*, unsigned*, int*,
                                                                   cudaStream_t);
-template void launch_coarse_updn<float, float>(const c64*, const c128*, c64*, size_t, int, int, cudaStream_t);
-template void launch_coarse_updn<double, double>(const c128*, const c128*, c128*, size_t, int, int, cudaStream_t);
+template void launch_coarse_updn<float, float>(const c64*, const c128*, c64*, size_t, int, int, cudaStream_t, long long);
+template void launch_coarse_updn<double, double>(const c128*, const c128*, c128*, size_t, int, int, cudaStream_t, long long);
 
 }  // namespace hh

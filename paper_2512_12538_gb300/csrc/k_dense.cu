@@ -68,10 +68,14 @@ __device__ __forceinline__ void ip_store_partial(cplx<ACC>* acc, int p, int q, i
     }
 }
 
+// ACOL: A column-major (column i at A + i lda), staged along the points (coalesced).
+// split_pt >= 0 (ACOL, a node's coarse basis): A's columns [0, p/2) vanish at points
+// >= split_pt and [p/2, p) below it, so a tile on one side skips the other half.
 template <typename TA, typename TB, typename ACC, bool ACOL>
 __global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __restrict__ A, size_t lda,
                                                            const cplx<TB>* __restrict__ B, int ldb,
-                                                           size_t N, int p, int q, c128* partial) {
+                                                           size_t N, int p, int q, c128* partial,
+                                                           long long split_pt = -1) {
     extern __shared__ __align__(16) unsigned char ipsm[];
     using CA = cplx<ACC>;
     CA* As = (CA*)ipsm;
@@ -85,28 +89,37 @@ __global__ void __launch_bounds__(IP_THREADS) k_ip_partial(const cplx<TA>* __res
     const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
         const int rows = (int)min((size_t)IP_TILE, n1 - t0);
+        // columns of A that can be nonzero on this tile: [ilo, ihi) (ihi = 0: all)
+        int ilo = 0, ihi = 0, c_lo = 0, c_n = p;
+        if (ACOL && split_pt >= 0) {
+            if ((long long)(t0 + rows) <= split_pt) { ihi = p / 2; c_n = p / 2; }
+            else if ((long long)t0 >= split_pt) { ilo = p / 2; ihi = p; c_lo = p / 2; c_n = p - p / 2; }
+        }
         {
-            // 8 loads in flight per thread before the shared-memory stores
-            const int na = rows * p, nbq = rows * q;
+            // 8 loads in flight per thread before the shared-memory stores; a column-major
+            // A is read along the points (element e: column c_lo + e / rows, point e % rows)
+            const int na = rows * c_n, nbq = rows * q;
             for (int base = threadIdx.x; base < na + nbq; base += 8 * IP_THREADS) {
                 cplx<ACC> tmp[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int e = base + u * IP_THREADS;
-                    if (e < na) tmp[u] = ACOL ? cvt<ACC>(A[(size_t)(e % p) * lda + t0 + e / p])
+                    if (e < na) tmp[u] = ACOL ? cvt<ACC>(A[(size_t)(c_lo + e / rows) * lda + t0 + e % rows])
                                               : cvt<ACC>(A[(t0 + e / p) * lda + e % p]);
                     else if (e < na + nbq) { const int e2 = e - na; tmp[u] = cvt<ACC>(B[(t0 + e2 / q) * ldb + e2 % q]); }
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int e = base + u * IP_THREADS;
-                    if (e < na) As[e] = tmp[u];
-                    else if (e < na + nbq) Bs[e - na] = tmp[u];
+                    if (e < na) {
+                        if (ACOL) As[(e % rows) * p + c_lo + e / rows] = tmp[u];
+                        else As[e] = tmp[u];
+                    } else if (e < na + nbq) Bs[e - na] = tmp[u];
                 }
             }
         }
         __syncthreads();
-        ip_tile_accumulate<ACC>(As, Bs, rows, p, q, split, acc, 0, 0);
+        ip_tile_accumulate<ACC>(As, Bs, rows, p, q, split, acc, ilo, ihi);
         __syncthreads();
     }
     ip_store_partial<ACC>(acc, p, q, split, red, partial + (size_t)blockIdx.x * nout);
@@ -192,14 +205,14 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
 // partial[blk][i][j] = sum conj(A[i * N + n]) B[n * ldb + j] with A column-major (p x N).
 template <typename TA, typename TB, typename ACC>
 int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t N, int p, int q, c128* partial,
-                           int max_blocks, cudaStream_t s) {
+                           int max_blocks, cudaStream_t s, long long split_pt) {
     int grid = (int)((N + 255) / 256);
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
     const size_t sm = ip_smem(p, q, sizeof(cplx<ACC>));
     static std::atomic<unsigned long long> attr{0};
     smem_limit_once(attr, k_ip_partial<TA, TB, ACC, true>, 200 * 1024);
-    k_ip_partial<TA, TB, ACC, true><<<grid, IP_THREADS, sm, s>>>(A, N, B, ldb, N, p, q, partial);
+    k_ip_partial<TA, TB, ACC, true><<<grid, IP_THREADS, sm, s>>>(A, N, B, ldb, N, p, q, partial, split_pt);
     note_launch();
     return grid;
 }
@@ -961,9 +974,9 @@ template int launch_ip_partial<float, double, float>(const c64*, int, const c128
 template int launch_ip_partial<float, double, double>(const c64*, int, const c128*, int, size_t, int, int, c128*,
                                                       int, cudaStream_t);
 template int launch_ip_partial_colA<float, float, float>(const c64*, const c64*, int, size_t, int, int, c128*, int,
-                                                        cudaStream_t);
+                                                        cudaStream_t, long long);
 template int launch_ip_partial_colA<double, double, double>(const c128*, const c128*, int, size_t, int, int, c128*,
-                                                            int, cudaStream_t);
+                                                            int, cudaStream_t, long long);
 template int launch_galerkin_partial<float, float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
 template int launch_galerkin_partial<float, double>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
 template int launch_galerkin_partial<double, double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t);

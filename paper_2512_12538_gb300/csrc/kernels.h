@@ -155,13 +155,15 @@ void set_wait_polls(long long polls);
 long long wait_polls(long long dflt);
 template <typename TC, typename TV, typename TW, typename TO>
 void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, int* err, cudaStream_t s);
-// W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns)
+// W[pt][c] += sum_j C[j][pt] y[j][c] (nc columns); split_pt as launch_ip_partial_colA
 template <typename TC, typename TW>
-void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s);
-// tiled inner products with a column-major A (p x N)
+void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s,
+                        long long split_pt = -1);
+// tiled inner products with a column-major A (p x N); split_pt >= 0: A's first p/2
+// columns vanish from point split_pt on and the others before it (a node's coarse basis)
 template <typename TA, typename TB, typename ACC>
 int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t N, int p, int q, c128* partial,
-                           int max_blocks, cudaStream_t s);
+                           int max_blocks, cudaStream_t s, long long split_pt = -1);
 
 // Krylov bases, point-major B[n * ld + j]:
 void launch_col_load(const c128* B, int ld, int col, c128* dst, size_t n, cudaStream_t s);
