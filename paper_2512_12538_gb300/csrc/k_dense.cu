@@ -19,17 +19,20 @@ static constexpr int GAL_FLUSH = 4;     // Galerkin tiles summed in FP32 before 
 // Rows i outside [ilo, ihi) contribute nothing for this tile (ihi = 0: no restriction).
 template <typename ACC, int KMAX = IP_MAXOUT>
 __device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cplx<ACC>* Bs, int rows, int p, int q,
-                                                   int split, cplx<ACC>* acc, int ilo, int ihi) {
+                                                   int split, cplx<ACC>* acc, int ilo, int ihi, int jlo = 0,
+                                                   int jhi = 0) {
     const int nout = p * q;
     if (split == 1) {
         // output o = threadIdx.x + k IP_THREADS; k is a compile-time index, so acc stays
-        // in registers
+        // in registers.  Columns j outside [jlo, jhi) contribute nothing for this tile
+        // (jhi = 0: no restriction); with q a multiple of 32 the skipped ones are whole warps
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int o = threadIdx.x + k * IP_THREADS;
             if (o >= nout) continue;
             const int i = o / q, j = o % q;
             if (ihi > 0 && (i < ilo || i >= ihi)) continue;
+            if (jhi > 0 && (j < jlo || j >= jhi)) continue;
             cplx<ACC> a = acc[k];
             for (int n = 0; n < rows; ++n) cfma_cj(a, As[n * p + i], Bs[n * q + j]);
             acc[k] = a;
@@ -39,6 +42,7 @@ __device__ __forceinline__ void ip_tile_accumulate(const cplx<ACC>* As, const cp
         if (s < split) {
             const int i = o / q, j = o % q;
             if (ihi > 0 && (i < ilo || i >= ihi)) return;
+            if (jhi > 0 && (j < jlo || j >= jhi)) return;
             cplx<ACC> a = acc[0];
             for (int n = s; n < rows; n += split) cfma_cj(a, As[n * p + i], Bs[n * q + j]);
             acc[0] = a;
@@ -329,9 +333,24 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<TI>*
     const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
         const int rows = (int)min((size_t)IP_TILE, n1 - t0);
+        // C's columns [0, p/2) live on rows < split_row, [p/2, p) on the others, and A~ C
+        // reaches one row further (the stencil).  A tile inside one row range needs one half
+        // of conj(C) (rows i of A_c: [ilo, ihi)) and, away from the rows next to the split,
+        // one half of A~ C (columns l: [jlo, jhi)); 0 as the upper end: every column.
+        int ilo = 0, ihi = 0, jlo = 0, jhi = 0;
+        if (split_row >= 0) {
+            const int j0 = (int)(t0 / g.Sx), j1 = (int)((t0 + rows - 1) / g.Sx);
+            if (j1 < split_row) { ilo = 0; ihi = p / 2; }
+            else if (j0 >= split_row) { ilo = p / 2; ihi = p; }
+            if (j1 < split_row - 1) { jlo = 0; jhi = p / 2; }
+            else if (j0 > split_row) { jlo = p / 2; jhi = p; }
+        }
         for (int e = threadIdx.x; e < rows * p; e += IP_THREADS) {
             const size_t pt = t0 + e / p;
             const int l = e % p;
+            const bool need_a = ihi == 0 || (l >= ilo && l < ihi);
+            const bool need_b = jhi == 0 || (l >= jlo && l < jhi);
+            if (!need_a && !need_b) continue;
             const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
             const size_t t = (size_t)l * N + pt;          // column-major basis
             const CT cv = cvt<T>(C[t]);
@@ -348,18 +367,11 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<TI>*
             Bs[e] = ax;
         }
         __syncthreads();
-        // C's columns [0, p/2) live on rows < split_row, [p/2, p) on the others; a tile
-        // inside one row touches one block of conj(C)
-        int ilo = 0, ihi = 0;
-        if (split_row >= 0) {
-            const int j0 = (int)(t0 / g.Sx), j1 = (int)((t0 + rows - 1) / g.Sx);
-            if (j1 < split_row) { ilo = 0; ihi = p / 2; }
-            else if (j0 >= split_row) { ilo = p / 2; ihi = p; }
-        }
         if (sizeof(T) == sizeof(double)) {
-            ip_tile_accumulate<double, KMAX>((const c128*)As, (const c128*)Bs, rows, p, p, split, acc, ilo, ihi);
+            ip_tile_accumulate<double, KMAX>((const c128*)As, (const c128*)Bs, rows, p, p, split, acc, ilo, ihi, jlo,
+                                             jhi);
         } else {
-            ip_tile_accumulate<T, KMAX>(As, Bs, rows, p, p, split, tacc, ilo, ihi);
+            ip_tile_accumulate<T, KMAX>(As, Bs, rows, p, p, split, tacc, ilo, ihi, jlo, jhi);
             if (++ntile == GAL_FLUSH || t0 + IP_TILE >= n1) {
 #pragma unroll
                 for (int k = 0; k < KMAX; ++k)
