@@ -318,6 +318,7 @@ def run_ours(args, rank, world):
         "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
                     for k, v in prof_all.items() if v[1] > 0},
         "kernels_from": f"untimed profiled pass of {PROFILED_PASS_STEPS} steps, every category timed",
+        "autotune": hh.hh_autotune_report(),
         "wall_s_timed": wall,
     }
     if batch is not None:

@@ -351,6 +351,16 @@ hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, lo
 /* Number of CUDA kernels this library has launched in the calling process. */
 unsigned long long hh_launch_count(void);
 
+/* Decisions of the library's autotuner in this process, as a JSON array: for each shape
+ * met so far, the candidates' measured milliseconds per launch and the one chosen.  The
+ * candidates are the complex64 multi-vector sweep transforms on the tensor cores or the
+ * CUDA cores (per transform, band height, columns and right-hand sides) and the cluster
+ * size (16 or 8) of the one-launch single-vector sweep; each is timed on the first use of
+ * its shape, outside any stream capture, and kept until exit.  The text (NUL-terminated,
+ * cut at cap - 1 bytes) goes to buf when buf is not NULL; *len (may be NULL) gets its
+ * full length.  An engineering aid: the paper has no counterpart. */
+hh_status hh_autotune_report(char* buf, size_t cap, size_t* len);
+
 /* --------------------------------------------------------------------------------
  * Failure detection (testing aid; the paper has no counterpart).  Every device-side
  * wait of the library is bounded: a wait that runs out records HH_ETIMEOUT, its kernel

@@ -22,7 +22,7 @@ _BINDING = {
     "HH_LEAF_EIGEN", "HH_LEAF_BLOCK", "HH_OUTER_ORAS", "HH_OUTER_GMRES",
     "hh_residual_noalloc", "HH_ETOOLARGE", "HH_NOALLOC_MAX_ROWS", "hh_setup_batch", "hh_solve_batch", "hh_server_create", "hh_server_submit",
     "hh_server_poll", "hh_server_destroy", "HH_EPENDING", "HH_FLAG_COARSE_FP32", "HH_FLAG_CUDA_CORE_SWEEPS",
-    "hh_debug_set_wait_limit",
+    "hh_debug_set_wait_limit", "hh_autotune_report",
 }
 
 

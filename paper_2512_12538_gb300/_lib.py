@@ -79,6 +79,7 @@ def _load():
         "hh_launch_count": (ctypes.c_ulonglong, []),
         "hh_residual_noalloc": (i, [i, i, d, vp, vp, vp, vp, P(d)]),
         "hh_debug_set_wait_limit": (i, [ctypes.c_longlong]),
+        "hh_autotune_report": (i, [vp, sz, P(sz)]),
         "hh_setup_batch": (i, [P(hh_params), i, vp, P(vp)]),
         "hh_server_create": (i, [sz, i, P(vp)]),
         "hh_server_submit": (i, [vp, P(hh_params), vp, vp, vp, P(ctypes.c_ulonglong)]),
@@ -351,3 +352,13 @@ def hh_launch_count() -> int:
 def hh_debug_set_wait_limit(polls: int) -> None:
     """Cap the polls of the library's give-up waits (0: give up at once; < 0: defaults)."""
     _check(LIB.hh_debug_set_wait_limit(int(polls)), "hh_debug_set_wait_limit")
+
+
+def hh_autotune_report() -> list:
+    """The autotuner's decisions so far (list of dicts)."""
+    import json
+    n = ctypes.c_size_t()
+    _check(LIB.hh_autotune_report(None, 0, ctypes.byref(n)), "hh_autotune_report")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(LIB.hh_autotune_report(buf, n.value + 1, ctypes.byref(n)), "hh_autotune_report")
+    return json.loads(buf.value.decode())

@@ -22,12 +22,15 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/hh.h"
@@ -146,6 +149,64 @@ static void dev_free(void* p, size_t bytes, cudaStream_t s, const AllocHook& a) 
         return;
     }
     cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------------- autotuner
+// Schedules of the leaf sweep are chosen by timing the candidates on the first use of
+// each shape, on the device and with the data of that use, and kept for the process:
+//   kind 0: the complex64 multi-vector transforms (f^ = V^T f, x = V x^) on the tensor
+//           cores (choice 1) or the CUDA cores (choice 0), per (transform, b_max, Sx, nrhs);
+//   kind 1: the cluster size of the one-launch single-vector sweep (16 or 8 CTAs per
+//           leaf), per (b_max, Sx), where both fit.
+// Candidates compute the same quantities (up to rounding), so the choice changes speed,
+// not the method.  Timing never runs inside a stream capture.
+struct TuneKey {
+    int dev, kind, a, b, c, d;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, kind, a, b, c, d) < std::tie(o.dev, o.kind, o.a, o.b, o.c, o.d);
+    }
+};
+struct TuneEntry {
+    int choice;
+    float ms[2];   // per launch: candidate 0, candidate 1
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneEntry> g_tune;
+static bool tune_find(const TuneKey& k, int& choice) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    choice = it->second.choice;
+    return true;
+}
+static void tune_store(const TuneKey& k, const TuneEntry& e) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.emplace(k, e);
+}
+static bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+// Times two candidates on `s` (each `reps` times after one warm-up run), returns the
+// faster (0 or 1) and their milliseconds per launch.  run(c) enqueues candidate c.
+template <typename F> static int tune_pair(cudaStream_t s, F&& run, float ms[2], int reps = 3) {
+    cudaEvent_t ev[3];
+    for (auto& e : ev) cudaEventCreate(&e);
+    run(0);
+    run(1);
+    cudaEventRecord(ev[0], s);
+    for (int i = 0; i < reps; ++i) run(0);
+    cudaEventRecord(ev[1], s);
+    for (int i = 0; i < reps; ++i) run(1);
+    cudaEventRecord(ev[2], s);
+    cudaEventSynchronize(ev[2]);
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    for (auto& e : ev) cudaEventDestroy(e);
+    ms[0] = a / reps;
+    ms[1] = b / reps;
+    return ms[1] < ms[0] ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------- hierarchy
@@ -642,11 +703,49 @@ struct Solver final : SolverBase {
         k.vn_emb = EVN[id];
         return k;
     }
+    // Cluster size of the one-launch single-vector sweep, 16 or 8 CTAs per leaf, timed on
+    // this handle's preconditioner tasks at the end of its set-up (their outputs are scratch
+    // there) where both fit.
+    void tune_fused_cluster() {
+        if (!eig || !eig_fused || !pre_direct || stream_capturing(stream)) return;
+        const int nl = (int)lev[L].size();
+        const TuneKey key{current_device(), 1, b_max, Sx, nl, (int)sizeof(T)};
+        int choice = 0;
+        if (!tune_find(key, choice)) {
+            if (!eig_sweep_fused_feasible<T>(16, b_max, Sx) || !eig_sweep_fused_feasible<T>(8, b_max, Sx)) return;
+            TuneEntry e{};
+            e.choice = tune_pair(stream, [&](int c) {
+                launch_eig_sweep_fused<T>(c ? 8 : 16, d_etasks_pre, nl, b_max, Sx, stream);
+            }, e.ms);
+            tune_store(key, e);
+            choice = e.choice;
+        }
+        eig_fused = choice ? 8 : 16;
+    }
     // The three-stage sweep of several right-hand sides: transforms on the tensor cores
     // in the complex64 form, else on the CUDA cores; the line recursions in between.
     void eig_sweep_stage(int stg, const EigTask* tasks, int ntasks, int nc) {
-        if (tc && stg != 1) launch_tc_transform(stg == 0 ? 0 : 1, tasks, ntasks, b_max, Sx, nc, derr, stream);
-        else launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream);
+        if (!tc || stg == 1) {
+            launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream);
+            return;
+        }
+        // transforms: tensor cores or CUDA cores, as the autotuner found faster for this shape
+        auto run = [&](int c) {
+            if (c) launch_tc_transform(stg == 0 ? 0 : 1, tasks, ntasks, b_max, Sx, nc, derr, stream);
+            else launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream);
+        };
+        const TuneKey key{current_device(), 0, stg, b_max, Sx, nc * 64 + std::min(ntasks, 63)};
+        int choice = 1;
+        if (!tune_find(key, choice)) {
+            if (stream_capturing(stream)) choice = 1;
+            else {
+                TuneEntry e{};
+                e.choice = tune_pair(stream, run, e.ms);
+                tune_store(key, e);
+                choice = e.choice;
+            }
+        }
+        run(choice);   // the outputs are those of the chosen candidate
     }
     void upload_eig_view_tasks(int nc) {
         std::vector<EigTask> t;
@@ -927,9 +1026,11 @@ struct Solver final : SolverBase {
             launch_copy<T, T>(W[c] + row_off(c, nodes[c].ifrow, m), Z[c], (size_t)Sx * m, false, true, stream);
         // SVD of Z^H = Q^H T: Gram Z^H Z (FP64), its Hermitian eigenproblem, V = Z U Sigma^{-1}
         for (int c : cs) {
-            // Gram matrix in the sketch precision (FP32 products for the complex64 sketch:
-            // their rounding matches that of the sketch itself), partial sums in FP64
-            const int nb = launch_ip_partial<T, T, T>(Z[c], m, Z[c], m, Sx, m, m, partial, MAX_PART_BLOCKS, stream);
+            // Gram matrix Z^H Z of the stored sketch in FP64 (the complex64 sketch widens
+            // exactly), so that forming it squares no FP32 rounding into the small singular
+            // values; the SVD that follows is FP64 as well
+            const int nb = launch_ip_partial<T, T, double>(Z[c], m, Z[c], m, Sx, m, m, partial, MAX_PART_BLOCKS,
+                                                           stream);
             launch_ip_reduce(partial, nb, m, m, Gm[c], nullptr, nullptr, stream);
         }
         std::vector<c128*> gs, us;
@@ -1019,6 +1120,7 @@ struct Solver final : SolverBase {
         pend(PC_FACTOR);
         for (int l = L; l >= 1; --l) sketch_level(l);
         upload_pre_tasks();
+        tune_fused_cluster();
         if (device_test_path() && recur_possible()) launch_apply_cols<T>(C[0], AC0, geom(0), 2 * r, stream);
         cudaEventRecord(e1, stream);
         hh_status st;
@@ -2630,6 +2732,42 @@ hh_status hh_profile_read(const hh_handle* h, int category, double* total_ms, lo
     return HH_OK;
 }
 unsigned long long hh_launch_count(void) { return hh::g_launches.load(); }
+
+hh_status hh_autotune_report(char* buf, size_t cap, size_t* len) {
+    std::string out = "[";
+    {
+        std::lock_guard<std::mutex> lk(hh::g_tune_mu);
+        bool first = true;
+        for (const auto& kv : hh::g_tune) {
+            const hh::TuneKey& k = kv.first;
+            const hh::TuneEntry& e = kv.second;
+            char line[320];
+            if (k.kind == 0)
+                std::snprintf(line, sizeof line,
+                              "{\"device\":%d,\"what\":\"%s\",\"b_max\":%d,\"Sx\":%d,\"nrhs\":%d,\"leaves\":%d,"
+                              "\"cuda_cores_ms\":%.4f,\"tensor_cores_ms\":%.4f,\"chosen\":\"%s\"}",
+                              k.dev, k.a == 0 ? "transform_in" : "transform_out", k.b, k.c, k.d / 64, k.d % 64,
+                              e.ms[0], e.ms[1], e.choice ? "tensor_cores" : "cuda_cores");
+            else
+                std::snprintf(line, sizeof line,
+                              "{\"device\":%d,\"what\":\"fused_sweep_cluster\",\"b_max\":%d,\"Sx\":%d,"
+                              "\"leaves\":%d,\"precision\":\"%s\",\"cluster16_ms\":%.4f,\"cluster8_ms\":%.4f,"
+                              "\"chosen\":%d}",
+                              k.dev, k.a, k.b, k.c, k.d == 4 ? "mixed" : "fp64", e.ms[0], e.ms[1], e.choice ? 8 : 16);
+            if (!first) out += ",";
+            out += line;
+            first = false;
+        }
+    }
+    out += "]";
+    if (len) *len = out.size();
+    if (buf && cap > 0) {
+        const size_t n = std::min(cap - 1, out.size());
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return HH_OK;
+}
 
 hh_status hh_debug_set_wait_limit(long long polls) {
     hh::set_wait_polls(polls < 0 ? -1 : polls);

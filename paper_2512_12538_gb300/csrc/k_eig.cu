@@ -861,6 +861,21 @@ int eig_sweep_fused_ready_query(int b_max, int Sx) {
     return 0;
 }
 
+// Whether clusters of `cl` CTAs can run the one-launch sweep for these sizes (the
+// attributes of eig_sweep_fused_ready must have been set on the device).
+template <typename T>
+bool eig_sweep_fused_feasible(int cl, int b_max, int Sx) {
+    if (Sx < cl || eig_sweep_fused_ready<T>(b_max, Sx) == 0) return false;
+    const size_t sm = sizeof(cplx<T>) * fs_geom(b_max, Sx, cl).elems;
+    if (sm > (size_t)FS_SMEM_MAX) return false;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = fs_config<T>(cl, 1, sm, nullptr, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_eig_sweep_fused<T>, &cfg) == cudaSuccess && n > 0) return true;
+    cudaGetLastError();
+    return false;
+}
+
 template <typename T>
 void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s,
                             const int* gate) {
@@ -883,5 +898,7 @@ template void launch_eig_sweep_fused<float>(int, const EigTask*, int, int, int, 
 template void launch_eig_sweep_fused<double>(int, const EigTask*, int, int, int, cudaStream_t, const int*);
 template int eig_sweep_fused_ready<float>(int, int);
 template int eig_sweep_fused_ready<double>(int, int);
+template bool eig_sweep_fused_feasible<float>(int, int, int);
+template bool eig_sweep_fused_feasible<double>(int, int, int);
 
 }  // namespace hh

@@ -273,6 +273,9 @@ void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int
 constexpr int FS_SMEM_MAX = 220 * 1024;
 template <typename T>
 int eig_sweep_fused_ready(int b_max, int Sx);
+// whether clusters of `cl` CTAs can run the one-launch sweep for these sizes
+template <typename T>
+bool eig_sweep_fused_feasible(int cl, int b_max, int Sx);
 // b_max, Sx: the largest band and column count among the tasks (shared-memory size).
 // gate (may be null): a device word; when it is nonzero at launch the launch does nothing.
 template <typename T>
