@@ -161,9 +161,10 @@ CATEGORY_BOUND = {
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum): 152 SMs x 2 x 2 flops x max SM clock.
 DFMA_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel from one ncu capture of this workload; None until a capture of the current
-# kernel on this workload is summarised under profiles/.
-TRAFFIC_BYTES_PER_LAUNCH = {}
+# kernel on this workload's shapes (mean of its three launches per step), from the ncu
+# capture summarised in profiles/coarse_batch_helm2d_n1023_k100_L3.md.  To be removed
+# whenever k_coarse_batch changes.
+TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 586.4e6}
 
 
 def whole_job_rate(local_ms, units_per_rank, world, device="cuda"):
