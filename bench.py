@@ -476,6 +476,30 @@ def run_serving_line(args):
     return out
 
 
+def run_case(args):
+    """--form case: one set-up and a few stationary steps of the workload's grid and
+    hierarchy at rank --case-rank (oversampling 4), with no timing: the small case the
+    profiler captures of single kernels run on (profiles/)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_12538_gb300 as hh
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w, f, g = workload_inputs()
+    fd = torch.from_numpy(f).cuda()
+    gd = torch.from_numpy(g).cuda()
+    u = torch.empty_like(fd)
+    p = hh.make_params(2, w.n, w.k, w.levels, w.overlap, args.case_rank, 4, 1, 1e-3, args.case_steps, "mixed", 1,
+                       "eigen", "oras", RESTART)
+    h, fp = hh.hh_setup(p)
+    st = hh.hh_solve(h, fd, gd, u, allow_noconv=True)
+    torch.cuda.synchronize()
+    hh.hh_destroy(h)
+    return {"case": WORKLOAD, "rank": args.case_rank, "footprint_bytes": fp, "iters": st.iters,
+            "rel_res": st.rel_res}
+
+
 def pct(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -653,8 +677,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="single", choices=["single", "serve"],
-                    help="serve: the serving-form stream instead of the headline workload")
+    ap.add_argument("--form", default="single", choices=["single", "serve", "case"],
+                    help="serve: the serving-form stream instead of the headline workload; case: the small "
+                         "case profiler captures run on (--case-rank, --case-steps)")
+    ap.add_argument("--case-rank", type=int, default=16)
+    ap.add_argument("--case-steps", type=int, default=12)
     ap.add_argument("--batch-form", default="on", choices=["on", "off"],
                     help="also measure the batching form (512 problems) after the headline")
     ap.add_argument("--serving-form", default="on", choices=["on", "off"],
@@ -667,6 +694,9 @@ def main():
     args = ap.parse_args()
     if args.form == "serve":
         print(json.dumps(run_serving_line(args)), flush=True)
+        return
+    if args.form == "case":
+        print(json.dumps(run_case(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
