@@ -94,10 +94,27 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
     if (stop.need && !*stop.need) return;
     const bool wt = !stop.anchor || *stop.anchor;
     const size_t total = (size_t)g.b * g.Sx;
+    // interior points of a 2D band with one k: the row is (4 - (kh)^2) x minus the four
+    // neighbours, the same FP64 operations in the same order as the general row below,
+    // without forming its weights and impedance terms (the FP64 pipe bounds this kernel)
+    const double d_in = 4.0 - g.kh * g.kh;
     double acc2 = 0.0;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t % g.Sx);
         const int j = (int)(t / g.Sx);
+        if (g.Sx > 1 && !g.khr && i > 0 && i < g.Sx - 1 && j > 0 && j < g.b - 1) {
+            const c128 xc = x[t];
+            c128 ax = {d_in * xc.re, d_in * xc.im};
+            ax = ax - x[t - 1];
+            ax = ax - x[t + 1];
+            ax = ax - x[t - g.Sx];
+            ax = ax - x[t + g.Sx];
+            const c128 out = v[t] - ax;
+            y[t] = out;
+            if (wt) yt[t] = cvt<T>(out);
+            acc2 += abs2(out);
+            continue;
+        }
         c128 ax = op_diag(j, i, g) * x[t];
         const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
         if (g.Sx > 1) {
