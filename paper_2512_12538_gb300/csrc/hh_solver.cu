@@ -1830,6 +1830,15 @@ struct BatchEngine {
     unsigned long long next_serial = 1;
     int cl = 0, bmax = 0, sxmax = 0;
     cudaError_t cerr = cudaSuccess;
+    // One lockstep iteration after the first (the preconditioner step of every current
+    // problem, then their residuals for the next test) is a CUDA graph, captured on a
+    // private stream for the current set of problems and replayed while the set stays.
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned long long> graph_key;
+    bool resid_pending = false;   // the current problems' residuals are already enqueued
+    unsigned long long replays = 0, captures = 0;
 
     hh_status init(cudaStream_t s, int probs, int tasks, const AllocHook& h) {
         stream = s;
@@ -1852,7 +1861,17 @@ struct BatchEngine {
         ck(cudaMemsetAsync(bar, 0, 256, stream), cerr);
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        graph_key.clear();
+    }
     void release() {
+        drop_graph();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
         if (h_norms) cudaFreeHost(h_norms);
         h_norms = nullptr;
         if (base) dev_free(base, bytes, stream, hook);
@@ -1892,11 +1911,12 @@ struct BatchEngine {
         q.serial = next_serial++;
         q.it = -1;   // the first step reads ||b||^2
         act.push_back(q);
+        resid_pending = false;   // the next step enqueues every current problem's residual
     }
     // One iteration for every current problem; problems that leave are appended to `done`
     // (their solution already copied to uo, the copy complete).
-    hh_status step(std::vector<Prob>& done) {
-        if (act.empty()) return HH_OK;
+    // Residuals of every current problem (norms[k] for act[k]), enqueued on `stream`.
+    void enqueue_residuals() {
         const int na = (int)act.size();
         for (int c0 = 0; c0 < na; c0 += RB_MAX_JOBS) {
             ResidBatch rb{};
@@ -1911,6 +1931,12 @@ struct BatchEngine {
             }
             launch_residual_batch<T>(rb, part, part_cap, norms + c0, stream);
         }
+    }
+    hh_status step(std::vector<Prob>& done) {
+        if (act.empty()) return HH_OK;
+        const int na = (int)act.size();
+        if (!resid_pending) enqueue_residuals();
+        resid_pending = false;
         ck(cudaMemcpyAsync(h_norms, norms, sizeof(double) * na, cudaMemcpyDeviceToHost, stream), cerr);
         ck(cudaMemcpyAsync(h_norms + cap_probs, berr, sizeof(int), cudaMemcpyDeviceToHost, stream), cerr);
         ck(cudaStreamSynchronize(stream), cerr);
@@ -1977,6 +2003,41 @@ struct BatchEngine {
             ck(cudaStreamSynchronize(stream), cerr);
             uploaded = key;
         }
+        if (key != graph_key) {
+            // capture the iteration for this set of problems: the preconditioner step and
+            // the residuals of the next test (launches only: no host synchronisation inside)
+            drop_graph();
+            if (!cap_stream) ck(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking), cerr);
+            cudaStream_t user = stream;
+            bool ok = cerr == cudaSuccess &&
+                      cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                stream = cap_stream;
+                enqueue_precond(ids);
+                enqueue_residuals();
+                stream = user;
+                ok = cudaStreamEndCapture(cap_stream, &graph) == cudaSuccess && graph &&
+                     cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+            }
+            stream = user;
+            if (!ok) {
+                cudaGetLastError();
+                drop_graph();
+                return HH_ECUDA;
+            }
+            graph_key = key;
+            ++captures;
+        }
+        ck(cudaGraphLaunch(gexec, stream), cerr);
+        ++replays;
+        resid_pending = true;
+        for (auto& q : act) ++q.it;
+        ck(cudaGetLastError(), cerr);
+        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+    }
+
+    // One preconditioner step for the problems `ids` (the current set, in order).
+    void enqueue_precond(const std::vector<Solver<T>*>& ids) {
         int nt = 0, lmax = 0;
         for (auto* p : ids) {
             nt += (int)p->h_pre.size();
@@ -2045,9 +2106,6 @@ struct BatchEngine {
             }
             if (bt.njobs) launch_coarse_batch<T, double, double, double>(bt, w, cpart, bar, berr, stream);
         }
-        for (auto& q : act) ++q.it;
-        ck(cudaGetLastError(), cerr);
-        return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
 };
 
