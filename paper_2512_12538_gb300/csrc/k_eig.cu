@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_eig_modes(const EigTask* __re
 // --------------------------------------------------------------- contractions
 // C[r][j] = sum_k op(V)[r][k] B[k][j] for r, k < b and j < J = Sx * nrhs; op = V^T (in)
 // or V (out).  Column j of the node layout is (i, c) = (j / nrhs, j % nrhs); the
-// transformed vectors are stored line by line, [m][c][i], so that each scalar recursion
-// reads one contiguous line.  One CTA per GT_N columns; V and B staged through shared
+// transformed vectors are stored as fh_col says (line by line, [m][c][i], for a few
+// right-hand sides, so that each scalar recursion reads one contiguous line).  One CTA per GT_N columns; V and B staged through shared
 // memory in k-chunks.
 static constexpr int GT_N = 8, GT_K = 32, GT_THREADS = 256, GT_ROWS = 32, GT_RPT = 5;
 
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
                     if (j0 + j < J) {
                         const int jj2 = j0 + j;
                         // which == 1 reads the line-major transformed vectors
-                        const size_t col = which == 0 ? (size_t)jj2 : (size_t)(jj2 % nrhs) * Sx + jj2 / nrhs;
+                        const size_t col = which == 0 ? (size_t)jj2 : fh_col((size_t)jj2, Sx, nrhs);
                         tmp[u] = B[(size_t)(k0 + k) * J + col];
                     }
                 }
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
     }
     if (j0 + jj < J) {
         const int jj2 = j0 + jj;
-        const size_t col = which == 0 ? (size_t)(jj2 % nrhs) * Sx + jj2 / nrhs : (size_t)jj2;
+        const size_t col = which == 0 ? fh_col((size_t)jj2, Sx, nrhs) : (size_t)jj2;
 #pragma unroll
         for (int t = 0; t < GT_RPT; ++t) {
             const int r = rg + t * GT_ROWS;
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256) k_eig_gemm2(const EigTask* __restrict__ t
             } else if (e < nv + nb2) {
                 const int e2 = e - nv, k = e2 / GN, c = e2 - k * GN, jj = j0 + c;
                 if (jj < J) {
-                    const size_t col = which == 0 ? (size_t)jj : (size_t)(jj % nrhs) * Sx + jj / nrhs;
+                    const size_t col = which == 0 ? (size_t)jj : fh_col((size_t)jj, Sx, nrhs);
                     tmp[u] = B[(size_t)k * J + col];
                 }
             }
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256) k_eig_gemm2(const EigTask* __restrict__ t
     for (int v = 0; v < CV; ++v) {
         const int jj = j0 + cg + 16 * v;
         if (jj >= J) continue;
-        const size_t col = which == 0 ? (size_t)(jj % nrhs) * Sx + jj / nrhs : (size_t)jj;
+        const size_t col = which == 0 ? fh_col((size_t)jj, Sx, nrhs) : (size_t)jj;
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
             const int r = rg + 16 * u;
@@ -553,6 +553,62 @@ __global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ t
     for (int i = lane; i < Sx; i += 32) fh[i] = fs[i];
 }
 
+// Scalar recursions of many right-hand sides (16 or more), in place on Fh[m][i][c]: one
+// warp per (mode m, 32 consecutive right-hand sides), each lane running its line's forward
+// and backward recursions along i (the same y_i = xi_i (y_{i-1} + f_i) and
+// x_i = y_i + xi_i x_{i+1} as warp_line_solve).  The lanes' Fh accesses are contiguous and
+// xi[m][i] is one broadcast load per warp and step.  Each lane loads RB steps of its line
+// and of xi at once before running them, so a chain step waits on no load.
+template <typename T>
+__global__ void __launch_bounds__(256) k_eig_recur_cols(const EigTask* __restrict__ tasks, int Sx, int nrhs) {
+    using C = cplx<T>;
+    constexpr int RB = 16;
+    const EigTask tk = tasks[blockIdx.y];
+    const int cgs = (nrhs + 31) / 32;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wg >= tk.b * cgs) return;
+    const int m = wg / cgs, c = (wg - m * cgs) * 32 + (threadIdx.x & 31);
+    if (c >= nrhs) return;
+    const C* xi = (const C*)tk.xi + (size_t)m * Sx;
+    C* fh = (C*)tk.Fh + (size_t)m * Sx * nrhs + c;
+    C y = {0, 0};
+    for (int i0 = 0; i0 < Sx; i0 += RB) {
+        C a[RB], f[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int i = min(i0 + u, Sx - 1);
+            a[u] = xi[i];
+            f[u] = fh[(size_t)i * nrhs];
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            if (i0 + u < Sx) {
+                y = a[u] * (f[u] + y);
+                fh[(size_t)(i0 + u) * nrhs] = y;
+            }
+        }
+    }
+    // backward from x_{Sx-1} = y_{Sx-1}, in blocks of RB ending at i1 (exclusive)
+    C x = y;
+    for (int i1 = Sx - 1; i1 > 0; i1 -= RB) {
+        C a[RB], yv[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int i = max(i1 - 1 - u, 0);
+            a[u] = xi[i];
+            yv[u] = fh[(size_t)i * nrhs];
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int i = i1 - 1 - u;
+            if (i >= 0) {
+                x = yv[u] + a[u] * x;
+                fh[(size_t)i * nrhs] = x;
+            }
+        }
+    }
+}
+
 template <typename T>
 void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err, cudaStream_t s) {
     if (b_max > EIG_BMAX) {
@@ -607,6 +663,10 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
         k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0, Sx, nrhs, kchunk);
     } else if (stage == 2) {
         k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1, Sx, nrhs, kchunk);
+    } else if (!eig_line_major(nrhs)) {
+        const int warps = b_max * ((nrhs + 31) / 32);
+        dim3 g3((warps + 7) / 8, ntasks);
+        k_eig_recur_cols<T><<<g3, 256, 0, s>>>(d_tasks, Sx, nrhs);
     } else {
         const size_t per_warp = 2 * sizeof(cplx<T>) * (size_t)Sx;
         const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp));

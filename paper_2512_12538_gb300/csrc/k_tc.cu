@@ -181,9 +181,9 @@ void launch_tc_prepare_v(const EigTask* d_tasks, int ntasks, int b_max, cudaStre
     note_launch();
 }
 
-// which = 0: Fh = V^T F (input F natural [b][J], output Fh permuted: column (c, x) at
-// c Sx + x); which = 1: W = V Fh (input Fh permuted, output W natural).  The tiles run
-// along the input's contiguous column index p.
+// which = 0: Fh = V^T F (input F in node order [b][J], output Fh as fh_col says);
+// which = 1: W = V Fh (input Fh, output W in node order).  The tiles run along the
+// input's contiguous column index p.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* __restrict__ tasks, int ntasks,
                                                                 int which, int Sx, int nrhs, int b_max,
                                                                 int tiles_per_task, uint32_t limit, int* err) {
@@ -337,7 +337,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         const bool even = (lane & 1) == 0;
         const int p = p0 + jl;
         size_t col = 0;
-        if (p < J) col = which == 0 ? (size_t)(p % nrhs) * Sx + p / nrhs : (size_t)(p % Sx) * nrhs + p / Sx;
+        // which = 0 writes Fh (fh_col of node column p); which = 1 reads Fh along p and
+        // writes the node column p (node order) or (p % Sx) nrhs + p / Sx (line-major Fh)
+        if (p < J)
+            col = which == 0 ? fh_col((size_t)p, Sx, nrhs)
+                             : (eig_line_major(nrhs) ? (size_t)(p % Sx) * nrhs + p / Sx : (size_t)p);
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         for (int m0 = 0; m0 < g.nb; m0 += 16) {
             float d0[16], d1[16];

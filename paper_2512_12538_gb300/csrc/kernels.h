@@ -248,6 +248,15 @@ struct EigTask {
     const void* vn_emb;   // (tc_prepare_v layout; null where the transforms run on CUDA cores)
 };
 
+// Layout of the transformed vectors Fh of a multi-vector sweep (b rows of J = Sx nrhs):
+// up to 15 right-hand sides line by line, [m][c][i] (each scalar recursion reads one
+// contiguous line; one warp per line); from 16 on in the node order [m][i][c] (one lane
+// per right-hand side, a warp's loads contiguous).  fh_col: the Fh column of node column jj.
+HH_HD bool eig_line_major(int nrhs) { return nrhs <= 15; }
+HH_HD size_t fh_col(size_t jj, int Sx, int nrhs) {
+    return eig_line_major(nrhs) ? (jj % (size_t)nrhs) * (size_t)Sx + jj / (size_t)nrhs : jj;
+}
+
 // ---- tensor-core transforms (k_tc.cu) -----------------------------------------------
 // Bytes of one B operand (one leaf, one transform) for bands of up to b_max rows.
 size_t tc_vemb_bytes(int b_max);
