@@ -183,10 +183,8 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
     CA acc[CB_COLS];
 #pragma unroll
     for (int u = 0; u < CB_COLS; ++u) acc[u] = {0, 0};
-    for (unsigned pt = P0 + ls * 256u + threadIdx.x; pt < P1; pt += ns * 256u) {
-        cplx<TC> cv[CB_COLS];
-#pragma unroll
-        for (int u = 0; u < CB_COLS; ++u) cv[u] = u < nc ? C[(size_t)(c0 + u) * N + pt] : CA{0, 0};
+    // r = v - A~ w_in at one point (w_in null: r = v), in the basis precision
+    auto resid_at = [&](unsigned pt) -> CA {
         cplx<R> rv = cvt<R>(v[pt]);
         if (w_in) {
             const int jr = (int)(pt / (unsigned)g.Sx), i = (int)(pt - (unsigned)jr * g.Sx);
@@ -203,6 +201,31 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
         }
         const CA ra = cvt<TC>(rv);
         if (bt.rr.AC && gi == 0) ((CA*)bt.rr.rp)[pt] = ra;   // r' for the next residual
+        return ra;
+    };
+    // two points per iteration: their basis and vector loads are in flight together
+    const unsigned stride = ns * 256u;
+    unsigned pt = P0 + ls * 256u + threadIdx.x;
+    for (; pt + stride < P1; pt += 2u * stride) {
+        const unsigned pb = pt + stride;
+        cplx<TC> ca[CB_COLS], cb[CB_COLS];
+#pragma unroll
+        for (int u = 0; u < CB_COLS; ++u) {
+            ca[u] = u < nc ? C[(size_t)(c0 + u) * N + pt] : CA{0, 0};
+            cb[u] = u < nc ? C[(size_t)(c0 + u) * N + pb] : CA{0, 0};
+        }
+        const CA ra = resid_at(pt), rb = resid_at(pb);
+#pragma unroll
+        for (int u = 0; u < CB_COLS; ++u) {
+            cfma_cj(acc[u], ca[u], ra);
+            cfma_cj(acc[u], cb[u], rb);
+        }
+    }
+    if (pt < P1) {
+        cplx<TC> cv[CB_COLS];
+#pragma unroll
+        for (int u = 0; u < CB_COLS; ++u) cv[u] = u < nc ? C[(size_t)(c0 + u) * N + pt] : CA{0, 0};
+        const CA ra = resid_at(pt);
 #pragma unroll
         for (int u = 0; u < CB_COLS; ++u) cfma_cj(acc[u], cv[u], ra);
     }
@@ -286,7 +309,15 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
             if ((int)(pt / (unsigned)g.Sx) < J.split) je = p >> 1;
             else j = p >> 1;
         }
-        // sixteen basis loads in flight per thread (the columns are far apart in memory)
+        // sixteen or more basis loads in flight per thread (the columns are far apart in
+        // memory)
+        for (; j + 32 <= je; j += 32) {
+            cplx<TC> cv[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) cv[u] = C[(size_t)(j + u) * N + pt];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) cfma(a, cv[u], s_y[j + u]);
+        }
         for (; j + 16 <= je; j += 16) {
             cplx<TC> cv[16];
 #pragma unroll
