@@ -490,8 +490,10 @@ def run_case(args):
     fd = torch.from_numpy(f).cuda()
     gd = torch.from_numpy(g).cuda()
     u = torch.empty_like(fd)
+    # the sweep transforms on the tensor cores without timing alternatives: under a
+    # profiler every launch is serialised, so the autotuner's timings would mean nothing
     p = hh.make_params(2, w.n, w.k, w.levels, w.overlap, args.case_rank, 4, 1, 1e-3, args.case_steps, "mixed", 1,
-                       "eigen", "oras", RESTART)
+                       "eigen", "oras", RESTART, flags=hh.HH_FLAG_TENSOR_CORE_SWEEPS)
     h, fp = hh.hh_setup(p)
     st = hh.hh_solve(h, fd, gd, u, allow_noconv=True)
     torch.cuda.synchronize()

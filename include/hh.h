@@ -103,6 +103,10 @@ typedef struct {
  * tensor cores (TF32 with a three-term split, FP32 accumulation).  Ignored by the FP64
  * form, which always uses the CUDA cores. */
 #define HH_FLAG_CUDA_CORE_SWEEPS 2u
+/* hh_params.flags: the mixed form runs those transforms on the tensor cores wherever it
+ * can, without timing the alternatives (the choice the autotuner otherwise makes per
+ * shape).  Not together with HH_FLAG_CUDA_CORE_SWEEPS. */
+#define HH_FLAG_TENSOR_CORE_SWEEPS 4u
 
 typedef enum {
     HH_LEAF_EIGEN = 0,    /* 2D leaves: the block Schur recursion evaluated in the eigenbasis */

@@ -263,7 +263,8 @@ static hh_status validate(const hh_params* P) {
     if (P->leaf_solver != HH_LEAF_EIGEN && P->leaf_solver != HH_LEAF_BLOCK) return HH_EINVAL;
     if (P->outer != HH_OUTER_ORAS && P->outer != HH_OUTER_GMRES) return HH_EINVAL;
     if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
-    if (P->flags & ~(HH_FLAG_COARSE_FP32 | HH_FLAG_CUDA_CORE_SWEEPS)) return HH_EINVAL;
+    if (P->flags & ~(HH_FLAG_COARSE_FP32 | HH_FLAG_CUDA_CORE_SWEEPS | HH_FLAG_TENSOR_CORE_SWEEPS)) return HH_EINVAL;
+    if ((P->flags & HH_FLAG_CUDA_CORE_SWEEPS) && (P->flags & HH_FLAG_TENSOR_CORE_SWEEPS)) return HH_EINVAL;
     if (P->k_rows) {
         // layered media: the wavenumber varies across the rows of a band, which the
         // column-pencil eigenbasis of the 2D leaves does not take (explicit inverses do)
@@ -736,7 +737,8 @@ struct Solver final : SolverBase {
         };
         const TuneKey key{current_device(), 0, stg, b_max, Sx, nc * 64 + std::min(ntasks, 63)};
         int choice = 1;
-        if (!tune_find(key, choice)) {
+        if (P.flags & HH_FLAG_TENSOR_CORE_SWEEPS) choice = 1;
+        else if (!tune_find(key, choice)) {
             if (stream_capturing(stream)) choice = 1;
             else {
                 TuneEntry e{};

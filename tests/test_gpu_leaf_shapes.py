@@ -55,9 +55,11 @@ def _oracle(name):
     return _oracles[name]
 
 
-# mixed form, eigenbasis path: the multi-vector transforms on the tensor cores (default)
-# or on the CUDA cores (HH_FLAG_CUDA_CORE_SWEEPS)
-CASES = [(ls, pr, 0) for ls in ("eigen", "block") for pr in ("fp64", "mixed")] + [("eigen", "mixed", 2)]
+# mixed form, eigenbasis path: the multi-vector transforms as the autotuner picks them
+# (flags 0), forced onto the CUDA cores (HH_FLAG_CUDA_CORE_SWEEPS) and forced onto the
+# tensor cores (HH_FLAG_TENSOR_CORE_SWEEPS)
+CASES = [(ls, pr, 0) for ls in ("eigen", "block") for pr in ("fp64", "mixed")] + [("eigen", "mixed", 2),
+                                                                                  ("eigen", "mixed", 4)]
 
 
 @pytest.mark.parametrize("name", ["n255", "n1023"])

@@ -50,7 +50,7 @@ def test_footprint_host_only_and_validation(hh):
     bad = [dict(overlap=3), dict(overlap=0), dict(levels=0), dict(n=2), dict(rank=0), dict(k=-1.0),
            dict(n=20, levels=4), dict(rank=40, oversample=0), dict(dim=3), dict(n_inner=0), dict(tol=0.0),
            dict(leaf_solver=7), dict(outer=3), dict(outer=1, restart=0), dict(outer=1, restart=65),
-           dict(n=1023, levels=2), dict(levels=7, n=4000), dict(flags=4), dict(flags=0x80000000)]
+           dict(n=1023, levels=2), dict(levels=7, n=4000), dict(flags=8), dict(flags=6), dict(flags=0x80000000)]
     for kw in bad:
         args = dict(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
         args.update(kw)
