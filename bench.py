@@ -164,7 +164,7 @@ DFMA_PER_SM_CLK = 2
 # kernel on this workload's shapes (mean of its three launches per step), from the ncu
 # capture summarised in profiles/coarse_batch_helm2d_n1023_k100_L3.md.  To be removed
 # whenever k_coarse_batch changes.
-TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 586.4e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 584.8e6}
 
 
 def whole_job_rate(local_ms, units_per_rank, world, device="cuda"):
@@ -223,7 +223,8 @@ def run_ours(args, rank, world):
     # warm-up
     for _ in range(args.warmup):
         one("mixed")
-    one("fp64")
+    if args.fp64_form == "on":
+        one("fp64")
 
     # untimed profiled pass: every kernel category timed with CUDA events on `stream`
     # (the per-category table, and which category dominates)
@@ -267,12 +268,12 @@ def run_ours(args, rank, world):
     # FP64 GPU form of the same method on the same workload
     fp64_ms = []
     fp64_iters = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(max(3, args.steps // 2) if args.fp64_form == "on" else 0):
         ms, st, _ = one("fp64")
         fp64_ms.append(ms)
         fp64_iters.append(st.iters)
-    fp64_value = whole_job_rate(sum(fp64_ms), len(fp64_ms), world)[0]
-    u_fp64 = u.cpu().numpy()
+    fp64_value = whole_job_rate(sum(fp64_ms), len(fp64_ms), world)[0] if fp64_ms else None
+    u_fp64 = u.cpu().numpy() if fp64_ms else None
 
     # end to end through the C-ABI with host buffers (pinned): H2D f, g and D2H u inside
     fh = torch.from_numpy(f).pin_memory()
@@ -309,12 +310,15 @@ def run_ours(args, rank, world):
         "config": workload_config(w, "mixed", "inputs larger than L2 (16.8 MB vectors, 2.3 GB factors and bases); "
                                              "L2 also flushed between steps (256 MB write)", f"replicas x{world}"),
         "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99)},
-        "iterations": {"mixed": statistics.median(iters), "fp64": statistics.median(fp64_iters)},
+        "iterations": {"mixed": statistics.median(iters),
+                       "fp64": statistics.median(fp64_iters) if fp64_iters else None},
         "setup_ms": {"mixed": setup_split.t_setup_ms, "solve_mixed": setup_split.t_solve_ms},
         "fp64_form": {"value": fp64_value, "unit": UNIT, "dtype": "c128/f64",
-                      "ms_per_step": statistics.mean(fp64_ms), "median_ms_per_step": statistics.median(fp64_ms),
-                      "iterations": statistics.median(fp64_iters), "step_ms": [round(x, 3) for x in fp64_ms]},
-        "mixed_over_fp64": value / fp64_value,
+                      "ms_per_step": statistics.mean(fp64_ms) if fp64_ms else None,
+                      "median_ms_per_step": statistics.median(fp64_ms) if fp64_ms else None,
+                      "iterations": statistics.median(fp64_iters) if fp64_iters else None,
+                      "step_ms": [round(x, 3) for x in fp64_ms]},
+        "mixed_over_fp64": value / fp64_value if fp64_value else None,
         "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
         "kernels": {k: dict(rate(k, v[0], v[2], v[3], pk, pk_kind), ms_total=v[0], launches=v[1])
                     for k, v in prof_all.items() if v[1] > 0},
@@ -330,7 +334,8 @@ def run_ours(args, rank, world):
         base, refs = cpu_baseline_leg(w, batch_u)
         out["cpu_baseline"] = base
         # relative errors against the oracle's direct solution u* = A^{-1} b
-        out["rel_err"] = {"mixed": rel_err(u_mixed, refs["u_star"]), "fp64": rel_err(u_fp64, refs["u_star"]),
+        out["rel_err"] = {"mixed": rel_err(u_mixed, refs["u_star"]),
+                          "fp64": rel_err(u_fp64, refs["u_star"]) if u_fp64 is not None else None,
                           "against": "oracle direct solve (sparse LU) of the same system"}
         if batch is not None and refs.get("batch"):
             errs = [rel_err(batch_u[i], us) for i, us in refs["batch"].items()]
@@ -688,6 +693,8 @@ def main():
                     help="also measure the batching form (512 problems) after the headline")
     ap.add_argument("--serving-form", default="on", choices=["on", "off"],
                     help="also run a short serving stream after the headline")
+    ap.add_argument("--fp64-form", default="on", choices=["on", "off"],
+                    help="also time the FP64 GPU form of the same workload")
     ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"],
                     help="time the oracle on the host cores and state the errors against its solution")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
