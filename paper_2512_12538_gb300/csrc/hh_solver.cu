@@ -649,7 +649,7 @@ struct Solver final : SolverBase {
         std::vector<LeafTask> t;
         for (int id : lev[L]) {
             const Node& nd = nodes[id];
-            LeafTask k;
+            LeafTask k{};
             k.X = X[id];
             k.W = W[id];
             k.b = nd.b();
@@ -673,7 +673,7 @@ struct Solver final : SolverBase {
         std::vector<const void*> key{(const void*)(size_t)nc};
         for (int id : lev[L]) {
             const Node& nd = nodes[id];
-            LeafTask k;
+            LeafTask k{};
             k.X = X[id];
             k.W = W[id];
             k.b = nd.b();
@@ -689,7 +689,7 @@ struct Solver final : SolverBase {
            cerr);
     }
     EigTask eig_task(int id, const void* F, void* Wout) const {
-        EigTask k;
+        EigTask k{};
         k.V = EV[id];
         k.xi = EXI[id];
         k.lam = ELAM[id];
@@ -783,7 +783,7 @@ struct Solver final : SolverBase {
                 }
                 et.push_back(k);
             } else {
-                LeafTask k;
+                LeafTask k{};
                 k.X = X[id];
                 k.W = W[id];
                 k.b = nd.b();
@@ -1659,7 +1659,7 @@ struct Solver final : SolverBase {
             else
                 for (int stg = 0; stg < 3; ++stg) eig_sweep_stage(stg, d_etask_one, 1, nc);
         } else {
-            LeafTask k;
+            LeafTask k{};
             k.X = X[id];
             k.F = Vs[id];
             k.W = W[id];
@@ -1811,6 +1811,7 @@ struct BatchEngine {
         int it = 0, chk_it = 0;
         double rel = 0.0, best = 0.0, chk = 0.0;
         hh_status st = HH_OK;
+        bool live = true;                // false once it has left (its jobs gated off)
     };
     cudaStream_t stream = nullptr;
     int cap_probs = 0, cap_tasks = 0;
@@ -1841,6 +1842,11 @@ struct BatchEngine {
     std::vector<unsigned long long> graph_key;
     bool resid_pending = false;   // the current problems' residuals are already enqueued
     unsigned long long replays = 0, captures = 0;
+    // Gate word per position of act: a problem that leaves keeps its place in the captured
+    // graph with its word set, so that its jobs return at once; the set is compacted (and
+    // the graph captured again) when a quarter of it has left or a problem joins.
+    int* gates = nullptr;
+    bool joined = false;
 
     hh_status init(cudaStream_t s, int probs, int tasks, const AllocHook& h) {
         stream = s;
@@ -1848,7 +1854,8 @@ struct BatchEngine {
         cap_tasks = std::max(tasks, 1);
         hook = h;
         bytes = align_up(sizeof(EigTask) * cap_tasks, 256) + align_up(sizeof(double) * part_cap, 256) +
-                align_up(sizeof(double) * (cap_probs + 8), 256) + align_up(sizeof(c128) * 304 * 64, 256) + 256;
+                align_up(sizeof(double) * (cap_probs + 8), 256) + align_up(sizeof(c128) * 304 * 64, 256) + 256 +
+                align_up(sizeof(int) * cap_probs, 256);
         base = (char*)dev_alloc(bytes, stream, hook);
         if (!base) return HH_ENOMEM;
         size_t off = 0;
@@ -1859,6 +1866,8 @@ struct BatchEngine {
         cpart = (c128*)take(sizeof(c128) * 304 * 64);
         bar = (unsigned*)take(256);
         berr = (int*)(bar + 4);
+        gates = (int*)take(sizeof(int) * cap_probs);
+        ck(cudaMemsetAsync(gates, 0, sizeof(int) * cap_probs, stream), cerr);
         ck(cudaMallocHost(&h_norms, sizeof(double) * (cap_probs + 8)), cerr);
         ck(cudaMemsetAsync(bar, 0, 256, stream), cerr);
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
@@ -1881,16 +1890,23 @@ struct BatchEngine {
     }
     int tasks_in_use() const {
         int n = 0;
-        for (auto& q : act) n += (int)q.p->h_pre.size();
+        for (auto& q : act)
+            if (q.live) n += (int)q.p->h_pre.size();
+        return n;
+    }
+    int live_count() const {
+        int n = 0;
+        for (auto& q : act) n += q.live;
         return n;
     }
     // whether p can join: lockstep-able, room left, and a fused-sweep cluster size that
     // serves every member
     bool can_add(Solver<T>* p) const {
-        if (!batchable(p) || (int)act.size() >= cap_probs) return false;
+        if (!batchable(p) || live_count() >= cap_probs) return false;
         if (tasks_in_use() + (int)p->h_pre.size() > cap_tasks) return false;
         int bm = p->b_max, sx = p->Sx, smin = p->Sx;
         for (auto& q : act) {
+            if (!q.live) continue;
             bm = std::max(bm, q.p->b_max);
             sx = std::max(sx, q.p->Sx);
             smin = std::min(smin, q.p->Sx);
@@ -1912,8 +1928,20 @@ struct BatchEngine {
         q.tag = tag;
         q.serial = next_serial++;
         q.it = -1;   // the first step reads ||b||^2
+        compact();   // a joining problem takes its place in a set without departed ones
         act.push_back(q);
+        ck(cudaMemsetAsync(gates, 0, sizeof(int) * act.size(), stream), cerr);
         resid_pending = false;   // the next step enqueues every current problem's residual
+        joined = true;
+    }
+    // drop the departed problems from the set (positions change: the gate words are reset)
+    void compact() {
+        std::vector<Prob> keep;
+        for (auto& q : act)
+            if (q.live) keep.push_back(q);
+        if (keep.size() == act.size()) return;
+        act.swap(keep);
+        ck(cudaMemsetAsync(gates, 0, sizeof(int) * std::max<size_t>(act.size(), 1), stream), cerr);
     }
     // One iteration for every current problem; problems that leave are appended to `done`
     // (their solution already copied to uo, the copy complete).
@@ -1930,6 +1958,7 @@ struct BatchEngine {
                 j.y = p->res;
                 j.yt = p->RT;
                 j.g = p->geom(0);
+                j.gate = gates + k;
             }
             launch_residual_batch<T>(rb, part, part_cap, norms + c0, stream);
         }
@@ -1944,10 +1973,10 @@ struct BatchEngine {
         ck(cudaStreamSynchronize(stream), cerr);
         if (cerr != cudaSuccess) return HH_ECUDA;
         if (*(const int*)(h_norms + cap_probs) == DEV_TIMEOUT) return HH_ETIMEOUT;
-        std::vector<Prob> still;
         bool left = false;
         for (int k = 0; k < na; ++k) {
             Prob& q = act[k];
+            if (!q.live) continue;
             if (q.it < 0) q.it = 0;
             const double b2 = q.p->h_norm[2];
             q.rel = b2 > 0 ? std::sqrt(h_norms[k] / b2) : 0.0;
@@ -1971,15 +2000,24 @@ struct BatchEngine {
                 ck(cudaMemcpyAsync(q.uo, q.p->u, sizeof(c128) * (size_t)q.p->Sy * q.p->Sx, cudaMemcpyDeviceToDevice,
                                    stream),
                    cerr);
+                // its jobs in the captured graph return at once from now on
+                const int one = 1;
+                ck(cudaMemcpyAsync(gates + k, &one, sizeof(int), cudaMemcpyHostToDevice, stream), cerr);
+                q.live = false;
                 done.push_back(q);
                 left = true;
-            } else {
-                still.push_back(q);
             }
         }
         if (left) ck(cudaStreamSynchronize(stream), cerr);
-        act.swap(still);
-        if (act.empty()) return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+        const int nl = live_count();
+        if (nl == 0) {
+            act.clear();
+            drop_graph();
+            return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
+        }
+        // compact once a quarter of the set has left (the graph is captured again)
+        if (4 * (na - nl) >= na) compact();
+        joined = false;
         // one preconditioner step for every current problem
         std::vector<Solver<T>*> ids;
         std::vector<unsigned long long> key;
@@ -1991,8 +2029,12 @@ struct BatchEngine {
             std::vector<EigTask> tk;
             bmax = sxmax = 0;
             int smin = 1 << 30;
-            for (auto* p : ids) {
-                tk.insert(tk.end(), p->h_pre.begin(), p->h_pre.end());
+            for (size_t k = 0; k < ids.size(); ++k) {
+                Solver<T>* p = ids[k];
+                for (EigTask t : p->h_pre) {
+                    t.gate = gates + k;
+                    tk.push_back(t);
+                }
                 bmax = std::max(bmax, p->b_max);
                 sxmax = std::max(sxmax, p->Sx);
                 smin = std::min(smin, p->Sx);
@@ -2033,7 +2075,8 @@ struct BatchEngine {
         ck(cudaGraphLaunch(gexec, stream), cerr);
         ++replays;
         resid_pending = true;
-        for (auto& q : act) ++q.it;
+        for (auto& q : act)
+            if (q.live) ++q.it;
         ck(cudaGetLastError(), cerr);
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
@@ -2049,16 +2092,21 @@ struct BatchEngine {
         // internal nodes, deepest first: height = L - level; level 1 writes into u (FP64)
         for (int hgt = 1; hgt < lmax; ++hgt) {
             for (int to64 = 0; to64 < 2; ++to64) {
-                std::vector<std::pair<Solver<T>*, int>> jobs;   // (problem, node)
-                for (auto* p : ids) {
+                struct NodeJob {
+                    Solver<T>* p;
+                    int id, k;   // node, position of the problem in the set
+                };
+                std::vector<NodeJob> jobs;
+                for (size_t k = 0; k < ids.size(); ++k) {
+                    Solver<T>* p = ids[k];
                     const int l = p->L - hgt;
                     if (l < 1 || (l == 1) != (to64 == 1)) continue;
-                    for (int id : p->lev[l]) jobs.push_back({p, id});
+                    for (int id : p->lev[l]) jobs.push_back({p, id, (int)k});
                 }
                 std::vector<int> widths;   // one launch per basis width and per CB_MAX_JOBS nodes
                 for (auto& jn : jobs)
-                    if (std::find(widths.begin(), widths.end(), 2 * jn.first->r) == widths.end())
-                        widths.push_back(2 * jn.first->r);
+                    if (std::find(widths.begin(), widths.end(), 2 * jn.p->r) == widths.end())
+                        widths.push_back(2 * jn.p->r);
                 for (int w : widths) {
                     CoarseBatch bt{};
                     auto flush = [&]() {
@@ -2068,9 +2116,9 @@ struct BatchEngine {
                         bt = CoarseBatch{};
                     };
                     for (auto& jn : jobs) {
-                        Solver<T>* p = jn.first;
+                        Solver<T>* p = jn.p;
                         if (2 * p->r != w) continue;
-                        const int id = jn.second;
+                        const int id = jn.id;
                         const Node& nd = p->nodes[id];
                         CoarseJob& j = bt.job[bt.njobs++];
                         j.C = p->C[id];
@@ -2086,6 +2134,7 @@ struct BatchEngine {
                         j.acc_out = to64;
                         j.add_w = 1;
                         j.split = p->split_row(id);
+                        j.gate = gates + jn.k;
                         if (bt.njobs == CB_MAX_JOBS) flush();
                     }
                     flush();
@@ -2098,9 +2147,11 @@ struct BatchEngine {
             if (std::find(widths.begin(), widths.end(), 2 * p->r) == widths.end()) widths.push_back(2 * p->r);
         for (int w : widths) {
             CoarseBatch bt{};
-            for (auto* p : ids) {
+            for (size_t k = 0; k < ids.size(); ++k) {
+                Solver<T>* p = ids[k];
                 if (2 * p->r != w) continue;
-                bt.job[bt.njobs++] = p->one_job(0, p->bvec, p->u, p->u, true).job[0];
+                bt.job[bt.njobs] = p->one_job(0, p->bvec, p->u, p->u, true).job[0];
+                bt.job[bt.njobs++].gate = gates + k;
                 if (bt.njobs == CB_MAX_JOBS) {
                     launch_coarse_batch<T, double, double, double>(bt, w, cpart, bar, berr, stream);
                     bt = CoarseBatch{};
@@ -2476,19 +2527,24 @@ struct Server {
             hh_status st64 = e64.step(d64);
             retire(e64, d64);
             if (st32 != HH_OK) {
-                for (auto& q : e32.act) complete((ServerReq*)q.tag, st32, es);
+                for (auto& q : e32.act)
+                    if (q.live) complete((ServerReq*)q.tag, st32, es);
                 e32.act.clear();
                 e32.uploaded.clear();
             }
             if (st64 != HH_OK) {
-                for (auto& q : e64.act) complete((ServerReq*)q.tag, st64, es);
+                for (auto& q : e64.act)
+                    if (q.live) complete((ServerReq*)q.tag, st64, es);
                 e64.act.clear();
                 e64.uploaded.clear();
             }
         }
-        // shutting down: requests still iterating are dropped (their handles freed)
-        for (auto& q : e32.act) complete((ServerReq*)q.tag, HH_ECUDA, es);
-        for (auto& q : e64.act) complete((ServerReq*)q.tag, HH_ECUDA, es);
+        // shutting down: requests still iterating are dropped (their handles freed); the
+        // entries that have left were completed when they left
+        for (auto& q : e32.act)
+            if (q.live) complete((ServerReq*)q.tag, HH_ECUDA, es);
+        for (auto& q : e64.act)
+            if (q.live) complete((ServerReq*)q.tag, HH_ECUDA, es);
         cudaStreamSynchronize(es);
         e32.release();
         e64.release();

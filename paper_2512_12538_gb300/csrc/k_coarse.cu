@@ -165,6 +165,12 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
     const unsigned N = (unsigned)g.b * (unsigned)g.Sx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ph = p >> 1, G = J.ngrp;
+    // a job of a problem that has left (the same word for all its blocks): its blocks take
+    // part in the grid barrier only, touching none of its buffers
+    if (J.gate && *J.gate) {
+        grid_barrier(bar, err, bt.wait_polls);
+        return;
+    }
     {
         const int chunks = (int)(sizeof(CA) * p * p / 16);
         for (int t = threadIdx.x; t < chunks; t += blockDim.x)

@@ -746,6 +746,9 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
     const int q = (int)cluster.block_rank();
     const int cl = (int)cluster.num_blocks();
     const EigTask tk = tasks[blockIdx.y];
+    // a task of a problem that has left (the same word for the whole cluster): return before
+    // any cluster barrier and any access to its buffers
+    if (tk.gate && *tk.gate) return;
     const int b = tk.b;
     const int Sx = tk.Sx;
     const FsGeom G = fs_geom(b, Sx, cl);

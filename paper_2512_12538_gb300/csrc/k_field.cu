@@ -234,6 +234,7 @@ __global__ void k_residual_batch(ResidBatch bt, double* part) {
     int jb = 0;
     while (jb + 1 < bt.njobs && blockIdx.x >= bt.job[jb + 1].blk0) ++jb;
     const ResidJob& J = bt.job[jb];
+    if (J.gate && *J.gate) return;   // a problem that has left: nothing of it is touched
     const OpGeom g = J.g;
     const size_t total = (size_t)g.b * g.Sx;
     const unsigned lb = blockIdx.x - J.blk0;
@@ -266,6 +267,7 @@ __global__ void k_residual_batch(ResidBatch bt, double* part) {
 }
 __global__ void k_sum_batch(ResidBatch bt, const double* part, double* norms) {
     const ResidJob& J = bt.job[blockIdx.x];
+    if (J.gate && *J.gate) return;
     double a = 0.0;
     for (unsigned i = threadIdx.x; i < J.nblk; i += blockDim.x) a += part[J.blk0 + i];
     __shared__ double red[32];

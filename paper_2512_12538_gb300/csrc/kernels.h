@@ -32,6 +32,7 @@ struct ResidJob {
     void* yt;
     OpGeom g;
     unsigned blk0, nblk;   // set by the launcher
+    const int* gate;       // may be null: while the word is nonzero the job touches nothing
 };
 struct ResidBatch {
     ResidJob job[RB_MAX_JOBS];
@@ -117,6 +118,8 @@ struct CoarseJob {
                            // out's old value), in the basis precision, at out's index
     int ngrp;              // set by the launcher: column groups per half (p/2 / CB_COLS, rounded up)
     unsigned sb[5];        // set by the launcher: blocks of set s are [sb[s], sb[s + 1])
+    const int* gate;       // may be null: while the word is nonzero the job's blocks only take
+                           // part in the grid barrier and touch none of the job's buffers
 };
 // Optional extras of a one-job launch on the root in the device-tested stationary loop.
 // Phase 1 keeps r' = v - A~ w (the residual after the level-1 update) in rp; phase 3
@@ -246,6 +249,8 @@ struct EigTask {
                       // W + (a - w0) Sx (the three-stage sweep: all rows, w0 = 0, w1 = b)
     const void* vt_emb;   // complex64 form: V^T and V as the tensor-core transforms' B operand
     const void* vn_emb;   // (tc_prepare_v layout; null where the transforms run on CUDA cores)
+    const int* gate;      // one-launch sweep: may be null; while the word is nonzero the task's
+                          // cluster returns at once, touching none of the task's buffers
 };
 
 // Layout of the transformed vectors Fh of a multi-vector sweep (b rows of J = Sx nrhs):
