@@ -726,14 +726,15 @@ struct Solver final : SolverBase {
     // The three-stage sweep of several right-hand sides: transforms on the tensor cores
     // in the complex64 form, else on the CUDA cores; the line recursions in between.
     void eig_sweep_stage(int stg, const EigTask* tasks, int ntasks, int nc) {
+        // inside a gated step (step_gate set) every launch is skipped once the stop word is set
         if (!tc || stg == 1) {
-            launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream);
+            launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream, step_gate);
             return;
         }
         // transforms: tensor cores or CUDA cores, as the autotuner found faster for this shape
         auto run = [&](int c) {
-            if (c) launch_tc_transform(stg == 0 ? 0 : 1, tasks, ntasks, b_max, Sx, nc, derr, stream);
-            else launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream);
+            if (c) launch_tc_transform(stg == 0 ? 0 : 1, tasks, ntasks, b_max, Sx, nc, derr, stream, step_gate);
+            else launch_eig_sweep_stage<T>(stg, tasks, ntasks, b_max, Sx, nc, stream, step_gate);
         };
         const TuneKey key{current_device(), 0, stg, b_max, Sx, nc * 64 + std::min(ntasks, 63)};
         int choice = 1;
@@ -762,12 +763,12 @@ struct Solver final : SolverBase {
            cerr);
     }
     // Leaf tasks of the preconditioner step (one vector, from the root's residual RT),
-    // fixed after set-up so that captured graphs can read them.  With n_i = 1 and the
-    // one-launch sweep, each leaf writes its owned rows straight into its parent's
-    // solution (restricted prolongation without a copy).
+    // fixed after set-up so that captured graphs can read them.  With n_i = 1 each leaf
+    // writes its owned rows straight into its parent's solution (restricted prolongation
+    // without a copy).
     void upload_pre_tasks() {
         const bool direct_in = P.n_inner == 1;
-        pre_direct = eig && eig_fused && direct_in && L >= 2;
+        pre_direct = eig && direct_in && L >= 2;
         std::vector<EigTask> et;
         std::vector<LeafTask> lt;
         for (int id : lev[L]) {
@@ -1367,15 +1368,16 @@ struct Solver final : SolverBase {
     // The launches of one stationary step on the fast path (n_i = 1, fused eigenbasis
     // leaf sweeps writing into the parents, L >= 2) are the leaf sweep and the batched
     // coarse corrections: all of them, and the residual that follows, take a gate.
+    // (the one-launch sweep and the three-stage one both take the stop word)
     bool device_test_path() const {
-        return eig && eig_fused && pre_direct && P.n_inner == 1 && L >= 2 && P.outer == HH_OUTER_ORAS;
+        return eig && pre_direct && P.n_inner == 1 && L >= 2 && P.outer == HH_OUTER_ORAS;
     }
 
-    // residual b - A u into res and RT, its norm and the device stopping test (ctl), one
-    // launch; dcounter[0] is its ticket
+    // residual b - A u into RT (the step's input; the FP64 vector itself is not kept), its
+    // norm and the device stopping test (ctl), one launch; dcounter[0] is its ticket
     void gated_residual(int* ctl, const int* need = nullptr, const int* anchor = nullptr) {
         pbeg(PC_SPMV, 48.0 * (double)Sy * Sx);
-        launch_residual_stop<T>(u, bvec, res, RT, geom(0), npart, dnorm, ctl, dcounter, P.tol, stream, need, anchor);
+        launch_residual_stop<T>(u, bvec, nullptr, RT, geom(0), npart, dnorm, ctl, dcounter, P.tol, stream, need, anchor);
         pend(PC_SPMV);
     }
 
@@ -1408,8 +1410,13 @@ struct Solver final : SolverBase {
     // The recursive residual serves the complex64 form: the FP64 form's residual is already
     // in its working precision, and there the recursion's extra FP64 work costs more than
     // the residual launch it saves.
+    // It reads the root's A~_0 C_0 (r columns at each point) in every step: worth it while
+    // that stays in the L2, not when it is read from HBM, where it costs about as much as the
+    // FP64 residual it replaces.
     bool recur_possible() const {
-        return sizeof(T) == sizeof(float) && eig && L >= 2 && P.n_inner == 1 && P.outer == HH_OUTER_ORAS;
+        const size_t ac_bytes = 2 * (size_t)r * Sy * Sx * sizeof(CT);
+        return sizeof(T) == sizeof(float) && eig && L >= 2 && P.n_inner == 1 && P.outer == HH_OUTER_ORAS &&
+               ac_bytes <= ((size_t)64 << 20);
     }
     hh_status loop_oras_device_test(int& it, double& rel) {
         // [0] stop (1 converged, 2 not finite), [1] FP64 tests run, [2] FP64 residual due,

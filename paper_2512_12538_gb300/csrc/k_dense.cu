@@ -387,6 +387,110 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<TI>*
     ip_store_partial<double, KMAX>(acc, p, p, split, red, partial + (size_t)blockIdx.x * nout);
 }
 
+// The FP64 form of the same partial sums with three real products per complex product
+// (the 3M method: Higham, "Accuracy and Stability of Numerical Algorithms", 2nd ed.,
+// Sec. 23.2.4).  For conj(a) b, with the staged sums a- = ar - ai, b- = bi - br and
+// b+ = br + bi,
+//   Re = br a- + ai b+,   Im = br a- + ar b-,
+// so a thread accumulates S1 = sum br a-, S2 = sum ar b-, S3 = sum ai b+ and forms
+// (S1 + S3, S1 + S2) at the end: 3 FP64 multiply-adds per product instead of 4, the
+// additions done once per staged element.  Each staged value is one FP64 rounding of an
+// exact sum (a complex64 basis widens exactly), so the error stays at FP64 level,
+// bounded like the 4-product form's by a few ulps of (|ar| + |ai|)(|br| + |bi|).
+// Block of G3_THREADS threads (one per SM: the three sums of KMAX outputs a thread fit the
+// registers of one such block), each thread owning KMAX whole outputs (p * p >= G3_THREADS).
+static constexpr int G3_THREADS = 512;
+template <typename TI, int KMAX>
+__global__ void __launch_bounds__(G3_THREADS, 1) k_galerkin_partial3(const cplx<TI>* __restrict__ C, OpGeom g, int p,
+                                                                     int split_row, c128* partial) {
+    extern __shared__ __align__(16) unsigned char gsm_[];
+    double* As = (double*)gsm_;                      // [IP_TILE][p] x {ar, ai, ar - ai}
+    double* Bs = As + 3 * (size_t)IP_TILE * p;       // [IP_TILE][p] x {br, bi - br, br + bi}
+    const int nout = p * p;
+    double s1[KMAX], s2[KMAX], s3[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) s1[k] = s2[k] = s3[k] = 0.0;
+    const size_t N = (size_t)g.b * g.Sx;
+    const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
+    const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+    for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
+        const int rows = (int)min((size_t)IP_TILE, n1 - t0);
+        // the half-block skipping of k_galerkin_partial
+        int ilo = 0, ihi = 0, jlo = 0, jhi = 0;
+        if (split_row >= 0) {
+            const int j0 = (int)(t0 / g.Sx), j1 = (int)((t0 + rows - 1) / g.Sx);
+            if (j1 < split_row) { ilo = 0; ihi = p / 2; }
+            else if (j0 >= split_row) { ilo = p / 2; ihi = p; }
+            if (j1 < split_row - 1) { jlo = 0; jhi = p / 2; }
+            else if (j0 > split_row) { jlo = p / 2; jhi = p; }
+        }
+        for (int e = threadIdx.x; e < rows * p; e += G3_THREADS) {
+            const size_t pt = t0 + e / p;
+            const int l = e % p;
+            const bool need_a = ihi == 0 || (l >= ilo && l < ihi);
+            const bool need_b = jhi == 0 || (l >= jlo && l < jhi);
+            if (!need_a && !need_b) continue;
+            const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
+            const size_t t = (size_t)l * N + pt;          // column-major basis
+            const c128 cv = cvt<double>(C[t]);
+            c128 ax;
+            if (g.Sx > 1 && i > 0 && i < g.Sx - 1 && j > 0 && j < g.b - 1) {
+                // interior row: unit weights, no impedance term, real diagonal 4 - (kh)^2
+                const double kr = g.khr ? g.khr[j] : g.kh;
+                const double d = 4.0 - kr * kr;
+                const c128 n1 = cvt<double>(C[t - 1]), n2 = cvt<double>(C[t + 1]);
+                const c128 n3 = cvt<double>(C[t - g.Sx]), n4 = cvt<double>(C[t + g.Sx]);
+                ax.re = d * cv.re - n1.re - n2.re - n3.re - n4.re;
+                ax.im = d * cv.im - n1.im - n2.im - n3.im - n4.im;
+            } else {
+                ax = op_diag(j, i, g) * cv;
+                const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+                if (g.Sx > 1) {
+                    if (i > 0) ax = ax - wj * cvt<double>(C[t - 1]);
+                    if (i < g.Sx - 1) ax = ax - wj * cvt<double>(C[t + 1]);
+                }
+                if (j > 0) ax = ax - wi * cvt<double>(C[t - g.Sx]);
+                if (j < g.b - 1) ax = ax - wi * cvt<double>(C[t + g.Sx]);
+            }
+            double* a = As + 3 * (size_t)e;
+            double* b = Bs + 3 * (size_t)e;
+            a[0] = cv.re;
+            a[1] = cv.im;
+            a[2] = cv.re - cv.im;
+            b[0] = ax.re;
+            b[1] = ax.im - ax.re;
+            b[2] = ax.re + ax.im;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int o = threadIdx.x + k * G3_THREADS;
+            if (o >= nout) continue;
+            const int i = o / p, j = o % p;
+            if (ihi > 0 && (i < ilo || i >= ihi)) continue;
+            if (jhi > 0 && (j < jlo || j >= jhi)) continue;
+            double x1 = s1[k], x2 = s2[k], x3 = s3[k];
+            for (int n = 0; n < rows; ++n) {
+                const double* a = As + 3 * ((size_t)n * p + i);
+                const double* b = Bs + 3 * ((size_t)n * p + j);
+                x1 = fma(b[0], a[2], x1);
+                x2 = fma(a[0], b[1], x2);
+                x3 = fma(a[1], b[2], x3);
+            }
+            s1[k] = x1;
+            s2[k] = x2;
+            s3[k] = x3;
+        }
+        __syncthreads();
+    }
+    c128* out = partial + (size_t)blockIdx.x * nout;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int o = threadIdx.x + k * G3_THREADS;
+        if (o < nout) out[o] = {s1[k] + s3[k], s1[k] + s2[k]};
+    }
+}
+
 template <typename TI, typename T>
 int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
                             cudaStream_t s) {
@@ -400,6 +504,23 @@ int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c
     static std::atomic<unsigned long long> attr4{0}, attrmax{0};
     smem_limit_once(attr4, k_galerkin_partial<TI, T, 4>, 200 * 1024);
     smem_limit_once(attrmax, k_galerkin_partial<TI, T, IP_MAXOUT>, 200 * 1024);
+    if (sizeof(T) == sizeof(double) && nout >= G3_THREADS && nout <= 8 * G3_THREADS) {
+        // FP64 products, whole outputs per thread: the 3M form, one block per SM
+        const size_t sm3 = sizeof(double) * 6 * (size_t)IP_TILE * p;
+        static std::atomic<unsigned long long> a32{0}, a34{0}, a38{0};
+        smem_limit_once(a32, k_galerkin_partial3<TI, 2>, 200 * 1024);
+        smem_limit_once(a34, k_galerkin_partial3<TI, 4>, 200 * 1024);
+        smem_limit_once(a38, k_galerkin_partial3<TI, 8>, 200 * 1024);
+        const int g3 = std::min(grid, max_blocks / 2 > 0 ? max_blocks / 2 : 1);
+        if (nout <= 2 * G3_THREADS)
+            k_galerkin_partial3<TI, 2><<<g3, G3_THREADS, sm3, s>>>(C, g, p, split_row, partial);
+        else if (nout <= 4 * G3_THREADS)
+            k_galerkin_partial3<TI, 4><<<g3, G3_THREADS, sm3, s>>>(C, g, p, split_row, partial);
+        else
+            k_galerkin_partial3<TI, 8><<<g3, G3_THREADS, sm3, s>>>(C, g, p, split_row, partial);
+        note_launch();
+        return g3;
+    }
     // accumulators sized to the outputs a thread owns (p <= 32: at most 4), so that the
     // registers allow two blocks per SM and the grid runs in one wave
     if (nout <= 4 * IP_THREADS)

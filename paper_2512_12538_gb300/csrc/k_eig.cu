@@ -296,7 +296,8 @@ static constexpr int GT_N = 8, GT_K = 32, GT_THREADS = 256, GT_ROWS = 32, GT_RPT
 
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restrict__ tasks, int J, int which,
-                                                         int Sx, int nrhs, int kchunk) {
+                                                         int Sx, int nrhs, int kchunk, const int* gate) {
+    if (gate && *gate) return;   // a set stop word skips the launch (the same for every block)
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
     const int j0 = blockIdx.x * GT_N;
@@ -373,10 +374,12 @@ __global__ void __launch_bounds__(GT_THREADS) k_eig_gemm(const EigTask* __restri
     if (j0 + jj < J) {
         const int jj2 = j0 + jj;
         const size_t col = which == 0 ? fh_col((size_t)jj2, Sx, nrhs) : (size_t)jj2;
+        // x = V x^ keeps rows [w0, w1) (all rows, or the owned rows written into the parent)
+        const int rlo = which == 0 ? 0 : tk.w0, rhi = which == 0 ? b : tk.w1;
 #pragma unroll
         for (int t = 0; t < GT_RPT; ++t) {
             const int r = rg + t * GT_ROWS;
-            if (r < b) C[(size_t)r * J + col] = acc[t];
+            if (r >= rlo && r < rhi) C[(size_t)(r - rlo) * J + col] = acc[t];
         }
     }
 }
@@ -390,7 +393,8 @@ template <> struct Gemm2Cols<double> { static constexpr int CV = 2; };
 
 template <typename T, bool TRANS, int RU>
 __global__ void __launch_bounds__(256) k_eig_gemm2(const EigTask* __restrict__ tasks, int J, int which, int Sx,
-                                                   int nrhs) {
+                                                   int nrhs, const int* gate) {
+    if (gate && *gate) return;   // a set stop word skips the launch (the same for every block)
     constexpr int CV = Gemm2Cols<T>::CV, GN = 16 * CV;
     using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.y];
@@ -446,6 +450,8 @@ __global__ void __launch_bounds__(256) k_eig_gemm2(const EigTask* __restrict__ t
 #pragma unroll
             for (int v = 0; v < CV; ++v) cfma(acc[u][v], vr[u], bc[v]);
     }
+    // x = V x^ keeps rows [w0, w1) (all rows, or the owned rows written into the parent)
+    const int rlo = which == 0 ? 0 : tk.w0, rhi = which == 0 ? b : tk.w1;
 #pragma unroll
     for (int v = 0; v < CV; ++v) {
         const int jj = j0 + cg + 16 * v;
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(256) k_eig_gemm2(const EigTask* __restrict__ t
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
             const int r = rg + 16 * u;
-            if (r < b) Cout[(size_t)r * J + col] = acc[u][v];
+            if (r >= rlo && r < rhi) Cout[(size_t)(r - rlo) * J + col] = acc[u][v];
         }
     }
 }
@@ -522,7 +528,9 @@ __device__ __forceinline__ void warp_line_solve(const cplx<T>* as, cplx<T>* fs, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs, int wpb) {
+__global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ tasks, int Sx, int nrhs, int wpb,
+                                                   const int* gate) {
+    if (gate && *gate) return;   // a set stop word skips the launch (the same for every block)
     using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
@@ -560,7 +568,9 @@ __global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ t
 // xi[m][i] is one broadcast load per warp and step.  Each lane loads RB steps of its line
 // and of xi at once before running them, so a chain step waits on no load.
 template <typename T>
-__global__ void __launch_bounds__(256) k_eig_recur_cols(const EigTask* __restrict__ tasks, int Sx, int nrhs) {
+__global__ void __launch_bounds__(256) k_eig_recur_cols(const EigTask* __restrict__ tasks, int Sx, int nrhs,
+                                                        const int* gate) {
+    if (gate && *gate) return;   // a set stop word skips the launch (the same for every block)
     using C = cplx<T>;
     constexpr int RB = 16;
     const EigTask tk = tasks[blockIdx.y];
@@ -629,7 +639,7 @@ void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, do
 // stage 0: transform in, 1: recursions, 2: transform out.
 template <typename T>
 void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* gate) {
     const int J = Sx * nrhs;
     dim3 g1((J + GT_N - 1) / GT_N, ntasks);
     // stage as much of V as fits in ~96 KB (all of it for complex64 bands up to 136 rows)
@@ -653,26 +663,26 @@ void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b
         dim3 g2((J + GN2 - 1) / GN2, ntasks);
         const bool small = b_max <= 80;
         if (stage == 0) {
-            if (small) k_eig_gemm2<T, true, 5><<<g2, 256, sm2, s>>>(d_tasks, J, 0, Sx, nrhs);
-            else k_eig_gemm2<T, true, 9><<<g2, 256, sm2, s>>>(d_tasks, J, 0, Sx, nrhs);
+            if (small) k_eig_gemm2<T, true, 5><<<g2, 256, sm2, s>>>(d_tasks, J, 0, Sx, nrhs, gate);
+            else k_eig_gemm2<T, true, 9><<<g2, 256, sm2, s>>>(d_tasks, J, 0, Sx, nrhs, gate);
         } else {
-            if (small) k_eig_gemm2<T, false, 5><<<g2, 256, sm2, s>>>(d_tasks, J, 1, Sx, nrhs);
-            else k_eig_gemm2<T, false, 9><<<g2, 256, sm2, s>>>(d_tasks, J, 1, Sx, nrhs);
+            if (small) k_eig_gemm2<T, false, 5><<<g2, 256, sm2, s>>>(d_tasks, J, 1, Sx, nrhs, gate);
+            else k_eig_gemm2<T, false, 9><<<g2, 256, sm2, s>>>(d_tasks, J, 1, Sx, nrhs, gate);
         }
     } else if (stage == 0) {
-        k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0, Sx, nrhs, kchunk);
+        k_eig_gemm<T, true><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 0, Sx, nrhs, kchunk, gate);
     } else if (stage == 2) {
-        k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1, Sx, nrhs, kchunk);
+        k_eig_gemm<T, false><<<g1, GT_THREADS, sm, s>>>(d_tasks, J, 1, Sx, nrhs, kchunk, gate);
     } else if (!eig_line_major(nrhs)) {
         const int warps = b_max * ((nrhs + 31) / 32);
         dim3 g3((warps + 7) / 8, ntasks);
-        k_eig_recur_cols<T><<<g3, 256, 0, s>>>(d_tasks, Sx, nrhs);
+        k_eig_recur_cols<T><<<g3, 256, 0, s>>>(d_tasks, Sx, nrhs, gate);
     } else {
         const size_t per_warp = 2 * sizeof(cplx<T>) * (size_t)Sx;
         const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp));
         const int lines = b_max * nrhs;
         dim3 g2((lines + wpb - 1) / wpb, ntasks);
-        k_eig_recur<T><<<g2, 32 * wpb, per_warp * wpb, s>>>(d_tasks, Sx, nrhs, wpb);
+        k_eig_recur<T><<<g2, 32 * wpb, per_warp * wpb, s>>>(d_tasks, Sx, nrhs, wpb, gate);
     }
     note_launch();
 }
@@ -954,8 +964,8 @@ int eig_bmax() { return GT_ROWS * GT_RPT < EIG_BMAX ? GT_ROWS * GT_RPT : EIG_BMA
 template void launch_eig_factor<float>(const EigTask*, int, int, int, double, int*, cudaStream_t);
 template void launch_eig_factor<double>(const EigTask*, int, int, int, double, int*, cudaStream_t);
 template void launch_eig_sweep<float>(const EigTask*, int, int, int, int, cudaStream_t);
-template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t);
-template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t);
+template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t, const int*);
+template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t, const int*);
 template void launch_eig_sweep<double>(const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep_fused<float>(int, const EigTask*, int, int, int, cudaStream_t, const int*);
 template void launch_eig_sweep_fused<double>(int, const EigTask*, int, int, int, cudaStream_t, const int*);

@@ -95,38 +95,45 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
     const bool wt = !stop.anchor || *stop.anchor;
     const size_t total = (size_t)g.b * g.Sx;
     // interior points of a 2D band with one k: the row is (4 - (kh)^2) x minus the four
-    // neighbours, the same FP64 operations in the same order as the general row below,
-    // without forming its weights and impedance terms (the FP64 pipe bounds this kernel)
+    // neighbours, formed as v - (4 - (kh)^2) x (one FMA) plus the neighbours' sum, without
+    // the weights and impedance terms of the general row below (the FP64 pipe bounds this
+    // kernel: 12 FP64 operations per interior point and the two conversions of yt)
     const double d_in = 4.0 - g.kh * g.kh;
     double acc2 = 0.0;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.Sx);
-        const int j = (int)(t / g.Sx);
-        if (g.Sx > 1 && !g.khr && i > 0 && i < g.Sx - 1 && j > 0 && j < g.b - 1) {
-            const c128 xc = x[t];
-            c128 ax = {d_in * xc.re, d_in * xc.im};
-            ax = ax - x[t - 1];
-            ax = ax - x[t + 1];
-            ax = ax - x[t - g.Sx];
-            ax = ax - x[t + g.Sx];
-            const c128 out = v[t] - ax;
-            y[t] = out;
-            if (wt) yt[t] = cvt<T>(out);
-            acc2 += abs2(out);
-            continue;
+    const unsigned Sx = (unsigned)g.Sx;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    // the point's column and row, advanced by the stride without a division per point
+    unsigned i = (unsigned)(t % Sx), j = (unsigned)(t / Sx);
+    const unsigned step_r = (unsigned)(stride % Sx), step_q = (unsigned)(stride / Sx);
+    for (; t < total; t += stride) {
+        c128 out;
+        if (Sx > 1 && !g.khr && i > 0 && i < Sx - 1 && j > 0 && j < (unsigned)g.b - 1) {
+            const c128 xc = x[t], vc = v[t];
+            const c128 w = x[t - 1], e = x[t + 1], s = x[t - Sx], n = x[t + Sx];
+            out.re = fma(-d_in, xc.re, vc.re) + ((w.re + e.re) + (s.re + n.re));
+            out.im = fma(-d_in, xc.im, vc.im) + ((w.im + e.im) + (s.im + n.im));
+        } else {
+            c128 ax = op_diag((int)j, (int)i, g) * x[t];
+            const double wj = wrow((int)j, g.b), wi = wcol((int)i, g.Sx);
+            if (Sx > 1) {
+                if (i > 0) ax = ax - wj * x[t - 1];
+                if (i < Sx - 1) ax = ax - wj * x[t + 1];
+            }
+            if (j > 0) ax = ax - wi * x[t - Sx];
+            if (j < (unsigned)g.b - 1) ax = ax - wi * x[t + Sx];
+            out = v[t] - ax;
         }
-        c128 ax = op_diag(j, i, g) * x[t];
-        const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
-        if (g.Sx > 1) {
-            if (i > 0) ax = ax - wj * x[t - 1];
-            if (i < g.Sx - 1) ax = ax - wj * x[t + 1];
-        }
-        if (j > 0) ax = ax - wi * x[t - g.Sx];
-        if (j < g.b - 1) ax = ax - wi * x[t + g.Sx];
-        const c128 out = v[t] - ax;
-        y[t] = out;
+        if (y) y[t] = out;
         if (wt) yt[t] = cvt<T>(out);
-        acc2 += abs2(out);
+        acc2 = fma(out.re, out.re, acc2);
+        acc2 = fma(out.im, out.im, acc2);
+        i += step_r;
+        j += step_q;
+        if (i >= Sx) {
+            i -= Sx;
+            ++j;
+        }
     }
     __shared__ double red[32];
     __shared__ unsigned s_last;

@@ -186,7 +186,11 @@ void launch_tc_prepare_v(const EigTask* d_tasks, int ntasks, int b_max, cudaStre
 // input's contiguous column index p.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* __restrict__ tasks, int ntasks,
                                                                 int which, int Sx, int nrhs, int b_max,
-                                                                int tiles_per_task, uint32_t limit, int* err) {
+                                                                int tiles_per_task, uint32_t limit, int* err,
+                                                                const int* gate) {
+    // a set stop word (written by an earlier launch: the same for every CTA) skips the
+    // launch before the tensor memory is allocated
+    if (gate && *gate) return;
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
     unsigned char* tsm = (unsigned char*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(tsm + 2 * TC_STAGE_BYTES);       // bulk copy of B landed, per stage
@@ -254,6 +258,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         const int p0 = (tile % tiles_per_task) * TC_COLS;
         const int b = tk.b;
         c64* outp = (c64*)(which == 0 ? tk.Fh : tk.W);
+        // x = V x^ keeps rows [w0, w1) (all rows, or the owned rows written into the parent)
+        const int rlo = which == 0 ? 0 : tk.w0, rhi = which == 0 ? b : tk.w1;
         const unsigned char* bsrc = (const unsigned char*)(which == 0 ? tk.vt_emb : tk.vn_emb);
 
         for (int q = 0; q < g.nq; ++q, ++chunk) {
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
                 c64 o;
                 if (even) o = c64{d0[t] - v1, d1[t] + v0};          // rr - ii, ri + ir
                 else o = c64{v0 - d1[8 + t], v1 + d0[8 + t]};
-                if (p < J && m < b) outp[(size_t)m * J + col] = o;
+                if (p < J && m >= rlo && m < rhi) outp[(size_t)(m - rlo) * J + col] = o;
             }
         }
         // the next tile's MMAs overwrite the accumulators
@@ -390,7 +396,7 @@ int tc_transform_ready() {
 }
 
 void launch_tc_transform(int which, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, int* err,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int* gate) {
     const int J = Sx * nrhs;
     const int tiles_per_task = (J + TC_COLS - 1) / TC_COLS;
     int dev = 0, sms = 0;
@@ -400,7 +406,7 @@ void launch_tc_transform(int which, const EigTask* d_tasks, int ntasks, int b_ma
     if (grid > sms) grid = sms > 0 ? sms : 1;     // one block per SM (shared and tensor memory)
     const uint32_t limit = (uint32_t)std::min<long long>(wait_polls(TC_WAIT_LIMIT), 0xFFFFFFFFll);
     k_tc_transform<<<grid, TC_THREADS, TC_SMEM, s>>>(d_tasks, ntasks, which, Sx, nrhs, b_max, tiles_per_task, limit,
-                                                     err);
+                                                     err, gate);
     note_launch();
 }
 

@@ -50,7 +50,8 @@ void launch_apply_cols(const cplx<T>* x, cplx<T>* y, OpGeom g, int p, cudaStream
 // launch_residual_cast with the stopping test of the stationary iteration kept on the
 // device, in the same launch.  Unless ctl[0] is already set, or need is given and zero
 // (then nothing is done); yt is written only when anchor is null or nonzero:
-// y, yt and the partials as launch_residual_cast, then nrm[0] = ||y||^2 (launch_sum's
+// y (may be null: not stored), yt and the partials as launch_residual_cast, then
+// nrm[0] = ||y||^2 (launch_sum's
 // order), ctl[1] += 1, and with rel = sqrt(nrm[0] / nrm[2]) (0 when nrm[2] <= 0)
 // ctl[0] = 2 if rel is not finite, 1 if rel < tol.  ctl[0] is the gate of the next
 // step's launches; ticket is a device counter that is zero between launches.
@@ -245,8 +246,8 @@ struct EigTask {
     void* W;          // solutions [b][Sx][nrhs]
     int b;
     int Sx;           // columns of the leaf's problem (tasks of several problems may share a launch)
-    int w0, w1;       // the one-launch sweep writes local rows [w0, w1) only, row a to
-                      // W + (a - w0) Sx (the three-stage sweep: all rows, w0 = 0, w1 = b)
+    int w0, w1;       // the sweep writes local rows [w0, w1) only, row a to W + (a - w0) Sx nrhs
+                      // (all rows: w0 = 0, w1 = b)
     const void* vt_emb;   // complex64 form: V^T and V as the tensor-core transforms' B operand
     const void* vn_emb;   // (tc_prepare_v layout; null where the transforms run on CUDA cores)
     const int* gate;      // one-launch sweep: may be null; while the word is nonzero the task's
@@ -271,9 +272,10 @@ void launch_tc_prepare_v(const EigTask* d_tasks, int ntasks, int b_max, cudaStre
 int tc_transform_ready();
 // The complex64 sweep transforms on the tensor cores: which = 0, Fh = V^T F; which = 1,
 // W = V Fh (layouts as the three-stage sweep).  err: device status word (DEV_TIMEOUT on a
-// bounded wait that gave up).
+// bounded wait that gave up).  gate (may be null): a device word; when it is nonzero at launch
+// the launch does nothing.
 void launch_tc_transform(int which, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, int* err,
-                         cudaStream_t s);
+                         cudaStream_t s, const int* gate = nullptr);
 template <typename T>
 void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,
                        cudaStream_t s);
@@ -295,10 +297,10 @@ bool eig_sweep_fused_feasible(int cl, int b_max, int Sx);
 template <typename T>
 void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_max, int Sx, cudaStream_t s,
                             const int* gate = nullptr);
-// stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^
+// stage 0: f^ = V^T f; 1: scalar recursions; 2: x = V x^.  gate as launch_eig_sweep_fused.
 template <typename T>
 void launch_eig_sweep_stage(int stage, const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* gate = nullptr);
 int eig_bmax();
 
 }  // namespace hh
