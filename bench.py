@@ -484,14 +484,21 @@ def run_serving_line(args):
 def run_case(args):
     """--form case: one set-up and a few stationary steps of the workload's grid and
     hierarchy at rank --case-rank (oversampling 4), with no timing: the small case the
-    profiler captures of single kernels run on (profiles/)."""
+    profiler captures of single kernels run on (profiles/).  --case-n takes a smaller grid
+    (n interior points a side, k scaled to keep the workload's k h) with the same hierarchy."""
+    import dataclasses
+
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     import paper_2512_12538_gb300 as hh
+    from workloads import problem_inputs
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     w, f, g = workload_inputs()
+    if args.case_n and args.case_n != w.n:
+        w = dataclasses.replace(w, n=args.case_n, k=w.k * (args.case_n + 1) / (w.n + 1))
+        f, g = problem_inputs(w)
     fd = torch.from_numpy(f).cuda()
     gd = torch.from_numpy(g).cuda()
     u = torch.empty_like(fd)
@@ -503,8 +510,8 @@ def run_case(args):
     st = hh.hh_solve(h, fd, gd, u, allow_noconv=True)
     torch.cuda.synchronize()
     hh.hh_destroy(h)
-    return {"case": WORKLOAD, "rank": args.case_rank, "footprint_bytes": fp, "iters": st.iters,
-            "rel_res": st.rel_res}
+    return {"case": WORKLOAD, "n": w.n, "k": w.k, "rank": args.case_rank, "footprint_bytes": fp,
+            "iters": st.iters, "rel_res": st.rel_res}
 
 
 def pct(xs, q):
@@ -689,6 +696,7 @@ def main():
                          "case profiler captures run on (--case-rank, --case-steps)")
     ap.add_argument("--case-rank", type=int, default=16)
     ap.add_argument("--case-steps", type=int, default=12)
+    ap.add_argument("--case-n", type=int, default=0, help="case: interior points a side (0: the workload's)")
     ap.add_argument("--batch-form", default="on", choices=["on", "off"],
                     help="also measure the batching form (512 problems) after the headline")
     ap.add_argument("--serving-form", default="on", choices=["on", "off"],

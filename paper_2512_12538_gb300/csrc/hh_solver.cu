@@ -1058,8 +1058,10 @@ struct Solver final : SolverBase {
                                       (size_t)(cn.own_a - nodes[p].ra) * Sx, (size_t)(cn.own_b - cn.own_a) * Sx,
                                       stream);
             }
-            // A_c = C_p^H A~_p C_p, then its inverse
-            pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT), 8.0 * 2.0 * r * r * pts(p));
+            // A_c = C_p^H A~_p C_p, then its inverse.  Algorithmic work: a point in one child's
+            // rows pairs that child's r columns of conj(C) with r columns of A~ C, r^2 complex
+            // products of 8 real flops (the two rows next to the split pair r with 2r)
+            pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT), 8.0 * r * r * (pts(p) + 2.0 * Sx));
             const int split = nodes[nodes[p].child[1]].own_a - nodes[p].ra;
             // FP64 products from the stored basis, or FP32 ones in the opt-in FP32 coarse
             // variant of the mixed form

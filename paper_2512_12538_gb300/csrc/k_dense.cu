@@ -304,6 +304,27 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 }
 
 // ------------------------------------------------------------------- Galerkin
+// Points of block `blk` of `nblk` in a Galerkin launch over N = b Sx points, shared out by
+// cost: with a split row the two rows next to it (split - 1 and split) need every column of
+// A~ C against one half of conj(C), twice a point's work elsewhere, so they count twice.
+// An even split of the points left the blocks on those rows with twice the mean work.
+__device__ __forceinline__ void gal_range(size_t N, int Sx, int split_row, unsigned blk, unsigned nblk,
+                                          size_t& n0, size_t& n1) {
+    size_t s0 = 0, s1 = 0;   // the rows of double cost: [s0, s1)
+    if (split_row >= 0) {
+        s0 = min(N, (size_t)max(split_row - 1, 0) * Sx);
+        s1 = min(N, (size_t)(split_row + 1) * Sx);
+    }
+    const size_t T = N + (s1 - s0);
+    auto inv = [&](size_t c) -> size_t {   // the point at cost c (monotone in c)
+        if (c <= s0) return c;
+        if (c <= s0 + 2 * (s1 - s0)) return s0 + (c - s0) / 2;
+        return c - (s1 - s0);
+    };
+    n0 = inv(T * blk / nblk);
+    n1 = blk + 1 == nblk ? N : inv(T * (blk + 1) / nblk);
+}
+
 // partial[blk][a][l] = sum over the block's points of conj(C[pt][a]) * (A~ C)[pt][l].
 // C is stored in TI (complex64 in the mixed form); the stencil and the products run in
 // T.  T = double: FP64 arithmetic on the basis values (a complex64 basis widens exactly),
@@ -329,8 +350,8 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<TI>*
     const int nk = split > 1 ? 1 : (nout + IP_THREADS - 1) / IP_THREADS;   // outputs owned
     int ntile = 0;
     const size_t N = (size_t)g.b * g.Sx;
-    const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
-    const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+    size_t n0, n1;
+    gal_range(N, g.Sx, split_row, blockIdx.x, gridDim.x, n0, n1);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
         const int rows = (int)min((size_t)IP_TILE, n1 - t0);
         // C's columns [0, p/2) live on rows < split_row, [p/2, p) on the others, and A~ C
@@ -411,8 +432,8 @@ __global__ void __launch_bounds__(G3_THREADS, 1) k_galerkin_partial3(const cplx<
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) s1[k] = s2[k] = s3[k] = 0.0;
     const size_t N = (size_t)g.b * g.Sx;
-    const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
-    const size_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+    size_t n0, n1;
+    gal_range(N, g.Sx, split_row, blockIdx.x, gridDim.x, n0, n1);
     for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
         const int rows = (int)min((size_t)IP_TILE, n1 - t0);
         // the half-block skipping of k_galerkin_partial
