@@ -107,6 +107,15 @@ typedef struct {
  * can, without timing the alternatives (the choice the autotuner otherwise makes per
  * shape).  Not together with HH_FLAG_CUDA_CORE_SWEEPS. */
 #define HH_FLAG_TENSOR_CORE_SWEEPS 4u
+/* hh_params.flags: discretise with the paper's bilinear (Q1) finite elements on the same
+ * nodes (Sec. 3: mass-weighted 9-point rows A = M_y (x) (X_x - (kh)^2 M_x - i kh B_x) +
+ * (X_y - i kh B_y) (x) M_x, with the consistent 1D masses M and stiffnesses X over h, and
+ * the load vector b = h^2 M_y F M_x^T + h (edge masses) g) instead of the weighted 5-point
+ * differences (which are these elements with lumped masses).  2D only, with
+ * leaf_solver = HH_LEAF_EIGEN and one wavenumber (k_rows NULL); otherwise HH_EINVAL.
+ * The lockstep engine takes 5-point problems only: hh_solve_batch and a server solve these
+ * one at a time. */
+#define HH_FLAG_BILINEAR 8u
 
 typedef enum {
     HH_LEAF_EIGEN = 0,    /* 2D leaves: the block Schur recursion evaluated in the eigenbasis */

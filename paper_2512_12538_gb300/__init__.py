@@ -21,7 +21,7 @@ _BINDING = {
     "use_torch_allocator", "hh_profile_enable", "hh_profile_categories", "hh_profile_read", "hh_launch_count", "PROFILE_CATEGORIES",
     "HH_LEAF_EIGEN", "HH_LEAF_BLOCK", "HH_OUTER_ORAS", "HH_OUTER_GMRES",
     "hh_residual_noalloc", "HH_ETOOLARGE", "HH_NOALLOC_MAX_ROWS", "hh_setup_batch", "hh_solve_batch", "hh_server_create", "hh_server_submit",
-    "hh_server_poll", "hh_server_destroy", "HH_EPENDING", "HH_FLAG_COARSE_FP32", "HH_FLAG_CUDA_CORE_SWEEPS", "HH_FLAG_TENSOR_CORE_SWEEPS",
+    "hh_server_poll", "hh_server_destroy", "HH_EPENDING", "HH_FLAG_COARSE_FP32", "HH_FLAG_CUDA_CORE_SWEEPS", "HH_FLAG_TENSOR_CORE_SWEEPS", "HH_FLAG_BILINEAR",
     "hh_debug_set_wait_limit", "hh_autotune_report",
 }
 

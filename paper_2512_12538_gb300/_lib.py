@@ -24,6 +24,7 @@ HH_OUTER_ORAS, HH_OUTER_GMRES = 0, 1
 HH_FLAG_COARSE_FP32 = 1
 HH_FLAG_CUDA_CORE_SWEEPS = 2
 HH_FLAG_TENSOR_CORE_SWEEPS = 4
+HH_FLAG_BILINEAR = 8
 
 
 class hh_params(ctypes.Structure):

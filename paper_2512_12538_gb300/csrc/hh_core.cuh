@@ -57,6 +57,7 @@ struct OpGeom {
     int Sx;       // columns
     double kh;    // k * h
     const double* khr;   // k h per row of the band (device; layered media, Sec. 3.3) or null: kh
+    int q1;       // nonzero: the bilinear elements below instead of the 5-point rows (one k)
 };
 
 HH_HD double wrow(int j, int b) { return (j == 0 || j == b - 1) ? 0.5 : 1.0; }
@@ -93,6 +94,40 @@ template <typename R> HH_HD cplx<R> op_diag_t(int j, int i, const OpGeom& g) {
     }
     const R kh = (R)(g.khr ? g.khr[j] : g.kh);
     return {wj * cx + wi * cy - kh * kh * wi * wj, -kh * (wj * bx + wi * (by ? (R)1 : (R)0))};
+}
+
+// Bilinear (Q1) elements of Sec. 3 on the same grid and band.  Over h, the 1D element
+// matrices of a line of n nodes are the mass M = tridiag(1, 4, 1) / 6 (2/6 at the two
+// ends) and the stiffness X = tridiag(-1, 2, -1) (1 at the ends); with B the end flags,
+//   A = M_y (x) K_x + K'_y (x) M_x,   K_x = X_x - (kh)^2 M_x - i kh B_x,   K'_y = X_y - i kh B_y,
+// (y the band's rows, x its columns; the impedance terms are the edge masses of the element
+// boundary integrals).  Its row (j, i) couples the 3 x 3 neighbourhood; q1_coef is the
+// coefficient of u(j + dj, i + di), for a neighbour inside the band.
+HH_HD double q1_mass(int a, int d, int n) { return d != 0 ? 1.0 / 6.0 : ((a == 0 || a == n - 1) ? 2.0 / 6.0 : 4.0 / 6.0); }
+HH_HD double q1_stiff(int a, int d, int n) { return d != 0 ? -1.0 : ((a == 0 || a == n - 1) ? 1.0 : 2.0); }
+HH_HD c128 q1_coef(int j, int dj, int i, int di, const OpGeom& g) {
+    const double q = g.kh;
+    const double my = q1_mass(j, dj, g.b), xy = q1_stiff(j, dj, g.b);
+    const double mx = q1_mass(i, di, g.Sx), xx = q1_stiff(i, di, g.Sx);
+    const double by = (dj == 0 && (j == 0 || j == g.b - 1)) ? 1.0 : 0.0;
+    const double bx = (di == 0 && (i == 0 || i == g.Sx - 1)) ? 1.0 : 0.0;
+    return {my * (xx - q * q * mx) + xy * mx, -q * (my * bx + by * mx)};
+}
+// (A u)(j, i) for the bilinear elements, in precision R; at(dj, di) returns u(j + dj, i + di)
+// (called for neighbours inside the band only).
+template <typename R, typename F> HH_HD cplx<R> q1_row(int j, int i, const OpGeom& g, F&& at) {
+    cplx<R> acc = {0, 0};
+    for (int dj = -1; dj <= 1; ++dj) {
+        if (j + dj < 0 || j + dj >= g.b) continue;
+        for (int di = -1; di <= 1; ++di) {
+            if (i + di < 0 || i + di >= g.Sx) continue;
+            const c128 c = q1_coef(j, dj, i, di, g);
+            const cplx<R> v = at(dj, di);
+            acc.re += (R)c.re * v.re - (R)c.im * v.im;
+            acc.im += (R)c.re * v.im + (R)c.im * v.re;
+        }
+    }
+    return acc;
 }
 
 // ------------------------------------------------------------------ error reporting

@@ -263,8 +263,12 @@ static hh_status validate(const hh_params* P) {
     if (P->leaf_solver != HH_LEAF_EIGEN && P->leaf_solver != HH_LEAF_BLOCK) return HH_EINVAL;
     if (P->outer != HH_OUTER_ORAS && P->outer != HH_OUTER_GMRES) return HH_EINVAL;
     if (P->outer == HH_OUTER_GMRES && (P->restart < 1 || P->restart > 64)) return HH_EINVAL;
-    if (P->flags & ~(HH_FLAG_COARSE_FP32 | HH_FLAG_CUDA_CORE_SWEEPS | HH_FLAG_TENSOR_CORE_SWEEPS)) return HH_EINVAL;
+    if (P->flags & ~(HH_FLAG_COARSE_FP32 | HH_FLAG_CUDA_CORE_SWEEPS | HH_FLAG_TENSOR_CORE_SWEEPS | HH_FLAG_BILINEAR))
+        return HH_EINVAL;
     if ((P->flags & HH_FLAG_CUDA_CORE_SWEEPS) && (P->flags & HH_FLAG_TENSOR_CORE_SWEEPS)) return HH_EINVAL;
+    // bilinear elements: the eigenbasis leaves of a 2D problem with one wavenumber
+    if ((P->flags & HH_FLAG_BILINEAR) && (P->dim != 2 || P->leaf_solver != HH_LEAF_EIGEN || P->k_rows))
+        return HH_EINVAL;
     if (P->k_rows) {
         // layered media: the wavenumber varies across the rows of a band, which the
         // column-pencil eigenbasis of the 2D leaves does not take (explicit inverses do)
@@ -463,7 +467,7 @@ struct Solver final : SolverBase {
     // eigenbasis leaf path
     bool eig = false;
     int eig_fused = 0;          // cluster size of the one-launch single-vector sweep (0: off)
-    std::vector<CT*> EV, EXI, EFh;
+    std::vector<CT*> EV, EXI, EFh, ESC;   // ESC: per-mode input scales (bilinear elements)
     std::vector<c128*> ELAM;
     // complex64 form: the sweep transforms' B operands for the tensor cores (V^T and V)
     bool tc = false;
@@ -512,7 +516,8 @@ struct Solver final : SolverBase {
 
     // the mixed form's opt-in FP32 Galerkin products and coarse elimination
     bool coarse_fp32() const { return sizeof(CT) != sizeof(c128) && (P.flags & HH_FLAG_COARSE_FP32); }
-    OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh, khr_at(nodes[id].ra)}; }
+    int q1() const { return (P.flags & HH_FLAG_BILINEAR) ? 1 : 0; }   // bilinear elements
+    OpGeom geom(int id) const { return OpGeom{nodes[id].b(), Sx, kh, khr_at(nodes[id].ra), q1()}; }
     const double* khr_at(int grow) const { return khr_dev ? khr_dev + grow : nullptr; }
     size_t pts(int id) const { return (size_t)nodes[id].b() * Sx; }
     size_t row_off(int id, int grow, int nc) const { return (size_t)(grow - nodes[id].ra) * Sx * nc; }
@@ -548,7 +553,7 @@ struct Solver final : SolverBase {
         Ainv.assign(nn, nullptr); ycoef.assign(nn, nullptr); Gm.assign(nn, nullptr); U.assign(nn, nullptr);
         AinvT.assign(nn, nullptr);
         lam.assign(nn, nullptr); ldx.assign(nn, 0);
-        EV.assign(nn, nullptr); EXI.assign(nn, nullptr); EFh.assign(nn, nullptr);
+        EV.assign(nn, nullptr); EXI.assign(nn, nullptr); EFh.assign(nn, nullptr); ESC.assign(nn, nullptr);
         EVT.assign(nn, nullptr); EVN.assign(nn, nullptr);
         ELAM.assign(nn, nullptr);
         const size_t N = (size_t)Sy * Sx;
@@ -586,6 +591,7 @@ struct Solver final : SolverBase {
                 EXI[id] = a.take<CT>((size_t)Sx * b);
                 ELAM[id] = a.take<c128>(b);
                 EFh[id] = a.take<CT>(np * nmax);
+                if (q1()) ESC[id] = a.take<CT>(b);
                 if (tc) {
                     EVT[id] = a.take<unsigned char>(tc_vemb_bytes(b_max));
                     EVN[id] = a.take<unsigned char>(tc_vemb_bytes(b_max));
@@ -702,6 +708,7 @@ struct Solver final : SolverBase {
         k.w1 = k.b;
         k.vt_emb = EVT[id];
         k.vn_emb = EVN[id];
+        k.sc = ESC[id];
         return k;
     }
     // Cluster size of the one-launch single-vector sweep, 16 or 8 CTAs per leaf, timed on
@@ -1008,7 +1015,7 @@ struct Solver final : SolverBase {
             const Node& cn = nodes[c];
             const Node& sn = nodes[cn.sib];
             launch_robin_trace<T>(W[c] + row_off(c, sn.ifrow, m), W[c] + row_off(c, sn.inward, m), Om[c], sn.b(), Sx,
-                                  m, kh, khr_at(sn.ifrow), stream);
+                                  m, kh, khr_at(sn.ifrow), stream, q1());
         }
         // Q = orth(Y)
         std::vector<CT*> ys;
@@ -1022,7 +1029,7 @@ struct Solver final : SolverBase {
             const Node& sn = nodes[cn.sib];
             zero(Vs[c], sizeof(CT) * pts(c) * m);
             launch_adjoint_place<T>(Om[c], Vs[c] + row_off(c, sn.ifrow, m), Vs[c] + row_off(c, sn.inward, m), sn.b(),
-                                    Sx, m, kh, khr_at(sn.ifrow), stream);
+                                    Sx, m, kh, khr_at(sn.ifrow), stream, q1());
         }
         apply_M(l, m, true);
         for (int c : cs)
@@ -1119,7 +1126,7 @@ struct Solver final : SolverBase {
         cudaEventCreate(&e1);
         cudaEventRecord(e0, stream);
         pbeg(PC_FACTOR);
-        if (eig) launch_eig_factor<T>(d_etasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
+        if (eig) launch_eig_factor<T>(d_etasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream, q1());
         else launch_factor<T>(d_tasks_own, (int)lev[L].size(), b_max, Sx, kh, derr, stream);
         if (tc) launch_tc_prepare_v(d_etasks_own, (int)lev[L].size(), b_max, stream);
         pend(PC_FACTOR);
@@ -1418,7 +1425,7 @@ struct Solver final : SolverBase {
     bool recur_possible() const {
         const size_t ac_bytes = 2 * (size_t)r * Sy * Sx * sizeof(CT);
         return sizeof(T) == sizeof(float) && eig && L >= 2 && P.n_inner == 1 && P.outer == HH_OUTER_ORAS &&
-               ac_bytes <= ((size_t)64 << 20);
+               ac_bytes <= ((size_t)64 << 20) && !q1();
     }
     hh_status loop_oras_device_test(int& it, double& rel) {
         // [0] stop (1 converged, 2 not finite), [1] FP64 tests run, [2] FP64 residual due,
@@ -1595,7 +1602,7 @@ struct Solver final : SolverBase {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, stream);
-        launch_rhs(f, g, bvec, P.dim, S, h, stream);
+        launch_rhs(f, g, bvec, P.dim, S, h, stream, q1());
         norm_sq(bvec, dnorm + 2);   // dnorm[2..3] = ||b||^2 as a complex
         ck(cudaMemcpyAsync(h_norm, dnorm, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
         zero(u, sizeof(c128) * N);
@@ -1625,7 +1632,7 @@ struct Solver final : SolverBase {
     }
 
     hh_status residual(const c128* f, const c128* g, const c128* uu, double* rel) override {
-        launch_rhs(f, g, bvec, P.dim, S, h, stream);
+        launch_rhs(f, g, bvec, P.dim, S, h, stream, q1());
         norm_sq(bvec, dnorm + 2);
         int nb = 0;
         launch_apply<double, double, double>(uu, bvec, res, geom(0), 1, 1.0, npart, &nb, stream);
@@ -1694,12 +1701,12 @@ struct Solver final : SolverBase {
             launch_copy<double, T>(in, Vs[c] + row_off(c, cn.ifrow, nc), (size_t)Sx * nc, false, false, stream);
             apply_M(l, nc, true);
             launch_robin_trace<T>(W[c] + row_off(c, sn.ifrow, nc), W[c] + row_off(c, sn.inward, nc), Om[c], sn.b(), Sx,
-                                  nc, kh, khr_at(sn.ifrow), stream);
+                                  nc, kh, khr_at(sn.ifrow), stream, q1());
             launch_copy<T, double>(Om[c], out, (size_t)Sx * nc, false, false, stream);
         } else {
             launch_copy<double, T>(in, Om[c], (size_t)Sx * nc, false, false, stream);
             launch_adjoint_place<T>(Om[c], Vs[c] + row_off(c, sn.ifrow, nc), Vs[c] + row_off(c, sn.inward, nc), sn.b(),
-                                    Sx, nc, kh, khr_at(sn.ifrow), stream);
+                                    Sx, nc, kh, khr_at(sn.ifrow), stream, q1());
             apply_M(l, nc, true);
             launch_copy<T, double>(W[c] + row_off(c, cn.ifrow, nc), out, (size_t)Sx * nc, false, true, stream);
         }
@@ -1801,7 +1808,8 @@ static hh_status setup_one(const hh_params* p, cudaStream_t s, SolverBase** out,
 // one-launch sweep and at least two levels, for every problem, in one precision.
 template <typename T>
 static bool batchable(const Solver<T>* p) {
-    return p->eig && p->eig_fused && p->pre_direct && p->P.n_inner == 1 && p->P.outer == HH_OUTER_ORAS && p->L >= 2;
+    return p->eig && p->eig_fused && p->pre_direct && p->P.n_inner == 1 && p->P.outer == HH_OUTER_ORAS && p->L >= 2 &&
+           !p->q1();
 }
 
 // Lockstep iteration of several set-up problems: the engine of the batching and serving
@@ -1927,7 +1935,7 @@ struct BatchEngine {
     void add(Solver<T>* p, const c128* f, const c128* g, c128* uo, void* tag) {
         p->stream = stream;
         p->zero(p->derr, sizeof(int) * 4);
-        launch_rhs(f, g, p->bvec, p->P.dim, p->S, p->h, stream);
+        launch_rhs(f, g, p->bvec, p->P.dim, p->S, p->h, stream, p->q1());
         p->norm_sq(p->bvec, p->dnorm + 2);
         ck(cudaMemcpyAsync(p->h_norm + 2, p->dnorm + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), cerr);
         p->zero(p->u, sizeof(c128) * (size_t)p->Sy * p->Sx);

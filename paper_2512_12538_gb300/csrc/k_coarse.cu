@@ -192,7 +192,12 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
     // r = v - A~ w_in at one point (w_in null: r = v), in the basis precision
     auto resid_at = [&](unsigned pt) -> CA {
         cplx<R> rv = cvt<R>(v[pt]);
-        if (w_in) {
+        if (w_in && g.q1) {
+            const int jr = (int)(pt / (unsigned)g.Sx), i = (int)(pt - (unsigned)jr * g.Sx);
+            rv = rv - q1_row<R>(jr, i, g, [&](int dj, int di) {
+                     return cvt<R>(w_in[(size_t)((long long)pt + (long long)dj * g.Sx + di)]);
+                 });
+        } else if (w_in) {
             const int jr = (int)(pt / (unsigned)g.Sx), i = (int)(pt - (unsigned)jr * g.Sx);
             cplx<R> ax = op_diag_t<R>(jr, i, g) * cvt<R>(w_in[pt]);
             const R wj = (jr == 0 || jr == g.b - 1) ? (R)0.5 : (R)1;

@@ -375,15 +375,22 @@ __global__ void __launch_bounds__(IP_THREADS) k_galerkin_partial(const cplx<TI>*
             const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
             const size_t t = (size_t)l * N + pt;          // column-major basis
             const CT cv = cvt<T>(C[t]);
-            CT ax = op_diag_t<T>(j, i, g) * cv;
-            const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
-            const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
-            if (g.Sx > 1) {
-                if (i > 0) ax = ax - wj * cvt<T>(C[t - 1]);
-                if (i < g.Sx - 1) ax = ax - wj * cvt<T>(C[t + 1]);
+            CT ax;
+            if (g.q1) {
+                ax = q1_row<T>(j, i, g, [&](int dj, int di) {
+                    return cvt<T>(C[(size_t)((long long)t + (long long)dj * g.Sx + di)]);
+                });
+            } else {
+                ax = op_diag_t<T>(j, i, g) * cv;
+                const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
+                const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
+                if (g.Sx > 1) {
+                    if (i > 0) ax = ax - wj * cvt<T>(C[t - 1]);
+                    if (i < g.Sx - 1) ax = ax - wj * cvt<T>(C[t + 1]);
+                }
+                if (j > 0) ax = ax - wi * cvt<T>(C[t - g.Sx]);
+                if (j < g.b - 1) ax = ax - wi * cvt<T>(C[t + g.Sx]);
             }
-            if (j > 0) ax = ax - wi * cvt<T>(C[t - g.Sx]);
-            if (j < g.b - 1) ax = ax - wi * cvt<T>(C[t + g.Sx]);
             As[e] = cv;
             Bs[e] = ax;
         }
@@ -455,7 +462,11 @@ __global__ void __launch_bounds__(G3_THREADS, 1) k_galerkin_partial3(const cplx<
             const size_t t = (size_t)l * N + pt;          // column-major basis
             const c128 cv = cvt<double>(C[t]);
             c128 ax;
-            if (g.Sx > 1 && i > 0 && i < g.Sx - 1 && j > 0 && j < g.b - 1) {
+            if (g.q1) {
+                ax = q1_row<double>(j, i, g, [&](int dj, int di) {
+                    return cvt<double>(C[(size_t)((long long)t + (long long)dj * g.Sx + di)]);
+                });
+            } else if (g.Sx > 1 && i > 0 && i < g.Sx - 1 && j > 0 && j < g.b - 1) {
                 // interior row: unit weights, no impedance term, real diagonal 4 - (kh)^2
                 const double kr = g.khr ? g.khr[j] : g.kh;
                 const double d = 4.0 - kr * kr;

@@ -21,6 +21,18 @@
 // tridiagonal W^{-1/2} K W^{-1/2}; eigenvalues by the Aberth-Ehrlich simultaneous
 // iteration on its characteristic polynomial, eigenvectors by inverse iteration with a
 // pivoted tridiagonal LU, normalised q^T q = 1 (no conjugation).
+//
+// Bilinear elements (Sec. 3): the blocks are D_i = (X_ii - i kh bx_i) M + M^x_ii K and
+// L_i = U_{i-1} = -M + K / 6, with M the consistent 1D mass of the band (tridiagonal),
+// K = X - (kh)^2 M - i kh E, and M^x_ii the column's mass (4/6, 2/6 at the ends).  The same
+// decoupling holds with K V = M V Lambda, V^T M V = I: delta_{i,m} = M^x_ii lambda_m + X_ii
+// - i kh bx_i and the coupling l_m = -1 + lambda_m / 6 (-1 for the 5-point rows), so
+//     xi_{i,m} = 1 / (delta_{i,m} - l_m^2 xi_{i-1,m}),
+//     y_i = xi_i (f^_i - l y_{i-1}),  x_i = y_i - xi_i l x_{i+1}.
+// Written as the 5-point recursions with a_i = -l xi_i and the input f^ / (-l) (the mode's
+// scale `sc`), the recursion kernels run unchanged.  The pencil has no diagonal scaling to
+// a standard problem (M is not diagonal), so the eigenvalue recurrences and the inverse
+// iteration take K - z M directly, and V is normalised V^T M V = I.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -78,6 +90,44 @@ __device__ __forceinline__ void band_tridiag(int b, double kh, int a, cplx<R>& d
     e = {(R)(a < b - 1 ? -1.0 / sqrt(wa * wrow(a + 1, b)) : 0.0), (R)0};
 }
 
+// The bilinear elements' pencil of a band: K (diagonal kd, coupling ke between rows a and
+// a + 1) and the consistent mass (md, me).
+template <typename R>
+__device__ __forceinline__ void band_pencil_q1(int b, double kh, int a, cplx<R>& kd, cplx<R>& ke, R& md, R& me) {
+    const bool edge = (a == 0 || a == b - 1);
+    const double m = edge ? 2.0 / 6.0 : 4.0 / 6.0;
+    kd = {(R)((edge ? 1.0 : 2.0) - kh * kh * m), (R)(edge ? -kh : 0.0)};
+    ke = {(R)(a < b - 1 ? -1.0 - kh * kh / 6.0 : 0.0), (R)0};
+    md = (R)m;
+    me = (R)(a < b - 1 ? 1.0 / 6.0 : 0.0);
+}
+
+// Newton correction p(z) / p'(z) of p(z) = det(K - z M) for a tridiagonal pencil, from the
+// ratios r_j = p_j / p_{j-1} of its leading principal minors, with e_j = ke_{j-1} - z me_{j-1}:
+//   r_0 = kd_0 - z md_0,  r_j = kd_j - z md_j - e_j^2 / r_{j-1},
+//   r'_j = -md_j + 2 me_{j-1} e_j / r_{j-1} + e_j^2 r'_{j-1} / r_{j-1}^2,   p'/p = sum_j r'_j / r_j.
+template <typename R>
+__device__ cplx<R> newton_step_pencil(const cplx<R>* kd, const cplx<R>* ke, const R* md, const R* me, int b,
+                                      cplx<R> z) {
+    const R tiny = Eps<R>::tiny;
+    cplx<R> r = kd[0] - md[0] * z;
+    if (abs2(r) < tiny * tiny) r = {tiny, 0};
+    cplx<R> rp = {-md[0], 0};
+    cplx<R> ir = crcp_(r);
+    cplx<R> s = rp * ir;
+    for (int j = 1; j < b; ++j) {
+        const cplx<R> e = ke[j - 1] - me[j - 1] * z;
+        const cplx<R> q = (e * e) * ir;           // e^2 / r
+        cplx<R> rn = kd[j] - md[j] * z - q;
+        if (abs2(rn) < tiny * tiny) rn = {tiny, 0};
+        rp = cplx<R>{-md[j], 0} + ((R)2 * me[j - 1]) * (e * ir) + q * (rp * ir);
+        r = rn;
+        ir = crcp_(r);
+        s = s + rp * ir;
+    }
+    return cdiv_(cplx<R>{1, 0}, s);
+}
+
 // Newton correction p(z) / p'(z) of the characteristic polynomial p of the tridiagonal
 // matrix, from the ratios r_j = p_j / p_{j-1} of its leading principal minors:
 //   r_0 = d_0 - z,  r_j = d_j - z - e_{j-1}^2 / r_{j-1},
@@ -107,9 +157,11 @@ __device__ cplx<R> newton_step(const cplx<R>* d, const cplx<R>* e2, int b, cplx<
 // pivoted tridiagonal LU (row interchanges between neighbours), three iterations,
 // normalised q^T q = 1 (complex symmetric, no conjugation).
 // dd, ee: the band's tridiagonal (band_tridiag), staged once per leaf.
+// With a mass (md, me non-null: the bilinear elements' pencil) the matrix is K - mu M and
+// the vector is normalised x^T M x = 1.
 template <typename R>
 __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, cplx<R> mu, cplx<R>* x,
-                                  cplx<R>* ws) {
+                                  cplx<R>* ws, const R* md = nullptr, const R* me = nullptr) {
     using C = cplx<R>;
     C* dg = ws;
     C* up = ws + b;
@@ -117,13 +169,13 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
     C* lo = ws + 3 * b;
     R* sw = (R*)(ws + 4 * b);   // interchange flags
     for (int a = 0; a < b; ++a) {
-        dg[a] = dd[a] - mu;
-        up[a] = ee[a];
+        dg[a] = md ? dd[a] - md[a] * mu : dd[a] - mu;
+        up[a] = me ? ee[a] - me[a] * mu : ee[a];
         up2[a] = {0, 0};
         x[a] = {(R)1 + (R)1e-3 * (R)a, (R)1e-3 * (R)(a % 7)};
     }
     for (int j = 0; j < b - 1; ++j) {
-        const C esub = ee[j];   // sub-diagonal entry (j+1, j)
+        const C esub = me ? ee[j] - me[j] * mu : ee[j];   // sub-diagonal entry (j+1, j)
         if (abs2(dg[j]) >= abs2(esub)) {
             sw[j] = 0;
             const C fact = abs2(dg[j]) > (R)0 ? cdiv_(esub, dg[j]) : C{0, 0};
@@ -168,7 +220,16 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
         for (int a = 0; a < b; ++a) x[a] = inv * x[a];
     }
     C qq = {0, 0};
-    for (int a = 0; a < b; ++a) qq = qq + x[a] * x[a];
+    if (md) {
+        for (int a = 0; a < b; ++a) {
+            C mx = md[a] * x[a];
+            if (a > 0) mx = mx + me[a - 1] * x[a - 1];
+            if (a < b - 1) mx = mx + me[a] * x[a + 1];
+            qq = qq + x[a] * mx;
+        }
+    } else {
+        for (int a = 0; a < b; ++a) qq = qq + x[a] * x[a];
+    }
     const C nr = csqrt_(qq);
     for (int a = 0; a < b; ++a) x[a] = cdiv_(x[a], nr);
 }
@@ -181,20 +242,35 @@ __device__ void inverse_iteration(int b, const cplx<R>* dd, const cplx<R>* ee, c
 // started from the closed-form spectrum of the real part, 2 - 2cos(j pi/(b-1)) - (kh)^2
 // (the halved-end second difference has the cosine eigenvectors), shifted by the
 // first-order effect of the two impedance corners.
+// Bilinear elements (q1): the same iteration on det(K - z M), started from the closed-form
+// spectrum of the real part, 6 (1 - cos t) / (2 + cos t) - (kh)^2 with t = j pi / (b - 1) (the
+// cosine vectors again; the ends of X and M are halved alike), shifted by the first-order
+// effect of the two impedance corners.
 template <typename T>
-__global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ tasks, double kh, int* err) {
+__global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ tasks, double kh, int* err, int q1) {
     using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.x];
     const int b = tk.b;
     __shared__ C d[EIG_BMAX], e[EIG_BMAX], e2[EIG_BMAX], z[EIG_BMAX];
+    __shared__ T md[EIG_BMAX], me[EIG_BMAX];
     for (int a = threadIdx.x; a < b; a += blockDim.x) {
         C dd, ee;
-        band_tridiag<T>(b, kh, a, dd, ee);
+        if (q1) {
+            T m0, m1;
+            band_pencil_q1<T>(b, kh, a, dd, ee, m0, m1);
+            md[a] = m0;
+            me[a] = m1;
+            const double ct = cos(M_PI * a / (b - 1));
+            const double mu = 6.0 * (1.0 - ct) / (2.0 + ct) - kh * kh;
+            z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 12.0 / (2.0 + ct)) / (b - 1))};
+        } else {
+            band_tridiag<T>(b, kh, a, dd, ee);
+            const double mu = 2.0 - 2.0 * cos(M_PI * a / (b - 1)) - kh * kh;
+            z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 4.0) / (b - 1))};
+        }
         d[a] = dd;
         e[a] = ee;
         e2[a] = ee * ee;
-        const double mu = 2.0 - 2.0 * cos(M_PI * a / (b - 1)) - kh * kh;
-        z[a] = {(T)mu, (T)(-kh * (a == 0 ? 2.0 : 4.0) / (b - 1))};
     }
     __syncthreads();
     // A root is done when its correction is below 64 eps |z|, or when, already below
@@ -208,7 +284,7 @@ __global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ t
         if (threadIdx.x < b) {
             const int j = threadIdx.x;
             const C zj = z[j];
-            const C w = newton_step<T>(d, e2, b, zj);
+            const C w = q1 ? newton_step_pencil<T>(d, e, md, me, b, zj) : newton_step<T>(d, e2, b, zj);
             C s = {0, 0};
             for (int k = 0; k < b; ++k)
                 if (k != j) s = s + crcp_(zj - z[k]);
@@ -239,7 +315,7 @@ __global__ void __launch_bounds__(256) k_eig_roots(const EigTask* __restrict__ t
 static constexpr int EM_WARPS = 4;
 template <typename T>
 __global__ void __launch_bounds__(32 * EM_WARPS) k_eig_modes(const EigTask* __restrict__ tasks, int Sx, double kh,
-                                                            int* err) {
+                                                            int* err, int q1) {
     using C = cplx<T>;
     const EigTask tk = tasks[blockIdx.y];
     const int b = tk.b;
@@ -247,13 +323,23 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_eig_modes(const EigTask* __re
     C* dd = (C*)emsm;                          // [b] tridiagonal of the band
     C* ee = dd + b;                            // [b]
     C* wsall = ee + b;                         // [EM_WARPS][6 b] per-warp workspace
-    T* rw = (T*)(wsall + (size_t)EM_WARPS * 6 * b);   // [b] 1 / sqrt(w_a)
+    T* rw = (T*)(wsall + (size_t)EM_WARPS * 6 * b);   // [b] 1 / sqrt(w_a) (1 for q1)
+    T* md = rw + b;                            // [b], [b] the consistent mass (q1)
+    T* me = md + b;
     for (int a = threadIdx.x; a < b; a += blockDim.x) {
         C d1, e1;
-        band_tridiag<T>(b, kh, a, d1, e1);
+        if (q1) {
+            T m0, m1;
+            band_pencil_q1<T>(b, kh, a, d1, e1, m0, m1);
+            md[a] = m0;
+            me[a] = m1;
+            rw[a] = (T)1;
+        } else {
+            band_tridiag<T>(b, kh, a, d1, e1);
+            rw[a] = (T)(1.0 / sqrt(wrow(a, b)));
+        }
         dd[a] = d1;
         ee[a] = e1;
-        rw[a] = (T)(1.0 / sqrt(wrow(a, b)));
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -265,24 +351,35 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_eig_modes(const EigTask* __re
     const C lm = {(T)l64.re, (T)l64.im};
     if (lane == 0) {
         const C mu = lm + C{(T)(8 * Eps<T>::v) * fmax(cabs_(lm), (T)1), (T)0};
-        inverse_iteration<T>(b, dd, ee, mu, q, ws);
+        if (q1) inverse_iteration<T>(b, dd, ee, mu, q, ws, md, me);
+        else inverse_iteration<T>(b, dd, ee, mu, q, ws);
     }
     __syncwarp();
     C* V = (C*)tk.V;
     for (int a = lane; a < b; a += 32) V[a * b + m] = rw[a] * q[a];
     if (lane != 0) return;
-    // scalar Schur recursions along the columns (in T: the FP64 pipe is slow here)
+    // scalar Schur recursions along the columns (in T: the FP64 pipe is slow here).  q1:
+    // nl = -l_m = 1 - lambda_m / 6 couples the columns; the stored coefficient is nl xi
+    // (the multiplier of both recursions) and the mode's input scale 1 / nl (a coupling that
+    // vanishes to rounding is replaced by a tiny one: the mode's columns then decouple)
     C* xi = (C*)tk.xi;
     const T khT = (T)kh;
+    C nl = {1, 0};
+    if (q1) {
+        nl = C{(T)1, (T)0} - ((T)1 / (T)6) * lm;
+        if (abs2(nl) < Eps<T>::tiny * Eps<T>::tiny) nl = {Eps<T>::tiny, 0};
+        ((C*)tk.sc)[m] = crcp_(nl);
+    }
+    const C nl2 = nl * nl;
     C prev = {0, 0};
     for (int i = 0; i < Sx; ++i) {
         const bool xb = (i == 0 || i == Sx - 1);
-        const T wi = (Sx > 1 && xb) ? (T)0.5 : (T)1;
+        const T wi = q1 ? (xb ? (T)(2.0 / 6.0) : (T)(4.0 / 6.0)) : ((Sx > 1 && xb) ? (T)0.5 : (T)1);
         const C delta = C{xb ? (T)1 : (T)2, xb ? -khT : (T)0} + wi * lm;
-        const C sdel = delta - prev;
+        const C sdel = delta - nl2 * prev;
         if (!(abs2(sdel) > (T)0)) atomicExch(err, DEV_BREAKDOWN);
         prev = crcp_(sdel);   // |sdel| is of order one here: no scaling needed
-        xi[(size_t)m * Sx + i] = prev;
+        xi[(size_t)m * Sx + i] = q1 ? nl * prev : prev;
     }
 }
 
@@ -543,12 +640,13 @@ __global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ t
     C* fs = as + Sx;
     const C* xi = (const C*)tk.xi + (size_t)m * Sx;
     C* fh = (C*)tk.Fh + (size_t)line * Sx;     // line = m * nrhs + c
+    const C sc = tk.sc ? ((const C*)tk.sc)[m] : C{1, 0};   // the mode's input scale (q1)
     for (int i0 = lane; i0 < Sx; i0 += 32 * 8) {
         C ta[8], tf[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int i = i0 + 32 * u;
-            if (i < Sx) { ta[u] = xi[i]; tf[u] = fh[i]; }
+            if (i < Sx) { ta[u] = xi[i]; tf[u] = tk.sc ? sc * fh[i] : fh[i]; }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -581,6 +679,7 @@ __global__ void __launch_bounds__(256) k_eig_recur_cols(const EigTask* __restric
     if (c >= nrhs) return;
     const C* xi = (const C*)tk.xi + (size_t)m * Sx;
     C* fh = (C*)tk.Fh + (size_t)m * Sx * nrhs + c;
+    const C sc = tk.sc ? ((const C*)tk.sc)[m] : C{1, 0};   // the mode's input scale (q1)
     C y = {0, 0};
     for (int i0 = 0; i0 < Sx; i0 += RB) {
         C a[RB], f[RB];
@@ -589,6 +688,10 @@ __global__ void __launch_bounds__(256) k_eig_recur_cols(const EigTask* __restric
             const int i = min(i0 + u, Sx - 1);
             a[u] = xi[i];
             f[u] = fh[(size_t)i * nrhs];
+        }
+        if (tk.sc) {
+#pragma unroll
+            for (int u = 0; u < RB; ++u) f[u] = sc * f[u];
         }
 #pragma unroll
         for (int u = 0; u < RB; ++u) {
@@ -620,18 +723,19 @@ __global__ void __launch_bounds__(256) k_eig_recur_cols(const EigTask* __restric
 }
 
 template <typename T>
-void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err, cudaStream_t s) {
+void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err, cudaStream_t s,
+                       int q1) {
     if (b_max > EIG_BMAX) {
         int one = DEV_BADARG;
         cudaMemcpyAsync(err, &one, sizeof(int), cudaMemcpyHostToDevice, s);
         return;
     }
-    k_eig_roots<T><<<ntasks, 160, 0, s>>>(d_tasks, kh, err);
+    k_eig_roots<T><<<ntasks, 160, 0, s>>>(d_tasks, kh, err, q1);
     note_launch();
-    const size_t sm = sizeof(cplx<T>) * (size_t)b_max * (2 + 6 * EM_WARPS) + sizeof(T) * (size_t)b_max;
+    const size_t sm = sizeof(cplx<T>) * (size_t)b_max * (2 + 6 * EM_WARPS) + 3 * sizeof(T) * (size_t)b_max;
     static std::atomic<unsigned long long> attr{0};
     smem_limit_once(attr, k_eig_modes<T>, 200 * 1024);
-    k_eig_modes<T><<<dim3((b_max + EM_WARPS - 1) / EM_WARPS, ntasks), 32 * EM_WARPS, sm, s>>>(d_tasks, Sx, kh, err);
+    k_eig_modes<T><<<dim3((b_max + EM_WARPS - 1) / EM_WARPS, ntasks), 32 * EM_WARPS, sm, s>>>(d_tasks, Sx, kh, err, q1);
     note_launch();
 }
 
@@ -824,10 +928,12 @@ __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* _
         C* fs = lines + (size_t)warp * Sx;
         for (int m = mb + warp; m < me; m += FS_WARPS) {
             const C* as = XI + (size_t)(m - mb) * Sx;
+            const C sc = tk.sc ? ((const C*)tk.sc)[m] : C{1, 0};   // the mode's input scale (q1)
             for (int i = lane; i < Sx; i += 32) {
                 const int r = i / G.ncol;
                 const C* rem = cluster.map_shared_rank(Fs, r);
-                fs[i] = rem[m * G.ldf + (i - r * G.ncol)];
+                const C v = rem[m * G.ldf + (i - r * G.ncol)];
+                fs[i] = tk.sc ? sc * v : v;
             }
             __syncwarp();
             warp_line_solve(as, fs, Sx, lane);
@@ -961,8 +1067,8 @@ void launch_eig_sweep_fused(int cl, const EigTask* d_tasks, int ntasks, int b_ma
 
 int eig_bmax() { return GT_ROWS * GT_RPT < EIG_BMAX ? GT_ROWS * GT_RPT : EIG_BMAX; }
 
-template void launch_eig_factor<float>(const EigTask*, int, int, int, double, int*, cudaStream_t);
-template void launch_eig_factor<double>(const EigTask*, int, int, int, double, int*, cudaStream_t);
+template void launch_eig_factor<float>(const EigTask*, int, int, int, double, int*, cudaStream_t, int);
+template void launch_eig_factor<double>(const EigTask*, int, int, int, double, int*, cudaStream_t, int);
 template void launch_eig_sweep<float>(const EigTask*, int, int, int, int, cudaStream_t);
 template void launch_eig_sweep_stage<float>(int, const EigTask*, int, int, int, int, cudaStream_t, const int*);
 template void launch_eig_sweep_stage<double>(int, const EigTask*, int, int, int, int, cudaStream_t, const int*);

@@ -30,17 +30,24 @@ __global__ void k_apply(const cplx<TX>* __restrict__ x, const cplx<TV>* __restri
         const I jr = pt / (I)g.Sx;
         const int i = (int)(pt - jr * (I)g.Sx);
         const int j = (int)jr;
-        cplx<TY> ax = op_diag_t<TY>(j, i, g) * cvt<TY>(x[t]);
-        const TY wj = (j == 0 || j == g.b - 1) ? (TY)0.5 : (TY)1;
-        const TY wi = g.Sx == 1 ? (TY)1 : ((i == 0 || i == g.Sx - 1) ? (TY)0.5 : (TY)1);
-        // x-neighbours: coefficient -w_j
-        if (g.Sx > 1) {
-            if (i > 0) ax = ax - wj * cvt<TY>(x[t - nc]);
-            if (i < g.Sx - 1) ax = ax - wj * cvt<TY>(x[t + nc]);
+        cplx<TY> ax;
+        if (g.q1) {
+            ax = q1_row<TY>(j, i, g, [&](int dj, int di) {
+                return cvt<TY>(x[(size_t)((long long)t + (long long)dj * (long long)ldr + (long long)di * nc)]);
+            });
+        } else {
+            ax = op_diag_t<TY>(j, i, g) * cvt<TY>(x[t]);
+            const TY wj = (j == 0 || j == g.b - 1) ? (TY)0.5 : (TY)1;
+            const TY wi = g.Sx == 1 ? (TY)1 : ((i == 0 || i == g.Sx - 1) ? (TY)0.5 : (TY)1);
+            // x-neighbours: coefficient -w_j
+            if (g.Sx > 1) {
+                if (i > 0) ax = ax - wj * cvt<TY>(x[t - nc]);
+                if (i < g.Sx - 1) ax = ax - wj * cvt<TY>(x[t + nc]);
+            }
+            // y-neighbours: coefficient -w_i
+            if (j > 0) ax = ax - wi * cvt<TY>(x[t - ldr]);
+            if (j < g.b - 1) ax = ax - wi * cvt<TY>(x[t + ldr]);
         }
-        // y-neighbours: coefficient -w_i
-        if (j > 0) ax = ax - wi * cvt<TY>(x[t - ldr]);
-        if (j < g.b - 1) ax = ax - wi * cvt<TY>(x[t + ldr]);
         cplx<TY> out = (-sgn) * ax;
         if (v) out = cvt<TY>(v[t]) + out;
         y[t] = out;
@@ -108,7 +115,11 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
     const unsigned step_r = (unsigned)(stride % Sx), step_q = (unsigned)(stride / Sx);
     for (; t < total; t += stride) {
         c128 out;
-        if (Sx > 1 && !g.khr && i > 0 && i < Sx - 1 && j > 0 && j < (unsigned)g.b - 1) {
+        if (g.q1) {
+            out = v[t] - q1_row<double>((int)j, (int)i, g, [&](int dj, int di) {
+                      return x[(size_t)((long long)t + (long long)dj * Sx + di)];
+                  });
+        } else if (Sx > 1 && !g.khr && i > 0 && i < Sx - 1 && j > 0 && j < (unsigned)g.b - 1) {
             const c128 xc = x[t], vc = v[t];
             const c128 w = x[t - 1], e = x[t + 1], s = x[t - Sx], n = x[t + Sx];
             out.re = fma(-d_in, xc.re, vc.re) + ((w.re + e.re) + (s.re + n.re));
@@ -208,15 +219,20 @@ __global__ void k_apply_cols(const cplx<T>* __restrict__ x, cplx<T>* __restrict_
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const size_t pt = t % N;
         const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
-        cplx<T> ax = op_diag_t<T>(j, i, g) * x[t];
-        const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
-        const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
-        if (g.Sx > 1) {
-            if (i > 0) ax = ax - wj * x[t - 1];
-            if (i < g.Sx - 1) ax = ax - wj * x[t + 1];
+        cplx<T> ax;
+        if (g.q1) {
+            ax = q1_row<T>(j, i, g, [&](int dj, int di) { return x[(size_t)((long long)t + (long long)dj * g.Sx + di)]; });
+        } else {
+            ax = op_diag_t<T>(j, i, g) * x[t];
+            const T wj = (j == 0 || j == g.b - 1) ? (T)0.5 : (T)1;
+            const T wi = g.Sx == 1 ? (T)1 : ((i == 0 || i == g.Sx - 1) ? (T)0.5 : (T)1);
+            if (g.Sx > 1) {
+                if (i > 0) ax = ax - wj * x[t - 1];
+                if (i < g.Sx - 1) ax = ax - wj * x[t + 1];
+            }
+            if (j > 0) ax = ax - wi * x[t - g.Sx];
+            if (j < g.b - 1) ax = ax - wi * x[t + g.Sx];
         }
-        if (j > 0) ax = ax - wi * x[t - g.Sx];
-        if (j < g.b - 1) ax = ax - wi * x[t + g.Sx];
         y[t] = ax;
     }
 }
@@ -249,14 +265,19 @@ __global__ void k_residual_batch(ResidBatch bt, double* part) {
     for (size_t t = lb * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)J.nblk * blockDim.x) {
         const int i = (int)(t % g.Sx);
         const int j = (int)(t / g.Sx);
-        c128 ax = op_diag(j, i, g) * J.x[t];
-        const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
-        if (g.Sx > 1) {
-            if (i > 0) ax = ax - wj * J.x[t - 1];
-            if (i < g.Sx - 1) ax = ax - wj * J.x[t + 1];
+        c128 ax;
+        if (g.q1) {
+            ax = q1_row<double>(j, i, g, [&](int dj, int di) { return J.x[(size_t)((long long)t + (long long)dj * g.Sx + di)]; });
+        } else {
+            ax = op_diag(j, i, g) * J.x[t];
+            const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+            if (g.Sx > 1) {
+                if (i > 0) ax = ax - wj * J.x[t - 1];
+                if (i < g.Sx - 1) ax = ax - wj * J.x[t + 1];
+            }
+            if (j > 0) ax = ax - wi * J.x[t - g.Sx];
+            if (j < g.b - 1) ax = ax - wi * J.x[t + g.Sx];
         }
-        if (j > 0) ax = ax - wi * J.x[t - g.Sx];
-        if (j < g.b - 1) ax = ax - wi * J.x[t + g.Sx];
         const c128 out = J.v[t] - ax;
         J.y[t] = out;
         ((cplx<T>*)J.yt)[t] = cvt<T>(out);
@@ -326,13 +347,40 @@ void launch_sum(const double* part, int n, double* out, cudaStream_t s) {
 
 
 // --------------------------------------------------------------------------- rhs
+// Bilinear elements (q1, 2D): b = h^2 (M_y F M_x^T) + h (the edge masses applied to g), M the
+// 1D consistent masses over h (q1_mass): the load vector of the element integrals.
+__device__ c128 rhs_q1(const c128* __restrict__ f, const c128* __restrict__ g, int S, double h, int j, int i) {
+    c128 v = {0.0, 0.0};
+    for (int dj = -1; dj <= 1; ++dj) {
+        if (j + dj < 0 || j + dj >= S) continue;
+        for (int di = -1; di <= 1; ++di) {
+            if (i + di < 0 || i + di >= S) continue;
+            v = v + (h * h * q1_mass(j, dj, S) * q1_mass(i, di, S)) * f[(size_t)(j + dj) * S + (i + di)];
+        }
+    }
+    for (int d = -1; d <= 1; ++d) {
+        if (j + d >= 0 && j + d < S) {
+            if (i == 0) v = v + (h * q1_mass(j, d, S)) * g[0 * S + j + d];
+            if (i == S - 1) v = v + (h * q1_mass(j, d, S)) * g[1 * S + j + d];
+        }
+        if (i + d >= 0 && i + d < S) {
+            if (j == 0) v = v + (h * q1_mass(i, d, S)) * g[2 * S + i + d];
+            if (j == S - 1) v = v + (h * q1_mass(i, d, S)) * g[3 * S + i + d];
+        }
+    }
+    return v;
+}
 __global__ void k_rhs(const c128* __restrict__ f, const c128* __restrict__ g, c128* __restrict__ b,
-                      int dim, int S, double h) {
+                      int dim, int S, double h, int q1) {
     const int Sx = dim == 2 ? S : 1;
     const size_t total = (size_t)S * Sx;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t % Sx), j = (int)(t / Sx);
+        if (q1) {
+            b[t] = rhs_q1(f, g, S, h, j, i);
+            continue;
+        }
         const double wj = wrow(j, S), wi = wcol(i, Sx);
         c128 v = (h * h * wi * wj) * f[t];
         if (dim == 1) {
@@ -347,9 +395,9 @@ __global__ void k_rhs(const c128* __restrict__ f, const c128* __restrict__ g, c1
         b[t] = v;
     }
 }
-void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s) {
+void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s, int q1) {
     const size_t total = (size_t)S * (dim == 2 ? S : 1);
-    k_rhs<<<grid_for(total, 256), 256, 0, s>>>(f, g, b, dim, S, h);
+    k_rhs<<<grid_for(total, 256), 256, 0, s>>>(f, g, b, dim, S, h, q1);
     note_launch();
 }
 
@@ -375,15 +423,28 @@ void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, 
 // Boundary row (local row 0 of a band of b_s rows; by symmetry the same for the last
 // row) of A~_s: coefficient op_diag on the row itself, -1/2 to the x-neighbours on the
 // row (X halved by w_j = 1/2), -w_i to the inward row.
+// Bilinear elements: the boundary row couples three columns of the row itself and three of
+// the inward row, with q1_coef(0, 0, i, di) and q1_coef(0, 1, i, di) (the same for the last
+// row by symmetry).
 template <typename T>
 __global__ void k_robin_trace(const cplx<T>* __restrict__ uif, const cplx<T>* __restrict__ uin,
                               cplx<T>* __restrict__ Y, int b_s, int Sx, int nc, double kh,
-                              const double* khr_row) {
-    const OpGeom g{b_s, Sx, kh, khr_row};
+                              const double* khr_row, int q1) {
+    const OpGeom g{b_s, Sx, kh, khr_row, q1};
     const size_t total = (size_t)Sx * nc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / nc);
+        if (q1) {
+            c128 y = {0.0, 0.0};
+            for (int di = -1; di <= 1; ++di) {
+                if (i + di < 0 || i + di >= Sx) continue;
+                const size_t tn = (size_t)((long long)t + (long long)di * nc);
+                y = y + q1_coef(0, 0, i, di, g) * cvt<double>(uif[tn]) + q1_coef(0, 1, i, di, g) * cvt<double>(uin[tn]);
+            }
+            Y[t] = cvt<T>(y);
+            continue;
+        }
         const c128 d = op_diag(0, i, g);
         c128 y = d * cvt<double>(uif[t]);
         if (Sx > 1) {
@@ -396,21 +457,34 @@ __global__ void k_robin_trace(const cplx<T>* __restrict__ uif, const cplx<T>* __
 }
 template <typename T>
 void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, int b_s, int Sx, int nc,
-                        double kh, const double* khr_row, cudaStream_t s) {
+                        double kh, const double* khr_row, cudaStream_t s, int q1) {
     const size_t total = (size_t)Sx * nc;
-    k_robin_trace<T><<<grid_for(total, 256), 256, 0, s>>>(u_if, u_in, Y, b_s, Sx, nc, kh, khr_row);
+    k_robin_trace<T><<<grid_for(total, 256), 256, 0, s>>>(u_if, u_in, Y, b_s, Sx, nc, kh, khr_row, q1);
     note_launch();
 }
 
 template <typename T>
 __global__ void k_adjoint_place(const cplx<T>* __restrict__ Q, cplx<T>* __restrict__ vif,
                                 cplx<T>* __restrict__ vin, int b_s, int Sx, int nc, double kh,
-                                const double* khr_row) {
-    const OpGeom g{b_s, Sx, kh, khr_row};
+                                const double* khr_row, int q1) {
+    const OpGeom g{b_s, Sx, kh, khr_row, q1};
     const size_t total = (size_t)Sx * nc;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
          t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / nc);
+        if (q1) {
+            // the transposed trace: both coefficient rows are symmetric in (i, i + di)
+            c128 yi = {0.0, 0.0}, yn = {0.0, 0.0};
+            for (int di = -1; di <= 1; ++di) {
+                if (i + di < 0 || i + di >= Sx) continue;
+                const c128 q = conj(cvt<double>(Q[(size_t)((long long)t + (long long)di * nc)]));
+                yi = yi + q1_coef(0, 0, i, di, g) * q;
+                yn = yn + q1_coef(0, 1, i, di, g) * q;
+            }
+            vif[t] = cvt<T>(yi);
+            vin[t] = cvt<T>(yn);
+            continue;
+        }
         const c128 d = op_diag(0, i, g);
         const c128 q = conj(cvt<double>(Q[t]));
         c128 y = d * q;
@@ -424,9 +498,9 @@ __global__ void k_adjoint_place(const cplx<T>* __restrict__ Q, cplx<T>* __restri
 }
 template <typename T>
 void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_s, int Sx, int nc,
-                          double kh, const double* khr_row, cudaStream_t s) {
+                          double kh, const double* khr_row, cudaStream_t s, int q1) {
     const size_t total = (size_t)Sx * nc;
-    k_adjoint_place<T><<<grid_for(total, 256), 256, 0, s>>>(Q, v_if, v_in, b_s, Sx, nc, kh, khr_row);
+    k_adjoint_place<T><<<grid_for(total, 256), 256, 0, s>>>(Q, v_if, v_in, b_s, Sx, nc, kh, khr_row, q1);
     note_launch();
 }
 
@@ -576,9 +650,9 @@ HH_COPY(float, double)
 
 #define HH_PREC(T)                                                                                    \
     template void launch_robin_trace<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, int, int, int, double, const double*, \
-                                        cudaStream_t);                                                \
+                                        cudaStream_t, int);                                           \
     template void launch_adjoint_place<T>(const cplx<T>*, cplx<T>*, cplx<T>*, int, int, int, double, const double*,   \
-                                          cudaStream_t);                                              \
+                                          cudaStream_t, int);                                         \
     template void launch_sketch<T>(cplx<T>*, int, int, int, unsigned long long, cudaStream_t);
 
 HH_PREC(float)

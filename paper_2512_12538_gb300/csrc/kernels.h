@@ -60,8 +60,9 @@ void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
                           int* ctl, unsigned* ticket, double tol, cudaStream_t s, const int* need = nullptr,
                           const int* anchor = nullptr);
 
-// b = h^2 w_i w_j f + h (w_j gx + w_i gy) for the global problem.
-void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s);
+// b = h^2 w_i w_j f + h (w_j gx + w_i gy) for the global problem (q1: the bilinear
+// elements' load vector, h^2 M_y F M_x^T + h (edge masses) g).
+void launch_rhs(const c128* f, const c128* g, c128* b, int dim, int S, double h, cudaStream_t s, int q1 = 0);
 
 // dst[i] (+)= (TD) src[i], i < n
 template <typename TS, typename TD>
@@ -72,13 +73,13 @@ void launch_copy(const cplx<TS>* src, cplx<TD>* dst, size_t n, bool accumulate, 
 // boundary, u_in = the next row inward (both rows of the child's solution).
 template <typename T>
 void launch_robin_trace(const cplx<T>* u_if, const cplx<T>* u_in, cplx<T>* Y, int b_s, int Sx, int nc,
-                        double kh, const double* khr_row, cudaStream_t s);
+                        double kh, const double* khr_row, cudaStream_t s, int q1 = 0);
 
 // v_if/v_in = rows of A~_s B_s^T conj(Q) (the adjoint trace, conjugated for the
 // conj o solve o conj adjoint); other rows untouched.
 template <typename T>
 void launch_adjoint_place(const cplx<T>* Q, cplx<T>* v_if, cplx<T>* v_in, int b_s, int Sx, int nc,
-                          double kh, const double* khr_row, cudaStream_t s);
+                          double kh, const double* khr_row, cudaStream_t s, int q1 = 0);
 
 // Omega[x][j] (Sx x m) for child `node`: SplitMix64 + Box-Muller, re/im ~ N(0,1/2).
 template <typename T>
@@ -252,6 +253,8 @@ struct EigTask {
     const void* vn_emb;   // (tc_prepare_v layout; null where the transforms run on CUDA cores)
     const int* gate;      // one-launch sweep: may be null; while the word is nonzero the task's
                           // cluster returns at once, touching none of the task's buffers
+    void* sc;             // bilinear elements: [b] per-mode scale of the recursions' input
+                          // (null: the 5-point rows, scale 1)
 };
 
 // Layout of the transformed vectors Fh of a multi-vector sweep (b rows of J = Sx nrhs):
@@ -278,7 +281,7 @@ void launch_tc_transform(int which, const EigTask* d_tasks, int ntasks, int b_ma
                          cudaStream_t s, const int* gate = nullptr);
 template <typename T>
 void launch_eig_factor(const EigTask* d_tasks, int ntasks, int b_max, int Sx, double kh, int* err,
-                       cudaStream_t s);
+                       cudaStream_t s, int q1 = 0);
 template <typename T>
 void launch_eig_sweep(const EigTask* d_tasks, int ntasks, int b_max, int Sx, int nrhs, cudaStream_t s);
 // One right-hand side (nrhs = 1, F/W [b][Sx]): the three stages in one launch, one

@@ -45,7 +45,7 @@ def test_enum_constants_match_the_header(hh):
         assert getattr(_lib, name) == v, name
     macro = re.search(r"#define\s+HH_NOALLOC_MAX_ROWS\s+(\d+)", _header())
     assert macro and _lib.HH_NOALLOC_MAX_ROWS == int(macro.group(1))
-    for name in ("HH_FLAG_COARSE_FP32", "HH_FLAG_CUDA_CORE_SWEEPS", "HH_FLAG_TENSOR_CORE_SWEEPS"):
+    for name in ("HH_FLAG_COARSE_FP32", "HH_FLAG_CUDA_CORE_SWEEPS", "HH_FLAG_TENSOR_CORE_SWEEPS", "HH_FLAG_BILINEAR"):
         flag = re.search(r"#define\s+" + name + r"\s+(\d+)u", _header())
         assert flag and getattr(_lib, name) == int(flag.group(1)), name
 

@@ -50,7 +50,7 @@ def test_footprint_host_only_and_validation(hh):
     bad = [dict(overlap=3), dict(overlap=0), dict(levels=0), dict(n=2), dict(rank=0), dict(k=-1.0),
            dict(n=20, levels=4), dict(rank=40, oversample=0), dict(dim=3), dict(n_inner=0), dict(tol=0.0),
            dict(leaf_solver=7), dict(outer=3), dict(outer=1, restart=0), dict(outer=1, restart=65),
-           dict(n=1023, levels=2), dict(levels=7, n=4000), dict(flags=8), dict(flags=6), dict(flags=0x80000000)]
+           dict(n=1023, levels=2), dict(levels=7, n=4000), dict(flags=16), dict(flags=6), dict(flags=0x80000000)]
     for kw in bad:
         args = dict(dim=2, n=255, k=40.0, levels=2, overlap=2, rank=16, oversample=10)
         args.update(kw)
@@ -99,3 +99,22 @@ def test_layered_media_parameters(hh):
         assert ei.value.status == hh.HH_EINVAL
     with pytest.raises(ValueError):
         hh.make_params(2, 63, 64.0, 2, 2, 16, 10, leaf_solver="block", k_rows=kr[:-1])
+
+
+def test_bilinear_element_parameters(hh):
+    # host-side validation only: the bilinear elements (HH_FLAG_BILINEAR) take 2D problems on
+    # the eigenbasis leaves with one wavenumber; their per-mode scales add b per leaf
+    import numpy as np
+    q1 = hh.HH_FLAG_BILINEAR
+    base = hh.hh_footprint(hh.make_params(2, 255, 40.0, 2, 2, 16, 10))
+    assert hh.hh_footprint(hh.make_params(2, 255, 40.0, 2, 2, 16, 10, flags=q1)) >= base
+    assert hh.hh_footprint(hh.make_params(2, 255, 40.0, 2, 2, 16, 10, precision="mixed",
+                                          flags=q1 | hh.HH_FLAG_TENSOR_CORE_SWEEPS)) > 0
+    kr = np.full(65, 64.0)
+    for p in (hh.make_params(1, 255, 40.0, 1, 4, 1, 0, flags=q1),
+              hh.make_params(2, 255, 40.0, 2, 2, 16, 10, leaf_solver="block", flags=q1),
+              hh.make_params(2, 63, 64.0, 2, 2, 16, 10, k_rows=kr, flags=q1),
+              hh.make_params(2, 63, 64.0, 2, 2, 16, 10, leaf_solver="block", k_rows=kr, flags=q1)):
+        with pytest.raises(hh.HHError) as ei:
+            hh.hh_footprint(p)
+        assert ei.value.status == hh.HH_EINVAL
