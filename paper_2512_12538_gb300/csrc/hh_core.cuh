@@ -17,6 +17,12 @@ struct alignas(2 * sizeof(T)) cplx {
 using c64 = cplx<float>;
 using c128 = cplx<double>;
 
+// two consecutive complex values, for one wide shared-memory load
+template <typename T>
+struct alignas(2 * sizeof(cplx<T>)) cpair {
+    cplx<T> x, y;
+};
+
 template <typename T> HH_HD cplx<T> mk(T r, T i) { return cplx<T>{r, i}; }
 template <typename T> HH_HD cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
 template <typename T> HH_HD cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
@@ -144,6 +150,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
+// 8-byte form; valid = false fills the 8 bytes with zeros (source size 0, nothing read)
+__device__ __forceinline__ void cp_async8_zfill(void* smem, const void* gmem, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

@@ -604,7 +604,9 @@ struct Solver final : SolverBase {
         R[0] = RT;
         cur_in.assign(nn, nullptr);
         cur_in[0] = RT;
-        partial = a.take<c128>((size_t)MAX_PART_BLOCKS * 64 * 64);
+        // per-block partial sums of up to 64 x 64 outputs, plus the block of sums that
+        // launch_ip_reduce writes just past the partials
+        partial = a.take<c128>((size_t)(MAX_PART_BLOCKS + 1) * 64 * 64);
         npart = a.take<double>(2048);
         // [0] ||r||^2 (FP64 residual), [1] ||r||^2 (recursive residual), [2..4) ||b||^2,
         // [4..6) the device status words, [6..10) the device-tested loop's control words

@@ -206,10 +206,148 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
     return grid;
 }
 
+// The complex64 form for a node's basis (the set-up's multi-column projections), as dense
+// products: rows [ilo, ilo + ni) of A (the columns that can be nonzero on the points
+// [pa, pb)) against all q columns of B.  Register-tiled: a thread owns 4 x 4 outputs and a
+// share (KG groups) of each 32-point tile's points; per point it reads 4 values of A and 4
+// of B from shared memory for 16 complex multiply-adds.  The tiles are double-buffered
+// with cp.async (8-byte copies, zero-filled past the range).  The groups' sums are added in
+// shared memory, and the block writes its whole [p][q] partial (zeros outside the rows).
+static constexpr int RT_TP = 32;
+template <int KG>
+__global__ void __launch_bounds__(256) k_ip_colA_rt(const c64* __restrict__ A, size_t lda, const c64* __restrict__ B,
+                                                    int ldb, int p, int q, int ilo, int ni, size_t pa, size_t pb,
+                                                    c128* partial) {
+    extern __shared__ __align__(16) unsigned char rtsm[];
+    const int IT = (ni + 3) / 4, CT = (q + 3) / 4, nt = IT * CT;
+    const int nr = 4 * IT, qp = 4 * CT;          // padded tile rows and columns
+    c64* As = (c64*)rtsm;                        // [2][nr][RT_TP]
+    c64* Bs = As + 2 * nr * RT_TP;               // [2][RT_TP][qp]
+    const int tid = threadIdx.x;
+    const int o = tid % nt, kg = tid / nt;
+    const int it = o / CT, ct = o - it * CT;
+    // this block's points: whole tiles of the range
+    const size_t ntiles_all = (pb - pa + RT_TP - 1) / RT_TP;
+    const size_t t0b = ntiles_all * blockIdx.x / gridDim.x, t1b = ntiles_all * (blockIdx.x + 1) / gridDim.x;
+    // padding rows / columns stay zero
+    for (int e = tid; e < 2 * nr * RT_TP; e += blockDim.x) As[e] = {0.f, 0.f};
+    for (int e = tid; e < 2 * RT_TP * qp; e += blockDim.x) Bs[e] = {0.f, 0.f};
+    __syncthreads();
+    auto stage = [&](size_t tile, int buf) {
+        const size_t x0 = pa + tile * RT_TP;
+        c64* as = As + (size_t)buf * nr * RT_TP;
+        c64* bs = Bs + (size_t)buf * RT_TP * qp;
+        for (int e = tid; e < ni * RT_TP; e += blockDim.x) {
+            const int i = e / RT_TP, k = e - i * RT_TP;
+            const size_t x = x0 + k;
+            const bool ok = x < pb;
+            cp_async8_zfill(as + i * RT_TP + k, A + (size_t)(ilo + i) * lda + (ok ? x : pa), ok);
+        }
+        for (int e = tid; e < RT_TP * q; e += blockDim.x) {
+            const int k = e / q, c = e - k * q;
+            const size_t x = x0 + k;
+            const bool ok = x < pb;
+            cp_async8_zfill(bs + k * qp + c, B + (ok ? x : pa) * ldb + c, ok);
+        }
+        cp_async_commit();
+    };
+    c64 acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = {0.f, 0.f};
+    if (t0b < t1b) stage(t0b, 0);
+    for (size_t tile = t0b; tile < t1b; ++tile) {
+        const int buf = (int)((tile - t0b) & 1);
+        if (tile + 1 < t1b) {
+            stage(tile + 1, buf ^ 1);
+            cp_async_wait_group1();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        if (kg < KG) {
+            const c64* as = As + (size_t)buf * nr * RT_TP + (size_t)(4 * it) * RT_TP;
+            const c64* bs = Bs + (size_t)buf * RT_TP * qp + 4 * ct;
+            for (int k = kg; k < RT_TP; k += KG) {
+                c64 a[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = as[u * RT_TP + k];
+                const cpair<float> b01 = *(const cpair<float>*)(bs + k * qp);
+                const cpair<float> b23 = *(const cpair<float>*)(bs + k * qp + 2);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    cfma_cj(acc[u][0], a[u], b01.x);
+                    cfma_cj(acc[u][1], a[u], b01.y);
+                    cfma_cj(acc[u][2], a[u], b23.x);
+                    cfma_cj(acc[u][3], a[u], b23.y);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // the groups' sums (the tile buffers are free now), then the block's [p][q] partial
+    c64* red = As;                               // [KG][nt][16]
+    if (kg < KG)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) red[((size_t)kg * nt + o) * 16 + u * 4 + v] = acc[u][v];
+    __syncthreads();
+    c128* out = partial + (size_t)blockIdx.x * p * q;
+    for (int e = tid; e < p * q; e += blockDim.x) {
+        const int i = e / q, c = e - i * q;
+        c128 t = {0.0, 0.0};
+        const int ir = i - ilo;
+        if (ir >= 0 && ir < ni) {
+            const int oo = (ir >> 2) * CT + (c >> 2), uv = (ir & 3) * 4 + (c & 3);
+            for (int g = 0; g < KG; ++g) t = t + cvt<double>(red[((size_t)g * nt + oo) * 16 + uv]);
+        }
+        out[e] = t;
+    }
+}
+
+static int ip_colA_rt_launch(const c64* A, size_t lda, const c64* B, int ldb, int p, int q, int ilo, int ni,
+                             size_t pa, size_t pb, c128* partial, int nblk, cudaStream_t s) {
+    const int IT = (ni + 3) / 4, CT = (q + 3) / 4, nt = IT * CT;
+    const int kg = std::max(1, std::min(4, 256 / nt));
+    const size_t sm = sizeof(c64) * std::max<size_t>((size_t)2 * (4 * IT * RT_TP + RT_TP * 4 * CT),
+                                                     (size_t)kg * nt * 16);
+    const int threads = nt * kg;
+    switch (kg) {
+        case 1: k_ip_colA_rt<1><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
+        case 2: k_ip_colA_rt<2><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
+        case 3: k_ip_colA_rt<3><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
+        default: k_ip_colA_rt<4><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
+    }
+    note_launch();
+    return nblk;
+}
+
 // partial[blk][i][j] = sum conj(A[i * N + n]) B[n * ldb + j] with A column-major (p x N).
 template <typename TA, typename TB, typename ACC>
 int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t N, int p, int q, c128* partial,
                            int max_blocks, cudaStream_t s, long long split_pt) {
+    if constexpr (sizeof(TA) == 4 && sizeof(TB) == 4 && sizeof(ACC) == 4) {
+        // complex64, at most 64 columns of B (the 4 x 4 tiles of a block fit 256 threads)
+        const int half = p / 2;
+        if (q <= 64 && p <= 64 && N > 0) {
+            const size_t sp = split_pt < 0 ? 0 : std::min<size_t>((size_t)split_pt, N);
+            if (split_pt < 0 || half == 0) {
+                const int nb = std::max(1, std::min(max_blocks, (int)((N + 255) / 256)));
+                return ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, 0, p, 0, N, partial, nb, s);
+            }
+            // the two halves of the basis on their own points, blocks in proportion
+            int nb1 = sp == 0 ? 0 : std::max(1, (int)std::lround((double)max_blocks * sp / N));
+            int nb2 = sp == N ? 0 : std::max(1, max_blocks - nb1);
+            if (nb1 + nb2 > max_blocks) nb1 = max_blocks - nb2;
+            if (nb1 > 0) ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, 0, half, 0, sp, partial, nb1, s);
+            if (nb2 > 0)
+                ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, half, p - half, sp, N,
+                                  partial + (size_t)nb1 * p * q, nb2, s);
+            return nb1 + nb2;
+        }
+    }
     int grid = (int)((N + 255) / 256);
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;

@@ -844,11 +844,6 @@ template <> __device__ __forceinline__ void cp_async_elem<double>(c128* smem, co
 }
 
 template <typename T>
-struct alignas(2 * sizeof(cplx<T>)) cpair {
-    cplx<T> x, y;
-};
-
-template <typename T>
 __global__ void __launch_bounds__(FS_THREADS) k_eig_sweep_fused(const EigTask* __restrict__ tasks,
                                                                  const int* __restrict__ gate) {
     // a set stop word (written by an earlier launch, so the same for every CTA) skips
