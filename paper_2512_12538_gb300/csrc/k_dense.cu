@@ -6,6 +6,8 @@
 //  * the small SVD: Hermitian eigenproblem of Z^H Z in FP64 (tridiagonal reduction,
 //    bisection, inverse iteration) and V = Z U Sigma^{-1};
 //  * Gauss-Jordan inversion with partial pivoting of A_c (FP64).
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace hh {
@@ -773,6 +775,90 @@ __global__ void __launch_bounds__(512) k_qr(cplx<T>* const* Yp, int Sx, int m, i
     if (staged)
         for (size_t e = threadIdx.x; e < tot; e += blockDim.x) Yg[e] = Y[(e / m) * ld + e % m];
 }
+// The same orthogonalisation for a block too large for one CTA's shared memory: a cluster
+// of QR_CL CTAs per block, each holding a slice of the rows in shared memory.  Each dot
+// product and norm is a sum of the CTAs' partial sums, added in rank order from
+// distributed shared memory, so every CTA takes the same coefficients; the partial-sum
+// arrays alternate between two buffers, and the cluster barrier after each write keeps a
+// CTA from overwriting a buffer another is still reading.
+static constexpr int QR_CL = 8;
+template <typename T>
+__global__ void __launch_bounds__(512) k_qr_cluster(cplx<T>* const* Yp, int Sx, int m) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    cplx<T>* Yg = Yp[blockIdx.x / QR_CL];
+    extern __shared__ __align__(16) unsigned char qcs[];
+    const int ld = m + 1;                       // padded rows (bank spread)
+    const int rows = (Sx + QR_CL - 1) / QR_CL;
+    const int r0 = min(Sx, rank * rows), r1 = min(Sx, r0 + rows), nr = r1 - r0;
+    cplx<T>* Y = (cplx<T>*)qcs;                 // [rows][ld]
+    __shared__ cplx<T> pd[2][128];              // partial dot products (two buffers)
+    __shared__ T pn[2];                         // partial squared norms
+    __shared__ cplx<T> dots[128];
+    __shared__ T red[32];
+    __shared__ T s_inv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
+        const int x = e / m, c = e - x * m;
+        Y[x * ld + c] = Yg[(size_t)(r0 + x) * m + c];
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int j = 0; j < m; ++j) {
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
+            for (int k = warp; k < j; k += nw) {
+                cplx<T> a = {0, 0};
+                for (int x = lane; x < nr; x += 32) cfma_cj(a, Y[x * ld + k], Y[x * ld + j]);
+                a = warp_sum(a);
+                if (lane == 0) pd[buf][k] = a;
+            }
+            cluster.sync();
+            for (int k = threadIdx.x; k < j; k += blockDim.x) {
+                cplx<T> a = {0, 0};
+                for (int r = 0; r < QR_CL; ++r) a = a + cluster.map_shared_rank(&pd[buf][0], r)[k];
+                dots[k] = a;
+            }
+            buf ^= 1;
+            __syncthreads();
+            for (int x = threadIdx.x; x < nr; x += blockDim.x) {
+                cplx<T> v = Y[x * ld + j];
+                for (int k = 0; k < j; ++k) v = v - Y[x * ld + k] * dots[k];
+                Y[x * ld + j] = v;
+            }
+            __syncthreads();
+        }
+        T a2 = 0;
+        for (int x = threadIdx.x; x < nr; x += blockDim.x) a2 += abs2(Y[x * ld + j]);
+        a2 = warp_sum(a2);
+        if (lane == 0) red[warp] = a2;
+        __syncthreads();
+        if (warp == 0) {
+            T v = lane < nw ? red[lane] : (T)0;
+            v = warp_sum(v);
+            if (lane == 0) pn[buf] = v;
+        }
+        cluster.sync();
+        if (threadIdx.x == 0) {
+            T v = 0;
+            for (int r = 0; r < QR_CL; ++r) v += *cluster.map_shared_rank(&pn[buf], r);
+            const T nrm = sqrt(v);
+            s_inv = nrm > (T)0 ? (T)1 / nrm : (T)0;
+        }
+        buf ^= 1;
+        __syncthreads();
+        const T inv = s_inv;
+        for (int x = threadIdx.x; x < nr; x += blockDim.x) Y[x * ld + j] = inv * Y[x * ld + j];
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
+        const int x = e / m, c = e - x * m;
+        Yg[(size_t)(r0 + x) * m + c] = Y[x * ld + c];
+    }
+    // no CTA leaves while another may still read its partial sums
+    cluster.sync();
+}
+
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s) {
     cudaMemcpyAsync(dev_ptr_scratch, Y, sizeof(cplx<T>*) * nq, cudaMemcpyHostToDevice, s);
@@ -780,6 +866,26 @@ void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scrat
     smem_limit_once(attr, k_qr<T>, 200 * 1024);
     const size_t bytes = sizeof(cplx<T>) * (size_t)Sx * (m + 1);   // padded rows
     const int staged = bytes <= (size_t)(200 * 1024) - 2048;
+    const size_t cbytes = sizeof(cplx<T>) * (size_t)((Sx + QR_CL - 1) / QR_CL) * (m + 1);
+    if (!staged && m <= 128 && cbytes <= (size_t)(200 * 1024) - 4096) {
+        static std::atomic<unsigned long long> attr_c{0};
+        smem_limit_once(attr_c, k_qr_cluster<T>, 200 * 1024);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        cfg.gridDim = dim3(nq * QR_CL);
+        cfg.blockDim = dim3(512);
+        cfg.dynamicSmemBytes = cbytes;
+        cfg.stream = s;
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = QR_CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_qr_cluster<T>, dev_ptr_scratch, Sx, m);
+        note_launch();
+        return;
+    }
     k_qr<T><<<nq, 512, staged ? bytes : 0, s>>>(dev_ptr_scratch, Sx, m, staged);
     note_launch();
 }
