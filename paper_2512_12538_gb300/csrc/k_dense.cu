@@ -1274,11 +1274,10 @@ void launch_form_v(const cplx<T>* Z, const c128* U, const double* lam, cplx<T>* 
 // ------------------------------------------------------- Gauss-Jordan (FP64)
 // In-place inverse with partial pivoting: row interchanges during elimination, the
 // inverse's columns unscrambled in reverse order at the end.
-// One block per matrix, in arithmetic R: FP64 for the FP64 form; FP32 for the complex64
-// form, whose one-column corrections apply the inverse in FP32 anyway (the outer FP64
-// refinement absorbs the difference; FP64 runs at 1/64 of the FP32 rate here).  The
-// pivot's reciprocal is formed once per step (thread 0) and shared.  The inverse is
-// written back to A in complex128 and, where AT is given, in complex64.
+// One block per matrix, in arithmetic R: FP64, or FP32 for the opt-in FP32 coarse variant
+// of the complex64 form.  The pivot's reciprocal is formed once per step (thread 0) and
+// shared.  The inverse is written back to A in complex128 and, where AT is given, in
+// complex64.  Matrices of 16 to 64 rows take the cluster form below.
 template <typename R>
 __global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
     using C = cplx<R>;
@@ -1358,8 +1357,134 @@ __global__ void __launch_bounds__(256) k_gj_inverse(GjBatch bt) {
         if (AT) AT[e] = cvt<float>(v);
     }
 }
+// The same elimination on a cluster of GJ_CL CTAs per matrix, each holding a slice of the
+// rows: per step every CTA proposes its best pivot row (cluster barrier), all take the
+// same pivot from the proposals (largest magnitude, then lowest row), read the pivot row
+// (and the owner of the pivot row, the old row k) from distributed shared memory, and
+// after a second barrier update their own rows.  The FP64 updates of a step spread over
+// GJ_CL SMs (FP64 issues at 2 multiply-adds per SM and clock on this GPU).
+static constexpr int GJ_CL = 8;
+template <typename R>
+__global__ void __launch_bounds__(256) k_gj_cluster(GjBatch bt) {
+    namespace cg = cooperative_groups;
+    using C = cplx<R>;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int mat = blockIdx.x / GJ_CL;
+    c128* A = bt.A[mat];
+    const int n = bt.n;
+    const int rpc = (n + GJ_CL - 1) / GJ_CL;
+    const int r0 = min(n, rank * rpc), r1 = min(n, r0 + rpc), nr = r1 - r0;
+    extern __shared__ __align__(16) unsigned char gjc[];
+    C* M = (C*)gjc;                 // [rpc][n] own rows
+    C* row = M + rpc * n;           // [n] the normalised pivot row
+    C* tmp = row + n;               // [n] the old row k (the pivot row's owner)
+    C* colk = tmp + n;              // [rpc] column k of the own rows, before the step
+    int* perm = (int*)(colk + rpc); // [n]
+    int* pos = perm + n;            // [n]
+    __shared__ R s_best;
+    __shared__ int s_idx, s_p;
+    __shared__ C s_ip, s_akk;
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) M[e] = cvt<R>(A[(size_t)r0 * n + e]);
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            R best = -1;
+            int bi = n;
+            for (int r = max(k, r0); r < r1; ++r) {
+                const R a = abs2(M[(r - r0) * n + k]);
+                if (a > best) { best = a; bi = r; }
+            }
+            s_best = best;
+            s_idx = bi;
+        }
+        cluster.sync();
+        if (threadIdx.x == 0) {
+            R best = -1;
+            int bi = n;
+            for (int q = 0; q < GJ_CL; ++q) {
+                const R ob = *cluster.map_shared_rank(&s_best, q);
+                const int oi = *cluster.map_shared_rank(&s_idx, q);
+                if (oi < n && (ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+            }
+            s_p = bi < n ? bi : k;
+            perm[k] = s_p;
+            const int ok_ = (bi < n) && (best > 0) && isfinite(best);
+            if (!ok_ && rank == 0) atomicExch(bt.err, DEV_BREAKDOWN);
+            const int ob = s_p / rpc, ok2 = k / rpc;
+            const C pk = ok_ ? cluster.map_shared_rank(M, ob)[(s_p - ob * rpc) * n + k] : C{1, 0};
+            s_ip = cinv(pk);
+            s_akk = cluster.map_shared_rank(M, ok2)[(k - ok2 * rpc) * n + k];
+        }
+        __syncthreads();
+        const int p = s_p;
+        const C ip = s_ip;
+        {
+            const int ob = p / rpc, okk = k / rpc;
+            const C* prow = cluster.map_shared_rank(M, ob) + (size_t)(p - ob * rpc) * n;
+            for (int c = threadIdx.x; c < n; c += blockDim.x) row[c] = prow[c] * ip;
+            if (p != k && p >= r0 && p < r1) {
+                const C* krow = cluster.map_shared_rank(M, okk) + (size_t)(k - okk * rpc) * n;
+                for (int c = threadIdx.x; c < n; c += blockDim.x) tmp[c] = krow[c];
+            }
+            for (int rl = threadIdx.x; rl < nr; rl += blockDim.x) colk[rl] = M[rl * n + k];
+        }
+        cluster.sync();   // every read of another CTA's rows is done before the updates
+        const C akk = s_akk;
+        for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+            const int rl = e / n, c = e - rl * n, r = r0 + rl;
+            C v;
+            if (r == k) {
+                v = (c == k) ? ip : row[c];
+            } else {
+                const C f = (r == p) ? akk : colk[rl];
+                const C cur = (r == p) ? tmp[c] : M[e];
+                v = (c == k) ? -(f * ip) : cur - f * row[c];
+            }
+            M[e] = v;
+        }
+        __syncthreads();
+    }
+    // unscramble columns: position c holds original column pos[c]
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < n; ++c) pos[c] = c;
+        for (int k = n - 1; k >= 0; --k) {
+            const int t = pos[k]; pos[k] = pos[perm[k]]; pos[perm[k]] = t;
+        }
+    }
+    __syncthreads();
+    c64* AT = (c64*)bt.AT[mat];
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+        const int rl = e / n, c = e - rl * n;
+        const C v = M[rl * n + pos[c]];
+        A[(size_t)(r0 + rl) * n + c] = cvt<double>(v);
+        if (AT) AT[(size_t)(r0 + rl) * n + c] = cvt<float>(v);
+    }
+}
+
 void launch_gj_inverse(const GjBatch& bt, int count, bool fp32, cudaStream_t s) {
     if (count < 1) return;
+    if (bt.n >= 16 && bt.n <= 64) {
+        const int n = bt.n, rpc = (n + GJ_CL - 1) / GJ_CL;
+        const size_t es = fp32 ? sizeof(c64) : sizeof(c128);
+        const size_t sm = es * ((size_t)rpc * n + 2 * n + rpc) + sizeof(int) * 2 * n;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        cfg.gridDim = dim3(count * GJ_CL);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = GJ_CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (fp32) cudaLaunchKernelEx(&cfg, k_gj_cluster<float>, bt);
+        else cudaLaunchKernelEx(&cfg, k_gj_cluster<double>, bt);
+        note_launch();
+        return;
+    }
     const int n = bt.n;
     const size_t es = fp32 ? sizeof(c64) : sizeof(c128);
     const size_t sm = es * (n * n + 2 * n) + sizeof(int) * 2 * n;
