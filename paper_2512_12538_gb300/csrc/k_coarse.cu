@@ -142,7 +142,9 @@ __device__ __forceinline__ void coarse_recur_tail(const CoarseRecur& R, float rr
 //            (in place: out = w_in, acc_out; straight into the parent's solution: the
 //            owned rows, add_w), and the added value alone into dout when given.  The
 //            barrier separates every read of w_in from the writes.
-template <typename TC, typename TV, typename TW, typename TO>
+// Q1: the jobs' operators are the bilinear elements' 9-point rows (a separate instantiation:
+// the 5-point kernel keeps its registers).
+template <typename TC, typename TV, typename TW, typename TO, bool Q1>
 __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(CoarseBatch bt, int p, cplx<TC>* partial, unsigned* bar,
                                                       int* err) {
     // a set stop word (written by an earlier launch: the same for every block) skips the
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256, sizeof(TC) == 4 ? 2 : 1) k_coarse_batch(C
     // r = v - A~ w_in at one point (w_in null: r = v), in the basis precision
     auto resid_at = [&](unsigned pt) -> CA {
         cplx<R> rv = cvt<R>(v[pt]);
-        if (w_in && g.q1) {
+        if (Q1 && w_in) {
             const int jr = (int)(pt / (unsigned)g.Sx), i = (int)(pt - (unsigned)jr * g.Sx);
             rv = rv - q1_row<R>(jr, i, g, [&](int dj, int di) {
                      return cvt<R>(w_in[(size_t)((long long)pt + (long long)dj * g.Sx + di)]);
@@ -383,7 +385,7 @@ int coarse_batch_max_grid() {
     if (!g) {
         int sms = 0, nb = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_batch<TC, TV, TW, TO>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_batch<TC, TV, TW, TO, false>, 256, 0);
         g = std::max(1, std::min(nb, 2) * sms);
         mg[dev & 63].store(g, std::memory_order_relaxed);
     }
@@ -437,7 +439,8 @@ void launch_coarse_batch(CoarseBatch bt, int p, void* partial, unsigned* bar, in
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_coarse_batch<TC, TV, TW, TO>, bt, p, (cplx<TC>*)partial, bar, err);
+    if (bt.job[0].g.q1) cudaLaunchKernelEx(&cfg, k_coarse_batch<TC, TV, TW, TO, true>, bt, p, (cplx<TC>*)partial, bar, err);
+    else cudaLaunchKernelEx(&cfg, k_coarse_batch<TC, TV, TW, TO, false>, bt, p, (cplx<TC>*)partial, bar, err);
     note_launch();
 }
 

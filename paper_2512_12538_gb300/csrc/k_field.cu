@@ -19,7 +19,7 @@ static int grid_for(size_t n, int threads, int cap = 152 * 16) {
 // One thread per (point, column); grid-stride.  Compute type = TY (the coefficients too,
 // so that a complex64 apply stays off the FP64 pipe).  I: the index type, 32-bit when
 // the launch's element count fits (the divisions by the sizes are then far shorter).
-template <typename TX, typename TV, typename TY, typename I>
+template <typename TX, typename TV, typename TY, typename I, bool Q1>
 __global__ void k_apply(const cplx<TX>* __restrict__ x, const cplx<TV>* __restrict__ v,
                         cplx<TY>* __restrict__ y, OpGeom g, int nc, TY sgn, double* part) {
     const I total = (I)g.b * (I)g.Sx * (I)nc;
@@ -31,7 +31,7 @@ __global__ void k_apply(const cplx<TX>* __restrict__ x, const cplx<TV>* __restri
         const int i = (int)(pt - jr * (I)g.Sx);
         const int j = (int)jr;
         cplx<TY> ax;
-        if (g.q1) {
+        if constexpr (Q1) {
             ax = q1_row<TY>(j, i, g, [&](int dj, int di) {
                 return cvt<TY>(x[(size_t)((long long)t + (long long)dj * (long long)ldr + (long long)di * nc)]);
             });
@@ -72,10 +72,16 @@ void launch_apply(const cplx<TX>* x, const cplx<TV>* v, cplx<TY>* y, OpGeom g, i
     const size_t total = (size_t)g.b * g.Sx * nc;
     const int th = 256;
     const int grid = grid_for(total, th, 152 * 8);
-    if (total + (size_t)grid * th < (1ull << 32))
-        k_apply<TX, TV, TY, unsigned><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
-    else
-        k_apply<TX, TV, TY, size_t><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    // the bilinear elements' 9-point rows are a separate instantiation (their registers
+    // would lower the 5-point kernel's occupancy)
+    const bool small = total + (size_t)grid * th < (1ull << 32);
+    if (g.q1) {
+        if (small) k_apply<TX, TV, TY, unsigned, true><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+        else k_apply<TX, TV, TY, size_t, true><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    } else {
+        if (small) k_apply<TX, TV, TY, unsigned, false><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+        else k_apply<TX, TV, TY, size_t, false><<<grid, th, 0, s>>>(x, v, y, g, nc, (TY)sgn, part);
+    }
     note_launch();
     if (nblk_out) *nblk_out = grid;
 }
@@ -94,7 +100,7 @@ struct ResidStop {
     const int* need;     // may be null: else the launch does nothing while *need is zero
     const int* anchor;   // may be null: else yt is written only while *anchor is nonzero
 };
-template <typename T>
+template <typename T, bool Q1>
 __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restrict__ v, c128* __restrict__ y,
                                 cplx<T>* __restrict__ yt, OpGeom g, double* part, const int* gate, ResidStop stop) {
     if (gate && *gate) return;
@@ -115,7 +121,7 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
     const unsigned step_r = (unsigned)(stride % Sx), step_q = (unsigned)(stride / Sx);
     for (; t < total; t += stride) {
         c128 out;
-        if (g.q1) {
+        if constexpr (Q1) {
             out = v[t] - q1_row<double>((int)j, (int)i, g, [&](int dj, int di) {
                       return x[(size_t)((long long)t + (long long)dj * Sx + di)];
                   });
@@ -193,8 +199,9 @@ void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
                           cudaStream_t s, const int* gate) {
     const size_t total = (size_t)g.b * g.Sx;
     const int grid = grid_for(total, 256, 152 * 8);
-    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, ResidStop{nullptr, nullptr, nullptr, 0.0,
-                                                                                nullptr, nullptr});
+    const ResidStop none{nullptr, nullptr, nullptr, 0.0, nullptr, nullptr};
+    if (g.q1) k_residual_cast<T, true><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, none);
+    else k_residual_cast<T, false><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, none);
     note_launch();
     if (nblk_out) *nblk_out = grid;
 }
@@ -204,7 +211,9 @@ void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
                           const int* anchor) {
     const size_t total = (size_t)g.b * g.Sx;
     const int grid = grid_for(total, 256, 152 * 8);
-    k_residual_cast<T><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, ResidStop{nrm, ctl, ticket, tol, need, anchor});
+    const ResidStop st{nrm, ctl, ticket, tol, need, anchor};
+    if (g.q1) k_residual_cast<T, true><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, st);
+    else k_residual_cast<T, false><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, st);
     note_launch();
 }
 template void launch_residual_stop<float>(const c128*, const c128*, c128*, c64*, OpGeom, double*, double*, int*,
