@@ -641,17 +641,30 @@ __global__ void __launch_bounds__(256) k_eig_recur(const EigTask* __restrict__ t
     const C* xi = (const C*)tk.xi + (size_t)m * Sx;
     C* fh = (C*)tk.Fh + (size_t)line * Sx;     // line = m * nrhs + c
     const C sc = tk.sc ? ((const C*)tk.sc)[m] : C{1, 0};   // the mode's input scale (q1)
-    for (int i0 = lane; i0 < Sx; i0 += 32 * 8) {
-        C ta[8], tf[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + 32 * u;
-            if (i < Sx) { ta[u] = xi[i]; tf[u] = tk.sc ? sc * fh[i] : fh[i]; }
+    if constexpr (sizeof(C) == 8) {
+        // complex64: the whole line in flight at once (asynchronous 8-byte copies)
+        for (int i = lane; i < Sx; i += 32) {
+            cp_async8_zfill(as + i, xi + i, true);
+            cp_async8_zfill(fs + i, fh + i, true);
         }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        if (tk.sc)
+            for (int i = lane; i < Sx; i += 32) fs[i] = sc * fs[i];
+    } else {
+        for (int i0 = lane; i0 < Sx; i0 += 32 * 8) {
+            C ta[8], tf[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + 32 * u;
-            if (i < Sx) { as[i] = ta[u]; fs[i] = tf[u]; }
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + 32 * u;
+                if (i < Sx) { ta[u] = xi[i]; tf[u] = tk.sc ? sc * fh[i] : fh[i]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + 32 * u;
+                if (i < Sx) { as[i] = ta[u]; fs[i] = tf[u]; }
+            }
         }
     }
     __syncwarp();

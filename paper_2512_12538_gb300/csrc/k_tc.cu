@@ -252,7 +252,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
                 pre[u][i] = c64{v.x, v.y};
             }
     };
-    if (blockIdx.x < ntiles) load_chunk(blockIdx.x, 0);
+    // thread 0: the bulk copy of chunk (t, q)'s B operand into stage s
+    auto issue_b = [&](int t, int q, int s) {
+        const EigTask& tq = tasks[t / tiles_per_task];
+        const unsigned char* src = (const unsigned char*)(which == 0 ? tq.vt_emb : tq.vn_emb);
+        mbar_arrive_expect_tx(&full[s], g.b_bytes);
+        bulk_g2s(tsm + s * TC_STAGE_BYTES + TC_A_BYTES, src + (size_t)q * g.b_bytes, g.b_bytes, &full[s]);
+        copy_pending[s] = true;
+    };
+    if (blockIdx.x < ntiles) {
+        load_chunk(blockIdx.x, 0);
+        if (tid == 0) issue_b(blockIdx.x, 0, 0);
+    }
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const EigTask tk = tasks[tile / tiles_per_task];
         const int p0 = (tile % tiles_per_task) * TC_COLS;
@@ -260,23 +271,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         c64* outp = (c64*)(which == 0 ? tk.Fh : tk.W);
         // x = V x^ keeps rows [w0, w1) (all rows, or the owned rows written into the parent)
         const int rlo = which == 0 ? 0 : tk.w0, rhi = which == 0 ? b : tk.w1;
-        const unsigned char* bsrc = (const unsigned char*)(which == 0 ? tk.vt_emb : tk.vn_emb);
-
         for (int q = 0; q < g.nq; ++q, ++chunk) {
             const int s = chunk & 1;
             unsigned char* As = tsm + s * TC_STAGE_BYTES;
             unsigned char* Bs = As + TC_A_BYTES;
-            if (tid == 0) {
-                // the stage's previous MMAs must have finished reading it
-                if (use[s] > 0 && !tc_wait(&done[s], (use[s] - 1) & 1, limit, err)) *abort_flag = 1;
-                else {
-                    mbar_arrive_expect_tx(&full[s], g.b_bytes);
-                    bulk_g2s(Bs, bsrc + (size_t)q * g.b_bytes, g.b_bytes, &full[s]);
-                    copy_pending[s] = true;
-                }
-            }
-            __syncthreads();
-            if (*abort_flag) { ok = false; break; }
+            // This chunk's B operand was requested one chunk ahead (or before the loop),
+            // after this stage's MMAs of two chunks ago had finished: its A tile may
+            // overwrite the stage now.
             // A tile chunk from the registers: rows 2j + c, split and transposed
 #pragma unroll
             for (int u = 0; u < TC_KC / 8; ++u) {
@@ -322,6 +323,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
                     }
                     mma_commit(&done[s]);
                     ++use[s];
+                    // the next chunk's B operand into the other stage, once that stage's
+                    // MMAs (the previous chunk's) have finished reading it: the copy runs
+                    // while the next chunk's A tile is staged
+                    int nt = tile, nq = q + 1;
+                    if (nq == g.nq) {
+                        nt = tile + (int)gridDim.x;
+                        nq = 0;
+                    }
+                    if (nt < ntiles) {
+                        const int s2 = s ^ 1;
+                        if (use[s2] > 0 && !tc_wait(&done[s2], (use[s2] - 1) & 1, limit, err)) *abort_flag = 1;
+                        else issue_b(nt, nq, s2);
+                    }
                 } else {
                     *abort_flag = 1;   // the bulk copy may still land: drained below
                 }
