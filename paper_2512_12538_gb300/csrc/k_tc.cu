@@ -40,7 +40,8 @@ namespace hh {
 
 namespace {
 
-constexpr int TC_THREADS = 128;          // 4 warps: the 128 lanes of tensor memory
+constexpr int TC_THREADS = 256;          // 8 warps: two per 32-lane quarter of tensor memory
+constexpr int TC_KQ_T = TC_THREADS / 64;  // K quads of a chunk a thread does not stage between its own
 constexpr int TC_COLS = 64;              // complex columns per tile (M = 128 real rows)
 constexpr int TC_KC = 32;                // K per pipeline chunk (4 MMAs of K = 8)
 constexpr int TC_NB_MAX = 144;           // N per accumulator (b <= 136 rounded up to 16)
@@ -232,21 +233,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
     // the same path and the block barriers stay matched.
     //
     // Each thread stages column j = tid % 64 of the tile and the K quads kq = tid / 64,
-    // tid / 64 + 2, ...: 16 complex values per chunk, loaded into registers one chunk
+    // tid / 64 + TC_KQ_T, ...: 8 complex values per chunk, loaded into registers one chunk
     // ahead (the loads of chunk q + 1, or of the next tile's first chunk, are in flight
     // while chunk q's MMAs are issued and run).
     const int jcol = tid & 63, kq0 = tid >> 6;
-    c64 pre[TC_KC / 8][4];
+    constexpr int NU = TC_KC / 4 / TC_KQ_T;   // K quads a thread stages per chunk
+    c64 pre[NU][4];
     auto load_chunk = [&](int t, int q) {
         const EigTask& tq = tasks[t / tiles_per_task];
         const int p = (t % tiles_per_task) * TC_COLS + jcol;
         const c64* src = (const c64*)(which == 0 ? tq.F : tq.Fh);
         const int bb = tq.b;
 #pragma unroll
-        for (int u = 0; u < TC_KC / 8; ++u)
+        for (int u = 0; u < NU; ++u)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int k = q * TC_KC + (kq0 + 2 * u) * 4 + i;
+                const int k = q * TC_KC + (kq0 + TC_KQ_T * u) * 4 + i;
                 float2 v = make_float2(0.f, 0.f);
                 if (p < J && k < bb) v = __ldg((const float2*)(src + (size_t)k * J + p));
                 pre[u][i] = c64{v.x, v.y};
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
             // overwrite the stage now.
             // A tile chunk from the registers: rows 2j + c, split and transposed
 #pragma unroll
-            for (int u = 0; u < TC_KC / 8; ++u) {
+            for (int u = 0; u < NU; ++u) {
                 uint4 hr, lr, hm, lm;
                 tf32_split(pre[u][0].re, hr.x, lr.x);
                 tf32_split(pre[u][1].re, hr.y, lr.y);
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
                 tf32_split(pre[u][1].im, hm.y, lm.y);
                 tf32_split(pre[u][2].im, hm.z, lm.z);
                 tf32_split(pre[u][3].im, hm.w, lm.w);
-                const int kq = kq0 + 2 * u;
+                const int kq = kq0 + TC_KQ_T * u;
                 const uint32_t o_re = kmaj_off(2 * jcol, kq * 4), o_im = kmaj_off(2 * jcol + 1, kq * 4);
                 *(uint4*)(As + o_re) = hr;
                 *(uint4*)(As + o_im) = hm;
@@ -353,7 +355,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         __syncthreads();
         if (*abort_flag) { ok = false; break; }
         tc_fence_after();
-        const int jl = warp * 16 + (lane >> 1);      // complex column of this lane pair
+        // warps w and w + 4 share the tensor-memory lanes 32 (w % 4) .. + 31 and take
+        // alternate 16-column groups of the accumulators
+        const int wq = warp & 3, wh = warp >> 2;
+        const int jl = wq * 16 + (lane >> 1);        // complex column of this lane pair
         const bool even = (lane & 1) == 0;
         const int p = p0 + jl;
         size_t col = 0;
@@ -362,8 +367,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         if (p < J)
             col = which == 0 ? fh_col((size_t)p, Sx, nrhs)
                              : (eig_line_major(nrhs) ? (size_t)(p % Sx) * nrhs + p / Sx : (size_t)p);
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int m0 = 0; m0 < g.nb; m0 += 16) {
+        const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+        for (int m0 = 16 * wh; m0 < g.nb; m0 += 32) {
             float d0[16], d1[16];
             tmem_ld16(lane_base + (uint32_t)m0, d0);
             tmem_ld16(lane_base + (uint32_t)(TC_D1_COL + m0), d1);
