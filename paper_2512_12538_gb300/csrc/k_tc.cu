@@ -40,7 +40,7 @@ namespace hh {
 
 namespace {
 
-constexpr int TC_THREADS = 256;          // 8 warps: two per 32-lane quarter of tensor memory
+constexpr int TC_THREADS = 512;          // 16 warps: four per 32-lane quarter of tensor memory
 constexpr int TC_KQ_T = TC_THREADS / 64;  // K quads of a chunk a thread does not stage between its own
 constexpr int TC_COLS = 64;              // complex columns per tile (M = 128 real rows)
 constexpr int TC_KC = 32;                // K per pipeline chunk (4 MMAs of K = 8)
@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         __syncthreads();
         if (*abort_flag) { ok = false; break; }
         tc_fence_after();
-        // warps w and w + 4 share the tensor-memory lanes 32 (w % 4) .. + 31 and take
-        // alternate 16-column groups of the accumulators
+        // the warps w, w + 4, ... share the tensor-memory lanes 32 (w % 4) .. + 31 and take
+        // interleaved 16-column groups of the accumulators
         const int wq = warp & 3, wh = warp >> 2;
         const int jl = wq * 16 + (lane >> 1);        // complex column of this lane pair
         const bool even = (lane & 1) == 0;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
             col = which == 0 ? fh_col((size_t)p, Sx, nrhs)
                              : (eig_line_major(nrhs) ? (size_t)(p % Sx) * nrhs + p / Sx : (size_t)p);
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
-        for (int m0 = 16 * wh; m0 < g.nb; m0 += 32) {
+        for (int m0 = 16 * wh; m0 < g.nb; m0 += 16 * (TC_THREADS / 128)) {
             float d0[16], d1[16];
             tmem_ld16(lane_base + (uint32_t)m0, d0);
             tmem_ld16(lane_base + (uint32_t)(TC_D1_COL + m0), d1);
