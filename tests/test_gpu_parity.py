@@ -209,6 +209,43 @@ def test_largest_sketch_bases_coarse_operator_and_solve(hh, precision, tol, tol_
         hh.hh_destroy(h)
 
 
+# A sketch block too large for one CTA's shared memory (S_x = 641 columns of r + p = 42
+# samples: 220 KB in complex64, 441 KB in complex128) takes the cluster form of the QR.
+# Three levels keep the leaves on the eigenbasis path; the oracle is set up once (~35 s).
+WIDE_SKETCH = dict(n=639, k=160.0, levels=3, overlap=4, rank=16, oversample=26, seed=9)
+_WIDE = {}
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-7), ("mixed", 1e-3)])
+def test_wide_sketch_bases_and_coarse_operator(hh, precision, tol):
+    cfg = WIDE_SKETCH
+    if "PO" not in _WIDE:
+        P0 = Problem(2, cfg["n"], cfg["k"])
+        _WIDE["PO"] = (P0, OMethod(P0, cfg["levels"], cfg["overlap"], cfg["rank"], cfg["oversample"],
+                                   seed=cfg["seed"]))
+    P, O = _WIDE["PO"]
+    params = hh.make_params(2, cfg["n"], cfg["k"], cfg["levels"], cfg["overlap"], cfg["rank"], cfg["oversample"], 1,
+                            1e-13, 400, precision, cfg["seed"])
+    h, _ = hh.hh_setup(params)
+    try:
+        assert O.m == 42 and P.Sx == 641
+        for c in (1, 2, 3, 6):
+            V = np.zeros((P.Sx, O.r), dtype=np.complex128)
+            sig = np.zeros(O.m)
+            hh.hh_get_basis(h, c, V, sig)
+            assert np.allclose(V.conj().T @ V, np.eye(O.r), atol=10 * tol)
+            np.testing.assert_allclose(sig, O.sigma[c][:O.m], rtol=tol, atol=tol * O.sigma[c][0])
+            gap = O.sigma[c][O.r - 1] / max(O.sigma[c][O.r], 1e-300)
+            if gap > 1.05:
+                assert _proj_dist(V, O.V[c]) < 50 * tol / (gap - 1.0), (c, gap)
+        rr = random_complex((P.S, P.Sx, 1), 91)
+        z = torch.empty_like(dev(rr))
+        hh.hh_coarse_apply(h, 0, dev(rr), z)
+        assert rel(host(z), O.coarse(0, rr)) < (1e-8 if precision == "fp64" else 1e-3)
+    finally:
+        hh.hh_destroy(h)
+
+
 @pytest.mark.parametrize("leaf_solver", ["eigen", "block"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-3)])
 def test_one_oras_step(hh, precision, tol, leaf_solver):
