@@ -155,7 +155,7 @@ CATEGORY_BOUND = {
     "qr": ("latency", "k_qr (sketch orthonormalisation, shared-memory CGS2)"),
     "svd": ("latency", "k_heig_tri + k_heig_vec (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
     "leaf_sweep": ("alu", "k_eig_sweep_fused (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
-    "coarse_multi": ("hbm", "k_ip_partial (multi-column coarse projections of the set-up's sub-level solves)"),
+    "coarse_multi": ("hbm", "k_ip_colA_rt (multi-column coarse projections of the set-up's sub-level solves)"),
 }
 # FP64 peak derived from the DFMA issue rate (2 per SM per cycle, the peak ncu reports for
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum): 152 SMs x 2 x 2 flops x max SM clock.

@@ -216,10 +216,17 @@ int launch_ip_partial(const cplx<TA>* A, int lda, const cplx<TB>* B, int ldb, si
 // with cp.async (8-byte copies, zero-filled past the range).  The groups' sums are added in
 // shared memory, and the block writes its whole [p][q] partial (zeros outside the rows).
 static constexpr int RT_TP = 32;
+// The two halves of a node's basis share one launch: blocks [0, nb0) take rows [ilo0, ilo0 +
+// ni) on the points [pa0, pb0), the others rows [ilo1, ilo1 + ni) on [pa1, pb1).
 template <int KG>
 __global__ void __launch_bounds__(256) k_ip_colA_rt(const c64* __restrict__ A, size_t lda, const c64* __restrict__ B,
-                                                    int ldb, int p, int q, int ilo, int ni, size_t pa, size_t pb,
-                                                    c128* partial) {
+                                                    int ldb, int p, int q, int ni, int nb0, int ilo0, size_t pa0,
+                                                    size_t pb0, int ilo1, size_t pa1, size_t pb1, c128* partial) {
+    const bool second = (int)blockIdx.x >= nb0;
+    const int ilo = second ? ilo1 : ilo0;
+    const size_t pa = second ? pa1 : pa0, pb = second ? pb1 : pb0;
+    const unsigned blk = second ? blockIdx.x - nb0 : blockIdx.x;
+    const unsigned nblk = second ? gridDim.x - nb0 : nb0;
     extern __shared__ __align__(16) unsigned char rtsm[];
     const int IT = (ni + 3) / 4, CT = (q + 3) / 4, nt = IT * CT;
     const int nr = 4 * IT, qp = 4 * CT;          // padded tile rows and columns
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(256) k_ip_colA_rt(const c64* __restrict__ A, s
     const int it = o / CT, ct = o - it * CT;
     // this block's points: whole tiles of the range
     const size_t ntiles_all = (pb - pa + RT_TP - 1) / RT_TP;
-    const size_t t0b = ntiles_all * blockIdx.x / gridDim.x, t1b = ntiles_all * (blockIdx.x + 1) / gridDim.x;
+    const size_t t0b = ntiles_all * blk / nblk, t1b = ntiles_all * (blk + 1) / nblk;
     // padding rows / columns stay zero
     for (int e = tid; e < 2 * nr * RT_TP; e += blockDim.x) As[e] = {0.f, 0.f};
     for (int e = tid; e < 2 * RT_TP * qp; e += blockDim.x) Bs[e] = {0.f, 0.f};
@@ -309,19 +316,23 @@ __global__ void __launch_bounds__(256) k_ip_colA_rt(const c64* __restrict__ A, s
     }
 }
 
-static int ip_colA_rt_launch(const c64* A, size_t lda, const c64* B, int ldb, int p, int q, int ilo, int ni,
-                             size_t pa, size_t pb, c128* partial, int nblk, cudaStream_t s) {
+// nb0 blocks for the first set, nb1 for the second (nb1 = 0: one set)
+static int ip_colA_rt_launch(const c64* A, size_t lda, const c64* B, int ldb, int p, int q, int ni, int nb0,
+                             int ilo0, size_t pa0, size_t pb0, int nb1, int ilo1, size_t pa1, size_t pb1,
+                             c128* partial, cudaStream_t s) {
     const int IT = (ni + 3) / 4, CT = (q + 3) / 4, nt = IT * CT;
     const int kg = std::max(1, std::min(4, 256 / nt));
     const size_t sm = sizeof(c64) * std::max<size_t>((size_t)2 * (4 * IT * RT_TP + RT_TP * 4 * CT),
                                                      (size_t)kg * nt * 16);
-    const int threads = nt * kg;
+    const int threads = nt * kg, nblk = nb0 + nb1;
+#define HH_COLA_ARGS A, lda, B, ldb, p, q, ni, nb0, ilo0, pa0, pb0, ilo1, pa1, pb1, partial
     switch (kg) {
-        case 1: k_ip_colA_rt<1><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
-        case 2: k_ip_colA_rt<2><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
-        case 3: k_ip_colA_rt<3><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
-        default: k_ip_colA_rt<4><<<nblk, threads, sm, s>>>(A, lda, B, ldb, p, q, ilo, ni, pa, pb, partial); break;
+        case 1: k_ip_colA_rt<1><<<nblk, threads, sm, s>>>(HH_COLA_ARGS); break;
+        case 2: k_ip_colA_rt<2><<<nblk, threads, sm, s>>>(HH_COLA_ARGS); break;
+        case 3: k_ip_colA_rt<3><<<nblk, threads, sm, s>>>(HH_COLA_ARGS); break;
+        default: k_ip_colA_rt<4><<<nblk, threads, sm, s>>>(HH_COLA_ARGS); break;
     }
+#undef HH_COLA_ARGS
     note_launch();
     return nblk;
 }
@@ -335,19 +346,19 @@ int launch_ip_partial_colA(const cplx<TA>* A, const cplx<TB>* B, int ldb, size_t
         const int half = p / 2;
         if (q <= 64 && p <= 64 && N > 0) {
             const size_t sp = split_pt < 0 ? 0 : std::min<size_t>((size_t)split_pt, N);
-            if (split_pt < 0 || half == 0) {
+            if (split_pt < 0 || half == 0 || sp == 0 || sp == N) {
+                // one set: every row on every point
                 const int nb = std::max(1, std::min(max_blocks, (int)((N + 255) / 256)));
-                return ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, 0, p, 0, N, partial, nb, s);
+                return ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, p, nb, 0, 0, N, 0, 0, 0, 0,
+                                         partial, s);
             }
-            // the two halves of the basis on their own points, blocks in proportion
-            int nb1 = sp == 0 ? 0 : std::max(1, (int)std::lround((double)max_blocks * sp / N));
-            int nb2 = sp == N ? 0 : std::max(1, max_blocks - nb1);
+            // the two halves of the basis on their own points, in one launch, blocks in
+            // proportion to the points
+            int nb1 = std::max(1, (int)std::lround((double)max_blocks * sp / N));
+            const int nb2 = std::max(1, max_blocks - nb1);
             if (nb1 + nb2 > max_blocks) nb1 = max_blocks - nb2;
-            if (nb1 > 0) ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, 0, half, 0, sp, partial, nb1, s);
-            if (nb2 > 0)
-                ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, half, p - half, sp, N,
-                                  partial + (size_t)nb1 * p * q, nb2, s);
-            return nb1 + nb2;
+            return ip_colA_rt_launch((const c64*)A, N, (const c64*)B, ldb, p, q, half, nb1, 0, 0, sp, nb2, half, sp,
+                                     N, partial, s);
         }
     }
     int grid = (int)((N + 255) / 256);
