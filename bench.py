@@ -145,14 +145,16 @@ def leaf_bands(w):
 # and flops; see hh_profile_read in include/hh.h).
 CATEGORY_BOUND = {
     "factor": ("latency", "k_eig_roots + k_eig_modes (eigenpairs of the column pencil, scalar Schur recursions)"),
-    "sweep_in": ("alu", "k_eig_gemm2 (f^ = V^T f, register-tiled complex contraction)"),
+    "sweep_in": ("tensor_tf32x3", "k_tc_transform (f^ = V^T f on the tensor cores, TF32 three-term split; "
+                                  "k_eig_gemm2 on the CUDA cores where the autotuner chose it)"),
     "sweep_recur": ("hbm", "k_eig_recur (scalar Schur recursions along the line, warp scans)"),
-    "sweep_out": ("alu", "k_eig_gemm2 (x = V x^, register-tiled complex contraction)"),
+    "sweep_out": ("tensor_tf32x3", "k_tc_transform (x = V x^ on the tensor cores, TF32 three-term split; "
+                                   "k_eig_gemm2 on the CUDA cores where the autotuner chose it)"),
     "residual": ("hbm", "k_residual_cast (FP64 residual b - A u, its norm partials and complex64 copy)"),
     "coarse_project": ("hbm", "k_coarse_batch (one-column coarse corrections: C^H r, A_c^-1, C y; "
                               "one cooperative launch per level)"),
-    "galerkin": ("alu64", "k_galerkin_partial (A_c = C^H A~ C: FP64 stencil and products of the stored basis)"),
-    "qr": ("latency", "k_qr (sketch orthonormalisation, shared-memory CGS2)"),
+    "galerkin": ("alu64", "k_galerkin_partial3 (A_c = C^H A~ C: FP64 stencil and 3M products of the stored basis)"),
+    "qr": ("latency", "k_qr / k_qr_cluster (sketch orthonormalisation, CGS2 in shared memory, one CTA or a cluster)"),
     "svd": ("latency", "k_heig_tri + k_heig_vec (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
     "leaf_sweep": ("alu", "k_eig_sweep_fused (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
     "coarse_multi": ("hbm", "k_ip_colA_rt (multi-column coarse projections of the set-up's sub-level solves)"),
@@ -536,6 +538,15 @@ def rate(cat, ms, by, fl, pk, pk_kind):
         a = fl / (ms / 1e3) / 1e12
         out.update({"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                     "peak_kind": "FP32 FFMA derived: 152 SMs x 128 lanes x 2 flops x max SM clock"})
+    elif bound == "tensor_tf32x3" and fl > 0:
+        # the transforms run as TF32 MMAs three times over (hi.hi + hi.lo + lo.hi): executed
+        # tensor flops = 3 x the algorithmic complex-GEMM flops, against the dense TF32 peak
+        # (the measured bf16 GEMM rate x the nominal TF32 / BF16 ratio, 1.1 / 2.25)
+        peak = pk["bf16_tflops"] * (1.1 / 2.25)
+        a = 3.0 * fl / (ms / 1e3) / 1e12
+        out.update({"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                    "peak_kind": f"{pk_kind} bf16_tflops x 1.1/2.25 (TF32 dense); achieved counts the three "
+                                 "TF32 passes"})
     elif bound == "alu64" and fl > 0:
         peak = SM_COUNT * DFMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         a = fl / (ms / 1e3) / 1e12
