@@ -486,9 +486,94 @@ __global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict_
             if (c < cn) wr[c] = wr[c] + cvt<TW>(acc[c]);
     }
 }
+// The complex64 form of the same update with the basis staged and the output tile
+// written whole: a block of UPD_SP threads owns UPD_SP consecutive points (their rows of W
+// are one contiguous span); it stages the points' basis values, 32 columns at a time, with
+// asynchronous 8-byte copies (the whole group in flight at once), runs every chunk of 16
+// right-hand sides from shared memory into a shared output tile, and adds the tile to W
+// with coalesced loads and stores.  (Per-thread row updates of W left partial sectors that
+// the memory system wrote back several times over.)  A block whose points straddle the
+// split stages both halves in turn (the vanishing half is stored as zeros).
+static constexpr int UPD_SP = 64;
+__global__ void __launch_bounds__(UPD_SP * 2) k_coarse_updn_s(const c64* __restrict__ C, const c128* __restrict__ y,
+                                                              c64* __restrict__ W, size_t N, int p, int nc,
+                                                              long long split_pt) {
+    extern __shared__ __align__(16) unsigned char usm[];
+    const int ncp = (nc + 15) / 16 * 16;        // right-hand sides padded to whole chunks
+    c64* ys = (c64*)usm;                        // [p][ncp]
+    c64* cs = ys + (size_t)p * ncp;             // [32][UPD_SP] one column group of the basis
+    c64* ot = cs + 32 * UPD_SP;                 // [UPD_SP][ncp] the block's output tile
+    const int t = threadIdx.x, nth = blockDim.x;
+    const int pl = t % UPD_SP, ch = t / UPD_SP; // a thread's point and first chunk of 16
+    for (int e = t; e < p * ncp; e += nth) {
+        const int j = e / ncp, c = e - j * ncp;
+        ys[e] = c < nc ? cvt<float>(y[j * nc + c]) : c64{0.f, 0.f};
+    }
+    for (size_t p0 = (size_t)blockIdx.x * UPD_SP; p0 < N; p0 += (size_t)gridDim.x * UPD_SP) {
+        const int np = (int)min((size_t)UPD_SP, N - p0);
+        const size_t plast = p0 + np - 1;
+        int jlo = 0, jhi = p;
+        if (split_pt >= 0) {
+            if ((long long)plast < split_pt) jhi = p / 2;
+            else if ((long long)p0 >= split_pt) jlo = p / 2;
+        }
+        __syncthreads();   // the previous span's tile is written out
+        for (int e = t; e < UPD_SP * ncp; e += nth) ot[e] = {0.f, 0.f};
+        for (int g0 = jlo; g0 < jhi; g0 += 32) {
+            const int gn = min(32, jhi - g0);
+            __syncthreads();   // the previous group's values are no longer read
+            for (int e = t; e < gn * UPD_SP; e += nth) {
+                const int j = e / UPD_SP, k = e - j * UPD_SP;
+                const size_t x = p0 + k;
+                cp_async8_zfill(cs + e, C + (size_t)(g0 + j) * N + (x < N ? x : 0), x < N);
+            }
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
+            for (int c0 = 16 * ch; c0 < nc; c0 += 16 * (nth / UPD_SP)) {
+                c64 acc[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[c] = {0.f, 0.f};
+                for (int j = 0; j < gn; ++j) {
+                    const c64 cv = cs[j * UPD_SP + pl];
+                    const cpair<float>* yr = (const cpair<float>*)(ys + (size_t)(g0 + j) * ncp + c0);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const cpair<float> yy = yr[c];
+                        cfma(acc[2 * c], cv, yy.x);
+                        cfma(acc[2 * c + 1], cv, yy.y);
+                    }
+                }
+                c64* orow = ot + (size_t)pl * ncp + c0;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) orow[c] = orow[c] + acc[c];
+            }
+        }
+        __syncthreads();
+        // W's rows p0 .. p0 + np - 1 are one span of np nc values
+        c64* wspan = W + p0 * nc;
+        for (int e = t; e < np * nc; e += nth) {
+            const int r = e / nc, c = e - r * nc;
+            wspan[e] = wspan[e] + ot[(size_t)r * ncp + c];
+        }
+    }
+}
+
 template <typename TC, typename TW>
 void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N, int p, int nc, cudaStream_t s,
                         long long split_pt) {
+    if constexpr (sizeof(TC) == 4 && sizeof(TW) == 4) {
+        const int ncp = (nc + 15) / 16 * 16;
+        const size_t sm = sizeof(c64) * ((size_t)p * ncp + 32 * UPD_SP + (size_t)UPD_SP * ncp);
+        if (sm <= (size_t)(200 * 1024)) {
+            static std::atomic<unsigned long long> attr{0};
+            smem_limit_once(attr, k_coarse_updn_s, 200 * 1024);
+            const int grid = blocks_for(N, UPD_SP, 152 * 16);
+            k_coarse_updn_s<<<grid, UPD_SP * 2, sm, s>>>(C, y, W, N, p, nc, split_pt);
+            note_launch();
+            return;
+        }
+    }
     const dim3 grid(blocks_for(N, 256, 152 * 8), (nc + UPD_COLS - 1) / UPD_COLS);
     k_coarse_updn<TC, TW><<<grid, 256, sizeof(cplx<TC>) * p * UPD_COLS, s>>>(C, y, W, N, p, nc, split_pt);
     note_launch();
