@@ -478,6 +478,10 @@ struct Solver final : SolverBase {
     c128 *Vb = nullptr, *Zb = nullptr, *gw = nullptr, *gv = nullptr, *gz = nullptr, *gdots = nullptr,
          *gy = nullptr;
     c128* h_dots = nullptr;                       // pinned host copy of the dot products
+    GmresLs gls{};                                // the cycle's least-squares problem (device)
+    GmresState* h_gst = nullptr;                  // pinned snapshots of its state, GM_SLOTS
+    static constexpr int GM_SLOTS = 4, GM_LAG = 2;
+    cudaEvent_t gm_ev[GM_SLOTS] = {};
     // captured graphs of the preconditioner step (slot 0: gv -> gz for GMRES, slot 1:
     // the stationary update of u, slot 2: one step of the device-tested loop, update and
     // residual)
@@ -512,6 +516,8 @@ struct Solver final : SolverBase {
         if (block) dev_free(block, footprint, stream, hook);
         if (stream) cudaStreamSynchronize(stream);
         pinned_put(h_pin);   // nothing copies into it any more
+        for (auto& e : gm_ev)
+            if (e) cudaEventDestroy(e);
     }
 
     // the mixed form's opt-in FP32 Galerkin products and coarse elimination
@@ -630,6 +636,12 @@ struct Solver final : SolverBase {
             gz = a.take<c128>(N);
             gdots = a.take<c128>(4 * 80);
             gy = a.take<c128>(80);
+            gls.mk = mk;
+            gls.H = a.take<c128>((size_t)(mk + 1) * mk);
+            gls.cs = a.take<double>(mk);
+            gls.sn = a.take<c128>(mk);
+            gls.g = a.take<c128>(mk + 1);
+            gls.st = a.take<GmresState>(1);
         }
         d_ptrs = a.take<void*>(3 * 64);
         return align_up(a.off, 256);
@@ -1147,11 +1159,18 @@ struct Solver final : SolverBase {
         cudaEventDestroy(e1);
         if (!ok) return st;
         // one pinned block: the norms (8 doubles) at 0, the dot products (320 complex) at 256
-        static_assert(256 + 4 * 80 * sizeof(c128) <= PIN_BLOCK, "pinned block too small");
+        // and GM_SLOTS snapshots of the GMRES state after them
+        static_assert(256 + 4 * 80 * sizeof(c128) + GM_SLOTS * sizeof(GmresState) <= PIN_BLOCK,
+                      "pinned block too small");
         h_pin = pinned_get();
         if (!h_pin) return HH_ENOMEM;
         h_norm = (double*)h_pin;
-        if (mk > 0) h_dots = (c128*)((char*)h_pin + 256);
+        if (mk > 0) {
+            h_dots = (c128*)((char*)h_pin + 256);
+            h_gst = (GmresState*)((char*)h_pin + 256 + 4 * 80 * sizeof(c128));
+            for (auto& e : gm_ev)
+                if (!e) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), cerr);
+        }
         return cerr == cudaSuccess ? HH_OK : HH_ECUDA;
     }
 
@@ -1518,8 +1537,13 @@ struct Solver final : SolverBase {
     // Flexible GMRES(mk) right-preconditioned by M (Sec. 3 solves the preconditioned
     // system by GMRES).  Arnoldi in FP64 with classical Gram-Schmidt applied twice; the
     // preconditioned directions z_j = M v_j are kept, so M may vary between steps (the
-    // complex64 form).  Convergence is tested on the recurrence residual and confirmed
-    // on the true residual at every restart.
+    // complex64 form).  The least-squares problem (Hessenberg column, Givens rotations,
+    // residual estimate and stopping test) is updated on the device after each step, so
+    // the host does not wait on a step: it queues step j once it has read the state after
+    // step j - GM_LAG (a pinned snapshot behind an event).  A step queued after the test
+    // stopped the cycle works on columns past the stopping one and changes nothing the
+    // update reads (g and H up to the stopping column).  Convergence is confirmed on the
+    // true residual at every restart.
     hh_status loop_gmres(int& it, double& rel) {
         const size_t N = (size_t)Sy * Sx;
         const int ld = mk + 1;
@@ -1527,9 +1551,10 @@ struct Solver final : SolverBase {
         const c128 one = {1.0, 0.0};
         c128* gone = gdots + 3 * 80;
         ck(cudaMemcpyAsync(gone, &one, sizeof(c128), cudaMemcpyHostToDevice, stream), cerr);
-        std::vector<c128> H((size_t)(mk + 1) * mk), sn(mk), gq(mk + 1), y(mk);
-        std::vector<double> cs(mk);
         const double nbv = std::sqrt(std::max(h_norm[2], 0.0));
+        // with the profiler on, the captured preconditioner's events are read after every
+        // step, which needs a synchronisation per step
+        const int lag = prof_on ? 0 : GM_LAG;
         for (;;) {
             if (!true_residual(gw, st)) return st;
             const double beta = std::sqrt(std::max(h_norm[0], 0.0));
@@ -1538,10 +1563,17 @@ struct Solver final : SolverBase {
             if (rel < P.tol) return HH_OK;
             if (it >= P.max_iter) return HH_ENOCONV;
             launch_col_store_normalised(Vb, ld, 0, gw, (const c128*)dnorm, N, stream);
-            std::fill(gq.begin(), gq.end(), c128{0.0, 0.0});
-            gq[0] = {beta, 0.0};
-            int j = 0;
-            while (j < mk && it < P.max_iter) {
+            launch_gmres_init(gls, beta, stream);
+            const int nsteps = std::min(mk, P.max_iter - it);
+            int launched = 0;
+            for (int j = 0; j < nsteps; ++j) {
+                if (j >= lag && lag > 0) {
+                    // the state after step j - lag
+                    const int sl = (j - lag) % GM_SLOTS;
+                    ck(cudaEventSynchronize(gm_ev[sl]), cerr);
+                    if (cerr != cudaSuccess) return HH_ECUDA;
+                    if (h_gst[sl].stop) break;
+                }
                 launch_col_load(Vb, ld, j, gv, N, stream);
                 via_graph(0, [&] { precond(gv, gz); });
                 launch_col_store_normalised(Zb, mk, j, gz, gone, N, stream);
@@ -1556,44 +1588,28 @@ struct Solver final : SolverBase {
                                                                   stream);
                 launch_ip_reduce(partial, nbn, 1, 1, gdots + 160, nullptr, nullptr, stream);
                 launch_col_store_normalised(Vb, ld, j + 1, gw, gdots + 160, N, stream);
-                ck(cudaMemcpyAsync(h_dots, gdots, sizeof(c128) * 3 * 80, cudaMemcpyDeviceToHost, stream), cerr);
-                if (!sync_check(st)) return st;
-                graphs_collect();
-                // column j of the Hessenberg matrix: h_ij = conj(sum conj(w) v_i) over both passes
-                for (int i = 0; i <= j; ++i) H[(size_t)i * mk + j] = conj(h_dots[i]) + conj(h_dots[80 + i]);
-                const double hn = std::sqrt(std::max(h_dots[160].re, 0.0));
-                for (int i = 0; i < j; ++i) {
-                    const c128 a0 = H[(size_t)i * mk + j], a1 = H[(size_t)(i + 1) * mk + j];
-                    H[(size_t)i * mk + j] = cs[i] * a0 + sn[i] * a1;
-                    H[(size_t)(i + 1) * mk + j] = cs[i] * a1 - conj(sn[i]) * a0;
+                launch_gmres_rotate(gls, gdots, gdots + 80, gdots + 160, j, nbv, P.tol, stream);
+                const int sl = j % GM_SLOTS;
+                ck(cudaMemcpyAsync(&h_gst[sl], gls.st, sizeof(GmresState), cudaMemcpyDeviceToHost, stream), cerr);
+                ck(cudaEventRecord(gm_ev[sl], stream), cerr);
+                ++launched;
+                if (lag == 0) {
+                    if (!sync_check(st)) return st;
+                    graphs_collect();
+                    if (h_gst[sl].stop) break;
                 }
-                const c128 a = H[(size_t)j * mk + j];
-                const double aa = std::sqrt(abs2(a)), t = std::sqrt(abs2(a) + hn * hn);
-                if (t == 0.0) { cs[j] = 1.0; sn[j] = {0.0, 0.0}; }
-                else if (aa == 0.0) { cs[j] = 0.0; sn[j] = {1.0, 0.0}; H[(size_t)j * mk + j] = {hn, 0.0}; }
-                else {
-                    const c128 ph = (1.0 / aa) * a;
-                    cs[j] = aa / t;
-                    sn[j] = (hn / t) * ph;
-                    H[(size_t)j * mk + j] = t * ph;
-                }
-                gq[j + 1] = -(conj(sn[j]) * gq[j]);
-                gq[j] = cs[j] * gq[j];
-                ++j;
-                ++it;
-                const double est = nbv > 0 ? std::sqrt(abs2(gq[j])) / nbv : 0.0;
-                if (!std::isfinite(est)) return HH_ENOCONV;
-                if (est < 0.5 * P.tol || hn == 0.0) break;
             }
-            // y = R^{-1} g  (j x j upper triangular), u += Z y
-            for (int i = j - 1; i >= 0; --i) {
-                c128 acc = gq[i];
-                for (int k = i + 1; k < j; ++k) acc = acc - H[(size_t)i * mk + k] * y[k];
-                const c128 d = H[(size_t)i * mk + i];
-                y[i] = abs2(d) > 0 ? acc * cinv(d) : c128{0.0, 0.0};
-            }
-            ck(cudaMemcpyAsync(gy, y.data(), sizeof(c128) * j, cudaMemcpyHostToDevice, stream), cerr);
-            launch_basis_combine(Zb, mk, j, gy, false, 1.0, u, N, stream);
+            if (!sync_check(st)) return st;
+            graphs_collect();
+            GmresState fin{};
+            ck(cudaMemcpy(&fin, gls.st, sizeof(GmresState), cudaMemcpyDeviceToHost), cerr);
+            if (cerr != cudaSuccess) return HH_ECUDA;
+            if (fin.bad) return HH_ENOCONV;
+            const int jn = fin.stop ? fin.jstop : launched;
+            it += jn;
+            // y = R^{-1} g  (jn x jn upper triangular), u += Z y
+            launch_gmres_solve(gls, jn, gy, stream);
+            launch_basis_combine(Zb, mk, jn, gy, false, 1.0, u, N, stream);
         }
     }
 

@@ -650,6 +650,81 @@ HH_APPLY(float, float, float)
 HH_APPLY(float, double, double)
 HH_APPLY(double, float, float)
 
+// ------------------------------------------------ GMRES least squares on the device
+__global__ void k_gmres_init(GmresLs ls, double beta) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i <= ls.mk; ++i) ls.g[i] = {0.0, 0.0};
+    ls.g[0] = {beta, 0.0};
+    *ls.st = GmresState{0, 0, 0, 0, 0.0, 0.0};
+}
+// The steps of a plain Givens QR of the Hessenberg matrix, column by column (the complex
+// rotation [c s; -conj(s) c] with real c zeroing the subdiagonal entry hn).
+__global__ void k_gmres_rotate(GmresLs ls, const c128* d1, const c128* d2, const c128* dn, int j, double nbv,
+                               double tol) {
+    if (threadIdx.x != 0 || ls.st->stop) return;
+    const int mk = ls.mk;
+    c128* H = ls.H;
+    for (int i = 0; i <= j; ++i) H[(size_t)i * mk + j] = conj(d1[i]) + conj(d2[i]);
+    const double hn = sqrt(fmax(dn->re, 0.0));
+    for (int i = 0; i < j; ++i) {
+        const c128 a0 = H[(size_t)i * mk + j], a1 = H[(size_t)(i + 1) * mk + j];
+        H[(size_t)i * mk + j] = ls.cs[i] * a0 + ls.sn[i] * a1;
+        H[(size_t)(i + 1) * mk + j] = ls.cs[i] * a1 - conj(ls.sn[i]) * a0;
+    }
+    const c128 a = H[(size_t)j * mk + j];
+    const double aa = sqrt(abs2(a)), t = sqrt(abs2(a) + hn * hn);
+    if (t == 0.0) {
+        ls.cs[j] = 1.0;
+        ls.sn[j] = {0.0, 0.0};
+    } else if (aa == 0.0) {
+        ls.cs[j] = 0.0;
+        ls.sn[j] = {1.0, 0.0};
+        H[(size_t)j * mk + j] = {hn, 0.0};
+    } else {
+        const c128 ph = (1.0 / aa) * a;
+        ls.cs[j] = aa / t;
+        ls.sn[j] = (hn / t) * ph;
+        H[(size_t)j * mk + j] = t * ph;
+    }
+    ls.g[j + 1] = -(conj(ls.sn[j]) * ls.g[j]);
+    ls.g[j] = ls.cs[j] * ls.g[j];
+    GmresState* st = ls.st;
+    st->steps = j + 1;
+    const double est = nbv > 0 ? sqrt(abs2(ls.g[j + 1])) / nbv : 0.0;
+    st->est = est;
+    if (!isfinite(est)) {
+        st->bad = 1;
+        st->stop = 1;
+        st->jstop = j + 1;
+    } else if (est < 0.5 * tol || hn == 0.0) {
+        st->stop = 1;
+        st->jstop = j + 1;
+    }
+}
+__global__ void k_gmres_solve(GmresLs ls, int jn, c128* y) {
+    if (threadIdx.x != 0) return;
+    const int mk = ls.mk;
+    for (int i = jn - 1; i >= 0; --i) {
+        c128 acc = ls.g[i];
+        for (int k = i + 1; k < jn; ++k) acc = acc - ls.H[(size_t)i * mk + k] * y[k];
+        const c128 d = ls.H[(size_t)i * mk + i];
+        y[i] = abs2(d) > 0 ? acc * cinv(d) : c128{0.0, 0.0};
+    }
+}
+void launch_gmres_init(GmresLs ls, double beta, cudaStream_t s) {
+    k_gmres_init<<<1, 32, 0, s>>>(ls, beta);
+    note_launch();
+}
+void launch_gmres_rotate(GmresLs ls, const c128* d1, const c128* d2, const c128* dn, int j, double nbv, double tol,
+                         cudaStream_t s) {
+    k_gmres_rotate<<<1, 32, 0, s>>>(ls, d1, d2, dn, j, nbv, tol);
+    note_launch();
+}
+void launch_gmres_solve(GmresLs ls, int jn, c128* y, cudaStream_t s) {
+    k_gmres_solve<<<1, 32, 0, s>>>(ls, jn, y);
+    note_launch();
+}
+
 #define HH_COPY(TS, TD) \
     template void launch_copy<TS, TD>(const cplx<TS>*, cplx<TD>*, size_t, bool, bool, cudaStream_t);
 HH_COPY(double, double)

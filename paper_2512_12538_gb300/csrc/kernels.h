@@ -178,6 +178,34 @@ void launch_col_store_normalised(c128* B, int ld, int col, const c128* src, cons
 void launch_basis_combine(const c128* B, int ld, int j, const c128* coef, bool cj, double sgn, c128* w, size_t n,
                           cudaStream_t s);
 
+// Flexible GMRES's least-squares problem on the device (one thread): the Hessenberg
+// matrix H (entry (i, j) at H[i * mk + j], mk + 1 rows), the Givens rotations (cs, sn) and
+// the rotated right-hand side g of one restart cycle.
+struct GmresState {
+    int stop;      // 1 once the estimate is below tol / 2, the new column vanished, or not finite
+    int jstop;     // columns of the cycle when it stopped
+    int bad;       // 1: the estimate was not finite
+    int steps;     // columns done
+    double est;    // |g[steps]| / ||b||, the residual estimate
+    double pad;
+};
+struct GmresLs {
+    c128* H;       // [(mk + 1) * mk]
+    double* cs;    // [mk]
+    c128* sn;      // [mk]
+    c128* g;       // [mk + 1]
+    GmresState* st;
+    int mk;
+};
+// start a cycle: g = (beta, 0, ...), state cleared
+void launch_gmres_init(GmresLs ls, double beta, cudaStream_t s);
+// column j from the dot products of the two Gram-Schmidt passes (d1, d2: conj(h_ij)) and
+// ||w||^2 (dn.re): rotations, g, the estimate and the stop test; does nothing once stopped
+void launch_gmres_rotate(GmresLs ls, const c128* d1, const c128* d2, const c128* dn, int j, double nbv, double tol,
+                         cudaStream_t s);
+// y = R^{-1} g over the first jn columns (R the rotated H)
+void launch_gmres_solve(GmresLs ls, int jn, c128* y, cudaStream_t s);
+
 // ---- dense kernels (k_dense.cu) ----------------------------------------------------
 // partial[blk][i][j] = sum_{n in blk} conj(A[n*lda+i]) * B[n*ldb+j]; returns nblk.
 // ACC is the accumulation precision (double, or float for complex64 working data).
