@@ -153,7 +153,9 @@ CATEGORY_BOUND = {
     "residual": ("hbm", "k_residual_cast (FP64 residual b - A u, its norm partials and complex64 copy)"),
     "coarse_project": ("hbm", "k_coarse_batch (one-column coarse corrections: C^H r, A_c^-1, C y; "
                               "one cooperative launch per level)"),
-    "galerkin": ("alu64", "k_galerkin_partial3 (A_c = C^H A~ C: FP64 stencil and 3M products of the stored basis)"),
+    "galerkin": ("alu64", "k_galerkin_herm + k_galerkin_bdry (A_c = C^H A~ C, Hermitian-packed: the upper "
+                          "triangle by FP64 3M products of the stored basis, the impedance terms on the boundary "
+                          "points)"),
     "qr": ("latency", "k_qr / k_qr_cluster (sketch orthonormalisation, CGS2 in shared memory, one CTA or a cluster)"),
     "svd": ("latency", "k_heig_tri + k_heig_vec (FP64 Hermitian eigenproblem of the sketch Gram matrix)"),
     "leaf_sweep": ("alu", "k_eig_sweep_fused (f^ = V^T f, scalar recursions, x = V x^; one cluster per leaf)"),
@@ -166,7 +168,7 @@ DFMA_PER_SM_CLK = 2
 # kernel on this workload's shapes (mean of its three launches per step), from the ncu
 # capture summarised in profiles/coarse_batch_helm2d_n1023_k100_L3.md.  To be removed
 # whenever k_coarse_batch changes.
-TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 585.0e6}
+TRAFFIC_BYTES_PER_LAUNCH = {}
 
 
 def whole_job_rate(local_ms, units_per_rank, world, device="cuda"):

@@ -147,6 +147,28 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 // Asynchronous 16-byte global -> shared copies (the copy engine of the load/store unit):
 // issue, commit, and wait for all of this thread's copies.
+// L2 eviction priorities for streamed loads: a policy from createpolicy and a read-only
+// load that carries it
+__device__ __forceinline__ unsigned long long l2_policy_first() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_normal() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ cplx<float> ld_hint(const cplx<float>* a, unsigned long long pol) {
+    cplx<float> v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.re), "=f"(v.im) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ cplx<double> ld_hint(const cplx<double>* a, unsigned long long pol) {
+    cplx<double> v;
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.re), "=d"(v.im) : "l"(a), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }

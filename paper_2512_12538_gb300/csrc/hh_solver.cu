@@ -1080,19 +1080,26 @@ struct Solver final : SolverBase {
                                       stream);
             }
             // A_c = C_p^H A~_p C_p, then its inverse.  Algorithmic work: a point in one child's
-            // rows pairs that child's r columns of conj(C) with r columns of A~ C, r^2 complex
-            // products of 8 real flops (the two rows next to the split pair r with 2r)
-            pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT), 8.0 * r * r * (pts(p) + 2.0 * Sx));
+            // rows pairs that child's r columns of conj(C) with r columns of A~ C, complex
+            // products of 8 real flops: r^2 of them (the two rows next to the split pair r with
+            // 2r), or r (r + 1) / 2 in the Hermitian-packed form of the FP64 5-point products
+            // (the row before the split adds r^2)
+            const bool herm_form = !coarse_fp32() && !q1();
+            pbeg(PC_GALERKIN, (double)pts(p) * 2 * r * sizeof(CT),
+                 herm_form ? 8.0 * (0.5 * r * (r + 1.0) * pts(p) + (double)r * r * Sx)
+                           : 8.0 * r * r * (pts(p) + 2.0 * Sx));
             const int split = nodes[nodes[p].child[1]].own_a - nodes[p].ra;
             // FP64 products from the stored basis, or FP32 ones in the opt-in FP32 coarse
             // variant of the mixed form
+            bool herm = false;
             const int nb = coarse_fp32()
                                ? launch_galerkin_partial<T, T>(C[p], geom(p), 2 * r, split, partial, MAX_PART_BLOCKS,
                                                                stream)
                                : launch_galerkin_partial<T, double>(C[p], geom(p), 2 * r, split, partial,
-                                                                    MAX_PART_BLOCKS, stream);
+                                                                    MAX_PART_BLOCKS, stream, &herm);
             pend(PC_GALERKIN);
             launch_ip_reduce(partial, nb, 2 * r, 2 * r, Ainv[p], nullptr, nullptr, stream);
+            if (herm) launch_herm_fill(Ainv[p], 2 * r, stream);
         }
         // the level's Galerkin matrices inverted together
         GjBatch bt{};

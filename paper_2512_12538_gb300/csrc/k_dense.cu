@@ -674,10 +674,269 @@ __global__ void __launch_bounds__(G3_THREADS, 1) k_galerkin_partial3(const cplx<
     }
 }
 
+// ------------------------------------------------ Hermitian-packed FP64 Galerkin matrix
+// For the 5-point rows A~ is complex symmetric with real couplings: A~ = S + i D, S = Re A~
+// real symmetric and D = Im A~ diagonal, nonzero only on the band's boundary points (the
+// impedance terms).  So A_c = C^H S C + i C^H D C with both terms Hermitian, and for i < j
+//   A_c[j][i] = conj(A_c[i][j]) + 2i conj(H_D[i][j]),   H_D = C^H D C.
+// k_galerkin_herm sums A_c[i][j] over its points for i <= j only (about half the products
+// of the full matrix) into slot [i][j] of the block's partial, zero below the diagonal;
+// k_galerkin_bdry sums 2i conj(H_D[i][j]) over boundary points into the slots [j][i]; after
+// the fixed-order sum over blocks k_herm_fill forms A_c[j][i] = conj(A_c[i][j]) + slot[j][i].
+// The sums of a pair are the 3M products of k_galerkin_partial3, in FP64.
+
+// Block point ranges of equal cost for k_galerkin_herm: a point of row split_row - 1 (the
+// only row where the first child's columns meet the second child's, through the stencil)
+// costs wgt, any other point 1.
+__device__ __forceinline__ void gal_range_w(size_t N, int Sx, int split_row, int wgt, unsigned blk, unsigned nblk,
+                                            size_t& n0, size_t& n1) {
+    size_t s0 = 0, s1 = 0;
+    if (split_row >= 1) {
+        s0 = min(N, (size_t)(split_row - 1) * Sx);
+        s1 = min(N, (size_t)split_row * Sx);
+    }
+    const size_t w = (size_t)wgt;
+    const size_t T = N + (w - 1) * (s1 - s0);
+    auto inv = [&](size_t c) -> size_t {
+        if (c <= s0) return c;
+        if (c <= s0 + w * (s1 - s0)) return s0 + (c - s0) / w;
+        return c - (w - 1) * (s1 - s0);
+    };
+    n0 = inv(T * blk / nblk);
+    n1 = blk + 1 == nblk ? N : inv(T * (blk + 1) / nblk);
+}
+
+// Pair t of the upper triangle (diagonal included) of an m x m block, rows folded in
+// pairs (r, m - 1 - r) so that consecutive t run along one row: t = r (m + 1) + c.
+__device__ __forceinline__ void tri_pair(int t, int m, int& i, int& j) {
+    const int r = t / (m + 1), c = t - r * (m + 1);
+    if (c < m - r) {
+        i = r;
+        j = r + c;
+    } else {
+        i = m - 1 - r;
+        j = c - 1;
+    }
+}
+
+static constexpr int GH_SLOTS = 6;
+template <typename TI>
+__global__ void __launch_bounds__(G3_THREADS, 1) k_galerkin_herm(const cplx<TI>* __restrict__ C, OpGeom g, int p,
+                                                                 int split_row, int wgt, c128* partial) {
+    extern __shared__ __align__(16) unsigned char gsm_[];
+    const int plane = IP_TILE * p;
+    double* A0 = (double*)gsm_;   // ar, ai, ar - ai of conj(C)'s factor
+    double* A1 = A0 + plane;
+    double* A2 = A1 + plane;
+    double* B0 = A2 + plane;      // br, bi - br, br + bi of A~ C
+    double* B1 = B0 + plane;
+    double* B2 = B1 + plane;
+    const int ph = p / 2, T = ph * (ph + 1) / 2, X = ph * ph;
+    const int RT = (T + G3_THREADS - 1) / G3_THREADS, RC = (X + G3_THREADS - 1) / G3_THREADS;
+    // the thread's pairs: slot k belongs to set 0 (first half's triangle), 1 (second
+    // half's) or 2 (first half's rows against the second half's columns), one round of
+    // G3_THREADS pairs each.  A warp's FP64 instruction costs the same however many of its
+    // lanes are active, so the pairs of a partial round are shared out over all sixteen
+    // warps, and the lanes given one pair split the tile's points between them (sn0: first
+    // point, snst: step); their sums are added across those lanes at the end.
+    int si[GH_SLOTS], sj[GH_SLOTS], ss[GH_SLOTS], sn0[GH_SLOTS], snst[GH_SLOTS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < GH_SLOTS; ++k) {
+        int set, rnd;
+        if (k < RT) { set = 0; rnd = k; }
+        else if (k < 2 * RT) { set = 1; rnd = k - RT; }
+        else { set = 2; rnd = k - 2 * RT; }
+        const int size = set == 2 ? X : T;
+        const int rem = k < 2 * RT + RC ? size - rnd * G3_THREADS : 0;
+        int e = -1;
+        sn0[k] = 0;
+        snst[k] = 1;
+        if (rem >= G3_THREADS) {
+            e = rnd * G3_THREADS + threadIdx.x;
+        } else if (rem > 0) {
+            const int ppw = (rem + 15) / 16, L = max(1, 32 / ppw);
+            const int gq = lane / L, m = w * ppw + gq;
+            sn0[k] = lane - gq * L;
+            snst[k] = L;
+            if (gq < ppw && m < rem) e = rnd * G3_THREADS + m;
+        }
+        ss[k] = e < 0 ? -1 : set;
+        si[k] = sj[k] = 0;
+        if (e >= 0) {
+            if (set == 2) {
+                si[k] = e / ph;
+                sj[k] = ph + e % ph;
+            } else {
+                tri_pair(e, ph, si[k], sj[k]);
+                si[k] += set * ph;
+                sj[k] += set * ph;
+            }
+        }
+    }
+    double s1[GH_SLOTS], s2[GH_SLOTS], s3[GH_SLOTS];
+#pragma unroll
+    for (int k = 0; k < GH_SLOTS; ++k) s1[k] = s2[k] = s3[k] = 0.0;
+    const size_t N = (size_t)g.b * g.Sx;
+    size_t n0, n1;
+    gal_range_w(N, g.Sx, split_row, wgt, blockIdx.x, gridDim.x, n0, n1);
+    for (size_t t0 = n0; t0 < n1; t0 += IP_TILE) {
+        const int rows = (int)min((size_t)IP_TILE, n1 - t0);
+        // the sets with nonzero terms on this tile's rows: the first half's columns of C
+        // live on rows < split_row, the second's on the others, and A~ C reaches one row
+        // further
+        bool act0 = true, act1 = true, actx = true;
+        if (split_row >= 0) {
+            const int j0 = (int)(t0 / g.Sx), j1 = (int)((t0 + rows - 1) / g.Sx);
+            act0 = j0 < split_row;
+            act1 = j1 >= split_row;
+            actx = j0 <= split_row - 1 && j1 >= split_row - 1;
+        }
+        for (int e = threadIdx.x; e < rows * p; e += G3_THREADS) {
+            const size_t pt = t0 + e / p;
+            const int l = e % p;
+            const bool lo = l < ph;
+            const bool need_a = lo ? (act0 || actx) : act1;
+            const bool need_b = lo ? act0 : (act1 || actx);
+            if (!need_a && !need_b) continue;
+            const int i = (int)(pt % g.Sx), j = (int)(pt / g.Sx);
+            const size_t t = (size_t)l * N + pt;
+            const c128 cv = cvt<double>(C[t]);
+            c128 ax;
+            if (g.Sx > 1 && i > 0 && i < g.Sx - 1 && j > 0 && j < g.b - 1) {
+                const double kr = g.khr ? g.khr[j] : g.kh;
+                const double d = 4.0 - kr * kr;
+                const c128 q1 = cvt<double>(C[t - 1]), q2 = cvt<double>(C[t + 1]);
+                const c128 q3 = cvt<double>(C[t - g.Sx]), q4 = cvt<double>(C[t + g.Sx]);
+                ax.re = d * cv.re - q1.re - q2.re - q3.re - q4.re;
+                ax.im = d * cv.im - q1.im - q2.im - q3.im - q4.im;
+            } else {
+                ax = op_diag(j, i, g) * cv;
+                const double wj = wrow(j, g.b), wi = wcol(i, g.Sx);
+                if (g.Sx > 1) {
+                    if (i > 0) ax = ax - wj * cvt<double>(C[t - 1]);
+                    if (i < g.Sx - 1) ax = ax - wj * cvt<double>(C[t + 1]);
+                }
+                if (j > 0) ax = ax - wi * cvt<double>(C[t - g.Sx]);
+                if (j < g.b - 1) ax = ax - wi * cvt<double>(C[t + g.Sx]);
+            }
+            A0[e] = cv.re;
+            A1[e] = cv.im;
+            A2[e] = cv.re - cv.im;
+            B0[e] = ax.re;
+            B1[e] = ax.im - ax.re;
+            B2[e] = ax.re + ax.im;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GH_SLOTS; ++k) {
+            const int set = ss[k];
+            if (set < 0 || !(set == 0 ? act0 : (set == 1 ? act1 : actx))) continue;
+            const int i = si[k], j = sj[k];
+            double x1 = s1[k], x2 = s2[k], x3 = s3[k];
+            for (int n = sn0[k]; n < rows; n += snst[k]) {
+                const int ai = n * p + i, bj = n * p + j;
+                x1 = fma(B0[bj], A2[ai], x1);
+                x2 = fma(A0[ai], B1[bj], x2);
+                x3 = fma(A1[ai], B2[bj], x3);
+            }
+            s1[k] = x1;
+            s2[k] = x2;
+            s3[k] = x3;
+        }
+        __syncthreads();
+    }
+    // the lanes that shared a pair's points: their sums added in lane order (the step is
+    // the same for the whole warp)
+#pragma unroll
+    for (int k = 0; k < GH_SLOTS; ++k) {
+        const int L = snst[k];
+        if (L > 1) {
+            const int base = lane - sn0[k];
+            double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            for (int d = 0; d < L; ++d) {
+                const int src = (base + d) & 31;
+                t1 += __shfl_sync(0xffffffffu, s1[k], src);
+                t2 += __shfl_sync(0xffffffffu, s2[k], src);
+                t3 += __shfl_sync(0xffffffffu, s3[k], src);
+            }
+            s1[k] = t1;
+            s2[k] = t2;
+            s3[k] = t3;
+            if (sn0[k] != 0) ss[k] = -1;   // one lane of the group writes
+        }
+    }
+    c128* out = partial + (size_t)blockIdx.x * p * p;
+    for (int o = threadIdx.x; o < p * p; o += G3_THREADS)
+        if (o / p > o % p) out[o] = {0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < GH_SLOTS; ++k)
+        if (ss[k] >= 0) out[(size_t)si[k] * p + sj[k]] = {s1[k] + s3[k], s1[k] + s2[k]};
+}
+
+// Boundary points of a band (those with an impedance term): rows 0 and b - 1, then the
+// first and last column of the rows between (Sx > 1).
+__host__ __device__ inline int band_boundary_points(int b, int Sx) {
+    if (b <= 1) return Sx;
+    return 2 * Sx + (Sx > 1 ? 2 * (b - 2) : 0);
+}
+__device__ __forceinline__ void band_boundary_point(int q, int b, int Sx, int& j, int& i) {
+    if (q < Sx) { j = 0; i = q; return; }
+    if (q < 2 * Sx) { j = b - 1; i = q - Sx; return; }
+    const int k = q - 2 * Sx;
+    j = 1 + k / 2;
+    i = (k & 1) ? Sx - 1 : 0;
+}
+
+// slot [j][i] (i < j) of block blockIdx.x's partial: 2i conj(sum conj(C_i) D C_j) over the
+// block's `chunk` boundary points; zero elsewhere (and for i, j in different halves of a
+// split basis, whose columns never meet at one point)
+template <typename TI>
+__global__ void __launch_bounds__(256) k_galerkin_bdry(const cplx<TI>* __restrict__ C, OpGeom g, int p, int split_row,
+                                                       int chunk, c128* partial) {
+    extern __shared__ c128 bsm_[];
+    c128* Cs = bsm_;                // [chunk][p] C
+    c128* Ds = bsm_ + (size_t)chunk * p;   // [chunk][p] D C
+    const size_t N = (size_t)g.b * g.Sx;
+    const int nbp = band_boundary_points(g.b, g.Sx);
+    const int q0 = blockIdx.x * chunk, nq = max(0, min(nbp, q0 + chunk) - q0);
+    for (int e = threadIdx.x; e < nq * p; e += blockDim.x) {
+        const int n = e / p, l = e % p;
+        int j, i;
+        band_boundary_point(q0 + n, g.b, g.Sx, j, i);
+        const c128 cv = cvt<double>(C[(size_t)l * N + (size_t)j * g.Sx + i]);
+        const double d = op_diag(j, i, g).im;
+        Cs[e] = cv;
+        Ds[e] = {d * cv.re, d * cv.im};
+    }
+    __syncthreads();
+    const int ph = p / 2;
+    c128* out = partial + (size_t)blockIdx.x * p * p;
+    for (int o = threadIdx.x; o < p * p; o += blockDim.x) {
+        const int jr = o / p, ic = o % p;   // slot [j][i]
+        c128 h = {0.0, 0.0};
+        if (jr > ic && !(split_row >= 0 && (ic < ph) != (jr < ph)))
+            for (int n = 0; n < nq; ++n) cfma_cj(h, Cs[n * p + ic], Ds[n * p + jr]);
+        out[o] = jr > ic ? c128{2.0 * h.im, 2.0 * h.re} : c128{0.0, 0.0};
+    }
+}
+
+__global__ void k_herm_fill(c128* A, int p) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < p * p; o += gridDim.x * blockDim.x) {
+        const int r = o / p, c = o % p;
+        if (r > c) A[o] = conj(A[(size_t)c * p + r]) + A[o];
+    }
+}
+void launch_herm_fill(c128* A, int p, cudaStream_t s) {
+    k_herm_fill<<<(p * p + 255) / 256, 256, 0, s>>>(A, p);
+    note_launch();
+}
+
 template <typename TI, typename T>
 int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool* herm) {
     const size_t N = (size_t)g.b * g.Sx;
+    if (herm) *herm = false;
     int grid = (int)((N + 127) / 128);
     if (grid > max_blocks) grid = max_blocks;
     if (grid < 1) grid = 1;
@@ -687,6 +946,33 @@ int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c
     static std::atomic<unsigned long long> attr4{0}, attrmax{0};
     smem_limit_once(attr4, k_galerkin_partial<TI, T, 4>, 200 * 1024);
     smem_limit_once(attrmax, k_galerkin_partial<TI, T, IP_MAXOUT>, 200 * 1024);
+    if (sizeof(T) == sizeof(double) && herm && !g.q1 && p % 2 == 0 && p <= 64 && nout >= G3_THREADS) {
+        // FP64 products of the 5-point rows: the Hermitian-packed form, the blocks' point
+        // ranges balanced with the rows' costs (the row before the split also pairs the
+        // first half's columns with the second's); the boundary terms go to the blocks
+        // after those (at most max_blocks + 1 - g3 of them)
+        const int g3 = std::min(grid, max_blocks / 2 > 0 ? max_blocks / 2 : 1);
+        const int nbp = band_boundary_points(g.b, g.Sx);
+        const int room = std::max(1, max_blocks + 1 - g3);
+        const int chunk = std::max(16, (nbp + room - 1) / room);
+        const int maxchunk = (int)((96 * 1024) / (2 * sizeof(c128) * p));
+        if (chunk <= maxchunk) {
+            const int ph = p / 2, T3 = ph * (ph + 1) / 2;
+            const int wgt = split_row >= 1 ? (T3 + ph * ph + T3 / 2) / T3 : 1;
+            const size_t smh = sizeof(double) * 6 * (size_t)IP_TILE * p;
+            static std::atomic<unsigned long long> ah{0}, ab{0};
+            smem_limit_once(ah, k_galerkin_herm<TI>, 200 * 1024);
+            smem_limit_once(ab, k_galerkin_bdry<TI>, 200 * 1024);
+            k_galerkin_herm<TI><<<g3, G3_THREADS, smh, s>>>(C, g, p, split_row, wgt, partial);
+            note_launch();
+            const int nbx = (nbp + chunk - 1) / chunk;
+            const size_t smb = 2 * sizeof(c128) * (size_t)chunk * p;
+            k_galerkin_bdry<TI><<<nbx, 256, smb, s>>>(C, g, p, split_row, chunk, partial + (size_t)g3 * nout);
+            note_launch();
+            *herm = true;
+            return g3 + nbx;
+        }
+    }
     if (sizeof(T) == sizeof(double) && nout >= G3_THREADS && nout <= 8 * G3_THREADS) {
         // FP64 products, whole outputs per thread: the 3M form, one block per SM
         const size_t sm3 = sizeof(double) * 6 * (size_t)IP_TILE * p;
@@ -1522,9 +1808,9 @@ template int launch_ip_partial_colA<float, float, float>(const c64*, const c64*,
                                                         cudaStream_t, long long);
 template int launch_ip_partial_colA<double, double, double>(const c128*, const c128*, int, size_t, int, int, c128*,
                                                             int, cudaStream_t, long long);
-template int launch_galerkin_partial<float, float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
-template int launch_galerkin_partial<float, double>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t);
-template int launch_galerkin_partial<double, double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t);
+template int launch_galerkin_partial<float, float>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t, bool*);
+template int launch_galerkin_partial<float, double>(const c64*, OpGeom, int, int, c128*, int, cudaStream_t, bool*);
+template int launch_galerkin_partial<double, double>(const c128*, OpGeom, int, int, c128*, int, cudaStream_t, bool*);
 template void launch_qr<float>(c64* const*, int, int, int, c64**, cudaStream_t);
 template void launch_qr<double>(c128* const*, int, int, int, c128**, cudaStream_t);
 template void launch_form_v<float>(const c64*, const c128*, const double*, c64*, int, int, int, cudaStream_t);

@@ -149,6 +149,7 @@ struct CoarseBatch {
     const int* gate;       // may be null: when the word is nonzero at launch, nothing is done
     CoarseRecur rr;
     long long wait_polls;  // polls of the grid barrier's wait before it gives up (set by the launcher)
+    float keep;            // set by the launcher: < 1 when the launch's basis exceeds the L2 (see the kernel)
 };
 
 // Polls a bounded device-side wait makes before giving up with DEV_TIMEOUT: the
@@ -219,9 +220,14 @@ void launch_ip_reduce(const c128* partial, int nblk, int p, int q, c128* out, co
 // C column-major).
 // split_row >= 0: columns [0, p/2) of C vanish on rows >= split_row and [p/2, p) below it.
 // Galerkin partial sums of A_c = C^H A~ C: basis stored in TI, stencil and products in T
+// Returns the number of partial blocks written (partial holds max_blocks + 1 blocks of p x p).
+// *herm set: the partials are in the Hermitian-packed form (FP64 products of the 5-point
+// rows), and launch_herm_fill completes the summed matrix.
 template <typename TI, typename T>
 int launch_galerkin_partial(const cplx<TI>* C, OpGeom g, int p, int split_row, c128* partial, int max_blocks,
-                            cudaStream_t s);
+                            cudaStream_t s, bool* herm = nullptr);
+// A[j][i] = conj(A[i][j]) + A[j][i] for i < j (p x p, row-major)
+void launch_herm_fill(c128* A, int p, cudaStream_t s);
 // In-place QR (classical Gram-Schmidt, two passes) of nq independent Sx x m blocks.
 template <typename T>
 void launch_qr(cplx<T>* const* Y, int nq, int Sx, int m, cplx<T>** dev_ptr_scratch, cudaStream_t s);
