@@ -168,7 +168,7 @@ DFMA_PER_SM_CLK = 2
 # kernel on this workload's shapes (mean of its three launches per step), from the ncu
 # capture summarised in profiles/coarse_batch_helm2d_n1023_k100_L3.md.  To be removed
 # whenever k_coarse_batch changes.
-TRAFFIC_BYTES_PER_LAUNCH = {}
+TRAFFIC_BYTES_PER_LAUNCH = {"coarse_project": 491.7e6}
 
 
 def whole_job_rate(local_ms, units_per_rank, world, device="cuda"):

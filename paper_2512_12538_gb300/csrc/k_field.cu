@@ -3,6 +3,7 @@
 // Sec. 3.1), precision casts and restricted prolongation (Sec. 1), the interface
 // traces B_s A~_s (Sec. 2), the counter-based sketch and the coarse update C y.
 #include <algorithm>
+#include <atomic>
 
 #include "kernels.h"
 
@@ -194,11 +195,27 @@ __global__ void k_residual_cast(const c128* __restrict__ x, const c128* __restri
         }
     }
 }
+// One wave of co-resident blocks (the grid-stride loop takes the rest): a second, partial
+// wave left most SMs idle at the end of the launch.
+template <typename T, bool Q1>
+static int resid_grid(size_t total) {
+    static std::atomic<int> cap[64];
+    const int dev = current_device();
+    int c = cap[dev & 63].load(std::memory_order_relaxed);
+    if (!c) {
+        int nb = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_residual_cast<T, Q1>, 256, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c = std::max(1, std::min(nb, 8)) * std::max(sms, 1);
+        cap[dev & 63].store(c, std::memory_order_relaxed);
+    }
+    return grid_for(total, 256, c);
+}
 template <typename T>
 void launch_residual_cast(const c128* x, const c128* v, c128* y, cplx<T>* yt, OpGeom g, double* part, int* nblk_out,
                           cudaStream_t s, const int* gate) {
     const size_t total = (size_t)g.b * g.Sx;
-    const int grid = grid_for(total, 256, 152 * 8);
+    const int grid = g.q1 ? resid_grid<T, true>(total) : resid_grid<T, false>(total);
     const ResidStop none{nullptr, nullptr, nullptr, 0.0, nullptr, nullptr};
     if (g.q1) k_residual_cast<T, true><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, none);
     else k_residual_cast<T, false><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, gate, none);
@@ -210,7 +227,7 @@ void launch_residual_stop(const c128* x, const c128* v, c128* y, cplx<T>* yt, Op
                           int* ctl, unsigned* ticket, double tol, cudaStream_t s, const int* need,
                           const int* anchor) {
     const size_t total = (size_t)g.b * g.Sx;
-    const int grid = grid_for(total, 256, 152 * 8);
+    const int grid = g.q1 ? resid_grid<T, true>(total) : resid_grid<T, false>(total);
     const ResidStop st{nrm, ctl, ticket, tol, need, anchor};
     if (g.q1) k_residual_cast<T, true><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, st);
     else k_residual_cast<T, false><<<grid, 256, 0, s>>>(x, v, y, yt, g, part, ctl, st);
