@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
         mbar_init(&full[1], 1);
         mbar_init(&done[0], 1);
         mbar_init(&done[1], 1);
-        *abort_flag = 0;
+        abort_flag[0] = abort_flag[1] = abort_flag[2] = 0;
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -277,9 +277,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
             const int s = chunk & 1;
             unsigned char* As = tsm + s * TC_STAGE_BYTES;
             unsigned char* Bs = As + TC_A_BYTES;
-            // This chunk's B operand was requested one chunk ahead (or before the loop),
-            // after this stage's MMAs of two chunks ago had finished: its A tile may
-            // overwrite the stage now.
+            // The stage's previous chunk (two back) must have finished its MMAs before its A
+            // tile is overwritten: every thread waits on that commit itself, so the staging
+            // below runs while thread 0 still issues the previous chunk's MMAs.  (Its B
+            // operand was requested into the stage after the same wait.)  A thread whose
+            // wait runs out raises this iteration's abort word.
+            if (chunk >= 2 && !mbar_wait_bounded(&done[s], ((chunk - 2) >> 1) & 1u, limit > 0 ? limit : 1u)) {
+                atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+                abort_flag[chunk & 1] = 1;
+            }
             // A tile chunk from the registers: rows 2j + c, split and transposed
 #pragma unroll
             for (int u = 0; u < NU; ++u) {
@@ -304,23 +310,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
             else if (tile + (int)gridDim.x < ntiles) load_chunk(tile + gridDim.x, 0);
             fence_async_smem();
             __syncthreads();
+            // Thread 0 writes only the next iteration's abort word after this barrier, so
+            // every thread reads the same value here.
+            if (abort_flag[chunk & 1]) { ok = false; break; }
             if (tid == 0) {
                 if (tc_wait(&full[s], use[s] & 1, limit, err)) {
                     copy_pending[s] = false;
                     tc_fence_after();
-                    const uint32_t a_hi = smem_u32(As), a_lo = a_hi + TC_A_BYTES / 2;
-                    const uint32_t b_hi = smem_u32(Bs), b_lo = b_hi + g.b_bytes / 2;
+                    // descriptors of the stage's operands, advanced by address offsets (the
+                    // 14-bit address field holds every shared-memory offset)
+                    const uint64_t da_hi = smem_desc(smem_u32(As)), da_lo = smem_desc(smem_u32(As) + TC_A_BYTES / 2);
+                    const uint64_t db_hi = smem_desc(smem_u32(Bs)), db_lo = smem_desc(smem_u32(Bs) + g.b_bytes / 2);
                     const uint32_t half = (uint32_t)(g.nb / 8) * 1024u;
                     const int nks = min(4, g.ks - 4 * q);
-                    for (int kk = 0; kk < nks; ++kk) {
-                        const uint32_t ko = (uint32_t)kk * 256u;
-                        for (int h = 0; h < 2; ++h) {
-                            const uint32_t d = tmem + (h ? TC_D1_COL : 0);
-                            const uint32_t bo = h * half + ko;
-                            const uint32_t acc0 = (q > 0 || kk > 0) ? 1u : 0u;
-                            mma_tf32(d, smem_desc(a_hi + ko), smem_desc(b_hi + bo), idesc, acc0);
-                            mma_tf32(d, smem_desc(a_hi + ko), smem_desc(b_lo + bo), idesc, 1u);
-                            mma_tf32(d, smem_desc(a_lo + ko), smem_desc(b_hi + bo), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        if (kk < nks) {
+                            const uint64_t ko = (uint64_t)(kk * 256) >> 4;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const uint32_t d = tmem + (h ? TC_D1_COL : 0);
+                                const uint64_t bo = ((uint64_t)(h * half) >> 4) + ko;
+                                const uint32_t acc0 = (q > 0 || kk > 0) ? 1u : 0u;
+                                mma_tf32(d, da_hi + ko, db_hi + bo, idesc, acc0);
+                                mma_tf32(d, da_hi + ko, db_lo + bo, idesc, 1u);
+                                mma_tf32(d, da_lo + ko, db_hi + bo, idesc, 1u);
+                            }
                         }
                     }
                     mma_commit(&done[s]);
@@ -335,25 +350,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
                     }
                     if (nt < ntiles) {
                         const int s2 = s ^ 1;
-                        if (use[s2] > 0 && !tc_wait(&done[s2], (use[s2] - 1) & 1, limit, err)) *abort_flag = 1;
+                        if (use[s2] > 0 && !tc_wait(&done[s2], (use[s2] - 1) & 1, limit, err))
+                            abort_flag[(chunk + 1) & 1] = 1;
                         else issue_b(nt, nq, s2);
                     }
                 } else {
-                    *abort_flag = 1;   // the bulk copy may still land: drained below
+                    abort_flag[(chunk + 1) & 1] = 1;   // the bulk copy may still land: drained below
                 }
             }
-            __syncthreads();
-            if (*abort_flag) { ok = false; break; }
         }
         if (!ok) break;
         // epilogue: thread 0 waits for the tile's last MMAs; then the lanes 2j, 2j + 1
-        // of each warp pair up
+        // of each warp pair up.  (An abort raised by thread 0 after the last chunk is in
+        // the word of the next iteration.)
         if (tid == 0) {
             const int sl = (chunk - 1) & 1;
-            if (!tc_wait(&done[sl], (use[sl] - 1) & 1, limit, err)) *abort_flag = 1;
+            if (abort_flag[chunk & 1] || !tc_wait(&done[sl], (use[sl] - 1) & 1, limit, err)) abort_flag[2] = 1;
         }
         __syncthreads();
-        if (*abort_flag) { ok = false; break; }
+        if (abort_flag[2]) { ok = false; break; }
         tc_fence_after();
         // the warps w, w + 4, ... share the tensor-memory lanes 32 (w % 4) .. + 31 and take
         // interleaved 16-column groups of the accumulators
