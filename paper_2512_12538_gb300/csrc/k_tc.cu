@@ -19,13 +19,15 @@
 // epilogue pairs the two lanes: Re = rr - ii, Im = ri + ir.
 //
 // Shared-memory operands are K-major without swizzle, in 8-row x 16-byte core matrices:
-// element (row, k) of a 32-wide K chunk at (row / 8) * 1024 + (k / 4) * 128 +
+// element (row, k) of a 16-wide K chunk at (row / 8) * 512 + (k / 4) * 128 +
 // (row % 8) * 16 + (k % 4) * 4 bytes (leading-dimension offset 128 B between core
-// matrices along K, stride offset 1024 B between 8-row groups).  The B operand is laid
+// matrices along K, stride offset 512 B between 8-row groups).  The B operand is laid
 // out that way once per leaf in global memory (tc_prepare_v) and each K chunk reaches
 // shared memory by one bulk copy (TMA engine); the A tile is split and transposed by
-// the threads on its way in.  One CTA per SM (212 KB of shared memory, all 512 tensor-
-// memory columns), persistent over the (leaf, column tile) pairs, two pipeline stages.
+// the threads on its way in.  One CTA per SM (209 KB of shared memory in four pipeline
+// stages, all 512 tensor-memory columns), persistent over the (leaf, column tile) pairs,
+// warp-specialised: sixteen staging warps, one warp issuing the MMAs and one issuing the
+// bulk copies, handing the stages over by mbarriers.
 //
 // Every wait is bounded: a wait that gives up records DEV_TIMEOUT, the CTA stops
 // issuing work, waits (bounded) for its tensor-core operations in flight, frees its
@@ -40,18 +42,24 @@ namespace hh {
 
 namespace {
 
-constexpr int TC_THREADS = 512;          // 16 warps: four per 32-lane quarter of tensor memory
-constexpr int TC_KQ_T = TC_THREADS / 64;  // K quads of a chunk a thread does not stage between its own
+constexpr int TC_STAGERS = 512;          // 16 warps stage A and run the epilogue (four per 32-lane quarter of tensor memory)
+constexpr int TC_THREADS = TC_STAGERS + 64;   // + the MMA-issuer warp and the B-producer warp
+constexpr int TC_ISSUER = TC_STAGERS;         // lane 0 of warp 16
+constexpr int TC_PRODUCER = TC_STAGERS + 32;  // lane 0 of warp 17
 constexpr int TC_COLS = 64;              // complex columns per tile (M = 128 real rows)
-constexpr int TC_KC = 32;                // K per pipeline chunk (4 MMAs of K = 8)
+constexpr int TC_KC = 16;                // K per pipeline chunk (2 MMAs of K = 8)
+constexpr int TC_STAGES = 4;             // pipeline stages (A tile and B operand each)
+constexpr uint32_t TC_SBO = 8u * TC_KC * 4u;   // bytes between 8-row groups of a chunk
 constexpr int TC_NB_MAX = 144;           // N per accumulator (b <= 136 rounded up to 16)
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_D1_COL = 256;           // tensor-memory column of the second accumulator
-constexpr uint32_t TC_A_BYTES = 2u * 128u * TC_KC * 4u;                    // hi + lo: 32 KiB
-constexpr uint32_t TC_B_BYTES_MAX = 2u * 2u * TC_NB_MAX * TC_KC * 4u;      // hi + lo: 72 KiB
+constexpr uint32_t TC_A_BYTES = 2u * 128u * TC_KC * 4u;                    // hi + lo: 16 KiB
+constexpr uint32_t TC_B_BYTES_MAX = 2u * 2u * TC_NB_MAX * TC_KC * 4u;      // hi + lo: 36 KiB
 constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES_MAX;
-constexpr uint32_t TC_SMEM = 2u * TC_STAGE_BYTES + 1024u + 256u;          // + alignment, barriers
+constexpr uint32_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024u + 256u;   // + alignment, barriers
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;                               // polls (~0.3-1 s)
+static_assert(TC_SMEM <= 227u * 1024u, "tensor-core transform stages exceed shared memory");
+static_assert(TC_STAGERS == 64 * (TC_KC / 4) * 2, "one (column, K quad, part) per staging thread");
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
     uint32_t r;
@@ -66,16 +74,16 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) 
 
 // byte offset of element (row, k) inside one K chunk of a K-major operand
 __device__ __forceinline__ uint32_t kmaj_off(int row, int kk) {
-    return (uint32_t)((row >> 3) * 1024 + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4);
+    return (uint32_t)((row >> 3) * (int)TC_SBO + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4);
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle, leading-dimension byte offset
-// 128 (next core matrix along K), stride byte offset 1024 (next 8-row group).
+// 128 (next core matrix along K), stride byte offset TC_SBO (next 8-row group).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((TC_SBO >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;                 // descriptor version of this architecture
     return d;                               // base offset 0, layout: no swizzle
 }
@@ -122,6 +130,23 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, uint32_t
     atomicCAS(err, DEV_OK, DEV_TIMEOUT);
     return false;
 }
+// The pipeline roles' wait: false after `limit` polls (the error word set and the shared
+// abort word raised, so that the other roles stop too) or as soon as another role has raised
+// the abort word.
+__device__ __forceinline__ bool role_wait(uint64_t* bar, uint32_t parity, uint32_t limit, int* err,
+                                          volatile int* abort_word) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_word) return false;
+        if (it > 64) __nanosleep(32);
+    }
+    atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+    *abort_word = 1;
+    return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 }  // namespace
 
@@ -129,14 +154,14 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, uint32_t
 struct TcGeom {
     int nb;      // N per accumulator: b_max rounded up to 16
     int ks;      // K steps of 8: b_max rounded up to 8, over 8
-    int nq;      // K chunks of 32
+    int nq;      // K chunks of TC_KC
     uint32_t b_bytes;   // bytes of one chunk of the B operand (hi + lo)
 };
 HH_HD TcGeom tc_geom(int b_max) {
     TcGeom g;
     g.nb = (b_max + 15) & ~15;
     g.ks = (b_max + 7) / 8;
-    g.nq = (g.ks + 3) / 4;
+    g.nq = (g.ks + TC_KC / 8 - 1) / (TC_KC / 8);
     g.b_bytes = 2u * 2u * (uint32_t)g.nb * TC_KC * 4u;
     return g;
 }
@@ -185,6 +210,21 @@ void launch_tc_prepare_v(const EigTask* d_tasks, int ntasks, int b_max, cudaStre
 // which = 0: Fh = V^T F (input F in node order [b][J], output Fh as fh_col says);
 // which = 1: W = V Fh (input Fh, output W in node order).  The tiles run along the
 // input's contiguous column index p.
+//
+// Warp-specialised pipeline over the CTA's chunks c = 0, 1, ... (stage c % TC_STAGES),
+// with no block barrier inside the loop:
+//   staging warps 0-15: wait until the MMAs of chunk c - TC_STAGES have finished (the
+//       stage is free), split and transpose their part of A(c) into the stage, arrive on
+//       a_full; after a tile's last chunk, wait for its MMAs, read the accumulators out of
+//       tensor memory, write the tile and arrive on tfree;
+//   producer (warp 17, lane 0): wait until the stage is free, bulk-copy B(c) into it
+//       (b_full), up to TC_STAGES chunks ahead of the MMAs;
+//   issuer (warp 16, lane 0): before a tile's first chunk wait for tfree (the previous
+//       tile's accumulators read out), then per chunk wait for a_full and b_full, issue
+//       the MMAs and commit them to done.
+// Every wait is bounded and also ends when another role has raised the abort word; the
+// roles then leave their loops, the issuer waits (bounded) for its MMAs and the producer
+// for its copies, and the tensor memory is freed.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* __restrict__ tasks, int ntasks,
                                                                 int which, int Sx, int nrhs, int b_max,
                                                                 int tiles_per_task, uint32_t limit, int* err,
@@ -194,20 +234,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
     if (gate && *gate) return;
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
     unsigned char* tsm = (unsigned char*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(tsm + 2 * TC_STAGE_BYTES);       // bulk copy of B landed, per stage
-    uint64_t* done = full + 2;                                     // MMAs of a stage finished, per stage
-    uint32_t* tmem_slot = (uint32_t*)(done + 2);
-    int* abort_flag = (int*)(tmem_slot + 1);
+    uint64_t* a_full = (uint64_t*)(tsm + TC_STAGES * TC_STAGE_BYTES);   // A part of a stage staged
+    uint64_t* b_full = a_full + TC_STAGES;                               // B operand of a stage landed
+    uint64_t* done = b_full + TC_STAGES;                                 // MMAs of a stage finished
+    uint64_t* tfree = done + TC_STAGES;                                  // accumulators read out
+    uint32_t* tmem_slot = (uint32_t*)(tfree + 1);
+    volatile int* abort_word = (volatile int*)(tmem_slot + 1);
     const TcGeom g = tc_geom(b_max);
     const int J = Sx * nrhs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lim = limit > 0 ? limit : 1u;
 
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&done[0], 1);
-        mbar_init(&done[1], 1);
-        abort_flag[0] = abort_flag[1] = abort_flag[2] = 0;
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&a_full[s], TC_STAGERS);
+            mbar_init(&b_full[s], 1);
+            mbar_init(&done[s], 1);
+        }
+        mbar_init(tfree, TC_STAGERS);
+        *abort_word = 0;
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -220,195 +265,168 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_transform(const EigTask* _
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    const uint32_t idesc = idesc_tf32(g.nb);
-    uint32_t use[2] = {0u, 0u};     // committed uses of each stage (this CTA)
-    bool copy_pending[2] = {false, false};   // thread 0: a bulk copy issued, not yet seen landed
-    uint32_t chunk = 0;             // chunks issued so far (stage = chunk & 1)
-    bool ok = true;
     const int ntiles = ntasks * tiles_per_task;
+    // the testing form of a wait that runs out (limit 0): the first wait of each role gives up
+    const bool give_up = limit == 0;
 
-    // Only thread 0 waits on the barriers (and issues the MMAs); the others learn the
-    // outcome through the shared abort word after a block barrier, so every thread takes
-    // the same path and the block barriers stay matched.
-    //
-    // Each thread stages column j = tid % 64 of the tile and the K quads kq = tid / 64,
-    // tid / 64 + TC_KQ_T, ...: 8 complex values per chunk, loaded into registers one chunk
-    // ahead (the loads of chunk q + 1, or of the next tile's first chunk, are in flight
-    // while chunk q's MMAs are issued and run).
-    const int jcol = tid & 63, kq0 = tid >> 6;
-    constexpr int NU = TC_KC / 4 / TC_KQ_T;   // K quads a thread stages per chunk
-    c64 pre[NU][4];
-    auto load_chunk = [&](int t, int q) {
-        const EigTask& tq = tasks[t / tiles_per_task];
-        const int p = (t % tiles_per_task) * TC_COLS + jcol;
-        const c64* src = (const c64*)(which == 0 ? tq.F : tq.Fh);
-        const int bb = tq.b;
-#pragma unroll
-        for (int u = 0; u < NU; ++u)
+    if (tid < TC_STAGERS) {
+        // ------------------------------------------------------------ staging warps
+        // part (re or im) of four consecutive K of one column: column tid % 64, K quad
+        // (tid / 64) % 4, part tid / 256; loaded into registers one chunk ahead
+        const int jcol = tid & 63, kq = (tid >> 6) & 3, part = tid >> 8;
+        float pre[4];
+        auto load_chunk = [&](int t, int q) {
+            const EigTask& tq = tasks[t / tiles_per_task];
+            const int p = (t % tiles_per_task) * TC_COLS + jcol;
+            const c64* src = (const c64*)(which == 0 ? tq.F : tq.Fh);
+            const int bb = tq.b;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int k = q * TC_KC + (kq0 + TC_KQ_T * u) * 4 + i;
-                float2 v = make_float2(0.f, 0.f);
-                if (p < J && k < bb) v = __ldg((const float2*)(src + (size_t)k * J + p));
-                pre[u][i] = c64{v.x, v.y};
+                const int k = q * TC_KC + kq * 4 + i;
+                pre[i] = (p < J && k < bb) ? __ldg((const float*)(src + (size_t)k * J + p) + part) : 0.f;
             }
-    };
-    // thread 0: the bulk copy of chunk (t, q)'s B operand into stage s
-    auto issue_b = [&](int t, int q, int s) {
-        const EigTask& tq = tasks[t / tiles_per_task];
-        const unsigned char* src = (const unsigned char*)(which == 0 ? tq.vt_emb : tq.vn_emb);
-        mbar_arrive_expect_tx(&full[s], g.b_bytes);
-        bulk_g2s(tsm + s * TC_STAGE_BYTES + TC_A_BYTES, src + (size_t)q * g.b_bytes, g.b_bytes, &full[s]);
-        copy_pending[s] = true;
-    };
-    if (blockIdx.x < ntiles) {
-        load_chunk(blockIdx.x, 0);
-        if (tid == 0) issue_b(blockIdx.x, 0, 0);
-    }
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const EigTask tk = tasks[tile / tiles_per_task];
-        const int p0 = (tile % tiles_per_task) * TC_COLS;
-        const int b = tk.b;
-        c64* outp = (c64*)(which == 0 ? tk.Fh : tk.W);
-        // x = V x^ keeps rows [w0, w1) (all rows, or the owned rows written into the parent)
-        const int rlo = which == 0 ? 0 : tk.w0, rhi = which == 0 ? b : tk.w1;
-        for (int q = 0; q < g.nq; ++q, ++chunk) {
-            const int s = chunk & 1;
-            unsigned char* As = tsm + s * TC_STAGE_BYTES;
-            unsigned char* Bs = As + TC_A_BYTES;
-            // The stage's previous chunk (two back) must have finished its MMAs before its A
-            // tile is overwritten: every thread waits on that commit itself, so the staging
-            // below runs while thread 0 still issues the previous chunk's MMAs.  (Its B
-            // operand was requested into the stage after the same wait.)  A thread whose
-            // wait runs out raises this iteration's abort word.
-            if (chunk >= 2 && !mbar_wait_bounded(&done[s], ((chunk - 2) >> 1) & 1u, limit > 0 ? limit : 1u)) {
-                atomicCAS(err, DEV_OK, DEV_TIMEOUT);
-                abort_flag[chunk & 1] = 1;
+        };
+        uint32_t c = 0;
+        bool ok = !give_up;
+        if (give_up) {
+            atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+            *abort_word = 1;
+        }
+        if (ok && blockIdx.x < ntiles) load_chunk(blockIdx.x, 0);
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            const EigTask tk = tasks[tile / tiles_per_task];
+            const int p0 = (tile % tiles_per_task) * TC_COLS;
+            const int b = tk.b;
+            c64* outp = (c64*)(which == 0 ? tk.Fh : tk.W);
+            // x = V x^ keeps rows [w0, w1) (all rows, or the owned rows written into the parent)
+            const int rlo = which == 0 ? 0 : tk.w0, rhi = which == 0 ? b : tk.w1;
+            for (int q = 0; q < g.nq; ++q, ++c) {
+                const int s = (int)(c % TC_STAGES);
+                if (c >= TC_STAGES && !role_wait(&done[s], ((c - TC_STAGES) / TC_STAGES) & 1u, lim, err, abort_word)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* As = tsm + s * TC_STAGE_BYTES;
+                uint4 hi, lo;
+                tf32_split(pre[0], hi.x, lo.x);
+                tf32_split(pre[1], hi.y, lo.y);
+                tf32_split(pre[2], hi.z, lo.z);
+                tf32_split(pre[3], hi.w, lo.w);
+                const uint32_t o = kmaj_off(2 * jcol + part, kq * 4);
+                *(uint4*)(As + o) = hi;
+                *(uint4*)(As + TC_A_BYTES / 2 + o) = lo;
+                // the next chunk's loads (this tile's next, or the next tile's first)
+                if (q + 1 < g.nq) load_chunk(tile, q + 1);
+                else if (tile + (int)gridDim.x < ntiles) load_chunk(tile + gridDim.x, 0);
+                fence_async_smem();
+                mbar_arrive(&a_full[s]);
             }
-            // A tile chunk from the registers: rows 2j + c, split and transposed
-#pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                uint4 hr, lr, hm, lm;
-                tf32_split(pre[u][0].re, hr.x, lr.x);
-                tf32_split(pre[u][1].re, hr.y, lr.y);
-                tf32_split(pre[u][2].re, hr.z, lr.z);
-                tf32_split(pre[u][3].re, hr.w, lr.w);
-                tf32_split(pre[u][0].im, hm.x, lm.x);
-                tf32_split(pre[u][1].im, hm.y, lm.y);
-                tf32_split(pre[u][2].im, hm.z, lm.z);
-                tf32_split(pre[u][3].im, hm.w, lm.w);
-                const int kq = kq0 + TC_KQ_T * u;
-                const uint32_t o_re = kmaj_off(2 * jcol, kq * 4), o_im = kmaj_off(2 * jcol + 1, kq * 4);
-                *(uint4*)(As + o_re) = hr;
-                *(uint4*)(As + o_im) = hm;
-                *(uint4*)(As + TC_A_BYTES / 2 + o_re) = lr;
-                *(uint4*)(As + TC_A_BYTES / 2 + o_im) = lm;
+            if (!ok) break;
+            // epilogue: the tile's last MMAs, then the lanes 2j, 2j + 1 of each warp pair up
+            const uint32_t cl = c - 1;
+            if (!role_wait(&done[cl % TC_STAGES], (cl / TC_STAGES) & 1u, lim, err, abort_word)) {
+                ok = false;
+                break;
             }
-            // prefetch the next chunk (this tile's next, or the next tile's first)
-            if (q + 1 < g.nq) load_chunk(tile, q + 1);
-            else if (tile + (int)gridDim.x < ntiles) load_chunk(tile + gridDim.x, 0);
-            fence_async_smem();
-            __syncthreads();
-            // Thread 0 writes only the next iteration's abort word after this barrier, so
-            // every thread reads the same value here.
-            if (abort_flag[chunk & 1]) { ok = false; break; }
-            if (tid == 0) {
-                if (tc_wait(&full[s], use[s] & 1, limit, err)) {
-                    copy_pending[s] = false;
-                    tc_fence_after();
-                    // descriptors of the stage's operands, advanced by address offsets (the
-                    // 14-bit address field holds every shared-memory offset)
-                    const uint64_t da_hi = smem_desc(smem_u32(As)), da_lo = smem_desc(smem_u32(As) + TC_A_BYTES / 2);
-                    const uint64_t db_hi = smem_desc(smem_u32(Bs)), db_lo = smem_desc(smem_u32(Bs) + g.b_bytes / 2);
-                    const uint32_t half = (uint32_t)(g.nb / 8) * 1024u;
-                    const int nks = min(4, g.ks - 4 * q);
+            tc_fence_after();
+            // the warps w, w + 4, ... share the tensor-memory lanes 32 (w % 4) .. + 31 and take
+            // interleaved 16-column groups of the accumulators
+            const int wq = warp & 3, wh = warp >> 2;
+            const int jl = wq * 16 + (lane >> 1);        // complex column of this lane pair
+            const bool even = (lane & 1) == 0;
+            const int p = p0 + jl;
+            size_t col = 0;
+            // which = 0 writes Fh (fh_col of node column p); which = 1 reads Fh along p and
+            // writes the node column p (node order) or (p % Sx) nrhs + p / Sx (line-major Fh)
+            if (p < J)
+                col = which == 0 ? fh_col((size_t)p, Sx, nrhs)
+                                 : (eig_line_major(nrhs) ? (size_t)(p % Sx) * nrhs + p / Sx : (size_t)p);
+            const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+            for (int m0 = 16 * wh; m0 < g.nb; m0 += 16 * (TC_STAGERS / 128)) {
+                float d0[16], d1[16];
+                tmem_ld16(lane_base + (uint32_t)m0, d0);
+                tmem_ld16(lane_base + (uint32_t)(TC_D1_COL + m0), d1);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        if (kk < nks) {
-                            const uint64_t ko = (uint64_t)(kk * 256) >> 4;
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const uint32_t d = tmem + (h ? TC_D1_COL : 0);
-                                const uint64_t bo = ((uint64_t)(h * half) >> 4) + ko;
-                                const uint32_t acc0 = (q > 0 || kk > 0) ? 1u : 0u;
-                                mma_tf32(d, da_hi + ko, db_hi + bo, idesc, acc0);
-                                mma_tf32(d, da_hi + ko, db_lo + bo, idesc, 1u);
-                                mma_tf32(d, da_lo + ko, db_hi + bo, idesc, 1u);
-                            }
-                        }
-                    }
-                    mma_commit(&done[s]);
-                    ++use[s];
-                    // the next chunk's B operand into the other stage, once that stage's
-                    // MMAs (the previous chunk's) have finished reading it: the copy runs
-                    // while the next chunk's A tile is staged
-                    int nt = tile, nq = q + 1;
-                    if (nq == g.nq) {
-                        nt = tile + (int)gridDim.x;
-                        nq = 0;
-                    }
-                    if (nt < ntiles) {
-                        const int s2 = s ^ 1;
-                        if (use[s2] > 0 && !tc_wait(&done[s2], (use[s2] - 1) & 1, limit, err))
-                            abort_flag[(chunk + 1) & 1] = 1;
-                        else issue_b(nt, nq, s2);
-                    }
-                } else {
-                    abort_flag[(chunk + 1) & 1] = 1;   // the bulk copy may still land: drained below
+                for (int t = 0; t < 8; ++t) {
+                    const float v0 = __shfl_xor_sync(0xffffffffu, even ? d0[8 + t] : d0[t], 1);
+                    const float v1 = __shfl_xor_sync(0xffffffffu, even ? d1[8 + t] : d1[t], 1);
+                    const int m = even ? m0 + t : m0 + 8 + t;
+                    c64 o;
+                    if (even) o = c64{d0[t] - v1, d1[t] + v0};          // rr - ii, ri + ir
+                    else o = c64{v0 - d1[8 + t], v1 + d0[8 + t]};
+                    if (p < J && m >= rlo && m < rhi) outp[(size_t)(m - rlo) * J + col] = o;
                 }
             }
+            // the next tile's MMAs may overwrite the accumulators
+            tc_fence_before();
+            mbar_arrive(tfree);
         }
-        if (!ok) break;
-        // epilogue: thread 0 waits for the tile's last MMAs; then the lanes 2j, 2j + 1
-        // of each warp pair up.  (An abort raised by thread 0 after the last chunk is in
-        // the word of the next iteration.)
-        if (tid == 0) {
-            const int sl = (chunk - 1) & 1;
-            if (abort_flag[chunk & 1] || !tc_wait(&done[sl], (use[sl] - 1) & 1, limit, err)) abort_flag[2] = 1;
-        }
-        __syncthreads();
-        if (abort_flag[2]) { ok = false; break; }
-        tc_fence_after();
-        // the warps w, w + 4, ... share the tensor-memory lanes 32 (w % 4) .. + 31 and take
-        // interleaved 16-column groups of the accumulators
-        const int wq = warp & 3, wh = warp >> 2;
-        const int jl = wq * 16 + (lane >> 1);        // complex column of this lane pair
-        const bool even = (lane & 1) == 0;
-        const int p = p0 + jl;
-        size_t col = 0;
-        // which = 0 writes Fh (fh_col of node column p); which = 1 reads Fh along p and
-        // writes the node column p (node order) or (p % Sx) nrhs + p / Sx (line-major Fh)
-        if (p < J)
-            col = which == 0 ? fh_col((size_t)p, Sx, nrhs)
-                             : (eig_line_major(nrhs) ? (size_t)(p % Sx) * nrhs + p / Sx : (size_t)p);
-        const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
-        for (int m0 = 16 * wh; m0 < g.nb; m0 += 16 * (TC_THREADS / 128)) {
-            float d0[16], d1[16];
-            tmem_ld16(lane_base + (uint32_t)m0, d0);
-            tmem_ld16(lane_base + (uint32_t)(TC_D1_COL + m0), d1);
+    } else if (tid == TC_ISSUER) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_tf32(g.nb);
+        uint32_t c = 0, ntile = 0;
+        bool ok = !give_up;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++ntile) {
+            if (ntile > 0 && !role_wait(tfree, (ntile - 1) & 1u, lim, err, abort_word)) break;
+            for (int q = 0; q < g.nq; ++q, ++c) {
+                const int s = (int)(c % TC_STAGES);
+                const uint32_t par = (c / TC_STAGES) & 1u;
+                if (!role_wait(&a_full[s], par, lim, err, abort_word) ||
+                    !role_wait(&b_full[s], par, lim, err, abort_word)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                unsigned char* As = tsm + s * TC_STAGE_BYTES;
+                const uint32_t a_addr = smem_u32(As), b_addr = a_addr + TC_A_BYTES;
+                // descriptors advanced by address offsets (the 14-bit address field holds
+                // every shared-memory offset)
+                const uint64_t da_hi = smem_desc(a_addr), da_lo = smem_desc(a_addr + TC_A_BYTES / 2);
+                const uint64_t db_hi = smem_desc(b_addr), db_lo = smem_desc(b_addr + g.b_bytes / 2);
+                const uint64_t half = (uint64_t)((g.nb / 8) * TC_SBO) >> 4;
+                const int nks = min(TC_KC / 8, g.ks - (TC_KC / 8) * q);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const float v0 = __shfl_xor_sync(0xffffffffu, even ? d0[8 + t] : d0[t], 1);
-                const float v1 = __shfl_xor_sync(0xffffffffu, even ? d1[8 + t] : d1[t], 1);
-                const int m = even ? m0 + t : m0 + 8 + t;
-                c64 o;
-                if (even) o = c64{d0[t] - v1, d1[t] + v0};          // rr - ii, ri + ir
-                else o = c64{v0 - d1[8 + t], v1 + d0[8 + t]};
-                if (p < J && m >= rlo && m < rhi) outp[(size_t)(m - rlo) * J + col] = o;
+                for (int kk = 0; kk < TC_KC / 8; ++kk) {
+                    if (kk < nks) {
+                        const uint64_t ko = (uint64_t)(kk * 256) >> 4;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t d = tmem + (h ? TC_D1_COL : 0);
+                            const uint64_t bo = (h ? half : 0) + ko;
+                            const uint32_t acc0 = (q > 0 || kk > 0) ? 1u : 0u;
+                            mma_tf32(d, da_hi + ko, db_hi + bo, idesc, acc0);
+                            mma_tf32(d, da_hi + ko, db_lo + bo, idesc, 1u);
+                            mma_tf32(d, da_lo + ko, db_hi + bo, idesc, 1u);
+                        }
+                    }
+                }
+                mma_commit(&done[s]);
             }
         }
-        // the next tile's MMAs overwrite the accumulators
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-    }
-    // drain after a failed wait: no tensor-core operation or bulk copy may be in flight
-    // when the block exits and its memory is freed (bounded as well)
-    if (!ok && tid == 0) {
-        for (int s = 0; s < 2; ++s) {
-            if (use[s] > 0) mbar_wait_bounded(&done[s], (use[s] - 1) & 1, TC_WAIT_LIMIT);
-            if (copy_pending[s]) mbar_wait_bounded(&full[s], use[s] & 1, TC_WAIT_LIMIT);
+        // no MMA may be in flight when the block's tensor memory is freed: they complete in
+        // order, so the last commit covers them all
+        if (c > 0) mbar_wait_bounded(&done[(c - 1) % TC_STAGES], ((c - 1) / TC_STAGES) & 1u, TC_WAIT_LIMIT);
+    } else if (tid == TC_PRODUCER) {
+        // ------------------------------------------------------------ B producer
+        uint32_t c = 0;
+        bool ok = !give_up;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            const EigTask& tq = tasks[tile / tiles_per_task];
+            const unsigned char* src = (const unsigned char*)(which == 0 ? tq.vt_emb : tq.vn_emb);
+            for (int q = 0; q < g.nq; ++q, ++c) {
+                const int s = (int)(c % TC_STAGES);
+                if (c >= TC_STAGES && !role_wait(&done[s], ((c - TC_STAGES) / TC_STAGES) & 1u, lim, err, abort_word)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&b_full[s], g.b_bytes);
+                bulk_g2s(tsm + s * TC_STAGE_BYTES + TC_A_BYTES, src + (size_t)q * g.b_bytes, g.b_bytes, &b_full[s]);
+            }
+        }
+        // no bulk copy may be in flight when the block exits: wait for the last ones issued
+        for (uint32_t k = 0; k < (uint32_t)TC_STAGES && k < c; ++k) {
+            const uint32_t ck = c - 1 - k;
+            mbar_wait_bounded(&b_full[ck % TC_STAGES], (ck / TC_STAGES) & 1u, TC_WAIT_LIMIT);
         }
     }
     tc_fence_before();
