@@ -531,15 +531,16 @@ __global__ void __launch_bounds__(256) k_coarse_updn(const cplx<TC>* __restrict_
     }
 }
 // The complex64 form of the same update with the basis staged and the output tile
-// written whole: a block of UPD_SP threads owns UPD_SP consecutive points (their rows of W
-// are one contiguous span); it stages the points' basis values, 32 columns at a time, with
+// written whole: a block owns UPD_SP consecutive points (their rows of W are one contiguous
+// span), one thread per point and chunk of 16 right-hand sides (up to four chunks at once);
+// it stages the points' basis values, 32 columns at a time, with
 // asynchronous 8-byte copies (the whole group in flight at once), runs every chunk of 16
 // right-hand sides from shared memory into a shared output tile, and adds the tile to W
 // with coalesced loads and stores.  (Per-thread row updates of W left partial sectors that
 // the memory system wrote back several times over.)  A block whose points straddle the
 // split stages both halves in turn (the vanishing half is stored as zeros).
 static constexpr int UPD_SP = 64;
-__global__ void __launch_bounds__(UPD_SP * 2) k_coarse_updn_s(const c64* __restrict__ C, const c128* __restrict__ y,
+__global__ void __launch_bounds__(UPD_SP * 4) k_coarse_updn_s(const c64* __restrict__ C, const c128* __restrict__ y,
                                                               c64* __restrict__ W, size_t N, int p, int nc,
                                                               long long split_pt) {
     extern __shared__ __align__(16) unsigned char usm[];
@@ -613,7 +614,10 @@ void launch_coarse_updn(const cplx<TC>* C, const c128* y, cplx<TW>* W, size_t N,
             static std::atomic<unsigned long long> attr{0};
             smem_limit_once(attr, k_coarse_updn_s, 200 * 1024);
             const int grid = blocks_for(N, UPD_SP, 152 * 16);
-            k_coarse_updn_s<<<grid, UPD_SP * 2, sm, s>>>(C, y, W, N, p, nc, split_pt);
+            // one group of UPD_SP threads per chunk of 16 right-hand sides (up to four), so
+            // that every thread has the same number of chunks
+            const int groups = std::min(4, ncp / 16);
+            k_coarse_updn_s<<<grid, UPD_SP * groups, sm, s>>>(C, y, W, N, p, nc, split_pt);
             note_launch();
             return;
         }
